@@ -1,0 +1,205 @@
+/*
+ * fc.h -- C-ABI of libfc, a single-GPU (GB300, sm_103a) geometric multigrid
+ * solver for finite cell Stokes problems with the restricted additive (RA)
+ * patch smoother of Saberi & Vogel, "A restricted additive smoother for
+ * finite cell flow problems".
+ *
+ * Problem (paper Sec. 2): -eta lap u + grad p = f, div u = 0 in the fluid
+ * Omega, embedded in the box Omega_e; the fictitious part (inside obstacles)
+ * is weighted by alpha << 1 (eq. stokes_weak_fcm); no-slip on the obstacle
+ * boundary is imposed weakly by the symmetric Nitsche method; equal-order
+ * Q1-Q1 elements with the local L2 pressure-projection stabilisation
+ * (eq. stabilization_l2) on a uniform background grid; strong Dirichlet data
+ * on box faces per boundary preset.  The discrete system is L x = b
+ * (Sec. 3, eq. linear_system).
+ *
+ * Conventions for every entry point:
+ *  - Vectors are caller-owned DEVICE pointers to float64 in node-interleaved
+ *    layout: node (i, j, k) with i fastest, then the d velocity components,
+ *    then the pressure: x[((k*(ny+1) + j)*(nx+1) + i)*(d+1) + c].
+ *  - Levels are numbered as in the paper (Sec. 3): 1 = coarsest, L = finest.
+ *  - All device work is enqueued on the stream given to fc_setup and is
+ *    asynchronous unless the entry point says it synchronises.
+ *  - Errors are returned as fc_status codes; fc_last_error(h) gives a
+ *    message.  No entry point aborts the process.  A handle stays valid
+ *    after FC_ERR_NOT_CONVERGED and after argument errors.
+ */
+#ifndef FC_H
+#define FC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fc_handle_s* fc_handle; /* opaque; owns all device memory it allocates */
+
+typedef enum {
+  FC_OK = 0,
+  FC_ERR_INVALID = 1,        /* bad argument or unsupported combination */
+  FC_ERR_OOM = 2,            /* device allocation failed */
+  FC_ERR_CUDA = 3,           /* a CUDA call or kernel failed */
+  FC_ERR_NOT_CONVERGED = 4,  /* fc_solve stopped at maxit above rtol */
+  FC_ERR_SINGULAR = 5,       /* a local or coarse LU met a zero pivot */
+  FC_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  FC_WARN_FP64_FALLBACK = 100 /* informational: some patches kept in FP64 */
+} fc_status;
+
+/* Patch cache policy (Sec. 3.1.2). */
+typedef enum {
+  FC_CACHE_INVERSE = 0, /* store the 1+d owned rows of L_i^{-1} */
+  FC_CACHE_MATRIX = 1,  /* store the block factorisation of L_i; solve per apply */
+  FC_CACHE_NONE = 2     /* gather L_i from the operator, factor and solve per apply */
+} fc_cache;
+
+/* Storage/arithmetic of the cached patch rows (cache_inverse only). */
+typedef enum {
+  FC_PREC_FP64 = 0, /* float64 rows, float64 arithmetic */
+  FC_PREC_FP32 = 1, /* float32 rows, float32 accumulation */
+  FC_PREC_BF16 = 2, /* bfloat16 rows, float32 accumulation */
+  FC_PREC_DF64 = 3  /* rows and residual as float32 pairs (hi + lo), pair arithmetic */
+} fc_prec;
+
+/* Uniform background grid of the finest level: n cells per direction on the
+ * box [lo, hi].  dim is 2 or 3; entries of n/lo/hi beyond dim are ignored. */
+typedef struct {
+  int dim;
+  int n[3];
+  double lo[3], hi[3];
+} fc_grid;
+
+/* Obstacle (fictitious region).  type 0: circle (2D) or sphere (3D) of
+ * radius r[0] around c; type 1: ellipse (2D) with semi-axes r[0] along the
+ * direction rot = (cos theta, sin theta) and r[1] across it.  The level set
+ * is phi = max over shapes, phi > 0 inside an obstacle (Sec. 2, alpha). */
+typedef struct {
+  int type;
+  double c[3];
+  double r[3];
+  double rot[2];
+} fc_shape;
+
+typedef struct {
+  int nshapes;
+  const fc_shape* shapes; /* host array, copied by fc_setup */
+} fc_levelset;
+
+typedef struct {
+  double eta;          /* viscosity (Sec. 4: 1e-3) */
+  double nitsche_beta; /* Nitsche lambda = beta * eta / h_min (default 100) */
+  double omega;        /* smoother damping (Sec. 4: 0.8) */
+  int nu_pre, nu_post; /* V-cycle smoothing steps */
+  int quad_depth;      /* cut-cell quadtree/octree depth k */
+  fc_cache cache;
+  fc_prec prec;
+  int fgmres_restart;  /* FGMRES(m) restart length (default 30) */
+  int bc_preset;       /* 0: channel (inflow x=lo, walls y(,z)), 1: porous (walls y(,z)), 2: none */
+  double ubar;         /* mean inflow speed of the channel preset (eq. cf_inflow) */
+  int force_kind;      /* 0: constant force[]; 1: (f0 sin(pi x), f1 cos(pi y));
+                          2: (f0 sin(pi y)[sin(pi z)], 0, 0); 3: (-f0 pi/2 sin(pi x/2), 0, 0) */
+  double force[3];
+} fc_options;
+
+/* Fill defaults: eta 1e-3, beta 100, omega 0.8, V(2,2), depth 4 (2D) / 3 (3D)
+ * is left to the caller (quad_depth = 4), cache_inverse, FP64, restart 30,
+ * channel preset, ubar 0.3, constant zero force. */
+fc_status fc_options_default(fc_options* o);
+
+/* Build the hierarchy of `depth` levels (paper Sec. 3, Algorithm 1 on a
+ * uniform grid: each coarser level halves n), discretise every level on the
+ * GPU (cut-cell quadrature, element matrices, operator), build the patch
+ * cache of every level above the coarsest (Sec. 3.1.2) and the dense coarse
+ * solve (Sec. 3).  n must be divisible by 2^(depth-1).  `cuda_stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Synchronises.
+ * Errors: FC_ERR_INVALID (arguments), FC_ERR_OOM, FC_ERR_CUDA,
+ * FC_ERR_SINGULAR (a local or coarse block could not be factored). */
+fc_status fc_setup(fc_handle* h, const fc_grid* g, const fc_levelset* ls, double alpha, int depth,
+                   const fc_options* o, void* cuda_stream);
+
+/* b_dev <- right-hand side of the finest level: the load f(v) and the
+ * lifted strong Dirichlet data (eq. stokes_disc_weak_fcm_2), b = w on
+ * constrained DoFs.  b_dev holds ndof(L) doubles. */
+fc_status fc_rhs(fc_handle h, double* b_dev);
+
+/* r_dev <- b_dev - L x_dev on `level` (FP64).  Constrained DoFs have
+ * identity rows. */
+fc_status fc_residual(fc_handle h, int level, const double* x_dev, const double* b_dev,
+                      double* r_dev);
+
+/* y_dev <- L x_dev on `level` (FP64). */
+fc_status fc_apply(fc_handle h, int level, const double* x_dev, double* y_dev);
+
+/* `nsweeps` RA smoother sweeps on `level` (eq. iteration with eq. smoother):
+ * r = b - L x over all DoFs, then for every pressure node i,
+ * x[owned DoFs of node i] += omega (L_i^{-1} R_i r)[owned]; constrained DoFs
+ * take b.  Uses the handle's cache policy and precision.  level >= 2
+ * (the coarsest level has no patch cache; use fc_coarse_solve). */
+fc_status fc_smooth(fc_handle h, int level, double* x_dev, const double* b_dev, int nsweeps);
+
+/* b_coarse <- R r_fine from `level` to `level-1` (eq. restriction_op with the
+ * transfer T the identity on one GPU; R = P^T, Q1 full weighting on every
+ * component); constrained coarse DoFs are set to zero. */
+fc_status fc_restrict(fc_handle h, int level, const double* r_fine, double* b_coarse);
+
+/* x_fine += P e_coarse from `level-1` to `level` (P = Q1 interpolation);
+ * constrained fine DoFs are left unchanged. */
+fc_status fc_prolong_add(fc_handle h, int level, const double* e_coarse, double* x_fine);
+
+/* x_dev <- L_1^{-1} b_dev on the coarsest level (direct solve, Sec. 3). */
+fc_status fc_coarse_solve(fc_handle h, const double* b_dev, double* x_dev);
+
+/* One V(nu_pre, nu_post) cycle on the finest level: x_dev is updated in
+ * place (coarse levels start from zero). */
+fc_status fc_vcycle(fc_handle h, double* x_dev, const double* b_dev);
+
+/* FGMRES(restart), right-preconditioned with one V-cycle, FP64 outer
+ * iteration (Sec. 4 remark on Krylov methods).  x_dev holds x0 on entry and
+ * the solution on exit.  Stops when ||b - L x||_2 <= rtol ||b||_2 (checked
+ * on the true residual) or after maxit preconditioner applications.
+ * *iters = preconditioner applications, *relres = true relative residual.
+ * Synchronises.  Returns FC_ERR_NOT_CONVERGED if rtol was not reached. */
+fc_status fc_solve(fc_handle h, const double* b_dev, double* x_dev, double rtol, int maxit,
+                   int* iters, double* relres);
+
+/* As fc_solve, with HOST buffers (pinned memory recommended): copies b to
+ * the device, solves from x0 = x_host, copies x back.  Synchronises. */
+fc_status fc_solve_host(fc_handle h, const double* b_host, double* x_host, double rtol, int maxit,
+                        int* iters, double* relres);
+
+/* Sizes of `level`: DoFs, patches (= pressure nodes) and device bytes by
+ * part: [0] operator, [1] patch cache, [2] vectors/workspace, [3] coarse
+ * solve, [4] setup temporaries peak, [5..7] reserved. Any pointer may be
+ * NULL. */
+fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch,
+                  size_t* bytes_by_part);
+
+/* Copy the cached rows of patch `node` on `level` to host memory (cache
+ * inverse only): rows[(d+1)][nslot] in float64 whatever the storage
+ * precision, nslot = 5^d d + 3^d; slot order: velocity nodes of the 5^d box
+ * around the node (x fastest) with the component inner, then the pressure
+ * nodes of the 3^d box; absent DoFs have zero coefficients.  Synchronises. */
+fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_host);
+
+/* Upper bound of the device bytes fc_setup would hold for this problem. */
+size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o);
+
+/* Per-kernel device time of the patch apply, the residual and the whole
+ * sweep, collected with CUDA events on the handle's stream while enabled.
+ * kind: 0 patch apply, 1 residual (smoother), 2 V-cycle, 3 patch-cache build.
+ * Reading synchronises and resets the counters of that kind. */
+fc_status fc_profile_enable(fc_handle h, int on);
+fc_status fc_profile_read(fc_handle h, int kind, long long* launches, double* total_ms,
+                          double* bytes_per_launch);
+
+/* Wait for all work enqueued by the handle. */
+fc_status fc_sync(fc_handle h);
+
+const char* fc_last_error(fc_handle h);
+fc_status fc_destroy(fc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FC_H */

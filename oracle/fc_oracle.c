@@ -606,8 +606,9 @@ long or_ncell(const or_level* L) { return L->ncell; }
 long or_nbpoints(const or_level* L) { return L->nbp; }
 
 /* element data of one cell, exported for the tests */
-void or_cell_element(const or_level* L, long cell, double* A, double* B, double* C, double* f,
-                     double* stats) {
+int or_cell_element(const or_level* L, long cell, double* A, double* B, double* C, double* f,
+                    double* stats) {
+  if (cell < 0 || cell >= L->ncell) return -1;
   or_elem e;
   compute_elem(L, cell, &e);
   int nloc = 1 << L->dim;
@@ -623,6 +624,7 @@ void or_cell_element(const or_level* L, long cell, double* A, double* B, double*
   stats[1] = e.boundary_measure;
   stats[2] = e.nvol;
   stats[3] = e.nbnd;
+  return 0;
 }
 
 void or_precompute_cells(or_level* L) {

@@ -57,6 +57,7 @@ def _load():
         getattr(lib, fn).argtypes = [vp]
     lib.or_phi.restype = d
     lib.or_phi.argtypes = [vp, P(d)]
+    lib.or_cell_element.restype = i
     lib.or_cell_element.argtypes = [vp, l, P(d), P(d), P(d), P(d), P(d)]
     lib.or_precompute_cells.argtypes = [vp]
     lib.or_dof_rows.argtypes = [vp, l, P(C.c_long), P(d), P(d)]
@@ -169,7 +170,8 @@ class Level:
         nl = 1 << self.dim
         A = np.zeros((nl, nl)); B = np.zeros((self.dim, nl, nl)); Cm = np.zeros((nl, nl))
         f = np.zeros((self.dim, nl)); st = np.zeros(4)
-        self.lib.or_cell_element(self.h, int(cell), _p(A), _p(B), _p(Cm), _p(f), _p(st))
+        if self.lib.or_cell_element(self.h, int(cell), _p(A), _p(B), _p(Cm), _p(f), _p(st)) != 0:
+            raise IndexError(f"cell {cell} out of range")
         return {"A": A, "B": B, "C": Cm, "f": f, "fluid_volume": st[0],
                 "boundary_measure": st[1], "nvol": int(st[2]), "nbnd": int(st[3])}
 

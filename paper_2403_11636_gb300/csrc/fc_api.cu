@@ -1,0 +1,732 @@
+// fc_api.cu -- the C-ABI of libfc: handle lifecycle, GPU setup of the
+// multigrid hierarchy, smoother / V-cycle / FGMRES drivers, profiling.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "fc_internal.cuh"
+
+using namespace fc;
+
+namespace {
+
+constexpr int kSmallScalars = 8;
+
+fc_status fail(fc_handle h, fc_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+fc_status cuda_fail(fc_handle h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return fail(h, e == cudaErrorMemoryAllocation ? FC_ERR_OOM : FC_ERR_CUDA, m);
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(fc_handle h, T** p, size_t count, int part) {
+  size_t bytes = count * sizeof(T);
+  if (bytes == 0) bytes = sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaSuccess && part >= 0) h->bytes[part] += bytes;
+  return e;
+}
+
+long long small_len(int m) { return (long long)(m + 1) * m + m + m + (m + 1) + m + kSmallScalars; }
+long long small_sc(int m) { return (long long)(m + 1) * m + m + m + (m + 1) + m; }
+
+size_t coef_elem_bytes(fc_prec p) {
+  switch (p) {
+    case FC_PREC_FP64: return 8;
+    case FC_PREC_FP32: return 4;
+    case FC_PREC_BF16: return 2;
+    case FC_PREC_DF64: return 8;
+  }
+  return 8;
+}
+
+bool need_r32(fc_prec p) { return p != FC_PREC_FP64; }
+
+// ---- profiling helpers --------------------------------------------------
+cudaEvent_t prof_event(fc_handle h) {
+  if (!h->prof.pool.empty()) {
+    cudaEvent_t e = h->prof.pool.back();
+    h->prof.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct ProfScope {
+  fc_handle h;
+  int kind;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(fc_handle hh, int k, double b) : h(hh), kind(k), bytes(b) {
+    if (h->prof.on) {
+      a = prof_event(h);
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = prof_event(h);
+      cudaEventRecord(b, h->stream);
+      h->prof.recs.push_back({a, b, kind, bytes});
+    }
+  }
+};
+
+}  // namespace
+
+namespace {
+
+__global__ void count_active_kernel(LevelGeom g, const unsigned char* __restrict__ mask,
+                                    unsigned long long* __restrict__ out) {
+  // number of active (in-grid, unconstrained) patch DoFs summed over patches
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.nnodes) return;
+  int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
+               g.dim == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
+  unsigned long long cnt = 0;
+  int r5 = g.dim == 3 ? 5 : 1;
+  for (int dz = 0; dz < r5; ++dz)
+    for (int dy = 0; dy < 5; ++dy)
+      for (int dx = 0; dx < 5; ++dx) {
+        int b0 = ia[0] + dx - 2, b1 = ia[1] + dy - 2, b2 = g.dim == 3 ? ia[2] + dz - 2 : 0;
+        if (b0 < 0 || b0 > g.n[0] || b1 < 0 || b1 > g.n[1]) continue;
+        if (g.dim == 3 && (b2 < 0 || b2 > g.n[2])) continue;
+        if (!(mask[b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2)] & 1)) cnt += g.dim;
+      }
+  int r3 = g.dim == 3 ? 3 : 1;
+  for (int dz = 0; dz < r3; ++dz)
+    for (int dy = 0; dy < 3; ++dy)
+      for (int dx = 0; dx < 3; ++dx) {
+        int b0 = ia[0] + dx - 1, b1 = ia[1] + dy - 1, b2 = g.dim == 3 ? ia[2] + dz - 1 : 0;
+        if (b0 < 0 || b0 > g.n[0] || b1 < 0 || b1 > g.n[1]) continue;
+        if (g.dim == 3 && (b2 < 0 || b2 > g.n[2])) continue;
+        cnt += 1;
+      }
+  atomicAdd(out, cnt);
+}
+
+__global__ void sqrt_kernel(double* p) { p[0] = sqrt(p[0]); }
+
+}  // namespace
+
+namespace {
+
+fc_status check_err(fc_handle h) {
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (e & kErrSingularCoarse) return fail(h, FC_ERR_SINGULAR, "coarse operator is singular");
+  if (e & kErrSingularPatch) return fail(h, FC_ERR_SINGULAR, "a patch block is singular");
+  if (e & kErrTooManyShapes) return fail(h, FC_ERR_INVALID, "more than 64 obstacles meet one cell");
+  if (e & kErrBadIndex) return fail(h, FC_ERR_CUDA, "device index check failed");
+  return FC_OK;
+}
+
+LevelGeom make_geom(const fc_grid* g, int nshape, const Shape* d_shapes, double alpha,
+                    const fc_options* o, int coarsen) {
+  LevelGeom G;
+  memset(&G, 0, sizeof(G));
+  G.dim = g->dim;
+  G.nd = g->dim + 1;
+  G.hmin = 1e300;
+  G.ncell = 1;
+  G.nnodes = 1;
+  for (int k = 0; k < 3; ++k) {
+    if (k < g->dim) {
+      G.n[k] = g->n[k] >> coarsen;
+      G.nn[k] = G.n[k] + 1;
+      G.lo[k] = g->lo[k];
+      G.hi[k] = g->hi[k];
+      G.h[k] = (g->hi[k] - g->lo[k]) / (double)G.n[k];
+      if (G.h[k] < G.hmin) G.hmin = G.h[k];
+      G.ncell *= G.n[k];
+      G.nnodes *= G.nn[k];
+    } else {
+      G.n[k] = 1;
+      G.nn[k] = 1;
+      G.lo[k] = 0.0;
+      G.hi[k] = 1.0;
+      G.h[k] = 1.0;
+    }
+  }
+  G.ndof = G.nnodes * G.nd;
+  G.nshape = nshape;
+  G.shapes = d_shapes;
+  G.alpha = alpha;
+  G.eta = o->eta;
+  G.lambda = o->nitsche_beta * o->eta / G.hmin;
+  G.ubar = o->ubar;
+  G.qdepth = o->quad_depth;
+  G.preset = o->bc_preset;
+  G.force_kind = o->force_kind;
+  for (int k = 0; k < 3; ++k) G.force[k] = o->force[k];
+  return G;
+}
+
+}  // namespace
+
+namespace {
+
+double level_apply_bytes(fc_handle h, int li) {
+  const Level& L = h->lev[li];
+  double cb = (double)coef_elem_bytes(h->opt.prec);
+  double rb = (h->opt.prec == FC_PREC_FP32 || h->opt.prec == FC_PREC_BF16) ? 4.0 : 8.0;
+  double act = (double)L.active_slots;
+  return act * L.g.nd * cb + (double)L.g.nnodes * L.g.nd * (rb + 16.0);
+}
+
+// residual into the smoother's input buffer (format per precision)
+fc_status smoother_residual(fc_handle h, int li, const double* x, const double* b) {
+  Level& L = h->lev[li];
+  ProfScope ps(h, 1, 0.0);
+  if (h->opt.cache == FC_CACHE_INVERSE && h->opt.prec == FC_PREC_DF64) {
+    CK(launch_residual_df(L.g, L.st, L.mask, x, b, L.rpad32, h->stream));
+  } else if (h->opt.cache == FC_CACHE_INVERSE && (h->opt.prec == FC_PREC_FP32 || h->opt.prec == FC_PREC_BF16)) {
+    CK(launch_residual_f32(L.g, L.st, L.mask, x, b, L.rpad32, h->stream));
+  } else {
+    CK(launch_residual(L.g, L.st, L.mask, x, b, nullptr, L.rpad, h->stream));
+  }
+  return FC_OK;
+}
+
+fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nsweeps) {
+  Level& L = h->lev[li];
+  for (int s = 0; s < nsweeps; ++s) {
+    fc_status st = smoother_residual(h, li, x, b);
+    if (st != FC_OK) return st;
+    if (h->opt.cache == FC_CACHE_INVERSE) {
+      ProfScope ps(h, 0, level_apply_bytes(h, li));
+      CK(launch_patch_apply(L.g, h->opt.prec, L.coef, L.mask, L.rpad, L.rpad32, h->opt.omega, x, h->stream));
+    } else if (h->opt.cache == FC_CACHE_MATRIX) {
+      ProfScope ps(h, 0, (double)L.fac_bytes);
+      CK(launch_factor_apply(L.g, L.fac, L.fpiv, L.mask, L.rpad, h->opt.omega, x, h->stream));
+    } else {
+      ProfScope ps(h, 0, 0.0);
+      CK(launch_patch_build(L.g, L.st, L.mask, 2, h->opt.omega, nullptr, nullptr, nullptr, L.rpad, x,
+                            h->d_err, h->stream));
+    }
+  }
+  return FC_OK;
+}
+
+fc_status vcycle_level(fc_handle h, int li, double* x, const double* b) {
+  Level& L = h->lev[li];
+  if (li == 0) {
+    CK(launch_dense_gemv(h->coarse_n, h->coarse_inv, b, x, h->stream));
+    return FC_OK;
+  }
+  Level& C = h->lev[li - 1];
+  fc_status st = smooth_level(h, li, x, b, h->opt.nu_pre);
+  if (st != FC_OK) return st;
+  CK(launch_residual(L.g, L.st, L.mask, x, b, L.r, nullptr, h->stream));
+  CK(launch_restrict(L.g, C.g, C.mask, L.r, C.b, h->stream));
+  CK(cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.ndof, h->stream));
+  st = vcycle_level(h, li - 1, C.x, C.b);
+  if (st != FC_OK) return st;
+  CK(launch_prolong_add(L.g, C.g, L.mask, C.x, x, h->stream));
+  return smooth_level(h, li, x, b, h->opt.nu_post);
+}
+
+fc_status level_ok(fc_handle h, int level, int min_level) {
+  if (!h) return FC_ERR_INVALID;
+  if (level < min_level || level > h->nlev) return fail(h, FC_ERR_INVALID, "level out of range");
+  return FC_OK;
+}
+
+fc_status read_scalar(fc_handle h, const double* dptr, double* out) {
+  CK(cudaMemcpyAsync(h->host_small, dptr, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *out = h->host_small[0];
+  return FC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fc_status fc_options_default(fc_options* o) {
+  if (!o) return FC_ERR_INVALID;
+  memset(o, 0, sizeof(*o));
+  o->eta = 1e-3;
+  o->nitsche_beta = 100.0;
+  o->omega = 0.8;
+  o->nu_pre = 2;
+  o->nu_post = 2;
+  o->quad_depth = 4;
+  o->cache = FC_CACHE_INVERSE;
+  o->prec = FC_PREC_FP64;
+  o->fgmres_restart = 30;
+  o->bc_preset = 0;
+  o->ubar = 0.3;
+  o->force_kind = 0;
+  return FC_OK;
+}
+
+size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o) {
+  if (!g || !o || (g->dim != 2 && g->dim != 3) || depth < 1) return 0;
+  size_t total = 0;
+  int dim = g->dim, nd = dim + 1, nb = dim == 3 ? 27 : 9;
+  for (int l = 0; l < depth; ++l) {
+    int c = depth - 1 - l;
+    long long nodes = 1, pad = 1, cells = 1;
+    for (int k = 0; k < dim; ++k) {
+      long long n = g->n[k] >> c;
+      nodes *= n + 1;
+      pad *= n + 5;
+      cells *= n;
+    }
+    total += (size_t)nodes * nb * (2 * dim + 2) * 8 + nodes + (size_t)nodes * nd * 8;  // st, mask, wfix
+    total += (size_t)nodes * nd * 8 * 3 + (size_t)pad * nd * 8 + (size_t)pad * nd * 8;   // vectors
+    if (l > 0) {
+      if (o->cache == FC_CACHE_INVERSE)
+        total += (size_t)nodes * nslot(dim) * nd * coef_elem_bytes(o->prec);
+      else if (o->cache == FC_CACHE_MATRIX)
+        total += (size_t)nodes * (factor_doubles(dim) * 8 + factor_ints(dim) * 4);
+    }
+  }
+  long long fine_nodes = 1;
+  for (int k = 0; k < dim; ++k) fine_nodes *= g->n[k] + 1;
+  int m = o->fgmres_restart > 0 ? o->fgmres_restart : 30;
+  total += (size_t)fine_nodes * nd * 8 * (2 * m + 4);
+  return total;
+}
+
+fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, double alpha, int depth,
+                   const fc_options* o, void* cuda_stream) {
+  if (!out || !g || !o) return FC_ERR_INVALID;
+  *out = nullptr;
+  fc_handle h = new (std::nothrow) fc_handle_s();
+  if (!h) return FC_ERR_OOM;
+  *out = h;
+  h->opt = *o;
+  h->alpha = alpha;
+  h->stream = (cudaStream_t)cuda_stream;
+  // ---- validation
+  if (g->dim != 2 && g->dim != 3) return fail(h, FC_ERR_INVALID, "dim must be 2 or 3");
+  if (depth < 1 || depth > kMaxLevels) return fail(h, FC_ERR_INVALID, "depth out of range");
+  for (int k = 0; k < g->dim; ++k) {
+    if (g->n[k] < 1 || (g->n[k] % (1 << (depth - 1))) != 0)
+      return fail(h, FC_ERR_INVALID, "n must be a positive multiple of 2^(depth-1)");
+    if (!(g->hi[k] > g->lo[k])) return fail(h, FC_ERR_INVALID, "empty box");
+  }
+  if (!(alpha > 0.0) || !(o->eta > 0.0) || !(o->omega > 0.0) || o->nu_pre < 0 || o->nu_post < 0 ||
+      o->quad_depth < 0 || o->quad_depth > 6 || o->fgmres_restart < 1 || o->fgmres_restart > 256 ||
+      o->bc_preset < 0 || o->bc_preset > 2 || o->force_kind < 0 || o->force_kind > 3 ||
+      !(o->nitsche_beta >= 0.0))
+    return fail(h, FC_ERR_INVALID, "invalid options");
+  if (o->cache < FC_CACHE_INVERSE || o->cache > FC_CACHE_NONE || o->prec < FC_PREC_FP64 || o->prec > FC_PREC_DF64)
+    return fail(h, FC_ERR_INVALID, "invalid cache policy or precision");
+  if (o->prec != FC_PREC_FP64 && o->cache != FC_CACHE_INVERSE)
+    return fail(h, FC_ERR_INVALID, "reduced-precision storage applies to cache_inverse only");
+  int nshape = ls ? ls->nshapes : 0;
+  if (nshape < 0 || (nshape > 0 && !ls->shapes)) return fail(h, FC_ERR_INVALID, "bad level set");
+  std::vector<Shape> hs(nshape);
+  for (int s = 0; s < nshape; ++s) {
+    const fc_shape& in = ls->shapes[s];
+    if (in.type != 0 && !(in.type == 1 && g->dim == 2)) return fail(h, FC_ERR_INVALID, "unsupported shape type");
+    if (!(in.r[0] > 0.0) || (in.type == 1 && !(in.r[1] > 0.0))) return fail(h, FC_ERR_INVALID, "bad radius");
+    Shape& S = hs[s];
+    S.type = in.type;
+    for (int k = 0; k < 3; ++k) { S.c[k] = in.c[k]; S.r[k] = in.r[k]; }
+    S.rot[0] = in.type == 1 ? in.rot[0] : 1.0;
+    S.rot[1] = in.type == 1 ? in.rot[1] : 0.0;
+    S.bbr = in.type == 0 ? in.r[0] : std::max(in.r[0], in.r[1]);
+  }
+  h->dim = g->dim;
+  h->nlev = depth;
+  h->restart = o->fgmres_restart;
+  h->nshape = nshape;
+
+  CK(dalloc(h, &h->d_err, 1, 2));
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
+  CK(dalloc(h, &h->d_shapes, (size_t)std::max(nshape, 1), 0));
+  if (nshape) CK(cudaMemcpyAsync(h->d_shapes, hs.data(), sizeof(Shape) * nshape, cudaMemcpyHostToDevice, h->stream));
+  unsigned long long* d_count = nullptr;
+  CK(dalloc(h, &d_count, 1, -1));
+
+  const int dim = g->dim, nd = dim + 1, nb = dim == 3 ? 27 : 9, nl = 1 << dim;
+  for (int li = 0; li < depth; ++li) {
+    Level& L = h->lev[li];
+    L.g = make_geom(g, nshape, h->d_shapes, alpha, o, depth - 1 - li);
+    const LevelGeom& G = L.g;
+    // ---- element data and operator
+    double *eA = nullptr, *eB = nullptr, *eF = nullptr;
+    CK(dalloc(h, &eA, (size_t)G.ncell * nl * nl, -1));
+    CK(dalloc(h, &eB, (size_t)G.ncell * dim * nl * nl, -1));
+    CK(dalloc(h, &eF, (size_t)G.ncell * dim * nl, -1));
+    size_t tmp_bytes = (size_t)G.ncell * (nl * nl * (1 + dim) + dim * nl) * 8;
+    h->bytes[4] = std::max(h->bytes[4], tmp_bytes);
+    CK(launch_cell_elements(G, eA, eB, eF, nullptr, h->d_err, h->stream));
+    CK(dalloc(h, &L.st, (size_t)G.nnodes * nb * spn(dim), 0));
+    CK(dalloc(h, &L.mask, (size_t)G.nnodes, 0));
+    CK(dalloc(h, &L.wfix, (size_t)G.ndof, 0));
+    CK(launch_assemble(G, eA, eB, L.st, h->stream));
+    CK(launch_masks(G, L.mask, L.wfix, h->stream));
+    // ---- vectors
+    long long padn = pad_nodes(G);
+    CK(dalloc(h, &L.x, (size_t)G.ndof, 2));
+    CK(dalloc(h, &L.b, (size_t)G.ndof, 2));
+    CK(dalloc(h, &L.r, (size_t)G.ndof, 2));
+    CK(dalloc(h, &L.rpad, (size_t)padn * nd, 2));
+    CK(cudaMemsetAsync(L.rpad, 0, sizeof(double) * padn * nd, h->stream));
+    if (need_r32(o->prec)) {
+      CK(dalloc(h, &L.rpad32, (size_t)padn * nd * 2, 2));
+      CK(cudaMemsetAsync(L.rpad32, 0, sizeof(float) * padn * nd * 2, h->stream));
+    }
+    if (li == depth - 1) {
+      // finest right-hand side kept in L.b until fc_rhs; L.b is not used as a
+      // V-cycle buffer on the finest level
+      CK(launch_rhs(G, eF, L.st, L.mask, L.wfix, L.b, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(eA);
+    cudaFree(eB);
+    cudaFree(eF);
+    fc_status st = check_err(h);
+    if (st != FC_OK) return st;
+    // ---- patch cache (every level above the coarsest)
+    if (li > 0) {
+      CK(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), h->stream));
+      count_active_kernel<<<(unsigned)((G.nnodes + 255) / 256), 256, 0, h->stream>>>(G, L.mask, d_count);
+      CK(cudaGetLastError());
+      unsigned long long cnt = 0;
+      CK(cudaMemcpyAsync(&cnt, d_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      L.active_slots = cnt;
+      if (o->cache == FC_CACHE_INVERSE) {
+        size_t n = (size_t)G.nnodes * nslot(dim) * nd;
+        double* c64 = nullptr;
+        CK(dalloc(h, &c64, n, o->prec == FC_PREC_FP64 ? 1 : -1));
+        {
+          ProfScope ps(h, 3, 0.0);
+          CK(launch_patch_build(G, L.st, L.mask, 0, o->omega, c64, nullptr, nullptr, nullptr, nullptr,
+                                h->d_err, h->stream));
+        }
+        if (o->prec == FC_PREC_FP64) {
+          L.coef = c64;
+          L.coef_bytes = n * 8;
+        } else {
+          size_t eb = coef_elem_bytes(o->prec);
+          void* cv = nullptr;
+          CK(cudaMalloc(&cv, n * eb));
+          h->bytes[1] += n * eb;
+          CK(launch_convert_rows(G, o->prec, c64, cv, h->stream));
+          CK(cudaStreamSynchronize(h->stream));
+          cudaFree(c64);
+          L.coef = cv;
+          L.coef_bytes = n * eb;
+        }
+      } else if (o->cache == FC_CACHE_MATRIX) {
+        CK(dalloc(h, &L.fac, (size_t)G.nnodes * factor_doubles(dim), 1));
+        CK(dalloc(h, &L.fpiv, (size_t)G.nnodes * factor_ints(dim), 1));
+        L.fac_bytes = (size_t)G.nnodes * (factor_doubles(dim) * 8 + factor_ints(dim) * 4);
+        ProfScope ps(h, 3, 0.0);
+        CK(launch_patch_build(G, L.st, L.mask, 1, o->omega, nullptr, L.fac, L.fpiv, nullptr, nullptr,
+                              h->d_err, h->stream));
+      }
+      CK(cudaStreamSynchronize(h->stream));
+      st = check_err(h);
+      if (st != FC_OK) return st;
+    }
+  }
+  cudaFree(d_count);
+  // ---- coarse solve
+  {
+    Level& C = h->lev[0];
+    long long n = C.g.ndof;
+    if (n > 4096) return fail(h, FC_ERR_INVALID, "coarsest level too large for the dense solve; increase depth");
+    h->coarse_n = (int)n;
+    double* work = nullptr;
+    double* dsc = nullptr;
+    int* piv = nullptr;
+    CK(dalloc(h, &work, (size_t)n * n, -1));
+    CK(dalloc(h, &dsc, (size_t)n, -1));
+    CK(dalloc(h, &piv, (size_t)n, -1));
+    CK(dalloc(h, &h->coarse_inv, (size_t)n * n, 3));
+    CK(launch_coarse_factor(C.g, C.st, C.mask, work, h->coarse_inv, piv, dsc, h->d_err, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFree(work);
+    cudaFree(dsc);
+    cudaFree(piv);
+    fc_status st = check_err(h);
+    if (st != FC_OK) return st;
+  }
+  // ---- FGMRES workspace
+  {
+    long long n = h->lev[depth - 1].g.ndof;
+    int m = h->restart;
+    CK(dalloc(h, &h->V, (size_t)n * (m + 1), 2));
+    CK(dalloc(h, &h->Z, (size_t)n * m, 2));
+    CK(dalloc(h, &h->w, (size_t)n, 2));
+    CK(dalloc(h, &h->red, 1024, 2));
+    CK(dalloc(h, &h->small, (size_t)small_len(m), 2));
+    CK(dalloc(h, &h->bh, (size_t)n, 2));
+    CK(dalloc(h, &h->xh, (size_t)n, 2));
+    CK(cudaMallocHost((void**)&h->host_small, sizeof(double) * (size_t)small_len(m)));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return FC_OK;
+}
+
+fc_status fc_rhs(fc_handle h, double* b_dev) {
+  if (!h || !b_dev) return FC_ERR_INVALID;
+  Level& L = h->lev[h->nlev - 1];
+  CK(cudaMemcpyAsync(b_dev, L.b, sizeof(double) * L.g.ndof, cudaMemcpyDeviceToDevice, h->stream));
+  return FC_OK;
+}
+
+fc_status fc_residual(fc_handle h, int level, const double* x, const double* b, double* r) {
+  fc_status st = level_ok(h, level, 1);
+  if (st != FC_OK) return st;
+  if (!x || !b || !r) return fail(h, FC_ERR_INVALID, "null vector");
+  Level& L = h->lev[level - 1];
+  CK(launch_residual(L.g, L.st, L.mask, x, b, r, nullptr, h->stream));
+  return FC_OK;
+}
+
+fc_status fc_apply(fc_handle h, int level, const double* x, double* y) {
+  fc_status st = level_ok(h, level, 1);
+  if (st != FC_OK) return st;
+  if (!x || !y) return fail(h, FC_ERR_INVALID, "null vector");
+  Level& L = h->lev[level - 1];
+  CK(launch_residual(L.g, L.st, L.mask, x, nullptr, y, nullptr, h->stream));
+  return FC_OK;
+}
+
+fc_status fc_smooth(fc_handle h, int level, double* x, const double* b, int nsweeps) {
+  fc_status st = level_ok(h, level, 2);
+  if (st != FC_OK) return st;
+  if (!x || !b || nsweeps < 0) return fail(h, FC_ERR_INVALID, "bad smoother arguments");
+  return smooth_level(h, level - 1, x, b, nsweeps);
+}
+
+fc_status fc_restrict(fc_handle h, int level, const double* rf, double* bc) {
+  fc_status st = level_ok(h, level, 2);
+  if (st != FC_OK) return st;
+  if (!rf || !bc) return fail(h, FC_ERR_INVALID, "null vector");
+  CK(launch_restrict(h->lev[level - 1].g, h->lev[level - 2].g, h->lev[level - 2].mask, rf, bc, h->stream));
+  return FC_OK;
+}
+
+fc_status fc_prolong_add(fc_handle h, int level, const double* ec, double* xf) {
+  fc_status st = level_ok(h, level, 2);
+  if (st != FC_OK) return st;
+  if (!ec || !xf) return fail(h, FC_ERR_INVALID, "null vector");
+  CK(launch_prolong_add(h->lev[level - 1].g, h->lev[level - 2].g, h->lev[level - 1].mask, ec, xf, h->stream));
+  return FC_OK;
+}
+
+fc_status fc_coarse_solve(fc_handle h, const double* b, double* x) {
+  if (!h || !b || !x) return FC_ERR_INVALID;
+  CK(launch_dense_gemv(h->coarse_n, h->coarse_inv, b, x, h->stream));
+  return FC_OK;
+}
+
+fc_status fc_vcycle(fc_handle h, double* x, const double* b) {
+  if (!h || !x || !b) return FC_ERR_INVALID;
+  ProfScope ps(h, 2, 0.0);
+  return vcycle_level(h, h->nlev - 1, x, b);
+}
+
+fc_status fc_solve(fc_handle h, const double* b, double* x, double rtol, int maxit, int* iters,
+                   double* relres) {
+  if (!h || !b || !x || !(rtol > 0.0) || maxit < 0) return h ? fail(h, FC_ERR_INVALID, "bad solve arguments") : FC_ERR_INVALID;
+  Level& F = h->lev[h->nlev - 1];
+  const long long n = F.g.ndof;
+  const int m = h->restart;
+  cudaStream_t s = h->stream;
+  double* H = h->small;
+  double* g = H + (long long)(m + 1) * m + m + m;
+  double* sc = H + small_sc(m);
+  double bn2 = 0.0;
+  CK(launch_dot(n, b, b, h->red, sc + 1, s));
+  fc_status st = read_scalar(h, sc + 1, &bn2);
+  if (st != FC_OK) return st;
+  double bn = sqrt(bn2);
+  int its = 0;
+  double rel = 0.0;
+  if (bn == 0.0) {
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    CK(cudaStreamSynchronize(s));
+    if (iters) *iters = 0;
+    if (relres) *relres = 0.0;
+    return FC_OK;
+  }
+  for (;;) {
+    CK(launch_residual(F.g, F.st, F.mask, x, b, h->w, nullptr, s));
+    double beta2 = 0.0;
+    CK(launch_dot(n, h->w, h->w, h->red, sc + 1, s));
+    st = read_scalar(h, sc + 1, &beta2);
+    if (st != FC_OK) return st;
+    double beta = sqrt(beta2);
+    rel = beta / bn;
+    if (beta <= rtol * bn || its >= maxit) break;
+    // g = (beta, 0, ...); V_0 = w / beta
+    for (int t = 0; t <= m; ++t) h->host_small[t] = t == 0 ? beta : 0.0;
+    CK(cudaMemcpyAsync(g, h->host_small, sizeof(double) * (m + 1), cudaMemcpyHostToDevice, s));
+    CK(launch_scale_copy(n, g, 0, 1, h->w, h->V, s));
+    int k = 0;
+    for (int j = 0; j < m && its < maxit; ++j) {
+      double* Vj = h->V + (long long)j * n;
+      double* Zj = h->Z + (long long)j * n;
+      CK(cudaMemsetAsync(Zj, 0, sizeof(double) * n, s));
+      {
+        ProfScope ps(h, 2, 0.0);
+        st = vcycle_level(h, h->nlev - 1, Zj, Vj);
+        if (st != FC_OK) return st;
+      }
+      its++;
+      CK(launch_residual(F.g, F.st, F.mask, Zj, nullptr, h->w, nullptr, s));
+      for (int i = 0; i <= j; ++i) {
+        double* hij = H + (long long)i * m + j;
+        CK(launch_dot(n, h->w, h->V + (long long)i * n, h->red, hij, s));
+        CK(launch_mgs_step(n, h->w, h->V + (long long)i * n, hij, s));
+      }
+      double* hn = H + (long long)(j + 1) * m + j;
+      CK(launch_dot(n, h->w, h->w, h->red, hn, s));
+      sqrt_kernel<<<1, 1, 0, s>>>(hn);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(sc + 2, hn, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(launch_scale_copy(n, hn, 0, 1, h->w, h->V + (long long)(j + 1) * n, s));
+      CK(launch_givens(H, m, j, bn, s));
+      CK(cudaMemcpyAsync(h->host_small, sc, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      double est = h->host_small[0], hnv = h->host_small[2];
+      k = j + 1;
+      if (est <= rtol || hnv == 0.0) break;
+    }
+    CK(launch_update_x(n, k, m, H, h->Z, x, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  if (iters) *iters = its;
+  if (relres) *relres = rel;
+  if (rel > rtol) return fail(h, FC_ERR_NOT_CONVERGED, "FGMRES reached maxit above rtol");
+  return FC_OK;
+}
+
+fc_status fc_solve_host(fc_handle h, const double* b_host, double* x_host, double rtol, int maxit,
+                        int* iters, double* relres) {
+  if (!h || !b_host || !x_host) return FC_ERR_INVALID;
+  long long n = h->lev[h->nlev - 1].g.ndof;
+  CK(cudaMemcpyAsync(h->bh, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->xh, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+  fc_status st = fc_solve(h, h->bh, h->xh, rtol, maxit, iters, relres);
+  if (st != FC_OK && st != FC_ERR_NOT_CONVERGED) return st;
+  CK(cudaMemcpyAsync(x_host, h->xh, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return st;
+}
+
+fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch, size_t* bytes_by_part) {
+  fc_status st = level_ok(h, level, 1);
+  if (st != FC_OK) return st;
+  const Level& L = h->lev[level - 1];
+  if (ndof) *ndof = L.g.ndof;
+  if (npatch) *npatch = level >= 2 ? L.g.nnodes : 0;
+  if (bytes_by_part)
+    for (int k = 0; k < 8; ++k) bytes_by_part[k] = h->bytes[k];
+  return FC_OK;
+}
+
+fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_host) {
+  fc_status st = level_ok(h, level, 2);
+  if (st != FC_OK) return st;
+  const Level& L = h->lev[level - 1];
+  if (!rows_host || node < 0 || node >= L.g.nnodes) return fail(h, FC_ERR_INVALID, "bad patch");
+  if (h->opt.cache != FC_CACHE_INVERSE || !L.coef) return fail(h, FC_ERR_INVALID, "no cached rows");
+  const int ns = nslot(h->dim), nd = h->dim + 1;
+  const size_t cnt = (size_t)ns * nd;
+  const size_t eb = coef_elem_bytes(h->opt.prec);
+  std::vector<unsigned char> raw(cnt * eb);
+  CK(cudaMemcpyAsync(raw.data(), (const char*)L.coef + (size_t)node * cnt * eb, cnt * eb,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int j = 0; j < ns; ++j)
+    for (int k = 0; k < nd; ++k) {
+      size_t t = (size_t)j * nd + k;
+      double v = 0.0;
+      if (h->opt.prec == FC_PREC_FP64) memcpy(&v, raw.data() + t * 8, 8);
+      else if (h->opt.prec == FC_PREC_FP32) { float f; memcpy(&f, raw.data() + t * 4, 4); v = f; }
+      else if (h->opt.prec == FC_PREC_BF16) {
+        unsigned short u; memcpy(&u, raw.data() + t * 2, 2);
+        unsigned int w = (unsigned int)u << 16; float f; memcpy(&f, &w, 4); v = f;
+      } else { float f2[2]; memcpy(f2, raw.data() + t * 8, 8); v = (double)f2[0] + (double)f2[1]; }
+      rows_host[(size_t)k * ns + j] = v;
+    }
+  return FC_OK;
+}
+
+fc_status fc_profile_enable(fc_handle h, int on) {
+  if (!h) return FC_ERR_INVALID;
+  h->prof.on = on != 0;
+  return FC_OK;
+}
+
+fc_status fc_profile_read(fc_handle h, int kind, long long* launches, double* total_ms,
+                          double* bytes_per_launch) {
+  if (!h) return FC_ERR_INVALID;
+  CK(cudaStreamSynchronize(h->stream));
+  long long cnt = 0;
+  double ms = 0.0, bytes = 0.0;
+  std::vector<Profile::Rec> keep;
+  for (auto& r : h->prof.recs) {
+    if (r.kind != kind) { keep.push_back(r); continue; }
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ms += t;
+    bytes += r.bytes;
+    cnt++;
+    h->prof.pool.push_back(r.a);
+    h->prof.pool.push_back(r.b);
+  }
+  h->prof.recs.swap(keep);
+  if (launches) *launches = cnt;
+  if (total_ms) *total_ms = ms;
+  if (bytes_per_launch) *bytes_per_launch = cnt ? bytes / cnt : 0.0;
+  return FC_OK;
+}
+
+fc_status fc_sync(fc_handle h) {
+  if (!h) return FC_ERR_INVALID;
+  CK(cudaStreamSynchronize(h->stream));
+  return FC_OK;
+}
+
+const char* fc_last_error(fc_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+fc_status fc_destroy(fc_handle h) {
+  if (!h) return FC_ERR_INVALID;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (int l = 0; l < kMaxLevels; ++l) {
+    Level& L = h->lev[l];
+    cudaFree(L.st); cudaFree(L.mask); cudaFree(L.wfix); cudaFree(L.coef); cudaFree(L.fac); cudaFree(L.fpiv);
+    cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); cudaFree(L.rpad); cudaFree(L.rpad32);
+  }
+  cudaFree(h->d_shapes); cudaFree(h->d_err); cudaFree(h->coarse_inv);
+  cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->red); cudaFree(h->small);
+  cudaFree(h->bh); cudaFree(h->xh);
+  if (h->host_small) cudaFreeHost(h->host_small);
+  for (auto& r : h->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : h->prof.pool) cudaEventDestroy(e);
+  delete h;
+  return FC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,189 @@
+// fc_assemble.cu -- global operator L and right-hand side b (paper Sec. 3,
+// eq. linear_system) from the element data.
+//
+// The operator is kept as a compressed node stencil: for node a and each of
+// its 3^d neighbours b the values A (velocity-velocity, equal for every
+// component), B_c (row (a,c), column p_b), T_c (row p_a, column (b,c)) and
+// C (pressure-pressure), summed over the cells that contain both nodes in
+// the order of the 2^d cells around a.  C comes from the closed form of the
+// stabilisation c(q,p) = -(1/eta)(q - Pi0 q, p - Pi0 p) on an axis-aligned
+// cell (eq. stabilization_l2): -(1/eta)(M_ab - |K| / 4^d), M the Q1 mass.
+// Strong Dirichlet DoFs are not baked in; the node masks turn their rows
+// into identity rows and their columns into right-hand-side lifting.
+#include "fc_internal.cuh"
+
+namespace fc {
+
+namespace {
+
+template <int DIM>
+__global__ void assemble_kernel(LevelGeom g, const double* __restrict__ eA,
+                                const double* __restrict__ eB, double* __restrict__ st) {
+  constexpr int NL = 1 << DIM, NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2;
+  long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= g.nnodes * NB) return;
+  long long node = tid % g.nnodes;
+  int nb = (int)(tid / g.nnodes);
+  int ia[3] = {(int)(node % g.nn[0]), (int)((node / g.nn[0]) % g.nn[1]),
+               DIM == 3 ? (int)(node / ((long long)g.nn[0] * g.nn[1])) : 0};
+  int off[3] = {nb % 3 - 1, (nb / 3) % 3 - 1, DIM == 3 ? nb / 9 - 1 : 0};
+  double vA = 0.0, vB[3] = {0, 0, 0}, vT[3] = {0, 0, 0}, vC = 0.0;
+  // closed-form stabilisation block
+  double vol = 1.0;
+  for (int k = 0; k < DIM; ++k) vol = vol * g.h[k];
+  for (int cc = 0; cc < NL; ++cc) {
+    int ic[3] = {0, 0, 0};
+    bool inside = true;
+    for (int k = 0; k < DIM; ++k) {
+      ic[k] = ia[k] - 1 + ((cc >> k) & 1);
+      if (ic[k] < 0 || ic[k] >= g.n[k]) inside = false;
+    }
+    if (!inside) continue;
+    int la = 0, lb = 0;
+    bool shared = true;
+    for (int k = 0; k < DIM; ++k) {
+      la |= (ia[k] - ic[k]) << k;
+      int d = ia[k] + off[k] - ic[k];
+      if (d < 0 || d > 1) shared = false;
+      lb |= (d & 1) << k;
+    }
+    if (!shared) continue;
+    long long cell = ic[0] + (long long)g.n[0] * (ic[1] + (long long)g.n[1] * ic[2]);
+    const double* A = eA + cell * NL * NL;
+    const double* B = eB + cell * DIM * NL * NL;
+    vA = vA + A[la * NL + lb];
+    for (int c = 0; c < DIM; ++c) {
+      vB[c] = vB[c] + B[(c * NL + la) * NL + lb];
+      vT[c] = vT[c] + B[(c * NL + lb) * NL + la];
+    }
+    double m = 1.0;
+    for (int k = 0; k < DIM; ++k) m = m * (((la >> k) & 1) == ((lb >> k) & 1) ? 1.0 / 3.0 : 1.0 / 6.0);
+    double quarter = 1.0;
+    for (int k = 0; k < DIM; ++k) quarter = quarter * 0.25;
+    vC = vC + (-(1.0 / g.eta) * (vol * m - vol * quarter));
+  }
+  long long base = (long long)nb * SP;
+  st[(base + 0) * g.nnodes + node] = vA;
+  for (int c = 0; c < DIM; ++c) {
+    st[(base + 1 + c) * g.nnodes + node] = vB[c];
+    st[(base + 1 + DIM + c) * g.nnodes + node] = vT[c];
+  }
+  st[(base + 1 + 2 * DIM) * g.nnodes + node] = vC;
+}
+
+// Dirichlet data per boundary preset: 0 channel (inflow at x = lo with the
+// parabolic profile of eq. cf_inflow, no-slip walls on the y (and z) faces),
+// 1 porous (no-slip on the y (and z) faces), 2 none.  All velocity
+// components of a node are constrained together.
+__global__ void mask_kernel(LevelGeom g, unsigned char* __restrict__ mask, double* __restrict__ wfix) {
+  long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nnodes) return;
+  int i = (int)(node % g.nn[0]), j = (int)((node / g.nn[0]) % g.nn[1]);
+  int k = g.dim == 3 ? (int)(node / ((long long)g.nn[0] * g.nn[1])) : 0;
+  bool wall = (j == 0 || j == g.n[1]);
+  if (g.dim == 3) wall = wall || k == 0 || k == g.n[2];
+  bool fixed = false;
+  double w0 = 0.0;
+  if (g.preset == 0) {
+    bool inflow = (i == 0);
+    fixed = wall || inflow;
+    if (!wall && inflow) {
+      double y = g.lo[1] + (double)j * g.h[1];
+      double H = g.hi[1] - g.lo[1];
+      double s = (y - g.lo[1]) / H;
+      double v = 4.0 * g.ubar * s * (1.0 - s);
+      if (g.dim == 3) {
+        double z = g.lo[2] + (double)k * g.h[2];
+        double t = (z - g.lo[2]) / (g.hi[2] - g.lo[2]);
+        v = v * 4.0 * t * (1.0 - t);
+      }
+      w0 = v;
+    }
+  } else if (g.preset == 1) {
+    fixed = wall;
+  }
+  unsigned char mk = 0;
+  if (fixed)
+    for (int c = 0; c < g.dim; ++c) mk |= (unsigned char)(1u << c);
+  mask[node] = mk;
+  for (int c = 0; c < g.nd; ++c) wfix[node * g.nd + c] = (fixed && c == 0) ? w0 : 0.0;
+}
+
+// b = f gathered from the cells around each node, minus the lifted
+// constrained columns; b = w on constrained DoFs.
+template <int DIM>
+__global__ void rhs_kernel(LevelGeom g, const double* __restrict__ eF, const double* __restrict__ st,
+                           const unsigned char* __restrict__ mask, const double* __restrict__ wfix,
+                           double* __restrict__ b) {
+  constexpr int NL = 1 << DIM, NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
+  long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nnodes) return;
+  int ia[3] = {(int)(node % g.nn[0]), (int)((node / g.nn[0]) % g.nn[1]),
+               DIM == 3 ? (int)(node / ((long long)g.nn[0] * g.nn[1])) : 0};
+  double f[DIM];
+  for (int c = 0; c < DIM; ++c) f[c] = 0.0;
+  for (int cc = 0; cc < NL; ++cc) {
+    int ic[3] = {0, 0, 0};
+    bool inside = true;
+    for (int k = 0; k < DIM; ++k) {
+      ic[k] = ia[k] - 1 + ((cc >> k) & 1);
+      if (ic[k] < 0 || ic[k] >= g.n[k]) inside = false;
+    }
+    if (!inside) continue;
+    int la = 0;
+    for (int k = 0; k < DIM; ++k) la |= (ia[k] - ic[k]) << k;
+    long long cell = ic[0] + (long long)g.n[0] * (ic[1] + (long long)g.n[1] * ic[2]);
+    for (int c = 0; c < DIM; ++c) f[c] = f[c] + eF[cell * DIM * NL + c * NL + la];
+  }
+  unsigned char ma = mask[node];
+  for (int ca = 0; ca < ND; ++ca) {
+    if (ca < DIM && ((ma >> ca) & 1)) {
+      b[node * ND + ca] = wfix[node * ND + ca];
+      continue;
+    }
+    double rhs = ca < DIM ? f[ca] : 0.0;
+    for (int nb = 0; nb < NB; ++nb) {
+      int ib[3] = {ia[0] + nb % 3 - 1, ia[1] + (nb / 3) % 3 - 1, DIM == 3 ? ia[2] + nb / 9 - 1 : 0};
+      bool inside = true;
+      for (int k = 0; k < DIM; ++k)
+        if (ib[k] < 0 || ib[k] > g.n[k]) inside = false;
+      if (!inside) continue;
+      long long bn = ib[0] + (long long)g.nn[0] * (ib[1] + (long long)g.nn[1] * ib[2]);
+      unsigned char mb = mask[bn];
+      for (int cb = 0; cb < DIM; ++cb) {
+        if (!((mb >> cb) & 1)) continue;
+        double v;
+        if (ca < DIM) v = (ca == cb) ? st[((long long)nb * SP + 0) * g.nnodes + node] : 0.0;
+        else v = st[((long long)nb * SP + 1 + DIM + cb) * g.nnodes + node];
+        rhs = rhs - v * wfix[bn * ND + cb];
+      }
+    }
+    b[node * ND + ca] = rhs;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_assemble(const LevelGeom& g, const double* eA, const double* eB, double* st,
+                            cudaStream_t s) {
+  long long n = g.nnodes * (g.dim == 3 ? 27 : 9);
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (g.dim == 2) assemble_kernel<2><<<blocks, 256, 0, s>>>(g, eA, eB, st);
+  else assemble_kernel<3><<<blocks, 256, 0, s>>>(g, eA, eB, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_masks(const LevelGeom& g, unsigned char* mask, double* wfix, cudaStream_t s) {
+  mask_kernel<<<(unsigned)((g.nnodes + 255) / 256), 256, 0, s>>>(g, mask, wfix);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rhs(const LevelGeom& g, const double* eF, const double* st,
+                       const unsigned char* mask, const double* wfix, double* b, cudaStream_t s) {
+  unsigned blocks = (unsigned)((g.nnodes + 127) / 128);
+  if (g.dim == 2) rhs_kernel<2><<<blocks, 128, 0, s>>>(g, eF, st, mask, wfix, b);
+  else rhs_kernel<3><<<blocks, 128, 0, s>>>(g, eF, st, mask, wfix, b);
+  return cudaGetLastError();
+}
+
+}  // namespace fc

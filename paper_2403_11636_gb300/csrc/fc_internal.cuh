@@ -1,0 +1,182 @@
+// fc_internal.cuh -- shared declarations of the libfc translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fc.h"
+
+namespace fc {
+
+constexpr int kMaxLevels = 12;
+constexpr int kMaxShapesPerCell = 64;
+
+// Device-side error word bits (set by kernels, read back at sync points).
+enum DevErr : unsigned {
+  kErrTooManyShapes = 1u,
+  kErrSingularPatch = 2u,
+  kErrSingularCoarse = 4u,
+  kErrBadIndex = 8u,
+};
+
+struct Shape {
+  int type;
+  double c[3], r[3], rot[2];
+  double bbr;  // bounding half-width (radius or max semi-axis)
+};
+
+// Geometry and discretisation parameters of one level (passed by value).
+struct LevelGeom {
+  int dim, nd;         // nd = dim + 1 DoFs per node
+  int n[3], nn[3];     // cells / nodes per direction (1 beyond dim)
+  double lo[3], hi[3], h[3], hmin;
+  long long ncell, nnodes, ndof;
+  int nshape;
+  const Shape* shapes;  // device
+  double alpha, eta, lambda, ubar;
+  int qdepth, preset, force_kind;
+  double force[3];
+};
+
+// Compressed operator stencil: for node a and neighbour offset nb (3^d,
+// lexicographic, x fastest) the values [A, B_0..B_{d-1}, T_0..T_{d-1}, C]
+// (SPN = 2d + 2 per pair), stored structure-of-arrays:
+// st[(nb * SPN + e) * nnodes + a].  A: velocity-velocity (same for every
+// component), B_c: row (a, c) col (b, p), T_c: row (a, p) col (b, c),
+// C: pressure-pressure.  Constrained DoFs are handled with the node masks.
+inline __host__ __device__ int spn(int dim) { return 2 * dim + 2; }
+inline __host__ __device__ int nbr_count(int dim) { return dim == 3 ? 27 : 9; }
+
+// Padded vector with a zero halo of two nodes on each side (for the patch
+// gathers): node (i,j,k) -> ((k+2)*(ny+5) + (j+2))*(nx+5) + (i+2).
+inline __host__ __device__ long long pad_node(const LevelGeom& g, int i, int j, int k) {
+  long long px = g.nn[0] + 4, py = g.nn[1] + 4;
+  int kk = g.dim == 3 ? k + 2 : 0;
+  return ((long long)kk * py + (j + 2)) * px + (i + 2);
+}
+inline long long pad_nodes(const LevelGeom& g) {
+  long long px = g.nn[0] + 4, py = g.nn[1] + 4, pz = g.dim == 3 ? g.nn[2] + 4 : 1;
+  return px * py * pz;
+}
+
+// Slot layout of the cached rows: nslot = 5^d * d + 3^d.
+inline __host__ __device__ int nslot_u(int dim) { return dim == 3 ? 375 : 50; }
+inline __host__ __device__ int nslot(int dim) { return dim == 3 ? 402 : 59; }
+
+struct Level {
+  LevelGeom g;
+  double* st = nullptr;         // stencil, SPN * 3^d * nnodes
+  unsigned char* mask = nullptr;  // per node: bit c = velocity comp c constrained
+  double* wfix = nullptr;       // Dirichlet values per DoF (0 where free)
+  // patch cache
+  void* coef = nullptr;         // cache_inverse rows
+  size_t coef_bytes = 0;
+  double* fac = nullptr;        // cache_matrix factors
+  int* fpiv = nullptr;
+  size_t fac_bytes = 0;
+  // level vectors (device)
+  double* x = nullptr;          // V-cycle correction on this level
+  double* b = nullptr;          // right-hand side on this level
+  double* r = nullptr;          // unpadded residual
+  double* rpad = nullptr;       // padded residual (smoother)
+  float* rpad32 = nullptr;      // padded residual in float32 / pairs (mixed paths)
+  size_t vec_bytes = 0;
+  unsigned long long active_slots = 0;  // sum over patches of active patch DoFs
+};
+
+struct Profile {
+  bool on = false;
+  struct Rec { cudaEvent_t a, b; int kind; double bytes; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+}  // namespace fc
+
+struct fc_handle_s {
+  int dim = 0, nlev = 0;
+  fc::Level lev[fc::kMaxLevels];  // index 0 = coarsest (paper level 1)
+  fc_options opt;
+  double alpha = 0;
+  cudaStream_t stream = nullptr;
+  fc::Shape* d_shapes = nullptr;
+  int nshape = 0;
+  unsigned* d_err = nullptr;
+  // coarse solve: dense inverse of the coarsest operator
+  double* coarse_inv = nullptr;
+  int coarse_n = 0;
+  // FGMRES workspace
+  double* V = nullptr;
+  double* Z = nullptr;
+  double* w = nullptr;
+  double* red = nullptr;    // reduction scratch
+  double* small = nullptr;  // Hessenberg, Givens, g, y (device)
+  double* host_small = nullptr;  // pinned
+  double* bh = nullptr;     // device staging for fc_solve_host
+  double* xh = nullptr;
+  int restart = 30;
+  size_t bytes[8] = {0};
+  fc::Profile prof;
+  std::string err;
+};
+
+namespace fc {
+
+// ---- launchers (defined in the .cu files) ----
+// geometry + element data (fc_geom.cu)
+cudaError_t launch_cell_elements(const LevelGeom& g, double* eA, double* eB, double* eF,
+                                 double* estat, unsigned* d_err, cudaStream_t s);
+// assembly (fc_assemble.cu)
+cudaError_t launch_assemble(const LevelGeom& g, const double* eA, const double* eB, double* st,
+                            cudaStream_t s);
+cudaError_t launch_masks(const LevelGeom& g, unsigned char* mask, double* wfix, cudaStream_t s);
+cudaError_t launch_rhs(const LevelGeom& g, const double* eF, const double* st,
+                       const unsigned char* mask, const double* wfix, double* b, cudaStream_t s);
+// operator application (fc_mg.cu)
+cudaError_t launch_residual(const LevelGeom& g, const double* st, const unsigned char* mask,
+                            const double* x, const double* b, double* r, double* rpad,
+                            cudaStream_t s);
+cudaError_t launch_residual_df(const LevelGeom& g, const double* st, const unsigned char* mask,
+                               const double* x, const double* b, float* rpad2, cudaStream_t s);
+cudaError_t launch_residual_f32(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                const double* x, const double* b, float* rpad, cudaStream_t s);
+cudaError_t launch_restrict(const LevelGeom& f, const LevelGeom& c, const unsigned char* cmask,
+                            const double* rf, double* bc, cudaStream_t s);
+cudaError_t launch_prolong_add(const LevelGeom& f, const LevelGeom& c, const unsigned char* fmask,
+                               const double* ec, double* xf, cudaStream_t s);
+cudaError_t launch_zero_pad_halo(double* p, long long n, cudaStream_t s);
+// patches (fc_patch.cu)
+cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsigned char* mask,
+                               int mode, double omega, double* coef64, double* fac, int* fpiv,
+                               const double* rpad, double* x, unsigned* d_err, cudaStream_t s);
+cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
+                               const unsigned char* mask, const double* rpad, const float* rpad32,
+                               double omega, double* x, cudaStream_t s);
+cudaError_t launch_factor_apply(const LevelGeom& g, const double* fac, const int* fpiv,
+                                const unsigned char* mask, const double* rpad, double omega,
+                                double* x, cudaStream_t s);
+cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* coef64, void* out,
+                                cudaStream_t s);
+size_t factor_doubles(int dim);
+size_t factor_ints(int dim);
+// coarse solve (fc_mg.cu)
+cudaError_t launch_coarse_factor(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                 double* work, double* inv, int* piv, double* dsc, unsigned* d_err,
+                                 cudaStream_t s);
+cudaError_t launch_dense_gemv(int n, const double* A, const double* x, double* y, cudaStream_t s);
+// vector ops (fc_mg.cu)
+cudaError_t launch_dot(long long n, const double* a, const double* b, double* partial,
+                       double* out, cudaStream_t s);
+cudaError_t launch_axpy(long long n, double alpha, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_scale_copy(long long n, const double* s, int sidx, int invert, const double* x,
+                              double* y, cudaStream_t st);
+cudaError_t launch_mgs_step(long long n, double* w, const double* vi, const double* hij,
+                            cudaStream_t s);
+cudaError_t launch_givens(double* small, int m, int j, double bnorm, cudaStream_t s);
+cudaError_t launch_update_x(long long n, int k, int m, const double* small, const double* Z,
+                            double* x, cudaStream_t s);
+
+}  // namespace fc

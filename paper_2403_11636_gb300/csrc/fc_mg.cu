@@ -1,0 +1,496 @@
+// fc_mg.cu -- operator application (residual r = b - L x, paper eq.
+// iteration), grid transfers R and P = R^T (eq. restriction_op), the dense
+// coarse solve (Sec. 3), and the vector kernels of the FP64 FGMRES outer
+// iteration (Sec. 4 remark on Krylov methods).
+#include <math.h>
+
+#include "fc_internal.cuh"
+
+namespace fc {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// residual / apply: one thread per node, the 3^d neighbour blocks of the
+// compressed stencil; constrained rows are identity rows and constrained
+// columns are skipped (their values live in b).
+// OUT: 0 -> r (unpadded, optional) and rpad (padded, optional) in float64,
+//      1 -> rpad as float32 pairs (hi, lo), 2 -> rpad as float32.
+template <int DIM, int OUT>
+__global__ void __launch_bounds__(256)
+    residual_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
+                    const double* __restrict__ x, const double* __restrict__ b,
+                    double* __restrict__ r, double* __restrict__ rpad, float* __restrict__ rpadf) {
+  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
+  long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nnodes) return;
+  int ia[3] = {(int)(node % g.nn[0]), (int)((node / g.nn[0]) % g.nn[1]),
+               DIM == 3 ? (int)(node / ((long long)g.nn[0] * g.nn[1])) : 0};
+  double acc[ND];
+#pragma unroll
+  for (int c = 0; c < ND; ++c) acc[c] = 0.0;
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb) {
+    int ib0 = ia[0] + nb % 3 - 1, ib1 = ia[1] + (nb / 3) % 3 - 1, ib2 = DIM == 3 ? ia[2] + nb / 9 - 1 : 0;
+    if (ib0 < 0 || ib0 > g.n[0] || ib1 < 0 || ib1 > g.n[1]) continue;
+    if (DIM == 3 && (ib2 < 0 || ib2 > g.n[2])) continue;
+    long long bn = ib0 + (long long)g.nn[0] * (ib1 + (long long)g.nn[1] * ib2);
+    unsigned char mb = mask[bn];
+    double xb[ND];
+#pragma unroll
+    for (int c = 0; c < ND; ++c) xb[c] = x[bn * ND + c];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+      if ((mb >> c) & 1) xb[c] = 0.0;
+    const double* s = st + (long long)nb * SP * g.nnodes + node;
+    double vA = s[0];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      acc[c] = acc[c] + vA * xb[c];
+      acc[c] = acc[c] + s[(1 + c) * g.nnodes] * xb[DIM];
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[DIM] = acc[DIM] + s[(1 + DIM + c) * g.nnodes] * xb[c];
+    acc[DIM] = acc[DIM] + s[(1 + 2 * DIM) * g.nnodes] * xb[DIM];
+  }
+  unsigned char ma = mask[node];
+  long long pn = pad_node(g, ia[0], ia[1], ia[2]);
+#pragma unroll
+  for (int c = 0; c < ND; ++c) {
+    double y = (c < DIM && ((ma >> c) & 1)) ? x[node * ND + c] : acc[c];
+    double v = b ? b[node * ND + c] - y : y;
+    if (OUT == 0) {
+      if (r) r[node * ND + c] = v;
+      if (rpad) rpad[pn * ND + c] = v;
+    } else if (OUT == 1) {
+      float hi = (float)v;
+      float lo = (float)(v - (double)hi);
+      rpadf[(pn * ND + c) * 2 + 0] = hi;
+      rpadf[(pn * ND + c) * 2 + 1] = lo;
+    } else {
+      rpadf[pn * ND + c] = (float)v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// transfers: Q1 interpolation between nested uniform grids (fine n = 2 nc)
+__device__ __forceinline__ double pw(int d) { return d == 0 ? 1.0 : 0.5; }
+
+template <int DIM>
+__global__ void restrict_kernel(LevelGeom f, LevelGeom c, const unsigned char* __restrict__ cmask,
+                                const double* __restrict__ rf, double* __restrict__ bc) {
+  constexpr int ND = DIM + 1;
+  long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= c.nnodes) return;
+  int I[3] = {(int)(node % c.nn[0]), (int)((node / c.nn[0]) % c.nn[1]),
+              DIM == 3 ? (int)(node / ((long long)c.nn[0] * c.nn[1])) : 0};
+  double acc[ND];
+  for (int q = 0; q < ND; ++q) acc[q] = 0.0;
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int i = 2 * I[0] + dx, j = 2 * I[1] + dy, k = DIM == 3 ? 2 * I[2] + dz : 0;
+        if (i < 0 || i > f.n[0] || j < 0 || j > f.n[1]) continue;
+        if (DIM == 3 && (k < 0 || k > f.n[2])) continue;
+        double w = pw(dx) * pw(dy) * (DIM == 3 ? pw(dz) : 1.0);
+        long long fn = i + (long long)f.nn[0] * (j + (long long)f.nn[1] * k);
+        for (int q = 0; q < ND; ++q) acc[q] = acc[q] + w * rf[fn * ND + q];
+      }
+  unsigned char m = cmask[node];
+  for (int q = 0; q < ND; ++q) bc[node * ND + q] = (q < DIM && ((m >> q) & 1)) ? 0.0 : acc[q];
+}
+
+template <int DIM>
+__global__ void prolong_kernel(LevelGeom f, LevelGeom c, const unsigned char* __restrict__ fmask,
+                               const double* __restrict__ ec, double* __restrict__ xf) {
+  constexpr int ND = DIM + 1;
+  long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= f.nnodes) return;
+  int ia[3] = {(int)(node % f.nn[0]), (int)((node / f.nn[0]) % f.nn[1]),
+               DIM == 3 ? (int)(node / ((long long)f.nn[0] * f.nn[1])) : 0};
+  int lo[3], hi[3];
+  for (int k = 0; k < 3; ++k) { lo[k] = ia[k] / 2; hi[k] = (ia[k] + 1) / 2; }
+  double acc[ND];
+  for (int q = 0; q < ND; ++q) acc[q] = 0.0;
+  for (int t = 0; t < (1 << DIM); ++t) {
+    int ic[3] = {0, 0, 0};
+    double w = 1.0;
+    bool dup = false;
+    for (int k = 0; k < DIM; ++k) {
+      int bit = (t >> k) & 1;
+      if (lo[k] == hi[k] && bit) dup = true;
+      ic[k] = bit ? hi[k] : lo[k];
+      w = w * (lo[k] == hi[k] ? 1.0 : 0.5);
+    }
+    if (dup) continue;
+    long long cn = ic[0] + (long long)c.nn[0] * (ic[1] + (long long)c.nn[1] * ic[2]);
+    for (int q = 0; q < ND; ++q) acc[q] = acc[q] + w * ec[cn * ND + q];
+  }
+  unsigned char m = fmask[node];
+  for (int q = 0; q < ND; ++q)
+    if (!(q < DIM && ((m >> q) & 1))) xf[node * ND + q] = xf[node * ND + q] + acc[q];
+}
+
+// ---------------------------------------------------------------------------
+// coarse operator: dense matrix of the coarsest level, equilibrated LU with
+// partial pivoting in one CTA, then the explicit inverse (columns solved
+// from the identity) so that each V-cycle applies one dense GEMV.
+template <int DIM>
+__global__ void coarse_dense_kernel(LevelGeom g, const double* __restrict__ st,
+                                    const unsigned char* __restrict__ mask, double* __restrict__ A) {
+  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
+  long long n = g.ndof;
+  long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  long long node = row / ND;
+  int ca = (int)(row % ND);
+  for (long long c2 = 0; c2 < n; ++c2) A[row * n + c2] = 0.0;
+  unsigned char ma = mask[node];
+  if (ca < DIM && ((ma >> ca) & 1)) { A[row * n + row] = 1.0; return; }
+  int ia[3] = {(int)(node % g.nn[0]), (int)((node / g.nn[0]) % g.nn[1]),
+               DIM == 3 ? (int)(node / ((long long)g.nn[0] * g.nn[1])) : 0};
+  for (int nb = 0; nb < NB; ++nb) {
+    int ib[3] = {ia[0] + nb % 3 - 1, ia[1] + (nb / 3) % 3 - 1, DIM == 3 ? ia[2] + nb / 9 - 1 : 0};
+    bool inside = true;
+    for (int k = 0; k < DIM; ++k)
+      if (ib[k] < 0 || ib[k] > g.n[k]) inside = false;
+    if (!inside) continue;
+    long long bn = ib[0] + (long long)g.nn[0] * (ib[1] + (long long)g.nn[1] * ib[2]);
+    unsigned char mb = mask[bn];
+    const double* s = st + (long long)nb * SP * g.nnodes + node;
+    for (int cb = 0; cb < ND; ++cb) {
+      if (cb < DIM && ((mb >> cb) & 1)) continue;
+      double v;
+      if (ca < DIM && cb < DIM) v = ca == cb ? s[0] : 0.0;
+      else if (ca < DIM) v = s[(1 + ca) * g.nnodes];
+      else if (cb < DIM) v = s[(1 + DIM + cb) * g.nnodes];
+      else v = s[(1 + 2 * DIM) * g.nnodes];
+      A[row * n + bn * ND + cb] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+    dense_inverse_kernel(int n, double* __restrict__ A, double* __restrict__ inv, int* __restrict__ piv,
+                         double* __restrict__ dsc, unsigned* __restrict__ d_err) {
+  __shared__ double sval[32];
+  __shared__ int sidx[32];
+  __shared__ int s_p;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // equilibration D A D, D = |diag A|^{-1/2}
+  for (int j = tid; j < n; j += nt) {
+    double v = fabs(A[(long long)j * n + j]);
+    dsc[j] = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+  }
+  __syncthreads();
+  for (long long t = tid; t < (long long)n * n; t += nt) {
+    long long rr = t / n, cc = t % n;
+    A[t] = dsc[rr] * A[t] * dsc[cc];
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // pivot: max |a_rk|, lowest row on ties
+    double best = -1.0;
+    int bi = k;
+    for (int rr = k + tid; rr < n; rr += nt) {
+      double v = fabs(A[(long long)rr * n + k]);
+      if (v > best) { best = v; bi = rr; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { sval[tid >> 5] = best; sidx[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      int nw = (nt + 31) / 32;
+      double bv = sval[0];
+      int bidx = sidx[0];
+      for (int w = 1; w < nw; ++w)
+        if (sval[w] > bv || (sval[w] == bv && sidx[w] < bidx)) { bv = sval[w]; bidx = sidx[w]; }
+      s_p = bidx;
+      piv[k] = bidx;
+      if (bv == 0.0) atomicOr(d_err, kErrSingularCoarse);
+    }
+    __syncthreads();
+    int p = s_p;
+    if (p != k)
+      for (int cc = tid; cc < n; cc += nt) {
+        double t0 = A[(long long)k * n + cc];
+        A[(long long)k * n + cc] = A[(long long)p * n + cc];
+        A[(long long)p * n + cc] = t0;
+      }
+    __syncthreads();
+    double d = A[(long long)k * n + k];
+    for (int rr = k + 1 + tid; rr < n; rr += nt) A[(long long)rr * n + k] = d != 0.0 ? A[(long long)rr * n + k] / d : 0.0;
+    __syncthreads();
+    long long rem = (long long)(n - k - 1) * (n - k - 1);
+    for (long long t = tid; t < rem; t += nt) {
+      int rr = k + 1 + (int)(t / (n - k - 1)), cc = k + 1 + (int)(t % (n - k - 1));
+      A[(long long)rr * n + cc] = A[(long long)rr * n + cc] - A[(long long)rr * n + k] * A[(long long)k * n + cc];
+    }
+    __syncthreads();
+  }
+  // inverse columns: solve (D A D) z = P e_j, inv = D z D; threads own columns
+  for (int j = tid; j < n; j += nt) {
+    double* z = inv + (long long)j * n;  // column j stored contiguously (transposed below)
+    for (int q = 0; q < n; ++q) z[q] = q == j ? 1.0 : 0.0;
+    for (int k = 0; k < n; ++k) {
+      int p = piv[k];
+      if (p != k) { double t0 = z[k]; z[k] = z[p]; z[p] = t0; }
+    }
+    for (int rr = 0; rr < n; ++rr) {
+      double s = z[rr];
+      for (int cc = 0; cc < rr; ++cc) s = s - A[(long long)rr * n + cc] * z[cc];
+      z[rr] = s;
+    }
+    for (int rr = n - 1; rr >= 0; --rr) {
+      double s = z[rr];
+      for (int cc = rr + 1; cc < n; ++cc) s = s - A[(long long)rr * n + cc] * z[cc];
+      z[rr] = s / A[(long long)rr * n + rr];
+    }
+  }
+  __syncthreads();
+  // z_j holds column j of (DAD)^{-1}; inv[r][j] = d_r z_j[r] d_j.  Transpose
+  // in place through A (no longer needed).
+  for (long long t = tid; t < (long long)n * n; t += nt) {
+    long long rr = t / n, cc = t % n;
+    A[rr * n + cc] = dsc[rr] * inv[cc * n + rr] * dsc[cc];
+  }
+  __syncthreads();
+  for (long long t = tid; t < (long long)n * n; t += nt) inv[t] = A[t];
+}
+
+// y = A x, one warp per row
+__global__ void gemv_kernel(int n, const double* __restrict__ A, const double* __restrict__ x,
+                            double* __restrict__ y) {
+  int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s += A[(long long)row * n + c] * x[c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = s;
+}
+
+// ---------------------------------------------------------------------------
+// deterministic reductions: a fixed grid of partial sums, then one block
+constexpr int kRedBlocks = 1024;
+
+__global__ void dot_partial_kernel(long long n, const double* __restrict__ a, const double* __restrict__ b,
+                                   double* __restrict__ partial) {
+  __shared__ double sm[32];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s += a[i] * b[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void sum_partial_kernel(int np, const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sm[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) out[0] = t;
+  }
+}
+
+__global__ void axpy_kernel(long long n, double alpha, const double* __restrict__ x, double* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = y[i] + alpha * x[i];
+}
+
+// y = x * s[sidx] (or / s[sidx] when invert), s a device scalar array
+__global__ void scale_copy_kernel(long long n, const double* __restrict__ s, int sidx, int invert,
+                                  const double* __restrict__ x, double* __restrict__ y) {
+  double f = s[sidx];
+  if (invert) f = f != 0.0 ? 1.0 / f : 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = x[i] * f;
+}
+
+// w -= h * v with h a device scalar
+__global__ void mgs_step_kernel(long long n, double* __restrict__ w, const double* __restrict__ v,
+                                const double* __restrict__ h) {
+  double hv = h[0];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    w[i] = w[i] - hv * v[i];
+}
+
+// Small FGMRES state (device, one thread):
+//   H[(m+1) x m] row-major at small[0], cs[m], sn[m], g[m+1], y[m],
+//   scalars at the end: [est, hn, beta, ...]
+__global__ void givens_kernel(double* small, int m, int j, double bnorm) {
+  double* H = small;
+  double* cs = H + (m + 1) * m;
+  double* sn = cs + m;
+  double* g = sn + m;
+  double* sc = g + (m + 1) + m;  // after y
+  // H[j+1][j] was written from the norm scalar
+  for (int i = 0; i < j; ++i) {
+    double a = H[i * m + j], c = H[(i + 1) * m + j];
+    H[i * m + j] = cs[i] * a + sn[i] * c;
+    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+  }
+  double a = H[j * m + j], c = H[(j + 1) * m + j];
+  double den = sqrt(a * a + c * c);
+  cs[j] = den == 0.0 ? 1.0 : a / den;
+  sn[j] = den == 0.0 ? 0.0 : c / den;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  sc[0] = fabs(g[j + 1]) / bnorm;
+}
+
+// y = H^{-1} g (k x k upper triangular), then x += sum_i y_i Z_i
+__global__ void solve_y_kernel(double* small, int m, int k) {
+  double* H = small;
+  double* cs = H + (m + 1) * m;
+  double* sn = cs + m;
+  double* g = sn + m;
+  double* y = g + (m + 1);
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int t = i + 1; t < k; ++t) s = s - H[i * m + t] * y[t];
+    y[i] = s / H[i * m + i];
+  }
+}
+
+__global__ void update_x_kernel(long long n, int k, int m, const double* __restrict__ small,
+                                const double* __restrict__ Z, double* __restrict__ x) {
+  const double* y = small + (m + 1) * m + m + m + (m + 1);
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double s = x[t];
+    for (int i = 0; i < k; ++i) s = s + y[i] * Z[(long long)i * n + t];
+    x[t] = s;
+  }
+}
+
+__global__ void zero_kernel(double* p, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = 0.0;
+}
+
+inline unsigned grid_for(long long n, int bs) {
+  long long b = (n + bs - 1) / bs;
+  if (b > 152LL * 16) b = 152LL * 16;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+cudaError_t launch_residual(const LevelGeom& g, const double* st, const unsigned char* mask,
+                            const double* x, const double* b, double* r, double* rpad,
+                            cudaStream_t s) {
+  unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
+  if (g.dim == 2) residual_kernel<2, 0><<<blocks, 256, 0, s>>>(g, st, mask, x, b, r, rpad, nullptr);
+  else residual_kernel<3, 0><<<blocks, 256, 0, s>>>(g, st, mask, x, b, r, rpad, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_df(const LevelGeom& g, const double* st, const unsigned char* mask,
+                               const double* x, const double* b, float* rpad2, cudaStream_t s) {
+  unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
+  if (g.dim == 2) residual_kernel<2, 1><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad2);
+  else residual_kernel<3, 1><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_f32(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                const double* x, const double* b, float* rpad, cudaStream_t s) {
+  unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
+  if (g.dim == 2) residual_kernel<2, 2><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad);
+  else residual_kernel<3, 2><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const LevelGeom& f, const LevelGeom& c, const unsigned char* cmask,
+                            const double* rf, double* bc, cudaStream_t s) {
+  unsigned blocks = (unsigned)((c.nnodes + 255) / 256);
+  if (f.dim == 2) restrict_kernel<2><<<blocks, 256, 0, s>>>(f, c, cmask, rf, bc);
+  else restrict_kernel<3><<<blocks, 256, 0, s>>>(f, c, cmask, rf, bc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(const LevelGeom& f, const LevelGeom& c, const unsigned char* fmask,
+                               const double* ec, double* xf, cudaStream_t s) {
+  unsigned blocks = (unsigned)((f.nnodes + 255) / 256);
+  if (f.dim == 2) prolong_kernel<2><<<blocks, 256, 0, s>>>(f, c, fmask, ec, xf);
+  else prolong_kernel<3><<<blocks, 256, 0, s>>>(f, c, fmask, ec, xf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_pad_halo(double* p, long long n, cudaStream_t s) {
+  zero_kernel<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_factor(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                 double* work, double* inv, int* piv, double* dsc, unsigned* d_err,
+                                 cudaStream_t s) {
+  unsigned blocks = (unsigned)((g.ndof + 127) / 128);
+  if (g.dim == 2) coarse_dense_kernel<2><<<blocks, 128, 0, s>>>(g, st, mask, work);
+  else coarse_dense_kernel<3><<<blocks, 128, 0, s>>>(g, st, mask, work);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dense_inverse_kernel<<<1, 1024, 0, s>>>((int)g.ndof, work, inv, piv, dsc, d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_gemv(int n, const double* A, const double* x, double* y, cudaStream_t s) {
+  long long threads = (long long)n * 32;
+  gemv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, A, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(long long n, const double* a, const double* b, double* partial, double* out,
+                       cudaStream_t s) {
+  dot_partial_kernel<<<kRedBlocks, 256, 0, s>>>(n, a, b, partial);
+  sum_partial_kernel<<<1, 1024, 0, s>>>(kRedBlocks, partial, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(long long n, double alpha, const double* x, double* y, cudaStream_t s) {
+  axpy_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, alpha, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(long long n, const double* sc, int sidx, int invert, const double* x,
+                              double* y, cudaStream_t s) {
+  scale_copy_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, sc, sidx, invert, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mgs_step(long long n, double* w, const double* vi, const double* hij, cudaStream_t s) {
+  mgs_step_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, w, vi, hij);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_givens(double* small, int m, int j, double bnorm, cudaStream_t s) {
+  givens_kernel<<<1, 1, 0, s>>>(small, m, j, bnorm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_x(long long n, int k, int m, const double* small, const double* Z, double* x,
+                            cudaStream_t s) {
+  solve_y_kernel<<<1, 1, 0, s>>>(const_cast<double*>(small), m, k);
+  update_x_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, k, m, small, Z, x);
+  return cudaGetLastError();
+}
+
+}  // namespace fc

@@ -1,0 +1,779 @@
+// fc_patch.cu -- the restricted additive patch smoother (paper Sec. 3.1).
+//
+// Patch S_i of pressure node i: velocity DoFs of the 5^d nodes around i and
+// pressure DoFs of the 3^d nodes around i (the pressures sharing a cell with
+// p_i and the velocities coupled to them through B^T, taken structurally),
+// without constrained or out-of-grid DoFs.  L_i = R_i L R_i^T is
+//   [ A_i  B_i ]      A_i = blockdiag(K, .., K): the velocity form acts on
+//   [ B_i' C_i ]      each component alike (eq. stokes_disc_weak_fcm_2).
+// The local solve is exact (Sec. 3.1.2).  It is taken on the symmetrically
+// equilibrated block D L_i D (D = |diag L_i|^{-1/2}) so that it reaches
+// machine accuracy although alpha-scaled and unscaled rows differ by many
+// orders of magnitude, and through the block elimination
+//   K~ = LU (partial pivoting), W~_c = K~^{-1} B~_c,
+//   S~ = C~ - sum_c B~_c' W~_c  (LU, partial pivoting)
+// instead of a dense LU of the whole (5^d d + 3^d)-square block: 4.4 instead
+// of 43 MFLOP per 3D patch.
+//
+// One CTA per patch builds the block factors in shared memory and then
+//   mode 0 (cache_inverse): writes the 1+d owned rows of L_i^{-1} (the rows
+//          that R~_i^T keeps, Sec. 3.1.2);
+//   mode 1 (cache_matrix):  writes the block factors for later solves;
+//   mode 2 (cache_none):    solves with the gathered residual at once and
+//          updates the owned DoFs (nothing stored).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "fc_internal.cuh"
+
+namespace fc {
+
+namespace {
+
+template <int DIM>
+struct PatchDims {
+  static constexpr int NU = DIM == 3 ? 125 : 25;   // velocity nodes (5^d)
+  static constexpr int NP = DIM == 3 ? 27 : 9;     // pressure nodes (3^d)
+  static constexpr int ND = DIM + 1;
+  static constexpr int SP = 2 * DIM + 2;
+  static constexpr int NSLOT = NU * DIM + NP;
+  static constexpr int NCOL = DIM * NP + 1 + DIM;  // B columns, e_centre, residual columns
+  static constexpr int THREADS = DIM == 3 ? 256 : 128;
+  // factor record (doubles): K LU (column-major), W (col-major), S LU, du, dp
+  static constexpr int REC = NU * NU + DIM * NP * NU + NP * NP + NU + NP;
+  static constexpr int RECI = NU + NP;
+};
+
+template <int DIM>
+__device__ __forceinline__ void vel_off(int v, int* o) {
+  o[0] = v % 5 - 2;
+  o[1] = (v / 5) % 5 - 2;
+  o[2] = DIM == 3 ? v / 25 - 2 : 0;
+}
+template <int DIM>
+__device__ __forceinline__ void prs_off(int p, int* o) {
+  o[0] = p % 3 - 1;
+  o[1] = (p / 3) % 3 - 1;
+  o[2] = DIM == 3 ? p / 9 - 1 : 0;
+}
+template <int DIM>
+__device__ __forceinline__ int nb_index(const int* d) {
+  return (d[0] + 1) + 3 * (d[1] + 1) + (DIM == 3 ? 9 * (d[2] + 1) : 0);
+}
+
+// CTA-cooperative LU with partial pivoting (max |a|, lowest row on ties),
+// row-major n x n with leading dimension ld.
+__device__ void cta_lu(double* A, int n, int ld, int* piv, int* s_flag) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < n; ++k) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = k;
+      for (int r = k + lane; r < n; r += 32) {
+        double v = fabs(A[r * ld + k]);
+        if (v > best) { best = v; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_down_sync(0xffffffffu, best, o);
+        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        piv[k] = bi;
+        if (best == 0.0) *s_flag = 1;
+      }
+    }
+    __syncthreads();
+    int p = piv[k];
+    if (p != k)
+      for (int c = tid; c < n; c += nt) {
+        double t = A[k * ld + c];
+        A[k * ld + c] = A[p * ld + c];
+        A[p * ld + c] = t;
+      }
+    __syncthreads();
+    double d = A[k * ld + k];
+    for (int r = k + 1 + tid; r < n; r += nt) A[r * ld + k] = d != 0.0 ? A[r * ld + k] / d : 0.0;
+    __syncthreads();
+    int m = n - k - 1;
+    for (int t = tid; t < m * m; t += nt) {
+      int r = k + 1 + t / m, c = k + 1 + t % m;
+      A[r * ld + c] = A[r * ld + c] - A[r * ld + k] * A[k * ld + c];
+    }
+    __syncthreads();
+  }
+}
+
+// z <- A^{-1} z with the row-major LU and pivots (one thread)
+__device__ void lu_solve_vec(const double* A, int n, int ld, const int* piv, double* z) {
+  for (int k = 0; k < n; ++k) {
+    int p = piv[k];
+    if (p != k) { double t = z[k]; z[k] = z[p]; z[p] = t; }
+  }
+  for (int r = 0; r < n; ++r) {
+    double s = z[r];
+    for (int c = 0; c < r; ++c) s = s - A[r * ld + c] * z[c];
+    z[r] = s;
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = z[r];
+    for (int c = r + 1; c < n; ++c) s = s - A[r * ld + c] * z[c];
+    z[r] = s / A[r * ld + r];
+  }
+}
+
+template <int DIM, int MODE>
+__global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
+    patch_factor_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
+                        double omega, double* __restrict__ coef, double* __restrict__ fac,
+                        int* __restrict__ fpiv, const double* __restrict__ rpad, double* __restrict__ x,
+                        unsigned* __restrict__ d_err) {
+  using P = PatchDims<DIM>;
+  constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP, NCOL = P::NCOL;
+  extern __shared__ double smem[];
+  double* K = smem;                 // NU x NU row-major
+  double* W = K + NU * NU;          // NCOL columns of length NU
+  double* S = W + NCOL * NU;        // NP x NP row-major
+  double* du = S + NP * NP;         // NU
+  double* dp = du + NU;             // NP
+  double* rp = dp + NP;             // NP: scaled pressure residual (mode 2) / scratch
+  double* zp = rp + NP;             // (DIM+1) x NP scratch
+  double* yo = zp + (DIM + 1) * NP; // ND owned results
+  int* pivK = (int*)(yo + ND);      // NU
+  int* pivS = pivK + NU;            // NP
+  long long* nodeU = (long long*)(((uintptr_t)(pivS + NP) + 7) & ~(uintptr_t)7);  // NU
+  long long* nodeP = nodeU + NU;    // NP
+  unsigned char* au = (unsigned char*)(nodeP + NP);  // NU
+  unsigned char* ap = au + NU;      // NP
+  __shared__ int s_flag;
+
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long i = blockIdx.x;
+  const int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
+                     DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
+  if (tid == 0) s_flag = 0;
+
+  // ---- patch DoFs
+  for (int v = tid; v < NU; v += nt) {
+    int o[3];
+    vel_off<DIM>(v, o);
+    int b0 = ia[0] + o[0], b1 = ia[1] + o[1], b2 = ia[2] + o[2];
+    bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && (DIM == 2 || (b2 >= 0 && b2 <= g.n[2]));
+    long long bn = in ? b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2) : -1;
+    nodeU[v] = bn;
+    au[v] = (unsigned char)(in && !(mask[bn] & 1));
+  }
+  for (int p = tid; p < NP; p += nt) {
+    int o[3];
+    prs_off<DIM>(p, o);
+    int b0 = ia[0] + o[0], b1 = ia[1] + o[1], b2 = ia[2] + o[2];
+    bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && (DIM == 2 || (b2 >= 0 && b2 <= g.n[2]));
+    nodeP[p] = in ? b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2) : -1;
+    ap[p] = (unsigned char)in;
+  }
+  __syncthreads();
+
+  // ---- gather K, B (into W columns), C (into S)
+  for (int e = tid; e < NU * NU; e += nt) {
+    int v = e / NU, w = e % NU;
+    double val = 0.0;
+    if (au[v] && au[w]) {
+      int ov[3], ow[3], d[3];
+      vel_off<DIM>(v, ov);
+      vel_off<DIM>(w, ow);
+      bool adj = true;
+      for (int k = 0; k < 3; ++k) { d[k] = ow[k] - ov[k]; if (d[k] < -1 || d[k] > 1) adj = false; }
+      if (adj) val = st[((long long)nb_index<DIM>(d) * SP) * g.nnodes + nodeU[v]];
+    } else if (v == w) {
+      val = 1.0;
+    }
+    K[e] = val;
+  }
+  for (int e = tid; e < DIM * NP * NU; e += nt) {
+    int col = e / NU, v = e % NU, c = col / NP, p = col % NP;
+    double val = 0.0;
+    if (au[v] && ap[p]) {
+      int ov[3], op[3], d[3];
+      vel_off<DIM>(v, ov);
+      prs_off<DIM>(p, op);
+      bool adj = true;
+      for (int k = 0; k < 3; ++k) { d[k] = op[k] - ov[k]; if (d[k] < -1 || d[k] > 1) adj = false; }
+      if (adj) val = st[((long long)nb_index<DIM>(d) * SP + 1 + c) * g.nnodes + nodeU[v]];
+    }
+    W[e] = val;
+  }
+  for (int e = tid; e < NP * NP; e += nt) {
+    int p = e / NP, q = e % NP;
+    double val = 0.0;
+    if (ap[p] && ap[q]) {
+      int op[3], oq[3], d[3];
+      prs_off<DIM>(p, op);
+      prs_off<DIM>(q, oq);
+      for (int k = 0; k < 3; ++k) d[k] = oq[k] - op[k];
+      val = st[((long long)nb_index<DIM>(d) * SP + 1 + 2 * DIM) * g.nnodes + nodeP[p]];
+    } else if (p == q) {
+      val = 1.0;
+    }
+    S[e] = val;
+  }
+  __syncthreads();
+  for (int v = tid; v < NU; v += nt) {
+    double a = fabs(K[v * NU + v]);
+    du[v] = (au[v] && a > 0.0) ? 1.0 / sqrt(a) : 1.0;
+  }
+  for (int p = tid; p < NP; p += nt) {
+    double a = fabs(S[p * NP + p]);
+    dp[p] = (ap[p] && a > 0.0) ? 1.0 / sqrt(a) : 1.0;
+  }
+  __syncthreads();
+  // ---- equilibrate; extra right-hand sides: e_centre and (mode 2) D r
+  const int v0 = DIM == 3 ? 62 : 12, p0 = DIM == 3 ? 13 : 4;
+  for (int e = tid; e < NU * NU; e += nt) K[e] = du[e / NU] * K[e] * du[e % NU];
+  for (int e = tid; e < DIM * NP * NU; e += nt) W[e] = du[e % NU] * W[e] * dp[(e / NU) % NP];
+  for (int e = tid; e < NP * NP; e += nt) S[e] = dp[e / NP] * S[e] * dp[e % NP];
+  for (int v = tid; v < NU; v += nt) {
+    W[(DIM * NP) * NU + v] = v == v0 ? 1.0 : 0.0;
+    for (int c = 0; c < DIM; ++c) {
+      double rv = 0.0;
+      if (MODE == 2 && au[v]) {
+        int o[3];
+        vel_off<DIM>(v, o);
+        long long pn = pad_node(g, ia[0] + o[0], ia[1] + o[1], ia[2] + o[2]);
+        rv = du[v] * rpad[pn * ND + c];
+      }
+      W[(DIM * NP + 1 + c) * NU + v] = rv;
+    }
+  }
+  for (int p = tid; p < NP; p += nt) {
+    double rv = 0.0;
+    if (MODE == 2 && ap[p]) {
+      int o[3];
+      prs_off<DIM>(p, o);
+      long long pn = pad_node(g, ia[0] + o[0], ia[1] + o[1], ia[2] + o[2]);
+      rv = dp[p] * rpad[pn * ND + DIM];
+    }
+    rp[p] = rv;
+  }
+  __syncthreads();
+
+  // ---- K~ = LU
+  cta_lu(K, NU, NU, pivK, &s_flag);
+  // ---- W~ = K~^{-1} [B~ | e_centre | D r_u]
+  const int ncol = MODE == 2 ? NCOL : DIM * NP + 1;
+  for (int col = tid; col < ncol; col += nt) lu_solve_vec(K, NU, NU, pivK, W + col * NU);
+  __syncthreads();
+  // ---- S~ = C~ - sum_c B~_c^T W~_c, B~ re-read from the operator (27 / 9
+  // velocity nodes are adjacent to a pressure node)
+  for (int e = tid; e < NP * NP; e += nt) {
+    int p = e / NP, q = e % NP;
+    double s = S[e];
+    if (ap[p]) {
+      int op[3];
+      prs_off<DIM>(p, op);
+      for (int t = 0; t < (DIM == 3 ? 27 : 9); ++t) {
+        int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+        int ov[3] = {op[0] + d[0], op[1] + d[1], op[2] + d[2]};
+        int v = (ov[0] + 2) + 5 * (ov[1] + 2) + (DIM == 3 ? 25 * (ov[2] + 2) : 0);
+        if (!au[v]) continue;
+        int dvp[3] = {-d[0], -d[1], -d[2]};  // pressure node relative to velocity node
+        long long base = (long long)nb_index<DIM>(dvp) * SP;
+        for (int c = 0; c < DIM; ++c) {
+          double bt = du[v] * st[(base + 1 + c) * g.nnodes + nodeU[v]] * dp[p];
+          s = s - bt * W[(c * NP + q) * NU + v];
+        }
+      }
+    }
+    S[e] = s;
+  }
+  __syncthreads();
+  cta_lu(S, NP, NP, pivS, &s_flag);
+  if (s_flag) {
+    if (tid == 0) atomicOr(d_err, kErrSingularPatch);
+  }
+
+  if (MODE == 0) {
+    // ---- owned rows: row k of L_i^{-1} = d_k (L~^{-1} e_k)^T D
+    // z_p for each owned k: velocity c -> -S~^{-1} (row v0 of W~_c); pressure -> S~^{-1} e_p0
+    if (tid < ND) {
+      double* z = zp + tid * NP;
+      for (int q = 0; q < NP; ++q)
+        z[q] = tid < DIM ? -W[(tid * NP + q) * NU + v0] : (q == p0 ? 1.0 : 0.0);
+      lu_solve_vec(S, NP, NP, pivS, z);
+    }
+    __syncthreads();
+    double* out = coef + (long long)i * P::NSLOT * ND;
+    for (int j = tid; j < P::NSLOT; j += nt) {
+      double vals[ND];
+      if (j < NU * DIM) {
+        int v = j / DIM, c2 = j % DIM;
+        for (int k = 0; k < ND; ++k) {
+          double z = 0.0;
+          if (au[v]) {
+            double s = (k == c2) ? W[(DIM * NP) * NU + v] : 0.0;
+            for (int q = 0; q < NP; ++q) s = s - W[(c2 * NP + q) * NU + v] * zp[k * NP + q];
+            z = s;
+          }
+          bool own_ok = k < DIM ? au[v0] != 0 : true;
+          double dk = k < DIM ? du[v0] : dp[p0];
+          vals[k] = (own_ok && au[v]) ? dk * z * du[v] : 0.0;
+        }
+      } else {
+        int p = j - NU * DIM;
+        for (int k = 0; k < ND; ++k) {
+          bool own_ok = k < DIM ? au[v0] != 0 : true;
+          double dk = k < DIM ? du[v0] : dp[p0];
+          vals[k] = (own_ok && ap[p]) ? dk * zp[k * NP + p] * dp[p] : 0.0;
+        }
+      }
+      for (int k = 0; k < ND; ++k) out[(long long)j * ND + k] = vals[k];
+    }
+  } else if (MODE == 1) {
+    // ---- store the block factors: K~ LU column-major, W~ (B~ columns),
+    // S~ LU row-major, du, dp; pivots
+    double* rec = fac + (long long)i * P::REC;
+    for (int e = tid; e < NU * NU; e += nt) {
+      int c = e / NU, r = e % NU;
+      rec[e] = K[r * NU + c];
+    }
+    for (int e = tid; e < DIM * NP * NU; e += nt) rec[NU * NU + e] = W[e];
+    for (int e = tid; e < NP * NP; e += nt) rec[NU * NU + DIM * NP * NU + e] = S[e];
+    for (int v = tid; v < NU; v += nt) rec[NU * NU + DIM * NP * NU + NP * NP + v] = du[v];
+    for (int p = tid; p < NP; p += nt) rec[NU * NU + DIM * NP * NU + NP * NP + NU + p] = dp[p];
+    int* ip = fpiv + (long long)i * P::RECI;
+    for (int v = tid; v < NU; v += nt) ip[v] = pivK[v];
+    for (int p = tid; p < NP; p += nt) ip[NU + p] = pivS[p];
+  } else {
+    // ---- solve with the gathered residual: t = r~_p - sum_c W~_c^T r~_c,
+    // z_p = S~^{-1} t, owned u_c = (K~^{-1} r~_c)[v0] - W~_c[v0,:] z_p
+    for (int q = tid; q < NP; q += nt) {
+      double s = rp[q];
+      for (int c = 0; c < DIM; ++c) {
+        // W~_c^T r~_c = B~_c^T (K~^{-1} r~_c) because K~ is symmetric; the
+        // residual columns were solved in place, B~ is re-read.
+        int op[3];
+        prs_off<DIM>(q, op);
+        if (!ap[q]) continue;
+        for (int t = 0; t < (DIM == 3 ? 27 : 9); ++t) {
+          int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+          int ov[3] = {op[0] + d[0], op[1] + d[1], op[2] + d[2]};
+          int v = (ov[0] + 2) + 5 * (ov[1] + 2) + (DIM == 3 ? 25 * (ov[2] + 2) : 0);
+          if (!au[v]) continue;
+          int dvp[3] = {-d[0], -d[1], -d[2]};
+          double bt = du[v] * st[((long long)nb_index<DIM>(dvp) * SP + 1 + c) * g.nnodes + nodeU[v]] * dp[q];
+          s = s - bt * W[(DIM * NP + 1 + c) * NU + v];
+        }
+      }
+      zp[q] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      lu_solve_vec(S, NP, NP, pivS, zp);
+      for (int c = 0; c < DIM; ++c) {
+        double s = W[(DIM * NP + 1 + c) * NU + v0];
+        for (int q = 0; q < NP; ++q) s = s - W[(c * NP + q) * NU + v0] * zp[q];
+        yo[c] = du[v0] * s;
+      }
+      yo[DIM] = dp[p0] * zp[p0];
+      unsigned char m = mask[i];
+      long long pc = pad_node(g, ia[0], ia[1], ia[2]);
+      for (int c = 0; c < DIM; ++c) {
+        if ((m >> c) & 1) x[i * ND + c] = x[i * ND + c] + rpad[pc * ND + c];
+        else x[i * ND + c] = x[i * ND + c] + omega * yo[c];
+      }
+      x[i * ND + DIM] = x[i * ND + DIM] + omega * yo[DIM];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// cache_inverse apply: y = omega * Inv_i r_i, x[node i] += y.  One warp per
+// patch; lane handles slots j = lane + 32 t, reads the ND coefficients of the
+// slot (one vector load) and the residual entry of the slot from the padded
+// residual (no bounds checks: the zero halo covers the 5^d box).
+template <int DIM>
+__device__ __forceinline__ long long slot_ridx(const LevelGeom& g, long long pbase, int j) {
+  constexpr int NU = PatchDims<DIM>::NU, ND = DIM + 1;
+  long long px = g.nn[0] + 4, py = g.nn[1] + 4;
+  int o[3], c;
+  if (j < NU * DIM) {
+    vel_off<DIM>(j / DIM, o);
+    c = j % DIM;
+  } else {
+    prs_off<DIM>(j - NU * DIM, o);
+    c = DIM;
+  }
+  return (pbase + o[0] + px * (o[1] + py * o[2])) * ND + c;
+}
+
+template <int DIM>
+__device__ __forceinline__ void finish_update(const LevelGeom& g, long long i, const int* ia,
+                                              const unsigned char* mask, const double* rc,
+                                              const double* y, double omega, double* x) {
+  constexpr int ND = DIM + 1;
+  unsigned char m = mask[i];
+  for (int c = 0; c < DIM; ++c) {
+    if ((m >> c) & 1) x[i * ND + c] = x[i * ND + c] + rc[c];
+    else x[i * ND + c] = x[i * ND + c] + omega * y[c];
+  }
+  x[i * ND + DIM] = x[i * ND + DIM] + omega * y[DIM];
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    apply_fp64_kernel(LevelGeom g, const double* __restrict__ coef, const unsigned char* __restrict__ mask,
+                      const double* __restrict__ rpad, double omega, double* __restrict__ x) {
+  using P = PatchDims<DIM>;
+  constexpr int ND = P::ND, NSLOT = P::NSLOT;
+  const int lane = threadIdx.x & 31;
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= g.nnodes) return;
+  int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
+               DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
+  long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
+  const double* cf = coef + i * (long long)NSLOT * ND;
+  double y[ND];
+#pragma unroll
+  for (int k = 0; k < ND; ++k) y[k] = 0.0;
+  for (int j = lane; j < NSLOT; j += 32) {
+    double rv = rpad[slot_ridx<DIM>(g, pbase, j)];
+    if (ND == 4) {
+      const double2* c2 = reinterpret_cast<const double2*>(cf + (long long)j * 4);
+      double2 a = __ldg(c2), b = __ldg(c2 + 1);
+      y[0] += a.x * rv; y[1] += a.y * rv; y[2] += b.x * rv; y[ND - 1] += b.y * rv;
+    } else {
+#pragma unroll
+      for (int k = 0; k < ND; ++k) y[k] += __ldg(cf + (long long)j * ND + k) * rv;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < ND; ++k)
+    for (int o = 16; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
+  if (lane == 0) {
+    double rc[ND];
+    for (int c = 0; c < ND; ++c) rc[c] = rpad[pbase * ND + c];
+    finish_update<DIM>(g, i, ia, mask, rc, y, omega, x);
+  }
+}
+
+// float32 / bfloat16 rows with float32 residual and float32 accumulation
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256)
+    apply_lowp_kernel(LevelGeom g, const T* __restrict__ coef, const unsigned char* __restrict__ mask,
+                      const float* __restrict__ rpad, double omega, double* __restrict__ x) {
+  using P = PatchDims<DIM>;
+  constexpr int ND = P::ND, NSLOT = P::NSLOT;
+  const int lane = threadIdx.x & 31;
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= g.nnodes) return;
+  int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
+               DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
+  long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
+  const T* cf = coef + i * (long long)NSLOT * ND;
+  float y[ND];
+#pragma unroll
+  for (int k = 0; k < ND; ++k) y[k] = 0.0f;
+  for (int j = lane; j < NSLOT; j += 32) {
+    float rv = rpad[slot_ridx<DIM>(g, pbase, j)];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) y[k] = fmaf((float)cf[(long long)j * ND + k], rv, y[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < ND; ++k)
+    for (int o = 16; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
+  if (lane == 0) {
+    double rc[ND], yd[ND];
+    for (int c = 0; c < ND; ++c) { rc[c] = (double)rpad[pbase * ND + c]; yd[c] = (double)y[c]; }
+    finish_update<DIM>(g, i, ia, mask, rc, yd, omega, x);
+  }
+}
+
+// Double-float arithmetic (pairs hi + lo of float32, ~48-bit significand)
+// on the float32 pipes: products by the exact FMA split, sums by two-sum.
+struct df { float hi, lo; };
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = df_two_sum(a.hi, b.hi);
+  df t = df_two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  float hi = s.hi + s.lo;
+  float lo = s.lo - (hi - s.hi);
+  lo += t.lo;
+  float h2 = hi + lo;
+  return {h2, lo - (h2 - hi)};
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  float hi = p + e;
+  return {hi, e - (hi - p)};
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    apply_df_kernel(LevelGeom g, const float2* __restrict__ coef, const unsigned char* __restrict__ mask,
+                    const float2* __restrict__ rpad, double omega, double* __restrict__ x) {
+  using P = PatchDims<DIM>;
+  constexpr int ND = P::ND, NSLOT = P::NSLOT;
+  const int lane = threadIdx.x & 31;
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= g.nnodes) return;
+  int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
+               DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
+  long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
+  const float2* cf = coef + i * (long long)NSLOT * ND;
+  df y[ND];
+#pragma unroll
+  for (int k = 0; k < ND; ++k) y[k] = {0.0f, 0.0f};
+  for (int j = lane; j < NSLOT; j += 32) {
+    float2 r2 = rpad[slot_ridx<DIM>(g, pbase, j)];
+    df rv = {r2.x, r2.y};
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      float2 c2 = __ldg(cf + (long long)j * ND + k);
+      y[k] = df_add(y[k], df_mul({c2.x, c2.y}, rv));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < ND; ++k)
+    for (int o = 16; o > 0; o >>= 1) {
+      df other = {__shfl_xor_sync(0xffffffffu, y[k].hi, o), __shfl_xor_sync(0xffffffffu, y[k].lo, o)};
+      y[k] = df_add(y[k], other);
+    }
+  if (lane == 0) {
+    double rc[ND], yd[ND];
+    for (int c = 0; c < ND; ++c) {
+      float2 r2 = rpad[pbase * ND + c];
+      rc[c] = (double)r2.x + (double)r2.y;
+      yd[c] = (double)y[c].hi + (double)y[c].lo;
+    }
+    finish_update<DIM>(g, i, ia, mask, rc, yd, omega, x);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// cache_matrix apply: block solve with the stored factors, one warp per patch.
+template <int DIM>
+__global__ void __launch_bounds__(128)
+    factor_apply_kernel(LevelGeom g, const double* __restrict__ fac, const int* __restrict__ fpiv,
+                        const unsigned char* __restrict__ mask, const double* __restrict__ rpad,
+                        double omega, double* __restrict__ x) {
+  using P = PatchDims<DIM>;
+  constexpr int NU = P::NU, NP = P::NP, ND = P::ND;
+  __shared__ double sz[4][DIM * NU + 2 * NP];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= g.nnodes) return;
+  double* z = sz[wib];             // DIM vectors of NU (component-major)
+  double* t = z + DIM * NU;        // NP
+  double* zpv = t + NP;            // NP
+  const double* rec = fac + i * (long long)P::REC;
+  const double* LUc = rec;                        // column-major
+  const double* Wm = rec + NU * NU;               // [c*NP+q][NU]
+  const double* Sm = Wm + DIM * NP * NU;          // row-major NP x NP
+  const double* du = Sm + NP * NP;
+  const double* dp = du + NU;
+  const int* piv = fpiv + i * (long long)P::RECI;
+  int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
+               DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
+  long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
+  long long px = g.nn[0] + 4, py = g.nn[1] + 4;
+  // scaled residual; inactive DoFs carry zero coefficients in du/B already
+  // (du = 1 there but B rows are zero and K is identity), so zero them
+  for (int v = lane; v < NU; v += 32) {
+    int o[3];
+    vel_off<DIM>(v, o);
+    long long pn = pbase + o[0] + px * (o[1] + py * o[2]);
+    int b0 = ia[0] + o[0], b1 = ia[1] + o[1], b2 = ia[2] + o[2];
+    bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && (DIM == 2 || (b2 >= 0 && b2 <= g.n[2]));
+    bool act = in && !(mask[b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2)] & 1);
+    for (int c = 0; c < DIM; ++c) z[c * NU + v] = act ? du[v] * rpad[pn * ND + c] : 0.0;
+  }
+  for (int p = lane; p < NP; p += 32) {
+    int o[3];
+    prs_off<DIM>(p, o);
+    long long pn = pbase + o[0] + px * (o[1] + py * o[2]);
+    t[p] = dp[p] * rpad[pn * ND + DIM];  // out-of-grid pressure: halo zero
+  }
+  __syncwarp();
+  // t -= sum_c W~_c^T r~_c   (W~ = K~^{-1} B~ and K~ symmetric)
+  for (int q = 0; q < NP; ++q) {
+    double s = 0.0;
+    for (int c = 0; c < DIM; ++c)
+      for (int v = lane; v < NU; v += 32) s += Wm[(long long)(c * NP + q) * NU + v] * z[c * NU + v];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) t[q] -= s;
+  }
+  __syncwarp();
+  // u* = K~^{-1} r~_c for every component (column-oriented sweeps)
+  if (lane == 0)
+    for (int k = 0; k < NU; ++k) {
+      int p = piv[k];
+      if (p != k)
+        for (int c = 0; c < DIM; ++c) { double tmp = z[c * NU + k]; z[c * NU + k] = z[c * NU + p]; z[c * NU + p] = tmp; }
+    }
+  __syncwarp();
+  for (int k = 0; k < NU; ++k) {
+    double zk[DIM];
+    for (int c = 0; c < DIM; ++c) zk[c] = z[c * NU + k];
+    for (int r = k + 1 + lane; r < NU; r += 32) {
+      double l = LUc[(long long)k * NU + r];
+      for (int c = 0; c < DIM; ++c) z[c * NU + r] -= l * zk[c];
+    }
+    __syncwarp();
+  }
+  for (int k = NU - 1; k >= 0; --k) {
+    double dkk = LUc[(long long)k * NU + k];
+    double zk[DIM];
+    for (int c = 0; c < DIM; ++c) zk[c] = z[c * NU + k] / dkk;
+    __syncwarp();
+    if (lane == 0)
+      for (int c = 0; c < DIM; ++c) z[c * NU + k] = zk[c];
+    for (int r = lane; r < k; r += 32) {
+      double u = LUc[(long long)k * NU + r];
+      for (int c = 0; c < DIM; ++c) z[c * NU + r] -= u * zk[c];
+    }
+    __syncwarp();
+  }
+  // z_p = S~^{-1} t
+  if (lane == 0) {
+    const int* pivS = piv + NU;
+    for (int q = 0; q < NP; ++q) zpv[q] = t[q];
+    for (int k = 0; k < NP; ++k) {
+      int p = pivS[k];
+      if (p != k) { double tmp = zpv[k]; zpv[k] = zpv[p]; zpv[p] = tmp; }
+    }
+    for (int r = 0; r < NP; ++r) {
+      double s = zpv[r];
+      for (int c = 0; c < r; ++c) s -= Sm[r * NP + c] * zpv[c];
+      zpv[r] = s;
+    }
+    for (int r = NP - 1; r >= 0; --r) {
+      double s = zpv[r];
+      for (int c = r + 1; c < NP; ++c) s -= Sm[r * NP + c] * zpv[c];
+      zpv[r] = s / Sm[r * NP + r];
+    }
+    const int v0 = DIM == 3 ? 62 : 12, p0 = DIM == 3 ? 13 : 4;
+    double y[ND];
+    for (int c = 0; c < DIM; ++c) {
+      double s = z[c * NU + v0];
+      for (int q = 0; q < NP; ++q) s -= Wm[(long long)(c * NP + q) * NU + v0] * zpv[q];
+      y[c] = du[v0] * s;
+    }
+    y[DIM] = dp[p0] * zpv[p0];
+    double rc[ND];
+    for (int c = 0; c < ND; ++c) rc[c] = rpad[pbase * ND + c];
+    finish_update<DIM>(g, i, ia, mask, rc, y, omega, x);
+  }
+}
+
+// float64 rows -> storage precision
+template <typename T>
+__global__ void convert_kernel(long long n, const double* __restrict__ in, T* __restrict__ out) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = (T)in[t];
+}
+template <>
+__global__ void convert_kernel<__nv_bfloat16>(long long n, const double* __restrict__ in, __nv_bfloat16* __restrict__ out) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = __double2bfloat16(in[t]);
+}
+template <>
+__global__ void convert_kernel<float2>(long long n, const double* __restrict__ in, float2* __restrict__ out) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double v = in[t];
+    float hi = (float)v;
+    float lo = (float)(v - (double)hi);
+    out[t] = make_float2(hi, lo);
+  }
+}
+
+template <int DIM>
+size_t factor_smem() {
+  using P = PatchDims<DIM>;
+  size_t d = (size_t)P::NU * P::NU + (size_t)P::NCOL * P::NU + P::NP * P::NP + P::NU + P::NP + P::NP +
+             (DIM + 1) * P::NP + P::ND;
+  size_t bytes = d * 8 + (P::NU + P::NP) * 4 + 8 + (P::NU + P::NP) * 8 + (P::NU + P::NP) + 16;
+  return (bytes + 15) & ~(size_t)15;
+}
+
+template <int DIM, int MODE>
+cudaError_t run_factor(const LevelGeom& g, const double* st, const unsigned char* mask, double omega,
+                       double* coef, double* fac, int* fpiv, const double* rpad, double* x,
+                       unsigned* d_err, cudaStream_t s) {
+  size_t sm = factor_smem<DIM>();
+  auto kern = patch_factor_kernel<DIM, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)g.nnodes, PatchDims<DIM>::THREADS, sm, s>>>(g, st, mask, omega, coef, fac, fpiv, rpad, x, d_err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t factor_doubles(int dim) { return dim == 3 ? PatchDims<3>::REC : PatchDims<2>::REC; }
+size_t factor_ints(int dim) { return dim == 3 ? PatchDims<3>::RECI : PatchDims<2>::RECI; }
+
+cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsigned char* mask, int mode,
+                               double omega, double* coef64, double* fac, int* fpiv,
+                               const double* rpad, double* x, unsigned* d_err, cudaStream_t s) {
+  if (g.dim == 2) {
+    if (mode == 0) return run_factor<2, 0>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
+    if (mode == 1) return run_factor<2, 1>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
+    return run_factor<2, 2>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
+  }
+  if (mode == 0) return run_factor<3, 0>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
+  if (mode == 1) return run_factor<3, 1>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
+  return run_factor<3, 2>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
+}
+
+cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
+                               const unsigned char* mask, const double* rpad, const float* rpad32,
+                               double omega, double* x, cudaStream_t s) {
+  long long threads = g.nnodes * 32;
+  unsigned blocks = (unsigned)((threads + 255) / 256);
+  if (prec == FC_PREC_FP64) {
+    if (g.dim == 2) apply_fp64_kernel<2><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x);
+    else apply_fp64_kernel<3><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x);
+  } else if (prec == FC_PREC_FP32) {
+    if (g.dim == 2) apply_lowp_kernel<2, float><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x);
+    else apply_lowp_kernel<3, float><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x);
+  } else if (prec == FC_PREC_BF16) {
+    if (g.dim == 2) apply_lowp_kernel<2, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x);
+    else apply_lowp_kernel<3, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x);
+  } else {
+    if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x);
+    else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_factor_apply(const LevelGeom& g, const double* fac, const int* fpiv,
+                                const unsigned char* mask, const double* rpad, double omega, double* x,
+                                cudaStream_t s) {
+  long long threads = g.nnodes * 32;
+  unsigned blocks = (unsigned)((threads + 127) / 128);
+  if (g.dim == 2) factor_apply_kernel<2><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x);
+  else factor_apply_kernel<3><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* coef64, void* out,
+                                cudaStream_t s) {
+  long long n = g.nnodes * (long long)nslot(g.dim) * g.nd;
+  unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32);
+  if (prec == FC_PREC_FP32) convert_kernel<float><<<blocks, 256, 0, s>>>(n, coef64, (float*)out);
+  else if (prec == FC_PREC_BF16) convert_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(n, coef64, (__nv_bfloat16*)out);
+  else if (prec == FC_PREC_DF64) convert_kernel<float2><<<blocks, 256, 0, s>>>(n, coef64, (float2*)out);
+  return cudaGetLastError();
+}
+
+}  // namespace fc

@@ -1,0 +1,301 @@
+"""ctypes binding of libfc (include/fc.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module allocates device
+vectors with PyTorch and passes their pointers.  There is no CPU fallback:
+importing it on a machine without the built library or without a GPU raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfc.so")
+
+FC_OK, FC_ERR_INVALID, FC_ERR_OOM, FC_ERR_CUDA = 0, 1, 2, 3
+FC_ERR_NOT_CONVERGED, FC_ERR_SINGULAR, FC_ERR_TIMEOUT = 4, 5, 6
+CACHE = {"inverse": 0, "matrix": 1, "none": 2}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "df64": 3}
+EXPORTS = ("fc_options_default", "fc_setup", "fc_rhs", "fc_residual", "fc_apply", "fc_smooth",
+           "fc_restrict", "fc_prolong_add", "fc_coarse_solve", "fc_vcycle", "fc_solve",
+           "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
+           "fc_profile_enable", "fc_profile_read", "fc_sync", "fc_last_error", "fc_destroy")
+
+
+class FcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libfc error {code}: {msg}")
+        self.code = code
+
+
+class FcShape(C.Structure):
+    _fields_ = [("type", C.c_int), ("c", C.c_double * 3), ("r", C.c_double * 3),
+                ("rot", C.c_double * 2)]
+
+
+class FcGrid(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+class FcLevelset(C.Structure):
+    _fields_ = [("nshapes", C.c_int), ("shapes", C.POINTER(FcShape))]
+
+
+class FcOptions(C.Structure):
+    _fields_ = [("eta", C.c_double), ("nitsche_beta", C.c_double), ("omega", C.c_double),
+                ("nu_pre", C.c_int), ("nu_post", C.c_int), ("quad_depth", C.c_int),
+                ("cache", C.c_int), ("prec", C.c_int), ("fgmres_restart", C.c_int),
+                ("bc_preset", C.c_int), ("ubar", C.c_double), ("force_kind", C.c_int),
+                ("force", C.c_double * 3)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfc.so; raises if it is missing (build it with build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FcError(-1, f"{path} not built; run paper_2403_11636_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, d, i, ll = C.c_void_p, C.c_double, C.c_int, C.c_longlong
+    P = C.POINTER
+    lib.fc_options_default.argtypes = [P(FcOptions)]
+    lib.fc_setup.argtypes = [P(vp), P(FcGrid), P(FcLevelset), d, i, P(FcOptions), vp]
+    lib.fc_rhs.argtypes = [vp, vp]
+    lib.fc_residual.argtypes = [vp, i, vp, vp, vp]
+    lib.fc_apply.argtypes = [vp, i, vp, vp]
+    lib.fc_smooth.argtypes = [vp, i, vp, vp, i]
+    lib.fc_restrict.argtypes = [vp, i, vp, vp]
+    lib.fc_prolong_add.argtypes = [vp, i, vp, vp]
+    lib.fc_coarse_solve.argtypes = [vp, vp, vp]
+    lib.fc_vcycle.argtypes = [vp, vp, vp]
+    lib.fc_solve.argtypes = [vp, vp, vp, d, i, P(i), P(d)]
+    lib.fc_solve_host.argtypes = [vp, vp, vp, d, i, P(i), P(d)]
+    lib.fc_info.argtypes = [vp, i, P(ll), P(ll), P(C.c_size_t)]
+    lib.fc_patch_rows.argtypes = [vp, i, ll, P(d)]
+    lib.fc_footprint_estimate.restype = C.c_size_t
+    lib.fc_footprint_estimate.argtypes = [P(FcGrid), i, P(FcOptions)]
+    lib.fc_profile_enable.argtypes = [vp, i]
+    lib.fc_profile_read.argtypes = [vp, i, P(ll), P(d), P(d)]
+    lib.fc_sync.argtypes = [vp]
+    lib.fc_last_error.restype = C.c_char_p
+    lib.fc_last_error.argtypes = [vp]
+    lib.fc_destroy.argtypes = [vp]
+    for name in EXPORTS:
+        if name != "fc_last_error" and name != "fc_footprint_estimate":
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _grid(prob) -> FcGrid:
+    g = FcGrid()
+    g.dim = prob.dim
+    for k in range(3):
+        g.n[k] = int(prob.n[k]) if k < prob.dim else 1
+        g.lo[k] = float(prob.lo[k]) if k < prob.dim else 0.0
+        g.hi[k] = float(prob.hi[k]) if k < prob.dim else 1.0
+    return g
+
+
+def _options(prob, cache: str, prec: str, nu=None) -> FcOptions:
+    o = FcOptions()
+    load().fc_options_default(C.byref(o))
+    o.eta, o.nitsche_beta, o.omega = prob.eta, prob.beta, prob.omega
+    o.nu_pre, o.nu_post = (prob.nu_pre, prob.nu_post) if nu is None else nu
+    o.quad_depth = prob.qdepth
+    o.cache, o.prec = CACHE[cache], PREC[prec]
+    o.fgmres_restart = prob.restart
+    o.bc_preset, o.ubar = prob.preset, prob.ubar
+    o.force_kind = prob.force_kind
+    for k in range(3):
+        o.force[k] = float(prob.force[k])
+    return o
+
+
+def footprint_estimate(prob, cache="inverse", prec="fp64") -> int:
+    return int(load().fc_footprint_estimate(C.byref(_grid(prob)), prob.nlevels,
+                                            C.byref(_options(prob, cache, prec))))
+
+
+class Solver:
+    """A finite cell Stokes problem set up on the GPU (one fc_handle)."""
+
+    def __init__(self, prob, cache: str = "inverse", prec: str = "fp64", stream=None, nu=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise FcError(-1, "libfc needs a CUDA GPU")
+        self.torch = torch
+        self.lib = load()
+        self.prob = prob
+        self.dim = prob.dim
+        self.nd = prob.dim + 1
+        self.nlevels = prob.nlevels
+        self.cache, self.prec = cache, prec
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        shapes = np.asarray(prob.shapes, dtype=np.float64).reshape(-1, 9)
+        arr = (FcShape * max(1, len(shapes)))()
+        for s, row in enumerate(shapes):
+            arr[s].type = int(row[0])
+            for k in range(3):
+                arr[s].c[k] = row[1 + k]
+                arr[s].r[k] = row[4 + k]
+            arr[s].rot[0], arr[s].rot[1] = row[7], row[8]
+        self._shapes = arr
+        ls = FcLevelset(len(shapes), C.cast(arr, C.POINTER(FcShape)))
+        self.h = C.c_void_p()
+        st = self.lib.fc_setup(C.byref(self.h), C.byref(_grid(prob)), C.byref(ls), float(prob.alpha),
+                               int(prob.nlevels), C.byref(_options(prob, cache, prec, nu)),
+                               C.c_void_p(self.stream.cuda_stream))
+        self._check(st)
+
+    # ---------------------------------------------------------------- util
+    def _check(self, st):
+        if st != FC_OK:
+            msg = self.lib.fc_last_error(self.h).decode() if self.h else ""
+            raise FcError(st, msg)
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.fc_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ndof(self, level=None) -> int:
+        n = C.c_longlong()
+        self._check(self.lib.fc_info(self.h, self.nlevels if level is None else level,
+                                     C.byref(n), None, None))
+        return n.value
+
+    def info(self, level=None):
+        n, p = C.c_longlong(), C.c_longlong()
+        parts = (C.c_size_t * 8)()
+        self._check(self.lib.fc_info(self.h, self.nlevels if level is None else level,
+                                     C.byref(n), C.byref(p), parts))
+        return {"ndof": n.value, "npatch": p.value, "bytes": list(parts)}
+
+    def zeros(self, level=None):
+        return self.torch.zeros(self.ndof(level), dtype=self.torch.float64, device="cuda")
+
+    def _dev(self, v):
+        t = v if self.torch.is_tensor(v) else self.torch.as_tensor(np.asarray(v, dtype=np.float64))
+        return t.to(device="cuda", dtype=self.torch.float64).contiguous()
+
+    @staticmethod
+    def _ptr(t):
+        return C.c_void_p(t.data_ptr())
+
+    # ---------------------------------------------------------------- ABI calls
+    def rhs(self):
+        b = self.zeros()
+        self._check(self.lib.fc_rhs(self.h, self._ptr(b)))
+        return b
+
+    def residual(self, x, b, level=None):
+        lv = self.nlevels if level is None else level
+        x, b = self._dev(x), self._dev(b)
+        r = self.zeros(lv)
+        self._check(self.lib.fc_residual(self.h, lv, self._ptr(x), self._ptr(b), self._ptr(r)))
+        return r
+
+    def apply(self, x, level=None):
+        lv = self.nlevels if level is None else level
+        x = self._dev(x)
+        y = self.zeros(lv)
+        self._check(self.lib.fc_apply(self.h, lv, self._ptr(x), self._ptr(y)))
+        return y
+
+    def smooth(self, x, b, level=None, nsweeps=1):
+        """Returns a new vector: x after ``nsweeps`` RA sweeps."""
+        lv = self.nlevels if level is None else level
+        xx = self._dev(x).clone()
+        b = self._dev(b)
+        self._check(self.lib.fc_smooth(self.h, lv, self._ptr(xx), self._ptr(b), int(nsweeps)))
+        return xx
+
+    def smooth_(self, x, b, level=None, nsweeps=1):
+        """In-place smoother on device tensors (no copies)."""
+        lv = self.nlevels if level is None else level
+        self._check(self.lib.fc_smooth(self.h, lv, self._ptr(x), self._ptr(b), int(nsweeps)))
+        return x
+
+    def restrict(self, r, level=None):
+        lv = self.nlevels if level is None else level
+        r = self._dev(r)
+        bc = self.zeros(lv - 1)
+        self._check(self.lib.fc_restrict(self.h, lv, self._ptr(r), self._ptr(bc)))
+        return bc
+
+    def prolong_add(self, e, x, level=None):
+        lv = self.nlevels if level is None else level
+        e = self._dev(e)
+        xx = self._dev(x).clone()
+        self._check(self.lib.fc_prolong_add(self.h, lv, self._ptr(e), self._ptr(xx)))
+        return xx
+
+    def coarse_solve(self, b):
+        b = self._dev(b)
+        x = self.zeros(1)
+        self._check(self.lib.fc_coarse_solve(self.h, self._ptr(b), self._ptr(x)))
+        return x
+
+    def vcycle(self, x, b):
+        xx = self._dev(x).clone()
+        b = self._dev(b)
+        self._check(self.lib.fc_vcycle(self.h, self._ptr(xx), self._ptr(b)))
+        return xx
+
+    def solve(self, b, x0=None, rtol=None, maxit=200):
+        """FGMRES + GMG; returns (x, iterations, true relative residual)."""
+        b = self._dev(b)
+        x = self.zeros() if x0 is None else self._dev(x0).clone()
+        its, rel = C.c_int(), C.c_double()
+        st = self.lib.fc_solve(self.h, self._ptr(b), self._ptr(x),
+                               float(self.prob.rtol if rtol is None else rtol), int(maxit),
+                               C.byref(its), C.byref(rel))
+        if st not in (FC_OK, FC_ERR_NOT_CONVERGED):
+            self._check(st)
+        return x, its.value, rel.value
+
+    def solve_host(self, b_host, x_host, rtol=None, maxit=200):
+        """FGMRES + GMG from host buffers (numpy or pinned torch CPU tensors)."""
+        def ptr(a):
+            if self.torch.is_tensor(a):
+                return C.c_void_p(a.data_ptr())
+            return a.ctypes.data_as(C.c_void_p)
+        its, rel = C.c_int(), C.c_double()
+        st = self.lib.fc_solve_host(self.h, ptr(b_host), ptr(x_host),
+                                    float(self.prob.rtol if rtol is None else rtol), int(maxit),
+                                    C.byref(its), C.byref(rel))
+        if st not in (FC_OK, FC_ERR_NOT_CONVERGED):
+            self._check(st)
+        return its.value, rel.value
+
+    def patch_rows(self, node: int, level=None):
+        lv = self.nlevels if level is None else level
+        ns = 402 if self.dim == 3 else 59
+        out = np.zeros((self.nd, ns))
+        self._check(self.lib.fc_patch_rows(self.h, lv, int(node),
+                                           out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def profile(self, on: bool = True):
+        self._check(self.lib.fc_profile_enable(self.h, 1 if on else 0))
+
+    def profile_read(self, kind: int):
+        n, ms, by = C.c_longlong(), C.c_double(), C.c_double()
+        self._check(self.lib.fc_profile_read(self.h, int(kind), C.byref(n), C.byref(ms), C.byref(by)))
+        return n.value, ms.value, by.value
+
+    def sync(self):
+        self._check(self.lib.fc_sync(self.h))

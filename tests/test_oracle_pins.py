@@ -103,7 +103,7 @@ def test_stabilisation_annihilates_constants(dim):
     """c(q, 1) = 0 for every q (q - Pi0 q has zero cell mean), c is symmetric
     negative semidefinite with a one-dimensional kernel per cell."""
     L = level(dim, 4, circle(0.5, 0.5, 0.3) if dim == 2 else sphere((0.5, 0.5, 0.5), 0.3))
-    for cell in (0, 7, 21):
+    for cell in (0, 7, 13 if dim == 2 else 21):
         Cm = L.cell_element(cell)["C"]
         np.testing.assert_allclose(Cm.sum(axis=1), 0.0, atol=1e-14 * np.abs(Cm).max())
         np.testing.assert_array_equal(Cm, Cm.T)
