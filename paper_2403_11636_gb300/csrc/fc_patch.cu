@@ -211,8 +211,9 @@ __global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
       int op[3], oq[3], d[3];
       prs_off<DIM>(p, op);
       prs_off<DIM>(q, oq);
-      for (int k = 0; k < 3; ++k) d[k] = oq[k] - op[k];
-      val = st[((long long)nb_index<DIM>(d) * SP + 1 + 2 * DIM) * g.nnodes + nodeP[p]];
+      bool adj = true;
+      for (int k = 0; k < 3; ++k) { d[k] = oq[k] - op[k]; if (d[k] < -1 || d[k] > 1) adj = false; }
+      if (adj) val = st[((long long)nb_index<DIM>(d) * SP + 1 + 2 * DIM) * g.nnodes + nodeP[p]];
     } else if (p == q) {
       val = 1.0;
     }
