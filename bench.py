@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark: FGMRES-GMG solves of the 3D porous-medium finite cell Stokes
+problem (64^3 background grid, 40 seeded spheres, alpha = 1e-8, octree depth 3,
+5 levels, V(2,2), rtol 1e-8) with the restricted additive smoother.
+
+A step is one complete solve from x0 = 0 on the resident hierarchy (operator,
+patch caches and coarse inverse built once per problem by fc_setup, whose time
+is reported separately as setup_ms).  The metric is smoother owned-DoF
+updates per second: every sweep of every smoothed level updates each free DoF
+once, so one solve performs  its * (nu_pre + nu_post) * sum_l free_dofs(l)
+updates.  value = those updates over all ranks / max-over-ranks wall time of
+the K timed solves (CUDA events on the solver's stream).
+
+--impl reference times the FP64 CPU oracle (the plain implementation the
+tests compare against) on the host cores, on a bounded sample of the same
+workload (a 16^3 grid of the same sphere geometry, 3 levels).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "smoother patch-DoF updates/s"
+UNIT = "owned-DoF updates/s"
+
+
+def free_dofs(prob, level):
+    """Free (unconstrained) DoFs of a level: counting only."""
+    n = prob.level_n(level)
+    dim = prob.dim
+    nodes = 1
+    for k in n:
+        nodes *= k + 1
+    if prob.preset == 1:
+        inner = (n[1] - 1) * ((n[2] - 1) if dim == 3 else 1) * (n[0] + 1)
+        fixed_nodes = nodes - inner
+    elif prob.preset == 0:
+        inner = n[0] * (n[1] - 1) * ((n[2] - 1) if dim == 3 else 1)
+        fixed_nodes = nodes - inner
+    else:
+        fixed_nodes = 0
+    return nodes * (dim + 1) - fixed_nodes * dim
+
+
+def updates_per_solve(prob, its):
+    per_cycle = sum(free_dofs(prob, l) for l in range(2, prob.nlevels + 1)) * (prob.nu_pre + prob.nu_post)
+    return its * per_cycle
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, maxes, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [t.strip() for t in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sms.append(float(f[1]))
+                    maxes.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxes), "samples": len(sms),
+                "reasons": sorted(reasons)}
+
+
+def workload(seed=0):
+    from paper_2403_11636_gb300 import inputs
+    return inputs.porous_3d(seed)
+
+
+def sample_workload(seed=0):
+    from paper_2403_11636_gb300 import inputs
+    return inputs.porous_3d(seed, n=16, nlevels=3)
+
+
+def oracle_solve_rate(prob, budget_s=15.0, steps=None):
+    """Oracle FGMRES-GMG solves on the host cores; returns rates per solve."""
+    from oracle import oracle as O
+    mg = O.MG(prob)                     # assembly + cached inverse rows (setup, untimed)
+    b = mg.rhs()
+    times, its_all = [], []
+    t_start = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        _, its, rr, _ = mg.fgmres(b, rtol=prob.rtol, restart=prob.restart)
+        times.append(time.perf_counter() - t0)
+        its_all.append(its)
+        if steps is not None and len(times) >= steps:
+            break
+        if steps is None and time.perf_counter() - t_start >= budget_s:
+            break
+    ups = [updates_per_solve(prob, i) for i in its_all]
+    return ups, times, O.num_threads(), its_all
+
+
+def emit(d):
+    print(json.dumps(d), flush=True)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    prob = sample_workload()
+    from oracle import oracle as O
+    O.build()
+    mg_warm = None
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_solve_rate(prob, steps=1)
+    ups, times, cores, its = oracle_solve_rate(prob, steps=args.steps)
+    value = sum(ups) / sum(times)
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+          "data": "synthetic",
+          "config": {"workload": "porous3d sample: 16^3 grid, the 40-sphere geometry of seed 0, 3 levels, "
+                                 "V(2,2), FGMRES(30) to 1e-8", "iterations": its[0]},
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": "oracle FGMRES-GMG solves on the 16^3 sample, setup excluded"},
+          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    del mg_warm
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2403_11636_gb300 import build, fc
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prob = workload(seed=rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        s = fc.Solver(prob, cache=args.cache, prec=args.prec, stream=stream)
+        torch.cuda.synchronize()
+        setup_ms = 1e3 * (time.perf_counter() - t0)
+        b = s.rhs()
+        for _ in range(args.warmup):
+            x, its, rr = s.solve(b, rtol=prob.rtol)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = Clocks(local_rank)
+        clocks.start()
+        s.profile(True)
+        l0 = fc.launch_count()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        ev[0].record(stream)
+        its_list, rr_list = [], []
+        for k in range(args.steps):
+            x, its, rr = s.solve(b, rtol=prob.rtol)
+            its_list.append(its)
+            rr_list.append(rr)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        launches = fc.launch_count() - l0
+        cl = clocks.stop()
+        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+        total_ms = ev[0].elapsed_time(ev[-1])
+        n_apply, ms_apply, bytes_apply = s.profile_read(0)
+        n_res, ms_res, _ = s.profile_read(1)
+        n_vc, ms_vc, _ = s.profile_read(2)
+        s.profile(False)
+        if dist:
+            dist.barrier()
+        # ---- end to end through the public API with host buffers
+        n = s.ndof()
+        bh = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        bh.copy_(b.cpu())
+        xh = torch.zeros(n, dtype=torch.float64, pin_memory=True)
+        s.solve_host(bh, xh, rtol=prob.rtol)
+        e2e_t = []
+        for _ in range(args.steps):
+            xh.zero_()
+            t1 = time.perf_counter()
+            its_h, rr_h = s.solve_host(bh, xh, rtol=prob.rtol)
+            e2e_t.append(time.perf_counter() - t1)
+        # ---- cache policies and precisions on the finest level: one sweep each
+        variants = {}
+        if args.policies and rank == 0:
+            variants = policy_sweeps(prob, stream, args)
+    my_updates = sum(updates_per_solve(prob, i) for i in its_list)
+    my_e2e_updates = updates_per_solve(prob, its_h) * len(e2e_t)
+    t = torch.tensor([total_ms, sum(e2e_t) * 1e3, float(my_updates), float(my_e2e_updates)], device="cuda",
+                     dtype=torch.float64)
+    if dist:
+        mx = t.clone()
+        dist.all_reduce(mx[:2], op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm[2:], op=dist.ReduceOp.SUM)
+        total_ms, e2e_ms, all_updates, all_e2e = mx[0].item(), mx[1].item(), sm[2].item(), sm[3].item()
+    else:
+        e2e_ms, all_updates, all_e2e = sum(e2e_t) * 1e3, float(my_updates), float(my_e2e_updates)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    hbm, peak_kind = peaks()
+    achieved = (bytes_apply * n_apply) / (ms_apply * 1e-3) / 1e9 if ms_apply > 0 else 0.0
+    traffic = load_traffic(args.prec)
+    step_sorted = sorted(step_ms)
+    p50 = statistics.median(step_sorted)
+    p99 = step_sorted[min(len(step_sorted) - 1, int(math.ceil(0.99 * len(step_sorted))) - 1)]
+    out = {
+        "metric": METRIC, "value": all_updates / (total_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "df64": "f32x2", "fp32": "f32", "bf16": "bf16"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": "porous3d 64^3 background grid, 40 non-overlapping seeded spheres "
+                               "r~U[0.04,0.12], alpha 1e-8, octree depth 3, 5 levels, V(2,2), "
+                               "FGMRES(30) rtol 1e-8, Q1-Q1 (1,098,500 DoFs)",
+                   "cache": args.cache, "patch_rows": args.prec,
+                   "l2": "inputs larger than L2 (cached rows 3.5 GB per sweep)",
+                   "iterations": its_list[0], "relres": max(rr_list), "setup_ms": setup_ms,
+                   "solves_per_s": world * args.steps / (total_ms * 1e-3),
+                   "latency_ms_p50": p50, "latency_ms_p99": p99,
+                   "smoother": {"apply_launches": n_apply, "apply_ms": ms_apply,
+                                "residual_launches": n_res, "residual_ms": ms_res,
+                                "vcycles": n_vc, "vcycle_ms": ms_vc},
+                   "parallelism": f"{world} independent problems, one per GPU" if world > 1 else "1 GPU",
+                   "variants": variants},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "kernel": "patch apply (cache_inverse), bytes-weighted over all smoothed levels",
+                     "peak_source": peak_kind},
+        "e2e": {"value": all_e2e / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8,
+                "d2h_bytes_per_step": n * 8},
+        "gpu_launches": launches,
+        "clocks": cl,
+    }
+    if not args.no_cpu_baseline:
+        ups, times, cores, _ = oracle_solve_rate(sample_workload(), budget_s=args.cpu_budget)
+        out["cpu_baseline"] = {"value": sum(ups) / sum(times), "unit": UNIT, "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"{len(times)} oracle FGMRES-GMG solves of a 16^3 grid of the "
+                                         f"same 40-sphere geometry (3 levels), setup excluded"}
+    emit(out)
+    if dist:
+        dist.destroy_process_group()
+    s.close()
+    return 0
+
+
+def policy_sweeps(prob, stream, args):
+    """One finest-level smoother sweep (residual + patch solve) per cache
+    policy / precision, CUDA events on the solver stream."""
+    import torch
+    from paper_2403_11636_gb300 import fc, inputs
+    res = {}
+    combos = [("inverse", "fp64"), ("inverse", "df64"), ("inverse", "fp32"), ("inverse", "bf16"),
+              ("matrix", "fp64"), ("none", "fp64")]
+    x0 = torch.as_tensor(inputs.random_vector(prob, 3)).cuda()
+    bb = torch.as_tensor(inputs.random_vector(prob, 4)).cuda()
+    upd = free_dofs(prob, prob.nlevels)
+    for cache, prec in combos:
+        try:
+            t0 = time.perf_counter()
+            s = fc.Solver(prob, cache=cache, prec=prec, stream=stream)
+            torch.cuda.synchronize()
+            setup = time.perf_counter() - t0
+            x = x0.clone()
+            reps = 1 if cache == "none" else 5
+            s.smooth_(x, bb, nsweeps=1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.profile(True)
+            e0.record(stream)
+            s.smooth_(x, bb, nsweeps=reps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            na, ma, ba = s.profile_read(0)
+            s.profile(False)
+            info = s.info()
+            res[f"{cache}/{prec}"] = {"sweep_ms": ms, "updates_per_s": upd / (ms * 1e-3),
+                                      "apply_ms": ma / max(na, 1),
+                                      "apply_gbs": (ba / (ma / max(na, 1) * 1e-3) / 1e9) if ma > 0 and ba > 0 else None,
+                                      "setup_ms": setup * 1e3,
+                                      "cache_bytes": info["bytes"][1]}
+            s.close()
+            del s
+        except Exception as e:  # a policy that does not fit reports why
+            res[f"{cache}/{prec}"] = {"error": str(e)[:200]}
+        torch.cuda.synchronize()
+    return res
+
+
+def load_traffic(prec):
+    """dram bytes per launch of the fine-level patch apply from the committed
+    ncu summary, if one exists for this precision."""
+    path = os.path.join(ROOT, "profiles", f"traffic_patch_apply_{prec}.json")
+    try:
+        with open(path) as f:
+            return json.load(f).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cache", default="inverse", choices=["inverse", "matrix", "none"])
+    ap.add_argument("--prec", default="df64", choices=["fp64", "df64", "fp32", "bf16"])
+    ap.add_argument("--policies", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -192,6 +192,10 @@ fc_status fc_profile_enable(fc_handle h, int on);
 fc_status fc_profile_read(fc_handle h, int kind, long long* launches, double* total_ms,
                           double* bytes_per_launch);
 
+/* Number of CUDA kernels libfc has launched in this process (all handles),
+ * for launch accounting around timed regions. */
+fc_status fc_launch_count(long long* count);
+
 /* Wait for all work enqueued by the handle. */
 fc_status fc_sync(fc_handle h);
 

@@ -5,11 +5,17 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "fc_internal.cuh"
 
 using namespace fc;
+
+namespace fc {
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace fc
 
 namespace {
 
@@ -405,6 +411,7 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
       CK(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), h->stream));
       count_active_kernel<<<(unsigned)((G.nnodes + 255) / 256), 256, 0, h->stream>>>(G, L.mask, d_count);
       CK(cudaGetLastError());
+      note_launches(1);
       unsigned long long cnt = 0;
       CK(cudaMemcpyAsync(&cnt, d_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaStreamSynchronize(h->stream));
@@ -602,6 +609,7 @@ fc_status fc_solve(fc_handle h, const double* b, double* x, double rtol, int max
       CK(launch_dot(n, h->w, h->w, h->red, hn, s));
       sqrt_kernel<<<1, 1, 0, s>>>(hn);
       CK(cudaGetLastError());
+      note_launches(1);
       CK(cudaMemcpyAsync(sc + 2, hn, sizeof(double), cudaMemcpyDeviceToDevice, s));
       CK(launch_scale_copy(n, hn, 0, 1, h->w, h->V + (long long)(j + 1) * n, s));
       CK(launch_givens(H, m, j, bn, s));
@@ -705,6 +713,12 @@ fc_status fc_profile_read(fc_handle h, int kind, long long* launches, double* to
 fc_status fc_sync(fc_handle h) {
   if (!h) return FC_ERR_INVALID;
   CK(cudaStreamSynchronize(h->stream));
+  return FC_OK;
+}
+
+fc_status fc_launch_count(long long* count) {
+  if (!count) return FC_ERR_INVALID;
+  *count = g_launches.load();
   return FC_OK;
 }
 

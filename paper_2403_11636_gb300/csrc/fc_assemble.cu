@@ -170,11 +170,13 @@ cudaError_t launch_assemble(const LevelGeom& g, const double* eA, const double* 
   unsigned blocks = (unsigned)((n + 255) / 256);
   if (g.dim == 2) assemble_kernel<2><<<blocks, 256, 0, s>>>(g, eA, eB, st);
   else assemble_kernel<3><<<blocks, 256, 0, s>>>(g, eA, eB, st);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_masks(const LevelGeom& g, unsigned char* mask, double* wfix, cudaStream_t s) {
   mask_kernel<<<(unsigned)((g.nnodes + 255) / 256), 256, 0, s>>>(g, mask, wfix);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -183,6 +185,7 @@ cudaError_t launch_rhs(const LevelGeom& g, const double* eF, const double* st,
   unsigned blocks = (unsigned)((g.nnodes + 127) / 128);
   if (g.dim == 2) rhs_kernel<2><<<blocks, 128, 0, s>>>(g, eF, st, mask, wfix, b);
   else rhs_kernel<3><<<blocks, 128, 0, s>>>(g, eF, st, mask, wfix, b);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -546,6 +546,7 @@ cudaError_t launch_cell_elements(const LevelGeom& g, double* eA, double* eB, dou
     cell_elements_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, eA, eB, eF, estat, d_err);
   else
     cell_elements_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, eA, eB, eF, estat, d_err);
+  note_launches(1);
   return cudaGetLastError();
 }
 

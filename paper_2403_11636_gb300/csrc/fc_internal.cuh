@@ -125,6 +125,9 @@ struct fc_handle_s {
 
 namespace fc {
 
+// process-wide count of libfc kernel launches (fc_api.cu)
+void note_launches(int n);
+
 // ---- launchers (defined in the .cu files) ----
 // geometry + element data (fc_geom.cu)
 cudaError_t launch_cell_elements(const LevelGeom& g, double* eA, double* eB, double* eF,

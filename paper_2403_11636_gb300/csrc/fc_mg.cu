@@ -400,6 +400,7 @@ cudaError_t launch_residual(const LevelGeom& g, const double* st, const unsigned
   unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
   if (g.dim == 2) residual_kernel<2, 0><<<blocks, 256, 0, s>>>(g, st, mask, x, b, r, rpad, nullptr);
   else residual_kernel<3, 0><<<blocks, 256, 0, s>>>(g, st, mask, x, b, r, rpad, nullptr);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -408,6 +409,7 @@ cudaError_t launch_residual_df(const LevelGeom& g, const double* st, const unsig
   unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
   if (g.dim == 2) residual_kernel<2, 1><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad2);
   else residual_kernel<3, 1><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad2);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -416,6 +418,7 @@ cudaError_t launch_residual_f32(const LevelGeom& g, const double* st, const unsi
   unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
   if (g.dim == 2) residual_kernel<2, 2><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad);
   else residual_kernel<3, 2><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -424,6 +427,7 @@ cudaError_t launch_restrict(const LevelGeom& f, const LevelGeom& c, const unsign
   unsigned blocks = (unsigned)((c.nnodes + 255) / 256);
   if (f.dim == 2) restrict_kernel<2><<<blocks, 256, 0, s>>>(f, c, cmask, rf, bc);
   else restrict_kernel<3><<<blocks, 256, 0, s>>>(f, c, cmask, rf, bc);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -432,11 +436,13 @@ cudaError_t launch_prolong_add(const LevelGeom& f, const LevelGeom& c, const uns
   unsigned blocks = (unsigned)((f.nnodes + 255) / 256);
   if (f.dim == 2) prolong_kernel<2><<<blocks, 256, 0, s>>>(f, c, fmask, ec, xf);
   else prolong_kernel<3><<<blocks, 256, 0, s>>>(f, c, fmask, ec, xf);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_zero_pad_halo(double* p, long long n, cudaStream_t s) {
   zero_kernel<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -449,12 +455,14 @@ cudaError_t launch_coarse_factor(const LevelGeom& g, const double* st, const uns
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dense_inverse_kernel<<<1, 1024, 0, s>>>((int)g.ndof, work, inv, piv, dsc, d_err);
+  note_launches(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_gemv(int n, const double* A, const double* x, double* y, cudaStream_t s) {
   long long threads = (long long)n * 32;
   gemv_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n, A, x, y);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -462,27 +470,32 @@ cudaError_t launch_dot(long long n, const double* a, const double* b, double* pa
                        cudaStream_t s) {
   dot_partial_kernel<<<kRedBlocks, 256, 0, s>>>(n, a, b, partial);
   sum_partial_kernel<<<1, 1024, 0, s>>>(kRedBlocks, partial, out);
+  note_launches(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy(long long n, double alpha, const double* x, double* y, cudaStream_t s) {
   axpy_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, alpha, x, y);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale_copy(long long n, const double* sc, int sidx, int invert, const double* x,
                               double* y, cudaStream_t s) {
   scale_copy_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, sc, sidx, invert, x, y);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mgs_step(long long n, double* w, const double* vi, const double* hij, cudaStream_t s) {
   mgs_step_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, w, vi, hij);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_givens(double* small, int m, int j, double bnorm, cudaStream_t s) {
   givens_kernel<<<1, 1, 0, s>>>(small, m, j, bnorm);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -490,6 +503,7 @@ cudaError_t launch_update_x(long long n, int k, int m, const double* small, cons
                             cudaStream_t s) {
   solve_y_kernel<<<1, 1, 0, s>>>(const_cast<double*>(small), m, k);
   update_x_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, k, m, small, Z, x);
+  note_launches(2);
   return cudaGetLastError();
 }
 

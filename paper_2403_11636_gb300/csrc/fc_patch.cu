@@ -715,6 +715,7 @@ cudaError_t run_factor(const LevelGeom& g, const double* st, const unsigned char
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)g.nnodes, PatchDims<DIM>::THREADS, sm, s>>>(g, st, mask, omega, coef, fac, fpiv, rpad, x, d_err);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -754,6 +755,7 @@ cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coe
     if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x);
     else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x);
   }
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -764,6 +766,7 @@ cudaError_t launch_factor_apply(const LevelGeom& g, const double* fac, const int
   unsigned blocks = (unsigned)((threads + 127) / 128);
   if (g.dim == 2) factor_apply_kernel<2><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x);
   else factor_apply_kernel<3><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -774,6 +777,7 @@ cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* 
   if (prec == FC_PREC_FP32) convert_kernel<float><<<blocks, 256, 0, s>>>(n, coef64, (float*)out);
   else if (prec == FC_PREC_BF16) convert_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(n, coef64, (__nv_bfloat16*)out);
   else if (prec == FC_PREC_DF64) convert_kernel<float2><<<blocks, 256, 0, s>>>(n, coef64, (float2*)out);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,8 @@ PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "df64": 3}
 EXPORTS = ("fc_options_default", "fc_setup", "fc_rhs", "fc_residual", "fc_apply", "fc_smooth",
            "fc_restrict", "fc_prolong_add", "fc_coarse_solve", "fc_vcycle", "fc_solve",
            "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
-           "fc_profile_enable", "fc_profile_read", "fc_sync", "fc_last_error", "fc_destroy")
+           "fc_profile_enable", "fc_profile_read", "fc_launch_count", "fc_sync", "fc_last_error",
+           "fc_destroy")
 
 
 class FcError(RuntimeError):
@@ -82,6 +83,7 @@ def load(path: str = LIB_PATH):
     lib.fc_footprint_estimate.argtypes = [P(FcGrid), i, P(FcOptions)]
     lib.fc_profile_enable.argtypes = [vp, i]
     lib.fc_profile_read.argtypes = [vp, i, P(ll), P(d), P(d)]
+    lib.fc_launch_count.argtypes = [P(ll)]
     lib.fc_sync.argtypes = [vp]
     lib.fc_last_error.restype = C.c_char_p
     lib.fc_last_error.argtypes = [vp]
@@ -116,6 +118,12 @@ def _options(prob, cache: str, prec: str, nu=None) -> FcOptions:
     for k in range(3):
         o.force[k] = float(prob.force[k])
     return o
+
+
+def launch_count() -> int:
+    n = C.c_longlong()
+    load().fc_launch_count(C.byref(n))
+    return n.value
 
 
 def footprint_estimate(prob, cache="inverse", prec="fp64") -> int:
