@@ -137,6 +137,23 @@ fc_status fc_apply(fc_handle h, int level, const double* x_dev, double* y_dev);
  * (the coarsest level has no patch cache; use fc_coarse_solve). */
 fc_status fc_smooth(fc_handle h, int level, double* x_dev, const double* b_dev, int nsweeps);
 
+/* As fc_smooth, but allocates nothing: the padded residual it needs lives in
+ * one file-scope static device array of 16 MiB (held on every GPU that loads
+ * the library until exit) instead of in handle memory.  The paper has no
+ * counterpart; this is for callers that cannot allocate at call time, such
+ * as a serving runtime that reserved its device memory up front, or a loop
+ * that must not enter the CUDA allocator (cudaMalloc/cudaFree can
+ * synchronise the device).  The caller passes x (in/out) and b as for
+ * fc_smooth; the handle's operator and patch cache are used read-only.
+ * The first call on a device looks up the array's address
+ * (cudaGetSymbolAddress, with that device current); make that call before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents: each call clears the part it uses first.  Calls whose
+ * work overlaps on the GPU race on the array.  Errors: FC_ERR_INVALID when
+ * the level's padded residual exceeds 16 MiB (3D up to 64^3 cells, 2D up to
+ * about 700^2 in float64), FC_ERR_CUDA. */
+fc_status fc_smooth_noalloc(fc_handle h, int level, double* x_dev, const double* b_dev, int nsweeps);
+
 /* b_coarse <- R r_fine from `level` to `level-1` (eq. restriction_op with the
  * transfer T the identity on one GPU; R = P^T, Q1 full weighting on every
  * component); constrained coarse DoFs are set to zero. */

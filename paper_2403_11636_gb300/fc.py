@@ -19,7 +19,7 @@ FC_ERR_NOT_CONVERGED, FC_ERR_SINGULAR, FC_ERR_TIMEOUT = 4, 5, 6
 CACHE = {"inverse": 0, "matrix": 1, "none": 2}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "df64": 3}
 EXPORTS = ("fc_options_default", "fc_setup", "fc_rhs", "fc_residual", "fc_apply", "fc_smooth",
-           "fc_restrict", "fc_prolong_add", "fc_coarse_solve", "fc_vcycle", "fc_solve",
+           "fc_smooth_noalloc", "fc_restrict", "fc_prolong_add", "fc_coarse_solve", "fc_vcycle", "fc_solve",
            "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
            "fc_profile_enable", "fc_profile_read", "fc_launch_count", "fc_sync", "fc_last_error",
            "fc_destroy")
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
     lib.fc_residual.argtypes = [vp, i, vp, vp, vp]
     lib.fc_apply.argtypes = [vp, i, vp, vp]
     lib.fc_smooth.argtypes = [vp, i, vp, vp, i]
+    lib.fc_smooth_noalloc.argtypes = [vp, i, vp, vp, i]
     lib.fc_restrict.argtypes = [vp, i, vp, vp]
     lib.fc_prolong_add.argtypes = [vp, i, vp, vp]
     lib.fc_coarse_solve.argtypes = [vp, vp, vp]
@@ -236,6 +237,12 @@ class Solver:
         lv = self.nlevels if level is None else level
         self._check(self.lib.fc_smooth(self.h, lv, self._ptr(x), self._ptr(b), int(nsweeps)))
         return x
+
+    def smooth_noalloc_(self, x, b, level=None, nsweeps=1):
+        """In-place smoother that allocates nothing (static device scratch);
+        returns the status code so callers can inspect rejections."""
+        lv = self.nlevels if level is None else level
+        return self.lib.fc_smooth_noalloc(self.h, lv, self._ptr(x), self._ptr(b), int(nsweeps))
 
     def restrict(self, r, level=None):
         lv = self.nlevels if level is None else level
