@@ -307,6 +307,38 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_sweeps(args):
+    """Finest-level smoother sweeps only (for bounded-size profiler captures):
+    setup of a porous problem with n^3 cells, then --warmup + --steps sweeps."""
+    import torch
+    from paper_2403_11636_gb300 import build, fc, inputs
+    build.build()
+    nlev = max(2, int(math.log2(args.n // 4)) + 1)
+    prob = inputs.porous_3d(0, n=args.n, nlevels=nlev)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = fc.Solver(prob, cache=args.cache, prec=args.prec, stream=stream)
+        x = torch.as_tensor(inputs.random_vector(prob, 3)).cuda()
+        b = torch.as_tensor(inputs.random_vector(prob, 4)).cuda()
+        s.smooth_(x, b, nsweeps=args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.profile(True)
+        e0.record(stream)
+        s.smooth_(x, b, nsweeps=args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        na, ma, ba = s.profile_read(0)
+        ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    upd = free_dofs(prob, prob.nlevels)
+    emit({"mode": "sweep", "workload": f"porous3d {args.n}^3 finest-level sweeps", "cache": args.cache,
+          "prec": args.prec, "sweep_ms": ms, "updates_per_s": upd / (ms * 1e-3),
+          "apply_ms": ma / max(na, 1), "apply_bytes": ba,
+          "apply_gbs": ba / (ma / max(na, 1) * 1e-3) / 1e9 if ma > 0 else None})
+    s.close()
+    return 0
+
+
 def policy_sweeps(prob, stream, args):
     """One finest-level smoother sweep (residual + patch solve) per cache
     policy / precision, CUDA events on the solver stream."""
@@ -373,12 +405,16 @@ def main():
     ap.add_argument("--policies", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep"])
+    ap.add_argument("--n", type=int, default=48, help="grid size of --mode sweep")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.mode == "sweep":
+        return run_sweeps(args)
     return run_ours(args, rank, world, local_rank)
 
 

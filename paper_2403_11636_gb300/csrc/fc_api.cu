@@ -340,6 +340,11 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     return fail(h, FC_ERR_INVALID, "invalid cache policy or precision");
   if (o->prec != FC_PREC_FP64 && o->cache != FC_CACHE_INVERSE)
     return fail(h, FC_ERR_INVALID, "reduced-precision storage applies to cache_inverse only");
+  {
+    long long nodes = 1;
+    for (int k = 0; k < g->dim; ++k) nodes *= (long long)g->n[k] + 1;
+    if (nodes >= (1LL << 30)) return fail(h, FC_ERR_INVALID, "grid too large (2^30 nodes at most)");
+  }
   int nshape = ls ? ls->nshapes : 0;
   if (nshape < 0 || (nshape > 0 && !ls->shapes)) return fail(h, FC_ERR_INVALID, "bad level set");
   std::vector<Shape> hs(nshape);

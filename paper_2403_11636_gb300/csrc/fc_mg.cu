@@ -24,8 +24,15 @@ __global__ void __launch_bounds__(256)
   constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
   long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g.nnodes) return;
-  int ia[3] = {(int)(node % g.nn[0]), (int)((node / g.nn[0]) % g.nn[1]),
-               DIM == 3 ? (int)(node / ((long long)g.nn[0] * g.nn[1])) : 0};
+  // 32-bit decode: 64-bit division would run on the slow FP64 pipe
+  int ia[3];
+  {
+    const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+    const unsigned t = u / nx;
+    ia[0] = (int)(u - t * nx);
+    ia[1] = DIM == 3 ? (int)(t % ny) : (int)t;
+    ia[2] = DIM == 3 ? (int)(t / ny) : 0;
+  }
   double acc[ND];
 #pragma unroll
   for (int c = 0; c < ND; ++c) acc[c] = 0.0;

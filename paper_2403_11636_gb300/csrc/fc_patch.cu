@@ -391,21 +391,43 @@ __global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
 // ---------------------------------------------------------------------------
 // cache_inverse apply: y = omega * Inv_i r_i, x[node i] += y.  One warp per
 // patch; lane handles slots j = lane + 32 t, reads the ND coefficients of the
-// slot (one vector load) and the residual entry of the slot from the padded
-// residual (no bounds checks: the zero halo covers the 5^d box).
+// slot with vector loads (streamed past L2: each row is read once per sweep)
+// and the residual entry of the slot from the padded residual, whose zero
+// halo covers the 5^d box so the gathers need no bounds checks.  The slot ->
+// residual offset table is built once per block in shared memory, and the
+// node index is decoded in 32-bit arithmetic (64-bit division would run on
+// the FP64 pipe, 1/70 of the FP32 rate on this part).
 template <int DIM>
-__device__ __forceinline__ long long slot_ridx(const LevelGeom& g, long long pbase, int j) {
-  constexpr int NU = PatchDims<DIM>::NU, ND = DIM + 1;
-  long long px = g.nn[0] + 4, py = g.nn[1] + 4;
-  int o[3], c;
-  if (j < NU * DIM) {
-    vel_off<DIM>(j / DIM, o);
-    c = j % DIM;
-  } else {
-    prs_off<DIM>(j - NU * DIM, o);
-    c = DIM;
+__device__ __forceinline__ void slot_table(const LevelGeom& g, int* soff) {
+  constexpr int NU = PatchDims<DIM>::NU, ND = DIM + 1, NSLOT = PatchDims<DIM>::NSLOT;
+  const int px = g.nn[0] + 4, py = g.nn[1] + 4;
+  for (int j = threadIdx.x; j < NSLOT; j += blockDim.x) {
+    int o[3], c;
+    if (j < NU * DIM) {
+      vel_off<DIM>(j / DIM, o);
+      c = j % DIM;
+    } else {
+      prs_off<DIM>(j - NU * DIM, o);
+      c = DIM;
+    }
+    soff[j] = (o[0] + px * (o[1] + py * o[2])) * ND + c;
   }
-  return (pbase + o[0] + px * (o[1] + py * o[2])) * ND + c;
+  __syncthreads();
+}
+
+template <int DIM>
+__device__ __forceinline__ void decode_node(const LevelGeom& g, unsigned i, int* ia) {
+  const unsigned nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+  unsigned t = i / nx;
+  ia[0] = (int)(i - t * nx);
+  if (DIM == 3) {
+    unsigned u = t / ny;
+    ia[1] = (int)(t - u * ny);
+    ia[2] = (int)u;
+  } else {
+    ia[1] = (int)t;
+    ia[2] = 0;
+  }
 }
 
 template <int DIM>
@@ -427,25 +449,29 @@ __global__ void __launch_bounds__(256)
                       const double* __restrict__ rpad, double omega, double* __restrict__ x) {
   using P = PatchDims<DIM>;
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
+  __shared__ int soff[NSLOT];
+  slot_table<DIM>(g, soff);
   const int lane = threadIdx.x & 31;
-  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= g.nnodes) return;
-  int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
-               DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
-  long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
-  const double* cf = coef + i * (long long)NSLOT * ND;
+  const unsigned i = (unsigned)(((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= (unsigned)g.nnodes) return;
+  int ia[3];
+  decode_node<DIM>(g, i, ia);
+  const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
+  const double* rp = rpad + pbase * ND;
+  const double* cf = coef + (size_t)i * NSLOT * ND;
   double y[ND];
 #pragma unroll
   for (int k = 0; k < ND; ++k) y[k] = 0.0;
+#pragma unroll 2
   for (int j = lane; j < NSLOT; j += 32) {
-    double rv = rpad[slot_ridx<DIM>(g, pbase, j)];
+    double rv = rp[soff[j]];
     if (ND == 4) {
-      const double2* c2 = reinterpret_cast<const double2*>(cf + (long long)j * 4);
-      double2 a = __ldg(c2), b = __ldg(c2 + 1);
+      const double2* c2 = reinterpret_cast<const double2*>(cf + (size_t)j * 4);
+      double2 a = __ldcs(c2), b = __ldcs(c2 + 1);
       y[0] += a.x * rv; y[1] += a.y * rv; y[2] += b.x * rv; y[ND - 1] += b.y * rv;
     } else {
 #pragma unroll
-      for (int k = 0; k < ND; ++k) y[k] += __ldg(cf + (long long)j * ND + k) * rv;
+      for (int k = 0; k < ND; ++k) y[k] += __ldcs(cf + (size_t)j * ND + k) * rv;
     }
   }
 #pragma unroll
@@ -453,45 +479,73 @@ __global__ void __launch_bounds__(256)
     for (int o = 16; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
   if (lane == 0) {
     double rc[ND];
-    for (int c = 0; c < ND; ++c) rc[c] = rpad[pbase * ND + c];
+    for (int c = 0; c < ND; ++c) rc[c] = rp[c];
     finish_update<DIM>(g, i, ia, mask, rc, y, omega, x);
   }
 }
 
 // float32 / bfloat16 rows with float32 residual and float32 accumulation
+template <typename T>
+__device__ __forceinline__ void load_row4(const T* p, float* v);
+template <>
+__device__ __forceinline__ void load_row4<float>(const float* p, float* v) {
+  float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void load_row4<__nv_bfloat16>(const __nv_bfloat16* p, float* v) {
+  uint2 a = __ldcs(reinterpret_cast<const uint2*>(p));
+  v[0] = __uint_as_float(a.x << 16); v[1] = __uint_as_float(a.x & 0xffff0000u);
+  v[2] = __uint_as_float(a.y << 16); v[3] = __uint_as_float(a.y & 0xffff0000u);
+}
+
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
     apply_lowp_kernel(LevelGeom g, const T* __restrict__ coef, const unsigned char* __restrict__ mask,
                       const float* __restrict__ rpad, double omega, double* __restrict__ x) {
   using P = PatchDims<DIM>;
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
+  __shared__ int soff[NSLOT];
+  slot_table<DIM>(g, soff);
   const int lane = threadIdx.x & 31;
-  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= g.nnodes) return;
-  int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
-               DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
-  long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
-  const T* cf = coef + i * (long long)NSLOT * ND;
+  const unsigned i = (unsigned)(((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= (unsigned)g.nnodes) return;
+  int ia[3];
+  decode_node<DIM>(g, i, ia);
+  const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
+  const float* rp = rpad + pbase * ND;
+  const T* cf = coef + (size_t)i * NSLOT * ND;
   float y[ND];
 #pragma unroll
   for (int k = 0; k < ND; ++k) y[k] = 0.0f;
+#pragma unroll 2
   for (int j = lane; j < NSLOT; j += 32) {
-    float rv = rpad[slot_ridx<DIM>(g, pbase, j)];
+    float rv = rp[soff[j]];
+    float cv[4];
+    if (ND == 4) {
+      load_row4<T>(cf + (size_t)j * 4, cv);
+    } else {
 #pragma unroll
-    for (int k = 0; k < ND; ++k) y[k] = fmaf((float)cf[(long long)j * ND + k], rv, y[k]);
+      for (int k = 0; k < ND; ++k) cv[k] = (float)cf[(size_t)j * ND + k];
+    }
+#pragma unroll
+    for (int k = 0; k < ND; ++k) y[k] = fmaf(cv[k], rv, y[k]);
   }
 #pragma unroll
   for (int k = 0; k < ND; ++k)
     for (int o = 16; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
   if (lane == 0) {
     double rc[ND], yd[ND];
-    for (int c = 0; c < ND; ++c) { rc[c] = (double)rpad[pbase * ND + c]; yd[c] = (double)y[c]; }
+    for (int c = 0; c < ND; ++c) { rc[c] = (double)rp[c]; yd[c] = (double)y[c]; }
     finish_update<DIM>(g, i, ia, mask, rc, yd, omega, x);
   }
 }
 
-// Double-float arithmetic (pairs hi + lo of float32, ~48-bit significand)
-// on the float32 pipes: products by the exact FMA split, sums by two-sum.
+// Float-pair arithmetic (hi + lo of float32, about 48-bit significand) on the
+// float32 pipes.  A product c r = (ch + cl)(rh + rl) is taken as the exact
+// ch rh split by one FMA plus the cross terms in float32; it is added to the
+// running sum with a two-sum on the high parts, the low parts accumulate
+// plainly and are folded in once at the end (Dekker 1971; Knuth TAOCP 4.2.2).
 struct df { float hi, lo; };
 __device__ __forceinline__ df df_two_sum(float a, float b) {
   float s = a + b;
@@ -509,13 +563,16 @@ __device__ __forceinline__ df df_add(df a, df b) {
   float h2 = hi + lo;
   return {h2, lo - (h2 - hi)};
 }
-__device__ __forceinline__ df df_mul(df a, df b) {
-  float p = a.hi * b.hi;
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  float hi = p + e;
-  return {hi, e - (hi - p)};
+// acc += c * r (c, r pairs); acc.lo collects every low-order term
+__device__ __forceinline__ void df_fma_acc(df& acc, float ch, float cl, float rh, float rl) {
+  float p = ch * rh;
+  float pe = fmaf(ch, rh, -p);
+  float cross = fmaf(ch, rl, cl * rh);
+  float s = acc.hi + p;
+  float bb = s - acc.hi;
+  float e = (acc.hi - (s - bb)) + (p - bb);
+  acc.hi = s;
+  acc.lo += e + (pe + cross);
 }
 
 template <int DIM>
@@ -524,35 +581,51 @@ __global__ void __launch_bounds__(256)
                     const float2* __restrict__ rpad, double omega, double* __restrict__ x) {
   using P = PatchDims<DIM>;
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
+  __shared__ int soff[NSLOT];
+  slot_table<DIM>(g, soff);
   const int lane = threadIdx.x & 31;
-  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= g.nnodes) return;
-  int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
-               DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
-  long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
-  const float2* cf = coef + i * (long long)NSLOT * ND;
+  const unsigned i = (unsigned)(((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (i >= (unsigned)g.nnodes) return;
+  int ia[3];
+  decode_node<DIM>(g, i, ia);
+  const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
+  const float2* rp = rpad + pbase * ND;
+  const float2* cf = coef + (size_t)i * NSLOT * ND;
   df y[ND];
 #pragma unroll
   for (int k = 0; k < ND; ++k) y[k] = {0.0f, 0.0f};
+#pragma unroll 2
   for (int j = lane; j < NSLOT; j += 32) {
-    float2 r2 = rpad[slot_ridx<DIM>(g, pbase, j)];
-    df rv = {r2.x, r2.y};
+    float2 r2 = rp[soff[j]];
+    float ch[4], cl[4];
+    if (ND == 4) {
+      const float4* c4 = reinterpret_cast<const float4*>(cf + (size_t)j * 4);
+      float4 a = __ldcs(c4), b = __ldcs(c4 + 1);
+      ch[0] = a.x; cl[0] = a.y; ch[1] = a.z; cl[1] = a.w;
+      ch[2] = b.x; cl[2] = b.y; ch[3] = b.z; cl[3] = b.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < ND; ++k) {
-      float2 c2 = __ldg(cf + (long long)j * ND + k);
-      y[k] = df_add(y[k], df_mul({c2.x, c2.y}, rv));
+      for (int k = 0; k < ND; ++k) {
+        float2 c2 = __ldcs(cf + (size_t)j * ND + k);
+        ch[k] = c2.x; cl[k] = c2.y;
+      }
     }
+#pragma unroll
+    for (int k = 0; k < ND; ++k) df_fma_acc(y[k], ch[k], cl[k], r2.x, r2.y);
   }
 #pragma unroll
-  for (int k = 0; k < ND; ++k)
+  for (int k = 0; k < ND; ++k) {
+    float h = y[k].hi + y[k].lo;
+    y[k] = {h, y[k].lo - (h - y[k].hi)};
     for (int o = 16; o > 0; o >>= 1) {
       df other = {__shfl_xor_sync(0xffffffffu, y[k].hi, o), __shfl_xor_sync(0xffffffffu, y[k].lo, o)};
       y[k] = df_add(y[k], other);
     }
+  }
   if (lane == 0) {
     double rc[ND], yd[ND];
     for (int c = 0; c < ND; ++c) {
-      float2 r2 = rpad[pbase * ND + c];
+      float2 r2 = rp[c];
       rc[c] = (double)r2.x + (double)r2.y;
       yd[c] = (double)y[c].hi + (double)y[c].lo;
     }
