@@ -329,11 +329,12 @@ def run_sweeps(args):
         e1.record(stream)
         torch.cuda.synchronize()
         na, ma, ba = s.profile_read(0)
+        nr, mr, _ = s.profile_read(1)
         ms = e0.elapsed_time(e1) / max(args.steps, 1)
     upd = free_dofs(prob, prob.nlevels)
     emit({"mode": "sweep", "workload": f"porous3d {args.n}^3 finest-level sweeps", "cache": args.cache,
           "prec": args.prec, "sweep_ms": ms, "updates_per_s": upd / (ms * 1e-3),
-          "apply_ms": ma / max(na, 1), "apply_bytes": ba,
+          "apply_ms": ma / max(na, 1), "apply_bytes": ba, "residual_ms": mr / max(nr, 1),
           "apply_gbs": ba / (ma / max(na, 1) * 1e-3) / 1e9 if ma > 0 else None})
     s.close()
     return 0

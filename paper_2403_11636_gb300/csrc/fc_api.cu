@@ -211,8 +211,31 @@ fc_status smoother_residual(fc_handle h, int li, const double* x, const double* 
   return FC_OK;
 }
 
+bool pair_path(fc_handle h) { return h->opt.cache == FC_CACHE_INVERSE && h->opt.prec == FC_PREC_DF64; }
+
+// Float-pair smoothing: x and (unless already current) b are split into
+// pairs once, then every sweep is a pair residual and a pair apply that
+// keeps the pair copy of x current.
+fc_status smooth_level_pairs(fc_handle h, int li, double* x, const double* b, int nsweeps, bool b_current) {
+  Level& L = h->lev[li];
+  if (nsweeps <= 0) return FC_OK;
+  CK(launch_split_x_padded(L.g, x, L.xp2, h->stream));
+  if (!b_current) CK(launch_split_pairs(L.g.ndof, b, L.bp2, h->stream));
+  for (int s = 0; s < nsweeps; ++s) {
+    {
+      ProfScope ps(h, 1, 0.0);
+      CK(launch_residual_df2(L.g, L.st2, L.mask, L.xp2, L.bp2, (float2*)L.rpad32, nullptr, h->stream));
+    }
+    ProfScope ps(h, 0, level_apply_bytes(h, li));
+    CK(launch_patch_apply_df2(L.g, L.coef, L.mask, L.rpad32, h->opt.omega, L.xp2, h->stream));
+  }
+  CK(launch_merge_x_padded(L.g, L.xp2, x, h->stream));
+  return FC_OK;
+}
+
 fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nsweeps) {
   Level& L = h->lev[li];
+  if (pair_path(h)) return smooth_level_pairs(h, li, x, b, nsweeps, false);
   for (int s = 0; s < nsweeps; ++s) {
     fc_status st = smoother_residual(h, li, x, b);
     if (st != FC_OK) return st;
@@ -238,14 +261,29 @@ fc_status vcycle_level(fc_handle h, int li, double* x, const double* b) {
     return FC_OK;
   }
   Level& C = h->lev[li - 1];
-  fc_status st = smooth_level(h, li, x, b, h->opt.nu_pre);
-  if (st != FC_OK) return st;
-  CK(launch_residual(L.g, L.st, L.mask, x, b, L.r, nullptr, h->stream));
+  fc_status st;
+  if (pair_path(h)) {
+    // b is split once per level visit; x after the pre-sweeps is current in
+    // pairs, so the residual for the restriction is a pair residual too
+    CK(launch_split_pairs(L.g.ndof, b, L.bp2, h->stream));
+    if (h->opt.nu_pre > 0) {
+      st = smooth_level_pairs(h, li, x, b, h->opt.nu_pre, true);
+      if (st != FC_OK) return st;
+    } else {
+      CK(launch_split_x_padded(L.g, x, L.xp2, h->stream));
+    }
+    CK(launch_residual_df2(L.g, L.st2, L.mask, L.xp2, L.bp2, nullptr, L.r, h->stream));
+  } else {
+    st = smooth_level(h, li, x, b, h->opt.nu_pre);
+    if (st != FC_OK) return st;
+    CK(launch_residual(L.g, L.st, L.mask, x, b, L.r, nullptr, h->stream));
+  }
   CK(launch_restrict(L.g, C.g, C.mask, L.r, C.b, h->stream));
   CK(cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.ndof, h->stream));
   st = vcycle_level(h, li - 1, C.x, C.b);
   if (st != FC_OK) return st;
   CK(launch_prolong_add(L.g, C.g, L.mask, C.x, x, h->stream));
+  if (pair_path(h)) return smooth_level_pairs(h, li, x, b, h->opt.nu_post, true);
   return smooth_level(h, li, x, b, h->opt.nu_post);
 }
 
@@ -396,6 +434,14 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     CK(dalloc(h, &L.r, (size_t)G.ndof, 2));
     CK(dalloc(h, &L.rpad, (size_t)padn * nd, 2));
     CK(cudaMemsetAsync(L.rpad, 0, sizeof(double) * padn * nd, h->stream));
+    if (li > 0 && o->cache == FC_CACHE_INVERSE && o->prec == FC_PREC_DF64) {
+      size_t nst = (size_t)G.nnodes * nb * spn(dim);
+      CK(dalloc(h, &L.st2, nst, 0));
+      CK(launch_fold_stencil_pairs(G, L.st, L.mask, L.st2, h->stream));
+      CK(dalloc(h, &L.xp2, (size_t)pad_nodes(G) * nd, 2));
+      CK(cudaMemsetAsync(L.xp2, 0, sizeof(float2) * pad_nodes(G) * nd, h->stream));
+      CK(dalloc(h, &L.bp2, (size_t)G.ndof, 2));
+    }
     if (need_r32(o->prec)) {
       CK(dalloc(h, &L.rpad32, (size_t)padn * nd * 2, 2));
       CK(cudaMemsetAsync(L.rpad32, 0, sizeof(float) * padn * nd * 2, h->stream));
@@ -737,6 +783,7 @@ fc_status fc_destroy(fc_handle h) {
     Level& L = h->lev[l];
     cudaFree(L.st); cudaFree(L.mask); cudaFree(L.wfix); cudaFree(L.coef); cudaFree(L.fac); cudaFree(L.fpiv);
     cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); cudaFree(L.rpad); cudaFree(L.rpad32);
+    cudaFree(L.st2); cudaFree(L.xp2); cudaFree(L.bp2);
   }
   cudaFree(h->d_shapes); cudaFree(h->d_err); cudaFree(h->coarse_inv);
   cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->red); cudaFree(h->small);

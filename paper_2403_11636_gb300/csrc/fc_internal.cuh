@@ -83,6 +83,12 @@ struct Level {
   double* r = nullptr;          // unpadded residual
   double* rpad = nullptr;       // padded residual (smoother)
   float* rpad32 = nullptr;      // padded residual in float32 / pairs (mixed paths)
+  // float-pair smoother state (FC_PREC_DF64): the stencil as (hi, lo) pairs
+  // with constrained columns folded in (zero), a padded pair copy of x (zero
+  // halo) that a smoothing phase updates in place, and a pair copy of b
+  float2* st2 = nullptr;
+  float2* xp2 = nullptr;
+  float2* bp2 = nullptr;
   size_t vec_bytes = 0;
   unsigned long long active_slots = 0;  // sum over patches of active patch DoFs
 };
@@ -155,6 +161,19 @@ cudaError_t launch_zero_pad_halo(double* p, long long n, cudaStream_t s);
 cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsigned char* mask,
                                int mode, double omega, double* coef64, double* fac, int* fpiv,
                                const double* rpad, double* x, unsigned* d_err, cudaStream_t s);
+// float-pair smoother pieces: split float64 into (hi, lo) pairs; residual
+// from the pair stencil and pair vectors into the padded pair residual
+// and/or an unpadded float64 residual; pair apply that also refreshes x2
+cudaError_t launch_split_pairs(long long n, const double* in, float2* out, cudaStream_t s);
+cudaError_t launch_fold_stencil_pairs(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                      float2* st2, cudaStream_t s);
+cudaError_t launch_split_x_padded(const LevelGeom& g, const double* x, float2* xp2, cudaStream_t s);
+cudaError_t launch_merge_x_padded(const LevelGeom& g, const float2* xp2, double* x, cudaStream_t s);
+cudaError_t launch_residual_df2(const LevelGeom& g, const float2* st2, const unsigned char* mask,
+                                const float2* xp2, const float2* b2, float2* rpad2, double* r,
+                                cudaStream_t s);
+cudaError_t launch_patch_apply_df2(const LevelGeom& g, const void* coef, const unsigned char* mask,
+                                   const float* rpad2, double omega, float2* xp2, cudaStream_t s);
 cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
                                const unsigned char* mask, const double* rpad, const float* rpad32,
                                double omega, double* x, cudaStream_t s);

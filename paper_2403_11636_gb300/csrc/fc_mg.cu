@@ -81,6 +81,158 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------
+// float-pair residual for the smoother (FC_PREC_DF64): the stencil, x and b
+// as (hi, lo) pairs of float32, products by the exact FMA split plus cross
+// terms, sums by two-sum of the high parts with the low parts collected
+// apart (about 48-bit significand), all on the float32 pipes.
+struct dfp { float hi, lo; };
+__device__ __forceinline__ void dfacc(dfp& acc, float2 a, float2 b) {
+  float p = a.x * b.x;
+  float pe = fmaf(a.x, b.x, -p);
+  float cross = fmaf(a.x, b.y, a.y * b.x);
+  float s = acc.hi + p;
+  float bb = s - acc.hi;
+  float e = (acc.hi - (s - bb)) + (p - bb);
+  acc.hi = s;
+  acc.lo += e + (pe + cross);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    residual_df2_kernel(LevelGeom g, const float2* __restrict__ st2, const unsigned char* __restrict__ mask,
+                        const float2* __restrict__ xp2, const float2* __restrict__ b2,
+                        float2* __restrict__ rpad2, double* __restrict__ r) {
+  // st2 has constrained columns folded to zero and xp2 is padded with a zero
+  // halo, so the 3^d neighbour loop has no branches
+  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
+  long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nnodes) return;
+  int ia[3];
+  {
+    const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+    const unsigned t = u / nx;
+    ia[0] = (int)(u - t * nx);
+    ia[1] = DIM == 3 ? (int)(t % ny) : (int)t;
+    ia[2] = DIM == 3 ? (int)(t / ny) : 0;
+  }
+  const int px = g.nn[0] + 4, py = g.nn[1] + 4;
+  const long long pn = pad_node(g, ia[0], ia[1], ia[2]);
+  const float2* xc = xp2 + pn * ND;
+  dfp acc[ND];
+#pragma unroll
+  for (int c = 0; c < ND; ++c) acc[c] = {0.0f, 0.0f};
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb) {
+    const int off = (nb % 3 - 1) + px * (((nb / 3) % 3 - 1) + (DIM == 3 ? py * (nb / 9 - 1) : 0));
+    const float2* xb = xc + off * ND;
+    const float2* sp = st2 + (long long)nb * SP * g.nnodes + node;
+    float2 vA = __ldcs(sp);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      dfacc(acc[c], vA, xb[c]);
+      dfacc(acc[c], __ldcs(sp + (1 + c) * g.nnodes), xb[DIM]);
+    }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) dfacc(acc[DIM], __ldcs(sp + (1 + DIM + c) * g.nnodes), xb[c]);
+    dfacc(acc[DIM], __ldcs(sp + (1 + 2 * DIM) * g.nnodes), xb[DIM]);
+  }
+  const unsigned char ma = mask[node];
+#pragma unroll
+  for (int c = 0; c < ND; ++c) {
+    float yh, yl;
+    if (c < DIM && ((ma >> c) & 1)) {
+      float2 xv = xc[c];
+      yh = xv.x; yl = xv.y;
+    } else {
+      yh = acc[c].hi + acc[c].lo;
+      yl = acc[c].lo - (yh - acc[c].hi);
+    }
+    float2 bv = b2[node * ND + c];
+    // (b - y) as a pair
+    float sh = bv.x - yh;
+    float bb = sh - bv.x;
+    float e = (bv.x - (sh - bb)) + (-yh - bb);
+    e += bv.y - yl;
+    float h = sh + e;
+    float l = e - (h - sh);
+    if (rpad2) rpad2[pn * ND + c] = make_float2(h, l);
+    if (r) r[node * ND + c] = (double)h + (double)l;
+  }
+}
+
+// pair stencil with the columns of constrained neighbours folded to zero
+// (all velocity components of a node are constrained together, so A and
+// T_c of such a neighbour never multiply a free unknown)
+template <int DIM>
+__global__ void fold_stencil_pairs_kernel(LevelGeom g, const double* __restrict__ st,
+                                          const unsigned char* __restrict__ mask, float2* __restrict__ st2) {
+  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nnodes * NB) return;
+  const long long node = t % g.nnodes;
+  const int nb = (int)(t / g.nnodes);
+  int ia[3];
+  {
+    const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+    const unsigned q = u / nx;
+    ia[0] = (int)(u - q * nx);
+    ia[1] = DIM == 3 ? (int)(q % ny) : (int)q;
+    ia[2] = DIM == 3 ? (int)(q / ny) : 0;
+  }
+  int ib0 = ia[0] + nb % 3 - 1, ib1 = ia[1] + (nb / 3) % 3 - 1, ib2 = DIM == 3 ? ia[2] + nb / 9 - 1 : 0;
+  bool inside = !(ib0 < 0 || ib0 > g.n[0] || ib1 < 0 || ib1 > g.n[1]) &&
+                !(DIM == 3 && (ib2 < 0 || ib2 > g.n[2]));
+  bool fixed = inside && (mask[ib0 + (long long)g.nn[0] * (ib1 + (long long)g.nn[1] * ib2)] & 1);
+  for (int e = 0; e < SP; ++e) {
+    const long long k = ((long long)nb * SP + e) * g.nnodes + node;
+    double v = inside ? st[k] : 0.0;
+    const bool velocity_column = (e == 0) || (e >= 1 + DIM && e < 1 + 2 * DIM);
+    if (fixed && velocity_column) v = 0.0;
+    float hi = (float)v;
+    st2[k] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
+template <int DIM>
+__global__ void split_x_padded_kernel(LevelGeom g, const double* __restrict__ x, float2* __restrict__ xp2) {
+  constexpr int ND = DIM + 1;
+  long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nnodes) return;
+  const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+  const unsigned q = u / nx;
+  const long long pn = pad_node(g, (int)(u - q * nx), DIM == 3 ? (int)(q % ny) : (int)q, DIM == 3 ? (int)(q / ny) : 0);
+#pragma unroll
+  for (int c = 0; c < ND; ++c) {
+    double v = x[node * ND + c];
+    float hi = (float)v;
+    xp2[pn * ND + c] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
+template <int DIM>
+__global__ void merge_x_padded_kernel(LevelGeom g, const float2* __restrict__ xp2, double* __restrict__ x) {
+  constexpr int ND = DIM + 1;
+  long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nnodes) return;
+  const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+  const unsigned q = u / nx;
+  const long long pn = pad_node(g, (int)(u - q * nx), DIM == 3 ? (int)(q % ny) : (int)q, DIM == 3 ? (int)(q / ny) : 0);
+#pragma unroll
+  for (int c = 0; c < ND; ++c) {
+    float2 v = xp2[pn * ND + c];
+    x[node * ND + c] = (double)v.x + (double)v.y;
+  }
+}
+
+__global__ void split_pairs_kernel(long long n, const double* __restrict__ in, float2* __restrict__ out) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    double v = in[t];
+    float hi = (float)v;
+    out[t] = make_float2(hi, (float)(v - (double)hi));
+  }
+}
+
+// ---------------------------------------------------------------------------
 // transfers: Q1 interpolation between nested uniform grids (fine n = 2 nc)
 __device__ __forceinline__ double pw(int d) { return d == 0 ? 1.0 : 0.5; }
 
@@ -425,6 +577,48 @@ cudaError_t launch_residual_f32(const LevelGeom& g, const double* st, const unsi
   unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
   if (g.dim == 2) residual_kernel<2, 2><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad);
   else residual_kernel<3, 2><<<blocks, 256, 0, s>>>(g, st, mask, x, b, nullptr, nullptr, rpad);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_pairs(long long n, const double* in, float2* out, cudaStream_t s) {
+  split_pairs_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, in, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_df2(const LevelGeom& g, const float2* st2, const unsigned char* mask,
+                                const float2* xp2, const float2* b2, float2* rpad2, double* r,
+                                cudaStream_t s) {
+  unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
+  if (g.dim == 2) residual_df2_kernel<2><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+  else residual_df2_kernel<3><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_stencil_pairs(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                      float2* st2, cudaStream_t s) {
+  long long n = g.nnodes * (g.dim == 3 ? 27 : 9);
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (g.dim == 2) fold_stencil_pairs_kernel<2><<<blocks, 256, 0, s>>>(g, st, mask, st2);
+  else fold_stencil_pairs_kernel<3><<<blocks, 256, 0, s>>>(g, st, mask, st2);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_x_padded(const LevelGeom& g, const double* x, float2* xp2, cudaStream_t s) {
+  unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
+  if (g.dim == 2) split_x_padded_kernel<2><<<blocks, 256, 0, s>>>(g, x, xp2);
+  else split_x_padded_kernel<3><<<blocks, 256, 0, s>>>(g, x, xp2);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_x_padded(const LevelGeom& g, const float2* xp2, double* x, cudaStream_t s) {
+  unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
+  if (g.dim == 2) merge_x_padded_kernel<2><<<blocks, 256, 0, s>>>(g, xp2, x);
+  else merge_x_padded_kernel<3><<<blocks, 256, 0, s>>>(g, xp2, x);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -443,6 +443,34 @@ __device__ __forceinline__ void finish_update(const LevelGeom& g, long long i, c
   x[i * ND + DIM] = x[i * ND + DIM] + omega * y[DIM];
 }
 
+// Restricted prolongation R~_i^T for the apply kernels: lane c < d+1
+// updates component c of node i from the warp-reduced y (all lanes hold the
+// sums); constrained velocity components take the residual (identity row).
+// x2, when given, receives the (hi, lo) float pair of the new value.
+template <int ND>
+__device__ __forceinline__ void owned_update(unsigned i, int lane, const unsigned char* mask, double rcv,
+                                             double yv, double omega, double* x, float2* x2) {
+  if (lane >= ND) return;
+  const int c = lane;
+  const size_t k = (size_t)i * ND + c;
+  const bool fixed = c < ND - 1 && ((mask[i] >> c) & 1);
+  const double nv = x[k] + (fixed ? rcv : omega * yv);
+  x[k] = nv;
+  if (x2) {
+    float hi = (float)nv;
+    x2[k] = make_float2(hi, (float)(nv - (double)hi));
+  }
+}
+
+template <int N, typename T>
+__device__ __forceinline__ T pick(const T* v, int c) {
+  T r = v[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k)
+    if (c == k) r = v[k];
+  return r;
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(256)
     apply_fp64_kernel(LevelGeom g, const double* __restrict__ coef, const unsigned char* __restrict__ mask,
@@ -477,11 +505,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int k = 0; k < ND; ++k)
     for (int o = 16; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
-  if (lane == 0) {
-    double rc[ND];
-    for (int c = 0; c < ND; ++c) rc[c] = rp[c];
-    finish_update<DIM>(g, i, ia, mask, rc, y, omega, x);
-  }
+  if (lane < ND) owned_update<ND>(i, lane, mask, rp[lane], pick<ND>(y, lane), omega, x, nullptr);
 }
 
 // float32 / bfloat16 rows with float32 residual and float32 accumulation
@@ -534,11 +558,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int k = 0; k < ND; ++k)
     for (int o = 16; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
-  if (lane == 0) {
-    double rc[ND], yd[ND];
-    for (int c = 0; c < ND; ++c) { rc[c] = (double)rp[c]; yd[c] = (double)y[c]; }
-    finish_update<DIM>(g, i, ia, mask, rc, yd, omega, x);
-  }
+  if (lane < ND) owned_update<ND>(i, lane, mask, (double)rp[lane], (double)pick<ND>(y, lane), omega, x, nullptr);
 }
 
 // Float-pair arithmetic (hi + lo of float32, about 48-bit significand) on the
@@ -563,6 +583,14 @@ __device__ __forceinline__ df df_add(df a, df b) {
   float h2 = hi + lo;
   return {h2, lo - (h2 - hi)};
 }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  float hi = p + e;
+  return {hi, e - (hi - p)};
+}
 // acc += c * r (c, r pairs); acc.lo collects every low-order term
 __device__ __forceinline__ void df_fma_acc(df& acc, float ch, float cl, float rh, float rl) {
   float p = ch * rh;
@@ -578,7 +606,8 @@ __device__ __forceinline__ void df_fma_acc(df& acc, float ch, float cl, float rh
 template <int DIM>
 __global__ void __launch_bounds__(256)
     apply_df_kernel(LevelGeom g, const float2* __restrict__ coef, const unsigned char* __restrict__ mask,
-                    const float2* __restrict__ rpad, double omega, double* __restrict__ x) {
+                    const float2* __restrict__ rpad, double omega, double* __restrict__ x,
+                    float2* __restrict__ xp2, float2 om2) {
   using P = PatchDims<DIM>;
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
   __shared__ int soff[NSLOT];
@@ -622,14 +651,22 @@ __global__ void __launch_bounds__(256)
       y[k] = df_add(y[k], other);
     }
   }
-  if (lane == 0) {
-    double rc[ND], yd[ND];
-    for (int c = 0; c < ND; ++c) {
-      float2 r2 = rp[c];
-      rc[c] = (double)r2.x + (double)r2.y;
-      yd[c] = (double)y[c].hi + (double)y[c].lo;
+  if (lane < ND) {
+    float2 r2 = rp[lane];
+    df yl = pick<ND>(y, lane);
+    if (xp2) {
+      // pair copy of x (padded like the residual), updated on the float32
+      // pipes: x + omega y, or x + r on a constrained component
+      const size_t k = (size_t)pbase * ND + lane;
+      const float2 xv = xp2[k];
+      const bool fixed = lane < DIM && ((mask[i] >> lane) & 1);
+      const df add = fixed ? df{r2.x, r2.y} : df_mul({om2.x, om2.y}, yl);
+      const df nv = df_add({xv.x, xv.y}, add);
+      xp2[k] = make_float2(nv.hi, nv.lo);
+    } else {
+      owned_update<ND>(i, lane, mask, (double)r2.x + (double)r2.y, (double)yl.hi + (double)yl.lo, omega, x,
+                       nullptr);
     }
-    finish_update<DIM>(g, i, ia, mask, rc, yd, omega, x);
   }
 }
 
@@ -825,9 +862,21 @@ cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coe
     if (g.dim == 2) apply_lowp_kernel<2, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x);
     else apply_lowp_kernel<3, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x);
   } else {
-    if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x);
-    else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x);
+    const float2 om2 = make_float2((float)omega, (float)(omega - (double)(float)omega));
+    if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x, nullptr, om2);
+    else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x, nullptr, om2);
   }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_patch_apply_df2(const LevelGeom& g, const void* coef, const unsigned char* mask,
+                                   const float* rpad2, double omega, float2* xp2, cudaStream_t s) {
+  long long threads = g.nnodes * 32;
+  unsigned blocks = (unsigned)((threads + 255) / 256);
+  const float2 om2 = make_float2((float)omega, (float)(omega - (double)(float)omega));
+  if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad2, omega, nullptr, xp2, om2);
+  else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad2, omega, nullptr, xp2, om2);
   note_launches(1);
   return cudaGetLastError();
 }
