@@ -223,6 +223,7 @@ def run_ours(args, rank, world, local_rank):
         step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
         total_ms = ev[0].elapsed_time(ev[-1])
         n_apply, ms_apply, bytes_apply = s.profile_read(0)
+        n_fine, ms_fine, bytes_fine = s.profile_read(4)
         n_res, ms_res, _ = s.profile_read(1)
         n_vc, ms_vc, _ = s.profile_read(2)
         s.profile(False)
@@ -261,7 +262,7 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return 0
     hbm, peak_kind = peaks()
-    achieved = (bytes_apply * n_apply) / (ms_apply * 1e-3) / 1e9 if ms_apply > 0 else 0.0
+    achieved = bytes_fine / (ms_fine / max(n_fine, 1) * 1e-3) / 1e9 if ms_fine > 0 else 0.0
     traffic = load_traffic(args.prec)
     step_sorted = sorted(step_ms)
     p50 = statistics.median(step_sorted)
@@ -287,7 +288,9 @@ def run_ours(args, rank, world, local_rank):
                    "variants": variants},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": "patch apply (cache_inverse), bytes-weighted over all smoothed levels",
+                     "kernel": "patch apply (cache_inverse) on the finest level",
+                     "launches": n_fine, "avg_launch_ms": ms_fine / max(n_fine, 1),
+                     "algorithmic_bytes_per_launch": bytes_fine,
                      "peak_source": peak_kind},
         "e2e": {"value": all_e2e / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8,
                 "d2h_bytes_per_step": n * 8},
@@ -385,14 +388,16 @@ def policy_sweeps(prob, stream, args):
 
 
 def load_traffic(prec):
-    """dram bytes per launch of the fine-level patch apply from the committed
-    ncu summary, if one exists for this precision."""
-    path = os.path.join(ROOT, "profiles", f"traffic_patch_apply_{prec}.json")
+    """DRAM bytes per finest-level launch of the patch apply, from the
+    committed ncu summary of this precision (a line 'traffic_bytes_64: N')."""
+    path = os.path.join(ROOT, "profiles", f"patch_apply_{prec}_porous48.md")
     try:
-        with open(path) as f:
-            return json.load(f).get("dram_bytes_per_launch")
+        for line in open(path):
+            if line.strip().startswith("traffic_bytes_64:"):
+                return float(line.split(":", 1)[1].strip().split()[0])
     except Exception:
-        return None
+        pass
+    return None
 
 
 def main():

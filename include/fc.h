@@ -203,7 +203,8 @@ size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o);
 
 /* Per-kernel device time of the patch apply, the residual and the whole
  * sweep, collected with CUDA events on the handle's stream while enabled.
- * kind: 0 patch apply, 1 residual (smoother), 2 V-cycle, 3 patch-cache build.
+ * kind: 0 patch apply (all levels), 1 residual (smoother), 2 V-cycle,
+ * 3 patch-cache build, 4 patch apply on the finest level only.
  * Reading synchronises and resets the counters of that kind. */
 fc_status fc_profile_enable(fc_handle h, int on);
 fc_status fc_profile_read(fc_handle h, int kind, long long* launches, double* total_ms,

@@ -80,7 +80,7 @@ struct ProfScope {
   double bytes;
   cudaEvent_t a = nullptr;
   ProfScope(fc_handle hh, int k, double b) : h(hh), kind(k), bytes(b) {
-    if (h->prof.on) {
+    if (h->prof.on && k >= 0) {
       a = prof_event(h);
       cudaEventRecord(a, h->stream);
     }
@@ -227,6 +227,7 @@ fc_status smooth_level_pairs(fc_handle h, int li, double* x, const double* b, in
       CK(launch_residual_df2(L.g, L.st2, L.mask, L.xp2, L.bp2, (float2*)L.rpad32, nullptr, h->stream));
     }
     ProfScope ps(h, 0, level_apply_bytes(h, li));
+    ProfScope pf(h, li == h->nlev - 1 ? 4 : -1, level_apply_bytes(h, li));
     CK(launch_patch_apply_df2(L.g, L.coef, L.mask, L.rpad32, h->opt.omega, L.xp2, h->stream));
   }
   CK(launch_merge_x_padded(L.g, L.xp2, x, h->stream));
@@ -241,6 +242,7 @@ fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nswe
     if (st != FC_OK) return st;
     if (h->opt.cache == FC_CACHE_INVERSE) {
       ProfScope ps(h, 0, level_apply_bytes(h, li));
+      ProfScope pf(h, li == h->nlev - 1 ? 4 : -1, level_apply_bytes(h, li));
       CK(launch_patch_apply(L.g, h->opt.prec, L.coef, L.mask, L.rpad, L.rpad32, h->opt.omega, x, h->stream));
     } else if (h->opt.cache == FC_CACHE_MATRIX) {
       ProfScope ps(h, 0, (double)L.fac_bytes);
