@@ -14,7 +14,10 @@ using namespace fc;
 
 namespace fc {
 static std::atomic<long long> g_launches{0};
-void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+static thread_local bool g_capturing = false;
+void note_launches(int n) {
+  if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
 }  // namespace fc
 
 namespace {
@@ -80,7 +83,7 @@ struct ProfScope {
   double bytes;
   cudaEvent_t a = nullptr;
   ProfScope(fc_handle hh, int k, double b) : h(hh), kind(k), bytes(b) {
-    if (h->prof.on && k >= 0) {
+    if (h->prof.on && k >= 0 && !h->capturing) {
       a = prof_event(h);
       cudaEventRecord(a, h->stream);
     }
@@ -256,6 +259,56 @@ fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nswe
   return FC_OK;
 }
 
+fc_status vcycle_level(fc_handle h, int li, double* x, const double* b);
+
+// Restriction of the finest residual buffer and the whole coarser V-cycle,
+// all on buffers fixed per handle: captured once into a CUDA graph (one
+// launch per V-cycle instead of one per kernel), replayed afterwards.
+fc_status coarse_part(fc_handle h) {
+  const int li = h->nlev - 1;
+  Level& L = h->lev[li];
+  Level& C = h->lev[li - 1];
+  if (!h->coarse_graph) {
+    cudaGraph_t graph = nullptr;
+    h->capturing = true;
+    fc::g_capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    fc_status st = FC_OK;
+    if (e == cudaSuccess) {
+      if (launch_restrict(L.g, C.g, C.mask, L.r, C.b, h->stream) != cudaSuccess ||
+          cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.ndof, h->stream) != cudaSuccess)
+        st = FC_ERR_CUDA;
+      if (st == FC_OK) st = vcycle_level(h, li - 1, C.x, C.b);
+      e = cudaStreamEndCapture(h->stream, &graph);
+    }
+    h->capturing = false;
+    fc::g_capturing = false;
+    if (e != cudaSuccess || st != FC_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return e != cudaSuccess ? cuda_fail(h, e, "V-cycle graph capture") : st;
+    }
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+    int kernels = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) kernels++;
+    }
+    e = cudaGraphInstantiate(&h->coarse_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->coarse_graph = nullptr;
+      return cuda_fail(h, e, "V-cycle graph instantiate");
+    }
+    h->coarse_graph_kernels = kernels;
+  }
+  CK(cudaGraphLaunch(h->coarse_graph, h->stream));
+  note_launches(h->coarse_graph_kernels);
+  return FC_OK;
+}
+
 fc_status vcycle_level(fc_handle h, int li, double* x, const double* b) {
   Level& L = h->lev[li];
   if (li == 0) {
@@ -280,9 +333,15 @@ fc_status vcycle_level(fc_handle h, int li, double* x, const double* b) {
     if (st != FC_OK) return st;
     CK(launch_residual(L.g, L.st, L.mask, x, b, L.r, nullptr, h->stream));
   }
-  CK(launch_restrict(L.g, C.g, C.mask, L.r, C.b, h->stream));
-  CK(cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.ndof, h->stream));
-  st = vcycle_level(h, li - 1, C.x, C.b);
+  if (li == h->nlev - 1 && h->stream != nullptr && h->stream != cudaStreamLegacy &&
+      h->stream != cudaStreamPerThread) {
+    // (the legacy default stream cannot be captured; it runs the launches directly)
+    st = coarse_part(h);
+  } else {
+    CK(launch_restrict(L.g, C.g, C.mask, L.r, C.b, h->stream));
+    CK(cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.ndof, h->stream));
+    st = vcycle_level(h, li - 1, C.x, C.b);
+  }
   if (st != FC_OK) return st;
   CK(launch_prolong_add(L.g, C.g, L.mask, C.x, x, h->stream));
   if (pair_path(h)) return smooth_level_pairs(h, li, x, b, h->opt.nu_post, true);
@@ -534,7 +593,7 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     CK(dalloc(h, &h->V, (size_t)n * (m + 1), 2));
     CK(dalloc(h, &h->Z, (size_t)n * m, 2));
     CK(dalloc(h, &h->w, (size_t)n, 2));
-    CK(dalloc(h, &h->red, 1024, 2));
+    CK(dalloc(h, &h->red, 2048, 2));
     CK(dalloc(h, &h->small, (size_t)small_len(m), 2));
     CK(dalloc(h, &h->bh, (size_t)n, 2));
     CK(dalloc(h, &h->xh, (size_t)n, 2));
@@ -653,18 +712,21 @@ fc_status fc_solve(fc_handle h, const double* b, double* x, double rtol, int max
       }
       its++;
       CK(launch_residual(F.g, F.st, F.mask, Zj, nullptr, h->w, nullptr, s));
-      for (int i = 0; i <= j; ++i) {
-        double* hij = H + (long long)i * m + j;
-        CK(launch_dot(n, h->w, h->V + (long long)i * n, h->red, hij, s));
-        CK(launch_mgs_step(n, h->w, h->V + (long long)i * n, hij, s));
+      // modified Gram-Schmidt, one fused kernel per step: step i finishes
+      // h_{i-1,j} from the block partials, subtracts it and starts the dot
+      // with v_i; the last two steps give the norm and v_{j+1}
+      double* pa = h->red;
+      double* pb = h->red + 1024;
+      CK(launch_mgs_fused(n, h->w, nullptr, nullptr, nullptr, h->V, pa, 0, nullptr, nullptr, s));
+      for (int i = 1; i <= j + 1; ++i) {
+        const double* vnext = i <= j ? h->V + (long long)i * n : nullptr;
+        CK(launch_mgs_fused(n, h->w, h->V + (long long)(i - 1) * n, pa, H + (long long)(i - 1) * m + j, vnext,
+                            pb, 0, nullptr, nullptr, s));
+        std::swap(pa, pb);
       }
       double* hn = H + (long long)(j + 1) * m + j;
-      CK(launch_dot(n, h->w, h->w, h->red, hn, s));
-      sqrt_kernel<<<1, 1, 0, s>>>(hn);
-      CK(cudaGetLastError());
-      note_launches(1);
-      CK(cudaMemcpyAsync(sc + 2, hn, sizeof(double), cudaMemcpyDeviceToDevice, s));
-      CK(launch_scale_copy(n, hn, 0, 1, h->w, h->V + (long long)(j + 1) * n, s));
+      CK(launch_mgs_fused(n, h->w, nullptr, pa, hn, nullptr, nullptr, 1, h->V + (long long)(j + 1) * n, sc + 2,
+                          s));
       CK(launch_givens(H, m, j, bn, s));
       CK(cudaMemcpyAsync(h->host_small, sc, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
@@ -787,6 +849,7 @@ fc_status fc_destroy(fc_handle h) {
     cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); cudaFree(L.rpad); cudaFree(L.rpad32);
     cudaFree(L.st2); cudaFree(L.xp2); cudaFree(L.bp2);
   }
+  if (h->coarse_graph) cudaGraphExecDestroy(h->coarse_graph);
   cudaFree(h->d_shapes); cudaFree(h->d_err); cudaFree(h->coarse_inv);
   cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->red); cudaFree(h->small);
   cudaFree(h->bh); cudaFree(h->xh);

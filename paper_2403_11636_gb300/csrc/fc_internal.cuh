@@ -125,6 +125,11 @@ struct fc_handle_s {
   double* xh = nullptr;
   int restart = 30;
   size_t bytes[8] = {0};
+  // coarse part of the V-cycle (restriction from the finest level's residual
+  // buffer down to the coarse solve) captured once as a CUDA graph
+  cudaGraphExec_t coarse_graph = nullptr;
+  int coarse_graph_kernels = 0;
+  bool capturing = false;
   fc::Profile prof;
   std::string err;
 };
@@ -197,6 +202,10 @@ cudaError_t launch_scale_copy(long long n, const double* s, int sidx, int invert
                               double* y, cudaStream_t st);
 cudaError_t launch_mgs_step(long long n, double* w, const double* vi, const double* hij,
                             cudaStream_t s);
+// one fused MGS step (see fc_mg.cu); partial arrays hold 1024 block sums
+cudaError_t launch_mgs_fused(long long n, double* w, const double* v_prev, const double* part_in,
+                             double* h_out, const double* v_next, double* part_out, int finish,
+                             double* v_out, double* hn_copy, cudaStream_t s);
 cudaError_t launch_givens(double* small, int m, int j, double bnorm, cudaStream_t s);
 cudaError_t launch_update_x(long long n, int k, int m, const double* small, const double* Z,
                             double* x, cudaStream_t s);
