@@ -195,7 +195,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
-        s = fc.Solver(prob, cache=args.cache, prec=args.prec, stream=stream)
+        s = fc.Solver(prob, cache=args.cache, prec=args.prec, stream=stream, dedup=args.dedup)
         torch.cuda.synchronize()
         setup_ms = 1e3 * (time.perf_counter() - t0)
         b = s.rhs()
@@ -276,7 +276,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": "porous3d 64^3 background grid, 40 non-overlapping seeded spheres "
                                "r~U[0.04,0.12], alpha 1e-8, octree depth 3, 5 levels, V(2,2), "
                                "FGMRES(30) rtol 1e-8, Q1-Q1 (1,098,500 DoFs)",
-                   "cache": args.cache, "patch_rows": args.prec,
+                   "cache": args.cache, "patch_rows": args.prec, "shared_class_blocks": bool(args.dedup),
                    "l2": "inputs larger than L2 (cached rows 3.5 GB per sweep)",
                    "iterations": its_list[0], "relres": max(rr_list), "setup_ms": setup_ms,
                    "solves_per_s": world * args.steps / (total_ms * 1e-3),
@@ -320,7 +320,7 @@ def run_sweeps(args):
     prob = inputs.porous_3d(0, n=args.n, nlevels=nlev)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        s = fc.Solver(prob, cache=args.cache, prec=args.prec, stream=stream)
+        s = fc.Solver(prob, cache=args.cache, prec=args.prec, stream=stream, dedup=args.dedup)
         x = torch.as_tensor(inputs.random_vector(prob, 3)).cuda()
         b = torch.as_tensor(inputs.random_vector(prob, 4)).cuda()
         s.smooth_(x, b, nsweeps=args.warmup)
@@ -336,7 +336,7 @@ def run_sweeps(args):
         ms = e0.elapsed_time(e1) / max(args.steps, 1)
     upd = free_dofs(prob, prob.nlevels)
     emit({"mode": "sweep", "workload": f"porous3d {args.n}^3 finest-level sweeps", "cache": args.cache,
-          "prec": args.prec, "sweep_ms": ms, "updates_per_s": upd / (ms * 1e-3),
+          "prec": args.prec, "dedup": args.dedup, "cache_bytes": s.info()["bytes"][1], "sweep_ms": ms, "updates_per_s": upd / (ms * 1e-3),
           "apply_ms": ma / max(na, 1), "apply_bytes": ba, "residual_ms": mr / max(nr, 1),
           "apply_gbs": ba / (ma / max(na, 1) * 1e-3) / 1e9 if ma > 0 else None})
     s.close()
@@ -349,15 +349,16 @@ def policy_sweeps(prob, stream, args):
     import torch
     from paper_2403_11636_gb300 import fc, inputs
     res = {}
-    combos = [("inverse", "fp64"), ("inverse", "df64"), ("inverse", "fp32"), ("inverse", "bf16"),
-              ("matrix", "fp64"), ("none", "fp64")]
+    combos = [("inverse", "fp64", 1), ("inverse", "df64", 1), ("inverse", "fp32", 1), ("inverse", "bf16", 1),
+              ("inverse", "df64", 0), ("inverse", "fp64", 0), ("matrix", "fp64", 1), ("matrix", "fp64", 0),
+              ("none", "fp64", 1)]
     x0 = torch.as_tensor(inputs.random_vector(prob, 3)).cuda()
     bb = torch.as_tensor(inputs.random_vector(prob, 4)).cuda()
     upd = free_dofs(prob, prob.nlevels)
-    for cache, prec in combos:
+    for cache, prec, dd in combos:
         try:
             t0 = time.perf_counter()
-            s = fc.Solver(prob, cache=cache, prec=prec, stream=stream)
+            s = fc.Solver(prob, cache=cache, prec=prec, stream=stream, dedup=dd)
             torch.cuda.synchronize()
             setup = time.perf_counter() - t0
             x = x0.clone()
@@ -374,7 +375,7 @@ def policy_sweeps(prob, stream, args):
             na, ma, ba = s.profile_read(0)
             s.profile(False)
             info = s.info()
-            res[f"{cache}/{prec}"] = {"sweep_ms": ms, "updates_per_s": upd / (ms * 1e-3),
+            res[f"{cache}/{prec}/{'shared' if dd else 'per-patch'}"] = {"sweep_ms": ms, "updates_per_s": upd / (ms * 1e-3),
                                       "apply_ms": ma / max(na, 1),
                                       "apply_gbs": (ba / (ma / max(na, 1) * 1e-3) / 1e9) if ma > 0 and ba > 0 else None,
                                       "setup_ms": setup * 1e3,
@@ -382,7 +383,7 @@ def policy_sweeps(prob, stream, args):
             s.close()
             del s
         except Exception as e:  # a policy that does not fit reports why
-            res[f"{cache}/{prec}"] = {"error": str(e)[:200]}
+            res[f"{cache}/{prec}/{'shared' if dd else 'per-patch'}"] = {"error": str(e)[:200]}
         torch.cuda.synchronize()
     return res
 
@@ -409,6 +410,7 @@ def main():
     ap.add_argument("--cache", default="inverse", choices=["inverse", "matrix", "none"])
     ap.add_argument("--prec", default="df64", choices=["fp64", "df64", "fp32", "bf16"])
     ap.add_argument("--policies", type=int, default=1)
+    ap.add_argument("--dedup", type=int, default=1, help="share the blocks of bit-identical patches")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--mode", default="solve", choices=["solve", "sweep"])

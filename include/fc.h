@@ -99,11 +99,14 @@ typedef struct {
   int force_kind;      /* 0: constant force[]; 1: (f0 sin(pi x), f1 cos(pi y));
                           2: (f0 sin(pi y)[sin(pi z)], 0, 0); 3: (-f0 pi/2 sin(pi x/2), 0, 0) */
   double force[3];
+  int dedup;           /* 1: patches with bit-identical blocks L_i (uncut, one alpha, away
+                          from constraints) share one stored row/factor block; 0: one block
+                          per patch (the paper's layout).  Same results either way. */
 } fc_options;
 
 /* Fill defaults: eta 1e-3, beta 100, omega 0.8, V(2,2), depth 4 (2D) / 3 (3D)
  * is left to the caller (quad_depth = 4), cache_inverse, FP64, restart 30,
- * channel preset, ubar 0.3, constant zero force. */
+ * channel preset, ubar 0.3, constant zero force, dedup 1. */
 fc_status fc_options_default(fc_options* o);
 
 /* Build the hierarchy of `depth` levels (paper Sec. 3, Algorithm 1 on a

@@ -102,10 +102,13 @@ struct ProfScope {
 namespace {
 
 __global__ void count_active_kernel(LevelGeom g, const unsigned char* __restrict__ mask,
-                                    unsigned long long* __restrict__ out) {
-  // number of active (in-grid, unconstrained) patch DoFs summed over patches
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.nnodes) return;
+                                    unsigned long long* __restrict__ out, const int* __restrict__ list,
+                                    long long nlist) {
+  // number of active (in-grid, unconstrained) patch DoFs summed over the
+  // patches of `list` (all patches when list is null)
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (list ? nlist : g.nnodes)) return;
+  long long i = list ? list[t] : t;
   int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
                g.dim == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
   unsigned long long cnt = 0;
@@ -129,8 +132,6 @@ __global__ void count_active_kernel(LevelGeom g, const unsigned char* __restrict
       }
   atomicAdd(out, cnt);
 }
-
-__global__ void sqrt_kernel(double* p) { p[0] = sqrt(p[0]); }
 
 }  // namespace
 
@@ -196,7 +197,7 @@ double level_apply_bytes(fc_handle h, int li) {
   const Level& L = h->lev[li];
   double cb = (double)coef_elem_bytes(h->opt.prec);
   double rb = (h->opt.prec == FC_PREC_FP32 || h->opt.prec == FC_PREC_BF16) ? 4.0 : 8.0;
-  double act = (double)L.active_slots;
+  double act = (double)L.active_work;  // rows streamed: stored blocks, each once
   return act * L.g.nd * cb + (double)L.g.nnodes * L.g.nd * (rb + 16.0);
 }
 
@@ -231,7 +232,7 @@ fc_status smooth_level_pairs(fc_handle h, int li, double* x, const double* b, in
     }
     ProfScope ps(h, 0, level_apply_bytes(h, li));
     ProfScope pf(h, li == h->nlev - 1 ? 4 : -1, level_apply_bytes(h, li));
-    CK(launch_patch_apply_df2(L.g, L.coef, L.mask, L.rpad32, h->opt.omega, L.xp2, h->stream));
+    CK(launch_patch_apply_df2(L.g, L.coef, L.mask, L.rpad32, h->opt.omega, L.xp2, L.prow, h->stream));
   }
   CK(launch_merge_x_padded(L.g, L.xp2, x, h->stream));
   return FC_OK;
@@ -246,14 +247,15 @@ fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nswe
     if (h->opt.cache == FC_CACHE_INVERSE) {
       ProfScope ps(h, 0, level_apply_bytes(h, li));
       ProfScope pf(h, li == h->nlev - 1 ? 4 : -1, level_apply_bytes(h, li));
-      CK(launch_patch_apply(L.g, h->opt.prec, L.coef, L.mask, L.rpad, L.rpad32, h->opt.omega, x, h->stream));
+      CK(launch_patch_apply(L.g, h->opt.prec, L.coef, L.mask, L.rpad, L.rpad32, h->opt.omega, x, L.prow,
+                            h->stream));
     } else if (h->opt.cache == FC_CACHE_MATRIX) {
       ProfScope ps(h, 0, (double)L.fac_bytes);
-      CK(launch_factor_apply(L.g, L.fac, L.fpiv, L.mask, L.rpad, h->opt.omega, x, h->stream));
+      CK(launch_factor_apply(L.g, L.fac, L.fpiv, L.mask, L.rpad, h->opt.omega, x, L.prow, h->stream));
     } else {
       ProfScope ps(h, 0, 0.0);
       CK(launch_patch_build(L.g, L.st, L.mask, 2, h->opt.omega, nullptr, nullptr, nullptr, L.rpad, x,
-                            h->d_err, h->stream));
+                            h->d_err, nullptr, 0, h->stream));
     }
   }
   return FC_OK;
@@ -380,6 +382,7 @@ fc_status fc_options_default(fc_options* o) {
   o->bc_preset = 0;
   o->ubar = 0.3;
   o->force_kind = 0;
+  o->dedup = 1;
   return FC_OK;
 }
 
@@ -433,7 +436,7 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   if (!(alpha > 0.0) || !(o->eta > 0.0) || !(o->omega > 0.0) || o->nu_pre < 0 || o->nu_post < 0 ||
       o->quad_depth < 0 || o->quad_depth > 6 || o->fgmres_restart < 1 || o->fgmres_restart > 256 ||
       o->bc_preset < 0 || o->bc_preset > 2 || o->force_kind < 0 || o->force_kind > 3 ||
-      !(o->nitsche_beta >= 0.0))
+      !(o->nitsche_beta >= 0.0) || o->dedup < 0 || o->dedup > 1)
     return fail(h, FC_ERR_INVALID, "invalid options");
   if (o->cache < FC_CACHE_INVERSE || o->cache > FC_CACHE_NONE || o->prec < FC_PREC_FP64 || o->prec > FC_PREC_DF64)
     return fail(h, FC_ERR_INVALID, "invalid cache policy or precision");
@@ -482,7 +485,32 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     CK(dalloc(h, &eF, (size_t)G.ncell * dim * nl, -1));
     size_t tmp_bytes = (size_t)G.ncell * (nl * nl * (1 + dim) + dim * nl) * 8;
     h->bytes[4] = std::max(h->bytes[4], tmp_bytes);
-    CK(launch_cell_elements(G, eA, eB, eF, nullptr, h->d_err, h->stream));
+    // reference element matrices of an uncut cell of this level (alpha = 1,
+    // same rule), then all cells; plain cells take alpha * reference
+    double *rA = nullptr, *rB = nullptr, *rF = nullptr;
+    unsigned char* cclass = nullptr;
+    CK(dalloc(h, &rA, (size_t)nl * nl, -1));
+    CK(dalloc(h, &rB, (size_t)dim * nl * nl, -1));
+    CK(dalloc(h, &rF, (size_t)dim * nl, -1));
+    CK(dalloc(h, &cclass, (size_t)G.ncell, -1));
+    {
+      LevelGeom R = G;
+      R.ncell = 1;
+      R.nnodes = 1;
+      for (int k = 0; k < dim; ++k) {
+        R.n[k] = 1;
+        R.nn[k] = 2;
+        R.lo[k] = 0.0;
+        R.hi[k] = G.h[k];
+        R.nnodes *= 2;
+      }
+      R.ndof = R.nnodes * nd;
+      R.nshape = 0;
+      R.force_kind = 0;
+      R.force[0] = R.force[1] = R.force[2] = 0.0;
+      CK(launch_cell_elements(R, rA, rB, rF, nullptr, h->d_err, nullptr, nullptr, nullptr, h->stream));
+    }
+    CK(launch_cell_elements(G, eA, eB, eF, nullptr, h->d_err, rA, rB, cclass, h->stream));
     CK(dalloc(h, &L.st, (size_t)G.nnodes * nb * spn(dim), 0));
     CK(dalloc(h, &L.mask, (size_t)G.nnodes, 0));
     CK(dalloc(h, &L.wfix, (size_t)G.ndof, 0));
@@ -512,30 +540,62 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
       // V-cycle buffer on the finest level
       CK(launch_rhs(G, eF, L.st, L.mask, L.wfix, L.b, h->stream));
     }
+    // ---- patch classes and the work list (patches factored and stored)
+    int* work = nullptr;
+    int* dnw = nullptr;
+    if (li > 0 && o->cache != FC_CACHE_NONE) {
+      unsigned char* nclass = nullptr;
+      int* pclass = nullptr;
+      int* rep = nullptr;
+      const long long nbk = (G.nnodes + 1023) / 1024;
+      CK(dalloc(h, &nclass, (size_t)G.nnodes, -1));
+      CK(dalloc(h, &pclass, (size_t)G.nnodes, -1));
+      CK(dalloc(h, &rep, 4, -1));
+      CK(dalloc(h, &work, (size_t)(G.nnodes + nbk), -1));
+      CK(dalloc(h, &dnw, 1, -1));
+      CK(dalloc(h, &L.prow, (size_t)G.nnodes, 1));
+      CK(launch_patch_classes(G, cclass, L.mask, nclass, pclass, rep, work, dnw, L.prow, o->dedup,
+                              h->stream));
+      CK(cudaMemcpyAsync(&L.nwork, dnw, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      cudaFree(nclass);
+      cudaFree(pclass);
+      cudaFree(rep);
+    }
     CK(cudaStreamSynchronize(h->stream));
     cudaFree(eA);
     cudaFree(eB);
     cudaFree(eF);
+    cudaFree(rA);
+    cudaFree(rB);
+    cudaFree(rF);
+    cudaFree(cclass);
     fc_status st = check_err(h);
     if (st != FC_OK) return st;
     // ---- patch cache (every level above the coarsest)
     if (li > 0) {
-      CK(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), h->stream));
-      count_active_kernel<<<(unsigned)((G.nnodes + 255) / 256), 256, 0, h->stream>>>(G, L.mask, d_count);
-      CK(cudaGetLastError());
-      note_launches(1);
-      unsigned long long cnt = 0;
-      CK(cudaMemcpyAsync(&cnt, d_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaStreamSynchronize(h->stream));
-      L.active_slots = cnt;
+      for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1 && !work) break;
+        CK(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), h->stream));
+        const long long cnt_n = pass == 0 ? G.nnodes : L.nwork;
+        count_active_kernel<<<(unsigned)((cnt_n + 255) / 256), 256, 0, h->stream>>>(
+            G, L.mask, d_count, pass == 0 ? nullptr : work, cnt_n);
+        CK(cudaGetLastError());
+        note_launches(1);
+        unsigned long long cnt = 0;
+        CK(cudaMemcpyAsync(&cnt, d_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (pass == 0) L.active_slots = cnt;
+        else L.active_work = cnt;
+      }
       if (o->cache == FC_CACHE_INVERSE) {
-        size_t n = (size_t)G.nnodes * nslot(dim) * nd;
+        size_t n = (size_t)L.nwork * nslot(dim) * nd;
         double* c64 = nullptr;
         CK(dalloc(h, &c64, n, o->prec == FC_PREC_FP64 ? 1 : -1));
         {
           ProfScope ps(h, 3, 0.0);
           CK(launch_patch_build(G, L.st, L.mask, 0, o->omega, c64, nullptr, nullptr, nullptr, nullptr,
-                                h->d_err, h->stream));
+                                h->d_err, work, L.nwork, h->stream));
         }
         if (o->prec == FC_PREC_FP64) {
           L.coef = c64;
@@ -545,21 +605,23 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
           void* cv = nullptr;
           CK(cudaMalloc(&cv, n * eb));
           h->bytes[1] += n * eb;
-          CK(launch_convert_rows(G, o->prec, c64, cv, h->stream));
+          CK(launch_convert_rows(G, o->prec, c64, cv, L.nwork, h->stream));
           CK(cudaStreamSynchronize(h->stream));
           cudaFree(c64);
           L.coef = cv;
           L.coef_bytes = n * eb;
         }
       } else if (o->cache == FC_CACHE_MATRIX) {
-        CK(dalloc(h, &L.fac, (size_t)G.nnodes * factor_doubles(dim), 1));
-        CK(dalloc(h, &L.fpiv, (size_t)G.nnodes * factor_ints(dim), 1));
-        L.fac_bytes = (size_t)G.nnodes * (factor_doubles(dim) * 8 + factor_ints(dim) * 4);
+        CK(dalloc(h, &L.fac, (size_t)L.nwork * factor_doubles(dim), 1));
+        CK(dalloc(h, &L.fpiv, (size_t)L.nwork * factor_ints(dim), 1));
+        L.fac_bytes = (size_t)L.nwork * (factor_doubles(dim) * 8 + factor_ints(dim) * 4);
         ProfScope ps(h, 3, 0.0);
         CK(launch_patch_build(G, L.st, L.mask, 1, o->omega, nullptr, L.fac, L.fpiv, nullptr, nullptr,
-                              h->d_err, h->stream));
+                              h->d_err, work, L.nwork, h->stream));
       }
       CK(cudaStreamSynchronize(h->stream));
+      cudaFree(work);
+      cudaFree(dnw);
       st = check_err(h);
       if (st != FC_OK) return st;
     }
@@ -777,7 +839,13 @@ fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_hos
   const size_t cnt = (size_t)ns * nd;
   const size_t eb = coef_elem_bytes(h->opt.prec);
   std::vector<unsigned char> raw(cnt * eb);
-  CK(cudaMemcpyAsync(raw.data(), (const char*)L.coef + (size_t)node * cnt * eb, cnt * eb,
+  int pr = (int)node;
+  if (L.prow) {
+    CK(cudaMemcpyAsync(&pr, L.prow + node, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  const size_t blk = pr < 0 ? (size_t)(-(long long)pr - 1) : (size_t)pr;
+  CK(cudaMemcpyAsync(raw.data(), (const char*)L.coef + blk * cnt * eb, cnt * eb,
                      cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   for (int j = 0; j < ns; ++j)
@@ -847,7 +915,7 @@ fc_status fc_destroy(fc_handle h) {
     Level& L = h->lev[l];
     cudaFree(L.st); cudaFree(L.mask); cudaFree(L.wfix); cudaFree(L.coef); cudaFree(L.fac); cudaFree(L.fpiv);
     cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); cudaFree(L.rpad); cudaFree(L.rpad32);
-    cudaFree(L.st2); cudaFree(L.xp2); cudaFree(L.bp2);
+    cudaFree(L.st2); cudaFree(L.xp2); cudaFree(L.bp2); cudaFree(L.prow);
   }
   if (h->coarse_graph) cudaGraphExecDestroy(h->coarse_graph);
   cudaFree(h->d_shapes); cudaFree(h->d_err); cudaFree(h->coarse_inv);

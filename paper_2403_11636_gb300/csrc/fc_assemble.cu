@@ -190,3 +190,156 @@ cudaError_t launch_rhs(const LevelGeom& g, const double* eF, const double* st,
 }
 
 }  // namespace fc
+
+// ---------------------------------------------------------------------------
+// Patch classes.  A node whose 2^d cells all exist and are plain with one
+// alpha (cell class 1 fluid, 2 fictitious) has a stencil bit-identical to
+// every other such node of the same class.  A patch whose 5^d nodes are all
+// in the grid, unconstrained and of one node class therefore has a
+// bit-identical block L_i: its rows of L_i^{-1} (or its factors) are those
+// of the class representative (the lowest patch index of the class).  The
+// work list holds the patches that are factored and stored -- every patch
+// of class 0 and one representative per class -- in increasing patch order.
+// prow[i] = stored block of patch i, encoded as -(block + 1) for blocks
+// shared by a class (read through the cache) and block for unique patches.
+namespace fc {
+namespace {
+
+template <int DIM>
+__global__ void node_class_kernel(LevelGeom g, const unsigned char* __restrict__ cclass,
+                                  unsigned char* __restrict__ nclass) {
+  long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nnodes) return;
+  const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+  const unsigned q = u / nx;
+  int ia[3] = {(int)(u - q * nx), DIM == 3 ? (int)(q % ny) : (int)q, DIM == 3 ? (int)(q / ny) : 0};
+  int cls = -1;
+  for (int cc = 0; cc < (1 << DIM); ++cc) {
+    int ic[3] = {0, 0, 0};
+    bool in = true;
+    for (int k = 0; k < DIM; ++k) {
+      ic[k] = ia[k] - 1 + ((cc >> k) & 1);
+      if (ic[k] < 0 || ic[k] >= g.n[k]) in = false;
+    }
+    if (!in) { cls = 0; break; }
+    int c = cclass[ic[0] + (long long)g.n[0] * (ic[1] + (long long)g.n[1] * ic[2])];
+    if (cls < 0) cls = c;
+    else if (c != cls) { cls = 0; break; }
+  }
+  nclass[node] = (unsigned char)(cls < 0 ? 0 : cls);
+}
+
+template <int DIM>
+__global__ void patch_class_kernel(LevelGeom g, const unsigned char* __restrict__ nclass,
+                                   const unsigned char* __restrict__ mask, int* __restrict__ pclass,
+                                   int* __restrict__ rep, int dedup) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.nnodes) return;
+  if (!dedup) { pclass[i] = 0; return; }
+  const unsigned u = (unsigned)i, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+  const unsigned q = u / nx;
+  int ia[3] = {(int)(u - q * nx), DIM == 3 ? (int)(q % ny) : (int)q, DIM == 3 ? (int)(q / ny) : 0};
+  int cls = nclass[i];
+  const int r5 = DIM == 3 ? 5 : 1;
+  for (int dz = 0; dz < r5 && cls; ++dz)
+    for (int dy = 0; dy < 5 && cls; ++dy)
+      for (int dx = 0; dx < 5 && cls; ++dx) {
+        int b0 = ia[0] + dx - 2, b1 = ia[1] + dy - 2, b2 = DIM == 3 ? ia[2] + dz - 2 : 0;
+        if (b0 < 0 || b0 > g.n[0] || b1 < 0 || b1 > g.n[1] || (DIM == 3 && (b2 < 0 || b2 > g.n[2]))) { cls = 0; break; }
+        long long bn = b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2);
+        if ((mask[bn] & 1) || nclass[bn] != cls) cls = 0;
+      }
+  pclass[i] = cls;
+  if (cls) atomicMin(&rep[cls], (int)i);
+}
+
+constexpr int kScanBlock = 1024;
+
+// flag: patch is stored (class 0 or a class representative)
+__device__ __forceinline__ bool stored(const int* pclass, const int* rep, long long i) {
+  int c = pclass[i];
+  return c == 0 || rep[c] == (int)i;
+}
+
+__global__ void count_stored_kernel(long long n, const int* __restrict__ pclass, const int* __restrict__ rep,
+                                    int* __restrict__ counts) {
+  __shared__ int sm[32];
+  long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+  int f = (i < n && stored(pclass, rep, i)) ? 1 : 0;
+  unsigned bal = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kScanBlock / 32; ++w) t += sm[w];
+    counts[blockIdx.x] = t;
+  }
+}
+
+__global__ void scan_counts_kernel(int nb, int* __restrict__ counts, int* __restrict__ total) {
+  // exclusive scan in one thread (nb is the number of 1024-patch blocks)
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int run = 0;
+  for (int b = 0; b < nb; ++b) {
+    int c = counts[b];
+    counts[b] = run;
+    run += c;
+  }
+  *total = run;
+}
+
+__global__ void place_stored_kernel(long long n, const int* __restrict__ pclass, const int* __restrict__ rep,
+                                    const int* __restrict__ offs, int* __restrict__ work, int* __restrict__ prow) {
+  __shared__ int sm[32];
+  long long i = (long long)blockIdx.x * kScanBlock + threadIdx.x;
+  int f = (i < n && stored(pclass, rep, i)) ? 1 : 0;
+  unsigned bal = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sm[wid] = __popc(bal);
+  __syncthreads();
+  int before = 0;
+  for (int w = 0; w < wid; ++w) before += sm[w];
+  if (f) {
+    int pos = offs[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u));
+    work[pos] = (int)i;
+    prow[i] = pclass[i] ? -(pos + 1) : pos;
+  }
+}
+
+__global__ void class_rows_kernel(long long n, const int* __restrict__ pclass, const int* __restrict__ rep,
+                                  int* __restrict__ prow) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = pclass[i];
+  if (c && rep[c] != (int)i) prow[i] = prow[rep[c]];
+}
+
+}  // namespace
+
+cudaError_t launch_patch_classes(const LevelGeom& g, const unsigned char* cclass, const unsigned char* mask,
+                                 unsigned char* nclass, int* pclass, int* rep, int* work, int* nwork,
+                                 int* prow, int dedup, cudaStream_t s) {
+  const long long n = g.nnodes;
+  const unsigned b256 = (unsigned)((n + 255) / 256);
+  const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
+  int init[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
+  cudaError_t e = cudaMemcpyAsync(rep, init, sizeof(init), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  if (g.dim == 2) {
+    node_class_kernel<2><<<b256, 256, 0, s>>>(g, cclass, nclass);
+    patch_class_kernel<2><<<b256, 256, 0, s>>>(g, nclass, mask, pclass, rep, dedup);
+  } else {
+    node_class_kernel<3><<<b256, 256, 0, s>>>(g, cclass, nclass);
+    patch_class_kernel<3><<<b256, 256, 0, s>>>(g, nclass, mask, pclass, rep, dedup);
+  }
+  // block counts live in the tail of `work` scratch: work has n + nb ints
+  int* counts = work + n;
+  count_stored_kernel<<<nb, kScanBlock, 0, s>>>(n, pclass, rep, counts);
+  scan_counts_kernel<<<1, 32, 0, s>>>(nb, counts, nwork);
+  place_stored_kernel<<<nb, kScanBlock, 0, s>>>(n, pclass, rep, counts, work, prow);
+  class_rows_kernel<<<b256, 256, 0, s>>>(n, pclass, rep, prow);
+  note_launches(6);
+  return cudaGetLastError();
+}
+
+}  // namespace fc

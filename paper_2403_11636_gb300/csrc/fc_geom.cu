@@ -178,7 +178,8 @@ template <int DIM>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     cell_elements_kernel(LevelGeom g, double* __restrict__ eA, double* __restrict__ eB,
                          double* __restrict__ eF, double* __restrict__ estat,
-                         unsigned* __restrict__ d_err) {
+                         unsigned* __restrict__ d_err, const double* __restrict__ refA,
+                         const double* __restrict__ refB, unsigned char* __restrict__ cclass) {
   using E = Entries<DIM>;
   constexpr int NL = E::NL;
   __shared__ WarpShared wsh[kWarpsPerBlock];
@@ -227,6 +228,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   for (int t = 0; t < E::PER; ++t) acc[t] = 0.0;
   double fluid_volume = 0.0, bmeasure = 0.0;
   int nvol = 0, nbnd = 0;
+  bool split = false, al_mixed = false;
+  double al_first = -1.0;
 
   // ---- volume rule: depth-first over the split tree
   const double gq[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
@@ -261,6 +264,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     int npos = __popc(bal);
     bool cut = (npos != 0 && npos != NS);
     if (cut && level < g.qdepth) {
+      split = true;
       // push children in reverse so that child 0 is processed first
       if (lane == 0) {
         for (int ch = NL - 1; ch >= 0; --ch) {
@@ -309,6 +313,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         }
       }
       if (al == 1.0) fluid_volume = fluid_volume + w;
+      if (al_first < 0.0) al_first = al;
+      else if (al != al_first) al_mixed = true;
       nvol++;
     }
   }
@@ -513,7 +519,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
   }
 
-  // ---- write back (A mirrored)
+  // ---- write back (A mirrored).  A plain cell (not split, one alpha at all
+  // its Gauss points, no boundary points) takes alpha times the reference
+  // element matrices of the same rule on an uncut cell: the same values up
+  // to rounding, but bit-identical across plain cells, which makes the
+  // patch blocks of uncut regions bit-identical (patch classes).
+  const bool plain = refA != nullptr && !split && nbnd == 0 && !al_mixed && al_first > 0.0;
   double* A = eA + cell * NL * NL;
   double* B = eB + cell * DIM * NL * NL;
   double* F = eF + cell * DIM * NL;
@@ -521,14 +532,16 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   for (int t = 0; t < E::PER; ++t) {
     EntryId id = entry_of<DIM>(lane + 32 * t);
     if (id.kind == 0) {
-      A[id.a * NL + id.b] = acc[t];
-      A[id.b * NL + id.a] = acc[t];
+      double v = plain ? al_first * refA[id.a * NL + id.b] : acc[t];
+      A[id.a * NL + id.b] = v;
+      A[id.b * NL + id.a] = v;
     } else if (id.kind == 1) {
-      B[(id.c * NL + id.a) * NL + id.b] = acc[t];
+      B[(id.c * NL + id.a) * NL + id.b] = plain ? al_first * refB[(id.c * NL + id.a) * NL + id.b] : acc[t];
     } else if (id.kind == 2) {
       F[id.c * NL + id.a] = acc[t];
     }
   }
+  if (lane == 0 && cclass) cclass[cell] = plain ? (al_first == 1.0 ? 1 : 2) : 0;
   if (lane == 0 && estat) {
     estat[cell * 4 + 0] = fluid_volume;
     estat[cell * 4 + 1] = bmeasure;
@@ -540,12 +553,15 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 }  // namespace
 
 cudaError_t launch_cell_elements(const LevelGeom& g, double* eA, double* eB, double* eF,
-                                 double* estat, unsigned* d_err, cudaStream_t s) {
+                                 double* estat, unsigned* d_err, const double* refA, const double* refB,
+                                 unsigned char* cclass, cudaStream_t s) {
   long long blocks = (g.ncell + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (g.dim == 2)
-    cell_elements_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, eA, eB, eF, estat, d_err);
+    cell_elements_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, eA, eB, eF, estat, d_err, refA,
+                                                                             refB, cclass);
   else
-    cell_elements_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, eA, eB, eF, estat, d_err);
+    cell_elements_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, eA, eB, eF, estat, d_err, refA,
+                                                                             refB, cclass);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -91,6 +91,11 @@ struct Level {
   float2* bp2 = nullptr;
   size_t vec_bytes = 0;
   unsigned long long active_slots = 0;  // sum over patches of active patch DoFs
+  // patch classes (bit-identical L_i): prow[i] = row block of patch i;
+  // nwork row blocks are factored and stored
+  int* prow = nullptr;
+  int nwork = 0;
+  unsigned long long active_work = 0;   // active DoFs summed over the stored blocks
 };
 
 struct Profile {
@@ -141,8 +146,18 @@ void note_launches(int n);
 
 // ---- launchers (defined in the .cu files) ----
 // geometry + element data (fc_geom.cu)
+// refA/refB (nullable): reference element matrices of an uncut cell for
+// alpha = 1; plain cells then store alpha * reference.  cclass (nullable):
+// 0 cut or mixed, 1 plain fluid, 2 plain fictitious.
 cudaError_t launch_cell_elements(const LevelGeom& g, double* eA, double* eB, double* eF,
-                                 double* estat, unsigned* d_err, cudaStream_t s);
+                                 double* estat, unsigned* d_err, const double* refA, const double* refB,
+                                 unsigned char* cclass, cudaStream_t s);
+// patch classes: node class from its 2^d cells, patch class from its 5^d
+// nodes (in grid, unconstrained, one class); representatives and the work
+// list of patches to factor; prow maps every patch to its row block
+cudaError_t launch_patch_classes(const LevelGeom& g, const unsigned char* cclass, const unsigned char* mask,
+                                 unsigned char* nclass, int* pclass, int* rep, int* work, int* nwork,
+                                 int* prow, int dedup, cudaStream_t s);
 // assembly (fc_assemble.cu)
 cudaError_t launch_assemble(const LevelGeom& g, const double* eA, const double* eB, double* st,
                             cudaStream_t s);
@@ -163,12 +178,25 @@ cudaError_t launch_prolong_add(const LevelGeom& f, const LevelGeom& c, const uns
                                const double* ec, double* xf, cudaStream_t s);
 cudaError_t launch_zero_pad_halo(double* p, long long n, cudaStream_t s);
 // patches (fc_patch.cu)
+// patch cache build (mode 0 rows, 1 factors) over the work list (block w
+// stores patch work[w]); mode 2 (solve on the fly) runs over all patches
 cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsigned char* mask,
                                int mode, double omega, double* coef64, double* fac, int* fpiv,
-                               const double* rpad, double* x, unsigned* d_err, cudaStream_t s);
-// float-pair smoother pieces: split float64 into (hi, lo) pairs; residual
-// from the pair stencil and pair vectors into the padded pair residual
-// and/or an unpadded float64 residual; pair apply that also refreshes x2
+                               const double* rpad, double* x, unsigned* d_err, const int* work,
+                               long long nwork, cudaStream_t s);
+// prow (nullable = identity) maps a patch to its stored row / factor block
+cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
+                               const unsigned char* mask, const double* rpad, const float* rpad32,
+                               double omega, double* x, const int* prow, cudaStream_t s);
+cudaError_t launch_factor_apply(const LevelGeom& g, const double* fac, const int* fpiv,
+                                const unsigned char* mask, const double* rpad, double omega,
+                                double* x, const int* prow, cudaStream_t s);
+cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* coef64, void* out,
+                                long long nblocks, cudaStream_t s);
+// float-pair smoother pieces: split float64 into (hi, lo) pairs; pair
+// stencil with constrained columns folded to zero; padded pair copy of x
+// and its merge back; pair residual into the padded pair residual and/or an
+// unpadded float64 residual; pair apply updating the padded pair copy of x
 cudaError_t launch_split_pairs(long long n, const double* in, float2* out, cudaStream_t s);
 cudaError_t launch_fold_stencil_pairs(const LevelGeom& g, const double* st, const unsigned char* mask,
                                       float2* st2, cudaStream_t s);
@@ -178,15 +206,8 @@ cudaError_t launch_residual_df2(const LevelGeom& g, const float2* st2, const uns
                                 const float2* xp2, const float2* b2, float2* rpad2, double* r,
                                 cudaStream_t s);
 cudaError_t launch_patch_apply_df2(const LevelGeom& g, const void* coef, const unsigned char* mask,
-                                   const float* rpad2, double omega, float2* xp2, cudaStream_t s);
-cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
-                               const unsigned char* mask, const double* rpad, const float* rpad32,
-                               double omega, double* x, cudaStream_t s);
-cudaError_t launch_factor_apply(const LevelGeom& g, const double* fac, const int* fpiv,
-                                const unsigned char* mask, const double* rpad, double omega,
-                                double* x, cudaStream_t s);
-cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* coef64, void* out,
-                                cudaStream_t s);
+                                   const float* rpad2, double omega, float2* xp2, const int* prow,
+                                   cudaStream_t s);
 size_t factor_doubles(int dim);
 size_t factor_ints(int dim);
 // coarse solve (fc_mg.cu)

@@ -161,30 +161,36 @@ __global__ void __launch_bounds__(256)
     }
     acc[c] = {h, l};
   }
-  if (!valid || part >= ND) return;
-  const int c = part;
-  float yh, yl;
-  {
-    dfp a = acc[0];
+  if (!valid) return;
+  const unsigned char ma = mask[node];
+  // lane `part` writes components part, part + NS, ... (all of them when NS = 1)
 #pragma unroll
-    for (int k = 1; k < ND; ++k)
-      if (c == k) a = acc[k];
-    yh = a.hi; yl = a.lo;
+  for (int c0 = 0; c0 < ND; c0 += NS) {
+    const int c = c0 + part;
+    if (c >= ND) break;
+    float yh, yl;
+    {
+      dfp a = acc[0];
+#pragma unroll
+      for (int k = 1; k < ND; ++k)
+        if (c == k) a = acc[k];
+      yh = a.hi; yl = a.lo;
+    }
+    if (c < DIM && ((ma >> c) & 1)) {
+      float2 xv = xc[c];
+      yh = xv.x; yl = xv.y;
+    }
+    float2 bv = b2[node * ND + c];
+    // (b - y) as a pair
+    float sh = bv.x - yh;
+    float bb = sh - bv.x;
+    float e = (bv.x - (sh - bb)) + (-yh - bb);
+    e += bv.y - yl;
+    float h = sh + e;
+    float l = e - (h - sh);
+    if (rpad2) rpad2[pn * ND + c] = make_float2(h, l);
+    if (r) r[node * ND + c] = (double)h + (double)l;
   }
-  if (c < DIM && ((mask[node] >> c) & 1)) {
-    float2 xv = xc[c];
-    yh = xv.x; yl = xv.y;
-  }
-  float2 bv = b2[node * ND + c];
-  // (b - y) as a pair
-  float sh = bv.x - yh;
-  float bb = sh - bv.x;
-  float e = (bv.x - (sh - bb)) + (-yh - bb);
-  e += bv.y - yl;
-  float h = sh + e;
-  float l = e - (h - sh);
-  if (rpad2) rpad2[pn * ND + c] = make_float2(h, l);
-  if (r) r[node * ND + c] = (double)h + (double)l;
 }
 
 // pair stencil with the columns of constrained neighbours folded to zero

@@ -89,12 +89,12 @@ extern "C" fc_status fc_smooth_noalloc(fc_handle h, int level, double* x, const 
     else e = launch_residual(L.g, L.st, L.mask, x, b, nullptr, rpad, h->stream);
     if (e != cudaSuccess) return fail(h, FC_ERR_CUDA, cudaGetErrorString(e));
     if (inverse)
-      e = launch_patch_apply(L.g, prec, L.coef, L.mask, rpad, rpadf, h->opt.omega, x, h->stream);
+      e = launch_patch_apply(L.g, prec, L.coef, L.mask, rpad, rpadf, h->opt.omega, x, L.prow, h->stream);
     else if (h->opt.cache == FC_CACHE_MATRIX)
-      e = launch_factor_apply(L.g, L.fac, L.fpiv, L.mask, rpad, h->opt.omega, x, h->stream);
+      e = launch_factor_apply(L.g, L.fac, L.fpiv, L.mask, rpad, h->opt.omega, x, L.prow, h->stream);
     else
       e = launch_patch_build(L.g, L.st, L.mask, 2, h->opt.omega, nullptr, nullptr, nullptr, rpad, x, h->d_err,
-                             h->stream);
+                             nullptr, 0, h->stream);
     if (e != cudaSuccess) return fail(h, FC_ERR_CUDA, cudaGetErrorString(e));
   }
   return FC_OK;

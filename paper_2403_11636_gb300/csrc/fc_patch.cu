@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
     patch_factor_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
                         double omega, double* __restrict__ coef, double* __restrict__ fac,
                         int* __restrict__ fpiv, const double* __restrict__ rpad, double* __restrict__ x,
-                        unsigned* __restrict__ d_err) {
+                        unsigned* __restrict__ d_err, const int* __restrict__ work) {
   using P = PatchDims<DIM>;
   constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP, NCOL = P::NCOL;
   extern __shared__ double smem[];
@@ -150,7 +150,10 @@ __global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
   __shared__ int s_flag;
 
   const int tid = threadIdx.x, nt = blockDim.x;
-  const long long i = blockIdx.x;
+  // block blockIdx.x factors patch work[blockIdx.x] (all patches in order
+  // without a work list) and stores into block blockIdx.x
+  const long long widx = blockIdx.x;
+  const long long i = work ? work[widx] : widx;
   const int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
                      DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
   if (tid == 0) s_flag = 0;
@@ -304,7 +307,7 @@ __global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
       lu_solve_vec(S, NP, NP, pivS, z);
     }
     __syncthreads();
-    double* out = coef + (long long)i * P::NSLOT * ND;
+    double* out = coef + widx * P::NSLOT * ND;
     for (int j = tid; j < P::NSLOT; j += nt) {
       double vals[ND];
       if (j < NU * DIM) {
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
   } else if (MODE == 1) {
     // ---- store the block factors: K~ LU column-major, W~ (B~ columns),
     // S~ LU row-major, du, dp; pivots
-    double* rec = fac + (long long)i * P::REC;
+    double* rec = fac + widx * P::REC;
     for (int e = tid; e < NU * NU; e += nt) {
       int c = e / NU, r = e % NU;
       rec[e] = K[r * NU + c];
@@ -342,7 +345,7 @@ __global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
     for (int e = tid; e < NP * NP; e += nt) rec[NU * NU + DIM * NP * NU + e] = S[e];
     for (int v = tid; v < NU; v += nt) rec[NU * NU + DIM * NP * NU + NP * NP + v] = du[v];
     for (int p = tid; p < NP; p += nt) rec[NU * NU + DIM * NP * NU + NP * NP + NU + p] = dp[p];
-    int* ip = fpiv + (long long)i * P::RECI;
+    int* ip = fpiv + widx * P::RECI;
     for (int v = tid; v < NU; v += nt) ip[v] = pivK[v];
     for (int p = tid; p < NP; p += nt) ip[NU + p] = pivS[p];
   } else {
@@ -397,6 +400,13 @@ __global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
 // residual offset table is built once per block in shared memory, and the
 // node index is decoded in 32-bit arithmetic (64-bit division would run on
 // the FP64 pipe, 1/70 of the FP32 rate on this part).
+// Row loads: rows shared by a class of patches stay in the caches; a
+// patch's own rows are read once per sweep and streamed past L2.
+template <typename V>
+__device__ __forceinline__ V ldrow(const V* p, bool cached) {
+  return cached ? __ldg(p) : __ldcs(p);
+}
+
 template <int DIM>
 __device__ __forceinline__ void slot_table(const LevelGeom& g, int* soff) {
   constexpr int NU = PatchDims<DIM>::NU, ND = DIM + 1, NSLOT = PatchDims<DIM>::NSLOT;
@@ -474,7 +484,8 @@ __device__ __forceinline__ T pick(const T* v, int c) {
 template <int DIM>
 __global__ void __launch_bounds__(256)
     apply_fp64_kernel(LevelGeom g, const double* __restrict__ coef, const unsigned char* __restrict__ mask,
-                      const double* __restrict__ rpad, double omega, double* __restrict__ x) {
+                      const double* __restrict__ rpad, double omega, double* __restrict__ x,
+                      const int* __restrict__ prow) {
   using P = PatchDims<DIM>;
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
   __shared__ int soff[NSLOT];
@@ -486,7 +497,9 @@ __global__ void __launch_bounds__(256)
   decode_node<DIM>(g, i, ia);
   const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
   const double* rp = rpad + pbase * ND;
-  const double* cf = coef + (size_t)i * NSLOT * ND;
+  const int pr = prow ? prow[i] : (int)i;
+  const bool shared_rows = pr < 0;  // class rows: read through the cache
+  const double* cf = coef + (size_t)(shared_rows ? -pr - 1 : pr) * NSLOT * ND;
   double y[ND];
 #pragma unroll
   for (int k = 0; k < ND; ++k) y[k] = 0.0;
@@ -495,11 +508,11 @@ __global__ void __launch_bounds__(256)
     double rv = rp[soff[j]];
     if (ND == 4) {
       const double2* c2 = reinterpret_cast<const double2*>(cf + (size_t)j * 4);
-      double2 a = __ldcs(c2), b = __ldcs(c2 + 1);
+      double2 a = ldrow(c2, shared_rows), b = ldrow(c2 + 1, shared_rows);
       y[0] += a.x * rv; y[1] += a.y * rv; y[2] += b.x * rv; y[ND - 1] += b.y * rv;
     } else {
 #pragma unroll
-      for (int k = 0; k < ND; ++k) y[k] += __ldcs(cf + (size_t)j * ND + k) * rv;
+      for (int k = 0; k < ND; ++k) y[k] += ldrow(cf + (size_t)j * ND + k, shared_rows) * rv;
     }
   }
 #pragma unroll
@@ -510,15 +523,15 @@ __global__ void __launch_bounds__(256)
 
 // float32 / bfloat16 rows with float32 residual and float32 accumulation
 template <typename T>
-__device__ __forceinline__ void load_row4(const T* p, float* v);
+__device__ __forceinline__ void load_row4(const T* p, float* v, bool cached);
 template <>
-__device__ __forceinline__ void load_row4<float>(const float* p, float* v) {
-  float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+__device__ __forceinline__ void load_row4<float>(const float* p, float* v, bool cached) {
+  float4 a = ldrow(reinterpret_cast<const float4*>(p), cached);
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
 }
 template <>
-__device__ __forceinline__ void load_row4<__nv_bfloat16>(const __nv_bfloat16* p, float* v) {
-  uint2 a = __ldcs(reinterpret_cast<const uint2*>(p));
+__device__ __forceinline__ void load_row4<__nv_bfloat16>(const __nv_bfloat16* p, float* v, bool cached) {
+  uint2 a = ldrow(reinterpret_cast<const uint2*>(p), cached);
   v[0] = __uint_as_float(a.x << 16); v[1] = __uint_as_float(a.x & 0xffff0000u);
   v[2] = __uint_as_float(a.y << 16); v[3] = __uint_as_float(a.y & 0xffff0000u);
 }
@@ -526,7 +539,8 @@ __device__ __forceinline__ void load_row4<__nv_bfloat16>(const __nv_bfloat16* p,
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
     apply_lowp_kernel(LevelGeom g, const T* __restrict__ coef, const unsigned char* __restrict__ mask,
-                      const float* __restrict__ rpad, double omega, double* __restrict__ x) {
+                      const float* __restrict__ rpad, double omega, double* __restrict__ x,
+                      const int* __restrict__ prow) {
   using P = PatchDims<DIM>;
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
   __shared__ int soff[NSLOT];
@@ -538,7 +552,9 @@ __global__ void __launch_bounds__(256)
   decode_node<DIM>(g, i, ia);
   const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
   const float* rp = rpad + pbase * ND;
-  const T* cf = coef + (size_t)i * NSLOT * ND;
+  const int pr = prow ? prow[i] : (int)i;
+  const bool shared_rows = pr < 0;  // class rows: read through the cache
+  const T* cf = coef + (size_t)(shared_rows ? -pr - 1 : pr) * NSLOT * ND;
   float y[ND];
 #pragma unroll
   for (int k = 0; k < ND; ++k) y[k] = 0.0f;
@@ -547,10 +563,10 @@ __global__ void __launch_bounds__(256)
     float rv = rp[soff[j]];
     float cv[4];
     if (ND == 4) {
-      load_row4<T>(cf + (size_t)j * 4, cv);
+      load_row4<T>(cf + (size_t)j * 4, cv, shared_rows);
     } else {
 #pragma unroll
-      for (int k = 0; k < ND; ++k) cv[k] = (float)cf[(size_t)j * ND + k];
+      for (int k = 0; k < ND; ++k) cv[k] = (float)cf[(size_t)j * ND + k];  // 2D: scalar loads
     }
 #pragma unroll
     for (int k = 0; k < ND; ++k) y[k] = fmaf(cv[k], rv, y[k]);
@@ -607,7 +623,7 @@ template <int DIM>
 __global__ void __launch_bounds__(256)
     apply_df_kernel(LevelGeom g, const float2* __restrict__ coef, const unsigned char* __restrict__ mask,
                     const float2* __restrict__ rpad, double omega, double* __restrict__ x,
-                    float2* __restrict__ xp2, float2 om2) {
+                    float2* __restrict__ xp2, float2 om2, const int* __restrict__ prow) {
   using P = PatchDims<DIM>;
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
   __shared__ int soff[NSLOT];
@@ -619,7 +635,9 @@ __global__ void __launch_bounds__(256)
   decode_node<DIM>(g, i, ia);
   const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
   const float2* rp = rpad + pbase * ND;
-  const float2* cf = coef + (size_t)i * NSLOT * ND;
+  const int pr = prow ? prow[i] : (int)i;
+  const bool shared_rows = pr < 0;  // class rows: read through the cache
+  const float2* cf = coef + (size_t)(shared_rows ? -pr - 1 : pr) * NSLOT * ND;
   df y[ND];
 #pragma unroll
   for (int k = 0; k < ND; ++k) y[k] = {0.0f, 0.0f};
@@ -629,13 +647,13 @@ __global__ void __launch_bounds__(256)
     float ch[4], cl[4];
     if (ND == 4) {
       const float4* c4 = reinterpret_cast<const float4*>(cf + (size_t)j * 4);
-      float4 a = __ldcs(c4), b = __ldcs(c4 + 1);
+      float4 a = ldrow(c4, shared_rows), b = ldrow(c4 + 1, shared_rows);
       ch[0] = a.x; cl[0] = a.y; ch[1] = a.z; cl[1] = a.w;
       ch[2] = b.x; cl[2] = b.y; ch[3] = b.z; cl[3] = b.w;
     } else {
 #pragma unroll
       for (int k = 0; k < ND; ++k) {
-        float2 c2 = __ldcs(cf + (size_t)j * ND + k);
+        float2 c2 = ldrow(cf + (size_t)j * ND + k, shared_rows);
         ch[k] = c2.x; cl[k] = c2.y;
       }
     }
@@ -676,7 +694,7 @@ template <int DIM>
 __global__ void __launch_bounds__(128)
     factor_apply_kernel(LevelGeom g, const double* __restrict__ fac, const int* __restrict__ fpiv,
                         const unsigned char* __restrict__ mask, const double* __restrict__ rpad,
-                        double omega, double* __restrict__ x) {
+                        double omega, double* __restrict__ x, const int* __restrict__ prow) {
   using P = PatchDims<DIM>;
   constexpr int NU = P::NU, NP = P::NP, ND = P::ND;
   __shared__ double sz[4][DIM * NU + 2 * NP];
@@ -686,13 +704,15 @@ __global__ void __launch_bounds__(128)
   double* z = sz[wib];             // DIM vectors of NU (component-major)
   double* t = z + DIM * NU;        // NP
   double* zpv = t + NP;            // NP
-  const double* rec = fac + i * (long long)P::REC;
+  const int pr = prow ? prow[i] : (int)i;
+  const long long blk = pr < 0 ? -(long long)pr - 1 : pr;
+  const double* rec = fac + blk * (long long)P::REC;
   const double* LUc = rec;                        // column-major
   const double* Wm = rec + NU * NU;               // [c*NP+q][NU]
   const double* Sm = Wm + DIM * NP * NU;          // row-major NP x NP
   const double* du = Sm + NP * NP;
   const double* dp = du + NU;
-  const int* piv = fpiv + i * (long long)P::RECI;
+  const int* piv = fpiv + blk * (long long)P::RECI;
   int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
                DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
   long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
@@ -819,12 +839,14 @@ size_t factor_smem() {
 template <int DIM, int MODE>
 cudaError_t run_factor(const LevelGeom& g, const double* st, const unsigned char* mask, double omega,
                        double* coef, double* fac, int* fpiv, const double* rpad, double* x,
-                       unsigned* d_err, cudaStream_t s) {
+                       unsigned* d_err, const int* work, long long nwork, cudaStream_t s) {
   size_t sm = factor_smem<DIM>();
   auto kern = patch_factor_kernel<DIM, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)g.nnodes, PatchDims<DIM>::THREADS, sm, s>>>(g, st, mask, omega, coef, fac, fpiv, rpad, x, d_err);
+  const long long nb = work ? nwork : g.nnodes;
+  if (nb <= 0) return cudaSuccess;
+  kern<<<(unsigned)nb, PatchDims<DIM>::THREADS, sm, s>>>(g, st, mask, omega, coef, fac, fpiv, rpad, x, d_err, work);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -836,65 +858,67 @@ size_t factor_ints(int dim) { return dim == 3 ? PatchDims<3>::RECI : PatchDims<2
 
 cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsigned char* mask, int mode,
                                double omega, double* coef64, double* fac, int* fpiv,
-                               const double* rpad, double* x, unsigned* d_err, cudaStream_t s) {
+                               const double* rpad, double* x, unsigned* d_err, const int* work,
+                               long long nwork, cudaStream_t s) {
   if (g.dim == 2) {
-    if (mode == 0) return run_factor<2, 0>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
-    if (mode == 1) return run_factor<2, 1>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
-    return run_factor<2, 2>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
+    if (mode == 0) return run_factor<2, 0>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, work, nwork, s);
+    if (mode == 1) return run_factor<2, 1>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, work, nwork, s);
+    return run_factor<2, 2>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, nullptr, 0, s);
   }
-  if (mode == 0) return run_factor<3, 0>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
-  if (mode == 1) return run_factor<3, 1>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
-  return run_factor<3, 2>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, s);
+  if (mode == 0) return run_factor<3, 0>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, work, nwork, s);
+  if (mode == 1) return run_factor<3, 1>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, work, nwork, s);
+  return run_factor<3, 2>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, nullptr, 0, s);
 }
 
 cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
                                const unsigned char* mask, const double* rpad, const float* rpad32,
-                               double omega, double* x, cudaStream_t s) {
+                               double omega, double* x, const int* prow, cudaStream_t s) {
   long long threads = g.nnodes * 32;
   unsigned blocks = (unsigned)((threads + 255) / 256);
   if (prec == FC_PREC_FP64) {
-    if (g.dim == 2) apply_fp64_kernel<2><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x);
-    else apply_fp64_kernel<3><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x);
+    if (g.dim == 2) apply_fp64_kernel<2><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x, prow);
+    else apply_fp64_kernel<3><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x, prow);
   } else if (prec == FC_PREC_FP32) {
-    if (g.dim == 2) apply_lowp_kernel<2, float><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x);
-    else apply_lowp_kernel<3, float><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x);
+    if (g.dim == 2) apply_lowp_kernel<2, float><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x, prow);
+    else apply_lowp_kernel<3, float><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x, prow);
   } else if (prec == FC_PREC_BF16) {
-    if (g.dim == 2) apply_lowp_kernel<2, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x);
-    else apply_lowp_kernel<3, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x);
+    if (g.dim == 2) apply_lowp_kernel<2, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x, prow);
+    else apply_lowp_kernel<3, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x, prow);
   } else {
     const float2 om2 = make_float2((float)omega, (float)(omega - (double)(float)omega));
-    if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x, nullptr, om2);
-    else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x, nullptr, om2);
+    if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x, nullptr, om2, prow);
+    else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x, nullptr, om2, prow);
   }
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_patch_apply_df2(const LevelGeom& g, const void* coef, const unsigned char* mask,
-                                   const float* rpad2, double omega, float2* xp2, cudaStream_t s) {
+                                   const float* rpad2, double omega, float2* xp2, const int* prow,
+                                   cudaStream_t s) {
   long long threads = g.nnodes * 32;
   unsigned blocks = (unsigned)((threads + 255) / 256);
   const float2 om2 = make_float2((float)omega, (float)(omega - (double)(float)omega));
-  if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad2, omega, nullptr, xp2, om2);
-  else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad2, omega, nullptr, xp2, om2);
+  if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad2, omega, nullptr, xp2, om2, prow);
+  else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad2, omega, nullptr, xp2, om2, prow);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_factor_apply(const LevelGeom& g, const double* fac, const int* fpiv,
                                 const unsigned char* mask, const double* rpad, double omega, double* x,
-                                cudaStream_t s) {
+                                const int* prow, cudaStream_t s) {
   long long threads = g.nnodes * 32;
   unsigned blocks = (unsigned)((threads + 127) / 128);
-  if (g.dim == 2) factor_apply_kernel<2><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x);
-  else factor_apply_kernel<3><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x);
+  if (g.dim == 2) factor_apply_kernel<2><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x, prow);
+  else factor_apply_kernel<3><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x, prow);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* coef64, void* out,
-                                cudaStream_t s) {
-  long long n = g.nnodes * (long long)nslot(g.dim) * g.nd;
+                                long long nblocks, cudaStream_t s) {
+  long long n = nblocks * (long long)nslot(g.dim) * g.nd;
   unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 152LL * 32);
   if (prec == FC_PREC_FP32) convert_kernel<float><<<blocks, 256, 0, s>>>(n, coef64, (float*)out);
   else if (prec == FC_PREC_BF16) convert_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(n, coef64, (__nv_bfloat16*)out);

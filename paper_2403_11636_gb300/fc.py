@@ -49,7 +49,7 @@ class FcOptions(C.Structure):
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("quad_depth", C.c_int),
                 ("cache", C.c_int), ("prec", C.c_int), ("fgmres_restart", C.c_int),
                 ("bc_preset", C.c_int), ("ubar", C.c_double), ("force_kind", C.c_int),
-                ("force", C.c_double * 3)]
+                ("force", C.c_double * 3), ("dedup", C.c_int)]
 
 
 _lib = None
@@ -106,7 +106,7 @@ def _grid(prob) -> FcGrid:
     return g
 
 
-def _options(prob, cache: str, prec: str, nu=None) -> FcOptions:
+def _options(prob, cache: str, prec: str, nu=None, dedup: int = 1) -> FcOptions:
     o = FcOptions()
     load().fc_options_default(C.byref(o))
     o.eta, o.nitsche_beta, o.omega = prob.eta, prob.beta, prob.omega
@@ -118,6 +118,7 @@ def _options(prob, cache: str, prec: str, nu=None) -> FcOptions:
     o.force_kind = prob.force_kind
     for k in range(3):
         o.force[k] = float(prob.force[k])
+    o.dedup = int(dedup)
     return o
 
 
@@ -135,7 +136,8 @@ def footprint_estimate(prob, cache="inverse", prec="fp64") -> int:
 class Solver:
     """A finite cell Stokes problem set up on the GPU (one fc_handle)."""
 
-    def __init__(self, prob, cache: str = "inverse", prec: str = "fp64", stream=None, nu=None):
+    def __init__(self, prob, cache: str = "inverse", prec: str = "fp64", stream=None, nu=None,
+                 dedup: int = 1):
         import torch
         if not torch.cuda.is_available():
             raise FcError(-1, "libfc needs a CUDA GPU")
@@ -159,7 +161,7 @@ class Solver:
         ls = FcLevelset(len(shapes), C.cast(arr, C.POINTER(FcShape)))
         self.h = C.c_void_p()
         st = self.lib.fc_setup(C.byref(self.h), C.byref(_grid(prob)), C.byref(ls), float(prob.alpha),
-                               int(prob.nlevels), C.byref(_options(prob, cache, prec, nu)),
+                               int(prob.nlevels), C.byref(_options(prob, cache, prec, nu, dedup)),
                                C.c_void_p(self.stream.cuda_stream))
         self._check(st)
 

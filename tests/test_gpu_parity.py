@@ -263,3 +263,22 @@ def test_ragged_and_anisotropic_grid(fc):
     x0 = inputs.random_vector(p, 101)
     assert rel(s.apply(x0).cpu().numpy(), A @ x0) <= OPER_TOL
     assert rel(s.smooth(x0, b).cpu().numpy() - x0, L.sweep(b, x0) - x0) <= SWEEP_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("name", ["ch2d", "por3d", "ell2d"])
+def test_shared_class_blocks_change_nothing(fc, name, prec):
+    """Patches with bit-identical blocks L_i share one stored block (dedup=1);
+    the results are bit-identical to one block per patch (dedup=0), and far
+    fewer blocks are factored."""
+    p = PROBS[name]
+    s1 = fc.Solver(p, prec=prec, dedup=1)
+    s0 = fc.Solver(p, prec=prec, dedup=0)
+    x0 = inputs.random_vector(p, 111)
+    b = inputs.random_vector(p, 112)
+    np.testing.assert_array_equal(s1.smooth(x0, b, nsweeps=2).cpu().numpy(),
+                                  s0.smooth(x0, b, nsweeps=2).cpu().numpy())
+    nn = np.prod([k + 1 for k in p.level_n(p.nlevels)])
+    for node in np.random.default_rng(3).choice(nn, 16, replace=False):
+        np.testing.assert_array_equal(s1.patch_rows(int(node)), s0.patch_rows(int(node)))
+    assert s1.info()["bytes"][1] <= s0.info()["bytes"][1]
