@@ -263,7 +263,7 @@ def run_ours(args, rank, world, local_rank):
         return 0
     hbm, peak_kind = peaks()
     achieved = bytes_fine / (ms_fine / max(n_fine, 1) * 1e-3) / 1e9 if ms_fine > 0 else 0.0
-    traffic = load_traffic(args.prec)
+    traffic = load_traffic(args.prec) if not args.dedup else None
     step_sorted = sorted(step_ms)
     p50 = statistics.median(step_sorted)
     p99 = step_sorted[min(len(step_sorted) - 1, int(math.ceil(0.99 * len(step_sorted))) - 1)]
@@ -392,6 +392,7 @@ def load_traffic(prec):
     """DRAM bytes per finest-level launch of the patch apply, from the
     committed ncu summary of this precision (a line 'traffic_bytes_64: N')."""
     path = os.path.join(ROOT, "profiles", f"patch_apply_{prec}_porous48.md")
+    # the summary is of the per-patch layout (one stored block per patch)
     try:
         for line in open(path):
             if line.strip().startswith("traffic_bytes_64:"):
@@ -410,7 +411,8 @@ def main():
     ap.add_argument("--cache", default="inverse", choices=["inverse", "matrix", "none"])
     ap.add_argument("--prec", default="df64", choices=["fp64", "df64", "fp32", "bf16"])
     ap.add_argument("--policies", type=int, default=1)
-    ap.add_argument("--dedup", type=int, default=1, help="share the blocks of bit-identical patches")
+    ap.add_argument("--dedup", type=int, default=0,
+                    help="1: patches with bit-identical blocks share one stored block (same results)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--mode", default="solve", choices=["solve", "sweep"])

@@ -232,7 +232,8 @@ fc_status smooth_level_pairs(fc_handle h, int li, double* x, const double* b, in
     }
     ProfScope ps(h, 0, level_apply_bytes(h, li));
     ProfScope pf(h, li == h->nlev - 1 ? 4 : -1, level_apply_bytes(h, li));
-    CK(launch_patch_apply_df2(L.g, L.coef, L.mask, L.rpad32, h->opt.omega, L.xp2, L.prow, h->stream));
+    CK(launch_patch_apply_df2(L.g, L.coef, L.mask, L.rpad32, h->opt.omega, L.xp2, L.prow, L.cls_blk,
+                              h->stream));
   }
   CK(launch_merge_x_padded(L.g, L.xp2, x, h->stream));
   return FC_OK;
@@ -557,7 +558,15 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
       CK(launch_patch_classes(G, cclass, L.mask, nclass, pclass, rep, work, dnw, L.prow, o->dedup,
                               h->stream));
       CK(cudaMemcpyAsync(&L.nwork, dnw, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+      int reph[4] = {0, 0, 0, 0};
+      CK(cudaMemcpyAsync(reph, rep, sizeof(reph), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaStreamSynchronize(h->stream));
+      for (int c = 1; c <= 2; ++c) {
+        if (reph[c] == 0x7fffffff) continue;
+        int pr = 0;
+        CK(cudaMemcpy(&pr, L.prow + reph[c], sizeof(int), cudaMemcpyDeviceToHost));
+        L.cls_blk[c - 1] = pr < 0 ? -pr - 1 : -1;
+      }
       cudaFree(nclass);
       cudaFree(pclass);
       cudaFree(rep);

@@ -95,6 +95,7 @@ struct Level {
   // nwork row blocks are factored and stored
   int* prow = nullptr;
   int nwork = 0;
+  int cls_blk[2] = {-1, -1};            // stored blocks of the patch classes 1 and 2
   unsigned long long active_work = 0;   // active DoFs summed over the stored blocks
 };
 
@@ -205,9 +206,11 @@ cudaError_t launch_merge_x_padded(const LevelGeom& g, const float2* xp2, double*
 cudaError_t launch_residual_df2(const LevelGeom& g, const float2* st2, const unsigned char* mask,
                                 const float2* xp2, const float2* b2, float2* rpad2, double* r,
                                 cudaStream_t s);
+// cls_blk: host array of the (up to two) stored blocks shared by the patch
+// classes, -1 for none; those blocks are staged in shared memory
 cudaError_t launch_patch_apply_df2(const LevelGeom& g, const void* coef, const unsigned char* mask,
                                    const float* rpad2, double omega, float2* xp2, const int* prow,
-                                   cudaStream_t s);
+                                   const int* cls_blk, cudaStream_t s);
 size_t factor_doubles(int dim);
 size_t factor_ints(int dim);
 // coarse solve (fc_mg.cu)

@@ -851,6 +851,133 @@ cudaError_t run_factor(const LevelGeom& g, const double* st, const unsigned char
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Persistent float-pair apply for the pair smoothing phase.  CTAs stay
+// resident (one wave); each first copies the row blocks shared by the patch
+// classes (at most two) into shared memory, then its warps stride over the
+// patches.  A class patch reads its rows from shared memory, a unique patch
+// streams its own rows from HBM; the residual gathers and the pair update of
+// x are those of apply_df_kernel.
+constexpr int kMaxClassBlocks = 2;
+
+template <int DIM, bool SMEM>
+__device__ __forceinline__ void df_patch_dot(const float2* __restrict__ cf, const float2* __restrict__ rp,
+                                             const int* soff, int lane, df* y) {
+  using P = PatchDims<DIM>;
+  constexpr int ND = P::ND, NSLOT = P::NSLOT;
+#pragma unroll 2
+  for (int j = lane; j < NSLOT; j += 32) {
+    float2 r2 = rp[soff[j]];
+    float ch[4], cl[4];
+    if (ND == 4) {
+      const float4* c4 = reinterpret_cast<const float4*>(cf + (size_t)j * 4);
+      float4 a, b;
+      if (SMEM) { a = c4[0]; b = c4[1]; }
+      else { a = __ldcs(c4); b = __ldcs(c4 + 1); }
+      ch[0] = a.x; cl[0] = a.y; ch[1] = a.z; cl[1] = a.w;
+      ch[2] = b.x; cl[2] = b.y; ch[3] = b.z; cl[3] = b.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < ND; ++k) {
+        float2 c2 = SMEM ? cf[(size_t)j * ND + k] : __ldcs(cf + (size_t)j * ND + k);
+        ch[k] = c2.x; cl[k] = c2.y;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < ND; ++k) df_fma_acc(y[k], ch[k], cl[k], r2.x, r2.y);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    apply_df_persistent_kernel(LevelGeom g, const float2* __restrict__ coef, const unsigned char* __restrict__ mask,
+                               const float2* __restrict__ rpad, float2* __restrict__ xp2, float2 om2,
+                               const int* __restrict__ prow, int2 cls_blk) {
+  using P = PatchDims<DIM>;
+  constexpr int ND = P::ND, NSLOT = P::NSLOT;
+  __shared__ int soff[NSLOT];
+  extern __shared__ float4 srow_raw[];
+  float2* srows = reinterpret_cast<float2*>(srow_raw);
+  const int nblk_sh = (cls_blk.x >= 0) + (cls_blk.y >= 0);
+  const int blk_id[2] = {cls_blk.x, cls_blk.y};
+  for (int b = 0; b < nblk_sh; ++b) {
+    // element-wise float2 copy: 2D blocks (177 pairs) are only 8-byte aligned
+    const float2* src = coef + (size_t)blk_id[b] * NSLOT * ND;
+    float2* dst = srows + (size_t)b * NSLOT * ND;
+    for (int t = threadIdx.x; t < NSLOT * ND; t += blockDim.x) dst[t] = __ldg(src + t);
+  }
+  slot_table<DIM>(g, soff);  // ends with __syncthreads()
+  const int lane = threadIdx.x & 31;
+  const unsigned wpb = blockDim.x >> 5;
+  const unsigned nwarps = gridDim.x * wpb;
+  for (unsigned i = blockIdx.x * wpb + (threadIdx.x >> 5); i < (unsigned)g.nnodes; i += nwarps) {
+    int ia[3];
+    decode_node<DIM>(g, i, ia);
+    const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
+    const float2* rp = rpad + pbase * ND;
+    const int pr = prow ? prow[i] : (int)i;
+    df y[ND];
+#pragma unroll
+    for (int k = 0; k < ND; ++k) y[k] = {0.0f, 0.0f};
+    int sh = -1;
+    if (pr < 0) {
+      const int blk = -pr - 1;
+      sh = blk == cls_blk.x ? 0 : (blk == cls_blk.y ? 1 : -1);
+    }
+    if (sh >= 0) {
+      df_patch_dot<DIM, true>(srows + (size_t)sh * NSLOT * ND, rp, soff, lane, y);
+    } else {
+      const size_t blk = pr < 0 ? (size_t)(-pr - 1) : (size_t)pr;
+      df_patch_dot<DIM, false>(coef + blk * NSLOT * ND, rp, soff, lane, y);
+    }
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+      float h = y[k].hi + y[k].lo;
+      y[k] = {h, y[k].lo - (h - y[k].hi)};
+      for (int o = 16; o > 0; o >>= 1) {
+        df other = {__shfl_xor_sync(0xffffffffu, y[k].hi, o), __shfl_xor_sync(0xffffffffu, y[k].lo, o)};
+        y[k] = df_add(y[k], other);
+      }
+    }
+    if (lane < ND) {
+      const float2 r2 = rp[lane];
+      const df yl = pick<ND>(y, lane);
+      const size_t k = (size_t)pbase * ND + lane;
+      const float2 xv = xp2[k];
+      const bool fixed = lane < DIM && ((mask[i] >> lane) & 1);
+      const df add = fixed ? df{r2.x, r2.y} : df_mul({om2.x, om2.y}, yl);
+      const df nv = df_add({xv.x, xv.y}, add);
+      xp2[k] = make_float2(nv.hi, nv.lo);
+    }
+  }
+}
+
+template <int DIM>
+cudaError_t run_df_persistent(const LevelGeom& g, const float2* coef, const unsigned char* mask,
+                              const float2* rpad, float2* xp2, float2 om2, const int* prow, int2 cls,
+                              cudaStream_t s) {
+  using P = PatchDims<DIM>;
+  const size_t smem = (size_t)kMaxClassBlocks * P::NSLOT * P::ND * sizeof(float2);
+  auto kern = apply_df_persistent_kernel<DIM>;
+  static int per_sm[4] = {0, 0, 0, 0};
+  static int nsm = 0;
+  if (!per_sm[DIM]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[DIM], kern, 256, smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (per_sm[DIM] < 1) per_sm[DIM] = 1;
+  }
+  long long need = (g.nnodes + 7) / 8;
+  long long blocks = std::min<long long>((long long)per_sm[DIM] * nsm, need);
+  kern<<<(unsigned)std::max<long long>(blocks, 1), 256, smem, s>>>(g, coef, mask, rpad, xp2, om2, prow, cls);
+  note_launches(1);
+  return cudaGetLastError();
+}
 }  // namespace
 
 size_t factor_doubles(int dim) { return dim == 3 ? PatchDims<3>::REC : PatchDims<2>::REC; }
@@ -895,14 +1022,12 @@ cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coe
 
 cudaError_t launch_patch_apply_df2(const LevelGeom& g, const void* coef, const unsigned char* mask,
                                    const float* rpad2, double omega, float2* xp2, const int* prow,
-                                   cudaStream_t s) {
-  long long threads = g.nnodes * 32;
-  unsigned blocks = (unsigned)((threads + 255) / 256);
+                                   const int* cls_blk, cudaStream_t s) {
   const float2 om2 = make_float2((float)omega, (float)(omega - (double)(float)omega));
-  if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad2, omega, nullptr, xp2, om2, prow);
-  else apply_df_kernel<3><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad2, omega, nullptr, xp2, om2, prow);
-  note_launches(1);
-  return cudaGetLastError();
+  const int2 cls = make_int2(cls_blk ? cls_blk[0] : -1, cls_blk ? cls_blk[1] : -1);
+  if (g.dim == 2)
+    return run_df_persistent<2>(g, (const float2*)coef, mask, (const float2*)rpad2, xp2, om2, prow, cls, s);
+  return run_df_persistent<3>(g, (const float2*)coef, mask, (const float2*)rpad2, xp2, om2, prow, cls, s);
 }
 
 cudaError_t launch_factor_apply(const LevelGeom& g, const double* fac, const int* fpiv,
