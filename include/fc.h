@@ -182,6 +182,14 @@ fc_status fc_vcycle(fc_handle h, double* x_dev, const double* b_dev);
 fc_status fc_solve(fc_handle h, const double* b_dev, double* x_dev, double rtol, int maxit,
                    int* iters, double* relres);
 
+/* Standalone geometric multigrid (the setting of the paper's experiments,
+ * Sec. 4): V(nu_pre, nu_post) cycles on x_dev until ||b - L x||_2 <=
+ * reduction * ||b - L x0||_2 or maxit cycles.  *iters = cycles,
+ * *relred = achieved reduction.  Synchronises once per cycle.  Returns
+ * FC_ERR_NOT_CONVERGED if the reduction was not reached. */
+fc_status fc_gmg_solve(fc_handle h, const double* b_dev, double* x_dev, double reduction, int maxit,
+                       int* iters, double* relred);
+
 /* As fc_solve, with HOST buffers (pinned memory recommended): copies b to
  * the device, solves from x0 = x_host, copies x back.  Synchronises. */
 fc_status fc_solve_host(fc_handle h, const double* b_host, double* x_host, double rtol, int maxit,

@@ -814,6 +814,42 @@ fc_status fc_solve(fc_handle h, const double* b, double* x, double rtol, int max
   return FC_OK;
 }
 
+fc_status fc_gmg_solve(fc_handle h, const double* b, double* x, double reduction, int maxit, int* iters,
+                       double* relred) {
+  if (!h || !b || !x || !(reduction > 0.0) || maxit < 0)
+    return h ? fail(h, FC_ERR_INVALID, "bad GMG arguments") : FC_ERR_INVALID;
+  Level& F = h->lev[h->nlev - 1];
+  const long long n = F.g.ndof;
+  cudaStream_t s = h->stream;
+  double* sc = h->small + small_sc(h->restart);
+  double r0 = 0.0, rn = 0.0;
+  CK(launch_residual(F.g, F.st, F.mask, x, b, h->w, nullptr, s));
+  CK(launch_dot(n, h->w, h->w, h->red, sc + 1, s));
+  fc_status st = read_scalar(h, sc + 1, &r0);
+  if (st != FC_OK) return st;
+  r0 = sqrt(r0);
+  rn = r0;
+  int it = 0;
+  while (it < maxit && rn > reduction * r0) {
+    {
+      ProfScope ps(h, 2, 0.0);
+      st = vcycle_level(h, h->nlev - 1, x, b);
+      if (st != FC_OK) return st;
+    }
+    CK(launch_residual(F.g, F.st, F.mask, x, b, h->w, nullptr, s));
+    CK(launch_dot(n, h->w, h->w, h->red, sc + 1, s));
+    st = read_scalar(h, sc + 1, &rn);
+    if (st != FC_OK) return st;
+    rn = sqrt(rn);
+    it++;
+  }
+  if (iters) *iters = it;
+  const double red = r0 > 0.0 ? rn / r0 : 0.0;
+  if (relred) *relred = red;
+  if (r0 > 0.0 && red > reduction) return fail(h, FC_ERR_NOT_CONVERGED, "GMG reached maxit above the reduction");
+  return FC_OK;
+}
+
 fc_status fc_solve_host(fc_handle h, const double* b_host, double* x_host, double rtol, int maxit,
                         int* iters, double* relres) {
   if (!h || !b_host || !x_host) return FC_ERR_INVALID;

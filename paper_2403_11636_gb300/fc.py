@@ -20,7 +20,7 @@ CACHE = {"inverse": 0, "matrix": 1, "none": 2}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "df64": 3}
 EXPORTS = ("fc_options_default", "fc_setup", "fc_rhs", "fc_residual", "fc_apply", "fc_smooth",
            "fc_smooth_noalloc", "fc_restrict", "fc_prolong_add", "fc_coarse_solve", "fc_vcycle", "fc_solve",
-           "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
+           "fc_gmg_solve", "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
            "fc_profile_enable", "fc_profile_read", "fc_launch_count", "fc_sync", "fc_last_error",
            "fc_destroy")
 
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     lib.fc_vcycle.argtypes = [vp, vp, vp]
     lib.fc_solve.argtypes = [vp, vp, vp, d, i, P(i), P(d)]
     lib.fc_solve_host.argtypes = [vp, vp, vp, d, i, P(i), P(d)]
+    lib.fc_gmg_solve.argtypes = [vp, vp, vp, d, i, P(i), P(d)]
     lib.fc_info.argtypes = [vp, i, P(ll), P(ll), P(C.c_size_t)]
     lib.fc_patch_rows.argtypes = [vp, i, ll, P(d)]
     lib.fc_footprint_estimate.restype = C.c_size_t
@@ -283,6 +284,18 @@ class Solver:
         if st not in (FC_OK, FC_ERR_NOT_CONVERGED):
             self._check(st)
         return x, its.value, rel.value
+
+    def gmg_solve(self, b, x0=None, reduction=1e-9, maxit=100):
+        """Standalone V-cycles until the residual falls by ``reduction``;
+        returns (x, cycles, achieved reduction)."""
+        b = self._dev(b)
+        x = self.zeros() if x0 is None else self._dev(x0).clone()
+        its, red = C.c_int(), C.c_double()
+        st = self.lib.fc_gmg_solve(self.h, self._ptr(b), self._ptr(x), float(reduction), int(maxit),
+                                   C.byref(its), C.byref(red))
+        if st not in (FC_OK, FC_ERR_NOT_CONVERGED):
+            self._check(st)
+        return x, its.value, red.value
 
     def solve_host(self, b_host, x_host, rtol=None, maxit=200):
         """FGMRES + GMG from host buffers (numpy or pinned torch CPU tensors)."""

@@ -202,6 +202,22 @@ def batch_2d(seed: int, sizes=(16, 32, 64, 128), alphas=(1e-6, 1e-8, 1e-10)) -> 
                    force_kind=1, force=(1.0, 1.0, 0.0))
 
 
+def channel_replay_2d(seed: int = 0, nx: int = 1024, ny: int = 256, nlevels: int = 6,
+                      alpha: float = 1e-10) -> Problem:
+    """Stand-in for the paper's channel flow benchmark (Sec. 4): a 2.2 x 0.41
+    channel on an nx x ny background grid (1024 x 256 is the size of the
+    paper's coarse grid Omega^1 in Table tab:grid), a cylinder of diameter 0.1
+    near the inflow (centre drawn in [0.15, 0.25] x [0.15, 0.26]: the exact
+    benchmark position is not given in the paper), parabolic inflow with
+    ubar = 0.3, eta = 1e-3, alpha = 1e-10, no body force, V(6,6) cycles."""
+    rng = SplitMix64(0xC4A77E1 + seed)
+    cx, cy = rng.uniform(0.15, 0.25), rng.uniform(0.15, 0.26)
+    shapes = np.array([[0.0, cx, cy, 0.0, 0.05, 0.05, 0.05, 1.0, 0.0]])
+    return Problem(name=f"channel_replay_{nx}x{ny}_s{seed}", dim=2, n=(nx, ny), lo=(0.0, 0.0),
+                   hi=(2.2, 0.41), shapes=shapes, alpha=alpha, qdepth=4, nlevels=nlevels,
+                   nu_pre=6, nu_post=6, preset=0, force_kind=0, force=(0.0, 0.0, 0.0))
+
+
 def roofline_2d(n: int = 4096, nlevels: int = 9) -> Problem:
     """2D case shaped like the paper's 53M-DoF grid: n^2 cells, one circle of
     radius 0.2 at the centre, alpha = 1e-10."""

@@ -282,3 +282,18 @@ def test_shared_class_blocks_change_nothing(fc, name, prec):
     for node in np.random.default_rng(3).choice(nn, 16, replace=False):
         np.testing.assert_array_equal(s1.patch_rows(int(node)), s0.patch_rows(int(node)))
     assert s1.info()["bytes"][1] <= s0.info()["bytes"][1]
+
+
+@pytest.mark.parametrize("nx,ny,nlev", [(128, 32, 3), (256, 64, 4)])
+def test_standalone_gmg_replay(fc, nx, ny, nlev):
+    """Standalone GMG in the paper's setting (Sec. 4: V(6,6), damping 0.8, a
+    1e9 residual reduction, alpha = 1e-10) on the channel stand-in: the GPU
+    needs the same number of cycles as the oracle."""
+    p = inputs.channel_replay_2d(0, nx=nx, ny=ny, nlevels=nlev)
+    mg = O.MG(p)
+    b = mg.rhs()
+    x_or, its_or, red_or = mg.gmg_solve(b, reduction=1e-9, maxit=60)
+    s = fc.Solver(p)
+    x_gpu, its, red = s.gmg_solve(s.rhs(), reduction=1e-9, maxit=60)
+    assert red <= 1e-9 and its == its_or
+    assert rel(x_gpu.cpu().numpy(), x_or) <= 1e-6
