@@ -22,6 +22,7 @@
 //   mode 2 (cache_none):    solves with the gathered residual at once and
 //          updates the owned DoFs (nothing stored).
 #include <cuda_bf16.h>
+#include <stdlib.h>
 #include <math.h>
 
 #include <algorithm>
@@ -124,8 +125,42 @@ __device__ void lu_solve_vec(const double* A, int n, int ld, const int* piv, dou
   }
 }
 
+// W <- A^{-1} W for ncol right-hand sides (column-major, length n) with the
+// row-major LU and pivots of A, all threads of the CTA cooperating: the row
+// swaps per column, then column-oriented forward and back substitution with
+// one barrier per pivot step (each step updates every column at once).
+__device__ void cta_lu_solve_multi(const double* A, int n, const int* piv, double* W, int ncol) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int col = tid; col < ncol; col += nt) {
+    double* z = W + col * n;
+    for (int k = 0; k < n; ++k) {
+      int p = piv[k];
+      if (p != k) { double t = z[k]; z[k] = z[p]; z[p] = t; }
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < n - 1; ++k) {
+    const int m = n - 1 - k;
+    for (int t = tid; t < m * ncol; t += nt) {
+      const int col = t / m, r = k + 1 + t % m;
+      W[col * n + r] = W[col * n + r] - A[r * n + k] * W[col * n + k];
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const double d = A[k * n + k];
+    for (int col = tid; col < ncol; col += nt) W[col * n + k] = W[col * n + k] / d;
+    __syncthreads();
+    for (int t = tid; t < k * ncol; t += nt) {
+      const int col = t / k, r = t % k;
+      W[col * n + r] = W[col * n + r] - A[r * n + k] * W[col * n + k];
+    }
+    __syncthreads();
+  }
+}
+
 template <int DIM, int MODE>
-__global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
+__global__ void __launch_bounds__(1024)
     patch_factor_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
                         double omega, double* __restrict__ coef, double* __restrict__ fac,
                         int* __restrict__ fpiv, const double* __restrict__ rpad, double* __restrict__ x,
@@ -266,7 +301,7 @@ __global__ void __launch_bounds__(PatchDims<DIM>::THREADS)
   cta_lu(K, NU, NU, pivK, &s_flag);
   // ---- W~ = K~^{-1} [B~ | e_centre | D r_u]
   const int ncol = MODE == 2 ? NCOL : DIM * NP + 1;
-  for (int col = tid; col < ncol; col += nt) lu_solve_vec(K, NU, NU, pivK, W + col * NU);
+  cta_lu_solve_multi(K, NU, pivK, W, ncol);
   __syncthreads();
   // ---- S~ = C~ - sum_c B~_c^T W~_c, B~ re-read from the operator (27 / 9
   // velocity nodes are adjacent to a pressure node)
@@ -846,7 +881,15 @@ cudaError_t run_factor(const LevelGeom& g, const double* st, const unsigned char
   if (e != cudaSuccess) return e;
   const long long nb = work ? nwork : g.nnodes;
   if (nb <= 0) return cudaSuccess;
-  kern<<<(unsigned)nb, PatchDims<DIM>::THREADS, sm, s>>>(g, st, mask, omega, coef, fac, fpiv, rpad, x, d_err, work);
+  // threads per CTA: the 3D block needs 220 KB of shared memory, so one CTA
+  // fills an SM and its warps alone hide the shared-memory and barrier
+  // latency; FC_FACTOR_THREADS overrides the choice for tuning runs
+  int threads = DIM == 3 ? 1024 : 128;
+  if (const char* env = getenv("FC_FACTOR_THREADS")) {
+    int t = atoi(env);
+    if (t >= 64 && t <= 1024 && t % 32 == 0) threads = t;
+  }
+  kern<<<(unsigned)nb, threads, sm, s>>>(g, st, mask, omega, coef, fac, fpiv, rpad, x, d_err, work);
   note_launches(1);
   return cudaGetLastError();
 }
