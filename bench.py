@@ -343,6 +343,33 @@ def run_sweeps(args):
     return 0
 
 
+def run_serve(args):
+    """Serving stream: Poisson arrivals (mean 50/s) of 3D porous solves on
+    grids {16,32,48,64,96}^3 with 5-200 spheres, admitted by HBM footprint
+    into a budget; mixed precision (FP32 rows, shared class blocks, FP64
+    FGMRES to 1e-8) on several slots, against the plain FP64 GPU solver
+    (FP64 rows, one block per patch) serving the same stream on one slot."""
+    from paper_2403_11636_gb300 import build, inputs
+    from paper_2403_11636_gb300.serve import Request, Server, latency_stats
+    build.build()
+    stream = inputs.serving_stream(0, count=args.requests, rate=args.rate)
+    reqs = [Request(k, p, t) for k, (t, p) in enumerate(stream)]
+    mixed = Server.gpu(budget_bytes=args.budget_gb * 1e9, slots=args.slots, prec="fp32", dedup=1).run(reqs)
+    plain = Server.gpu(budget_bytes=args.budget_gb * 1e9, slots=1, prec="fp64", dedup=0).run(reqs)
+    sm, sp = latency_stats(mixed), latency_stats(plain)
+    emit({"mode": "serve", "metric": "GMG solves/s", "value": sm["solves_per_s"], "unit": "solves/s",
+          "higher_is_better": True, "data": "synthetic",
+          "config": {"workload": f"{args.requests} requests, Poisson arrivals {args.rate}/s, porous3d "
+                                 "n in {16,32,48,64,96}, 5-200 spheres, FGMRES rtol 1e-8",
+                     "budget_gb": args.budget_gb, "slots": args.slots},
+          "mixed": {**sm, "iterations_mean": statistics.mean(r.iterations for r in mixed),
+                    "max_relres": max(r.relres for r in mixed)},
+          "plain_fp64_gpu": {**sp, "iterations_mean": statistics.mean(r.iterations for r in plain),
+                             "max_relres": max(r.relres for r in plain)},
+          "speedup_solves_per_s": sm["solves_per_s"] / sp["solves_per_s"]})
+    return 0
+
+
 def policy_sweeps(prob, stream, args):
     """One finest-level smoother sweep (residual + patch solve) per cache
     policy / precision, CUDA events on the solver stream."""
@@ -415,7 +442,11 @@ def main():
                     help="1: patches with bit-identical blocks share one stored block (same results)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve"])
+    ap.add_argument("--requests", type=int, default=24, help="requests of --mode serve")
+    ap.add_argument("--rate", type=float, default=50.0, help="arrivals per second of --mode serve")
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--n", type=int, default=48, help="grid size of --mode sweep")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -425,6 +456,8 @@ def main():
         return run_reference(args, rank, world)
     if args.mode == "sweep":
         return run_sweeps(args)
+    if args.mode == "serve":
+        return run_serve(args)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -45,9 +45,16 @@ template <typename T>
 cudaError_t dalloc(fc_handle h, T** p, size_t count, int part) {
   size_t bytes = count * sizeof(T);
   if (bytes == 0) bytes = sizeof(T);
-  cudaError_t e = cudaMalloc((void**)p, bytes);
+  // stream-ordered allocation: setup and teardown of one handle do not
+  // synchronise the device, so handles on other streams keep running
+  cudaError_t e = cudaMallocAsync((void**)p, bytes, h->stream);
   if (e == cudaSuccess && part >= 0) h->bytes[part] += bytes;
   return e;
+}
+
+// stream-ordered free of a possibly null pointer
+void dfree(fc_handle h, void* p) {
+  if (p) cudaFreeAsync(p, h->stream);
 }
 
 long long small_len(int m) { return (long long)(m + 1) * m + m + m + (m + 1) + m + kSmallScalars; }
@@ -567,18 +574,18 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
         CK(cudaMemcpy(&pr, L.prow + reph[c], sizeof(int), cudaMemcpyDeviceToHost));
         L.cls_blk[c - 1] = pr < 0 ? -pr - 1 : -1;
       }
-      cudaFree(nclass);
-      cudaFree(pclass);
-      cudaFree(rep);
+      dfree(h, nclass);
+      dfree(h, pclass);
+      dfree(h, rep);
     }
     CK(cudaStreamSynchronize(h->stream));
-    cudaFree(eA);
-    cudaFree(eB);
-    cudaFree(eF);
-    cudaFree(rA);
-    cudaFree(rB);
-    cudaFree(rF);
-    cudaFree(cclass);
+    dfree(h, eA);
+    dfree(h, eB);
+    dfree(h, eF);
+    dfree(h, rA);
+    dfree(h, rB);
+    dfree(h, rF);
+    dfree(h, cclass);
     fc_status st = check_err(h);
     if (st != FC_OK) return st;
     // ---- patch cache (every level above the coarsest)
@@ -612,11 +619,11 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
         } else {
           size_t eb = coef_elem_bytes(o->prec);
           void* cv = nullptr;
-          CK(cudaMalloc(&cv, n * eb));
+          CK(cudaMallocAsync(&cv, n * eb, h->stream));
           h->bytes[1] += n * eb;
           CK(launch_convert_rows(G, o->prec, c64, cv, L.nwork, h->stream));
           CK(cudaStreamSynchronize(h->stream));
-          cudaFree(c64);
+          dfree(h, c64);
           L.coef = cv;
           L.coef_bytes = n * eb;
         }
@@ -629,13 +636,13 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
                               h->d_err, work, L.nwork, h->stream));
       }
       CK(cudaStreamSynchronize(h->stream));
-      cudaFree(work);
-      cudaFree(dnw);
+      dfree(h, work);
+      dfree(h, dnw);
       st = check_err(h);
       if (st != FC_OK) return st;
     }
   }
-  cudaFree(d_count);
+  dfree(h, d_count);
   // ---- coarse solve
   {
     Level& C = h->lev[0];
@@ -651,9 +658,9 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     CK(dalloc(h, &h->coarse_inv, (size_t)n * n, 3));
     CK(launch_coarse_factor(C.g, C.st, C.mask, work, h->coarse_inv, piv, dsc, h->d_err, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    cudaFree(work);
-    cudaFree(dsc);
-    cudaFree(piv);
+    dfree(h, work);
+    dfree(h, dsc);
+    dfree(h, piv);
     fc_status st = check_err(h);
     if (st != FC_OK) return st;
   }
@@ -958,14 +965,16 @@ fc_status fc_destroy(fc_handle h) {
   else cudaDeviceSynchronize();
   for (int l = 0; l < kMaxLevels; ++l) {
     Level& L = h->lev[l];
-    cudaFree(L.st); cudaFree(L.mask); cudaFree(L.wfix); cudaFree(L.coef); cudaFree(L.fac); cudaFree(L.fpiv);
-    cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); cudaFree(L.rpad); cudaFree(L.rpad32);
-    cudaFree(L.st2); cudaFree(L.xp2); cudaFree(L.bp2); cudaFree(L.prow);
+    dfree(h, L.st); dfree(h, L.mask); dfree(h, L.wfix); dfree(h, L.coef); dfree(h, L.fac); dfree(h, L.fpiv);
+    dfree(h, L.x); dfree(h, L.b); dfree(h, L.r); dfree(h, L.rpad); dfree(h, L.rpad32);
+    dfree(h, L.st2); dfree(h, L.xp2); dfree(h, L.bp2); dfree(h, L.prow);
   }
   if (h->coarse_graph) cudaGraphExecDestroy(h->coarse_graph);
-  cudaFree(h->d_shapes); cudaFree(h->d_err); cudaFree(h->coarse_inv);
-  cudaFree(h->V); cudaFree(h->Z); cudaFree(h->w); cudaFree(h->red); cudaFree(h->small);
-  cudaFree(h->bh); cudaFree(h->xh);
+  dfree(h, h->d_shapes); dfree(h, h->d_err); dfree(h, h->coarse_inv);
+  dfree(h, h->V); dfree(h, h->Z); dfree(h, h->w); dfree(h, h->red); dfree(h, h->small);
+  dfree(h, h->bh); dfree(h, h->xh);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
   if (h->host_small) cudaFreeHost(h->host_small);
   for (auto& r : h->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : h->prof.pool) cudaEventDestroy(e);

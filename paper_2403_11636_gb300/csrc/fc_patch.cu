@@ -41,7 +41,6 @@ struct PatchDims {
   static constexpr int SP = 2 * DIM + 2;
   static constexpr int NSLOT = NU * DIM + NP;
   static constexpr int NCOL = DIM * NP + 1 + DIM;  // B columns, e_centre, residual columns
-  static constexpr int THREADS = DIM == 3 ? 256 : 128;
   // factor record (doubles): K LU (column-major), W (col-major), S LU, du, dp
   static constexpr int REC = NU * NU + DIM * NP * NU + NP * NP + NU + NP;
   static constexpr int RECI = NU + NP;

@@ -230,3 +230,28 @@ def roofline_2d(n: int = 4096, nlevels: int = 9) -> Problem:
 def random_vector(problem: Problem, seed: int, level: int | None = None) -> np.ndarray:
     """Uniform(-1, 1) vector of the level's DoF count."""
     return uniform_array(problem.ndof(level), seed)
+
+
+def serving_stream(seed: int = 0, count: int = 2000, rate: float = 50.0,
+                   sizes=(16, 32, 48, 64, 96), min_spheres: int = 5, max_spheres: int = 200):
+    """Poisson arrivals (exponential gaps, mean 1/rate) of 3D porous-medium
+    solves: grid n from ``sizes``, sphere count uniform in [min, max] with the
+    radius law of ``radius_scale``.  Returns a list of (arrival_s, Problem).
+    Draw order per request: gap, size, count, then the geometry seed."""
+    rng = SplitMix64(0x5E4E0000 + seed)
+    t = 0.0
+    out = []
+    for k in range(count):
+        t += -math.log(1.0 - rng.uniform()) / rate
+        n = sizes[rng.randint(0, len(sizes) - 1)]
+        ns = rng.randint(min_spheres, max_spheres)
+        gseed = rng.next_u64() & 0xFFFFFFFF
+        nlev = 1
+        m = n
+        while m % 2 == 0 and m // 2 >= 4:
+            m //= 2
+            nlev += 1
+        p = porous_3d(gseed, n=n, nspheres=ns, nlevels=nlev)
+        p.name = f"serve{k}_n{n}_k{ns}"
+        out.append((t, p))
+    return out

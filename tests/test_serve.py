@@ -1,0 +1,101 @@
+"""Scheduling logic of the continuous-batching server (CPU, fake solver) and,
+on the GPU, that every result is the same alone and in the mix."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2403_11636_gb300 import inputs
+from paper_2403_11636_gb300.serve import Request, Server, latency_stats
+
+
+class FakeProblem:
+    def __init__(self, fp, dur):
+        self.fp, self.dur = fp, dur
+
+
+def make_fake(log):
+    lock = threading.Lock()
+    active = {"mem": 0, "n": 0, "max_mem": 0, "max_n": 0}
+
+    def solve(p, stream):
+        with lock:
+            active["mem"] += p.fp
+            active["n"] += 1
+            active["max_mem"] = max(active["max_mem"], active["mem"])
+            active["max_n"] = max(active["max_n"], active["n"])
+        time.sleep(p.dur)
+        with lock:
+            active["mem"] -= p.fp
+            active["n"] -= 1
+        log.append(p)
+        return 3, 1e-9, 0.0, p.dur, None
+
+    return solve, active
+
+
+def test_admission_respects_budget_and_slots():
+    log = []
+    solve, active = make_fake(log)
+    reqs = [Request(k, FakeProblem(fp=40 + 10 * (k % 3), dur=0.02), arrival=0.001 * k) for k in range(12)]
+    srv = Server(solve, lambda p: p.fp, budget_bytes=100, slots=3)
+    res = srv.run(reqs)
+    assert [r.rid for r in res] == list(range(12))
+    assert active["max_mem"] <= 100 and active["max_n"] <= 3
+    assert active["max_n"] >= 2          # work overlapped
+    assert all(r.admitted >= r.arrival - 1e-9 and r.finished >= r.admitted for r in res)
+
+
+def test_fifo_order_and_arrivals_wait():
+    log = []
+    solve, _ = make_fake(log)
+    reqs = [Request(0, FakeProblem(90, 0.05), 0.0), Request(1, FakeProblem(90, 0.01), 0.01),
+            Request(2, FakeProblem(5, 0.01), 0.02)]
+    res = Server(solve, lambda p: p.fp, budget_bytes=100, slots=4).run(reqs)
+    # request 2 fits next to request 0 but arrives after request 1, which
+    # does not fit: first come, first served keeps it waiting
+    assert res[2].admitted >= res[1].admitted
+    assert res[1].admitted >= res[0].finished - 1e-3
+
+
+def test_oversized_request_rejected():
+    solve, _ = make_fake([])
+    with pytest.raises(ValueError):
+        Server(solve, lambda p: p.fp, budget_bytes=10, slots=1).run([Request(0, FakeProblem(11, 0.0), 0.0)])
+
+
+def test_latency_stats():
+    from paper_2403_11636_gb300.serve import Result
+    rs = [Result(k, 0.0, 0.0, float(k + 1), 1, 0.0, 0.0, 0.0, 0) for k in range(100)]
+    st = latency_stats(rs)
+    assert st["p50_s"] in (50.0, 51.0) and st["p99_s"] >= 99.0 and abs(st["solves_per_s"] - 1.0) < 1e-12
+
+
+def test_serving_stream_recipe():
+    s1 = inputs.serving_stream(0, count=20)
+    s2 = inputs.serving_stream(0, count=20)
+    assert [t for t, _ in s1] == [t for t, _ in s2]
+    gaps = np.diff([0.0] + [t for t, _ in inputs.serving_stream(1, count=400)])
+    assert 0.015 < gaps.mean() < 0.025          # mean gap 1/50 s
+    for _, p in s1:
+        assert p.n[0] in (16, 32, 48, 64, 96) and 5 <= len(p.shapes) <= 200
+        assert p.n[0] % 2 ** (p.nlevels - 1) == 0
+
+
+@pytest.mark.gpu
+def test_results_same_alone_and_in_the_mix():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2403_11636_gb300 import build
+    build.build()
+    probs = [inputs.porous_3d(k, n=16, nspheres=5 + 3 * k, nlevels=3) for k in range(4)]
+    probs.append(inputs.porous_3d(9, n=32, nspheres=20, nlevels=4))
+    alone = Server.gpu(budget_bytes=150e9, slots=1, keep_solutions=True).run(
+        [Request(k, p, 0.0) for k, p in enumerate(probs)])
+    mixed = Server.gpu(budget_bytes=150e9, slots=4, keep_solutions=True).run(
+        [Request(k, p, 0.0) for k, p in enumerate(probs)])
+    for a, m in zip(alone, mixed):
+        assert a.iterations == m.iterations and m.relres <= 1e-8
+        np.testing.assert_array_equal(a.solution, m.solution)
