@@ -610,8 +610,11 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
         CK(dalloc(h, &c64, n, o->prec == FC_PREC_FP64 ? 1 : -1));
         {
           ProfScope ps(h, 3, 0.0);
-          CK(launch_patch_build(G, L.st, L.mask, 0, o->omega, c64, nullptr, nullptr, nullptr, nullptr,
-                                h->d_err, work, L.nwork, h->stream));
+          if (o->prec == FC_PREC_FP64)
+            CK(launch_patch_build(G, L.st, L.mask, 0, o->omega, c64, nullptr, nullptr, nullptr, nullptr,
+                                  h->d_err, work, L.nwork, h->stream));
+          else  // rows kept in reduced precision: float-pair factorisation
+            CK(launch_patch_rows_pair(G, L.st, L.mask, c64, h->d_err, work, L.nwork, h->stream));
         }
         if (o->prec == FC_PREC_FP64) {
           L.coef = c64;

@@ -185,6 +185,11 @@ cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsig
                                int mode, double omega, double* coef64, double* fac, int* fpiv,
                                const double* rpad, double* x, unsigned* d_err, const int* work,
                                long long nwork, cudaStream_t s);
+// owned rows of the work-list patches by a float-pair factorisation (for
+// rows stored in reduced precision); float64 output like mode 0
+cudaError_t launch_patch_rows_pair(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                   double* coef64, unsigned* d_err, const int* work, long long nwork,
+                                   cudaStream_t s);
 // prow (nullable = identity) maps a patch to its stored row / factor block
 cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
                                const unsigned char* mask, const double* rpad, const float* rpad32,

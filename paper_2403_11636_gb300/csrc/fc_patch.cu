@@ -1020,6 +1020,337 @@ cudaError_t run_df_persistent(const LevelGeom& g, const float2* coef, const unsi
   note_launches(1);
   return cudaGetLastError();
 }
+// ---------------------------------------------------------------------------
+// Float-pair patch factorisation (rows for the reduced-precision modes).
+// The same block elimination as patch_factor_kernel mode 0, with the gather
+// and the equilibration in float64 and every elimination step -- the LU of
+// K~, the multi-right-hand-side solves, the Schur complement S~ and its LU,
+// the owned rows -- in float-pair arithmetic on the float32 pipes (about 48
+// significant bits; the blocks are equilibrated, so the rows keep ~14
+// digits).  FP64 runs at about 1/70 of FP32 on this part.
+struct pr { float h, l; };
+__device__ __forceinline__ pr pr_norm(float s, float e) {
+  float h = s + e;
+  return {h, e - (h - s)};
+}
+__device__ __forceinline__ pr pr_add(pr a, pr b) {
+  float s = a.h + b.h;
+  float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  return pr_norm(s, e);
+}
+__device__ __forceinline__ pr pr_mul(pr a, pr b) {
+  float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return pr_norm(p, e);
+}
+// c - a b
+__device__ __forceinline__ pr pr_fms(pr c, pr a, pr b) {
+  pr m = pr_mul(a, b);
+  return pr_add(c, {-m.h, -m.l});
+}
+__device__ __forceinline__ pr pr_div(pr a, pr b) {
+  float q1 = a.h / b.h;
+  pr r = pr_fms(a, {q1, 0.0f}, b);
+  float q2 = r.h / b.h;
+  return pr_norm(q1, q2);
+}
+__device__ __forceinline__ pr pr_from(double v) {
+  float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double pr_to(pr a) { return (double)a.h + (double)a.l; }
+
+__device__ void cta_lu_pair(pr* A, int n, int* piv, int* s_flag) {
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < n; ++k) {
+    if (warp == 0) {
+      float best = -1.0f;
+      int bi = k;
+      for (int r = k + lane; r < n; r += 32) {
+        float v = fabsf(A[r * n + k].h);
+        if (v > best) { best = v; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_down_sync(0xffffffffu, best, o);
+        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (lane == 0) {
+        piv[k] = bi;
+        if (best == 0.0f) *s_flag = 1;
+      }
+    }
+    __syncthreads();
+    const int p = piv[k];
+    if (p != k)
+      for (int c = tid; c < n; c += nt) {
+        pr t = A[k * n + c];
+        A[k * n + c] = A[p * n + c];
+        A[p * n + c] = t;
+      }
+    __syncthreads();
+    const pr d = A[k * n + k];
+    for (int r = k + 1 + tid; r < n; r += nt)
+      A[r * n + k] = d.h != 0.0f ? pr_div(A[r * n + k], d) : pr{0.0f, 0.0f};
+    __syncthreads();
+    const int m = n - k - 1;
+    for (int t = tid; t < m * m; t += nt) {
+      const int r = k + 1 + t / m, c = k + 1 + t % m;
+      A[r * n + c] = pr_fms(A[r * n + c], A[r * n + k], A[k * n + c]);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void cta_solve_multi_pair(const pr* A, int n, const int* piv, pr* W, int ncol) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int col = tid; col < ncol; col += nt) {
+    pr* z = W + col * n;
+    for (int k = 0; k < n; ++k) {
+      int p = piv[k];
+      if (p != k) { pr t = z[k]; z[k] = z[p]; z[p] = t; }
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < n - 1; ++k) {
+    const int m = n - 1 - k;
+    for (int t = tid; t < m * ncol; t += nt) {
+      const int col = t / m, r = k + 1 + t % m;
+      W[col * n + r] = pr_fms(W[col * n + r], A[r * n + k], W[col * n + k]);
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const pr d = A[k * n + k];
+    for (int col = tid; col < ncol; col += nt) W[col * n + k] = pr_div(W[col * n + k], d);
+    __syncthreads();
+    for (int t = tid; t < k * ncol; t += nt) {
+      const int col = t / k, r = t % k;
+      W[col * n + r] = pr_fms(W[col * n + r], A[r * n + k], W[col * n + k]);
+    }
+    __syncthreads();
+  }
+}
+
+// one thread: z <- A^{-1} z with the pair LU
+__device__ void lu_solve_vec_pair(const pr* A, int n, const int* piv, pr* z) {
+  for (int k = 0; k < n; ++k) {
+    int p = piv[k];
+    if (p != k) { pr t = z[k]; z[k] = z[p]; z[p] = t; }
+  }
+  for (int r = 0; r < n; ++r) {
+    pr s = z[r];
+    for (int c = 0; c < r; ++c) s = pr_fms(s, A[r * n + c], z[c]);
+    z[r] = s;
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    pr s = z[r];
+    for (int c = r + 1; c < n; ++c) s = pr_fms(s, A[r * n + c], z[c]);
+    z[r] = pr_div(s, A[r * n + r]);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(1024)
+    patch_factor_pair_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
+                             double* __restrict__ coef, unsigned* __restrict__ d_err,
+                             const int* __restrict__ work) {
+  using P = PatchDims<DIM>;
+  constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP;
+  constexpr int NC = DIM * NP + 1;  // B columns and e_centre
+  constexpr int C0 = DIM == 3 ? 13 : 4;  // neighbour index of the zero offset
+  extern __shared__ double smem[];
+  pr* K = reinterpret_cast<pr*>(smem);   // NU x NU
+  pr* W = K + NU * NU;                   // NC x NU
+  pr* S = W + NC * NU;                   // NP x NP
+  pr* zp = S + NP * NP;                  // ND x NP
+  double* du = reinterpret_cast<double*>(zp + ND * NP);  // NU
+  double* dp = du + NU;                                 // NP
+  int* pivK = reinterpret_cast<int*>(dp + NP);
+  int* pivS = pivK + NU;
+  long long* nodeU = reinterpret_cast<long long*>(((uintptr_t)(pivS + NP) + 7) & ~(uintptr_t)7);
+  long long* nodeP = nodeU + NU;
+  unsigned char* au = reinterpret_cast<unsigned char*>(nodeP + NP);
+  unsigned char* ap = au + NU;
+  __shared__ int s_flag;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long widx = blockIdx.x;
+  const long long i = work ? work[widx] : widx;
+  const int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
+                     DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
+  if (tid == 0) s_flag = 0;
+  for (int v = tid; v < NU; v += nt) {
+    int o[3];
+    vel_off<DIM>(v, o);
+    int b0 = ia[0] + o[0], b1 = ia[1] + o[1], b2 = ia[2] + o[2];
+    bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && (DIM == 2 || (b2 >= 0 && b2 <= g.n[2]));
+    long long bn = in ? b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2) : -1;
+    nodeU[v] = bn;
+    au[v] = (unsigned char)(in && !(mask[bn] & 1));
+  }
+  for (int p = tid; p < NP; p += nt) {
+    int o[3];
+    prs_off<DIM>(p, o);
+    int b0 = ia[0] + o[0], b1 = ia[1] + o[1], b2 = ia[2] + o[2];
+    bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && (DIM == 2 || (b2 >= 0 && b2 <= g.n[2]));
+    nodeP[p] = in ? b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2) : -1;
+    ap[p] = (unsigned char)in;
+  }
+  __syncthreads();
+  // equilibration from the diagonal entries (float64)
+  for (int v = tid; v < NU; v += nt) {
+    double a = au[v] ? fabs(st[((long long)C0 * SP) * g.nnodes + nodeU[v]]) : 0.0;
+    du[v] = (au[v] && a > 0.0) ? 1.0 / sqrt(a) : 1.0;
+  }
+  for (int p = tid; p < NP; p += nt) {
+    double a = ap[p] ? fabs(st[((long long)C0 * SP + 1 + 2 * DIM) * g.nnodes + nodeP[p]]) : 0.0;
+    dp[p] = (ap[p] && a > 0.0) ? 1.0 / sqrt(a) : 1.0;
+  }
+  __syncthreads();
+  // gather, equilibrate (float64), store as pairs
+  const int v0 = DIM == 3 ? 62 : 12, p0 = DIM == 3 ? 13 : 4;
+  for (int e = tid; e < NU * NU; e += nt) {
+    int v = e / NU, w = e % NU;
+    double val = 0.0;
+    if (au[v] && au[w]) {
+      int ov[3], ow[3], d[3];
+      vel_off<DIM>(v, ov);
+      vel_off<DIM>(w, ow);
+      bool adj = true;
+      for (int k = 0; k < 3; ++k) { d[k] = ow[k] - ov[k]; if (d[k] < -1 || d[k] > 1) adj = false; }
+      if (adj) val = du[v] * st[((long long)nb_index<DIM>(d) * SP) * g.nnodes + nodeU[v]] * du[w];
+    } else if (v == w) {
+      val = 1.0;
+    }
+    K[e] = pr_from(val);
+  }
+  for (int e = tid; e < DIM * NP * NU; e += nt) {
+    int col = e / NU, v = e % NU, c = col / NP, p = col % NP;
+    double val = 0.0;
+    if (au[v] && ap[p]) {
+      int ov[3], op[3], d[3];
+      vel_off<DIM>(v, ov);
+      prs_off<DIM>(p, op);
+      bool adj = true;
+      for (int k = 0; k < 3; ++k) { d[k] = op[k] - ov[k]; if (d[k] < -1 || d[k] > 1) adj = false; }
+      if (adj) val = du[v] * st[((long long)nb_index<DIM>(d) * SP + 1 + c) * g.nnodes + nodeU[v]] * dp[p];
+    }
+    W[e] = pr_from(val);
+  }
+  for (int v = tid; v < NU; v += nt) W[(DIM * NP) * NU + v] = pr{v == v0 ? 1.0f : 0.0f, 0.0f};
+  for (int e = tid; e < NP * NP; e += nt) {
+    int p = e / NP, q = e % NP;
+    double val = 0.0;
+    if (ap[p] && ap[q]) {
+      int op[3], oq[3], d[3];
+      prs_off<DIM>(p, op);
+      prs_off<DIM>(q, oq);
+      bool adj = true;
+      for (int k = 0; k < 3; ++k) { d[k] = oq[k] - op[k]; if (d[k] < -1 || d[k] > 1) adj = false; }
+      if (adj) val = dp[p] * st[((long long)nb_index<DIM>(d) * SP + 1 + 2 * DIM) * g.nnodes + nodeP[p]] * dp[q];
+    } else if (p == q) {
+      val = 1.0;
+    }
+    S[e] = pr_from(val);
+  }
+  __syncthreads();
+  cta_lu_pair(K, NU, pivK, &s_flag);
+  cta_solve_multi_pair(K, NU, pivK, W, NC);
+  // S~ = C~ - sum_c B~_c^T W~_c, B~ re-read from the operator
+  for (int e = tid; e < NP * NP; e += nt) {
+    int p = e / NP, q = e % NP;
+    pr s = S[e];
+    if (ap[p]) {
+      int op[3];
+      prs_off<DIM>(p, op);
+      for (int t = 0; t < (DIM == 3 ? 27 : 9); ++t) {
+        int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+        int ov[3] = {op[0] + d[0], op[1] + d[1], op[2] + d[2]};
+        int v = (ov[0] + 2) + 5 * (ov[1] + 2) + (DIM == 3 ? 25 * (ov[2] + 2) : 0);
+        if (!au[v]) continue;
+        int dvp[3] = {-d[0], -d[1], -d[2]};
+        long long base = (long long)nb_index<DIM>(dvp) * SP;
+        for (int c = 0; c < DIM; ++c) {
+          pr bt = pr_from(du[v] * st[(base + 1 + c) * g.nnodes + nodeU[v]] * dp[p]);
+          s = pr_fms(s, bt, W[(c * NP + q) * NU + v]);
+        }
+      }
+    }
+    S[e] = s;
+  }
+  __syncthreads();
+  cta_lu_pair(S, NP, pivS, &s_flag);
+  if (s_flag && tid == 0) atomicOr(d_err, kErrSingularPatch);
+  // owned rows: velocity c -> z_p = -S~^{-1} (row v0 of W~_c); pressure -> S~^{-1} e_p0
+  if (tid < ND) {
+    pr* z = zp + tid * NP;
+    for (int q = 0; q < NP; ++q) {
+      pr w = W[(tid * NP + q) * NU + v0];
+      z[q] = tid < DIM ? pr{-w.h, -w.l} : pr{q == p0 ? 1.0f : 0.0f, 0.0f};
+    }
+    lu_solve_vec_pair(S, NP, pivS, z);
+  }
+  __syncthreads();
+  double* out = coef + widx * P::NSLOT * ND;
+  for (int j = tid; j < P::NSLOT; j += nt) {
+    double vals[ND];
+    if (j < NU * DIM) {
+      int v = j / DIM, c2 = j % DIM;
+      for (int k = 0; k < ND; ++k) {
+        double z = 0.0;
+        if (au[v]) {
+          pr s = (k == c2) ? W[(DIM * NP) * NU + v] : pr{0.0f, 0.0f};
+          for (int q = 0; q < NP; ++q) s = pr_fms(s, W[(c2 * NP + q) * NU + v], zp[k * NP + q]);
+          z = pr_to(s);
+        }
+        bool own_ok = k < DIM ? au[v0] != 0 : true;
+        double dk = k < DIM ? du[v0] : dp[p0];
+        vals[k] = (own_ok && au[v]) ? dk * z * du[v] : 0.0;
+      }
+    } else {
+      int p = j - NU * DIM;
+      for (int k = 0; k < ND; ++k) {
+        bool own_ok = k < DIM ? au[v0] != 0 : true;
+        double dk = k < DIM ? du[v0] : dp[p0];
+        vals[k] = (own_ok && ap[p]) ? dk * pr_to(zp[k * NP + p]) * dp[p] : 0.0;
+      }
+    }
+    for (int k = 0; k < ND; ++k) out[(long long)j * ND + k] = vals[k];
+  }
+}
+
+template <int DIM>
+size_t pair_factor_smem() {
+  using P = PatchDims<DIM>;
+  const int NC = DIM * P::NP + 1;
+  size_t b = (size_t)(P::NU * P::NU + NC * P::NU + P::NP * P::NP + P::ND * P::NP) * 8 +
+             (P::NU + P::NP) * 8 + (P::NU + P::NP) * 4 + 8 + (P::NU + P::NP) * 8 + (P::NU + P::NP) + 16;
+  return (b + 15) & ~(size_t)15;
+}
+
+template <int DIM>
+cudaError_t run_pair_factor(const LevelGeom& g, const double* st, const unsigned char* mask, double* coef,
+                            unsigned* d_err, const int* work, long long nwork, cudaStream_t s) {
+  size_t sm = pair_factor_smem<DIM>();
+  auto kern = patch_factor_pair_kernel<DIM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long nb = work ? nwork : g.nnodes;
+  if (nb <= 0) return cudaSuccess;
+  int threads = DIM == 3 ? 1024 : 128;
+  if (const char* env = getenv("FC_FACTOR_THREADS")) {
+    int t = atoi(env);
+    if (t >= 64 && t <= 1024 && t % 32 == 0) threads = t;
+  }
+  kern<<<(unsigned)nb, threads, sm, s>>>(g, st, mask, coef, d_err, work);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 size_t factor_doubles(int dim) { return dim == 3 ? PatchDims<3>::REC : PatchDims<2>::REC; }
@@ -1037,6 +1368,13 @@ cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsig
   if (mode == 0) return run_factor<3, 0>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, work, nwork, s);
   if (mode == 1) return run_factor<3, 1>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, work, nwork, s);
   return run_factor<3, 2>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, nullptr, 0, s);
+}
+
+cudaError_t launch_patch_rows_pair(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                   double* coef64, unsigned* d_err, const int* work, long long nwork,
+                                   cudaStream_t s) {
+  if (g.dim == 2) return run_pair_factor<2>(g, st, mask, coef64, d_err, work, nwork, s);
+  return run_pair_factor<3>(g, st, mask, coef64, d_err, work, nwork, s);
 }
 
 cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
