@@ -225,6 +225,66 @@ fc_status fc_profile_read(fc_handle h, int kind, long long* launches, double* to
  * for launch accounting around timed regions. */
 fc_status fc_launch_count(long long* count);
 
+/* ---- Batches: many independent problems in one set of launches --------
+ *
+ * A batch groups handles made by fc_setup (same dimension; cache_inverse
+ * with FC_PREC_FP64, FP32 or BF16 rows; equal nu_pre, nu_post and
+ * fgmres_restart) and runs their smoother sweeps, V-cycles and FGMRES
+ * solves together: each phase of the paper's V-cycle (Sec. 3: RA sweeps of
+ * Sec. 3.1, transfers of eq. restriction_op, coarse direct solve) is one
+ * persistent launch over the patches of every problem, with levels aligned
+ * at the coarsest grid, and each Arnoldi step of the solve is one CUDA
+ * graph.  The batch references the handles' device data: they must
+ * outlive it and must not be used by other calls while a batch call runs.
+ *
+ * Vectors of a batch are PACKED: one device array of float64 holding every
+ * problem's finest-level vector (node-interleaved as above) back to back,
+ * problem p at [offsets[p], offsets[p+1]).  All calls are asynchronous on
+ * the stream given to fc_batch_create unless they say they synchronise.
+ * A problem's result does not depend on the other problems in the batch. */
+typedef struct fc_batch_s* fc_batch;
+
+/* Build a batch of nprob handles on cuda_stream (NULL = legacy default
+ * stream).  Times every patch-apply tile candidate (lanes per patch
+ * {4,8,16,32} x threads per CTA {128,256,512} x CTAs per SM {2,4,8,16},
+ * at most 2048 threads per SM) on the batch's finest levels and keeps the
+ * fastest.  Synchronises.  Errors: FC_ERR_INVALID (mixed dimensions,
+ * policies, precisions or sweep counts; DF64 rows), FC_ERR_CUDA. On error
+ * *out is still set and must be passed to fc_batch_destroy. */
+fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream);
+
+/* offsets[0..nprob] (host) of the packed finest-level vectors. */
+fc_status fc_batch_offsets(fc_batch b, long long* offsets);
+
+/* Tile picked by the autotuner, or set by fc_batch_set_tile (tests and
+ * sweeps): lanes per patch in {4,8,16,32}, threads per CTA in
+ * {128,256,512}, CTAs per SM in 1..64 (persistent grid size). */
+fc_status fc_batch_tile(fc_batch b, int* lanes_per_patch, int* threads, int* ctas_per_sm);
+fc_status fc_batch_set_tile(fc_batch b, int lanes_per_patch, int threads, int ctas_per_sm);
+
+/* nsweeps RA sweeps on every problem's finest level (packed x, b);
+ * problems with a single level (no smoothed level) are left unchanged. */
+fc_status fc_batch_smooth(fc_batch b, double* x_dev, const double* b_dev, int nsweeps);
+
+/* One V(nu_pre, nu_post) cycle on every problem (packed x updated in place). */
+fc_status fc_batch_vcycle(fc_batch b, double* x_dev, const double* b_dev);
+
+/* FGMRES(restart) with one V-cycle as right preconditioner, per problem,
+ * with each problem's own stopping test as in fc_solve; x_dev holds x0.
+ * iters[p], relres[p] (host arrays of nprob, may be NULL) as in fc_solve.
+ * Synchronises once per Arnoldi step.  Returns FC_ERR_NOT_CONVERGED if any
+ * problem stopped above rtol. */
+fc_status fc_batch_solve(fc_batch b, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters,
+                         double* relres);
+
+/* Problems, total packed DoFs, patches on the finest levels (of problems
+ * with more than one level), deepest hierarchy.  Any pointer may be NULL. */
+fc_status fc_batch_info(fc_batch b, int* nprob, long long* ndof_total, long long* npatch_finest,
+                        int* levels_max);
+fc_status fc_batch_sync(fc_batch b);
+const char* fc_batch_last_error(fc_batch b);
+fc_status fc_batch_destroy(fc_batch b);
+
 /* Wait for all work enqueued by the handle. */
 fc_status fc_sync(fc_handle h);
 

@@ -18,6 +18,7 @@ static thread_local bool g_capturing = false;
 void note_launches(int n) {
   if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }
+void set_capturing(bool on) { g_capturing = on; }
 }  // namespace fc
 
 namespace {

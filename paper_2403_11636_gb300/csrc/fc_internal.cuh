@@ -144,6 +144,8 @@ namespace fc {
 
 // process-wide count of libfc kernel launches (fc_api.cu)
 void note_launches(int n);
+// launches recorded while a stream capture is open are counted at replay
+void set_capturing(bool on);
 
 // ---- launchers (defined in the .cu files) ----
 // geometry + element data (fc_geom.cu)

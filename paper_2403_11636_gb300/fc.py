@@ -22,7 +22,9 @@ EXPORTS = ("fc_options_default", "fc_setup", "fc_rhs", "fc_residual", "fc_apply"
            "fc_smooth_noalloc", "fc_restrict", "fc_prolong_add", "fc_coarse_solve", "fc_vcycle", "fc_solve",
            "fc_gmg_solve", "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
            "fc_profile_enable", "fc_profile_read", "fc_launch_count", "fc_sync", "fc_last_error",
-           "fc_destroy")
+           "fc_destroy", "fc_batch_create", "fc_batch_offsets", "fc_batch_tile", "fc_batch_set_tile",
+           "fc_batch_smooth", "fc_batch_vcycle", "fc_batch_solve", "fc_batch_info", "fc_batch_sync",
+           "fc_batch_last_error", "fc_batch_destroy")
 
 
 class FcError(RuntimeError):
@@ -90,8 +92,20 @@ def load(path: str = LIB_PATH):
     lib.fc_last_error.restype = C.c_char_p
     lib.fc_last_error.argtypes = [vp]
     lib.fc_destroy.argtypes = [vp]
+    lib.fc_batch_create.argtypes = [P(vp), P(vp), i, vp]
+    lib.fc_batch_offsets.argtypes = [vp, P(ll)]
+    lib.fc_batch_tile.argtypes = [vp, P(i), P(i), P(i)]
+    lib.fc_batch_set_tile.argtypes = [vp, i, i, i]
+    lib.fc_batch_smooth.argtypes = [vp, vp, vp, i]
+    lib.fc_batch_vcycle.argtypes = [vp, vp, vp]
+    lib.fc_batch_solve.argtypes = [vp, vp, vp, d, i, P(i), P(d)]
+    lib.fc_batch_info.argtypes = [vp, P(i), P(ll), P(ll), P(i)]
+    lib.fc_batch_sync.argtypes = [vp]
+    lib.fc_batch_last_error.restype = C.c_char_p
+    lib.fc_batch_last_error.argtypes = [vp]
+    lib.fc_batch_destroy.argtypes = [vp]
     for name in EXPORTS:
-        if name != "fc_last_error" and name != "fc_footprint_estimate":
+        if name not in ("fc_last_error", "fc_footprint_estimate", "fc_batch_last_error"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -329,3 +343,93 @@ class Solver:
 
     def sync(self):
         self._check(self.lib.fc_sync(self.h))
+
+
+class Batch:
+    """Many Solver problems smoothed, cycled and solved together
+    (fc_batch_*).  Vectors are packed: every problem's finest-level vector
+    back to back, problem p at ``offsets[p]:offsets[p+1]``."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.solvers = list(solvers)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        hs = (C.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        self.b = C.c_void_p()
+        st = self.lib.fc_batch_create(C.byref(self.b), hs, len(self.solvers), C.c_void_p(self.stream.cuda_stream))
+        self._check(st)
+        off = (C.c_longlong * (len(self.solvers) + 1))()
+        self._check(self.lib.fc_batch_offsets(self.b, off))
+        self.offsets = [int(v) for v in off]
+
+    def _check(self, st):
+        if st != FC_OK:
+            msg = self.lib.fc_batch_last_error(self.b).decode() if self.b else ""
+            raise FcError(st, msg)
+
+    def close(self):
+        if getattr(self, "b", None) and self.b.value:
+            self.lib.fc_batch_destroy(self.b)
+            self.b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def ndof(self) -> int:
+        return self.offsets[-1]
+
+    def pack(self, vectors):
+        out = self.torch.empty(self.ndof, dtype=self.torch.float64, device="cuda")
+        for p, v in enumerate(vectors):
+            t = v if self.torch.is_tensor(v) else self.torch.as_tensor(np.asarray(v, dtype=np.float64))
+            out[self.offsets[p]:self.offsets[p + 1]] = t.to(device="cuda", dtype=self.torch.float64)
+        return out
+
+    def unpack(self, packed):
+        return [packed[self.offsets[p]:self.offsets[p + 1]] for p in range(len(self.solvers))]
+
+    def rhs(self):
+        return self.pack([s.rhs() for s in self.solvers])
+
+    def tile(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        self._check(self.lib.fc_batch_tile(self.b, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def set_tile(self, lanes_per_patch, threads, ctas_per_sm):
+        self._check(self.lib.fc_batch_set_tile(self.b, int(lanes_per_patch), int(threads), int(ctas_per_sm)))
+
+    def info(self):
+        n, nd, npch, lv = C.c_int(), C.c_longlong(), C.c_longlong(), C.c_int()
+        self._check(self.lib.fc_batch_info(self.b, C.byref(n), C.byref(nd), C.byref(npch), C.byref(lv)))
+        return {"nprob": n.value, "ndof": nd.value, "npatch_finest": npch.value, "levels_max": lv.value}
+
+    def smooth_(self, x, b, nsweeps=1):
+        self._check(self.lib.fc_batch_smooth(self.b, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()),
+                                             int(nsweeps)))
+        return x
+
+    def vcycle_(self, x, b):
+        self._check(self.lib.fc_batch_vcycle(self.b, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr())))
+        return x
+
+    def solve(self, b, x0=None, rtol=1e-8, maxit=200):
+        """Per-problem FGMRES + GMG; returns (packed x, iterations, relres)."""
+        x = self.torch.zeros(self.ndof, dtype=self.torch.float64, device="cuda") if x0 is None else x0.clone()
+        n = len(self.solvers)
+        its = (C.c_int * n)()
+        rel = (C.c_double * n)()
+        st = self.lib.fc_batch_solve(self.b, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr()), float(rtol),
+                                     int(maxit), its, rel)
+        if st not in (FC_OK, FC_ERR_NOT_CONVERGED):
+            self._check(st)
+        return x, list(its), list(rel)
+
+    def sync(self):
+        self._check(self.lib.fc_batch_sync(self.b))
