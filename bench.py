@@ -370,6 +370,174 @@ def run_serve(args):
     return 0
 
 
+def run_batch(args):
+    """Uneven batch: 256 independent 2D channel problems (grids 16..128^2,
+    1-8 ellipses, alpha 1e-6..1e-10) solved together by fc_batch_solve
+    (persistent launches over all problems, one CUDA graph per Arnoldi step,
+    autotuned patch tile), reduced-precision rows inside the FP64 FGMRES to
+    1e-8; against the plain FP64 GPU solver taking the same problems one at
+    a time."""
+    import torch
+    from paper_2403_11636_gb300 import build, fc, inputs
+    build.build()
+    probs = [inputs.batch_2d(s) for s in range(args.batch)]
+    rtol, maxit = 1e-8, 400
+    t0 = time.perf_counter()
+    solvers = [fc.Solver(p, prec=args.batch_prec, dedup=1) for p in probs]
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    B = fc.Batch(solvers)
+    create_ms = 1e3 * (time.perf_counter() - t0)
+    stream = torch.cuda.current_stream()
+    b = B.rhs()
+    for _ in range(args.warmup):
+        B.solve(b, rtol=rtol, maxit=maxit)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    l0 = fc.launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    its_all, rr_all = [], []
+    for k in range(args.steps):
+        _, its, rr = B.solve(b, rtol=rtol, maxit=maxit)
+        its_all.append(its)
+        rr_all.append(max(rr))
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = fc.launch_count() - l0
+    cl = clocks.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    updates = sum(updates_per_solve(p, i) for its in its_all for p, i in zip(probs, its))
+    # the dominant kernel: the batched patch apply over every finest level
+    X = torch.zeros_like(b)
+    B.smooth_(X, b, nsweeps=3)
+    B.profile(True)
+    B.smooth_(X, b, nsweeps=20)
+    na, ma, ba = B.profile_read(0)
+    nr, mr, _ = B.profile_read(1)
+    B.profile(False)
+    hbm, peak_kind = peaks()
+    achieved = ba / (ma / na * 1e-3) / 1e9
+    # end to end from pinned host buffers
+    bh = torch.empty(B.ndof, dtype=torch.float64, pin_memory=True)
+    bh.copy_(b.cpu())
+    xh = torch.zeros(B.ndof, dtype=torch.float64, pin_memory=True)
+    B.solve_host(bh, xh, rtol=rtol, maxit=maxit)
+    e2e_t, e2e_up = [], 0
+    for _ in range(args.steps):
+        xh.zero_()
+        t1 = time.perf_counter()
+        its_h, _ = B.solve_host(bh, xh, rtol=rtol, maxit=maxit)
+        e2e_t.append(time.perf_counter() - t1)
+        e2e_up += sum(updates_per_solve(p, i) for p, i in zip(probs, its_h))
+    tile = B.tile()
+    info = B.info()
+    B.close()
+    for s_ in solvers:
+        s_.close()
+    # the plain FP64 GPU solver, one problem at a time, same problems
+    plain = [fc.Solver(p, prec="fp64", dedup=0) for p in probs]
+    rhs = [s_.rhs() for s_ in plain]
+    for s_, r in zip(plain[:8], rhs[:8]):
+        s_.solve(r, rtol=rtol, maxit=maxit)
+    torch.cuda.synchronize()
+    lat = []
+    its_plain = []
+    tp0 = time.perf_counter()
+    for s_, r in zip(plain, rhs):
+        t1 = time.perf_counter()
+        _, i1, _ = s_.solve(r, rtol=rtol, maxit=maxit)
+        lat.append(time.perf_counter() - t1)
+        its_plain.append(i1)
+    plain_s = time.perf_counter() - tp0
+    for s_ in plain:
+        s_.close()
+    lat.sort()
+    step_sorted = sorted(step_ms)
+    solves_per_s = len(probs) * args.steps / (total_ms * 1e-3)
+    out = {
+        "mode": "batch", "metric": METRIC, "value": updates / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.batch_prec], "data": "synthetic",
+        "config": {"workload": f"{len(probs)} independent 2D channel problems, grids drawn from "
+                               "{16,32,64,128}^2, 1-8 seeded ellipses (semi-axes U[0.03,0.2]), alpha in "
+                               "{1e-6,1e-8,1e-10}, levels down to 4^2 cells, V(2,2), FGMRES(30) rtol 1e-8 "
+                               "per problem; a step solves all of them",
+                   "problems": len(probs), "ndof_total": info["ndof"], "patches_finest": info["npatch_finest"],
+                   "levels_max": info["levels_max"], "patch_rows": args.batch_prec,
+                   "tile": {"lanes_per_patch": tile[0], "threads": tile[1], "ctas_per_sm": tile[2]},
+                   "l2": "rows of all finest levels exceed L2 (about 1 GB in FP32)",
+                   "iterations_min_max": [min(its_all[0]), max(its_all[0])], "relres_max": max(rr_all),
+                   "setup_ms": setup_ms, "batch_create_ms": create_ms,
+                   "solves_per_s": solves_per_s,
+                   "latency_ms_p50": statistics.median(step_sorted),
+                   "latency_ms_p99": step_sorted[min(len(step_sorted) - 1,
+                                                     int(math.ceil(0.99 * len(step_sorted))) - 1)],
+                   "plain_fp64_gpu": {"solves_per_s": len(probs) / plain_s,
+                                      "latency_ms_p50": 1e3 * statistics.median(lat),
+                                      "latency_ms_p99": 1e3 * lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                                      "iterations_min_max": [min(its_plain), max(its_plain)],
+                                      "note": "same problems solved one after another, FP64 rows"},
+                   "speedup_solves_per_s_vs_plain_fp64": solves_per_s / (len(probs) / plain_s),
+                   "smoother": {"apply_launches": na, "apply_ms": ma / na, "residual_ms": mr / max(nr, 1)}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "batched patch apply over all finest levels",
+                     "launches": na, "avg_launch_ms": ma / na, "algorithmic_bytes_per_launch": ba,
+                     "peak_source": peak_kind},
+        "e2e": {"value": e2e_up / sum(e2e_t), "unit": UNIT, "h2d_bytes_per_step": 2 * B.ndof * 8,
+                "d2h_bytes_per_step": B.ndof * 8},
+        "gpu_launches": launches,
+        "clocks": cl,
+    }
+    if not args.no_cpu_baseline:
+        sample = [p for p in probs if p.n[0] <= 32][:4]
+        tot_u, tot_t, cores = 0.0, 0.0, 1
+        for p in sample:
+            ups, times, cores, _ = oracle_solve_rate(p, budget_s=args.cpu_budget / max(len(sample), 1))
+            tot_u += sum(ups)
+            tot_t += sum(times)
+        out["cpu_baseline"] = {"value": tot_u / tot_t, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"oracle FGMRES-GMG solves of {len(sample)} problems of the batch "
+                                         "with grids <= 32^2, setup excluded"}
+    emit(out)
+    return 0
+
+
+def run_batch_sweeps(args):
+    """Finest-level smoother sweeps of the uneven 2D batch only (bounded
+    profiler captures): --warmup + --steps batched sweeps, optionally with a
+    fixed patch-apply tile (--tile lanes,threads,ctas_per_sm)."""
+    import torch
+    from paper_2403_11636_gb300 import build, fc, inputs
+    build.build()
+    probs = [inputs.batch_2d(s) for s in range(args.batch)]
+    solvers = [fc.Solver(p, prec=args.batch_prec, dedup=args.dedup) for p in probs]
+    B = fc.Batch(solvers)
+    if args.tile:
+        B.set_tile(*[int(v) for v in args.tile.split(",")])
+    b = B.rhs()
+    X = torch.zeros_like(b)
+    B.smooth_(X, b, nsweeps=args.warmup)
+    B.profile(True)
+    B.smooth_(X, b, nsweeps=args.steps)
+    na, ma, ba = B.profile_read(0)
+    nr, mr, _ = B.profile_read(1)
+    hbm, _ = peaks()
+    info = B.info()
+    emit({"mode": "batch-sweep", "problems": len(probs), "patches_finest": info["npatch_finest"],
+          "prec": args.batch_prec, "dedup": args.dedup, "tile": B.tile(),
+          "apply_ms": ma / max(na, 1), "apply_bytes": ba,
+          "apply_gbs": ba / (ma / na * 1e-3) / 1e9 if na else None,
+          "residual_ms": mr / max(nr, 1),
+          "updates_per_s": info["npatch_finest"] * 3 / ((ma / max(na, 1) + mr / max(nr, 1)) * 1e-3)})
+    B.close()
+    return 0
+
+
 def policy_sweeps(prob, stream, args):
     """One finest-level smoother sweep (residual + patch solve) per cache
     policy / precision, CUDA events on the solver stream."""
@@ -442,7 +610,10 @@ def main():
                     help="1: patches with bit-identical blocks share one stored block (same results)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep"])
+    ap.add_argument("--tile", default="", help="lanes,threads,ctas_per_sm of --mode batch-sweep")
+    ap.add_argument("--batch", type=int, default=256, help="problems of --mode batch")
+    ap.add_argument("--batch-prec", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--requests", type=int, default=24, help="requests of --mode serve")
     ap.add_argument("--rate", type=float, default=50.0, help="arrivals per second of --mode serve")
     ap.add_argument("--slots", type=int, default=8)
@@ -458,6 +629,10 @@ def main():
         return run_sweeps(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "batch-sweep":
+        return run_batch_sweeps(args)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -277,10 +277,24 @@ fc_status fc_batch_vcycle(fc_batch b, double* x_dev, const double* b_dev);
 fc_status fc_batch_solve(fc_batch b, const double* b_dev, double* x_dev, double rtol, int maxit, int* iters,
                          double* relres);
 
+/* As fc_batch_solve with packed HOST buffers (pinned memory recommended):
+ * b and x0 are copied in on the caller's stream, x is copied back.
+ * Synchronises. */
+fc_status fc_batch_solve_host(fc_batch b, const double* b_host, double* x_host, double rtol, int maxit,
+                              int* iters, double* relres);
+
 /* Problems, total packed DoFs, patches on the finest levels (of problems
  * with more than one level), deepest hierarchy.  Any pointer may be NULL. */
 fc_status fc_batch_info(fc_batch b, int* nprob, long long* ndof_total, long long* npatch_finest,
                         int* levels_max);
+/* Per-launch device time of the finest-level smoothing in fc_batch_smooth
+ * while enabled (CUDA events on the batch stream): kind 0 patch apply,
+ * 1 residual; bytes_per_launch = algorithmic bytes of one apply (stored
+ * rows once, residual gathered once, x read and written).  Reading
+ * synchronises and resets that kind. */
+fc_status fc_batch_profile_enable(fc_batch b, int on);
+fc_status fc_batch_profile_read(fc_batch b, int kind, long long* launches, double* total_ms,
+                                double* bytes_per_launch);
 fc_status fc_batch_sync(fc_batch b);
 const char* fc_batch_last_error(fc_batch b);
 fc_status fc_batch_destroy(fc_batch b);

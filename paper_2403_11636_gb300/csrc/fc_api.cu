@@ -225,6 +225,11 @@ fc_status smoother_residual(fc_handle h, int li, const double* x, const double* 
 
 bool pair_path(fc_handle h) { return h->opt.cache == FC_CACHE_INVERSE && h->opt.prec == FC_PREC_DF64; }
 
+// float32 / bfloat16 rows: V-cycles in the float32 correction form
+bool f32_path(fc_handle h) {
+  return h->opt.cache == FC_CACHE_INVERSE && (h->opt.prec == FC_PREC_FP32 || h->opt.prec == FC_PREC_BF16);
+}
+
 // Float-pair smoothing: x and (unless already current) b are split into
 // pairs once, then every sweep is a pair residual and a pair apply that
 // keeps the pair copy of x current.
@@ -410,6 +415,8 @@ size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o) {
     }
     total += (size_t)nodes * nb * (2 * dim + 2) * 8 + nodes + (size_t)nodes * nd * 8;  // st, mask, wfix
     total += (size_t)nodes * nd * 8 * 3 + (size_t)pad * nd * 8 + (size_t)pad * nd * 8;   // vectors
+    if (o->cache == FC_CACHE_INVERSE && (o->prec == FC_PREC_FP32 || o->prec == FC_PREC_BF16))
+      total += (size_t)(l > 0 ? nodes * nb * (2 * dim + 2) * 4 : 0) + (size_t)pad * nd * 4 + (size_t)nodes * nd * 4;
     if (l > 0) {
       if (o->cache == FC_CACHE_INVERSE)
         total += (size_t)nodes * nslot(dim) * nd * coef_elem_bytes(o->prec);
@@ -543,6 +550,17 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     if (need_r32(o->prec)) {
       CK(dalloc(h, &L.rpad32, (size_t)padn * nd * 2, 2));
       CK(cudaMemsetAsync(L.rpad32, 0, sizeof(float) * padn * nd * 2, h->stream));
+    }
+    if (o->cache == FC_CACHE_INVERSE && (o->prec == FC_PREC_FP32 || o->prec == FC_PREC_BF16)) {
+      // float32 correction-form V-cycle: folded float32 stencil, padded
+      // correction (zero halo) and float32 right-hand side
+      if (li > 0) {
+        CK(dalloc(h, &L.st32, (size_t)G.nnodes * nb * spn(dim), 0));
+        CK(launch_fold_stencil_f32(G, L.st, L.mask, L.st32, h->stream));
+      }
+      CK(dalloc(h, &L.d32, (size_t)padn * nd, 2));
+      CK(cudaMemsetAsync(L.d32, 0, sizeof(float) * padn * nd, h->stream));
+      CK(dalloc(h, &L.b32, (size_t)G.ndof, 2));
     }
     if (li == depth - 1) {
       // finest right-hand side kept in L.b until fc_rhs; L.b is not used as a
@@ -742,6 +760,7 @@ fc_status fc_coarse_solve(fc_handle h, const double* b, double* x) {
 fc_status fc_vcycle(fc_handle h, double* x, const double* b) {
   if (!h || !x || !b) return FC_ERR_INVALID;
   ProfScope ps(h, 2, 0.0);
+  if (f32_path(h)) return handle_vcycle_f32(h, x, b, false);
   return vcycle_level(h, h->nlev - 1, x, b);
 }
 
@@ -789,7 +808,7 @@ fc_status fc_solve(fc_handle h, const double* b, double* x, double rtol, int max
       CK(cudaMemsetAsync(Zj, 0, sizeof(double) * n, s));
       {
         ProfScope ps(h, 2, 0.0);
-        st = vcycle_level(h, h->nlev - 1, Zj, Vj);
+        st = f32_path(h) ? handle_vcycle_f32(h, Zj, Vj, true) : vcycle_level(h, h->nlev - 1, Zj, Vj);
         if (st != FC_OK) return st;
       }
       its++;
@@ -844,7 +863,7 @@ fc_status fc_gmg_solve(fc_handle h, const double* b, double* x, double reduction
   while (it < maxit && rn > reduction * r0) {
     {
       ProfScope ps(h, 2, 0.0);
-      st = vcycle_level(h, h->nlev - 1, x, b);
+      st = f32_path(h) ? handle_vcycle_f32(h, x, b, false) : vcycle_level(h, h->nlev - 1, x, b);
       if (st != FC_OK) return st;
     }
     CK(launch_residual(F.g, F.st, F.mask, x, b, h->w, nullptr, s));
@@ -967,11 +986,13 @@ fc_status fc_destroy(fc_handle h) {
   if (!h) return FC_ERR_INVALID;
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  handle_batch_free(h);
   for (int l = 0; l < kMaxLevels; ++l) {
     Level& L = h->lev[l];
     dfree(h, L.st); dfree(h, L.mask); dfree(h, L.wfix); dfree(h, L.coef); dfree(h, L.fac); dfree(h, L.fpiv);
     dfree(h, L.x); dfree(h, L.b); dfree(h, L.r); dfree(h, L.rpad); dfree(h, L.rpad32);
     dfree(h, L.st2); dfree(h, L.xp2); dfree(h, L.bp2); dfree(h, L.prow);
+    dfree(h, L.st32); dfree(h, L.d32); dfree(h, L.b32);
   }
   if (h->coarse_graph) cudaGraphExecDestroy(h->coarse_graph);
   dfree(h, h->d_shapes); dfree(h, h->d_err); dfree(h, h->coarse_inv);

@@ -63,6 +63,12 @@ struct BSeg {
   float* rpadf;        // padded float32 residual (float32 / bfloat16 rows)
   const double* cinv;  // coarse inverse (level 0)
   int cn;
+  // float32 correction form (float32 / bfloat16 rows): folded float32
+  // stencil, padded correction d and right-hand side b32 of the level
+  const float* st32;
+  float* d32;
+  float* b32;
+  float omega_f;
 };
 
 struct Chunk {
@@ -93,11 +99,54 @@ __device__ __forceinline__ long long padded(const BGeom& g, int dim, const int* 
 // OUT 0: r (unpadded float64), 1: rpad (padded float64), 2: rpadf (padded
 // float32).  use_b = 0 gives L x instead of b - L x.  With a state array
 // only problems whose state equals `gate` are processed.
+// v = b - L x (or L x when b is null) at one node, float64
+template <int DIM>
+__device__ __forceinline__ void residual64(const BSeg* S, const BGeom& g, long long node, const int* ia,
+                                           const double* b, double* v) {
+  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
+  const double* __restrict__ st = S->st;
+  const unsigned char* __restrict__ mask = S->mask;
+  const double* x = S->x;
+  double acc[ND];
+#pragma unroll
+  for (int q = 0; q < ND; ++q) acc[q] = 0.0;
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb) {
+    const int ib0 = ia[0] + nb % 3 - 1, ib1 = ia[1] + (nb / 3) % 3 - 1, ib2 = DIM == 3 ? ia[2] + nb / 9 - 1 : 0;
+    if (ib0 < 0 || ib0 > g.n[0] || ib1 < 0 || ib1 > g.n[1]) continue;
+    if (DIM == 3 && (ib2 < 0 || ib2 > g.n[2])) continue;
+    const long long bn = ib0 + (long long)g.nn[0] * (ib1 + (long long)g.nn[1] * ib2);
+    const unsigned char mb = mask[bn];
+    double xb[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) xb[q] = x[bn * ND + q];
+#pragma unroll
+    for (int q = 0; q < DIM; ++q)
+      if ((mb >> q) & 1) xb[q] = 0.0;
+    const double* s = st + (long long)nb * SP * g.nnodes + node;
+    const double vA = s[0];
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) {
+      acc[q] = acc[q] + vA * xb[q];
+      acc[q] = acc[q] + s[(1 + q) * g.nnodes] * xb[DIM];
+    }
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) acc[DIM] = acc[DIM] + s[(1 + DIM + q) * g.nnodes] * xb[q];
+    acc[DIM] = acc[DIM] + s[(1 + 2 * DIM) * g.nnodes] * xb[DIM];
+  }
+  const unsigned char ma = mask[node];
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    const double y = (q < DIM && ((ma >> q) & 1)) ? x[node * ND + q] : acc[q];
+    v[q] = b ? b[node * ND + q] - y : y;
+  }
+}
+
 template <int DIM, int OUT>
 __global__ void __launch_bounds__(256)
     b_residual_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch, int use_b,
                       const int* __restrict__ state, int gate) {
-  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
+  constexpr int ND = DIM + 1;
   for (int c = blockIdx.x; c < nch; c += gridDim.x) {
     const Chunk k = ch[c];
     const BSeg* S = segs + k.seg;
@@ -105,48 +154,16 @@ __global__ void __launch_bounds__(256)
     const BGeom g = S->g;
     const long long node = (long long)k.node0 + threadIdx.x;
     if (node >= g.nnodes) continue;
-    const double* __restrict__ st = S->st;
-    const unsigned char* __restrict__ mask = S->mask;
-    const double* x = S->x;
-    const double* b = use_b ? S->b : nullptr;
     int ia[3];
     decode(g, DIM, (unsigned)node, ia);
-    double acc[ND];
-#pragma unroll
-    for (int q = 0; q < ND; ++q) acc[q] = 0.0;
-#pragma unroll
-    for (int nb = 0; nb < NB; ++nb) {
-      const int ib0 = ia[0] + nb % 3 - 1, ib1 = ia[1] + (nb / 3) % 3 - 1, ib2 = DIM == 3 ? ia[2] + nb / 9 - 1 : 0;
-      if (ib0 < 0 || ib0 > g.n[0] || ib1 < 0 || ib1 > g.n[1]) continue;
-      if (DIM == 3 && (ib2 < 0 || ib2 > g.n[2])) continue;
-      const long long bn = ib0 + (long long)g.nn[0] * (ib1 + (long long)g.nn[1] * ib2);
-      const unsigned char mb = mask[bn];
-      double xb[ND];
-#pragma unroll
-      for (int q = 0; q < ND; ++q) xb[q] = x[bn * ND + q];
-#pragma unroll
-      for (int q = 0; q < DIM; ++q)
-        if ((mb >> q) & 1) xb[q] = 0.0;
-      const double* s = st + (long long)nb * SP * g.nnodes + node;
-      const double vA = s[0];
-#pragma unroll
-      for (int q = 0; q < DIM; ++q) {
-        acc[q] = acc[q] + vA * xb[q];
-        acc[q] = acc[q] + s[(1 + q) * g.nnodes] * xb[DIM];
-      }
-#pragma unroll
-      for (int q = 0; q < DIM; ++q) acc[DIM] = acc[DIM] + s[(1 + DIM + q) * g.nnodes] * xb[q];
-      acc[DIM] = acc[DIM] + s[(1 + 2 * DIM) * g.nnodes] * xb[DIM];
-    }
-    const unsigned char ma = mask[node];
+    double v[ND];
+    residual64<DIM>(S, g, node, ia, use_b ? S->b : nullptr, v);
     const long long pn = padded(g, DIM, ia);
 #pragma unroll
     for (int q = 0; q < ND; ++q) {
-      const double y = (q < DIM && ((ma >> q) & 1)) ? x[node * ND + q] : acc[q];
-      const double v = b ? b[node * ND + q] - y : y;
-      if (OUT == 0) S->r[node * ND + q] = v;
-      else if (OUT == 1) S->rpad[pn * ND + q] = v;
-      else S->rpadf[pn * ND + q] = (float)v;
+      if (OUT == 0) S->r[node * ND + q] = v[q];
+      else if (OUT == 1) S->rpad[pn * ND + q] = v[q];
+      else S->rpadf[pn * ND + q] = (float)v[q];
     }
   }
 }
@@ -432,6 +449,304 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Float32 correction form (float32 / bfloat16 rows).  A V-cycle or a
+// smoothing phase on (x, b) runs on the correction d with d = 0 at the start
+// and right-hand side b32 = b - L x (float64 residual, skipped when x is
+// known to be zero), entirely in float32: residual r = b32 - L32 d with the
+// float32 stencil (constrained neighbour columns folded to zero), patch
+// solves d += omega L_i^{-1} r on the owned DoFs, transfers and prolongation
+// on d; the coarse solve reads b32 and sums in float64.  At the end x += d
+// in float64.  In exact arithmetic this is the same iteration as on x.
+
+// b32 = b - L x (float64) or b, d = 0, on the finest levels
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    f_enter_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch, int xzero,
+                   const int* __restrict__ state, int gate) {
+  constexpr int ND = DIM + 1;
+  for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const Chunk k = ch[c];
+    const BSeg* S = segs + k.seg;
+    if (state && state[S->prob] != gate) continue;
+    const BGeom g = S->g;
+    const long long node = (long long)k.node0 + threadIdx.x;
+    if (node >= g.nnodes) continue;
+    int ia[3];
+    decode(g, DIM, (unsigned)node, ia);
+    double v[ND];
+    if (xzero) {
+#pragma unroll
+      for (int q = 0; q < ND; ++q) v[q] = S->b[node * ND + q];
+    } else {
+      residual64<DIM>(S, g, node, ia, S->b, v);
+    }
+    const long long pn = padded(g, DIM, ia);
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      S->b32[node * ND + q] = (float)v[q];
+      S->d32[pn * ND + q] = 0.0f;
+    }
+  }
+}
+
+// x = x + d (or x = d when x was zero), float64, on the finest levels
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    f_exit_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch, int xzero,
+                  const int* __restrict__ state, int gate) {
+  constexpr int ND = DIM + 1;
+  for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const Chunk k = ch[c];
+    const BSeg* S = segs + k.seg;
+    if (state && state[S->prob] != gate) continue;
+    const BGeom g = S->g;
+    const long long node = (long long)k.node0 + threadIdx.x;
+    if (node >= g.nnodes) continue;
+    int ia[3];
+    decode(g, DIM, (unsigned)node, ia);
+    const long long pn = padded(g, DIM, ia);
+    double* x = S->x;
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      const double dv = (double)S->d32[pn * ND + q];
+      x[node * ND + q] = xzero ? dv : x[node * ND + q] + dv;
+    }
+  }
+}
+
+// r = b32 - L32 d into the padded float32 residual
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    f_residual_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch,
+                      const int* __restrict__ state, int gate) {
+  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
+  for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const Chunk k = ch[c];
+    const BSeg* S = segs + k.seg;
+    if (state && state[S->prob] != gate) continue;
+    const BGeom g = S->g;
+    const long long node = (long long)k.node0 + threadIdx.x;
+    if (node >= g.nnodes) continue;
+    int ia[3];
+    decode(g, DIM, (unsigned)node, ia);
+    const int px = g.nn[0] + 4, py = g.nn[1] + 4;
+    const long long pn = padded(g, DIM, ia);
+    const float* __restrict__ d = S->d32;
+    const float* __restrict__ st = S->st32;
+    float acc[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) acc[q] = 0.0f;
+#pragma unroll
+    for (int nb = 0; nb < NB; ++nb) {
+      const int off = (nb % 3 - 1) + px * (((nb / 3) % 3 - 1) + (DIM == 3 ? py * (nb / 9 - 1) : 0));
+      const float* db = d + (pn + off) * ND;
+      const float* sp = st + (long long)nb * SP * g.nnodes + node;
+      float dv[ND];
+#pragma unroll
+      for (int q = 0; q < ND; ++q) dv[q] = db[q];
+      const float vA = __ldcs(sp);
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) {
+        acc[q] = fmaf(vA, dv[q], acc[q]);
+        acc[q] = fmaf(__ldcs(sp + (1 + q) * g.nnodes), dv[DIM], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) acc[DIM] = fmaf(__ldcs(sp + (1 + DIM + q) * g.nnodes), dv[q], acc[DIM]);
+      acc[DIM] = fmaf(__ldcs(sp + (1 + 2 * DIM) * g.nnodes), dv[DIM], acc[DIM]);
+    }
+    const unsigned char ma = S->mask[node];
+    const float* dc = d + pn * ND;
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      const float y = (q < DIM && ((ma >> q) & 1)) ? dc[q] : acc[q];
+      S->rpadf[pn * ND + q] = S->b32[node * ND + q] - y;
+    }
+  }
+}
+
+// d += omega L_i^{-1} r on the owned DoFs (PT 1: float32 rows, 2: bfloat16)
+template <int DIM, int PT, int TPP>
+__global__ void __launch_bounds__(512)
+    f_apply_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch,
+                   const int* __restrict__ state, int gate) {
+  constexpr int ND = DIM + 1, NSLOT = DIM == 3 ? 402 : 59;
+  using RL = RowLoad<PT, ND>;
+  using T = typename RL::T;
+  __shared__ int soff[NSLOT];
+  int cur_px = -1, cur_py = -1;
+  const int lane = threadIdx.x % TPP, grp = threadIdx.x / TPP, ngrp = blockDim.x / TPP;
+  for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const Chunk k = ch[c];
+    const BSeg* S = segs + k.seg;
+    if (state && state[S->prob] != gate) continue;  // uniform over the CTA
+    const BGeom g = S->g;
+    const int px = g.nn[0] + 4, py = g.nn[1] + 4;
+    if (px != cur_px || py != cur_py) {
+      __syncthreads();
+      for (int j = threadIdx.x; j < NSLOT; j += blockDim.x) soff[j] = slot_offset<DIM>(j, px, py);
+      __syncthreads();
+      cur_px = px;
+      cur_py = py;
+    }
+    const T* __restrict__ coef = static_cast<const T*>(S->coef);
+    const int* __restrict__ prow = S->prow;
+    const unsigned char* __restrict__ mask = S->mask;
+    const float* __restrict__ rpad = S->rpadf;
+    float* d = S->d32;
+    const float omega = S->omega_f;
+    for (int q = grp; q < kChunk; q += ngrp) {
+      const long long node = (long long)k.node0 + q;
+      const bool valid = node < g.nnodes;
+      const unsigned i = (unsigned)(valid ? node : g.nnodes - 1);
+      int ia[3];
+      decode(g, DIM, i, ia);
+      const long long pb = padded(g, DIM, ia) * ND;
+      const float* rp = rpad + pb;
+      const int pr = prow ? prow[i] : (int)i;
+      const bool shared_rows = pr < 0;
+      const T* cf = coef + (size_t)(shared_rows ? -pr - 1 : pr) * NSLOT * ND;
+      float y[ND];
+#pragma unroll
+      for (int t = 0; t < ND; ++t) y[t] = 0.0f;
+#pragma unroll 4
+      for (int j = lane; j < NSLOT; j += TPP) {
+        const float rv = rp[soff[j]];
+        float cv[ND];
+        RL::load(cf + (size_t)j * ND, shared_rows, cv);
+#pragma unroll
+        for (int t = 0; t < ND; ++t) y[t] = fmaf(cv[t], rv, y[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < ND; ++t)
+#pragma unroll
+        for (int o = TPP / 2; o > 0; o >>= 1) y[t] += __shfl_xor_sync(0xffffffffu, y[t], o);
+      if (valid && lane < ND) {
+        float yl = y[0];
+#pragma unroll
+        for (int t = 1; t < ND; ++t)
+          if (lane == t) yl = y[t];
+        const bool fixed = lane < DIM && ((mask[i] >> lane) & 1);
+        d[pb + lane] += fixed ? rp[lane] : omega * yl;
+      }
+    }
+  }
+}
+
+// coarse b32 = R r (fine padded residual), coarse d = 0
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    f_restrict_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch,
+                      const int* __restrict__ state, int gate) {
+  constexpr int ND = DIM + 1;
+  for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const Chunk k = ch[c];
+    const BSeg* C = segs + k.seg;
+    const BSeg* F = C + 1;
+    if (state && state[C->prob] != gate) continue;
+    const BGeom cg_ = C->g, fg = F->g;
+    const long long node = (long long)k.node0 + threadIdx.x;
+    if (node >= cg_.nnodes) continue;
+    int I[3];
+    decode(cg_, DIM, (unsigned)node, I);
+    const float* rf = F->rpadf;
+    float acc[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) acc[q] = 0.0f;
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int fi[3] = {2 * I[0] + dx, 2 * I[1] + dy, DIM == 3 ? 2 * I[2] + dz : 0};
+          if (fi[0] < 0 || fi[0] > fg.n[0] || fi[1] < 0 || fi[1] > fg.n[1]) continue;
+          if (DIM == 3 && (fi[2] < 0 || fi[2] > fg.n[2])) continue;
+          const float w = (dx == 0 ? 1.0f : 0.5f) * (dy == 0 ? 1.0f : 0.5f) * (dz == 0 ? 1.0f : 0.5f);
+          const long long fp = padded(fg, DIM, fi);
+#pragma unroll
+          for (int q = 0; q < ND; ++q) acc[q] = fmaf(w, rf[fp * ND + q], acc[q]);
+        }
+    const unsigned char m = C->mask[node];
+    const long long pc = padded(cg_, DIM, I);
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      C->b32[node * ND + q] = (q < DIM && ((m >> q) & 1)) ? 0.0f : acc[q];
+      C->d32[pc * ND + q] = 0.0f;
+    }
+  }
+}
+
+// fine d += P (coarse d)
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    f_prolong_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch,
+                     const int* __restrict__ state, int gate) {
+  constexpr int ND = DIM + 1;
+  for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const Chunk k = ch[c];
+    const BSeg* F = segs + k.seg;
+    const BSeg* C = F - 1;
+    if (state && state[F->prob] != gate) continue;
+    const BGeom fg = F->g, cg_ = C->g;
+    const long long node = (long long)k.node0 + threadIdx.x;
+    if (node >= fg.nnodes) continue;
+    int ia[3];
+    decode(fg, DIM, (unsigned)node, ia);
+    int lo[3], hi[3];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      lo[t] = ia[t] / 2;
+      hi[t] = (ia[t] + 1) / 2;
+    }
+    const float* ec = C->d32;
+    float acc[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) acc[q] = 0.0f;
+    for (int t = 0; t < (1 << DIM); ++t) {
+      int ic[3] = {0, 0, 0};
+      float w = 1.0f;
+      bool dup = false;
+      for (int dd = 0; dd < DIM; ++dd) {
+        const int bit = (t >> dd) & 1;
+        if (lo[dd] == hi[dd] && bit) dup = true;
+        ic[dd] = bit ? hi[dd] : lo[dd];
+        w = w * (lo[dd] == hi[dd] ? 1.0f : 0.5f);
+      }
+      if (dup) continue;
+      const long long cp = padded(cg_, DIM, ic);
+#pragma unroll
+      for (int q = 0; q < ND; ++q) acc[q] = fmaf(w, ec[cp * ND + q], acc[q]);
+    }
+    const unsigned char m = F->mask[node];
+    float* df = F->d32 + padded(fg, DIM, ia) * ND;
+#pragma unroll
+    for (int q = 0; q < ND; ++q)
+      if (!(q < DIM && ((m >> q) & 1))) df[q] += acc[q];
+  }
+}
+
+// coarse d = A^{-1} b32 (float64 inverse and sums), one CTA per problem
+template <int DIM>
+__global__ void __launch_bounds__(256)
+    f_coarse_kernel(const BSeg* __restrict__ segs, const int* __restrict__ cseg, const int* __restrict__ state,
+                    int gate) {
+  constexpr int ND = DIM + 1;
+  const BSeg* S = segs + cseg[blockIdx.x];
+  if (state && state[S->prob] != gate) return;
+  const BGeom g = S->g;
+  const int n = S->cn, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* A = S->cinv;
+  const float* b = S->b32;
+  for (int row = warp; row < n; row += nw) {
+    double s = 0.0;
+    for (int c = lane; c < n; c += 32) s += A[(long long)row * n + c] * (double)b[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      int ia[3];
+      decode(g, DIM, (unsigned)(row / ND), ia);
+      S->d32[padded(g, DIM, ia) * ND + row % ND] = (float)s;
+    }
+  }
+}
+
 // finest-level vectors of every problem: x = xb + j*xstep + off[p] (j from
 // the device counter dj when given), likewise b; r = rb + off[p]
 __global__ void b_point_kernel(BSeg* segs, const int* __restrict__ fin, const long long* __restrict__ off,
@@ -689,7 +1004,19 @@ ApplyFn apply_fn(int tpp) {
   }
 }
 
+template <int DIM, int PT>
+ApplyFn fapply_fn(int tpp) {
+  switch (tpp) {
+    case 4: return f_apply_kernel<DIM, PT, 4>;
+    case 8: return f_apply_kernel<DIM, PT, 8>;
+    case 16: return f_apply_kernel<DIM, PT, 16>;
+    default: return f_apply_kernel<DIM, PT, 32>;
+  }
+}
+
 ApplyFn pick_apply(int dim, fc_prec prec, int tpp) {
+  if (prec == FC_PREC_FP32) return dim == 2 ? fapply_fn<2, 1>(tpp) : fapply_fn<3, 1>(tpp);
+  if (prec == FC_PREC_BF16) return dim == 2 ? fapply_fn<2, 2>(tpp) : fapply_fn<3, 2>(tpp);
   const int pt = prec == FC_PREC_FP64 ? 0 : prec == FC_PREC_FP32 ? 1 : 2;
   if (dim == 2) return pt == 0 ? apply_fn<2, 0>(tpp) : pt == 1 ? apply_fn<2, 1>(tpp) : apply_fn<2, 2>(tpp);
   return pt == 0 ? apply_fn<3, 0>(tpp) : pt == 1 ? apply_fn<3, 1>(tpp) : apply_fn<3, 2>(tpp);
@@ -701,6 +1028,7 @@ ApplyFn pick_apply(int dim, fc_prec prec, int tpp) {
 struct fc_batch_s {
   int nprob = 0, dim = 0, maxl = 0, m = 30, nu_pre = 0, nu_post = 0;
   fc_prec prec = FC_PREC_FP32;
+  bool f32 = false;  // float32 correction form (float32 / bfloat16 rows)
   cudaStream_t user = nullptr, s = nullptr;
   cudaEvent_t ev = nullptr;
   std::vector<fc_handle> hs;
@@ -730,8 +1058,17 @@ struct fc_batch_s {
   int* dj = nullptr;
   int* count = nullptr;
   int* hcount = nullptr;  // pinned
+  // per-launch timing of the finest-level smoothing (fc_batch_smooth):
+  // kind 0 patch apply, 1 residual
+  bool prof_on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof[2];
+  double apply_bytes = 0.0;  // algorithmic bytes of one finest-level apply
+  double* bh = nullptr;  // device staging of fc_batch_solve_host
+  double* xh = nullptr;
   cudaGraphExec_t step_graph = nullptr;
   int step_kernels = 0;
+  cudaGraphExec_t vgraph[2] = {nullptr, nullptr};  // float32 V-cycle (handle path)
+  int vgraph_kernels = 0;
   double graph_rtol = -1.0;  // the captured step bakes these in
   int graph_maxit = -1;
   std::string err;
@@ -785,10 +1122,39 @@ fc_status apply(fc_batch B, const Plan& p, const Tile& t, const int* state, int 
   return FC_OK;
 }
 
+// float32 correction-form phases: 0 enter (xzero), 1 exit (xzero),
+// 2 residual, 3 restrict, 4 prolong
+fc_status fphase(fc_batch B, int kind, const Plan& p, int xzero, const int* state, int gate) {
+  if (p.count == 0) return FC_OK;
+  const unsigned grid = grid_of(B, p, 8);
+  const Chunk* c = B->chunks + p.first;
+  const int n = p.count;
+  if (B->dim == 2) {
+    switch (kind) {
+      case 0: f_enter_kernel<2><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, xzero, state, gate); break;
+      case 1: f_exit_kernel<2><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, xzero, state, gate); break;
+      case 2: f_residual_kernel<2><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, state, gate); break;
+      case 3: f_restrict_kernel<2><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, state, gate); break;
+      default: f_prolong_kernel<2><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, state, gate); break;
+    }
+  } else {
+    switch (kind) {
+      case 0: f_enter_kernel<3><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, xzero, state, gate); break;
+      case 1: f_exit_kernel<3><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, xzero, state, gate); break;
+      case 2: f_residual_kernel<3><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, state, gate); break;
+      case 3: f_restrict_kernel<3><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, state, gate); break;
+      default: f_prolong_kernel<3><<<grid, kChunk, 0, B->s>>>(B->segs, c, n, state, gate); break;
+    }
+  }
+  note_launches(1);
+  BK(cudaGetLastError());
+  return FC_OK;
+}
+
 fc_status sweeps(fc_batch B, const Plan& p, int n, const int* state, int gate) {
   const int out = B->prec == FC_PREC_FP64 ? 1 : 2;
   for (int s = 0; s < n; ++s) {
-    fc_status st = residual(B, p, out, 1, state, gate);
+    fc_status st = B->f32 ? fphase(B, 2, p, 0, state, gate) : residual(B, p, out, 1, state, gate);
     if (st == FC_OK) st = apply(B, p, B->tile, state, gate);
     if (st != FC_OK) return st;
   }
@@ -809,6 +1175,27 @@ fc_status transfer(fc_batch B, int kind, const Plan& p, const int* state, int ga
   note_launches(1);
   BK(cudaGetLastError());
   return FC_OK;
+}
+
+// V(nu_pre, nu_post) in the float32 correction form (x known zero: xzero)
+fc_status vcycle_f32(fc_batch B, int xzero, const int* state, int gate) {
+  fc_status st = fphase(B, 0, B->pfin, xzero, state, gate);
+  for (int li = B->maxl - 1; li >= 1 && st == FC_OK; --li) {
+    st = sweeps(B, B->pn[li], B->nu_pre, state, gate);
+    if (st == FC_OK) st = fphase(B, 2, B->pn[li], 0, state, gate);
+    if (st == FC_OK) st = fphase(B, 3, B->prc[li - 1], 0, state, gate);
+  }
+  if (st != FC_OK) return st;
+  if (B->dim == 2) f_coarse_kernel<2><<<B->nprob, 256, 0, B->s>>>(B->segs, B->cseg, state, gate);
+  else f_coarse_kernel<3><<<B->nprob, 256, 0, B->s>>>(B->segs, B->cseg, state, gate);
+  note_launches(1);
+  BK(cudaGetLastError());
+  for (int li = 1; li < B->maxl && st == FC_OK; ++li) {
+    st = fphase(B, 4, B->pn[li], 0, state, gate);
+    if (st == FC_OK) st = sweeps(B, B->pn[li], B->nu_post, state, gate);
+  }
+  if (st == FC_OK) st = fphase(B, 1, B->pfin, xzero, state, gate);
+  return st;
 }
 
 // V(nu_pre, nu_post) on every problem at once: levels aligned at the
@@ -895,12 +1282,24 @@ fc_status autotune(fc_batch B) {
   return FC_OK;
 }
 
+void prof_clear(fc_batch B, int kind) {
+  for (auto& pr : B->prof[kind]) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  B->prof[kind].clear();
+}
+
 void free_batch(fc_batch B) {
   if (!B) return;
   if (B->s) cudaStreamSynchronize(B->s);
+  prof_clear(B, 0);
+  prof_clear(B, 1);
   if (B->step_graph) cudaGraphExecDestroy(B->step_graph);
+  for (auto& g : B->vgraph)
+    if (g) cudaGraphExecDestroy(g);
   void* ptrs[] = {B->segs, B->fin, B->cseg, B->doff, B->chunks, B->V, B->Z, B->R, B->small, B->bn, B->rel,
-                  B->state, B->its, B->kk, B->dj, B->count};
+                  B->state, B->its, B->kk, B->dj, B->count, B->bh, B->xh};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (B->hcount) cudaFreeHost(B->hcount);
@@ -910,6 +1309,25 @@ void free_batch(fc_batch B) {
 
 // order the batch stream after the caller's stream (entry) and the
 // caller's stream after the batch stream (exit)
+fc_status krylov_alloc(fc_batch B) {
+  if (B->V) return FC_OK;
+  const size_t nt = (size_t)B->ntot;
+  const int nprob = B->nprob;
+  BK(cudaMalloc(&B->V, sizeof(double) * nt * (B->m + 1)));
+  BK(cudaMalloc(&B->Z, sizeof(double) * nt * B->m));
+  BK(cudaMalloc(&B->small, sizeof(double) * small_stride(B->m) * nprob));
+  BK(cudaMalloc(&B->bn, sizeof(double) * nprob));
+  BK(cudaMalloc(&B->rel, sizeof(double) * nprob));
+  BK(cudaMalloc(&B->state, sizeof(int) * nprob));
+  BK(cudaMalloc(&B->its, sizeof(int) * nprob));
+  BK(cudaMalloc(&B->kk, sizeof(int) * nprob));
+  BK(cudaMalloc(&B->dj, sizeof(int)));
+  BK(cudaMalloc(&B->count, sizeof(int)));
+  BK(cudaMallocHost(&B->hcount, sizeof(int)));
+  BK(cudaMemsetAsync(B->state, 0, sizeof(int) * nprob, B->s));
+  return FC_OK;
+}
+
 fc_status enter(fc_batch B) {
   BK(cudaEventRecord(B->ev, B->user));
   BK(cudaStreamWaitEvent(B->s, B->ev, 0));
@@ -927,8 +1345,12 @@ fc_status step_graph(fc_batch B, KrylovArgs& ka) {
   set_capturing(true);
   fc_status st = point(B, B->Z, B->ntot, B->V, B->ntot, B->R, B->dj);
   if (st == FC_OK && cudaMemsetAsync(B->count, 0, sizeof(int), B->s) != cudaSuccess) st = FC_ERR_CUDA;
-  if (st == FC_OK) st = zero_finest(B, B->state, 1);
-  if (st == FC_OK) st = vcycle_all(B, B->state, 1);
+  if (B->f32) {
+    if (st == FC_OK) st = vcycle_f32(B, 1, B->state, 1);
+  } else {
+    if (st == FC_OK) st = zero_finest(B, B->state, 1);
+    if (st == FC_OK) st = vcycle_all(B, B->state, 1);
+  }
   if (st == FC_OK) st = residual(B, B->pfin, 0, 0, B->state, 1);  // R = L z_j
   if (st == FC_OK) {
     k_arnoldi_kernel<<<B->nprob * kCL, kKThreads, 0, B->s>>>(ka);
@@ -963,6 +1385,65 @@ fc_status step_graph(fc_batch B, KrylovArgs& ka) {
 
 }  // namespace
 
+namespace fc {
+
+// V-cycle of one handle with float32 / bfloat16 rows in the float32
+// correction form, through a batch holding that handle alone (created on
+// first use; the tile tuned on the handle's finest level).  The V-cycle
+// after the pointer update is captured once per x-is-zero flag as a CUDA
+// graph.
+fc_status handle_vcycle_f32(fc_handle h, double* x, const double* b, bool xzero) {
+  if (!h->self_batch) {
+    fc_handle one = h;
+    fc_status st = fc_batch_create(&h->self_batch, &one, 1, h->stream);
+    if (st != FC_OK) {
+      h->err = std::string("float32 V-cycle: ") + fc_batch_last_error(h->self_batch);
+      fc_batch_destroy(h->self_batch);
+      h->self_batch = nullptr;
+      return st;
+    }
+  }
+  fc_batch B = h->self_batch;
+  fc_status st = enter(B);
+  if (st == FC_OK) st = point(B, x, 0, b, 0, B->R, nullptr);
+  cudaGraphExec_t& gx = B->vgraph[xzero ? 1 : 0];
+  if (st == FC_OK && !gx) {
+    cudaGraph_t graph = nullptr;
+    BK(cudaStreamBeginCapture(B->s, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
+    st = vcycle_f32(B, xzero ? 1 : 0, nullptr, 0);
+    cudaError_t e = cudaStreamEndCapture(B->s, &graph);
+    set_capturing(false);
+    if (e == cudaSuccess && st == FC_OK) {
+      size_t nn = 0;
+      cudaGraphGetNodes(graph, nullptr, &nn);
+      B->vgraph_kernels = (int)nn;
+      e = cudaGraphInstantiate(&gx, graph, 0);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      gx = nullptr;
+      st = bfail(B, FC_ERR_CUDA, std::string("V-cycle graph: ") + cudaGetErrorString(e));
+    }
+  }
+  if (st == FC_OK) {
+    BK(cudaGraphLaunch(gx, B->s));
+    note_launches(B->vgraph_kernels);
+  }
+  st = leave(B, st);
+  if (st != FC_OK) h->err = std::string("float32 V-cycle: ") + B->err;
+  return st;
+}
+
+void handle_batch_free(fc_handle h) {
+  if (h->self_batch) {
+    fc_batch_destroy(h->self_batch);
+    h->self_batch = nullptr;
+  }
+}
+
+}  // namespace fc
+
 extern "C" {
 
 fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream) {
@@ -978,6 +1459,7 @@ fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, vo
   B->nprob = nprob;
   B->dim = h0->dim;
   B->prec = h0->opt.prec;
+  B->f32 = B->prec == FC_PREC_FP32 || B->prec == FC_PREC_BF16;
   B->m = h0->restart;
   B->nu_pre = h0->opt.nu_pre;
   B->nu_post = h0->opt.nu_post;
@@ -1028,6 +1510,12 @@ fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, vo
       S.rpadf = L.rpad32;
       S.cinv = li == 0 ? h->coarse_inv : nullptr;
       S.cn = li == 0 ? h->coarse_n : 0;
+      S.st32 = L.st32;
+      S.d32 = L.d32;
+      S.b32 = L.b32;
+      S.omega_f = (float)h->opt.omega;
+      if (B->f32 && (!L.d32 || !L.b32 || (li > 0 && !L.st32)))
+        return bfail(B, FC_ERR_INVALID, "handle without float32 level vectors");
       if (li > 0 && !L.coef) return bfail(B, FC_ERR_INVALID, "handle without a patch cache");
       if (li > 0 && B->prec != FC_PREC_FP64 && !L.rpad32) return bfail(B, FC_ERR_INVALID, "handle without float residual");
       segs.push_back(S);
@@ -1062,11 +1550,19 @@ fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, vo
   // smoothed finest levels: problems with more than one level (the only
   // level of a one-level problem is the coarse solve's)
   B->psm.first = (int)chunks.size();
-  for (int p = 0; p < nprob; ++p)
-    if (B->hs[p]->nlev > 1) {
-      add_seg(fin[p]);
-      B->fin_patches += segs[fin[p]].g.nnodes;
-    }
+  {
+    const double cb = B->prec == FC_PREC_FP64 ? 8.0 : B->prec == FC_PREC_FP32 ? 4.0 : 2.0;
+    const double rb = B->prec == FC_PREC_FP64 ? 8.0 : 4.0;
+    for (int p = 0; p < nprob; ++p)
+      if (B->hs[p]->nlev > 1) {
+        add_seg(fin[p]);
+        const Level& L = B->hs[p]->lev[B->hs[p]->nlev - 1];
+        B->fin_patches += L.g.nnodes;
+        // stored rows streamed once, residual gathered once, x read and written
+        // (float32 correction form: d read and written in float32)
+        B->apply_bytes += (double)L.active_work * L.g.nd * cb + (double)L.g.nnodes * L.g.nd * (rb + (B->f32 ? 8.0 : 16.0));
+      }
+  }
   B->psm.count = (int)chunks.size() - B->psm.first;
 
   BK(cudaMalloc(&B->segs, sizeof(BSeg) * segs.size()));
@@ -1080,21 +1576,8 @@ fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, vo
   BK(cudaMemcpyAsync(B->doff, B->off.data(), sizeof(long long) * (nprob + 1), cudaMemcpyHostToDevice, B->s));
   if (!chunks.empty())
     BK(cudaMemcpyAsync(B->chunks, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice, B->s));
-  // Krylov workspace
-  const size_t nt = (size_t)B->ntot;
-  BK(cudaMalloc(&B->V, sizeof(double) * nt * (B->m + 1)));
-  BK(cudaMalloc(&B->Z, sizeof(double) * nt * B->m));
-  BK(cudaMalloc(&B->R, sizeof(double) * nt));
-  BK(cudaMalloc(&B->small, sizeof(double) * small_stride(B->m) * nprob));
-  BK(cudaMalloc(&B->bn, sizeof(double) * nprob));
-  BK(cudaMalloc(&B->rel, sizeof(double) * nprob));
-  BK(cudaMalloc(&B->state, sizeof(int) * nprob));
-  BK(cudaMalloc(&B->its, sizeof(int) * nprob));
-  BK(cudaMalloc(&B->kk, sizeof(int) * nprob));
-  BK(cudaMalloc(&B->dj, sizeof(int)));
-  BK(cudaMalloc(&B->count, sizeof(int)));
-  BK(cudaMallocHost(&B->hcount, sizeof(int)));
-  BK(cudaMemsetAsync(B->state, 0, sizeof(int) * nprob, B->s));
+  // packed work vector (the Krylov basis is allocated by the first solve)
+  BK(cudaMalloc(&B->R, sizeof(double) * (size_t)B->ntot));
   fc_status st = autotune(B);
   if (st != FC_OK) return st;
   BK(cudaStreamSynchronize(B->s));
@@ -1121,11 +1604,16 @@ fc_status fc_batch_set_tile(fc_batch B, int tpp, int threads, int ctas_per_sm) {
   if ((tpp != 4 && tpp != 8 && tpp != 16 && tpp != 32) || (threads != 128 && threads != 256 && threads != 512) ||
       ctas_per_sm < 1 || ctas_per_sm > 64)
     return bfail(B, FC_ERR_INVALID, "tile: tpp in {4,8,16,32}, threads in {128,256,512}, 1..64 CTAs per SM");
+  cudaStreamSynchronize(B->s);
   if (B->step_graph) {
-    cudaStreamSynchronize(B->s);
     cudaGraphExecDestroy(B->step_graph);
     B->step_graph = nullptr;
   }
+  for (auto& g : B->vgraph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
   B->tile = Tile{tpp, threads, ctas_per_sm};
   return FC_OK;
 }
@@ -1134,7 +1622,26 @@ fc_status fc_batch_smooth(fc_batch B, double* x, const double* b, int nsweeps) {
   if (!B || !x || !b || nsweeps < 0) return B ? bfail(B, FC_ERR_INVALID, "bad smoother arguments") : FC_ERR_INVALID;
   fc_status st = enter(B);
   if (st == FC_OK) st = point(B, x, 0, b, 0, B->R, nullptr);
-  if (st == FC_OK) st = sweeps(B, B->psm, nsweeps, nullptr, 0);
+  if (st == FC_OK && B->f32) st = fphase(B, 0, B->psm, 0, nullptr, 0);
+  if (!B->prof_on) {
+    if (st == FC_OK) st = sweeps(B, B->psm, nsweeps, nullptr, 0);
+  } else {
+    const int out = B->prec == FC_PREC_FP64 ? 1 : 2;
+    for (int k = 0; k < nsweeps && st == FC_OK; ++k)
+      for (int kind = 1; kind >= 0 && st == FC_OK; --kind) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+          st = bfail(B, FC_ERR_CUDA, "profile event");
+          break;
+        }
+        B->prof[kind].push_back({e0, e1});
+        cudaEventRecord(e0, B->s);
+        if (kind == 0) st = apply(B, B->psm, B->tile, nullptr, 0);
+        else st = B->f32 ? fphase(B, 2, B->psm, 0, nullptr, 0) : residual(B, B->psm, out, 1, nullptr, 0);
+        cudaEventRecord(e1, B->s);
+      }
+  }
+  if (st == FC_OK && B->f32) st = fphase(B, 1, B->psm, 0, nullptr, 0);
   return leave(B, st);
 }
 
@@ -1142,7 +1649,7 @@ fc_status fc_batch_vcycle(fc_batch B, double* x, const double* b) {
   if (!B || !x || !b) return B ? bfail(B, FC_ERR_INVALID, "bad V-cycle arguments") : FC_ERR_INVALID;
   fc_status st = enter(B);
   if (st == FC_OK) st = point(B, x, 0, b, 0, B->R, nullptr);
-  if (st == FC_OK) st = vcycle_all(B, nullptr, 0);
+  if (st == FC_OK) st = B->f32 ? vcycle_f32(B, 0, nullptr, 0) : vcycle_all(B, nullptr, 0);
   return leave(B, st);
 }
 
@@ -1150,7 +1657,8 @@ fc_status fc_batch_solve(fc_batch B, const double* b, double* x, double rtol, in
                          double* relres) {
   if (!B || !b || !x || !(rtol > 0.0) || maxit < 0)
     return B ? bfail(B, FC_ERR_INVALID, "bad solve arguments") : FC_ERR_INVALID;
-  fc_status st = enter(B);
+  fc_status st = krylov_alloc(B);
+  if (st == FC_OK) st = enter(B);
   if (st != FC_OK) return st;
   KrylovArgs ka{};
   ka.nprob = B->nprob;
@@ -1222,12 +1730,51 @@ fc_status fc_batch_solve(fc_batch B, const double* b, double* x, double rtol, in
   return leave(B, FC_OK);
 }
 
+fc_status fc_batch_solve_host(fc_batch B, const double* b_host, double* x_host, double rtol, int maxit,
+                              int* iters, double* relres) {
+  if (!B || !b_host || !x_host) return B ? bfail(B, FC_ERR_INVALID, "bad solve arguments") : FC_ERR_INVALID;
+  if (!B->bh) {
+    BK(cudaMalloc(&B->bh, sizeof(double) * B->ntot));
+    BK(cudaMalloc(&B->xh, sizeof(double) * B->ntot));
+  }
+  BK(cudaMemcpyAsync(B->bh, b_host, sizeof(double) * B->ntot, cudaMemcpyHostToDevice, B->user));
+  BK(cudaMemcpyAsync(B->xh, x_host, sizeof(double) * B->ntot, cudaMemcpyHostToDevice, B->user));
+  fc_status st = fc_batch_solve(B, B->bh, B->xh, rtol, maxit, iters, relres);
+  if (st != FC_OK && st != FC_ERR_NOT_CONVERGED) return st;
+  BK(cudaMemcpyAsync(x_host, B->xh, sizeof(double) * B->ntot, cudaMemcpyDeviceToHost, B->user));
+  BK(cudaStreamSynchronize(B->user));
+  return st;
+}
+
 fc_status fc_batch_info(fc_batch B, int* nprob, long long* ndof_total, long long* npatch_finest, int* levels_max) {
   if (!B) return FC_ERR_INVALID;
   if (nprob) *nprob = B->nprob;
   if (ndof_total) *ndof_total = B->ntot;
   if (npatch_finest) *npatch_finest = B->fin_patches;
   if (levels_max) *levels_max = B->maxl;
+  return FC_OK;
+}
+
+fc_status fc_batch_profile_enable(fc_batch B, int on) {
+  if (!B) return FC_ERR_INVALID;
+  B->prof_on = on != 0;
+  return FC_OK;
+}
+
+fc_status fc_batch_profile_read(fc_batch B, int kind, long long* launches, double* total_ms,
+                                double* bytes_per_launch) {
+  if (!B || kind < 0 || kind > 1) return B ? bfail(B, FC_ERR_INVALID, "profile kind is 0 or 1") : FC_ERR_INVALID;
+  BK(cudaStreamSynchronize(B->s));
+  double ms = 0.0;
+  for (auto& pr : B->prof[kind]) {
+    float t = 0.0f;
+    BK(cudaEventElapsedTime(&t, pr.first, pr.second));
+    ms += t;
+  }
+  if (launches) *launches = (long long)B->prof[kind].size();
+  if (total_ms) *total_ms = ms;
+  if (bytes_per_launch) *bytes_per_launch = kind == 0 ? B->apply_bytes : 0.0;
+  prof_clear(B, kind);
   return FC_OK;
 }
 

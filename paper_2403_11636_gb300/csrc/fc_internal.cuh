@@ -89,6 +89,13 @@ struct Level {
   float2* st2 = nullptr;
   float2* xp2 = nullptr;
   float2* bp2 = nullptr;
+  // float32 correction form of the V-cycle (float32 / bfloat16 rows): the
+  // stencil in float32 with constrained neighbour columns folded to zero
+  // (levels above the coarsest), the padded correction and the right-hand
+  // side in float32 (every level)
+  float* st32 = nullptr;
+  float* d32 = nullptr;
+  float* b32 = nullptr;
   size_t vec_bytes = 0;
   unsigned long long active_slots = 0;  // sum over patches of active patch DoFs
   // patch classes (bit-identical L_i): prow[i] = row block of patch i;
@@ -135,6 +142,9 @@ struct fc_handle_s {
   // buffer down to the coarse solve) captured once as a CUDA graph
   cudaGraphExec_t coarse_graph = nullptr;
   int coarse_graph_kernels = 0;
+  // float32 / bfloat16 rows: the V-cycle runs in the float32 correction form
+  // through a batch holding this handle alone (created on first use)
+  struct fc_batch_s* self_batch = nullptr;
   bool capturing = false;
   fc::Profile prof;
   std::string err;
@@ -146,6 +156,9 @@ namespace fc {
 void note_launches(int n);
 // launches recorded while a stream capture is open are counted at replay
 void set_capturing(bool on);
+// float32 correction-form V-cycle of a handle (x known zero: xzero)
+fc_status handle_vcycle_f32(fc_handle h, double* x, const double* b, bool xzero);
+void handle_batch_free(fc_handle h);
 
 // ---- launchers (defined in the .cu files) ----
 // geometry + element data (fc_geom.cu)
@@ -206,6 +219,8 @@ cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* 
 // and its merge back; pair residual into the padded pair residual and/or an
 // unpadded float64 residual; pair apply updating the padded pair copy of x
 cudaError_t launch_split_pairs(long long n, const double* in, float2* out, cudaStream_t s);
+cudaError_t launch_fold_stencil_f32(const LevelGeom& g, const double* st, const unsigned char* mask, float* st32,
+                                    cudaStream_t s);
 cudaError_t launch_fold_stencil_pairs(const LevelGeom& g, const double* st, const unsigned char* mask,
                                       float2* st2, cudaStream_t s);
 cudaError_t launch_split_x_padded(const LevelGeom& g, const double* x, float2* xp2, cudaStream_t s);

@@ -23,7 +23,8 @@ EXPORTS = ("fc_options_default", "fc_setup", "fc_rhs", "fc_residual", "fc_apply"
            "fc_gmg_solve", "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
            "fc_profile_enable", "fc_profile_read", "fc_launch_count", "fc_sync", "fc_last_error",
            "fc_destroy", "fc_batch_create", "fc_batch_offsets", "fc_batch_tile", "fc_batch_set_tile",
-           "fc_batch_smooth", "fc_batch_vcycle", "fc_batch_solve", "fc_batch_info", "fc_batch_sync",
+           "fc_batch_smooth", "fc_batch_vcycle", "fc_batch_solve", "fc_batch_solve_host", "fc_batch_info", "fc_batch_profile_enable",
+           "fc_batch_profile_read", "fc_batch_sync",
            "fc_batch_last_error", "fc_batch_destroy")
 
 
@@ -99,7 +100,10 @@ def load(path: str = LIB_PATH):
     lib.fc_batch_smooth.argtypes = [vp, vp, vp, i]
     lib.fc_batch_vcycle.argtypes = [vp, vp, vp]
     lib.fc_batch_solve.argtypes = [vp, vp, vp, d, i, P(i), P(d)]
+    lib.fc_batch_solve_host.argtypes = [vp, vp, vp, d, i, P(i), P(d)]
     lib.fc_batch_info.argtypes = [vp, P(i), P(ll), P(ll), P(i)]
+    lib.fc_batch_profile_enable.argtypes = [vp, i]
+    lib.fc_batch_profile_read.argtypes = [vp, i, P(ll), P(d), P(d)]
     lib.fc_batch_sync.argtypes = [vp]
     lib.fc_batch_last_error.restype = C.c_char_p
     lib.fc_batch_last_error.argtypes = [vp]
@@ -430,6 +434,26 @@ class Batch:
         if st not in (FC_OK, FC_ERR_NOT_CONVERGED):
             self._check(st)
         return x, list(its), list(rel)
+
+    def solve_host(self, b_host, x_host, rtol=1e-8, maxit=200):
+        """Per-problem solves from packed pinned host tensors; x_host holds x0
+        and receives x.  Returns (iterations, relres)."""
+        n = len(self.solvers)
+        its = (C.c_int * n)()
+        rel = (C.c_double * n)()
+        st = self.lib.fc_batch_solve_host(self.b, C.c_void_p(b_host.data_ptr()), C.c_void_p(x_host.data_ptr()),
+                                          float(rtol), int(maxit), its, rel)
+        if st not in (FC_OK, FC_ERR_NOT_CONVERGED):
+            self._check(st)
+        return list(its), list(rel)
+
+    def profile(self, on: bool = True):
+        self._check(self.lib.fc_batch_profile_enable(self.b, 1 if on else 0))
+
+    def profile_read(self, kind: int):
+        n, ms, by = C.c_longlong(), C.c_double(), C.c_double()
+        self._check(self.lib.fc_batch_profile_read(self.b, int(kind), C.byref(n), C.byref(ms), C.byref(by)))
+        return n.value, ms.value, by.value
 
     def sync(self):
         self._check(self.lib.fc_batch_sync(self.b))

@@ -297,3 +297,22 @@ def test_standalone_gmg_replay(fc, nx, ny, nlev):
     x_gpu, its, red = s.gmg_solve(s.rhs(), reduction=1e-9, maxit=60)
     assert red <= 1e-9 and its == its_or
     assert rel(x_gpu.cpu().numpy(), x_or) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("name", ["ch2d", "por3d", "ell2d"])
+def test_float32_vcycle_error(fc, name, prec):
+    """Reduced-precision rows: the V-cycle runs in the float32 correction
+    form (float32 residuals, transfers and patch solves on the correction,
+    float64 anchor b - L x0 and float64 accumulation of x).  Stated error
+    against the oracle's FP64 V-cycle on the same input: the correction
+    within 2e-5 (float32 rows) / 2e-2 (bfloat16 rows) relative."""
+    p = PROBS[name]
+    s = fc.Solver(p, prec=prec)
+    mg = O.MG(p)
+    b = inputs.random_vector(p, 71)
+    x0 = inputs.random_vector(p, 72)
+    want = mg.vcycle(x0, b)
+    got = s.vcycle(x0, b).cpu().numpy()
+    err = rel(got - x0, want - x0)
+    assert err <= (2e-5 if prec == "fp32" else 2e-2), err
