@@ -241,14 +241,16 @@ fc_status fc_launch_count(long long* count);
  * problem's finest-level vector (node-interleaved as above) back to back,
  * problem p at [offsets[p], offsets[p+1]).  All calls are asynchronous on
  * the stream given to fc_batch_create unless they say they synchronise.
- * A problem's result does not depend on the other problems in the batch. */
+ * With the same patch-apply tile (see fc_batch_tile / fc_batch_set_tile)
+ * a problem's result is bit-identical alone and in any batch; different
+ * tiles change only the rounding order. */
 typedef struct fc_batch_s* fc_batch;
 
 /* Build a batch of nprob handles on cuda_stream (NULL = legacy default
  * stream).  Times every patch-apply tile candidate (lanes per patch
- * {4,8,16,32} x threads per CTA {128,256,512} x CTAs per SM {2,4,8,16},
- * at most 2048 threads per SM) on the batch's finest levels and keeps the
- * fastest.  Synchronises.  Errors: FC_ERR_INVALID (mixed dimensions,
+ * {1,2,4,8,16,32} x threads per CTA {128,256,512} x CTAs per SM
+ * {2,4,8,16}, at most 2048 threads per SM and 256 patches per CTA pass) on
+ * the batch's finest levels and keeps the fastest.  Synchronises.  Errors: FC_ERR_INVALID (mixed dimensions,
  * policies, precisions or sweep counts; DF64 rows), FC_ERR_CUDA. On error
  * *out is still set and must be passed to fc_batch_destroy. */
 fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream);
@@ -257,8 +259,9 @@ fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, vo
 fc_status fc_batch_offsets(fc_batch b, long long* offsets);
 
 /* Tile picked by the autotuner, or set by fc_batch_set_tile (tests and
- * sweeps): lanes per patch in {4,8,16,32}, threads per CTA in
- * {128,256,512}, CTAs per SM in 1..64 (persistent grid size). */
+ * sweeps): lanes per patch in {1,2,4,8,16,32}, threads per CTA in
+ * {128,256,512} with threads / lanes <= 256, CTAs per SM in 1..64
+ * (persistent grid size).  FC_ERR_INVALID otherwise. */
 fc_status fc_batch_tile(fc_batch b, int* lanes_per_patch, int* threads, int* ctas_per_sm);
 fc_status fc_batch_set_tile(fc_batch b, int lanes_per_patch, int threads, int ctas_per_sm);
 

@@ -27,6 +27,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -307,14 +309,21 @@ __global__ void __launch_bounds__(512)
       for (int t = 0; t < ND; ++t)
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1) y[t] += __shfl_xor_sync(0xffffffffu, y[t], o);
-      if (valid && lane < ND) {
-        A yl = y[0];
+      if (valid) {
+        const unsigned char mi = mask[i];
+        // lane t of the group updates component t (all of them when TPP = 1)
 #pragma unroll
-        for (int t = 1; t < ND; ++t)
-          if (lane == t) yl = y[t];
-        const size_t xi = (size_t)i * ND + lane;
-        const bool fixed = lane < DIM && ((mask[i] >> lane) & 1);
-        x[xi] = x[xi] + (fixed ? (double)rp[lane] : omega * (double)yl);
+        for (int t0 = 0; t0 < ND; t0 += TPP) {
+          const int t = t0 + lane;
+          if (t >= ND) break;
+          A yl = y[0];
+#pragma unroll
+          for (int u = 1; u < ND; ++u)
+            if (t == u) yl = y[u];
+          const size_t xi = (size_t)i * ND + t;
+          const bool fixed = t < DIM && ((mi >> t) & 1);
+          x[xi] = x[xi] + (fixed ? (double)rp[t] : omega * (double)yl);
+        }
       }
     }
   }
@@ -621,13 +630,19 @@ __global__ void __launch_bounds__(512)
       for (int t = 0; t < ND; ++t)
 #pragma unroll
         for (int o = TPP / 2; o > 0; o >>= 1) y[t] += __shfl_xor_sync(0xffffffffu, y[t], o);
-      if (valid && lane < ND) {
-        float yl = y[0];
+      if (valid) {
+        const unsigned char mi = mask[i];
 #pragma unroll
-        for (int t = 1; t < ND; ++t)
-          if (lane == t) yl = y[t];
-        const bool fixed = lane < DIM && ((mask[i] >> lane) & 1);
-        d[pb + lane] += fixed ? rp[lane] : omega * yl;
+        for (int t0 = 0; t0 < ND; t0 += TPP) {
+          const int t = t0 + lane;
+          if (t >= ND) break;
+          float yl = y[0];
+#pragma unroll
+          for (int u = 1; u < ND; ++u)
+            if (t == u) yl = y[u];
+          const bool fixed = t < DIM && ((mi >> t) & 1);
+          d[pb + t] += fixed ? rp[t] : omega * yl;
+        }
       }
     }
   }
@@ -997,6 +1012,8 @@ typedef void (*ApplyFn)(const BSeg*, const Chunk*, int, const int*, int);
 template <int DIM, int PT>
 ApplyFn apply_fn(int tpp) {
   switch (tpp) {
+    case 1: return b_apply_kernel<DIM, PT, 1>;
+    case 2: return b_apply_kernel<DIM, PT, 2>;
     case 4: return b_apply_kernel<DIM, PT, 4>;
     case 8: return b_apply_kernel<DIM, PT, 8>;
     case 16: return b_apply_kernel<DIM, PT, 16>;
@@ -1007,6 +1024,8 @@ ApplyFn apply_fn(int tpp) {
 template <int DIM, int PT>
 ApplyFn fapply_fn(int tpp) {
   switch (tpp) {
+    case 1: return f_apply_kernel<DIM, PT, 1>;
+    case 2: return f_apply_kernel<DIM, PT, 2>;
     case 4: return f_apply_kernel<DIM, PT, 4>;
     case 8: return f_apply_kernel<DIM, PT, 8>;
     case 16: return f_apply_kernel<DIM, PT, 16>;
@@ -1252,13 +1271,13 @@ fc_status autotune(fc_batch B) {
   BK(cudaEventCreate(&e1));
   float best = 1e30f;
   Tile bt = B->tile;
-  const int tpps[4] = {4, 8, 16, 32};
+  const int tpps[6] = {1, 2, 4, 8, 16, 32};
   const int thr[3] = {128, 256, 512};
   const int cps[4] = {2, 4, 8, 16};
-  for (int a = 0; a < 4 && st == FC_OK; ++a)
+  for (int a = 0; a < 6 && st == FC_OK; ++a)
     for (int t = 0; t < 3 && st == FC_OK; ++t)
       for (int c = 0; c < 4 && st == FC_OK; ++c) {
-        if (thr[t] * cps[c] > 2048) continue;
+        if (thr[t] * cps[c] > 2048 || thr[t] / tpps[a] > kChunk) continue;
         Tile cand{tpps[a], thr[t], cps[c]};
         float tmin = 1e30f;
         for (int rep = 0; rep < 4 && st == FC_OK; ++rep) {
@@ -1385,6 +1404,10 @@ fc_status step_graph(fc_batch B, KrylovArgs& ka) {
 
 }  // namespace
 
+namespace {
+fc_status create_batch(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream, const Tile* fixed);
+}
+
 namespace fc {
 
 // V-cycle of one handle with float32 / bfloat16 rows in the float32
@@ -1392,10 +1415,25 @@ namespace fc {
 // first use; the tile tuned on the handle's finest level).  The V-cycle
 // after the pointer update is captured once per x-is-zero flag as a CUDA
 // graph.
+// Tiles of the single-handle V-cycles, one per (dimension, row precision,
+// size class = log2 of the finest patch count), tuned by the first handle of
+// a class and reused by every later one: a problem's rounding then does not
+// depend on what else ran while its tile was timed (serving runs problems
+// side by side).
+std::mutex g_tile_mu;
+std::map<long long, Tile> g_tiles;
+
 fc_status handle_vcycle_f32(fc_handle h, double* x, const double* b, bool xzero) {
   if (!h->self_batch) {
     fc_handle one = h;
-    fc_status st = fc_batch_create(&h->self_batch, &one, 1, h->stream);
+    const long long np = h->lev[h->nlev - 1].g.nnodes;
+    int cls = 0;
+    while ((1LL << (cls + 1)) <= np) ++cls;
+    const long long key = ((long long)h->dim * 8 + (long long)h->opt.prec) * 64 + cls;
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    auto it = g_tiles.find(key);
+    fc_status st = create_batch(&h->self_batch, &one, 1, h->stream, it == g_tiles.end() ? nullptr : &it->second);
+    if (st == FC_OK && it == g_tiles.end()) g_tiles[key] = h->self_batch->tile;
     if (st != FC_OK) {
       h->err = std::string("float32 V-cycle: ") + fc_batch_last_error(h->self_batch);
       fc_batch_destroy(h->self_batch);
@@ -1447,6 +1485,14 @@ void handle_batch_free(fc_handle h) {
 extern "C" {
 
 fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream) {
+  return create_batch(out, handles, nprob, cuda_stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+fc_status create_batch(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream, const Tile* fixed) {
   if (!out) return FC_ERR_INVALID;
   *out = nullptr;
   fc_batch B = new (std::nothrow) fc_batch_s();
@@ -1578,11 +1624,19 @@ fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, vo
     BK(cudaMemcpyAsync(B->chunks, chunks.data(), sizeof(Chunk) * chunks.size(), cudaMemcpyHostToDevice, B->s));
   // packed work vector (the Krylov basis is allocated by the first solve)
   BK(cudaMalloc(&B->R, sizeof(double) * (size_t)B->ntot));
-  fc_status st = autotune(B);
-  if (st != FC_OK) return st;
+  if (fixed) {
+    B->tile = *fixed;
+  } else {
+    fc_status st = autotune(B);
+    if (st != FC_OK) return st;
+  }
   BK(cudaStreamSynchronize(B->s));
   return FC_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 fc_status fc_batch_offsets(fc_batch B, long long* offsets) {
   if (!B || !offsets) return FC_ERR_INVALID;
@@ -1601,9 +1655,12 @@ fc_status fc_batch_tile(fc_batch B, int* tpp, int* threads, int* ctas_per_sm) {
 
 fc_status fc_batch_set_tile(fc_batch B, int tpp, int threads, int ctas_per_sm) {
   if (!B) return FC_ERR_INVALID;
-  if ((tpp != 4 && tpp != 8 && tpp != 16 && tpp != 32) || (threads != 128 && threads != 256 && threads != 512) ||
-      ctas_per_sm < 1 || ctas_per_sm > 64)
-    return bfail(B, FC_ERR_INVALID, "tile: tpp in {4,8,16,32}, threads in {128,256,512}, 1..64 CTAs per SM");
+  if ((tpp != 1 && tpp != 2 && tpp != 4 && tpp != 8 && tpp != 16 && tpp != 32) ||
+      (threads != 128 && threads != 256 && threads != 512) || threads / tpp > kChunk || ctas_per_sm < 1 ||
+      ctas_per_sm > 64)
+    return bfail(B, FC_ERR_INVALID,
+                 "tile: lanes per patch in {1,2,4,8,16,32}, threads in {128,256,512} with at most 256 patches "
+                 "per pass, 1..64 CTAs per SM");
   cudaStreamSynchronize(B->s);
   if (B->step_graph) {
     cudaGraphExecDestroy(B->step_graph);

@@ -15,8 +15,9 @@
 //
 // The warp walks the split tree in depth-first order (children in
 // lexicographic order) and adds point contributions in rule order, so every
-// entry is a sum over the same points in the same order as the definition.
-// This translation unit is compiled with --fmad=false.
+// entry is a sum over the same points in the same order as the definition;
+// the points themselves (level set, basis, force) are evaluated one per lane
+// and broadcast.  This translation unit is compiled with --fmad=false.
 #include <math.h>
 
 #include "fc_internal.cuh"
@@ -144,6 +145,15 @@ struct WarpShared {
   int cand[kMaxShapesPerCell];
   double stk_lo[kStack][3];
   int stk_lev[kStack];
+  // Gauss points of the volume rule waiting for evaluation, in rule order:
+  // position and weight, then per point alpha, force, basis values and
+  // gradients (filled one point per lane)
+  double px[32][3];
+  double pw[32];
+  double pal[32];
+  double pf[32][3];
+  double pval[32][8];
+  double pgrad[32][8][3];
 };
 
 // Angular index range [lo, hi] (before wrapping) of rule points t = step *
@@ -231,8 +241,52 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   bool split = false, al_mixed = false;
   double al_first = -1.0;
 
-  // ---- volume rule: depth-first over the split tree
+  // ---- volume rule: depth-first over the split tree.  The Gauss points of
+  // the leaves are queued in rule order and evaluated 32 at a time, one
+  // point per lane (level set, alpha, basis, force); the lanes then add the
+  // queued points to their entries in queue order, so every entry is still
+  // the sum over the points in rule order.
   const double gq[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
+  constexpr int NG = DIM == 3 ? 8 : 4;
+  int npt = 0;
+  auto flush = [&]() {
+    if (lane < npt) {
+      const double x[3] = {S.px[lane][0], S.px[lane][1], S.px[lane][2]};
+      S.pal[lane] = inside_obstacle(g.shapes, S.cand, nc, DIM, x) ? g.alpha : 1.0;
+      double val[8], grad[8][3];
+      q1_basis(DIM, x0, g.h, x, val, grad);
+      for (int a = 0; a < NL; ++a) {
+        S.pval[lane][a] = val[a];
+        for (int k = 0; k < 3; ++k) S.pgrad[lane][a][k] = grad[a][k];
+      }
+      double f[3] = {0.0, 0.0, 0.0};
+      force_at(g, x, f);
+      for (int k = 0; k < 3; ++k) S.pf[lane][k] = f[k];
+    }
+    __syncwarp();
+    for (int q = 0; q < npt; ++q) {
+      const double w = S.pw[q], al = S.pal[q];
+#pragma unroll
+      for (int t = 0; t < E::PER; ++t) {
+        EntryId id = entry_of<DIM>(lane + 32 * t);
+        if (id.kind == 0) {
+          double gg = 0.0;
+          for (int kk = 0; kk < DIM; ++kk) gg = gg + S.pgrad[q][id.a][kk] * S.pgrad[q][id.b][kk];
+          acc[t] = acc[t] + w * al * g.eta * gg;
+        } else if (id.kind == 1) {
+          acc[t] = acc[t] - w * al * S.pgrad[q][id.a][id.c] * S.pval[q][id.b];
+        } else if (id.kind == 2) {
+          acc[t] = acc[t] + w * al * S.pf[q][id.c] * S.pval[q][id.a];
+        }
+      }
+      if (al == 1.0) fluid_volume = fluid_volume + w;
+      if (al_first < 0.0) al_first = al;
+      else if (al != al_first) al_mixed = true;
+      nvol++;
+    }
+    __syncwarp();
+    npt = 0;
+  };
   int sp = 0;
   if (lane == 0) {
     S.stk_lo[0][0] = x0[0]; S.stk_lo[0][1] = x0[1]; S.stk_lo[0][2] = x0[2];
@@ -287,37 +341,21 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       __syncwarp();
       continue;
     }
+    // a leaf: queue its Gauss points
+    if (npt + NG > 32) flush();
     double w = 1.0;
     for (int k = 0; k < DIM; ++k) w = w * (hb[k] * 0.5);
-    constexpr int NG = DIM == 3 ? 8 : 4;
-    for (int p = 0; p < NG; ++p) {
-      int i = p & 1, j = (p >> 1) & 1, k = p >> 2;
-      double x[3] = {lo[0] + hb[0] * gq[i], lo[1] + hb[1] * gq[j],
-                     DIM == 3 ? lo[2] + hb[2] * gq[k] : 0.0};
-      double al = inside_obstacle(g.shapes, S.cand, nc, DIM, x) ? g.alpha : 1.0;
-      double val[8], grad[8][3];
-      q1_basis(DIM, x0, g.h, x, val, grad);
-      double f[3] = {0.0, 0.0, 0.0};
-      if (E::NF) force_at(g, x, f);
-#pragma unroll
-      for (int t = 0; t < E::PER; ++t) {
-        EntryId id = entry_of<DIM>(lane + 32 * t);
-        if (id.kind == 0) {
-          double gg = 0.0;
-          for (int kk = 0; kk < DIM; ++kk) gg = gg + grad[id.a][kk] * grad[id.b][kk];
-          acc[t] = acc[t] + w * al * g.eta * gg;
-        } else if (id.kind == 1) {
-          acc[t] = acc[t] - w * al * grad[id.a][id.c] * val[id.b];
-        } else if (id.kind == 2) {
-          acc[t] = acc[t] + w * al * f[id.c] * val[id.a];
-        }
-      }
-      if (al == 1.0) fluid_volume = fluid_volume + w;
-      if (al_first < 0.0) al_first = al;
-      else if (al != al_first) al_mixed = true;
-      nvol++;
+    if (lane < NG) {
+      const int i = lane & 1, j = (lane >> 1) & 1, k = lane >> 2;
+      S.px[npt + lane][0] = lo[0] + hb[0] * gq[i];
+      S.px[npt + lane][1] = lo[1] + hb[1] * gq[j];
+      S.px[npt + lane][2] = DIM == 3 ? lo[2] + hb[2] * gq[k] : 0.0;
+      S.pw[npt + lane] = w;
     }
+    npt += NG;
+    __syncwarp();
   }
+  if (npt > 0) flush();
 
   // ---- boundary rule of every candidate shape, points owned by this cell
   const int k2 = 1 << g.qdepth;
@@ -388,19 +426,32 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                 if (S.cand[u] != s && phi_shape(g.shapes[S.cand[u]], 2, xx) > 0.0) { ok = false; break; }
             }
           }
+          // each lane evaluates the basis at its own point; the points are
+          // then added in rule order with their values broadcast by shuffle
+          double lval[NL], ldn[NL];
+          {
+            double bx[3] = {px, py, 0.0};
+            double val[8], grad[8][3];
+            q1_basis(DIM, x0, g.h, bx, val, grad);
+            for (int q = 0; q < NL; ++q) {
+              double sdn = 0.0;
+              const double bnl[3] = {nx, ny, 0.0};
+              for (int k = 0; k < DIM; ++k) sdn = sdn + bnl[k] * grad[q][k];
+              lval[q] = val[q];
+              ldn[q] = sdn;
+            }
+          }
           unsigned vb = __ballot_sync(FULL, ok);
           while (vb) {
             int src = __ffs(vb) - 1;
             vb &= vb - 1;
-            double bx[3] = {__shfl_sync(FULL, px, src), __shfl_sync(FULL, py, src), 0.0};
             double bn[3] = {__shfl_sync(FULL, nx, src), __shfl_sync(FULL, ny, src), 0.0};
             double bw = __shfl_sync(FULL, wgt, src);
-            double val[8], grad[8][3], dn[8];
-            q1_basis(DIM, x0, g.h, bx, val, grad);
+            double val[8], dn[8];
+#pragma unroll
             for (int q = 0; q < NL; ++q) {
-              double sdn = 0.0;
-              for (int k = 0; k < DIM; ++k) sdn = sdn + bn[k] * grad[q][k];
-              dn[q] = sdn;
+              val[q] = __shfl_sync(FULL, lval[q], src);
+              dn[q] = __shfl_sync(FULL, ldn[q], src);
             }
 #pragma unroll
             for (int u = 0; u < E::PER; ++u) {
@@ -484,19 +535,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                     if (S.cand[u] != s && phi_shape(g.shapes[S.cand[u]], 3, xx) > 0.0) { ok = false; break; }
                 }
               }
+              double lval[NL], ldn[NL];
+              {
+                double val[8], grad[8][3];
+                q1_basis(DIM, x0, g.h, xx, val, grad);
+                const double bnl[3] = {-ex, -ey, -mu};
+                for (int qq = 0; qq < NL; ++qq) {
+                  double sdn = 0.0;
+                  for (int k = 0; k < DIM; ++k) sdn = sdn + bnl[k] * grad[qq][k];
+                  lval[qq] = val[qq];
+                  ldn[qq] = sdn;
+                }
+              }
               unsigned vb = __ballot_sync(FULL, ok);
               while (vb) {
                 int src = __ffs(vb) - 1;
                 vb &= vb - 1;
-                double bx[3] = {__shfl_sync(FULL, xx[0], src), __shfl_sync(FULL, xx[1], src),
-                                __shfl_sync(FULL, xx[2], src)};
                 double bn[3] = {-__shfl_sync(FULL, ex, src), -__shfl_sync(FULL, ey, src), -mu};
-                double val[8], grad[8][3], dn[8];
-                q1_basis(DIM, x0, g.h, bx, val, grad);
+                double val[8], dn[8];
+#pragma unroll
                 for (int qq = 0; qq < NL; ++qq) {
-                  double sdn = 0.0;
-                  for (int k = 0; k < DIM; ++k) sdn = sdn + bn[k] * grad[qq][k];
-                  dn[qq] = sdn;
+                  val[qq] = __shfl_sync(FULL, lval[qq], src);
+                  dn[qq] = __shfl_sync(FULL, ldn[qq], src);
                 }
 #pragma unroll
                 for (int u = 0; u < E::PER; ++u) {

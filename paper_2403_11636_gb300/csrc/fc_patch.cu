@@ -1047,10 +1047,17 @@ __device__ __forceinline__ pr pr_mul(pr a, pr b) {
   e = fmaf(a.l, b.h, e);
   return pr_norm(p, e);
 }
-// c - a b
+// c - a b: the product as p + e (exact FMA split plus the cross terms), a
+// two-sum of the high parts, the low parts added, one renormalisation
 __device__ __forceinline__ pr pr_fms(pr c, pr a, pr b) {
-  pr m = pr_mul(a, b);
-  return pr_add(c, {-m.h, -m.l});
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = c.h - p;
+  const float bb = s - c.h;
+  const float err = (c.h - (s - bb)) + (-p - bb);
+  return pr_norm(s, (c.l - e) + err);
 }
 __device__ __forceinline__ pr pr_div(pr a, pr b) {
   float q1 = a.h / b.h;
@@ -1064,75 +1071,165 @@ __device__ __forceinline__ pr pr_from(double v) {
 }
 __device__ __forceinline__ double pr_to(pr a) { return (double)a.h + (double)a.l; }
 
-__device__ void cta_lu_pair(pr* A, int n, int* piv, int* s_flag) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  for (int k = 0; k < n; ++k) {
+// CTA LU with partial pivoting (max |hi|, lowest row on ties) of the N x N
+// pair matrix A (row-major).  Per pivot step: warp 0 finds the pivot, the
+// rows are interchanged and the multipliers formed, then warp w updates the
+// trailing rows w, w + nw, ... with its lanes on the columns and the pivot
+// row held in registers (no index division in the inner loops).
+template <int N>
+__device__ void cta_lu_pair_rows(pr* A, int* piv, int* s_flag, pr* s_scal) {
+  constexpr int CJ = (N + 31) / 32;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  for (int k = 0; k < N; ++k) {
     if (warp == 0) {
       float best = -1.0f;
       int bi = k;
-      for (int r = k + lane; r < n; r += 32) {
-        float v = fabsf(A[r * n + k].h);
+      for (int r = k + lane; r < N; r += 32) {
+        const float v = fabsf(A[r * N + k].h);
         if (v > best) { best = v; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
-        float ov = __shfl_down_sync(0xffffffffu, best, o);
-        int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        const float ov = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
       if (lane == 0) {
         piv[k] = bi;
+        s_scal[0] = A[bi * N + k];
+        s_scal[1] = A[k * N + k];
         if (best == 0.0f) *s_flag = 1;
       }
     }
     __syncthreads();
     const int p = piv[k];
+    const pr pv = s_scal[0], akk = s_scal[1];
+    // interchange rows k and p outside column k; column k gets the pivot and
+    // the multipliers (row p's old entry is the old a_kk)
     if (p != k)
-      for (int c = tid; c < n; c += nt) {
-        pr t = A[k * n + c];
-        A[k * n + c] = A[p * n + c];
-        A[p * n + c] = t;
+      for (int c = tid; c < N; c += nt)
+        if (c != k) {
+          const pr t = A[k * N + c];
+          A[k * N + c] = A[p * N + c];
+          A[p * N + c] = t;
+        }
+    for (int r = k + tid; r < N; r += nt) {
+      if (r == k) {
+        A[k * N + k] = pv;
+      } else {
+        const pr a = r == p ? akk : A[r * N + k];
+        A[r * N + k] = pv.h != 0.0f ? pr_div(a, pv) : pr{0.0f, 0.0f};
       }
+    }
     __syncthreads();
-    const pr d = A[k * n + k];
-    for (int r = k + 1 + tid; r < n; r += nt)
-      A[r * n + k] = d.h != 0.0f ? pr_div(A[r * n + k], d) : pr{0.0f, 0.0f};
-    __syncthreads();
-    const int m = n - k - 1;
-    for (int t = tid; t < m * m; t += nt) {
-      const int r = k + 1 + t / m, c = k + 1 + t % m;
-      A[r * n + c] = pr_fms(A[r * n + c], A[r * n + k], A[k * n + c]);
+    pr pk[CJ];
+#pragma unroll
+    for (int j = 0; j < CJ; ++j) {
+      const int c = lane + 32 * j;
+      pk[j] = (c > k && c < N) ? A[k * N + c] : pr{0.0f, 0.0f};
+    }
+    int r = warp;
+    if (r <= k) r += ((k + 1 - r + nw - 1) / nw) * nw;
+    for (; r < N; r += nw) {
+      const pr m = A[r * N + k];
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) {
+        if (32 * j + 31 <= k) continue;  // whole 32-column chunk done (warp-uniform)
+        const int c = lane + 32 * j;
+        if (c > k && c < N) A[r * N + c] = pr_fms(A[r * N + c], m, pk[j]);
+      }
     }
     __syncthreads();
   }
 }
 
-__device__ void cta_solve_multi_pair(const pr* A, int n, const int* piv, pr* W, int ncol) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int col = tid; col < ncol; col += nt) {
-    pr* z = W + col * n;
-    for (int k = 0; k < n; ++k) {
-      int p = piv[k];
-      if (p != k) { pr t = z[k]; z[k] = z[p]; z[p] = t; }
+// W <- A^{-1} W for ncol right-hand sides (column-major, length N) with the
+// row-major pair LU of A and the row permutation perm (perm[r] = original
+// row placed at r by the interchanges).  Warp w takes the columns w, w + nw,
+// ... (CB of them at a time); lane l keeps rows l, l + 32, ... of those
+// columns in registers, so an entry never leaves its lane and the
+// substitutions need no block barrier: the entry of each pivot step is
+// broadcast by shuffle.
+template <int N, int CB>
+__device__ void cta_solve_pair_cols(const pr* A, const pr* rdiag, const int* perm, pr* W, int ncol) {
+  constexpr int RI = (N + 31) / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int g0 = warp; g0 < ncol; g0 += nw * CB) {
+    int nb = 0;  // columns of this group that exist (warp-uniform)
+#pragma unroll
+    for (int b = 0; b < CB; ++b)
+      if (g0 + b * nw < ncol) nb = b + 1;
+    pr z[CB][RI];
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int col = g0 + b * nw;
+#pragma unroll
+      for (int i = 0; i < RI; ++i) {
+        const int r = lane + 32 * i;
+        z[b][i] = (col < ncol && r < N) ? W[col * N + perm[r]] : pr{0.0f, 0.0f};
+      }
     }
-  }
-  __syncthreads();
-  for (int k = 0; k < n - 1; ++k) {
-    const int m = n - 1 - k;
-    for (int t = tid; t < m * ncol; t += nt) {
-      const int col = t / m, r = k + 1 + t % m;
-      W[col * n + r] = pr_fms(W[col * n + r], A[r * n + k], W[col * n + k]);
+    // forward substitution with the unit lower factor
+#pragma unroll
+    for (int kb = 0; kb < RI; ++kb) {
+      for (int kl = 0; kl < 32; ++kl) {
+        const int k = kb * 32 + kl;
+        if (k >= N - 1) break;
+        pr wk[CB];
+#pragma unroll
+        for (int b = 0; b < CB; ++b)
+          wk[b] = {__shfl_sync(0xffffffffu, z[b][kb].h, kl), __shfl_sync(0xffffffffu, z[b][kb].l, kl)};
+#pragma unroll
+        for (int i = 0; i < RI; ++i) {
+          if (32 * i + 31 <= k) continue;  // rows of this chunk final (warp-uniform)
+          const int r = lane + 32 * i;
+          if (r > k && r < N) {
+            const pr l = A[r * N + k];
+#pragma unroll
+            for (int b = 0; b < CB; ++b)
+              if (b < nb) z[b][i] = pr_fms(z[b][i], l, wk[b]);
+          }
+        }
+      }
     }
-    __syncthreads();
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    const pr d = A[k * n + k];
-    for (int col = tid; col < ncol; col += nt) W[col * n + k] = pr_div(W[col * n + k], d);
-    __syncthreads();
-    for (int t = tid; t < k * ncol; t += nt) {
-      const int col = t / k, r = t % k;
-      W[col * n + r] = pr_fms(W[col * n + r], A[r * n + k], W[col * n + k]);
+    // back substitution with the upper factor
+#pragma unroll
+    for (int kb = RI - 1; kb >= 0; --kb) {
+      for (int kl = 31; kl >= 0; --kl) {
+        const int k = kb * 32 + kl;
+        if (k >= N) continue;
+        const pr rd = rdiag[k];
+        pr q[CB];
+#pragma unroll
+        for (int b = 0; b < CB; ++b) {
+          if (b >= nb) continue;
+          const pr own = pr_mul(z[b][kb], rd);  // meaningful in lane kl only
+          q[b] = {__shfl_sync(0xffffffffu, own.h, kl), __shfl_sync(0xffffffffu, own.l, kl)};
+          if (lane == kl) z[b][kb] = q[b];
+        }
+#pragma unroll
+        for (int i = 0; i < RI; ++i) {
+          if (32 * i >= k) continue;  // no row of this chunk above k (warp-uniform)
+          const int r = lane + 32 * i;
+          if (r < k) {
+            const pr u = A[r * N + k];
+#pragma unroll
+            for (int b = 0; b < CB; ++b)
+              if (b < nb) z[b][i] = pr_fms(z[b][i], u, q[b]);
+          }
+        }
+      }
     }
-    __syncthreads();
+    __syncwarp();  // every lane's loads of the column precede the stores
+#pragma unroll
+    for (int b = 0; b < CB; ++b) {
+      const int col = g0 + b * nw;
+      if (col >= ncol) continue;
+#pragma unroll
+      for (int i = 0; i < RI; ++i) {
+        const int r = lane + 32 * i;
+        if (r < N) W[col * N + r] = z[b][i];
+      }
+    }
   }
 }
 
@@ -1176,7 +1273,10 @@ __global__ void __launch_bounds__(1024)
   long long* nodeP = nodeU + NU;
   unsigned char* au = reinterpret_cast<unsigned char*>(nodeP + NP);
   unsigned char* ap = au + NU;
+  int* perm = reinterpret_cast<int*>(((uintptr_t)(ap + NP) + 3) & ~(uintptr_t)3);  // NU
+  pr* rdiag = reinterpret_cast<pr*>(((uintptr_t)(perm + NU) + 7) & ~(uintptr_t)7);  // NU
   __shared__ int s_flag;
+  __shared__ pr s_scal[2];
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long widx = blockIdx.x;
   const long long i = work ? work[widx] : widx;
@@ -1211,79 +1311,106 @@ __global__ void __launch_bounds__(1024)
     dp[p] = (ap[p] && a > 0.0) ? 1.0 / sqrt(a) : 1.0;
   }
   __syncthreads();
-  // gather, equilibrate (float64), store as pairs
+  // gather, equilibrate (float64), store as pairs (structural zeros and the
+  // identity rows of absent DoFs without float64 arithmetic)
   const int v0 = DIM == 3 ? 62 : 12, p0 = DIM == 3 ? 13 : 4;
   for (int e = tid; e < NU * NU; e += nt) {
-    int v = e / NU, w = e % NU;
-    double val = 0.0;
+    const int v = e / NU, w = e % NU;
+    pr val = {v == w && !(au[v] && au[w]) ? 1.0f : 0.0f, 0.0f};
     if (au[v] && au[w]) {
       int ov[3], ow[3], d[3];
       vel_off<DIM>(v, ov);
       vel_off<DIM>(w, ow);
       bool adj = true;
       for (int k = 0; k < 3; ++k) { d[k] = ow[k] - ov[k]; if (d[k] < -1 || d[k] > 1) adj = false; }
-      if (adj) val = du[v] * st[((long long)nb_index<DIM>(d) * SP) * g.nnodes + nodeU[v]] * du[w];
-    } else if (v == w) {
-      val = 1.0;
+      if (adj) val = pr_from(du[v] * st[((long long)nb_index<DIM>(d) * SP) * g.nnodes + nodeU[v]] * du[w]);
     }
-    K[e] = pr_from(val);
+    K[e] = val;
   }
   for (int e = tid; e < DIM * NP * NU; e += nt) {
-    int col = e / NU, v = e % NU, c = col / NP, p = col % NP;
-    double val = 0.0;
+    const int col = e / NU, v = e % NU, c = col / NP, p = col % NP;
+    pr val = {0.0f, 0.0f};
     if (au[v] && ap[p]) {
       int ov[3], op[3], d[3];
       vel_off<DIM>(v, ov);
       prs_off<DIM>(p, op);
       bool adj = true;
       for (int k = 0; k < 3; ++k) { d[k] = op[k] - ov[k]; if (d[k] < -1 || d[k] > 1) adj = false; }
-      if (adj) val = du[v] * st[((long long)nb_index<DIM>(d) * SP + 1 + c) * g.nnodes + nodeU[v]] * dp[p];
+      if (adj) val = pr_from(du[v] * st[((long long)nb_index<DIM>(d) * SP + 1 + c) * g.nnodes + nodeU[v]] * dp[p]);
     }
-    W[e] = pr_from(val);
+    W[e] = val;
   }
   for (int v = tid; v < NU; v += nt) W[(DIM * NP) * NU + v] = pr{v == v0 ? 1.0f : 0.0f, 0.0f};
   for (int e = tid; e < NP * NP; e += nt) {
-    int p = e / NP, q = e % NP;
-    double val = 0.0;
+    const int p = e / NP, q = e % NP;
+    pr val = {p == q && !(ap[p] && ap[q]) ? 1.0f : 0.0f, 0.0f};
     if (ap[p] && ap[q]) {
       int op[3], oq[3], d[3];
       prs_off<DIM>(p, op);
       prs_off<DIM>(q, oq);
       bool adj = true;
       for (int k = 0; k < 3; ++k) { d[k] = oq[k] - op[k]; if (d[k] < -1 || d[k] > 1) adj = false; }
-      if (adj) val = dp[p] * st[((long long)nb_index<DIM>(d) * SP + 1 + 2 * DIM) * g.nnodes + nodeP[p]] * dp[q];
-    } else if (p == q) {
-      val = 1.0;
+      if (adj) val = pr_from(dp[p] * st[((long long)nb_index<DIM>(d) * SP + 1 + 2 * DIM) * g.nnodes + nodeP[p]] * dp[q]);
     }
-    S[e] = pr_from(val);
+    S[e] = val;
   }
   __syncthreads();
-  cta_lu_pair(K, NU, pivK, &s_flag);
-  cta_solve_multi_pair(K, NU, pivK, W, NC);
-  // S~ = C~ - sum_c B~_c^T W~_c, B~ re-read from the operator
+  cta_lu_pair_rows<NU>(K, pivK, &s_flag, s_scal);
+  // reciprocals of the pivots for the back substitution
+  for (int k = tid; k < NU; k += nt) {
+    const pr d = K[k * NU + k];
+    rdiag[k] = d.h != 0.0f ? pr_div({1.0f, 0.0f}, d) : pr{0.0f, 0.0f};
+  }
+  if (tid == 0) {
+    for (int r = 0; r < NU; ++r) perm[r] = r;
+    for (int k = 0; k < NU; ++k) {
+      const int pk = pivK[k];
+      const int t = perm[k];
+      perm[k] = perm[pk];
+      perm[pk] = t;
+    }
+  }
+  __syncthreads();
+  cta_solve_pair_cols<NU, 3>(K, rdiag, perm, W, NC);
+  __syncthreads();
+  // the LU of K~ is no longer needed: its space takes B~ in compact form,
+  // Bc[(p * NT + t) * DIM + c] = B~_c of pressure p and its neighbour
+  // velocity node t (3^d box around p)
+  constexpr int NT = DIM == 3 ? 27 : 9;
+  pr* Bc = K;
+  for (int e = tid; e < NP * NT * DIM; e += nt) {
+    const int p = e / (NT * DIM), rem = e - p * (NT * DIM), t = rem / DIM, c = rem - t * DIM;
+    int op[3];
+    prs_off<DIM>(p, op);
+    const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+    const int v = (op[0] + d[0] + 2) + 5 * (op[1] + d[1] + 2) + (DIM == 3 ? 25 * (op[2] + d[2] + 2) : 0);
+    pr val = {0.0f, 0.0f};
+    if (ap[p] && au[v]) {
+      const int dvp[3] = {-d[0], -d[1], -d[2]};
+      const long long base = (long long)nb_index<DIM>(dvp) * SP;
+      val = pr_from(du[v] * st[(base + 1 + c) * g.nnodes + nodeU[v]] * dp[p]);
+    }
+    Bc[e] = val;
+  }
+  __syncthreads();
+  // S~ = C~ - sum_c B~_c^T W~_c
   for (int e = tid; e < NP * NP; e += nt) {
-    int p = e / NP, q = e % NP;
-    pr s = S[e];
+    const int p = e / NP, q = e % NP;
+    pr sv = S[e];
     if (ap[p]) {
       int op[3];
       prs_off<DIM>(p, op);
-      for (int t = 0; t < (DIM == 3 ? 27 : 9); ++t) {
-        int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
-        int ov[3] = {op[0] + d[0], op[1] + d[1], op[2] + d[2]};
-        int v = (ov[0] + 2) + 5 * (ov[1] + 2) + (DIM == 3 ? 25 * (ov[2] + 2) : 0);
+      for (int t = 0; t < NT; ++t) {
+        const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+        const int v = (op[0] + d[0] + 2) + 5 * (op[1] + d[1] + 2) + (DIM == 3 ? 25 * (op[2] + d[2] + 2) : 0);
         if (!au[v]) continue;
-        int dvp[3] = {-d[0], -d[1], -d[2]};
-        long long base = (long long)nb_index<DIM>(dvp) * SP;
-        for (int c = 0; c < DIM; ++c) {
-          pr bt = pr_from(du[v] * st[(base + 1 + c) * g.nnodes + nodeU[v]] * dp[p]);
-          s = pr_fms(s, bt, W[(c * NP + q) * NU + v]);
-        }
+        for (int c = 0; c < DIM; ++c) sv = pr_fms(sv, Bc[(p * NT + t) * DIM + c], W[(c * NP + q) * NU + v]);
       }
     }
-    S[e] = s;
+    S[e] = sv;
   }
   __syncthreads();
-  cta_lu_pair(S, NP, pivS, &s_flag);
+  cta_lu_pair_rows<NP>(S, pivS, &s_flag, s_scal);
   if (s_flag && tid == 0) atomicOr(d_err, kErrSingularPatch);
   // owned rows: velocity c -> z_p = -S~^{-1} (row v0 of W~_c); pressure -> S~^{-1} e_p0
   if (tid < ND) {
@@ -1328,7 +1455,8 @@ size_t pair_factor_smem() {
   using P = PatchDims<DIM>;
   const int NC = DIM * P::NP + 1;
   size_t b = (size_t)(P::NU * P::NU + NC * P::NU + P::NP * P::NP + P::ND * P::NP) * 8 +
-             (P::NU + P::NP) * 8 + (P::NU + P::NP) * 4 + 8 + (P::NU + P::NP) * 8 + (P::NU + P::NP) + 16;
+             (P::NU + P::NP) * 8 + (P::NU + P::NP) * 4 + 8 + (P::NU + P::NP) * 8 + (P::NU + P::NP) + 16 +
+             P::NU * 4 + 4 + P::NU * 8 + 8;
   return (b + 15) & ~(size_t)15;
 }
 

@@ -61,7 +61,7 @@ def test_batch_layout(fc):
     # patches of the smoothed finest levels (the one-level problem has none)
     assert info["npatch_finest"] == sum(np.prod([k + 1 for k in p.n[:2]]) for p in probs if p.nlevels > 1)
     tpp, thr, cps = B.tile()
-    assert tpp in (4, 8, 16, 32) and thr in (128, 256, 512) and thr * cps <= 2048
+    assert tpp in (1, 2, 4, 8, 16, 32) and thr in (128, 256, 512) and thr * cps <= 2048 and thr // tpp <= 256
 
 
 @pytest.mark.parametrize("which", ["2d", "3d"])
@@ -163,8 +163,10 @@ def test_batch_tiles_agree(fc):
     x0 = B.pack([inputs.random_vector(p, 11 + k) for k, p in enumerate(probs)])
     bb = B.pack([inputs.random_vector(p, 21 + k) for k, p in enumerate(probs)])
     ref = None
-    for tpp in (4, 8, 16, 32):
+    for tpp in (1, 2, 4, 8, 16, 32):
         for thr, cps in ((128, 16), (512, 2)):
+            if thr // tpp > 256:
+                continue
             B.set_tile(tpp, thr, cps)
             X = B.smooth_(x0.clone(), bb, nsweeps=2).cpu().numpy()
             if ref is None:
@@ -188,3 +190,5 @@ def test_batch_invalid(fc):
     B = fc.Batch([s2])
     with pytest.raises(fc.FcError):
         B.set_tile(3, 256, 4)
+    with pytest.raises(fc.FcError):
+        B.set_tile(1, 512, 4)   # 512 patches per pass

@@ -73,10 +73,14 @@ def test_coarse_levels_operator(fc, name):
 
 
 @pytest.mark.parametrize("name", ["ch2d", "por3d", "ell2d"])
-def test_patch_rows(fc, name):
-    """Cached owned rows of L_i^{-1} (cache_inverse) equal the oracle's."""
+@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
+def test_patch_rows(fc, name, prec):
+    """Cached owned rows of L_i^{-1} (cache_inverse) equal the oracle's: the
+    FP64 build and the float-pair build (df64 rows; fp32 rows are the pair
+    rows rounded to float32)."""
+    tol = {"fp64": 1e-11, "df64": 1e-11, "fp32": 2e-7}[prec]
     p = PROBS[name]
-    s = fc.Solver(p)
+    s = fc.Solver(p, prec=prec)
     L = O.Level.from_problem(p)
     L.assemble()
     rng = np.random.default_rng(0)
@@ -88,7 +92,7 @@ def test_patch_rows(fc, name):
             if np.abs(o[k]).max() == 0:
                 assert np.abs(g[k]).max() == 0
             else:
-                assert rel(g[k], o[k]) <= 1e-11
+                assert rel(g[k], o[k]) <= tol, (prec, node, k, rel(g[k], o[k]))
 
 
 @pytest.mark.parametrize("cache", ["inverse", "matrix", "none"])
