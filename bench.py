@@ -316,11 +316,19 @@ def run_sweeps(args):
     import torch
     from paper_2403_11636_gb300 import build, fc, inputs
     build.build()
-    nlev = max(2, int(math.log2(args.n // 4)) + 1)
-    prob = inputs.porous_3d(0, n=args.n, nlevels=nlev)
+    if args.workload == "roofline2d":
+        # 2D roofline case: n^2 cells, one circle r = 0.2, alpha 1e-10,
+        # levels halved down to 16^2 cells
+        prob = inputs.roofline_2d(n=args.n, nlevels=max(2, int(math.log2(args.n // 16)) + 1))
+    else:
+        nlev = max(2, int(math.log2(args.n // 4)) + 1)
+        prob = inputs.porous_3d(0, n=args.n, nlevels=nlev)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
         s = fc.Solver(prob, cache=args.cache, prec=args.prec, stream=stream, dedup=args.dedup)
+        torch.cuda.synchronize()
+        setup_ms = 1e3 * (time.perf_counter() - t0)
         x = torch.as_tensor(inputs.random_vector(prob, 3)).cuda()
         b = torch.as_tensor(inputs.random_vector(prob, 4)).cuda()
         s.smooth_(x, b, nsweeps=args.warmup)
@@ -335,10 +343,15 @@ def run_sweeps(args):
         nr, mr, _ = s.profile_read(1)
         ms = e0.elapsed_time(e1) / max(args.steps, 1)
     upd = free_dofs(prob, prob.nlevels)
-    emit({"mode": "sweep", "workload": f"porous3d {args.n}^3 finest-level sweeps", "cache": args.cache,
+    hbm, _ = peaks()
+    wl = f"roofline2d {args.n}^2 finest-level sweeps" if args.workload == "roofline2d" else \
+        f"porous3d {args.n}^3 finest-level sweeps"
+    emit({"mode": "sweep", "workload": wl, "cache": args.cache,
           "prec": args.prec, "dedup": args.dedup, "cache_bytes": s.info()["bytes"][1], "sweep_ms": ms, "updates_per_s": upd / (ms * 1e-3),
           "apply_ms": ma / max(na, 1), "apply_bytes": ba, "residual_ms": mr / max(nr, 1),
-          "apply_gbs": ba / (ma / max(na, 1) * 1e-3) / 1e9 if ma > 0 else None})
+          "apply_gbs": ba / (ma / max(na, 1) * 1e-3) / 1e9 if ma > 0 else None,
+          "apply_frac_of_measured_hbm": (ba / (ma / max(na, 1) * 1e-3) / 1e9) / hbm if ma > 0 else None,
+          "setup_ms": setup_ms})
     s.close()
     return 0
 
@@ -439,7 +452,8 @@ def run_batch(args):
     for s_ in solvers:
         s_.close()
     # the plain FP64 GPU solver, one problem at a time, same problems
-    plain = [fc.Solver(p, prec="fp64", dedup=0) for p in probs]
+    probs_plain = [] if args.no_plain else probs
+    plain = [fc.Solver(p, prec="fp64", dedup=0) for p in probs_plain]
     rhs = [s_.rhs() for s_ in plain]
     for s_, r in zip(plain[:8], rhs[:8]):
         s_.solve(r, rtol=rtol, maxit=maxit)
@@ -452,10 +466,11 @@ def run_batch(args):
         _, i1, _ = s_.solve(r, rtol=rtol, maxit=maxit)
         lat.append(time.perf_counter() - t1)
         its_plain.append(i1)
-    plain_s = time.perf_counter() - tp0
+    plain_s = max(time.perf_counter() - tp0, 1e-9)
     for s_ in plain:
         s_.close()
-    lat.sort()
+    lat = sorted(lat) or [float("nan")]
+    its_plain = its_plain or [0]
     step_sorted = sorted(step_ms)
     solves_per_s = len(probs) * args.steps / (total_ms * 1e-3)
     out = {
@@ -477,12 +492,12 @@ def run_batch(args):
                    "latency_ms_p50": statistics.median(step_sorted),
                    "latency_ms_p99": step_sorted[min(len(step_sorted) - 1,
                                                      int(math.ceil(0.99 * len(step_sorted))) - 1)],
-                   "plain_fp64_gpu": {"solves_per_s": len(probs) / plain_s,
+                   "plain_fp64_gpu": None if args.no_plain else {"solves_per_s": len(probs) / plain_s,
                                       "latency_ms_p50": 1e3 * statistics.median(lat),
                                       "latency_ms_p99": 1e3 * lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
                                       "iterations_min_max": [min(its_plain), max(its_plain)],
                                       "note": "same problems solved one after another, FP64 rows"},
-                   "speedup_solves_per_s_vs_plain_fp64": solves_per_s / (len(probs) / plain_s),
+                   "speedup_solves_per_s_vs_plain_fp64": None if args.no_plain else solves_per_s / (len(probs) / plain_s),
                    "smoother": {"apply_launches": na, "apply_ms": ma / na, "residual_ms": mr / max(nr, 1)}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": None, "kernel": "batched patch apply over all finest levels",
@@ -614,11 +629,14 @@ def main():
     ap.add_argument("--tile", default="", help="lanes,threads,ctas_per_sm of --mode batch-sweep")
     ap.add_argument("--batch", type=int, default=256, help="problems of --mode batch")
     ap.add_argument("--batch-prec", default="fp32", choices=["fp64", "fp32", "bf16"])
+    ap.add_argument("--no-plain", action="store_true", help="--mode batch without the one-at-a-time FP64 runs")
     ap.add_argument("--requests", type=int, default=24, help="requests of --mode serve")
     ap.add_argument("--rate", type=float, default=50.0, help="arrivals per second of --mode serve")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--n", type=int, default=48, help="grid size of --mode sweep")
+    ap.add_argument("--workload", default="porous3d", choices=["porous3d", "roofline2d"],
+                    help="problem of --mode sweep")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

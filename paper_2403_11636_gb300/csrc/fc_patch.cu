@@ -515,7 +515,7 @@ __device__ __forceinline__ T pick(const T* v, int c) {
   return r;
 }
 
-template <int DIM>
+template <int DIM, int TPP>
 __global__ void __launch_bounds__(256)
     apply_fp64_kernel(LevelGeom g, const double* __restrict__ coef, const unsigned char* __restrict__ mask,
                       const double* __restrict__ rpad, double omega, double* __restrict__ x,
@@ -524,9 +524,12 @@ __global__ void __launch_bounds__(256)
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
   __shared__ int soff[NSLOT];
   slot_table<DIM>(g, soff);
-  const int lane = threadIdx.x & 31;
-  const unsigned i = (unsigned)(((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (i >= (unsigned)g.nnodes) return;
+  // a group of TPP lanes per patch; groups past the last patch still take
+  // part in the shuffles of their warp
+  const int lane = threadIdx.x % TPP;
+  const unsigned gi = (unsigned)(((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) / TPP);
+  const bool valid = gi < (unsigned)g.nnodes;
+  const unsigned i = valid ? gi : (unsigned)g.nnodes - 1;
   int ia[3];
   decode_node<DIM>(g, i, ia);
   const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
@@ -538,7 +541,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int k = 0; k < ND; ++k) y[k] = 0.0;
 #pragma unroll 2
-  for (int j = lane; j < NSLOT; j += 32) {
+  for (int j = lane; j < NSLOT; j += TPP) {
     double rv = rp[soff[j]];
     if (ND == 4) {
       const double2* c2 = reinterpret_cast<const double2*>(cf + (size_t)j * 4);
@@ -551,8 +554,9 @@ __global__ void __launch_bounds__(256)
   }
 #pragma unroll
   for (int k = 0; k < ND; ++k)
-    for (int o = 16; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
-  if (lane < ND) owned_update<ND>(i, lane, mask, rp[lane], pick<ND>(y, lane), omega, x, nullptr);
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
+  if (valid && lane < ND) owned_update<ND>(i, lane, mask, rp[lane], pick<ND>(y, lane), omega, x, nullptr);
 }
 
 // float32 / bfloat16 rows with float32 residual and float32 accumulation
@@ -570,7 +574,7 @@ __device__ __forceinline__ void load_row4<__nv_bfloat16>(const __nv_bfloat16* p,
   v[2] = __uint_as_float(a.y << 16); v[3] = __uint_as_float(a.y & 0xffff0000u);
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, int TPP>
 __global__ void __launch_bounds__(256)
     apply_lowp_kernel(LevelGeom g, const T* __restrict__ coef, const unsigned char* __restrict__ mask,
                       const float* __restrict__ rpad, double omega, double* __restrict__ x,
@@ -579,9 +583,10 @@ __global__ void __launch_bounds__(256)
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
   __shared__ int soff[NSLOT];
   slot_table<DIM>(g, soff);
-  const int lane = threadIdx.x & 31;
-  const unsigned i = (unsigned)(((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (i >= (unsigned)g.nnodes) return;
+  const int lane = threadIdx.x % TPP;
+  const unsigned gi = (unsigned)(((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) / TPP);
+  const bool valid = gi < (unsigned)g.nnodes;
+  const unsigned i = valid ? gi : (unsigned)g.nnodes - 1;
   int ia[3];
   decode_node<DIM>(g, i, ia);
   const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
@@ -593,7 +598,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int k = 0; k < ND; ++k) y[k] = 0.0f;
 #pragma unroll 2
-  for (int j = lane; j < NSLOT; j += 32) {
+  for (int j = lane; j < NSLOT; j += TPP) {
     float rv = rp[soff[j]];
     float cv[4];
     if (ND == 4) {
@@ -607,8 +612,10 @@ __global__ void __launch_bounds__(256)
   }
 #pragma unroll
   for (int k = 0; k < ND; ++k)
-    for (int o = 16; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
-  if (lane < ND) owned_update<ND>(i, lane, mask, (double)rp[lane], (double)pick<ND>(y, lane), omega, x, nullptr);
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
+  if (valid && lane < ND)
+    owned_update<ND>(i, lane, mask, (double)rp[lane], (double)pick<ND>(y, lane), omega, x, nullptr);
 }
 
 // Float-pair arithmetic (hi + lo of float32, about 48-bit significand) on the
@@ -903,13 +910,13 @@ cudaError_t run_factor(const LevelGeom& g, const double* st, const unsigned char
 // x are those of apply_df_kernel.
 constexpr int kMaxClassBlocks = 2;
 
-template <int DIM, bool SMEM>
+template <int DIM, bool SMEM, int TPP>
 __device__ __forceinline__ void df_patch_dot(const float2* __restrict__ cf, const float2* __restrict__ rp,
                                              const int* soff, int lane, df* y) {
   using P = PatchDims<DIM>;
   constexpr int ND = P::ND, NSLOT = P::NSLOT;
 #pragma unroll 2
-  for (int j = lane; j < NSLOT; j += 32) {
+  for (int j = lane; j < NSLOT; j += TPP) {
     float2 r2 = rp[soff[j]];
     float ch[4], cl[4];
     if (ND == 4) {
@@ -931,7 +938,7 @@ __device__ __forceinline__ void df_patch_dot(const float2* __restrict__ cf, cons
   }
 }
 
-template <int DIM>
+template <int DIM, int TPP>
 __global__ void __launch_bounds__(256)
     apply_df_persistent_kernel(LevelGeom g, const float2* __restrict__ coef, const unsigned char* __restrict__ mask,
                                const float2* __restrict__ rpad, float2* __restrict__ xp2, float2 om2,
@@ -950,10 +957,18 @@ __global__ void __launch_bounds__(256)
     for (int t = threadIdx.x; t < NSLOT * ND; t += blockDim.x) dst[t] = __ldg(src + t);
   }
   slot_table<DIM>(g, soff);  // ends with __syncthreads()
-  const int lane = threadIdx.x & 31;
-  const unsigned wpb = blockDim.x >> 5;
-  const unsigned nwarps = gridDim.x * wpb;
-  for (unsigned i = blockIdx.x * wpb + (threadIdx.x >> 5); i < (unsigned)g.nnodes; i += nwarps) {
+  // groups of TPP lanes take one patch each (TPP = 32: a warp per patch);
+  // every group of a warp runs the same number of passes so that the
+  // shuffles below always see full warps
+  const int lane = threadIdx.x % TPP;
+  const unsigned gpb = blockDim.x / TPP;
+  const unsigned ngroups = gridDim.x * gpb;
+  const unsigned first = blockIdx.x * gpb + threadIdx.x / TPP;
+  const unsigned warp_first = first - (threadIdx.x & 31) / TPP;
+  for (unsigned i0 = warp_first; i0 < (unsigned)g.nnodes; i0 += ngroups) {
+    const unsigned iv = i0 + (first - warp_first);
+    const bool valid = iv < (unsigned)g.nnodes;
+    const unsigned i = valid ? iv : (unsigned)g.nnodes - 1;
     int ia[3];
     decode_node<DIM>(g, i, ia);
     const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
@@ -968,26 +983,31 @@ __global__ void __launch_bounds__(256)
       sh = blk == cls_blk.x ? 0 : (blk == cls_blk.y ? 1 : -1);
     }
     if (sh >= 0) {
-      df_patch_dot<DIM, true>(srows + (size_t)sh * NSLOT * ND, rp, soff, lane, y);
+      df_patch_dot<DIM, true, TPP>(srows + (size_t)sh * NSLOT * ND, rp, soff, lane, y);
     } else {
       const size_t blk = pr < 0 ? (size_t)(-pr - 1) : (size_t)pr;
-      df_patch_dot<DIM, false>(coef + blk * NSLOT * ND, rp, soff, lane, y);
+      df_patch_dot<DIM, false, TPP>(coef + blk * NSLOT * ND, rp, soff, lane, y);
     }
 #pragma unroll
     for (int k = 0; k < ND; ++k) {
       float h = y[k].hi + y[k].lo;
       y[k] = {h, y[k].lo - (h - y[k].hi)};
-      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int o = TPP / 2; o > 0; o >>= 1) {
         df other = {__shfl_xor_sync(0xffffffffu, y[k].hi, o), __shfl_xor_sync(0xffffffffu, y[k].lo, o)};
         y[k] = df_add(y[k], other);
       }
     }
-    if (lane < ND) {
-      const float2 r2 = rp[lane];
-      const df yl = pick<ND>(y, lane);
-      const size_t k = (size_t)pbase * ND + lane;
+    // lane t of the group updates component t (two per lane when TPP = 2)
+#pragma unroll
+    for (int t0 = 0; t0 < ND; t0 += TPP) {
+      const int c = t0 + lane;
+      if (!valid || c >= ND) break;
+      const float2 r2 = rp[c];
+      const df yl = pick<ND>(y, c);
+      const size_t k = (size_t)pbase * ND + c;
       const float2 xv = xp2[k];
-      const bool fixed = lane < DIM && ((mask[i] >> lane) & 1);
+      const bool fixed = c < DIM && ((mask[i] >> c) & 1);
       const df add = fixed ? df{r2.x, r2.y} : df_mul({om2.x, om2.y}, yl);
       const df nv = df_add({xv.x, xv.y}, add);
       xp2[k] = make_float2(nv.hi, nv.lo);
@@ -995,30 +1015,60 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <int DIM>
-cudaError_t run_df_persistent(const LevelGeom& g, const float2* coef, const unsigned char* mask,
-                              const float2* rpad, float2* xp2, float2 om2, const int* prow, int2 cls,
-                              cudaStream_t s) {
+// lanes per patch of the single-problem apply kernels: a warp per 3D patch
+// (402 slots), 4 lanes per 2D patch (59 slots; a warp per 2D patch leaves
+// the loads latency-bound).  FC_APPLY_TPP (2, 4, 8, 16, 32) overrides the
+// choice of the float-pair apply for tuning runs.
+int apply_tpp(int dim) {
+  static int env = -1;
+  if (env < 0) {
+    env = 0;
+    if (const char* e = getenv("FC_APPLY_TPP")) {
+      const int t = atoi(e);
+      if (t == 2 || t == 4 || t == 8 || t == 16 || t == 32) env = t;
+    }
+  }
+  if (env) return env;
+  return dim == 3 ? 32 : 4;
+}
+
+template <int DIM, int TPP>
+cudaError_t run_df_persistent_t(const LevelGeom& g, const float2* coef, const unsigned char* mask,
+                                const float2* rpad, float2* xp2, float2 om2, const int* prow, int2 cls,
+                                cudaStream_t s) {
   using P = PatchDims<DIM>;
   const size_t smem = (size_t)kMaxClassBlocks * P::NSLOT * P::ND * sizeof(float2);
-  auto kern = apply_df_persistent_kernel<DIM>;
-  static int per_sm[4] = {0, 0, 0, 0};
+  auto kern = apply_df_persistent_kernel<DIM, TPP>;
+  static int per_sm = 0;
   static int nsm = 0;
-  if (!per_sm[DIM]) {
+  if (!per_sm) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[DIM], kern, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
     if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (per_sm[DIM] < 1) per_sm[DIM] = 1;
+    if (per_sm < 1) per_sm = 1;
   }
-  long long need = (g.nnodes + 7) / 8;
-  long long blocks = std::min<long long>((long long)per_sm[DIM] * nsm, need);
+  const long long need = (g.nnodes + 256 / TPP - 1) / (256 / TPP);
+  const long long blocks = std::min<long long>((long long)per_sm * nsm, need);
   kern<<<(unsigned)std::max<long long>(blocks, 1), 256, smem, s>>>(g, coef, mask, rpad, xp2, om2, prow, cls);
   note_launches(1);
   return cudaGetLastError();
+}
+
+template <int DIM>
+cudaError_t run_df_persistent(const LevelGeom& g, const float2* coef, const unsigned char* mask,
+                              const float2* rpad, float2* xp2, float2 om2, const int* prow, int2 cls,
+                              cudaStream_t s) {
+  switch (apply_tpp(DIM)) {
+    case 2: return run_df_persistent_t<DIM, 2>(g, coef, mask, rpad, xp2, om2, prow, cls, s);
+    case 4: return run_df_persistent_t<DIM, 4>(g, coef, mask, rpad, xp2, om2, prow, cls, s);
+    case 8: return run_df_persistent_t<DIM, 8>(g, coef, mask, rpad, xp2, om2, prow, cls, s);
+    case 16: return run_df_persistent_t<DIM, 16>(g, coef, mask, rpad, xp2, om2, prow, cls, s);
+    default: return run_df_persistent_t<DIM, 32>(g, coef, mask, rpad, xp2, om2, prow, cls, s);
+  }
 }
 // ---------------------------------------------------------------------------
 // Float-pair patch factorisation (rows for the reduced-precision modes).
@@ -1508,17 +1558,19 @@ cudaError_t launch_patch_rows_pair(const LevelGeom& g, const double* st, const u
 cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
                                const unsigned char* mask, const double* rpad, const float* rpad32,
                                double omega, double* x, const int* prow, cudaStream_t s) {
-  long long threads = g.nnodes * 32;
-  unsigned blocks = (unsigned)((threads + 255) / 256);
+  const long long threads32 = g.nnodes * 32;
+  const unsigned blocks = (unsigned)((threads32 + 255) / 256);
+  // 2D: 4 lanes per patch (see apply_tpp); 3D: a warp per patch
+  const unsigned blocks4 = (unsigned)((g.nnodes * 4 + 255) / 256);
   if (prec == FC_PREC_FP64) {
-    if (g.dim == 2) apply_fp64_kernel<2><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x, prow);
-    else apply_fp64_kernel<3><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x, prow);
+    if (g.dim == 2) apply_fp64_kernel<2, 4><<<blocks4, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x, prow);
+    else apply_fp64_kernel<3, 32><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x, prow);
   } else if (prec == FC_PREC_FP32) {
-    if (g.dim == 2) apply_lowp_kernel<2, float><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x, prow);
-    else apply_lowp_kernel<3, float><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x, prow);
+    if (g.dim == 2) apply_lowp_kernel<2, float, 4><<<blocks4, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x, prow);
+    else apply_lowp_kernel<3, float, 32><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x, prow);
   } else if (prec == FC_PREC_BF16) {
-    if (g.dim == 2) apply_lowp_kernel<2, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x, prow);
-    else apply_lowp_kernel<3, __nv_bfloat16><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x, prow);
+    if (g.dim == 2) apply_lowp_kernel<2, __nv_bfloat16, 4><<<blocks4, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x, prow);
+    else apply_lowp_kernel<3, __nv_bfloat16, 32><<<blocks, 256, 0, s>>>(g, (const __nv_bfloat16*)coef, mask, rpad32, omega, x, prow);
   } else {
     const float2 om2 = make_float2((float)omega, (float)(omega - (double)(float)omega));
     if (g.dim == 2) apply_df_kernel<2><<<blocks, 256, 0, s>>>(g, (const float2*)coef, mask, (const float2*)rpad32, omega, x, nullptr, om2, prow);
