@@ -632,8 +632,10 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
           if (o->prec == FC_PREC_FP64)
             CK(launch_patch_build(G, L.st, L.mask, 0, o->omega, c64, nullptr, nullptr, nullptr, nullptr,
                                   h->d_err, work, L.nwork, h->stream));
-          else  // rows kept in reduced precision: float-pair factorisation
+          else if (o->prec == FC_PREC_DF64)  // rows kept as float pairs: float-pair factorisation
             CK(launch_patch_rows_pair(G, L.st, L.mask, c64, h->d_err, work, L.nwork, h->stream));
+          else  // float32 / bfloat16 rows: float32 factors and iterative refinement
+            CK(launch_patch_rows_ir(G, L.st, L.mask, c64, h->d_err, work, L.nwork, h->stream));
         }
         if (o->prec == FC_PREC_FP64) {
           L.coef = c64;

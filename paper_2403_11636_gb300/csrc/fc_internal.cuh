@@ -202,6 +202,11 @@ cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsig
                                long long nwork, cudaStream_t s);
 // owned rows of the work-list patches by a float-pair factorisation (for
 // rows stored in reduced precision); float64 output like mode 0
+// owned rows of the work-list patches by a float32 factorisation with two
+// steps of iterative refinement (rows stored in float32 / bfloat16)
+cudaError_t launch_patch_rows_ir(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                 double* coef64, unsigned* d_err, const int* work, long long nwork,
+                                 cudaStream_t s);
 cudaError_t launch_patch_rows_pair(const LevelGeom& g, const double* st, const unsigned char* mask,
                                    double* coef64, unsigned* d_err, const int* work, long long nwork,
                                    cudaStream_t s);

@@ -1121,13 +1121,39 @@ __device__ __forceinline__ pr pr_from(double v) {
 }
 __device__ __forceinline__ double pr_to(pr a) { return (double)a.h + (double)a.l; }
 
-// CTA LU with partial pivoting (max |hi|, lowest row on ties) of the N x N
-// pair matrix A (row-major).  Per pivot step: warp 0 finds the pivot, the
+// Arithmetic of the CTA factorisations: float pairs (Ops = OpsPair) or
+// plain float32 (Ops = OpsF32).
+struct OpsPair {
+  using T = pr;
+  static __device__ __forceinline__ T zero() { return {0.0f, 0.0f}; }
+  static __device__ __forceinline__ float mag(T a) { return fabsf(a.h); }
+  static __device__ __forceinline__ bool nonzero(T a) { return a.h != 0.0f; }
+  static __device__ __forceinline__ T fms(T c, T a, T b) { return pr_fms(c, a, b); }
+  static __device__ __forceinline__ T div(T a, T b) { return pr_div(a, b); }
+  static __device__ __forceinline__ T mul(T a, T b) { return pr_mul(a, b); }
+  static __device__ __forceinline__ T shfl(T a, int src) {
+    return {__shfl_sync(0xffffffffu, a.h, src), __shfl_sync(0xffffffffu, a.l, src)};
+  }
+};
+struct OpsF32 {
+  using T = float;
+  static __device__ __forceinline__ T zero() { return 0.0f; }
+  static __device__ __forceinline__ float mag(T a) { return fabsf(a); }
+  static __device__ __forceinline__ bool nonzero(T a) { return a != 0.0f; }
+  static __device__ __forceinline__ T fms(T c, T a, T b) { return fmaf(-a, b, c); }
+  static __device__ __forceinline__ T div(T a, T b) { return a / b; }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T shfl(T a, int src) { return __shfl_sync(0xffffffffu, a, src); }
+};
+
+// CTA LU with partial pivoting (max |a|, the high part for pairs; lowest
+// row on ties) of the N x N matrix A (row-major).  Per pivot step: warp 0 finds the pivot, the
 // rows are interchanged and the multipliers formed, then warp w updates the
 // trailing rows w, w + nw, ... with its lanes on the columns and the pivot
 // row held in registers (no index division in the inner loops).
-template <int N>
-__device__ void cta_lu_pair_rows(pr* A, int* piv, int* s_flag, pr* s_scal) {
+template <int N, class Ops>
+__device__ void cta_lu_rows(typename Ops::T* A, int* piv, int* s_flag, typename Ops::T* s_scal) {
+  using T = typename Ops::T;
   constexpr int CJ = (N + 31) / 32;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   for (int k = 0; k < N; ++k) {
@@ -1135,7 +1161,7 @@ __device__ void cta_lu_pair_rows(pr* A, int* piv, int* s_flag, pr* s_scal) {
       float best = -1.0f;
       int bi = k;
       for (int r = k + lane; r < N; r += 32) {
-        const float v = fabsf(A[r * N + k].h);
+        const float v = Ops::mag(A[r * N + k]);
         if (v > best) { best = v; bi = r; }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -1152,13 +1178,13 @@ __device__ void cta_lu_pair_rows(pr* A, int* piv, int* s_flag, pr* s_scal) {
     }
     __syncthreads();
     const int p = piv[k];
-    const pr pv = s_scal[0], akk = s_scal[1];
+    const T pv = s_scal[0], akk = s_scal[1];
     // interchange rows k and p outside column k; column k gets the pivot and
     // the multipliers (row p's old entry is the old a_kk)
     if (p != k)
       for (int c = tid; c < N; c += nt)
         if (c != k) {
-          const pr t = A[k * N + c];
+          const T t = A[k * N + c];
           A[k * N + c] = A[p * N + c];
           A[p * N + c] = t;
         }
@@ -1166,26 +1192,26 @@ __device__ void cta_lu_pair_rows(pr* A, int* piv, int* s_flag, pr* s_scal) {
       if (r == k) {
         A[k * N + k] = pv;
       } else {
-        const pr a = r == p ? akk : A[r * N + k];
-        A[r * N + k] = pv.h != 0.0f ? pr_div(a, pv) : pr{0.0f, 0.0f};
+        const T a = r == p ? akk : A[r * N + k];
+        A[r * N + k] = Ops::nonzero(pv) ? Ops::div(a, pv) : Ops::zero();
       }
     }
     __syncthreads();
-    pr pk[CJ];
+    T pk[CJ];
 #pragma unroll
     for (int j = 0; j < CJ; ++j) {
       const int c = lane + 32 * j;
-      pk[j] = (c > k && c < N) ? A[k * N + c] : pr{0.0f, 0.0f};
+      pk[j] = (c > k && c < N) ? A[k * N + c] : Ops::zero();
     }
     int r = warp;
     if (r <= k) r += ((k + 1 - r + nw - 1) / nw) * nw;
     for (; r < N; r += nw) {
-      const pr m = A[r * N + k];
+      const T m = A[r * N + k];
 #pragma unroll
       for (int j = 0; j < CJ; ++j) {
         if (32 * j + 31 <= k) continue;  // whole 32-column chunk done (warp-uniform)
         const int c = lane + 32 * j;
-        if (c > k && c < N) A[r * N + c] = pr_fms(A[r * N + c], m, pk[j]);
+        if (c > k && c < N) A[r * N + c] = Ops::fms(A[r * N + c], m, pk[j]);
       }
     }
     __syncthreads();
@@ -1193,14 +1219,16 @@ __device__ void cta_lu_pair_rows(pr* A, int* piv, int* s_flag, pr* s_scal) {
 }
 
 // W <- A^{-1} W for ncol right-hand sides (column-major, length N) with the
-// row-major pair LU of A and the row permutation perm (perm[r] = original
+// row-major LU of A and the row permutation perm (perm[r] = original
 // row placed at r by the interchanges).  Warp w takes the columns w, w + nw,
 // ... (CB of them at a time); lane l keeps rows l, l + 32, ... of those
 // columns in registers, so an entry never leaves its lane and the
 // substitutions need no block barrier: the entry of each pivot step is
 // broadcast by shuffle.
-template <int N, int CB>
-__device__ void cta_solve_pair_cols(const pr* A, const pr* rdiag, const int* perm, pr* W, int ncol) {
+template <int N, int CB, class Ops>
+__device__ void cta_solve_cols(const typename Ops::T* A, const typename Ops::T* rdiag, const int* perm,
+                               typename Ops::T* W, int ncol) {
+  using T = typename Ops::T;
   constexpr int RI = (N + 31) / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int g0 = warp; g0 < ncol; g0 += nw * CB) {
@@ -1208,14 +1236,14 @@ __device__ void cta_solve_pair_cols(const pr* A, const pr* rdiag, const int* per
 #pragma unroll
     for (int b = 0; b < CB; ++b)
       if (g0 + b * nw < ncol) nb = b + 1;
-    pr z[CB][RI];
+    T z[CB][RI];
 #pragma unroll
     for (int b = 0; b < CB; ++b) {
       const int col = g0 + b * nw;
 #pragma unroll
       for (int i = 0; i < RI; ++i) {
         const int r = lane + 32 * i;
-        z[b][i] = (col < ncol && r < N) ? W[col * N + perm[r]] : pr{0.0f, 0.0f};
+        z[b][i] = (col < ncol && r < N) ? W[col * N + perm[r]] : Ops::zero();
       }
     }
     // forward substitution with the unit lower factor
@@ -1224,19 +1252,18 @@ __device__ void cta_solve_pair_cols(const pr* A, const pr* rdiag, const int* per
       for (int kl = 0; kl < 32; ++kl) {
         const int k = kb * 32 + kl;
         if (k >= N - 1) break;
-        pr wk[CB];
+        T wk[CB];
 #pragma unroll
-        for (int b = 0; b < CB; ++b)
-          wk[b] = {__shfl_sync(0xffffffffu, z[b][kb].h, kl), __shfl_sync(0xffffffffu, z[b][kb].l, kl)};
+        for (int b = 0; b < CB; ++b) wk[b] = Ops::shfl(z[b][kb], kl);
 #pragma unroll
         for (int i = 0; i < RI; ++i) {
           if (32 * i + 31 <= k) continue;  // rows of this chunk final (warp-uniform)
           const int r = lane + 32 * i;
           if (r > k && r < N) {
-            const pr l = A[r * N + k];
+            const T l = A[r * N + k];
 #pragma unroll
             for (int b = 0; b < CB; ++b)
-              if (b < nb) z[b][i] = pr_fms(z[b][i], l, wk[b]);
+              if (b < nb) z[b][i] = Ops::fms(z[b][i], l, wk[b]);
           }
         }
       }
@@ -1247,13 +1274,13 @@ __device__ void cta_solve_pair_cols(const pr* A, const pr* rdiag, const int* per
       for (int kl = 31; kl >= 0; --kl) {
         const int k = kb * 32 + kl;
         if (k >= N) continue;
-        const pr rd = rdiag[k];
-        pr q[CB];
+        const T rd = rdiag[k];
+        T q[CB];
 #pragma unroll
         for (int b = 0; b < CB; ++b) {
           if (b >= nb) continue;
-          const pr own = pr_mul(z[b][kb], rd);  // meaningful in lane kl only
-          q[b] = {__shfl_sync(0xffffffffu, own.h, kl), __shfl_sync(0xffffffffu, own.l, kl)};
+          const T own = Ops::mul(z[b][kb], rd);  // meaningful in lane kl only
+          q[b] = Ops::shfl(own, kl);
           if (lane == kl) z[b][kb] = q[b];
         }
 #pragma unroll
@@ -1261,10 +1288,10 @@ __device__ void cta_solve_pair_cols(const pr* A, const pr* rdiag, const int* per
           if (32 * i >= k) continue;  // no row of this chunk above k (warp-uniform)
           const int r = lane + 32 * i;
           if (r < k) {
-            const pr u = A[r * N + k];
+            const T u = A[r * N + k];
 #pragma unroll
             for (int b = 0; b < CB; ++b)
-              if (b < nb) z[b][i] = pr_fms(z[b][i], u, q[b]);
+              if (b < nb) z[b][i] = Ops::fms(z[b][i], u, q[b]);
           }
         }
       }
@@ -1405,7 +1432,7 @@ __global__ void __launch_bounds__(1024)
     S[e] = val;
   }
   __syncthreads();
-  cta_lu_pair_rows<NU>(K, pivK, &s_flag, s_scal);
+  cta_lu_rows<NU, OpsPair>(K, pivK, &s_flag, s_scal);
   // reciprocals of the pivots for the back substitution
   for (int k = tid; k < NU; k += nt) {
     const pr d = K[k * NU + k];
@@ -1421,7 +1448,7 @@ __global__ void __launch_bounds__(1024)
     }
   }
   __syncthreads();
-  cta_solve_pair_cols<NU, 3>(K, rdiag, perm, W, NC);
+  cta_solve_cols<NU, 3, OpsPair>(K, rdiag, perm, W, NC);
   __syncthreads();
   // the LU of K~ is no longer needed: its space takes B~ in compact form,
   // Bc[(p * NT + t) * DIM + c] = B~_c of pressure p and its neighbour
@@ -1460,7 +1487,7 @@ __global__ void __launch_bounds__(1024)
     S[e] = sv;
   }
   __syncthreads();
-  cta_lu_pair_rows<NP>(S, pivS, &s_flag, s_scal);
+  cta_lu_rows<NP, OpsPair>(S, pivS, &s_flag, s_scal);
   if (s_flag && tid == 0) atomicOr(d_err, kErrSingularPatch);
   // owned rows: velocity c -> z_p = -S~^{-1} (row v0 of W~_c); pressure -> S~^{-1} e_p0
   if (tid < ND) {
@@ -1498,6 +1525,328 @@ __global__ void __launch_bounds__(1024)
     }
     for (int k = 0; k < ND; ++k) out[(long long)j * ND + k] = vals[k];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Float32 factorisation with iterative refinement, for rows stored in
+// float32 or bfloat16.  The equilibrated block M~ = D L_i D (absent DoFs as
+// identity rows) is gathered once in float64 and kept in float pairs in its
+// sparse form (A~: 3^d velocity neighbours per velocity node; B~_c and C~ by
+// pressure node and neighbour); its dense blocks are factored in float32
+// (LU of A~, W = A~^{-1} B~, the Schur complement S~ = C~ - sum_c B~_c' W_c
+// and its LU).  The owned columns z_k = M~^{-1} e_k (= the owned rows, M~
+// being symmetric) are then solved with these factors through the block
+// elimination and refined twice: r = e_k - M~ z_k in float pairs from the
+// exact entries, z_k += M~^{-1} r.  Each step multiplies the error by about
+// cond(M~) x 2^-24, so the rows reach float64-class accuracy before they are
+// rounded to float32 / bfloat16, at a fraction of the cost of float-pair
+// elimination.
+template <int DIM>
+__global__ void __launch_bounds__(1024)
+    patch_factor_ir_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
+                           double* __restrict__ coef, unsigned* __restrict__ d_err,
+                           const int* __restrict__ work) {
+  using P = PatchDims<DIM>;
+  constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP, NSLOT = P::NSLOT;
+  constexpr int NT = DIM == 3 ? 27 : 9;   // 3^d neighbour offsets
+  constexpr int NB = DIM * NP;            // columns of B~
+  constexpr int NV = ND * DIM;            // velocity blocks of the ND owned vectors
+  constexpr int C0 = DIM == 3 ? 13 : 4;   // offset index of the zero offset
+  constexpr int NPASS = 3;                // first solve and two refinements
+  const int v0 = DIM == 3 ? 62 : 12, p0 = DIM == 3 ? 13 : 4;
+  extern __shared__ double smem[];
+  pr* Asp = reinterpret_cast<pr*>(smem);  // [v][t]
+  pr* Bsp = Asp + NU * NT;                // [(p * NT + t) * DIM + c]
+  pr* Csp = Bsp + NP * NT * DIM;          // [p][t]
+  pr* Zv = Csp + NP * NT;                 // [(k * DIM + c) * NU + v]
+  pr* Zp = Zv + NV * NU;                  // [k * NP + p]
+  double* du = reinterpret_cast<double*>(Zp + ND * NP);
+  double* dp = du + NU;
+  float* Af = reinterpret_cast<float*>(dp + NP);  // NU x NU
+  float* Wf = Af + NU * NU;               // NB columns of NU
+  float* Sf = Wf + NB * NU;               // NP x NP
+  float* Rv = Sf + NP * NP;               // NV columns of NU
+  float* Rp = Rv + NV * NU;               // ND x NP
+  float* Hp = Rp + ND * NP;               // ND x NP
+  float* rdiag = Hp + ND * NP;            // NU
+  int* pivA = reinterpret_cast<int*>(rdiag + NU);
+  int* permA = pivA + NU;
+  int* pivS = permA + NU;
+  long long* nodeU = reinterpret_cast<long long*>(((uintptr_t)(pivS + NP) + 7) & ~(uintptr_t)7);
+  long long* nodeP = nodeU + NU;
+  unsigned char* au = reinterpret_cast<unsigned char*>(nodeP + NP);
+  unsigned char* ap = au + NU;
+  __shared__ int s_flag;
+  __shared__ float s_scal[2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long widx = blockIdx.x;
+  const long long i = work ? work[widx] : widx;
+  const int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
+                     DIM == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
+  if (tid == 0) s_flag = 0;
+  for (int v = tid; v < NU; v += nt) {
+    int o[3];
+    vel_off<DIM>(v, o);
+    const int b0 = ia[0] + o[0], b1 = ia[1] + o[1], b2 = ia[2] + o[2];
+    const bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && (DIM == 2 || (b2 >= 0 && b2 <= g.n[2]));
+    const long long bn = in ? b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2) : -1;
+    nodeU[v] = bn;
+    au[v] = (unsigned char)(in && !(mask[bn] & 1));
+  }
+  for (int p = tid; p < NP; p += nt) {
+    int o[3];
+    prs_off<DIM>(p, o);
+    const int b0 = ia[0] + o[0], b1 = ia[1] + o[1], b2 = ia[2] + o[2];
+    const bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && (DIM == 2 || (b2 >= 0 && b2 <= g.n[2]));
+    nodeP[p] = in ? b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2) : -1;
+    ap[p] = (unsigned char)in;
+  }
+  __syncthreads();
+  for (int v = tid; v < NU; v += nt) {
+    const double a = au[v] ? fabs(st[((long long)C0 * SP) * g.nnodes + nodeU[v]]) : 0.0;
+    du[v] = (au[v] && a > 0.0) ? 1.0 / sqrt(a) : 1.0;
+  }
+  for (int p = tid; p < NP; p += nt) {
+    const double a = ap[p] ? fabs(st[((long long)C0 * SP + 1 + 2 * DIM) * g.nnodes + nodeP[p]]) : 0.0;
+    dp[p] = (ap[p] && a > 0.0) ? 1.0 / sqrt(a) : 1.0;
+  }
+  // dense float32 blocks start from zero
+  for (int e = tid; e < NU * NU; e += nt) Af[e] = 0.0f;
+  for (int e = tid; e < NB * NU; e += nt) Wf[e] = 0.0f;
+  for (int e = tid; e < NP * NP; e += nt) Sf[e] = 0.0f;
+  __syncthreads();
+  // the sparse equilibrated entries, float64 products kept as pairs
+  for (int e = tid; e < NU * NT; e += nt) {
+    const int v = e / NT, t = e - v * NT;
+    const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+    int ov[3];
+    vel_off<DIM>(v, ov);
+    const int ow[3] = {ov[0] + d[0], ov[1] + d[1], ov[2] + d[2]};
+    const bool inbox = ow[0] >= -2 && ow[0] <= 2 && ow[1] >= -2 && ow[1] <= 2 && ow[2] >= -2 && ow[2] <= 2;
+    pr val = {t == C0 && !au[v] ? 1.0f : 0.0f, 0.0f};
+    if (inbox) {
+      const int w = (ow[0] + 2) + 5 * (ow[1] + 2) + (DIM == 3 ? 25 * (ow[2] + 2) : 0);
+      if (au[v] && au[w]) val = pr_from(du[v] * st[((long long)nb_index<DIM>(d) * SP) * g.nnodes + nodeU[v]] * du[w]);
+      if (val.h != 0.0f) Af[v * NU + w] = val.h;
+    }
+    Asp[e] = val;
+  }
+  for (int e = tid; e < NP * NT * DIM; e += nt) {
+    const int p = e / (NT * DIM), rem = e - p * (NT * DIM), t = rem / DIM, c = rem - t * DIM;
+    int op[3];
+    prs_off<DIM>(p, op);
+    const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+    const int v = (op[0] + d[0] + 2) + 5 * (op[1] + d[1] + 2) + (DIM == 3 ? 25 * (op[2] + d[2] + 2) : 0);
+    pr val = {0.0f, 0.0f};
+    if (ap[p] && au[v]) {
+      const int dvp[3] = {-d[0], -d[1], -d[2]};
+      val = pr_from(du[v] * st[((long long)nb_index<DIM>(dvp) * SP + 1 + c) * g.nnodes + nodeU[v]] * dp[p]);
+      Wf[(c * NP + p) * NU + v] = val.h;
+    }
+    Bsp[e] = val;
+  }
+  for (int e = tid; e < NP * NT; e += nt) {
+    const int p = e / NT, t = e - p * NT;
+    const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+    int op[3];
+    prs_off<DIM>(p, op);
+    const int oq[3] = {op[0] + d[0], op[1] + d[1], op[2] + d[2]};
+    const bool inbox = oq[0] >= -1 && oq[0] <= 1 && oq[1] >= -1 && oq[1] <= 1 && oq[2] >= -1 && oq[2] <= 1;
+    pr val = {t == C0 && !ap[p] ? 1.0f : 0.0f, 0.0f};
+    if (inbox) {
+      const int q = (oq[0] + 1) + 3 * (oq[1] + 1) + (DIM == 3 ? 9 * (oq[2] + 1) : 0);
+      if (ap[p] && ap[q])
+        val = pr_from(dp[p] * st[((long long)nb_index<DIM>(d) * SP + 1 + 2 * DIM) * g.nnodes + nodeP[p]] * dp[q]);
+      if (val.h != 0.0f) Sf[p * NP + q] = val.h;
+    }
+    Csp[e] = val;
+  }
+  __syncthreads();
+  // float32 LU of A~, W = A~^{-1} B~, S~ and its LU
+  cta_lu_rows<NU, OpsF32>(Af, pivA, &s_flag, s_scal);
+  for (int k = tid; k < NU; k += nt) {
+    const float dk = Af[k * NU + k];
+    rdiag[k] = dk != 0.0f ? 1.0f / dk : 0.0f;
+  }
+  if (tid == 0) {
+    for (int r = 0; r < NU; ++r) permA[r] = r;
+    for (int k = 0; k < NU; ++k) {
+      const int pk = pivA[k];
+      const int tmp = permA[k];
+      permA[k] = permA[pk];
+      permA[pk] = tmp;
+    }
+  }
+  __syncthreads();
+  cta_solve_cols<NU, 3, OpsF32>(Af, rdiag, permA, Wf, NB);
+  __syncthreads();
+  for (int e = tid; e < NP * NP; e += nt) {
+    const int p = e / NP, q = e - p * NP;
+    float sv = Sf[e];
+    if (ap[p]) {
+      int op[3];
+      prs_off<DIM>(p, op);
+      for (int t = 0; t < NT; ++t) {
+        const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+        const int v = (op[0] + d[0] + 2) + 5 * (op[1] + d[1] + 2) + (DIM == 3 ? 25 * (op[2] + d[2] + 2) : 0);
+        if (!au[v]) continue;
+        for (int c = 0; c < DIM; ++c) sv = fmaf(-Bsp[(p * NT + t) * DIM + c].h, Wf[(c * NP + q) * NU + v], sv);
+      }
+    }
+    Sf[e] = sv;
+  }
+  __syncthreads();
+  cta_lu_rows<NP, OpsF32>(Sf, pivS, &s_flag, s_scal);
+  if (s_flag && tid == 0) atomicOr(d_err, kErrSingularPatch);
+  // right-hand sides e_k (owned velocity components, then the owned
+  // pressure) and zero solutions
+  for (int e = tid; e < NV * NU; e += nt) {
+    const int col = e / NU, v = e - col * NU, k = col / DIM, c = col - k * DIM;
+    Rv[e] = (k < DIM && c == k && v == v0) ? 1.0f : 0.0f;
+    Zv[e] = {0.0f, 0.0f};
+  }
+  for (int e = tid; e < ND * NP; e += nt) {
+    const int k = e / NP, p = e - k * NP;
+    Rp[e] = (k == DIM && p == p0) ? 1.0f : 0.0f;
+    Zp[e] = {0.0f, 0.0f};
+  }
+  __syncthreads();
+  for (int pass = 0; pass < NPASS; ++pass) {
+    // block solve M~ (u, p) = (Rv, Rp) in float32, in place
+    cta_solve_cols<NU, 3, OpsF32>(Af, rdiag, permA, Rv, NV);  // y_c = A~^{-1} f_c
+    __syncthreads();
+    for (int e = tid; e < ND * NP; e += nt) {  // h = g - sum_c B~_c' y_c
+      const int k = e / NP, p = e - k * NP;
+      float h = Rp[e];
+      int op[3];
+      prs_off<DIM>(p, op);
+      for (int t = 0; t < NT; ++t) {
+        const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+        const int v = (op[0] + d[0] + 2) + 5 * (op[1] + d[1] + 2) + (DIM == 3 ? 25 * (op[2] + d[2] + 2) : 0);
+        for (int c = 0; c < DIM; ++c) h = fmaf(-Bsp[(p * NT + t) * DIM + c].h, Rv[(k * DIM + c) * NU + v], h);
+      }
+      Hp[e] = h;
+    }
+    __syncthreads();
+    if (tid < ND) {  // p = S~^{-1} h
+      float* z = Hp + tid * NP;
+      for (int k = 0; k < NP; ++k) {
+        const int pk = pivS[k];
+        if (pk != k) { const float tmp = z[k]; z[k] = z[pk]; z[pk] = tmp; }
+      }
+      for (int r = 0; r < NP; ++r) {
+        float sv = z[r];
+        for (int c = 0; c < r; ++c) sv = fmaf(-Sf[r * NP + c], z[c], sv);
+        z[r] = sv;
+      }
+      for (int r = NP - 1; r >= 0; --r) {
+        float sv = z[r];
+        for (int c = r + 1; c < NP; ++c) sv = fmaf(-Sf[r * NP + c], z[c], sv);
+        z[r] = sv / Sf[r * NP + r];
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < NV * NU; e += nt) {  // u_c = y_c - W_c p, then z += (u, p)
+      const int col = e / NU, v = e - col * NU, k = col / DIM, c = col - k * DIM;
+      float u = Rv[e];
+      for (int q = 0; q < NP; ++q) u = fmaf(-Wf[(c * NP + q) * NU + v], Hp[k * NP + q], u);
+      Zv[e] = pr_add(Zv[e], {u, 0.0f});
+    }
+    for (int e = tid; e < ND * NP; e += nt) Zp[e] = pr_add(Zp[e], {Hp[e], 0.0f});
+    __syncthreads();
+    if (pass == NPASS - 1) break;
+    // residual e_k - M~ z in float pairs from the sparse entries
+    for (int e = tid; e < NV * NU; e += nt) {
+      const int col = e / NU, v = e - col * NU, k = col / DIM, c = col - k * DIM;
+      pr sv = {(k < DIM && c == k && v == v0) ? 1.0f : 0.0f, 0.0f};
+      int ov[3];
+      vel_off<DIM>(v, ov);
+      for (int t = 0; t < NT; ++t) {
+        const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+        const int ow[3] = {ov[0] + d[0], ov[1] + d[1], ov[2] + d[2]};
+        if (ow[0] < -2 || ow[0] > 2 || ow[1] < -2 || ow[1] > 2 || ow[2] < -2 || ow[2] > 2) continue;
+        const int w = (ow[0] + 2) + 5 * (ow[1] + 2) + (DIM == 3 ? 25 * (ow[2] + 2) : 0);
+        sv = pr_fms(sv, Asp[v * NT + t], Zv[(k * DIM + c) * NU + w]);
+        // pressure neighbour at the same offset (the 3^d box around the
+        // patch centre), coupled through B~_c(v, q)
+        const int oq[3] = {ov[0] + d[0], ov[1] + d[1], ov[2] + d[2]};
+        if (oq[0] < -1 || oq[0] > 1 || oq[1] < -1 || oq[1] > 1 || oq[2] < -1 || oq[2] > 1) continue;
+        const int q = (oq[0] + 1) + 3 * (oq[1] + 1) + (DIM == 3 ? 9 * (oq[2] + 1) : 0);
+        // v relative to q is -d: offset index of -d
+        const int tq = (-d[0] + 1) + 3 * (-d[1] + 1) + (DIM == 3 ? 9 * (-d[2] + 1) : 0);
+        sv = pr_fms(sv, Bsp[(q * NT + tq) * DIM + c], Zp[k * NP + q]);
+      }
+      Rv[e] = sv.h + sv.l;
+    }
+    for (int e = tid; e < ND * NP; e += nt) {
+      const int k = e / NP, p = e - k * NP;
+      pr sv = {(k == DIM && p == p0) ? 1.0f : 0.0f, 0.0f};
+      int op[3];
+      prs_off<DIM>(p, op);
+      for (int t = 0; t < NT; ++t) {
+        const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, DIM == 3 ? t / 9 - 1 : 0};
+        const int v = (op[0] + d[0] + 2) + 5 * (op[1] + d[1] + 2) + (DIM == 3 ? 25 * (op[2] + d[2] + 2) : 0);
+        for (int c = 0; c < DIM; ++c) sv = pr_fms(sv, Bsp[(p * NT + t) * DIM + c], Zv[(k * DIM + c) * NU + v]);
+        const int oq[3] = {op[0] + d[0], op[1] + d[1], op[2] + d[2]};
+        if (oq[0] < -1 || oq[0] > 1 || oq[1] < -1 || oq[1] > 1 || oq[2] < -1 || oq[2] > 1) continue;
+        const int q = (oq[0] + 1) + 3 * (oq[1] + 1) + (DIM == 3 ? 9 * (oq[2] + 1) : 0);
+        sv = pr_fms(sv, Csp[p * NT + t], Zp[k * NP + q]);
+      }
+      Rp[e] = sv.h + sv.l;
+    }
+    __syncthreads();
+  }
+  // owned rows of L_i^{-1} = D z_k D, in the slot layout
+  double* out = coef + widx * NSLOT * ND;
+  for (int j = tid; j < NSLOT; j += nt) {
+    double vals[ND];
+    if (j < NU * DIM) {
+      const int v = j / DIM, c2 = j % DIM;
+      for (int k = 0; k < ND; ++k) {
+        const bool own_ok = k < DIM ? au[v0] != 0 : true;
+        const double dk = k < DIM ? du[v0] : dp[p0];
+        vals[k] = (own_ok && au[v]) ? dk * pr_to(Zv[(k * DIM + c2) * NU + v]) * du[v] : 0.0;
+      }
+    } else {
+      const int p = j - NU * DIM;
+      for (int k = 0; k < ND; ++k) {
+        const bool own_ok = k < DIM ? au[v0] != 0 : true;
+        const double dk = k < DIM ? du[v0] : dp[p0];
+        vals[k] = (own_ok && ap[p]) ? dk * pr_to(Zp[k * NP + p]) * dp[p] : 0.0;
+      }
+    }
+    for (int k = 0; k < ND; ++k) out[(long long)j * ND + k] = vals[k];
+  }
+}
+
+template <int DIM>
+size_t ir_factor_smem() {
+  using P = PatchDims<DIM>;
+  constexpr int NT = DIM == 3 ? 27 : 9, NB = DIM * P::NP, NV = P::ND * DIM;
+  size_t b = (size_t)(P::NU * NT + P::NP * NT * DIM + P::NP * NT + NV * P::NU + P::ND * P::NP) * 8 +
+             (size_t)(P::NU + P::NP) * 8 +
+             (size_t)(P::NU * P::NU + NB * P::NU + P::NP * P::NP + NV * P::NU + 2 * P::ND * P::NP + P::NU) * 4 +
+             (size_t)(2 * P::NU + P::NP) * 4 + 8 + (size_t)(P::NU + P::NP) * 8 + (P::NU + P::NP) + 16;
+  return (b + 15) & ~(size_t)15;
+}
+
+template <int DIM>
+cudaError_t run_ir_factor(const LevelGeom& g, const double* st, const unsigned char* mask, double* coef,
+                          unsigned* d_err, const int* work, long long nwork, cudaStream_t s) {
+  const size_t sm = ir_factor_smem<DIM>();
+  auto kern = patch_factor_ir_kernel<DIM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long nb = work ? nwork : g.nnodes;
+  if (nb <= 0) return cudaSuccess;
+  int threads = DIM == 3 ? 1024 : 128;
+  if (const char* env = getenv("FC_FACTOR_THREADS")) {
+    const int t = atoi(env);
+    if (t >= 64 && t <= 1024 && t % 32 == 0) threads = t;
+  }
+  kern<<<(unsigned)nb, threads, sm, s>>>(g, st, mask, coef, d_err, work);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 template <int DIM>
@@ -1546,6 +1895,13 @@ cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsig
   if (mode == 0) return run_factor<3, 0>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, work, nwork, s);
   if (mode == 1) return run_factor<3, 1>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, work, nwork, s);
   return run_factor<3, 2>(g, st, mask, omega, coef64, fac, fpiv, rpad, x, d_err, nullptr, 0, s);
+}
+
+cudaError_t launch_patch_rows_ir(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                 double* coef64, unsigned* d_err, const int* work, long long nwork,
+                                 cudaStream_t s) {
+  if (g.dim == 2) return run_ir_factor<2>(g, st, mask, coef64, d_err, work, nwork, s);
+  return run_ir_factor<3>(g, st, mask, coef64, d_err, work, nwork, s);
 }
 
 cudaError_t launch_patch_rows_pair(const LevelGeom& g, const double* st, const unsigned char* mask,
