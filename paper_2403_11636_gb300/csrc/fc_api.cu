@@ -540,7 +540,9 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     CK(dalloc(h, &L.rpad, (size_t)padn * nd, 2));
     CK(cudaMemsetAsync(L.rpad, 0, sizeof(double) * padn * nd, h->stream));
     if (li > 0 && o->cache == FC_CACHE_INVERSE && o->prec == FC_PREC_DF64) {
-      size_t nst = (size_t)G.nnodes * nb * spn(dim);
+      // half pair stencil: the zero offset and the offsets after it (the
+      // operator is symmetric; the residual reads the others transposed)
+      size_t nst = (size_t)G.nnodes * (nb / 2 + 1) * spn(dim);
       CK(dalloc(h, &L.st2, nst, 0));
       CK(launch_fold_stencil_pairs(G, L.st, L.mask, L.st2, h->stream));
       CK(dalloc(h, &L.xp2, (size_t)pad_nodes(G) * nd, 2));

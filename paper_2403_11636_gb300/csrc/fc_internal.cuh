@@ -84,8 +84,10 @@ struct Level {
   double* rpad = nullptr;       // padded residual (smoother)
   float* rpad32 = nullptr;      // padded residual in float32 / pairs (mixed paths)
   // float-pair smoother state (FC_PREC_DF64): the stencil as (hi, lo) pairs
-  // with constrained columns folded in (zero), a padded pair copy of x (zero
-  // halo) that a smoothing phase updates in place, and a pair copy of b
+  // for the zero offset and the offsets after it (the operator is
+  // symmetric), with constrained columns folded in (zero), a padded pair copy
+  // of x (zero halo) that a smoothing phase updates in place, and a pair
+  // copy of b
   float2* st2 = nullptr;
   float2* xp2 = nullptr;
   float2* bp2 = nullptr;

@@ -97,21 +97,28 @@ __device__ __forceinline__ void dfacc(dfp& acc, float2 a, float2 b) {
   acc.lo += e + (pe + cross);
 }
 
-template <int DIM, int NS>
+// The operator is symmetric, so the pair stencil keeps half of the
+// neighbour offsets: the zero offset and the NH - 1 offsets after it in
+// lexicographic order (the "own" offsets).  The entries of node a for a
+// mirrored offset -d are the transposed entries that its neighbour b = a - d
+// stores for offset +d:  A(a,b) = A(b,a), B_c(a,b) = T_c(b,a),
+// T_c(a,b) = B_c(b,a), C(a,b) = C(b,a).  Each node reads its own entries
+// and those of its neighbours for the mirrored offsets (mostly from L2), so
+// the stencil's DRAM bytes halve.
+template <int DIM>
+__device__ __forceinline__ constexpr int half_offsets() { return (DIM == 3 ? 27 : 9) - (DIM == 3 ? 13 : 4); }
+
+// float-pair residual on the half stencil, one thread per node; own
+// entries of out-of-grid neighbours are stored as zero and x has a zero
+// halo, mirrored entries are read only from neighbours inside the grid
+template <int DIM>
 __global__ void __launch_bounds__(256)
-    residual_df2_kernel(LevelGeom g, const float2* __restrict__ st2, const unsigned char* __restrict__ mask,
+    residual_df2_kernel(LevelGeom g, const float2* __restrict__ sth, const unsigned char* __restrict__ mask,
                         const float2* __restrict__ xp2, const float2* __restrict__ b2,
                         float2* __restrict__ rpad2, double* __restrict__ r) {
-  // A group of NS lanes computes one node: lane `part` takes the neighbours
-  // nb = part, part + NS, ...; the partial sums are combined by shuffles and
-  // lane c writes component c.  st2 has constrained columns folded to zero
-  // and xp2 has a zero halo, so the neighbour loop has no branches.
-  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int part = (int)(t % NS);
-  long long node = t / NS;
-  const bool valid = node < g.nnodes;
-  if (!valid) node = g.nnodes - 1;  // stays in the shuffles, writes nothing
+  constexpr int CEN = DIM == 3 ? 13 : 4, NH = half_offsets<DIM>(), SP = 2 * DIM + 2, ND = DIM + 1;
+  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nnodes) return;
   int ia[3];
   {
     const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
@@ -127,13 +134,14 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int c = 0; c < ND; ++c) acc[c] = {0.0f, 0.0f};
 #pragma unroll
-  for (int k = 0; k < (NB + NS - 1) / NS; ++k) {
-    const int nb = part + k * NS;
-    if (nb < NB) {
-      const int off = (nb % 3 - 1) + px * (((nb / 3) % 3 - 1) + (DIM == 3 ? py * (nb / 9 - 1) : 0));
+  for (int h = 0; h < NH; ++h) {
+    const int nb = CEN + h;
+    const int d0 = nb % 3 - 1, d1 = (nb / 3) % 3 - 1, d2 = DIM == 3 ? nb / 9 - 1 : 0;
+    const int off = d0 + px * (d1 + (DIM == 3 ? py * d2 : 0));
+    {  // own entries, neighbour a + d
       const float2* xb = xc + off * ND;
-      const float2* sp = st2 + (long long)nb * SP * g.nnodes + node;
-      float2 vA = __ldcs(sp);
+      const float2* sp = sth + (long long)h * SP * g.nnodes + node;
+      const float2 vA = __ldcs(sp);
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         dfacc(acc[c], vA, xb[c]);
@@ -143,67 +151,61 @@ __global__ void __launch_bounds__(256)
       for (int c = 0; c < DIM; ++c) dfacc(acc[DIM], __ldcs(sp + (1 + DIM + c) * g.nnodes), xb[c]);
       dfacc(acc[DIM], __ldcs(sp + (1 + 2 * DIM) * g.nnodes), xb[DIM]);
     }
+    if (h > 0) {  // mirrored offset -d: transposed entries of b = a - d
+      const int b0 = ia[0] - d0, b1 = ia[1] - d1, b2i = ia[2] - d2;
+      const bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && (DIM == 2 || (b2i >= 0 && b2i <= g.n[2]));
+      if (in) {
+        const long long bnode = node - (d0 + (long long)g.nn[0] * (d1 + (long long)g.nn[1] * d2));
+        const float2* xm = xc - off * ND;
+        const float2* sm = sth + (long long)h * SP * g.nnodes + bnode;
+        const float2 vA = sm[0];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          dfacc(acc[c], vA, xm[c]);
+          dfacc(acc[c], sm[(1 + DIM + c) * g.nnodes], xm[DIM]);
+        }
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) dfacc(acc[DIM], sm[(1 + c) * g.nnodes], xm[c]);
+        dfacc(acc[DIM], sm[(1 + 2 * DIM) * g.nnodes], xm[DIM]);
+      }
+    }
   }
-  // combine the NS partial sums (renormalised pairs, two-sum of the parts)
+  const unsigned char ma = mask[node];
 #pragma unroll
   for (int c = 0; c < ND; ++c) {
-    float h = acc[c].hi + acc[c].lo;
-    float l = acc[c].lo - (h - acc[c].hi);
-#pragma unroll
-    for (int o = 1; o < NS; o <<= 1) {
-      float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
-      float s2 = h + oh;
-      float bb = s2 - h;
-      float e = (h - (s2 - bb)) + (oh - bb);
-      e += l + ol;
-      h = s2 + e;
-      l = e - (h - s2);
-    }
-    acc[c] = {h, l};
-  }
-  if (!valid) return;
-  const unsigned char ma = mask[node];
-  // lane `part` writes components part, part + NS, ... (all of them when NS = 1)
-#pragma unroll
-  for (int c0 = 0; c0 < ND; c0 += NS) {
-    const int c = c0 + part;
-    if (c >= ND) break;
-    float yh, yl;
-    {
-      dfp a = acc[0];
-#pragma unroll
-      for (int k = 1; k < ND; ++k)
-        if (c == k) a = acc[k];
-      yh = a.hi; yl = a.lo;
-    }
+    float yh = acc[c].hi + acc[c].lo;
+    float yl = acc[c].lo - (yh - acc[c].hi);
     if (c < DIM && ((ma >> c) & 1)) {
-      float2 xv = xc[c];
+      const float2 xv = xc[c];
       yh = xv.x; yl = xv.y;
     }
-    float2 bv = b2[node * ND + c];
+    const float2 bv = b2[node * ND + c];
     // (b - y) as a pair
-    float sh = bv.x - yh;
-    float bb = sh - bv.x;
+    const float sh = bv.x - yh;
+    const float bb = sh - bv.x;
     float e = (bv.x - (sh - bb)) + (-yh - bb);
     e += bv.y - yl;
-    float h = sh + e;
-    float l = e - (h - sh);
-    if (rpad2) rpad2[pn * ND + c] = make_float2(h, l);
-    if (r) r[node * ND + c] = (double)h + (double)l;
+    const float hh = sh + e;
+    const float l = e - (hh - sh);
+    if (rpad2) rpad2[pn * ND + c] = make_float2(hh, l);
+    if (r) r[node * ND + c] = (double)hh + (double)l;
   }
 }
 
-// pair stencil with the columns of constrained neighbours folded to zero
-// (all velocity components of a node are constrained together, so A and
-// T_c of such a neighbour never multiply a free unknown)
+// half pair stencil (own offsets only, see residual_df2_kernel) with the
+// columns of constrained DoFs folded to zero.  A stored entry serves row a
+// (column b) and, transposed, row b (column a); all velocity components of
+// a node are constrained together and rows of constrained velocities are
+// identity rows, so:  A is zero when a or b is constrained, B_c (also the
+// T_c of row b) when a is, T_c (also the B_c of row b) when b is.
 template <int DIM>
 __global__ void fold_stencil_pairs_kernel(LevelGeom g, const double* __restrict__ st,
-                                          const unsigned char* __restrict__ mask, float2* __restrict__ st2) {
-  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2;
+                                          const unsigned char* __restrict__ mask, float2* __restrict__ sth) {
+  constexpr int CEN = DIM == 3 ? 13 : 4, NH = half_offsets<DIM>(), SP = 2 * DIM + 2;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.nnodes * NB) return;
+  if (t >= g.nnodes * NH) return;
   const long long node = t % g.nnodes;
-  const int nb = (int)(t / g.nnodes);
+  const int h = (int)(t / g.nnodes), nb = CEN + h;
   int ia[3];
   {
     const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
@@ -212,22 +214,24 @@ __global__ void fold_stencil_pairs_kernel(LevelGeom g, const double* __restrict_
     ia[1] = DIM == 3 ? (int)(q % ny) : (int)q;
     ia[2] = DIM == 3 ? (int)(q / ny) : 0;
   }
-  int ib0 = ia[0] + nb % 3 - 1, ib1 = ia[1] + (nb / 3) % 3 - 1, ib2 = DIM == 3 ? ia[2] + nb / 9 - 1 : 0;
-  bool inside = !(ib0 < 0 || ib0 > g.n[0] || ib1 < 0 || ib1 > g.n[1]) &&
-                !(DIM == 3 && (ib2 < 0 || ib2 > g.n[2]));
-  bool fixed = inside && (mask[ib0 + (long long)g.nn[0] * (ib1 + (long long)g.nn[1] * ib2)] & 1);
+  const int ib0 = ia[0] + nb % 3 - 1, ib1 = ia[1] + (nb / 3) % 3 - 1, ib2 = DIM == 3 ? ia[2] + nb / 9 - 1 : 0;
+  const bool inside = !(ib0 < 0 || ib0 > g.n[0] || ib1 < 0 || ib1 > g.n[1]) &&
+                      !(DIM == 3 && (ib2 < 0 || ib2 > g.n[2]));
+  const bool own_fixed = mask[node] & 1;
+  const bool nb_fixed = inside && (mask[ib0 + (long long)g.nn[0] * (ib1 + (long long)g.nn[1] * ib2)] & 1);
   for (int e = 0; e < SP; ++e) {
-    const long long k = ((long long)nb * SP + e) * g.nnodes + node;
-    double v = inside ? st[k] : 0.0;
-    const bool velocity_column = (e == 0) || (e >= 1 + DIM && e < 1 + 2 * DIM);
-    if (fixed && velocity_column) v = 0.0;
-    float hi = (float)v;
-    st2[k] = make_float2(hi, (float)(v - (double)hi));
+    double v = inside ? st[((long long)nb * SP + e) * g.nnodes + node] : 0.0;
+    if (e == 0 && (own_fixed || nb_fixed)) v = 0.0;
+    else if (e >= 1 && e <= DIM && own_fixed) v = 0.0;
+    else if (e >= 1 + DIM && e < 1 + 2 * DIM && nb_fixed) v = 0.0;
+    const float hi = (float)v;
+    sth[((long long)h * SP + e) * g.nnodes + node] = make_float2(hi, (float)(v - (double)hi));
   }
 }
 
-// float32 stencil with the same folding (and zeros for out-of-grid
-// neighbours), for the float32 correction-form V-cycle
+// float32 stencil, all neighbour offsets, with the columns of constrained
+// neighbours folded to zero (A and T_c) and zeros for out-of-grid
+// neighbours, for the float32 correction-form V-cycle
 template <int DIM>
 __global__ void fold_stencil_f32_kernel(LevelGeom g, const double* __restrict__ st,
                                         const unsigned char* __restrict__ mask, float* __restrict__ st32) {
@@ -718,18 +722,18 @@ cudaError_t launch_split_pairs(long long n, const double* in, float2* out, cudaS
 cudaError_t launch_residual_df2(const LevelGeom& g, const float2* st2, const unsigned char* mask,
                                 const float2* xp2, const float2* b2, float2* rpad2, double* r,
                                 cudaStream_t s) {
-  // one lane per node measured faster than splitting the neighbours over a
-  // group of lanes (0.111 vs 0.134 ms at 64^3)
+  // one thread per node (splitting the neighbours over a group of lanes
+  // measured slower: 0.134 vs 0.111 ms at 64^3 on the full stencil)
   unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
-  if (g.dim == 2) residual_df2_kernel<2, 1><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
-  else residual_df2_kernel<3, 1><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+  if (g.dim == 2) residual_df2_kernel<2><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+  else residual_df2_kernel<3><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fold_stencil_pairs(const LevelGeom& g, const double* st, const unsigned char* mask,
                                       float2* st2, cudaStream_t s) {
-  long long n = g.nnodes * (g.dim == 3 ? 27 : 9);
+  long long n = g.nnodes * (g.dim == 3 ? 14 : 5);  // own (half) offsets
   unsigned blocks = (unsigned)((n + 255) / 256);
   if (g.dim == 2) fold_stencil_pairs_kernel<2><<<blocks, 256, 0, s>>>(g, st, mask, st2);
   else fold_stencil_pairs_kernel<3><<<blocks, 256, 0, s>>>(g, st, mask, st2);
