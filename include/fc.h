@@ -197,8 +197,10 @@ fc_status fc_solve_host(fc_handle h, const double* b_host, double* x_host, doubl
 
 /* Sizes of `level`: DoFs, patches (= pressure nodes) and device bytes by
  * part: [0] operator, [1] patch cache, [2] vectors/workspace, [3] coarse
- * solve, [4] setup temporaries peak, [5..7] reserved. Any pointer may be
- * NULL. */
+ * solve, [4] setup temporaries peak; [5] is a count, not bytes: patches (all
+ * levels) whose float32 factorisation with iterative refinement did not
+ * converge and that were rebuilt by float-pair elimination (float32 /
+ * bfloat16 rows only); [6..7] reserved. Any pointer may be NULL. */
 fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch,
                   size_t* bytes_by_part);
 

@@ -416,7 +416,7 @@ size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o) {
     total += (size_t)nodes * nb * (2 * dim + 2) * 8 + nodes + (size_t)nodes * nd * 8;  // st, mask, wfix
     total += (size_t)nodes * nd * 8 * 3 + (size_t)pad * nd * 8 + (size_t)pad * nd * 8;   // vectors
     if (o->cache == FC_CACHE_INVERSE && (o->prec == FC_PREC_FP32 || o->prec == FC_PREC_BF16))
-      total += (size_t)(l > 0 ? nodes * nb * (2 * dim + 2) * 4 : 0) + (size_t)pad * nd * 4 + (size_t)nodes * nd * 4;
+      total += (size_t)(l > 0 ? nodes * (nb / 2 + 1) * (2 * dim + 2) * 4 : 0) + (size_t)pad * nd * 4 + (size_t)nodes * nd * 4;
     if (l > 0) {
       if (o->cache == FC_CACHE_INVERSE)
         total += (size_t)nodes * nslot(dim) * nd * coef_elem_bytes(o->prec);
@@ -557,7 +557,7 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
       // float32 correction-form V-cycle: folded float32 stencil, padded
       // correction (zero halo) and float32 right-hand side
       if (li > 0) {
-        CK(dalloc(h, &L.st32, (size_t)G.nnodes * nb * spn(dim), 0));
+        CK(dalloc(h, &L.st32, (size_t)G.nnodes * (nb / 2 + 1) * spn(dim), 0));  // half stencil
         CK(launch_fold_stencil_f32(G, L.st, L.mask, L.st32, h->stream));
       }
       CK(dalloc(h, &L.d32, (size_t)padn * nd, 2));
@@ -635,9 +635,27 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
             CK(launch_patch_build(G, L.st, L.mask, 0, o->omega, c64, nullptr, nullptr, nullptr, nullptr,
                                   h->d_err, work, L.nwork, h->stream));
           else if (o->prec == FC_PREC_DF64)  // rows kept as float pairs: float-pair factorisation
-            CK(launch_patch_rows_pair(G, L.st, L.mask, c64, h->d_err, work, L.nwork, h->stream));
-          else  // float32 / bfloat16 rows: float32 factors and iterative refinement
-            CK(launch_patch_rows_ir(G, L.st, L.mask, c64, h->d_err, work, L.nwork, h->stream));
+            CK(launch_patch_rows_pair(G, L.st, L.mask, c64, h->d_err, work, L.nwork, nullptr, h->stream));
+          else {  // float32 / bfloat16 rows: float32 factors and iterative refinement
+            const long long nw = work ? L.nwork : G.nnodes;
+            int *redo_node = nullptr, *redo_out = nullptr, *nredo = nullptr;
+            CK(dalloc(h, &redo_node, (size_t)std::max(nw, 1LL), -1));
+            CK(dalloc(h, &redo_out, (size_t)std::max(nw, 1LL), -1));
+            CK(dalloc(h, &nredo, 1, -1));
+            CK(cudaMemsetAsync(nredo, 0, sizeof(int), h->stream));
+            CK(launch_patch_rows_ir(G, L.st, L.mask, c64, h->d_err, work, L.nwork, redo_node, redo_out, nredo,
+                                    h->stream));
+            int nr = 0;
+            CK(cudaMemcpyAsync(&nr, nredo, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            // patches whose float32 refinement did not converge: float pairs
+            if (nr > 0)
+              CK(launch_patch_rows_pair(G, L.st, L.mask, c64, h->d_err, redo_node, nr, redo_out, h->stream));
+            h->pair_fallback += nr;
+            dfree(h, redo_node);
+            dfree(h, redo_out);
+            dfree(h, nredo);
+          }
         }
         if (o->prec == FC_PREC_FP64) {
           L.coef = c64;
@@ -903,8 +921,10 @@ fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch, si
   const Level& L = h->lev[level - 1];
   if (ndof) *ndof = L.g.ndof;
   if (npatch) *npatch = level >= 2 ? L.g.nnodes : 0;
-  if (bytes_by_part)
+  if (bytes_by_part) {
     for (int k = 0; k < 8; ++k) bytes_by_part[k] = h->bytes[k];
+    bytes_by_part[5] = (size_t)h->pair_fallback;
+  }
   return FC_OK;
 }
 

@@ -65,7 +65,7 @@ struct BSeg {
   float* rpadf;        // padded float32 residual (float32 / bfloat16 rows)
   const double* cinv;  // coarse inverse (level 0)
   int cn;
-  // float32 correction form (float32 / bfloat16 rows): folded float32
+  // float32 correction form (float32 / bfloat16 rows): folded float32 half
   // stencil, padded correction d and right-hand side b32 of the level
   const float* st32;
   float* d32;
@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(256)
 // smoothing phase on (x, b) runs on the correction d with d = 0 at the start
 // and right-hand side b32 = b - L x (float64 residual, skipped when x is
 // known to be zero), entirely in float32: residual r = b32 - L32 d with the
-// float32 stencil (constrained neighbour columns folded to zero), patch
+// float32 half stencil (constrained columns folded to zero), patch
 // solves d += omega L_i^{-1} r on the owned DoFs, transfers and prolongation
 // on d; the coarse solve reads b32 and sums in float64.  At the end x += d
 // in float64.  In exact arithmetic this is the same iteration as on x.
@@ -529,7 +529,11 @@ template <int DIM>
 __global__ void __launch_bounds__(256)
     f_residual_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch,
                       const int* __restrict__ state, int gate) {
-  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2, ND = DIM + 1;
+  // half stencil: the zero offset and the offsets after it are the node's
+  // own entries; a mirrored offset -d takes the transposed entries of the
+  // neighbour b = a - d (A(a,b) = A(b,a), B_c(a,b) = T_c(b,a),
+  // T_c(a,b) = B_c(b,a), C(a,b) = C(b,a))
+  constexpr int CEN = DIM == 3 ? 13 : 4, NH = (DIM == 3 ? 27 : 9) - CEN, SP = 2 * DIM + 2, ND = DIM + 1;
   for (int c = blockIdx.x; c < nch; c += gridDim.x) {
     const Chunk k = ch[c];
     const BSeg* S = segs + k.seg;
@@ -547,22 +551,47 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int q = 0; q < ND; ++q) acc[q] = 0.0f;
 #pragma unroll
-    for (int nb = 0; nb < NB; ++nb) {
-      const int off = (nb % 3 - 1) + px * (((nb / 3) % 3 - 1) + (DIM == 3 ? py * (nb / 9 - 1) : 0));
-      const float* db = d + (pn + off) * ND;
-      const float* sp = st + (long long)nb * SP * g.nnodes + node;
-      float dv[ND];
+    for (int h = 0; h < NH; ++h) {
+      const int nb = CEN + h;
+      const int d0 = nb % 3 - 1, d1 = (nb / 3) % 3 - 1, d2 = DIM == 3 ? nb / 9 - 1 : 0;
+      const int off = d0 + px * (d1 + (DIM == 3 ? py * d2 : 0));
+      {
+        const float* db = d + (pn + off) * ND;
+        const float* sp = st + (long long)h * SP * g.nnodes + node;
+        float dv[ND];
 #pragma unroll
-      for (int q = 0; q < ND; ++q) dv[q] = db[q];
-      const float vA = __ldcs(sp);
+        for (int q = 0; q < ND; ++q) dv[q] = db[q];
+        const float vA = __ldcs(sp);
 #pragma unroll
-      for (int q = 0; q < DIM; ++q) {
-        acc[q] = fmaf(vA, dv[q], acc[q]);
-        acc[q] = fmaf(__ldcs(sp + (1 + q) * g.nnodes), dv[DIM], acc[q]);
+        for (int q = 0; q < DIM; ++q) {
+          acc[q] = fmaf(vA, dv[q], acc[q]);
+          acc[q] = fmaf(__ldcs(sp + (1 + q) * g.nnodes), dv[DIM], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) acc[DIM] = fmaf(__ldcs(sp + (1 + DIM + q) * g.nnodes), dv[q], acc[DIM]);
+        acc[DIM] = fmaf(__ldcs(sp + (1 + 2 * DIM) * g.nnodes), dv[DIM], acc[DIM]);
       }
+      if (h > 0) {
+        const int b0 = ia[0] - d0, b1 = ia[1] - d1, b2 = ia[2] - d2;
+        const bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && (DIM == 2 || (b2 >= 0 && b2 <= g.n[2]));
+        if (in) {
+          const long long bnode = node - (d0 + (long long)g.nn[0] * (d1 + (long long)g.nn[1] * d2));
+          const float* db = d + (pn - off) * ND;
+          const float* sm = st + (long long)h * SP * g.nnodes + bnode;
+          float dv[ND];
 #pragma unroll
-      for (int q = 0; q < DIM; ++q) acc[DIM] = fmaf(__ldcs(sp + (1 + DIM + q) * g.nnodes), dv[q], acc[DIM]);
-      acc[DIM] = fmaf(__ldcs(sp + (1 + 2 * DIM) * g.nnodes), dv[DIM], acc[DIM]);
+          for (int q = 0; q < ND; ++q) dv[q] = db[q];
+          const float vA = sm[0];
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) {
+            acc[q] = fmaf(vA, dv[q], acc[q]);
+            acc[q] = fmaf(sm[(1 + DIM + q) * g.nnodes], dv[DIM], acc[q]);
+          }
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) acc[DIM] = fmaf(sm[(1 + q) * g.nnodes], dv[q], acc[DIM]);
+          acc[DIM] = fmaf(sm[(1 + 2 * DIM) * g.nnodes], dv[DIM], acc[DIM]);
+        }
+      }
     }
     const unsigned char ma = S->mask[node];
     const float* dc = d + pn * ND;

@@ -92,9 +92,9 @@ struct Level {
   float2* xp2 = nullptr;
   float2* bp2 = nullptr;
   // float32 correction form of the V-cycle (float32 / bfloat16 rows): the
-  // stencil in float32 with constrained neighbour columns folded to zero
-  // (levels above the coarsest), the padded correction and the right-hand
-  // side in float32 (every level)
+  // half stencil (zero offset and the offsets after it) in float32 with the
+  // columns of constrained DoFs folded to zero (levels above the coarsest),
+  // the padded correction and the right-hand side in float32 (every level)
   float* st32 = nullptr;
   float* d32 = nullptr;
   float* b32 = nullptr;
@@ -147,6 +147,9 @@ struct fc_handle_s {
   // float32 / bfloat16 rows: the V-cycle runs in the float32 correction form
   // through a batch holding this handle alone (created on first use)
   struct fc_batch_s* self_batch = nullptr;
+  // float32 / bfloat16 rows: patches rebuilt by the float-pair elimination
+  // because float32 refinement did not converge (all levels)
+  long long pair_fallback = 0;
   bool capturing = false;
   fc::Profile prof;
   std::string err;
@@ -205,13 +208,16 @@ cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsig
 // owned rows of the work-list patches by a float-pair factorisation (for
 // rows stored in reduced precision); float64 output like mode 0
 // owned rows of the work-list patches by a float32 factorisation with two
-// steps of iterative refinement (rows stored in float32 / bfloat16)
+// steps of iterative refinement (rows stored in float32 / bfloat16);
+// patches whose refinement did not converge are appended to redo_node
+// (patch) / redo_out (row block), *nredo counting them
 cudaError_t launch_patch_rows_ir(const LevelGeom& g, const double* st, const unsigned char* mask,
                                  double* coef64, unsigned* d_err, const int* work, long long nwork,
-                                 cudaStream_t s);
+                                 int* redo_node, int* redo_out, int* nredo, cudaStream_t s);
+// float-pair elimination; outidx (nullable) maps a work entry to its row block
 cudaError_t launch_patch_rows_pair(const LevelGeom& g, const double* st, const unsigned char* mask,
                                    double* coef64, unsigned* d_err, const int* work, long long nwork,
-                                   cudaStream_t s);
+                                   const int* outidx, cudaStream_t s);
 // prow (nullable = identity) maps a patch to its stored row / factor block
 cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
                                const unsigned char* mask, const double* rpad, const float* rpad32,

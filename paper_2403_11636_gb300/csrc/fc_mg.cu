@@ -229,17 +229,16 @@ __global__ void fold_stencil_pairs_kernel(LevelGeom g, const double* __restrict_
   }
 }
 
-// float32 stencil, all neighbour offsets, with the columns of constrained
-// neighbours folded to zero (A and T_c) and zeros for out-of-grid
-// neighbours, for the float32 correction-form V-cycle
+// float32 half stencil for the float32 correction-form V-cycle: the same
+// own offsets and folding rules as the pair stencil above
 template <int DIM>
 __global__ void fold_stencil_f32_kernel(LevelGeom g, const double* __restrict__ st,
                                         const unsigned char* __restrict__ mask, float* __restrict__ st32) {
-  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2;
+  constexpr int CEN = DIM == 3 ? 13 : 4, NH = half_offsets<DIM>(), SP = 2 * DIM + 2;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.nnodes * NB) return;
+  if (t >= g.nnodes * NH) return;
   const long long node = t % g.nnodes;
-  const int nb = (int)(t / g.nnodes);
+  const int h = (int)(t / g.nnodes), nb = CEN + h;
   int ia[3];
   {
     const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
@@ -248,16 +247,17 @@ __global__ void fold_stencil_f32_kernel(LevelGeom g, const double* __restrict__ 
     ia[1] = DIM == 3 ? (int)(q % ny) : (int)q;
     ia[2] = DIM == 3 ? (int)(q / ny) : 0;
   }
-  int ib0 = ia[0] + nb % 3 - 1, ib1 = ia[1] + (nb / 3) % 3 - 1, ib2 = DIM == 3 ? ia[2] + nb / 9 - 1 : 0;
-  bool inside = !(ib0 < 0 || ib0 > g.n[0] || ib1 < 0 || ib1 > g.n[1]) &&
-                !(DIM == 3 && (ib2 < 0 || ib2 > g.n[2]));
-  bool fixed = inside && (mask[ib0 + (long long)g.nn[0] * (ib1 + (long long)g.nn[1] * ib2)] & 1);
+  const int ib0 = ia[0] + nb % 3 - 1, ib1 = ia[1] + (nb / 3) % 3 - 1, ib2 = DIM == 3 ? ia[2] + nb / 9 - 1 : 0;
+  const bool inside = !(ib0 < 0 || ib0 > g.n[0] || ib1 < 0 || ib1 > g.n[1]) &&
+                      !(DIM == 3 && (ib2 < 0 || ib2 > g.n[2]));
+  const bool own_fixed = mask[node] & 1;
+  const bool nb_fixed = inside && (mask[ib0 + (long long)g.nn[0] * (ib1 + (long long)g.nn[1] * ib2)] & 1);
   for (int e = 0; e < SP; ++e) {
-    const long long k = ((long long)nb * SP + e) * g.nnodes + node;
-    double v = inside ? st[k] : 0.0;
-    const bool velocity_column = (e == 0) || (e >= 1 + DIM && e < 1 + 2 * DIM);
-    if (fixed && velocity_column) v = 0.0;
-    st32[k] = (float)v;
+    double v = inside ? st[((long long)nb * SP + e) * g.nnodes + node] : 0.0;
+    if (e == 0 && (own_fixed || nb_fixed)) v = 0.0;
+    else if (e >= 1 && e <= DIM && own_fixed) v = 0.0;
+    else if (e >= 1 + DIM && e < 1 + 2 * DIM && nb_fixed) v = 0.0;
+    st32[((long long)h * SP + e) * g.nnodes + node] = (float)v;
   }
 }
 
@@ -743,7 +743,7 @@ cudaError_t launch_fold_stencil_pairs(const LevelGeom& g, const double* st, cons
 
 cudaError_t launch_fold_stencil_f32(const LevelGeom& g, const double* st, const unsigned char* mask, float* st32,
                                     cudaStream_t s) {
-  long long n = g.nnodes * (g.dim == 3 ? 27 : 9);
+  long long n = g.nnodes * (g.dim == 3 ? 14 : 5);  // own (half) offsets
   unsigned blocks = (unsigned)((n + 255) / 256);
   if (g.dim == 2) fold_stencil_f32_kernel<2><<<blocks, 256, 0, s>>>(g, st, mask, st32);
   else fold_stencil_f32_kernel<3><<<blocks, 256, 0, s>>>(g, st, mask, st32);

@@ -1332,7 +1332,7 @@ template <int DIM>
 __global__ void __launch_bounds__(1024)
     patch_factor_pair_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
                              double* __restrict__ coef, unsigned* __restrict__ d_err,
-                             const int* __restrict__ work) {
+                             const int* __restrict__ work, const int* __restrict__ outidx) {
   using P = PatchDims<DIM>;
   constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP;
   constexpr int NC = DIM * NP + 1;  // B columns and e_centre
@@ -1499,7 +1499,7 @@ __global__ void __launch_bounds__(1024)
     lu_solve_vec_pair(S, NP, pivS, z);
   }
   __syncthreads();
-  double* out = coef + widx * P::NSLOT * ND;
+  double* out = coef + (outidx ? (long long)outidx[widx] : widx) * P::NSLOT * ND;
   for (int j = tid; j < P::NSLOT; j += nt) {
     double vals[ND];
     if (j < NU * DIM) {
@@ -1540,12 +1540,15 @@ __global__ void __launch_bounds__(1024)
 // exact entries, z_k += M~^{-1} r.  Each step multiplies the error by about
 // cond(M~) x 2^-24, so the rows reach float64-class accuracy before they are
 // rounded to float32 / bfloat16, at a fraction of the cost of float-pair
-// elimination.
+// elimination.  Where cond(M~) x 2^-24 is not small the refinement does not
+// converge; such patches are listed (redo_node / redo_out) for the
+// float-pair elimination.
 template <int DIM>
 __global__ void __launch_bounds__(1024)
     patch_factor_ir_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
                            double* __restrict__ coef, unsigned* __restrict__ d_err,
-                           const int* __restrict__ work) {
+                           const int* __restrict__ work, int* __restrict__ redo_node, int* __restrict__ redo_out,
+                           int* __restrict__ nredo) {
   using P = PatchDims<DIM>;
   constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP, NSLOT = P::NSLOT;
   constexpr int NT = DIM == 3 ? 27 : 9;   // 3^d neighbour offsets
@@ -1578,6 +1581,7 @@ __global__ void __launch_bounds__(1024)
   unsigned char* ap = au + NU;
   __shared__ int s_flag;
   __shared__ float s_scal[2];
+  __shared__ int s_rmax;  // largest |residual| of the last refinement (float bits)
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long widx = blockIdx.x;
   const long long i = work ? work[widx] : widx;
@@ -1753,9 +1757,11 @@ __global__ void __launch_bounds__(1024)
       Zv[e] = pr_add(Zv[e], {u, 0.0f});
     }
     for (int e = tid; e < ND * NP; e += nt) Zp[e] = pr_add(Zp[e], {Hp[e], 0.0f});
+    if (tid == 0) s_rmax = 0;
     __syncthreads();
-    if (pass == NPASS - 1) break;
-    // residual e_k - M~ z in float pairs from the sparse entries
+    // residual e_k - M~ z in float pairs from the sparse entries (after the
+    // last solve it only measures convergence)
+    float rmax = 0.0f;
     for (int e = tid; e < NV * NU; e += nt) {
       const int col = e / NU, v = e - col * NU, k = col / DIM, c = col - k * DIM;
       pr sv = {(k < DIM && c == k && v == v0) ? 1.0f : 0.0f, 0.0f};
@@ -1777,6 +1783,7 @@ __global__ void __launch_bounds__(1024)
         sv = pr_fms(sv, Bsp[(q * NT + tq) * DIM + c], Zp[k * NP + q]);
       }
       Rv[e] = sv.h + sv.l;
+      rmax = fmaxf(rmax, fabsf(sv.h));
     }
     for (int e = tid; e < ND * NP; e += nt) {
       const int k = e / NP, p = e - k * NP;
@@ -1793,8 +1800,21 @@ __global__ void __launch_bounds__(1024)
         sv = pr_fms(sv, Csp[p * NT + t], Zp[k * NP + q]);
       }
       Rp[e] = sv.h + sv.l;
+      rmax = fmaxf(rmax, fabsf(sv.h));
     }
+    // a NaN compares false everywhere: count it as no convergence
+    if (rmax != rmax) rmax = 3.0e38f;
+    atomicMax(&s_rmax, __float_as_int(rmax));
     __syncthreads();
+  }
+  // Refinement that did not bring the residual of the unit right-hand sides
+  // below 1e-9 (an equilibrated block too ill-conditioned for float32
+  // factors, typically a badly cut patch): the patch goes on the list that
+  // the float-pair elimination rebuilds afterwards.
+  if (tid == 0 && nredo && s_rmax > __float_as_int(1.0e-9f)) {
+    const int slot = atomicAdd(nredo, 1);
+    redo_node[slot] = (int)i;
+    redo_out[slot] = (int)widx;
   }
   // owned rows of L_i^{-1} = D z_k D, in the slot layout
   double* out = coef + widx * NSLOT * ND;
@@ -1832,7 +1852,8 @@ size_t ir_factor_smem() {
 
 template <int DIM>
 cudaError_t run_ir_factor(const LevelGeom& g, const double* st, const unsigned char* mask, double* coef,
-                          unsigned* d_err, const int* work, long long nwork, cudaStream_t s) {
+                          unsigned* d_err, const int* work, long long nwork, int* redo_node, int* redo_out,
+                          int* nredo, cudaStream_t s) {
   const size_t sm = ir_factor_smem<DIM>();
   auto kern = patch_factor_ir_kernel<DIM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1844,7 +1865,7 @@ cudaError_t run_ir_factor(const LevelGeom& g, const double* st, const unsigned c
     const int t = atoi(env);
     if (t >= 64 && t <= 1024 && t % 32 == 0) threads = t;
   }
-  kern<<<(unsigned)nb, threads, sm, s>>>(g, st, mask, coef, d_err, work);
+  kern<<<(unsigned)nb, threads, sm, s>>>(g, st, mask, coef, d_err, work, redo_node, redo_out, nredo);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -1861,7 +1882,8 @@ size_t pair_factor_smem() {
 
 template <int DIM>
 cudaError_t run_pair_factor(const LevelGeom& g, const double* st, const unsigned char* mask, double* coef,
-                            unsigned* d_err, const int* work, long long nwork, cudaStream_t s) {
+                            unsigned* d_err, const int* work, long long nwork, const int* outidx,
+                            cudaStream_t s) {
   size_t sm = pair_factor_smem<DIM>();
   auto kern = patch_factor_pair_kernel<DIM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1873,7 +1895,7 @@ cudaError_t run_pair_factor(const LevelGeom& g, const double* st, const unsigned
     int t = atoi(env);
     if (t >= 64 && t <= 1024 && t % 32 == 0) threads = t;
   }
-  kern<<<(unsigned)nb, threads, sm, s>>>(g, st, mask, coef, d_err, work);
+  kern<<<(unsigned)nb, threads, sm, s>>>(g, st, mask, coef, d_err, work, outidx);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -1899,16 +1921,16 @@ cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsig
 
 cudaError_t launch_patch_rows_ir(const LevelGeom& g, const double* st, const unsigned char* mask,
                                  double* coef64, unsigned* d_err, const int* work, long long nwork,
-                                 cudaStream_t s) {
-  if (g.dim == 2) return run_ir_factor<2>(g, st, mask, coef64, d_err, work, nwork, s);
-  return run_ir_factor<3>(g, st, mask, coef64, d_err, work, nwork, s);
+                                 int* redo_node, int* redo_out, int* nredo, cudaStream_t s) {
+  if (g.dim == 2) return run_ir_factor<2>(g, st, mask, coef64, d_err, work, nwork, redo_node, redo_out, nredo, s);
+  return run_ir_factor<3>(g, st, mask, coef64, d_err, work, nwork, redo_node, redo_out, nredo, s);
 }
 
 cudaError_t launch_patch_rows_pair(const LevelGeom& g, const double* st, const unsigned char* mask,
                                    double* coef64, unsigned* d_err, const int* work, long long nwork,
-                                   cudaStream_t s) {
-  if (g.dim == 2) return run_pair_factor<2>(g, st, mask, coef64, d_err, work, nwork, s);
-  return run_pair_factor<3>(g, st, mask, coef64, d_err, work, nwork, s);
+                                   const int* outidx, cudaStream_t s) {
+  if (g.dim == 2) return run_pair_factor<2>(g, st, mask, coef64, d_err, work, nwork, outidx, s);
+  return run_pair_factor<3>(g, st, mask, coef64, d_err, work, nwork, outidx, s);
 }
 
 cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,

@@ -320,3 +320,25 @@ def test_float32_vcycle_error(fc, name, prec):
     got = s.vcycle(x0, b).cpu().numpy()
     err = rel(got - x0, want - x0)
     assert err <= (2e-5 if prec == "fp32" else 2e-2), err
+
+
+def test_float32_build_falls_back_on_ill_conditioned_patches(fc):
+    """Float32 / bfloat16 rows come from a float32 factorisation with
+    iterative refinement; where the refinement cannot converge (an
+    equilibrated block too ill-conditioned for float32 factors, here a badly
+    cut patch of an alpha = 1e-10 geometry) the patch is rebuilt by the
+    float-pair elimination.  Every stored row then matches the float-pair
+    build of the same problem to float32 rounding."""
+    p = inputs.batch_2d(63)
+    s32 = fc.Solver(p, prec="fp32")
+    sdf = fc.Solver(p, prec="df64")
+    assert s32.info()["bytes"][5] >= 1          # at least one patch fell back
+    nn = (p.n[0] + 1) * (p.n[1] + 1)
+    for node in [1583, 1518, 1519, 1648, 7, nn // 2]:
+        a, b = s32.patch_rows(node), sdf.patch_rows(node)
+        den = np.abs(b).max()
+        assert den == 0 or np.abs(a - b).max() <= 2e-7 * den, node
+    # same iteration count as the float-pair rows
+    _, i32, r32 = s32.solve(s32.rhs(), rtol=1e-8, maxit=400)
+    _, idf, _ = sdf.solve(sdf.rhs(), rtol=1e-8, maxit=400)
+    assert r32 <= 1e-8 and abs(i32 - idf) <= 1
