@@ -108,16 +108,35 @@ __device__ __forceinline__ void dfacc(dfp& acc, float2 a, float2 b) {
 template <int DIM>
 __device__ __forceinline__ constexpr int half_offsets() { return (DIM == 3 ? 27 : 9) - (DIM == 3 ? 13 : 4); }
 
-// float-pair residual on the half stencil, one thread per node; own
-// entries of out-of-grid neighbours are stored as zero and x has a zero
-// halo, mirrored entries are read only from neighbours inside the grid
-template <int DIM>
+// sum of two running pair sums (high parts by an exact two-sum, low parts
+// plainly); symmetric in its arguments, so both lanes of a shuffle pair get
+// the same result
+__device__ __forceinline__ dfp dfp_join(dfp a, dfp b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  return {s, e + (a.lo + b.lo)};
+}
+
+// float-pair residual on the half stencil, TPP lanes per node: lane l takes
+// the half-stencil offsets l, l + TPP, ... (own and mirrored entries), the
+// group adds its partial sums by shuffles.  TPP = 1 on large levels; small levels, where one
+// thread per node leaves most SMs idle and each thread walks all 27
+// neighbours' loads in turn, take a group.  Own entries of out-of-grid
+// neighbours are stored as zero and x has a zero halo, mirrored entries are
+// read only from neighbours inside the grid.
+template <int DIM, int TPP>
 __global__ void __launch_bounds__(256)
     residual_df2_kernel(LevelGeom g, const float2* __restrict__ sth, const unsigned char* __restrict__ mask,
                         const float2* __restrict__ xp2, const float2* __restrict__ b2,
                         float2* __restrict__ rpad2, double* __restrict__ r) {
   constexpr int CEN = DIM == 3 ? 13 : 4, NH = half_offsets<DIM>(), SP = 2 * DIM + 2, ND = DIM + 1;
-  const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = (int)(gid % TPP);
+  // a group past the last node leaves as a whole; groups are aligned runs
+  // of TPP lanes of one warp and shuffle within their own lanes only
+  const unsigned gmask = TPP == 32 ? 0xffffffffu : ((1u << TPP) - 1u) << ((threadIdx.x & 31) & ~(TPP - 1));
+  const long long node = gid / TPP;
   if (node >= g.nnodes) return;
   int ia[3];
   {
@@ -133,8 +152,12 @@ __global__ void __launch_bounds__(256)
   dfp acc[ND];
 #pragma unroll
   for (int c = 0; c < ND; ++c) acc[c] = {0.0f, 0.0f};
+  // every lane of a group runs the same iterations (offset k TPP + lane)
+  constexpr int NIT = (NH + TPP - 1) / TPP;
 #pragma unroll
-  for (int h = 0; h < NH; ++h) {
+  for (int k = 0; k < NIT; ++k) {
+    const int h = TPP == 1 ? k : k * TPP + lane;
+    if (TPP > 1 && h >= NH) break;
     const int nb = CEN + h;
     const int d0 = nb % 3 - 1, d1 = (nb / 3) % 3 - 1, d2 = DIM == 3 ? nb / 9 - 1 : 0;
     const int off = d0 + px * (d1 + (DIM == 3 ? py * d2 : 0));
@@ -170,9 +193,17 @@ __global__ void __launch_bounds__(256)
       }
     }
   }
+#pragma unroll
+  for (int o = TPP / 2; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < ND; ++c) {
+      const dfp other = {__shfl_xor_sync(gmask, acc[c].hi, o), __shfl_xor_sync(gmask, acc[c].lo, o)};
+      acc[c] = dfp_join(acc[c], other);
+    }
   const unsigned char ma = mask[node];
 #pragma unroll
   for (int c = 0; c < ND; ++c) {
+    if (TPP > 1 && c % TPP != lane) continue;
     float yh = acc[c].hi + acc[c].lo;
     float yl = acc[c].lo - (yh - acc[c].hi);
     if (c < DIM && ((ma >> c) & 1)) {
@@ -722,11 +753,20 @@ cudaError_t launch_split_pairs(long long n, const double* in, float2* out, cudaS
 cudaError_t launch_residual_df2(const LevelGeom& g, const float2* st2, const unsigned char* mask,
                                 const float2* xp2, const float2* b2, float2* rpad2, double* r,
                                 cudaStream_t s) {
-  // one thread per node (splitting the neighbours over a group of lanes
-  // measured slower: 0.134 vs 0.111 ms at 64^3 on the full stencil)
-  unsigned blocks = (unsigned)((g.nnodes + 255) / 256);
-  if (g.dim == 2) residual_df2_kernel<2><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
-  else residual_df2_kernel<3><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+  // one thread per node where the level fills the GPU (a group of lanes
+  // per node measured slower there: 0.134 vs 0.111 ms at 64^3 on the full
+  // stencil); on levels below about two 256-thread blocks per SM a group of
+  // 16 (3D) or 8 (2D) lanes, one half-stencil offset per lane
+  const bool small = g.nnodes < 152LL * 512;
+  const int tpp = small ? (g.dim == 3 ? 16 : 8) : 1;
+  const unsigned blocks = (unsigned)((g.nnodes * tpp + 255) / 256);
+  if (g.dim == 2) {
+    if (small) residual_df2_kernel<2, 8><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+    else residual_df2_kernel<2, 1><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+  } else {
+    if (small) residual_df2_kernel<3, 16><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+    else residual_df2_kernel<3, 1><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+  }
   note_launches(1);
   return cudaGetLastError();
 }
