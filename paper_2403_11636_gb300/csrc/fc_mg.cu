@@ -131,12 +131,17 @@ __global__ void __launch_bounds__(256)
                         const float2* __restrict__ xp2, const float2* __restrict__ b2,
                         float2* __restrict__ rpad2, double* __restrict__ r) {
   constexpr int CEN = DIM == 3 ? 13 : 4, NH = half_offsets<DIM>(), SP = 2 * DIM + 2, ND = DIM + 1;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = (int)(gid % TPP);
-  // a group past the last node leaves as a whole; groups are aligned runs
-  // of TPP lanes of one warp and shuffle within their own lanes only
-  const unsigned gmask = TPP == 32 ? 0xffffffffu : ((1u << TPP) - 1u) << ((threadIdx.x & 31) & ~(TPP - 1));
-  const long long node = gid / TPP;
+  // a warp covers W = 32 / TPP consecutive nodes; warp lane w takes node
+  // w % W and offset slot w / W, so the lanes of one slot read W consecutive
+  // nodes of each stencil plane.  A node's group (the lanes w % W equal)
+  // leaves as a whole past the last node and shuffles among its own lanes.
+  constexpr int W = 32 / TPP;
+  const int wl = threadIdx.x & 31;
+  const int lane = wl / W;
+  const long long node = ((long long)blockIdx.x * blockDim.x + (threadIdx.x - wl)) / TPP + wl % W;
+  unsigned gmask = 0u;
+#pragma unroll
+  for (int j = 0; j < TPP; ++j) gmask |= 1u << (wl % W + W * j);
   if (node >= g.nnodes) return;
   int ia[3];
   {
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(256)
   for (int o = TPP / 2; o > 0; o >>= 1)
 #pragma unroll
     for (int c = 0; c < ND; ++c) {
-      const dfp other = {__shfl_xor_sync(gmask, acc[c].hi, o), __shfl_xor_sync(gmask, acc[c].lo, o)};
+      const dfp other = {__shfl_xor_sync(gmask, acc[c].hi, o * W), __shfl_xor_sync(gmask, acc[c].lo, o * W)};
       acc[c] = dfp_join(acc[c], other);
     }
   const unsigned char ma = mask[node];
@@ -753,19 +758,22 @@ cudaError_t launch_split_pairs(long long n, const double* in, float2* out, cudaS
 cudaError_t launch_residual_df2(const LevelGeom& g, const float2* st2, const unsigned char* mask,
                                 const float2* xp2, const float2* b2, float2* rpad2, double* r,
                                 cudaStream_t s) {
-  // one thread per node where the level fills the GPU (a group of lanes
-  // per node measured slower there: 0.134 vs 0.111 ms at 64^3 on the full
-  // stencil); on levels below about two 256-thread blocks per SM a group of
-  // 16 (3D) or 8 (2D) lanes, one half-stencil offset per lane
-  const bool small = g.nnodes < 152LL * 512;
-  const int tpp = small ? (g.dim == 3 ? 16 : 8) : 1;
-  const unsigned blocks = (unsigned)((g.nnodes * tpp + 255) / 256);
+  // lanes per node by level size (3D, GB300, ms per launch for 1 / 8 / 16
+  // lanes): 64^3 nodes 0.087 / 0.131 / 0.170, 32^3 0.029 / 0.021 / 0.026,
+  // 16^3 0.029 / 0.012 / 0.010.  One thread per node where the level fills
+  // the GPU, a group where it leaves most SMs idle.
+  const long long nn = g.nnodes;
+  const int tpp = nn >= 152LL * 512 ? 1 : g.dim == 2 ? 8 : nn >= 152LL * 128 ? 8 : 16;
+  const unsigned blocks = (unsigned)((nn * tpp + 255) / 256);
   if (g.dim == 2) {
-    if (small) residual_df2_kernel<2, 8><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
-    else residual_df2_kernel<2, 1><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+    if (tpp == 1) residual_df2_kernel<2, 1><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+    else residual_df2_kernel<2, 8><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+  } else if (tpp == 1) {
+    residual_df2_kernel<3, 1><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+  } else if (tpp == 8) {
+    residual_df2_kernel<3, 8><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
   } else {
-    if (small) residual_df2_kernel<3, 16><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
-    else residual_df2_kernel<3, 1><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
+    residual_df2_kernel<3, 16><<<blocks, 256, 0, s>>>(g, st2, mask, xp2, b2, rpad2, r);
   }
   note_launches(1);
   return cudaGetLastError();
