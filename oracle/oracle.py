@@ -9,6 +9,10 @@ A ``Level`` is one uniform background grid of the multigrid hierarchy
 and FGMRES.  Problems are passed in duck-typed (any object with the fields
 dim, n, lo, hi, shapes, alpha, qdepth, nlevels, eta, beta, omega, nu_pre,
 nu_post, preset, force_kind, force, ubar).
+
+The environment variable FC_ORACLE_LIB, when set, names another build of
+fc_oracle.c to load instead of the one built here; the planted-mistake
+tests use it to run the pins against altered copies of the oracle.
 """
 from __future__ import annotations
 
@@ -29,14 +33,20 @@ PMAX = 402
 OMAX = 4
 
 
+def compile_source(src: str, out: str) -> None:
+    """gcc of one oracle source into a shared library (plain C, OpenMP, no FP
+    contraction)."""
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+           "-shared", "-o", out, src, "-lm"]
+    subprocess.check_call(cmd)
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C, OpenMP, no FP contraction)."""
+    """Compile fc_oracle.c next to this file (when it changed)."""
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
-            cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
-                   "-shared", "-o", tmp, _SRC, "-lm"]
-            subprocess.check_call(cmd)
+            compile_source(_SRC, tmp)
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -45,8 +55,12 @@ def _load():
     global _lib
     if _lib is not None:
         return _lib
-    build()
-    lib = C.CDLL(_LIB)
+    alt = os.environ.get("FC_ORACLE_LIB")
+    if alt:
+        lib = C.CDLL(alt)
+    else:
+        build()
+        lib = C.CDLL(_LIB)
     vp, d, i, l = C.c_void_p, C.c_double, C.c_int, C.c_long
     P = C.POINTER
     lib.or_level_new.restype = vp

@@ -395,6 +395,32 @@ def test_restriction_is_transpose_of_prolongation(dim):
     assert abs(lhs - rhs) <= 1e-13 * (np.abs(r).sum())
 
 
+@pytest.mark.parametrize("dim,preset", [(2, 0), (2, 1), (3, 0), (3, 1)])
+def test_restriction_with_strong_dirichlet_rows(dim, preset):
+    """With strong Dirichlet data the coarse correction lives in the space of
+    coarse functions that vanish on the constrained DoFs (Sec. 3): R r is
+    exactly zero there, and on the free DoFs R = P^T for every fine residual
+    that vanishes on the constrained fine DoFs (a smoothed residual, whose
+    identity rows are satisfied): <R r, e> = <r, P e> for every coarse e that
+    vanishes on the constrained coarse DoFs."""
+    C = level(dim, 4, None, preset=preset)
+    F = level(dim, 8, None, preset=preset)
+    C.assemble()
+    F.assemble()
+    fixc, fixf = C.csr()[2], F.csr()[2]
+    assert fixc.any() and fixf.any() and not fixc.all()
+    r = inputs.uniform_array(F.ndof, 7)
+    r[fixf] = 0.0
+    e = inputs.uniform_array(C.ndof, 8)
+    e[fixc] = 0.0
+    rc = O.restrict(F, C, r)
+    assert np.all(rc[fixc] == 0.0)
+    assert np.any(rc[~fixc] != 0.0)
+    lhs = rc @ e
+    rhs = r @ O.prolong_add(F, C, e, np.zeros(F.ndof))
+    assert abs(lhs - rhs) <= 1e-13 * (np.abs(r).sum())
+
+
 # ---------------------------------------------------------------- discretisation
 def test_manufactured_2d_channel_convergence():
     """Poiseuille flow plus a pressure field balanced by the body force,
