@@ -118,9 +118,61 @@ MUTANTS = [
      0, "test_fgmres_reaches_direct_solution[2]"),
     ("hessenberg_transposed", "for (int t = i + 1; t < k; ++t) s = s - H[i * m + t] * y[t];",
      "for (int t = i + 1; t < k; ++t) s = s - H[t * m + i] * y[t];", 0, "test_fgmres_reaches_direct_solution[2]"),
-    # strong Dirichlet data: the channel inflow profile
+    # strong Dirichlet data of the two setups
     ("inflow_profile_scale", "double v = 4.0 * L->ubar * s * (1.0 - s);", "double v = L->ubar * s * (1.0 - s);", 0,
      "test_manufactured_2d_channel_convergence"),
+    ("inflow_all_components", "if (!wall && inflow && c == 0) {", "if (!wall && inflow) {", 0,
+     "test_manufactured_2d_channel_convergence"),
+    ("channel_upper_wall_missing", "int wall = (idx[1] == 0 || idx[1] == L->n[1]);", "int wall = (idx[1] == 0);", 0,
+     "test_presets_constrain_the_faces_of_the_setups[2-0]"),
+    ("porous_upper_wall_missing", "int wall = (idx[1] == 0 || idx[1] == L->n[1]);", "int wall = (idx[1] == 0);", 1,
+     "test_presets_constrain_the_faces_of_the_setups[2-1]"),
+    # level set and alpha (Sec. 2)
+    ("ellipse_rotation_sign", "double yp = -s->rot[1] * dx + s->rot[0] * dy;",
+     "double yp = s->rot[1] * dx + s->rot[0] * dy;", 0, "test_ellipse_area"),
+    ("circle_sqrt_dropped", "return s->r[0] - sqrt(q);", "return s->r[0] - q;", 0,
+     "test_fluid_volume_converges_with_depth[2]"),
+    ("union_as_intersection", "if (s == 0 || q > p) p = q;", "if (s == 0 || q < p) p = q;", 0,
+     "test_overlapping_obstacles_form_a_union"),
+    ("alpha_swapped", "return phi_all(L, x) > 0.0 ? L->alpha : 1.0;", "return phi_all(L, x) > 0.0 ? 1.0 : L->alpha;",
+     0, "test_uncut_element_matrices_closed_form[True-2]"),
+    ("sample_points_quarter", "double x[3] = {lo[0] + hb[0] * (0.5 * i), lo[1] + hb[1] * (0.5 * j),",
+     "double x[3] = {lo[0] + hb[0] * (0.25 * i), lo[1] + hb[1] * (0.25 * j),", 0,
+     "test_fluid_volume_converges_with_depth[3]"),
+    ("stabilisation_gauss_weight", "for (int k = 0; k < dim; ++k) w = w * (L->h[k] * 0.5);",
+     "for (int k = 0; k < dim; ++k) w = w * L->h[k];", 0, "test_uncut_element_matrices_closed_form[True-2]"),
+    # body force
+    ("force_cos_as_sin", "f[1] = L->force[1] * cos(pi * x[1]);", "f[1] = L->force[1] * sin(pi * x[1]);", 0,
+     "test_load_vector_channel_force"),
+    ("force_z_factor_dropped", "if (L->dim == 3) f[0] = f[0] * sin(pi * x[2]);", "", 0,
+     "test_manufactured_3d_duct_convergence"),
+    # boundary rule, more
+    ("sphere_weight_radius", "double w = r * r * (0.5 * dm) * df;", "double w = r * (0.5 * dm) * df;", 0,
+     "test_boundary_rule_exact_integrals[3-sphere]"),
+    ("ellipse_normal_axes", "double nx = b * ct, ny = a * st;", "double nx = a * ct, ny = b * st;", 0,
+     "test_boundary_rule_exact_integrals[2-ellipse]"),
+    ("boundary_point_other_shape_kept", "if (!ok || point_in_other_shape(L, s, x)) continue;", "if (!ok) continue;",
+     0, "test_overlapping_obstacles_form_a_union"),
+    # assembly of the rows of L and of the residual
+    ("coupling_transposed", "else if (cb < dim) v = e->B[cb][lb][la];", "else if (cb < dim) v = e->B[cb][la][lb];",
+     0, "test_operator_exactly_symmetric[2-0]"),
+    ("velocity_components_coupled", "if (ca < dim && cb < dim) v = (ca == cb) ? e->A[la][lb] : 0.0;",
+     "if (ca < dim && cb < dim) v = e->A[la][lb];", 0, "test_manufactured_2d_channel_convergence"),
+    ("lift_sign", "rhs = rhs - out[nb * nd + cb] * wb;", "rhs = rhs + out[nb * nd + cb] * wb;", 0,
+     "test_manufactured_2d_channel_convergence"),
+    ("constrained_column_kept", "        rhs = rhs - out[nb * nd + cb] * wb;\n        out[nb * nd + cb] = 0.0;",
+     "        rhs = rhs - out[nb * nd + cb] * wb;", 0, "test_operator_exactly_symmetric[2-0]"),
+    ("residual_sign", "for (long i = 0; i < L->ndof; ++i) r[i] = b[i] - r[i];",
+     "for (long i = 0; i < L->ndof; ++i) r[i] = r[i] - b[i];", 0, "test_fgmres_reaches_direct_solution[2]"),
+    ("pressure_not_owned", "if (nb == node) own[dim] = n;", ";", 0, "test_owner_count_is_one[2]"),
+    # coarse solve and FGMRES, more
+    ("coarse_solve_unequilibrated_rhs", "eq_solve((int)L->ndof, M->coarse_lu, M->coarse_d, M->coarse_piv, t);",
+     "lu_solve((int)L->ndof, M->coarse_lu, M->coarse_piv, t);", 0, "test_standalone_gmg_reduces_residual"),
+    ("fgmres_restart_residual_sign", "for (long i = 0; i < n; ++i) V[i] = w[i] / beta;",
+     "for (long i = 0; i < n; ++i) V[i] = -w[i] / beta;", 0, "test_fgmres_reaches_direct_solution[2]"),
+    ("fgmres_update_uses_v", "for (long t = 0; t < n; ++t) x[t] = x[t] + y[i] * Z[(long)i * n + t];",
+     "for (long t = 0; t < n; ++t) x[t] = x[t] + y[i] * V[(long)i * n + t];", 0,
+     "test_fgmres_reaches_direct_solution[2]"),
 ]
 
 

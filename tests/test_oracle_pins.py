@@ -144,6 +144,55 @@ def test_ellipse_area():
     assert abs(vf - (1.0 - math.pi * a * b)) < 2 * math.pi * a * (1.0 / 16) / 2 ** 5
 
 
+def test_overlapping_obstacles_form_a_union():
+    """Several obstacles: the fictitious part is the union of the shapes
+    (phi = max over shapes, Sec. 2), and the boundary rule keeps only the
+    parts of each curve outside the other obstacles, so the fluid measure is
+    1 - |union| and the boundary weights add up to the union's perimeter.  Two
+    circles of radius r at distance d < 2 r: |union| = 2 pi r^2 - lens,
+    lens = 2 r^2 acos(d / 2r) - (d / 2) sqrt(4 r^2 - d^2), perimeter
+    4 r (pi - acos(d / 2r))."""
+    r, c1, c2 = 0.18, (0.40, 0.50), (0.62, 0.52)
+    d = math.hypot(c2[0] - c1[0], c2[1] - c1[1])
+    th = math.acos(d / (2 * r))
+    union = 2 * math.pi * r * r - (2 * r * r * th - 0.5 * d * math.sqrt(4 * r * r - d * d))
+    perim = 4 * r * (math.pi - th)
+    n, k = 16, 5
+    L = level(2, n, np.vstack([circle(*c1, r), circle(*c2, r)]), qdepth=k)
+    vf = sum(L.cell_element(cc)["fluid_volume"] for cc in range(L.ncell))
+    assert abs(vf - (1.0 - union)) < perim * (1.0 / n) / 2 ** k
+    x, nrm, w, cell = L.bpoints()
+    # four rule intervals straddle the two intersection points at most
+    npts = 8 * math.ceil(2 * math.pi * r * n) * 2 ** k
+    assert abs(w.sum() - perim) <= 4 * (2 * math.pi * r / npts)
+    # divergence theorem over the union, n pointing out of the fluid
+    xn = (w * ((x[:, :2] - np.array(c1)) * nrm[:, :2]).sum(axis=1)).sum()
+    assert abs(xn + 2 * union) < 4 * (2 * math.pi * r / npts) * 2 * r
+
+
+@pytest.mark.parametrize("dim,preset", [(2, 0), (2, 1), (3, 0), (3, 1)])
+def test_presets_constrain_the_faces_of_the_setups(dim, preset):
+    """Strong Dirichlet data of the two setups (Sec. 4): no-slip velocity on
+    the walls y = lo, hi (and z = lo, hi), and for the channel also the
+    inflow face x = lo; the outflow face x = hi stays free (natural
+    condition) and the pressure is never constrained.  Wall values are zero."""
+    n = 6
+    L = level(dim, n, None, preset=preset)
+    L.assemble()
+    _, rhs, fixed = L.csr()
+    nd = dim + 1
+    idx = np.indices((n + 1,) * dim).reshape(dim, -1)[::-1]   # x fastest
+    wall = (idx[1] == 0) | (idx[1] == n)
+    if dim == 3:
+        wall |= (idx[2] == 0) | (idx[2] == n)
+    want = wall | (idx[0] == 0) if preset == 0 else wall
+    fixed = fixed.reshape(-1, nd)
+    for c in range(dim):
+        np.testing.assert_array_equal(fixed[:, c], want)
+    assert not fixed[:, dim].any()
+    assert np.all(rhs.reshape(-1, nd)[wall, :dim] == 0.0)
+
+
 def test_load_vector_channel_force():
     """f(v) = (v, alpha f) for f = (sin(pi x), cos(pi y)) on an uncut cell
     equals an adaptive 2D quadrature of f_c times the Q1 nodal function."""
