@@ -156,6 +156,20 @@ def emit(d):
     print(json.dumps(d), flush=True)
 
 
+def reduce_over_ranks(dist, device, times, counts):
+    """Whole-job aggregates of independent per-rank runs: the maximum over
+    ranks of each timing and the sum over ranks of each count (identity
+    without a process group).  Returns (times, counts) as lists of floats."""
+    if dist is None:
+        return [float(v) for v in times], [float(v) for v in counts]
+    import torch
+    t = torch.tensor([float(v) for v in times], dtype=torch.float64, device=device)
+    c = torch.tensor([float(v) for v in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return t.tolist(), c.tolist()
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -247,16 +261,8 @@ def run_ours(args, rank, world, local_rank):
             variants = policy_sweeps(prob, stream, args)
     my_updates = sum(updates_per_solve(prob, i) for i in its_list)
     my_e2e_updates = updates_per_solve(prob, its_h) * len(e2e_t)
-    t = torch.tensor([total_ms, sum(e2e_t) * 1e3, float(my_updates), float(my_e2e_updates)], device="cuda",
-                     dtype=torch.float64)
-    if dist:
-        mx = t.clone()
-        dist.all_reduce(mx[:2], op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm[2:], op=dist.ReduceOp.SUM)
-        total_ms, e2e_ms, all_updates, all_e2e = mx[0].item(), mx[1].item(), sm[2].item(), sm[3].item()
-    else:
-        e2e_ms, all_updates, all_e2e = sum(e2e_t) * 1e3, float(my_updates), float(my_e2e_updates)
+    (total_ms, e2e_ms), (all_updates, all_e2e) = reduce_over_ranks(
+        dist, "cuda", [total_ms, sum(e2e_t) * 1e3], [my_updates, my_e2e_updates])
     if rank != 0:
         if dist:
             dist.destroy_process_group()
