@@ -34,6 +34,39 @@ class FcError(RuntimeError):
         self.code = code
 
 
+def _describe(t) -> str:
+    if hasattr(t, "dtype") and hasattr(t, "shape"):
+        dev = getattr(t, "device", "host")
+        return f"{type(t).__name__} {tuple(t.shape)} {t.dtype} on {dev}"
+    return type(t).__name__
+
+
+def check_device_vector(torch, t, n: int, device: int, name: str):
+    """The library reads or writes exactly n float64 values at a device
+    pointer: anything else is rejected here, before the pointer reaches a
+    kernel (a host pointer, a short vector or another GPU's memory would be
+    an illegal access on the device)."""
+    ok = (torch.is_tensor(t) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+          and t.numel() == n and (t.device.index if t.device.index is not None else 0) == device)
+    if not ok:
+        raise FcError(FC_ERR_INVALID, f"{name}: expected a contiguous float64 tensor of {n} values on "
+                                      f"cuda:{device}, got {_describe(t)}")
+    return t
+
+
+def check_host_vector(torch, a, n: int, name: str, writable: bool = False):
+    """A host buffer of exactly n contiguous float64 values (numpy array or
+    CPU tensor, pinned or not); ``writable`` for a buffer the call fills."""
+    if torch.is_tensor(a):
+        ok = (not a.is_cuda) and a.dtype == torch.float64 and a.is_contiguous() and a.numel() == n
+    else:
+        ok = (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+              and a.size == n and (a.flags["WRITEABLE"] or not writable))
+    if not ok:
+        raise FcError(FC_ERR_INVALID, f"{name}: expected {n} contiguous float64 host values, got {_describe(a)}")
+    return a
+
+
 class FcShape(C.Structure):
     _fields_ = [("type", C.c_int), ("c", C.c_double * 3), ("r", C.c_double * 3),
                 ("rot", C.c_double * 2)]
@@ -168,6 +201,8 @@ class Solver:
         self.nlevels = prob.nlevels
         self.cache, self.prec = cache, prec
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = torch.cuda.current_device()
+        self._sizes = {}
         shapes = np.asarray(prob.shapes, dtype=np.float64).reshape(-1, 9)
         arr = (FcShape * max(1, len(shapes)))()
         for s, row in enumerate(shapes):
@@ -202,10 +237,12 @@ class Solver:
             pass
 
     def ndof(self, level=None) -> int:
-        n = C.c_longlong()
-        self._check(self.lib.fc_info(self.h, self.nlevels if level is None else level,
-                                     C.byref(n), None, None))
-        return n.value
+        lv = self.nlevels if level is None else int(level)
+        if lv not in self._sizes:
+            n = C.c_longlong()
+            self._check(self.lib.fc_info(self.h, lv, C.byref(n), None, None))
+            self._sizes[lv] = n.value
+        return self._sizes[lv]
 
     def info(self, level=None):
         n, p = C.c_longlong(), C.c_longlong()
@@ -215,11 +252,17 @@ class Solver:
         return {"ndof": n.value, "npatch": p.value, "bytes": list(parts)}
 
     def zeros(self, level=None):
-        return self.torch.zeros(self.ndof(level), dtype=self.torch.float64, device="cuda")
+        return self.torch.zeros(self.ndof(level), dtype=self.torch.float64, device=f"cuda:{self.device}")
 
-    def _dev(self, v):
+    def _dev(self, v, level, name):
+        """A contiguous float64 copy (or view) of v on this solver's GPU,
+        checked to hold the level's DoF count."""
         t = v if self.torch.is_tensor(v) else self.torch.as_tensor(np.asarray(v, dtype=np.float64))
-        return t.to(device="cuda", dtype=self.torch.float64).contiguous()
+        t = t.to(device=f"cuda:{self.device}", dtype=self.torch.float64).contiguous()
+        return self._need(t, level, name)
+
+    def _need(self, t, level, name):
+        return check_device_vector(self.torch, t, self.ndof(level), self.device, name)
 
     @staticmethod
     def _ptr(t):
@@ -233,14 +276,14 @@ class Solver:
 
     def residual(self, x, b, level=None):
         lv = self.nlevels if level is None else level
-        x, b = self._dev(x), self._dev(b)
+        x, b = self._dev(x, lv, "x"), self._dev(b, lv, "b")
         r = self.zeros(lv)
         self._check(self.lib.fc_residual(self.h, lv, self._ptr(x), self._ptr(b), self._ptr(r)))
         return r
 
     def apply(self, x, level=None):
         lv = self.nlevels if level is None else level
-        x = self._dev(x)
+        x = self._dev(x, lv, "x")
         y = self.zeros(lv)
         self._check(self.lib.fc_apply(self.h, lv, self._ptr(x), self._ptr(y)))
         return y
@@ -248,14 +291,16 @@ class Solver:
     def smooth(self, x, b, level=None, nsweeps=1):
         """Returns a new vector: x after ``nsweeps`` RA sweeps."""
         lv = self.nlevels if level is None else level
-        xx = self._dev(x).clone()
-        b = self._dev(b)
+        xx = self._dev(x, lv, "x").clone()
+        b = self._dev(b, lv, "b")
         self._check(self.lib.fc_smooth(self.h, lv, self._ptr(xx), self._ptr(b), int(nsweeps)))
         return xx
 
     def smooth_(self, x, b, level=None, nsweeps=1):
         """In-place smoother on device tensors (no copies)."""
         lv = self.nlevels if level is None else level
+        self._need(x, lv, "x")
+        self._need(b, lv, "b")
         self._check(self.lib.fc_smooth(self.h, lv, self._ptr(x), self._ptr(b), int(nsweeps)))
         return x
 
@@ -263,38 +308,40 @@ class Solver:
         """In-place smoother that allocates nothing (static device scratch);
         returns the status code so callers can inspect rejections."""
         lv = self.nlevels if level is None else level
+        self._need(x, lv, "x")
+        self._need(b, lv, "b")
         return self.lib.fc_smooth_noalloc(self.h, lv, self._ptr(x), self._ptr(b), int(nsweeps))
 
     def restrict(self, r, level=None):
         lv = self.nlevels if level is None else level
-        r = self._dev(r)
+        r = self._dev(r, lv, "r")
         bc = self.zeros(lv - 1)
         self._check(self.lib.fc_restrict(self.h, lv, self._ptr(r), self._ptr(bc)))
         return bc
 
     def prolong_add(self, e, x, level=None):
         lv = self.nlevels if level is None else level
-        e = self._dev(e)
-        xx = self._dev(x).clone()
+        e = self._dev(e, lv - 1, "e")
+        xx = self._dev(x, lv, "x").clone()
         self._check(self.lib.fc_prolong_add(self.h, lv, self._ptr(e), self._ptr(xx)))
         return xx
 
     def coarse_solve(self, b):
-        b = self._dev(b)
+        b = self._dev(b, 1, "b")
         x = self.zeros(1)
         self._check(self.lib.fc_coarse_solve(self.h, self._ptr(b), self._ptr(x)))
         return x
 
     def vcycle(self, x, b):
-        xx = self._dev(x).clone()
-        b = self._dev(b)
+        xx = self._dev(x, None, "x").clone()
+        b = self._dev(b, None, "b")
         self._check(self.lib.fc_vcycle(self.h, self._ptr(xx), self._ptr(b)))
         return xx
 
     def solve(self, b, x0=None, rtol=None, maxit=200):
         """FGMRES + GMG; returns (x, iterations, true relative residual)."""
-        b = self._dev(b)
-        x = self.zeros() if x0 is None else self._dev(x0).clone()
+        b = self._dev(b, None, "b")
+        x = self.zeros() if x0 is None else self._dev(x0, None, "x0").clone()
         its, rel = C.c_int(), C.c_double()
         st = self.lib.fc_solve(self.h, self._ptr(b), self._ptr(x),
                                float(self.prob.rtol if rtol is None else rtol), int(maxit),
@@ -306,8 +353,8 @@ class Solver:
     def gmg_solve(self, b, x0=None, reduction=1e-9, maxit=100):
         """Standalone V-cycles until the residual falls by ``reduction``;
         returns (x, cycles, achieved reduction)."""
-        b = self._dev(b)
-        x = self.zeros() if x0 is None else self._dev(x0).clone()
+        b = self._dev(b, None, "b")
+        x = self.zeros() if x0 is None else self._dev(x0, None, "x0").clone()
         its, red = C.c_int(), C.c_double()
         st = self.lib.fc_gmg_solve(self.h, self._ptr(b), self._ptr(x), float(reduction), int(maxit),
                                    C.byref(its), C.byref(red))
@@ -317,12 +364,13 @@ class Solver:
 
     def solve_host(self, b_host, x_host, rtol=None, maxit=200):
         """FGMRES + GMG from host buffers (numpy or pinned torch CPU tensors)."""
-        def ptr(a):
+        def ptr(a, name, writable):
+            check_host_vector(self.torch, a, self.ndof(), name, writable)
             if self.torch.is_tensor(a):
                 return C.c_void_p(a.data_ptr())
             return a.ctypes.data_as(C.c_void_p)
         its, rel = C.c_int(), C.c_double()
-        st = self.lib.fc_solve_host(self.h, ptr(b_host), ptr(x_host),
+        st = self.lib.fc_solve_host(self.h, ptr(b_host, "b_host", False), ptr(x_host, "x_host", True),
                                     float(self.prob.rtol if rtol is None else rtol), int(maxit),
                                     C.byref(its), C.byref(rel))
         if st not in (FC_OK, FC_ERR_NOT_CONVERGED):
@@ -360,6 +408,7 @@ class Batch:
         self.lib = load()
         self.solvers = list(solvers)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.device = torch.cuda.current_device()
         hs = (C.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
         self.b = C.c_void_p()
         st = self.lib.fc_batch_create(C.byref(self.b), hs, len(self.solvers), C.c_void_p(self.stream.cuda_stream))
@@ -388,11 +437,20 @@ class Batch:
     def ndof(self) -> int:
         return self.offsets[-1]
 
+    def _need(self, t, name):
+        return check_device_vector(self.torch, t, self.ndof, self.device, name)
+
     def pack(self, vectors):
-        out = self.torch.empty(self.ndof, dtype=self.torch.float64, device="cuda")
+        vectors = list(vectors)
+        if len(vectors) != len(self.solvers):
+            raise FcError(FC_ERR_INVALID, f"pack: {len(vectors)} vectors for {len(self.solvers)} problems")
+        out = self.torch.empty(self.ndof, dtype=self.torch.float64, device=f"cuda:{self.device}")
         for p, v in enumerate(vectors):
             t = v if self.torch.is_tensor(v) else self.torch.as_tensor(np.asarray(v, dtype=np.float64))
-            out[self.offsets[p]:self.offsets[p + 1]] = t.to(device="cuda", dtype=self.torch.float64)
+            n = self.offsets[p + 1] - self.offsets[p]
+            if t.numel() != n:
+                raise FcError(FC_ERR_INVALID, f"pack: problem {p} needs {n} values, got {t.numel()}")
+            out[self.offsets[p]:self.offsets[p + 1]] = t.reshape(-1).to(device=out.device, dtype=self.torch.float64)
         return out
 
     def unpack(self, packed):
@@ -415,17 +473,23 @@ class Batch:
         return {"nprob": n.value, "ndof": nd.value, "npatch_finest": npch.value, "levels_max": lv.value}
 
     def smooth_(self, x, b, nsweeps=1):
+        self._need(x, "x")
+        self._need(b, "b")
         self._check(self.lib.fc_batch_smooth(self.b, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()),
                                              int(nsweeps)))
         return x
 
     def vcycle_(self, x, b):
+        self._need(x, "x")
+        self._need(b, "b")
         self._check(self.lib.fc_batch_vcycle(self.b, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr())))
         return x
 
     def solve(self, b, x0=None, rtol=1e-8, maxit=200):
         """Per-problem FGMRES + GMG; returns (packed x, iterations, relres)."""
-        x = self.torch.zeros(self.ndof, dtype=self.torch.float64, device="cuda") if x0 is None else x0.clone()
+        self._need(b, "b")
+        x = (self.torch.zeros(self.ndof, dtype=self.torch.float64, device=f"cuda:{self.device}") if x0 is None
+             else self._need(x0, "x0").clone())
         n = len(self.solvers)
         its = (C.c_int * n)()
         rel = (C.c_double * n)()
@@ -438,6 +502,8 @@ class Batch:
     def solve_host(self, b_host, x_host, rtol=1e-8, maxit=200):
         """Per-problem solves from packed pinned host tensors; x_host holds x0
         and receives x.  Returns (iterations, relres)."""
+        check_host_vector(self.torch, b_host, self.ndof, "b_host")
+        check_host_vector(self.torch, x_host, self.ndof, "x_host", writable=True)
         n = len(self.solvers)
         its = (C.c_int * n)()
         rel = (C.c_double * n)()

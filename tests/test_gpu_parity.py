@@ -240,6 +240,46 @@ def test_invalid_arguments_rejected(fc):
         fc.Solver(inputs.porous_3d(0, n=8, nspheres=2, nlevels=2), cache="matrix", prec="fp32")
 
 
+def test_binding_rejects_bad_vectors(fc):
+    """Vectors of the wrong length, type, layout or memory are rejected by
+    the binding before a pointer reaches the library; valid calls still run."""
+    import torch
+    p = inputs.channel_2d(0, n=16, nlevels=2)
+    s = fc.Solver(p)
+    n = s.ndof()
+    good = s.zeros()
+    bad = {
+        "short": torch.zeros(n - 1, dtype=torch.float64, device="cuda"),
+        "host": torch.zeros(n, dtype=torch.float64),
+        "float32": torch.zeros(n, dtype=torch.float32, device="cuda"),
+        "strided": torch.zeros(2 * n, dtype=torch.float64, device="cuda")[::2],
+    }
+    for name, v in bad.items():
+        with pytest.raises(fc.FcError) as e:
+            s.smooth_(v, good)
+        assert e.value.code == fc.FC_ERR_INVALID, name
+        with pytest.raises(fc.FcError):
+            s.smooth_noalloc_(good, v)
+    with pytest.raises(fc.FcError):
+        s.residual(bad["short"], good)
+    with pytest.raises(fc.FcError):
+        s.restrict(good, level=1)
+    with pytest.raises(fc.FcError):
+        s.solve_host(np.zeros(n - 1), np.zeros(n))
+    b = s.rhs()
+    x = s.smooth(good, b)
+    assert x.shape == (n,) and torch.isfinite(x).all()
+    _, its, rr = s.solve(b, rtol=1e-8)
+    assert rr <= 1e-8
+    B = fc.Batch([s])
+    with pytest.raises(fc.FcError):
+        B.smooth_(bad["host"], good)
+    with pytest.raises(fc.FcError):
+        B.pack([bad["short"]])
+    B.close()
+    s.close()
+
+
 def test_no_obstacle_and_one_level(fc):
     """Degenerate cases: no obstacle at all; a one-level hierarchy (direct
     solve only, FGMRES converges in one step)."""
