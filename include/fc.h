@@ -18,6 +18,12 @@
  *    layout: node (i, j, k) with i fastest, then the d velocity components,
  *    then the pressure: x[((k*(ny+1) + j)*(nx+1) + i)*(d+1) + c].
  *  - Levels are numbered as in the paper (Sec. 3): 1 = coarsest, L = finest.
+ *  - A vector of level l holds ndof(l) = (d+1) prod_k (n_k / 2^(L-l) + 1)
+ *    doubles (fc_info reports it).  The library reads or writes exactly that
+ *    many values at each pointer and cannot check a pointer's extent or
+ *    memory space: a shorter buffer, a host pointer or another GPU's memory
+ *    is an illegal access on the device.  The Python binding checks all
+ *    three before it passes a pointer.
  *  - All device work is enqueued on the stream given to fc_setup and is
  *    asynchronous unless the entry point says it synchronises.
  *  - Errors are returned as fc_status codes; fc_last_error(h) gives a
@@ -304,10 +310,20 @@ fc_status fc_batch_sync(fc_batch b);
 const char* fc_batch_last_error(fc_batch b);
 fc_status fc_batch_destroy(fc_batch b);
 
-/* Wait for all work enqueued by the handle. */
+/* Wait for all work enqueued by the handle.  Errors: FC_ERR_INVALID (NULL
+ * handle), FC_ERR_CUDA (the stream reported an error). */
 fc_status fc_sync(fc_handle h);
 
+/* Message of the handle's last error ("" if none).  The string belongs to
+ * the handle and stays valid until the next call on it or fc_destroy; for a
+ * NULL handle a static message is returned. */
 const char* fc_last_error(fc_handle h);
+
+/* Wait for the handle's stream, release every device and host buffer it
+ * holds (including the CUDA graphs and the single-problem batch of the
+ * float32 V-cycle) and free the handle.  Every handle that fc_setup stored
+ * into *h, also one returned with an error status, is destroyed exactly
+ * once.  FC_ERR_INVALID for NULL. */
 fc_status fc_destroy(fc_handle h);
 
 #ifdef __cplusplus
