@@ -65,6 +65,25 @@ def test_oversized_request_rejected():
         Server(solve, lambda p: p.fp, budget_bytes=10, slots=1).run([Request(0, FakeProblem(11, 0.0), 0.0)])
 
 
+def test_failed_request_is_reported_and_frees_its_slot():
+    """A request whose solve raises (an FcError from setup, for instance)
+    frees its slot and memory; every other request is still served, and
+    run() reports the failure at the end."""
+    log = []
+    solve, active = make_fake(log)
+
+    def flaky(p, stream):
+        if p.fp == 77:
+            raise RuntimeError("setup failed")
+        return solve(p, stream)
+
+    reqs = [Request(k, FakeProblem(fp=77 if k == 2 else 30, dur=0.01), arrival=0.002 * k) for k in range(8)]
+    with pytest.raises(RuntimeError) as e:
+        Server(flaky, lambda p: p.fp, budget_bytes=100, slots=1).run(reqs)
+    assert "1 requests failed" in str(e.value) and "setup failed" in str(e.value)
+    assert len(log) == 7 and active["mem"] == 0 and active["n"] == 0
+
+
 def test_latency_stats():
     from paper_2403_11636_gb300.serve import Result
     rs = [Result(k, 0.0, 0.0, float(k + 1), 1, 0.0, 0.0, 0.0, 0) for k in range(100)]
