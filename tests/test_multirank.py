@@ -1,4 +1,5 @@
-"""The multi-rank benchmark path on CPU (gloo, world size 2).
+"""The benchmark's host logic on CPU: the multi-rank path (gloo, world size
+2) and the update count behind the metric.
 
 With N GPUs the benchmark runs N independent problems, one per rank, with no
 collective on the data path: each rank solves its own seeded porous problem,
@@ -80,3 +81,26 @@ def test_reference_arm_runs_on_rank_0_only():
     with contextlib.redirect_stdout(buf):
         assert bench.run_reference(args, 1, 2) == 0
     assert buf.getvalue() == ""
+
+
+def test_update_count_matches_the_free_dofs_of_the_oracle():
+    """The metric counts one update per free DoF per sweep on every smoothed
+    level; bench.free_dofs counts them in closed form, the oracle's
+    constraint mask counts them directly."""
+    import dataclasses
+
+    from oracle import oracle as O
+    from paper_2403_11636_gb300 import inputs
+    probs = [inputs.porous_3d(0, n=8, nspheres=3, nlevels=2),
+             dataclasses.replace(inputs.porous_3d(1, n=8, nspheres=3, nlevels=2), preset=0),
+             inputs.channel_2d(0, n=16, nlevels=3),
+             dataclasses.replace(inputs.channel_2d(1, n=16, nlevels=3), preset=1)]
+    for p in probs:
+        total = 0
+        for level in range(2, p.nlevels + 1):
+            L = O.Level.from_problem(p, level)
+            L.assemble()
+            fixed = L.csr()[2]
+            assert bench.free_dofs(p, level) == fixed.size - int(fixed.sum()), (p.name, level)
+            total += fixed.size - int(fixed.sum())
+        assert bench.updates_per_solve(p, 3) == 3 * (p.nu_pre + p.nu_post) * total
