@@ -1,0 +1,65 @@
+"""The hot-path kernels compile without register spills.
+
+A spill in the smoother's apply or residual kernels turns into local-memory
+traffic on every patch or node, so each of them is compiled for sm_103a
+with the library's own flags plus ptxas's resource report, and the report
+must show no spill stores.  Needs only nvcc (no GPU).
+"""
+import concurrent.futures as cf
+import os
+import re
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2403_11636_gb300 import build
+
+# translation unit -> kernels (name prefixes) on the smoother's hot path
+HOT = {
+    "fc_patch.cu": ("apply_df_persistent_kernel", "apply_df_kernel", "apply_fp64_kernel", "apply_lowp_kernel",
+                    "factor_apply_kernel"),
+    "fc_mg.cu": ("residual_df2_kernel", "residual_kernel", "restrict_kernel", "prolong_kernel"),
+    "fc_batch.cu": ("f_apply_kernel", "f_residual_kernel", "b_apply_kernel", "f_restrict_kernel",
+                    "f_prolong_kernel"),
+}
+
+
+def resources(src, tmp):
+    nvcc = build._nvcc()
+    cmd = [nvcc, *build.ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", build.INCLUDE,
+           *build.EXTRA.get(src, []), "-Xptxas", "-v", "-c", os.path.join(build.CSRC, src),
+           "-o", os.path.join(tmp, src + ".o")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out, cur = {}, None
+    for line in r.stderr.splitlines():
+        m = re.search(r"Compiling entry function '(\S+)'", line)
+        if m:
+            cur = m.group(1)
+            continue
+        m = re.search(r"(\d+) bytes spill stores", line)
+        if m and cur:
+            out[cur] = int(m.group(1))
+    return out
+
+
+@pytest.fixture(scope="module")
+def reports():
+    if shutil.which(build._nvcc()) is None and not os.path.exists(build._nvcc()):
+        pytest.skip("nvcc not found")
+    with tempfile.TemporaryDirectory() as tmp:
+        with cf.ThreadPoolExecutor(len(HOT)) as ex:
+            return dict(zip(HOT, ex.map(lambda s: resources(s, tmp), HOT)))
+
+
+@pytest.mark.parametrize("src", list(HOT))
+def test_hot_kernels_do_not_spill(reports, src):
+    rep = reports[src]
+    hot = {k: v for k, v in rep.items() if any(re.search(r"\d" + p + r"I", k) for p in HOT[src])}
+    # every listed kernel family is present (the pattern still matches the names)
+    for p in HOT[src]:
+        assert any(re.search(r"\d" + p + r"I", k) for k in hot), (src, p)
+    spilling = {k: v for k, v in hot.items() if v > 0}
+    assert not spilling, spilling
