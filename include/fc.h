@@ -217,7 +217,13 @@ fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch,
  * nodes of the 3^d box; absent DoFs have zero coefficients.  Synchronises. */
 fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_host);
 
-/* Upper bound of the device bytes fc_setup would hold for this problem. */
+/* Upper bound of the device bytes a handle for this problem holds at the
+ * peak of fc_setup: everything it keeps, plus the largest setup temporary
+ * (element matrices of a level, or the float64 build of reduced-precision
+ * rows, which coexists with the converted rows), assuming that no two patches
+ * share a stored block (dedup = 1 can only lower the real use), plus 2 % and
+ * 8 MiB for small buffers and allocator rounding.  Pure host arithmetic; 0
+ * for invalid arguments. */
 size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o);
 
 /* Per-kernel device time of the patch apply, the residual and the whole

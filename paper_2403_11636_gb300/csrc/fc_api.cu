@@ -402,33 +402,59 @@ fc_status fc_options_default(fc_options* o) {
 
 size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o) {
   if (!g || !o || (g->dim != 2 && g->dim != 3) || depth < 1) return 0;
-  size_t total = 0;
-  int dim = g->dim, nd = dim + 1, nb = dim == 3 ? 27 : 9;
+  const int dim = g->dim, nd = dim + 1, nb = dim == 3 ? 27 : 9, nl = 1 << dim, sp = spn(dim);
+  const bool inverse = o->cache == FC_CACHE_INVERSE;
+  const bool pairs = inverse && o->prec == FC_PREC_DF64;
+  const bool f32 = inverse && (o->prec == FC_PREC_FP32 || o->prec == FC_PREC_BF16);
+  // held: what the handle keeps after setup; transient: the largest setup
+  // temporary, which coexists with what is held at that point
+  size_t held = 0, transient = 0;
+  size_t coarse_dof = 0, fine_dof = 0;
   for (int l = 0; l < depth; ++l) {
-    int c = depth - 1 - l;
-    long long nodes = 1, pad = 1, cells = 1;
+    const int c = depth - 1 - l;
+    size_t nodes = 1, pad = 1, cells = 1;
     for (int k = 0; k < dim; ++k) {
-      long long n = g->n[k] >> c;
+      const size_t n = (size_t)(g->n[k] >> c);
       nodes *= n + 1;
       pad *= n + 5;
       cells *= n;
     }
-    total += (size_t)nodes * nb * (2 * dim + 2) * 8 + nodes + (size_t)nodes * nd * 8;  // st, mask, wfix
-    total += (size_t)nodes * nd * 8 * 3 + (size_t)pad * nd * 8 + (size_t)pad * nd * 8;   // vectors
-    if (o->cache == FC_CACHE_INVERSE && (o->prec == FC_PREC_FP32 || o->prec == FC_PREC_BF16))
-      total += (size_t)(l > 0 ? nodes * (nb / 2 + 1) * (2 * dim + 2) * 4 : 0) + (size_t)pad * nd * 4 + (size_t)nodes * nd * 4;
-    if (l > 0) {
-      if (o->cache == FC_CACHE_INVERSE)
-        total += (size_t)nodes * nslot(dim) * nd * coef_elem_bytes(o->prec);
-      else if (o->cache == FC_CACHE_MATRIX)
-        total += (size_t)nodes * (factor_doubles(dim) * 8 + factor_ints(dim) * 4);
+    const size_t dof = nodes * nd, pv = pad * nd;
+    if (l == 0) coarse_dof = dof;
+    if (l == depth - 1) fine_dof = dof;
+    held += nodes * nb * sp * 8 + nodes + dof * 8;                  // stencil, mask, Dirichlet values
+    held += 3 * dof * 8 + pv * 8;                                   // x, b, r, padded residual
+    if (pairs && l > 0) held += nodes * (nb / 2 + 1) * sp * 8 + pv * 8 + dof * 8;  // pair half stencil, x, b
+    if (need_r32(o->prec)) held += pv * 8;                          // pair / float32 padded residual
+    if (f32) held += (l > 0 ? nodes * (nb / 2 + 1) * sp * 4 : 0) + pv * 4 + dof * 4;  // float32 V-cycle
+    // class tables and the work list of the patches (every patch may be
+    // cut: no sharing is assumed)
+    const size_t classes = l > 0 && o->cache != FC_CACHE_NONE ? nodes * 9 + (nodes / 1024 + 1) * 4 : 0;
+    // element matrices and cell classes of the level, which live until the
+    // patch classes are known
+    transient = std::max(transient, cells * ((size_t)nl * nl * (1 + dim) + (size_t)dim * nl) * 8 + cells + classes);
+    if (l > 0 && o->cache != FC_CACHE_NONE) {
+      held += nodes * 4;                                            // patch -> stored block
+      size_t tmp = classes;
+      if (inverse) {
+        const size_t rows = nodes * nslot(dim) * nd;
+        held += rows * coef_elem_bytes(o->prec);
+        // reduced-precision rows are built in float64 and converted
+        if (o->prec != FC_PREC_FP64) tmp += rows * 8 + nodes * 8;
+      } else {
+        held += nodes * (factor_doubles(dim) * 8 + factor_ints(dim) * 4);
+      }
+      transient = std::max(transient, tmp);
     }
   }
-  long long fine_nodes = 1;
-  for (int k = 0; k < dim; ++k) fine_nodes *= g->n[k] + 1;
-  int m = o->fgmres_restart > 0 ? o->fgmres_restart : 30;
-  total += (size_t)fine_nodes * nd * 8 * (2 * m + 4);
-  return total;
+  held += coarse_dof * coarse_dof * 8;                              // coarse inverse
+  transient = std::max(transient, coarse_dof * coarse_dof * 8 + coarse_dof * 12);  // its factorisation
+  const int m = o->fgmres_restart > 0 ? o->fgmres_restart : 30;
+  held += fine_dof * 8 * (2 * (size_t)m + 4) + 2048 * 8 + (size_t)small_len(m) * 8;  // FGMRES
+  // error word, shapes, counters, the float32 V-cycle's batch tables and
+  // allocator rounding
+  const size_t total = held + transient;
+  return total + total / 50 + (8u << 20);
 }
 
 fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, double alpha, int depth,

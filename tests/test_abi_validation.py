@@ -152,11 +152,18 @@ def test_footprint_estimate(lib):
     assert lib.fc_footprint_estimate(C.byref(g), 3, C.byref(o)) == 0
     g.dim = 3
     f64 = lib.fc_footprint_estimate(C.byref(g), 3, C.byref(o))
-    o.prec = fc.PREC["fp32"]
-    f32 = lib.fc_footprint_estimate(C.byref(g), 3, C.byref(o))
-    o.prec = fc.PREC["bf16"]
-    b16 = lib.fc_footprint_estimate(C.byref(g), 3, C.byref(o))
-    assert f64 > f32 > b16 > 0
+    est = {}
+    for name in ("fp32", "bf16", "df64"):
+        o.prec = fc.PREC[name]
+        est[name] = lib.fc_footprint_estimate(C.byref(g), 3, C.byref(o))
+    # reduced-precision rows are built in float64 and then converted: the
+    # finest level's float64 rows coexist with the converted rows of every
+    # level; narrower rows still need less
+    finest, coarser = 17 ** 3 * 402 * 4, 9 ** 3 * 402 * 4
+    for name, eb in (("fp32", 4), ("bf16", 2), ("df64", 8)):
+        assert est[name] >= finest * 8 + (finest + coarser) * eb, name
+    assert est["df64"] > est["fp32"] > est["bf16"] > 0
+    assert f64 >= (finest + coarser) * 8
     o.prec = fc.PREC["fp64"]
     g.n[0] = g.n[1] = g.n[2] = 32
     assert 6 < lib.fc_footprint_estimate(C.byref(g), 4, C.byref(o)) / f64 < 10
