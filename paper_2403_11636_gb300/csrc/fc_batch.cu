@@ -31,6 +31,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "fc_internal.cuh"
@@ -1538,9 +1539,12 @@ fc_status create_batch(fc_batch* out, const fc_handle* handles, int nprob, void*
   B->m = h0->restart;
   B->nu_pre = h0->opt.nu_pre;
   B->nu_post = h0->opt.nu_post;
+  std::unordered_set<const void*> seen;
   for (int p = 0; p < nprob; ++p) {
     const fc_handle h = handles[p];
     if (!h) return bfail(B, FC_ERR_INVALID, "null handle");
+    // each problem's level vectors are the batch's workspace for it
+    if (!seen.insert(h).second) return bfail(B, FC_ERR_INVALID, "a handle appears twice in the batch");
     if (h->dim != B->dim) return bfail(B, FC_ERR_INVALID, "all problems of a batch must have the same dimension");
     if (h->opt.cache != FC_CACHE_INVERSE || h->opt.prec == FC_PREC_DF64)
       return bfail(B, FC_ERR_INVALID, "batches take cache_inverse handles with fp64, fp32 or bf16 rows");

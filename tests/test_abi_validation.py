@@ -144,6 +144,30 @@ def test_entry_points_without_a_handle(lib):
         assert call() == fc.FC_ERR_INVALID, k
 
 
+def test_batch_rejects_a_handle_given_twice(lib):
+    """A batch uses each problem's level vectors as its workspace, so one
+    handle may appear once only.  Without a GPU, fc_setup stops at its first
+    allocation but leaves a handle with the problem's parameters, which is
+    enough for the batch's argument checks."""
+    g, ls, shapes, o = valid(dim=2)
+    h = C.c_void_p()
+    st = lib.fc_setup(C.byref(h), C.byref(g), C.byref(ls), 1e-8, 3, C.byref(o), None)
+    assert h.value
+    try:
+        if st == fc.FC_OK:
+            pytest.skip("a GPU is present")
+        b = C.c_void_p()
+        hs = (C.c_void_p * 3)(h.value, h.value, h.value)
+        assert lib.fc_batch_create(C.byref(b), hs, 3, None) == fc.FC_ERR_INVALID
+        assert b"appears twice" in lib.fc_batch_last_error(b)
+        assert lib.fc_batch_destroy(b) == fc.FC_OK
+        b = C.c_void_p()
+        assert lib.fc_batch_create(C.byref(b), hs, 0, None) == fc.FC_ERR_INVALID
+        assert lib.fc_batch_destroy(b) == fc.FC_OK
+    finally:
+        assert lib.fc_destroy(h) == fc.FC_OK
+
+
 def test_footprint_estimate(lib):
     g, ls, shapes, o = valid()
     assert lib.fc_footprint_estimate(None, 3, C.byref(o)) == 0
