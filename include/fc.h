@@ -264,9 +264,11 @@ typedef struct fc_batch_s* fc_batch;
  * stream).  Times every patch-apply tile candidate (lanes per patch
  * {1,2,4,8,16,32} x threads per CTA {128,256,512} x CTAs per SM
  * {2,4,8,16}, at most 2048 threads per SM and 256 patches per CTA pass) on
- * the batch's finest levels and keeps the fastest.  Synchronises.  Errors: FC_ERR_INVALID (mixed dimensions,
- * policies, precisions or sweep counts; DF64 rows), FC_ERR_CUDA. On error
- * *out is still set and must be passed to fc_batch_destroy. */
+ * the batch's finest levels and keeps the fastest.  Synchronises.  Errors:
+ * FC_ERR_INVALID (no handles, a NULL handle or one given twice, mixed
+ * dimensions, policies, precisions or sweep counts; DF64 rows),
+ * FC_ERR_CUDA.  On error *out is still set and must be passed to
+ * fc_batch_destroy. */
 fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream);
 
 /* offsets[0..nprob] (host) of the packed finest-level vectors. */
