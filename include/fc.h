@@ -28,7 +28,9 @@
  *    asynchronous unless the entry point says it synchronises.
  *  - Errors are returned as fc_status codes; fc_last_error(h) gives a
  *    message.  No entry point aborts the process.  A handle stays valid
- *    after FC_ERR_NOT_CONVERGED and after argument errors.
+ *    after FC_ERR_NOT_CONVERGED and after argument errors.  A handle whose
+ *    fc_setup failed answers only fc_last_error, fc_sync and fc_destroy;
+ *    every other call returns FC_ERR_INVALID without touching the device.
  */
 #ifndef FC_H
 #define FC_H

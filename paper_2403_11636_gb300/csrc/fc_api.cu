@@ -364,8 +364,16 @@ fc_status vcycle_level(fc_handle h, int li, double* x, const double* b) {
   return smooth_level(h, li, x, b, h->opt.nu_post);
 }
 
-fc_status level_ok(fc_handle h, int level, int min_level) {
+// a handle whose fc_setup failed holds partial data: no kernel may run on it
+fc_status ready_ok(fc_handle h) {
   if (!h) return FC_ERR_INVALID;
+  if (!h->ready) return fail(h, FC_ERR_INVALID, "handle not set up (fc_setup failed)");
+  return FC_OK;
+}
+
+fc_status level_ok(fc_handle h, int level, int min_level) {
+  fc_status st = ready_ok(h);
+  if (st != FC_OK) return st;
   if (level < min_level || level > h->nlev) return fail(h, FC_ERR_INVALID, "level out of range");
   return FC_OK;
 }
@@ -748,11 +756,14 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     CK(cudaMallocHost((void**)&h->host_small, sizeof(double) * (size_t)small_len(m)));
   }
   CK(cudaStreamSynchronize(h->stream));
+  h->ready = true;
   return FC_OK;
 }
 
 fc_status fc_rhs(fc_handle h, double* b_dev) {
-  if (!h || !b_dev) return FC_ERR_INVALID;
+  fc_status st = ready_ok(h);
+  if (st != FC_OK) return st;
+  if (!b_dev) return fail(h, FC_ERR_INVALID, "null vector");
   Level& L = h->lev[h->nlev - 1];
   CK(cudaMemcpyAsync(b_dev, L.b, sizeof(double) * L.g.ndof, cudaMemcpyDeviceToDevice, h->stream));
   return FC_OK;
@@ -800,13 +811,17 @@ fc_status fc_prolong_add(fc_handle h, int level, const double* ec, double* xf) {
 }
 
 fc_status fc_coarse_solve(fc_handle h, const double* b, double* x) {
-  if (!h || !b || !x) return FC_ERR_INVALID;
+  fc_status st = ready_ok(h);
+  if (st != FC_OK) return st;
+  if (!b || !x) return fail(h, FC_ERR_INVALID, "null vector");
   CK(launch_dense_gemv(h->coarse_n, h->coarse_inv, b, x, h->stream));
   return FC_OK;
 }
 
 fc_status fc_vcycle(fc_handle h, double* x, const double* b) {
-  if (!h || !x || !b) return FC_ERR_INVALID;
+  fc_status st = ready_ok(h);
+  if (st != FC_OK) return st;
+  if (!x || !b) return fail(h, FC_ERR_INVALID, "null vector");
   ProfScope ps(h, 2, 0.0);
   if (f32_path(h)) return handle_vcycle_f32(h, x, b, false);
   return vcycle_level(h, h->nlev - 1, x, b);
@@ -814,7 +829,9 @@ fc_status fc_vcycle(fc_handle h, double* x, const double* b) {
 
 fc_status fc_solve(fc_handle h, const double* b, double* x, double rtol, int maxit, int* iters,
                    double* relres) {
-  if (!h || !b || !x || !(rtol > 0.0) || maxit < 0) return h ? fail(h, FC_ERR_INVALID, "bad solve arguments") : FC_ERR_INVALID;
+  const fc_status rs = ready_ok(h);
+  if (rs != FC_OK) return rs;
+  if (!b || !x || !(rtol > 0.0) || maxit < 0) return fail(h, FC_ERR_INVALID, "bad solve arguments");
   Level& F = h->lev[h->nlev - 1];
   const long long n = F.g.ndof;
   const int m = h->restart;
@@ -894,8 +911,9 @@ fc_status fc_solve(fc_handle h, const double* b, double* x, double rtol, int max
 
 fc_status fc_gmg_solve(fc_handle h, const double* b, double* x, double reduction, int maxit, int* iters,
                        double* relred) {
-  if (!h || !b || !x || !(reduction > 0.0) || maxit < 0)
-    return h ? fail(h, FC_ERR_INVALID, "bad GMG arguments") : FC_ERR_INVALID;
+  const fc_status rs = ready_ok(h);
+  if (rs != FC_OK) return rs;
+  if (!b || !x || !(reduction > 0.0) || maxit < 0) return fail(h, FC_ERR_INVALID, "bad GMG arguments");
   Level& F = h->lev[h->nlev - 1];
   const long long n = F.g.ndof;
   cudaStream_t s = h->stream;
@@ -930,7 +948,9 @@ fc_status fc_gmg_solve(fc_handle h, const double* b, double* x, double reduction
 
 fc_status fc_solve_host(fc_handle h, const double* b_host, double* x_host, double rtol, int maxit,
                         int* iters, double* relres) {
-  if (!h || !b_host || !x_host) return FC_ERR_INVALID;
+  const fc_status rs = ready_ok(h);
+  if (rs != FC_OK) return rs;
+  if (!b_host || !x_host) return fail(h, FC_ERR_INVALID, "null buffer");
   long long n = h->lev[h->nlev - 1].g.ndof;
   CK(cudaMemcpyAsync(h->bh, b_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->xh, x_host, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));

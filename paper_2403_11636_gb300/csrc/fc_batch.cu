@@ -1539,12 +1539,15 @@ fc_status create_batch(fc_batch* out, const fc_handle* handles, int nprob, void*
   B->m = h0->restart;
   B->nu_pre = h0->opt.nu_pre;
   B->nu_post = h0->opt.nu_post;
+  // each problem's level vectors are the batch's workspace for it
   std::unordered_set<const void*> seen;
   for (int p = 0; p < nprob; ++p) {
+    if (!handles[p]) return bfail(B, FC_ERR_INVALID, "null handle");
+    if (!seen.insert(handles[p]).second) return bfail(B, FC_ERR_INVALID, "a handle appears twice in the batch");
+  }
+  for (int p = 0; p < nprob; ++p) {
     const fc_handle h = handles[p];
-    if (!h) return bfail(B, FC_ERR_INVALID, "null handle");
-    // each problem's level vectors are the batch's workspace for it
-    if (!seen.insert(h).second) return bfail(B, FC_ERR_INVALID, "a handle appears twice in the batch");
+    if (!h->ready) return bfail(B, FC_ERR_INVALID, "handle not set up (fc_setup failed)");
     if (h->dim != B->dim) return bfail(B, FC_ERR_INVALID, "all problems of a batch must have the same dimension");
     if (h->opt.cache != FC_CACHE_INVERSE || h->opt.prec == FC_PREC_DF64)
       return bfail(B, FC_ERR_INVALID, "batches take cache_inverse handles with fp64, fp32 or bf16 rows");

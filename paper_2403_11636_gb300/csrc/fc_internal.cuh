@@ -119,6 +119,9 @@ struct Profile {
 
 struct fc_handle_s {
   int dim = 0, nlev = 0;
+  // set when fc_setup completed; a handle whose setup failed holds partial
+  // data and only answers fc_last_error, fc_sync and fc_destroy
+  bool ready = false;
   fc::Level lev[fc::kMaxLevels];  // index 0 = coarsest (paper level 1)
   fc_options opt;
   double alpha = 0;

@@ -62,6 +62,7 @@ fc_status fail(fc_handle h, fc_status st, const char* msg) {
 extern "C" fc_status fc_smooth_noalloc(fc_handle h, int level, double* x, const double* b, int nsweeps) {
   using namespace fc;
   if (!h) return FC_ERR_INVALID;
+  if (!h->ready) return fail(h, FC_ERR_INVALID, "handle not set up (fc_setup failed)");
   if (level < 2 || level > h->nlev) return fail(h, FC_ERR_INVALID, "level out of range");
   if (!x || !b || nsweeps < 0) return fail(h, FC_ERR_INVALID, "bad smoother arguments");
   const Level& L = h->lev[level - 1];

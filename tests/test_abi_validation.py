@@ -144,6 +144,49 @@ def test_entry_points_without_a_handle(lib):
         assert call() == fc.FC_ERR_INVALID, k
 
 
+def test_failed_setup_leaves_a_handle_that_runs_nothing(lib):
+    """Without a GPU, fc_setup stops at its first allocation.  The handle it
+    leaves holds partial data: every call that would launch work on it
+    returns FC_ERR_INVALID, so no kernel can run on missing buffers."""
+    g, ls, shapes, o = valid(dim=2)
+    h = C.c_void_p()
+    st = lib.fc_setup(C.byref(h), C.byref(g), C.byref(ls), 1e-8, 3, C.byref(o), None)
+    assert h.value
+    try:
+        if st == fc.FC_OK:
+            pytest.skip("a GPU is present")
+        assert st == fc.FC_ERR_CUDA
+        buf = (C.c_double * 4)()
+        p = C.cast(buf, C.c_void_p)
+        i, d, ll = C.c_int(), C.c_double(), C.c_longlong()
+        calls = {
+            "rhs": lambda: lib.fc_rhs(h, p),
+            "residual": lambda: lib.fc_residual(h, 3, p, p, p),
+            "apply": lambda: lib.fc_apply(h, 3, p, p),
+            "smooth": lambda: lib.fc_smooth(h, 3, p, p, 1),
+            "smooth_noalloc": lambda: lib.fc_smooth_noalloc(h, 3, p, p, 1),
+            "restrict": lambda: lib.fc_restrict(h, 3, p, p),
+            "prolong": lambda: lib.fc_prolong_add(h, 3, p, p),
+            "coarse": lambda: lib.fc_coarse_solve(h, p, p),
+            "vcycle": lambda: lib.fc_vcycle(h, p, p),
+            "solve": lambda: lib.fc_solve(h, p, p, 1e-8, 10, C.byref(i), C.byref(d)),
+            "gmg": lambda: lib.fc_gmg_solve(h, p, p, 1e-9, 10, C.byref(i), C.byref(d)),
+            "solve_host": lambda: lib.fc_solve_host(h, p, p, 1e-8, 10, C.byref(i), C.byref(d)),
+            "info": lambda: lib.fc_info(h, 3, C.byref(ll), None, None),
+            "patch_rows": lambda: lib.fc_patch_rows(h, 3, 0, C.cast(buf, C.POINTER(C.c_double))),
+        }
+        for name, call in calls.items():
+            assert call() == fc.FC_ERR_INVALID, name
+            assert b"not set up" in lib.fc_last_error(h), name
+        b = C.c_void_p()
+        hs = (C.c_void_p * 1)(h.value)
+        assert lib.fc_batch_create(C.byref(b), hs, 1, None) == fc.FC_ERR_INVALID
+        assert b"not set up" in lib.fc_batch_last_error(b)
+        assert lib.fc_batch_destroy(b) == fc.FC_OK
+    finally:
+        assert lib.fc_destroy(h) == fc.FC_OK
+
+
 def test_batch_rejects_a_handle_given_twice(lib):
     """A batch uses each problem's level vectors as its workspace, so one
     handle may appear once only.  Without a GPU, fc_setup stops at its first
