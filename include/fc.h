@@ -26,6 +26,10 @@
  *    three before it passes a pointer.
  *  - All device work is enqueued on the stream given to fc_setup and is
  *    asynchronous unless the entry point says it synchronises.
+ *  - Threads: different handles are independent and may be used from
+ *    different host threads at the same time (fc_smooth_noalloc excepted,
+ *    see there); calls on one handle, and on a batch together with the
+ *    handles it groups, must not overlap.
  *  - Errors are returned as fc_status codes; fc_last_error(h) gives a
  *    message.  No entry point aborts the process.  A handle stays valid
  *    after FC_ERR_NOT_CONVERGED and after argument errors.  A handle whose
