@@ -440,6 +440,14 @@ class Batch:
     def _need(self, t, name):
         return check_device_vector(self.torch, t, self.ndof, self.device, name)
 
+    def _open(self):
+        """The batch works on its solvers' device data: refuse to run once
+        the batch or any of its solvers was closed."""
+        if not (getattr(self, "b", None) and self.b.value):
+            raise FcError(FC_ERR_INVALID, "the batch was closed")
+        if not all(getattr(s, "h", None) and s.h.value for s in self.solvers):
+            raise FcError(FC_ERR_INVALID, "a solver of this batch was closed")
+
     def pack(self, vectors):
         vectors = list(vectors)
         if len(vectors) != len(self.solvers):
@@ -473,6 +481,7 @@ class Batch:
         return {"nprob": n.value, "ndof": nd.value, "npatch_finest": npch.value, "levels_max": lv.value}
 
     def smooth_(self, x, b, nsweeps=1):
+        self._open()
         self._need(x, "x")
         self._need(b, "b")
         self._check(self.lib.fc_batch_smooth(self.b, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr()),
@@ -480,6 +489,7 @@ class Batch:
         return x
 
     def vcycle_(self, x, b):
+        self._open()
         self._need(x, "x")
         self._need(b, "b")
         self._check(self.lib.fc_batch_vcycle(self.b, C.c_void_p(x.data_ptr()), C.c_void_p(b.data_ptr())))
@@ -487,6 +497,7 @@ class Batch:
 
     def solve(self, b, x0=None, rtol=1e-8, maxit=200):
         """Per-problem FGMRES + GMG; returns (packed x, iterations, relres)."""
+        self._open()
         self._need(b, "b")
         x = (self.torch.zeros(self.ndof, dtype=self.torch.float64, device=f"cuda:{self.device}") if x0 is None
              else self._need(x0, "x0").clone())
@@ -502,6 +513,7 @@ class Batch:
     def solve_host(self, b_host, x_host, rtol=1e-8, maxit=200):
         """Per-problem solves from packed pinned host tensors; x_host holds x0
         and receives x.  Returns (iterations, relres)."""
+        self._open()
         check_host_vector(self.torch, b_host, self.ndof, "b_host")
         check_host_vector(self.torch, x_host, self.ndof, "x_host", writable=True)
         n = len(self.solvers)

@@ -84,3 +84,22 @@ def test_solver_needs_a_gpu():
     rejects_any = pytest.raises(fc.FcError)
     with rejects_any:
         fc.Solver(inputs.channel_2d(0, n=8, nlevels=1))
+
+
+def test_batch_refuses_to_run_on_closed_solvers():
+    """A batch works on its solvers' device data; once one of them (or the
+    batch) is closed, every batch call is refused before it reaches the
+    library.  The batch object is assembled by hand here (no GPU)."""
+    import ctypes as C
+    B = object.__new__(fc.Batch)
+    B.torch = torch
+    B.b = C.c_void_p(0x1000)          # stands for an open batch; never passed on
+    B.solvers = [types.SimpleNamespace(h=C.c_void_p(0x2000)), types.SimpleNamespace(h=C.c_void_p())]
+    B.offsets, B.device = [0, 4, 8], 0
+    x = FakeCudaTensor(8)
+    for call in (lambda: B.smooth_(x, x), lambda: B.vcycle_(x, x), lambda: B.solve(x),
+                 lambda: B.solve_host(np.zeros(8), np.zeros(8))):
+        assert "solver of this batch was closed" in rejects(call)
+    B.solvers[1].h = C.c_void_p(0x3000)
+    B.b = C.c_void_p()
+    assert "batch was closed" in rejects(lambda: B.smooth_(x, x))
