@@ -1,7 +1,9 @@
 #!/usr/bin/env python
 """Benchmark: FGMRES-GMG solves of the 3D porous-medium finite cell Stokes
 problem (64^3 background grid, 40 seeded spheres, alpha = 1e-8, octree depth 3,
-5 levels, V(2,2), rtol 1e-8) with the restricted additive smoother.
+5 levels, V(2,2), rtol 1e-8) with the restricted additive smoother, by
+default with FP64 patch rows and FP64 arithmetic throughout (the plain
+method).  --prec df64 / fp32 / bf16 selects the reduced-precision rows.
 
 A step is one complete solve from x0 = 0 on the resident hierarchy (operator,
 patch caches and coarse inverse built once per problem by fc_setup, whose time
@@ -9,7 +11,12 @@ is reported separately as setup_ms).  The metric is smoother owned-DoF
 updates per second: every sweep of every smoothed level updates each free DoF
 once, so one solve performs  its * (nu_pre + nu_post) * sum_l free_dofs(l)
 updates.  value = those updates over all ranks / max-over-ranks wall time of
-the K timed solves (CUDA events on the solver's stream).
+the K timed solves (CUDA events on the solver's stream, nothing else
+instrumented).  Per-kernel times for the roofline come from a separate pass
+of profiled solves after the timed ones.  With FP64 rows the patch apply is
+bound by the FP64 pipe (GB300 runs FP64 at 1/64 of the FP32 rate), so its
+roofline is FP64 FLOP/s against the nominal pipe peak, with the live FMA
+probe and the HBM fraction beside it.
 
 --impl reference times the FP64 CPU oracle (the plain implementation the
 tests compare against) on the host cores, on a bounded sample of the same
@@ -194,6 +201,47 @@ def run_reference(args, rank, world):
     return 0
 
 
+FP64_FMA_PER_CLK_PER_SM = 2      # GB300: FP64 at 1/64 of the FP32 rate (128 FMA/clk/SM)
+
+
+def fp64_peak(torch):
+    """Nominal FP64 FMA throughput from unit counts and the maximum SM clock:
+    SMs x 2 FP64 FMA/clock x 2 FLOP x clock (GB300: 152 x 2 x 2 x 2.07 GHz =
+    1.2586 TFLOP/s, the 1.25 TFLOP/s of the part's data).  Returns TFLOP/s and
+    a note of the figures used."""
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    tf = nsm * FP64_FMA_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12
+    return tf, f"derived: {nsm} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x 2 FLOP x {mhz:.0f} MHz"
+
+
+def pct(vals, q):
+    """Nearest-rank percentile of a list (q in (0, 100])."""
+    v = sorted(vals)
+    return v[min(len(v) - 1, max(0, int(math.ceil(q / 100.0 * len(v))) - 1))]
+
+
+def timed_solves(s, b, prob, steps, stream, torch):
+    """`steps` solves from x0 = 0 bracketed by CUDA events on the solver's
+    stream; returns (per-step ms, total ms, iterations, relres)."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    its_list, rr_list = [], []
+    for k in range(steps):
+        _, its, rr = s.solve(b, rtol=prob.rtol)
+        its_list.append(its)
+        rr_list.append(rr)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    return step_ms, ev[0].elapsed_time(ev[-1]), its_list, rr_list
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -207,6 +255,9 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     prob = workload(seed=rank)
     stream = torch.cuda.Stream()
+    # arithmetic peaks of this GPU, measured before the timed region
+    fp64_probe, _ = fc.probe_fma_rate("fp64")
+    fp32_probe, _ = fc.probe_fma_rate("fp32")
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
         s = fc.Solver(prob, cache=args.cache, prec=args.prec, stream=stream, dedup=args.dedup)
@@ -219,30 +270,25 @@ def run_ours(args, rank, world, local_rank):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+        # ---- headline: the timed solves, nothing instrumented
         clocks = Clocks(local_rank)
         clocks.start()
-        s.profile(True)
         l0 = fc.launch_count()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-        ev[0].record(stream)
-        its_list, rr_list = [], []
-        for k in range(args.steps):
-            x, its, rr = s.solve(b, rtol=prob.rtol)
-            its_list.append(its)
-            rr_list.append(rr)
-            ev[k + 1].record(stream)
-        torch.cuda.synchronize()
+        step_ms, total_ms, its_list, rr_list = timed_solves(s, b, prob, args.steps, stream, torch)
         launches = fc.launch_count() - l0
         cl = clocks.stop()
-        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-        total_ms = ev[0].elapsed_time(ev[-1])
-        n_apply, ms_apply, bytes_apply = s.profile_read(0)
+        if dist:
+            dist.barrier()
+        # ---- per-kernel times from a separate profiled pass (CUDA events on
+        # the solver stream around every apply / residual / V-cycle)
+        s.profile(True)
+        timed_solves(s, b, prob, max(1, min(args.steps, args.profile_steps)), stream, torch)
+        n_apply, ms_apply, _ = s.profile_read(0)
         n_fine, ms_fine, bytes_fine = s.profile_read(4)
         n_res, ms_res, _ = s.profile_read(1)
         n_vc, ms_vc, _ = s.profile_read(2)
         s.profile(False)
-        if dist:
-            dist.barrier()
+        flops_fine = s.info()["bytes"][6]
         # ---- end to end through the public API with host buffers
         n = s.ndof()
         bh = torch.empty(n, dtype=torch.float64, pin_memory=True)
@@ -255,10 +301,13 @@ def run_ours(args, rank, world, local_rank):
             t1 = time.perf_counter()
             its_h, rr_h = s.solve_host(bh, xh, rtol=prob.rtol)
             e2e_t.append(time.perf_counter() - t1)
-        # ---- cache policies and precisions on the finest level: one sweep each
+        x_ref = torch.from_numpy(xh.numpy().copy())
+        # ---- variants on rank 0: the float-pair solve, and one finest-level
+        # sweep per cache policy / precision
         variants = {}
-        if args.policies and rank == 0:
-            variants = policy_sweeps(prob, stream, args)
+        if rank == 0 and args.policies:
+            variants = {"solves": pair_solve_variant(prob, stream, args, s, b, x_ref),
+                        "sweeps": policy_sweeps(prob, stream, args)}
     my_updates = sum(updates_per_solve(prob, i) for i in its_list)
     my_e2e_updates = updates_per_solve(prob, its_h) * len(e2e_t)
     (total_ms, e2e_ms), (all_updates, all_e2e) = reduce_over_ranks(
@@ -266,13 +315,28 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         if dist:
             dist.destroy_process_group()
+        s.close()
         return 0
     hbm, peak_kind = peaks()
-    achieved = bytes_fine / (ms_fine / max(n_fine, 1) * 1e-3) / 1e9 if ms_fine > 0 else 0.0
+    avg_fine_ms = ms_fine / max(n_fine, 1)
+    gbs = bytes_fine / (avg_fine_ms * 1e-3) / 1e9 if ms_fine > 0 else 0.0
+    tflops = flops_fine / (avg_fine_ms * 1e-3) / 1e12 if ms_fine > 0 else 0.0
     traffic = load_traffic(args.prec) if not args.dedup else None
-    step_sorted = sorted(step_ms)
-    p50 = statistics.median(step_sorted)
-    p99 = step_sorted[min(len(step_sorted) - 1, int(math.ceil(0.99 * len(step_sorted))) - 1)]
+    if args.prec == "fp64":
+        peak_tf, peak_note = fp64_peak(torch)
+        roof = {"bound": "alu", "achieved": tflops, "peak": peak_tf, "unit": "TFLOP/s", "frac": tflops / peak_tf,
+                "traffic": traffic, "pipe": "FP64 (DFMA)",
+                "peak_source": peak_note,
+                "peak_probe_tflops": fp64_probe / 1e12, "frac_of_probe": tflops / (fp64_probe / 1e12),
+                "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm, "frac": gbs / hbm, "peak_source": peak_kind}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": traffic,
+                "peak_source": peak_kind}
+    roof.update({"kernel": "patch apply (cache_inverse) on the finest level", "launches": n_fine,
+                 "avg_launch_ms": avg_fine_ms, "algorithmic_bytes_per_launch": bytes_fine,
+                 "algorithmic_flop_per_launch": flops_fine,
+                 "timing": f"CUDA events on the solver stream around every finest-level apply of "
+                           f"{max(1, min(args.steps, args.profile_steps))} profiled solves after the timed ones"})
     out = {
         "metric": METRIC, "value": all_updates / (total_ms * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -283,37 +347,122 @@ def run_ours(args, rank, world, local_rank):
                                "r~U[0.04,0.12], alpha 1e-8, octree depth 3, 5 levels, V(2,2), "
                                "FGMRES(30) rtol 1e-8, Q1-Q1 (1,098,500 DoFs)",
                    "cache": args.cache, "patch_rows": args.prec, "shared_class_blocks": bool(args.dedup),
-                   "l2": "inputs larger than L2 (cached rows 3.5 GB per sweep)",
+                   "l2": "inputs larger than L2 (cached rows 4.1 GB per V-cycle)",
                    "iterations": its_list[0], "relres": max(rr_list), "setup_ms": setup_ms,
                    "solves_per_s": world * args.steps / (total_ms * 1e-3),
-                   "latency_ms_p50": p50, "latency_ms_p99": p99,
-                   "smoother": {"apply_launches": n_apply, "apply_ms": ms_apply,
-                                "residual_launches": n_res, "residual_ms": ms_res,
-                                "vcycles": n_vc, "vcycle_ms": ms_vc},
+                   "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99), "n": len(step_ms),
+                                  "note": "p99 of fewer than 100 samples is their maximum"},
+                   "smoother_profiled_pass": {"apply_launches": n_apply, "apply_ms": ms_apply,
+                                              "residual_launches": n_res, "residual_ms": ms_res,
+                                              "vcycles": n_vc, "vcycle_ms": ms_vc},
+                   "arith_probe": {"fp64_tflops": fp64_probe / 1e12, "fp32_tflops": fp32_probe / 1e12},
                    "parallelism": f"{world} independent problems, one per GPU" if world > 1 else "1 GPU",
                    "variants": variants},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": "patch apply (cache_inverse) on the finest level",
-                     "launches": n_fine, "avg_launch_ms": ms_fine / max(n_fine, 1),
-                     "algorithmic_bytes_per_launch": bytes_fine,
-                     "peak_source": peak_kind},
+        "roofline": roof,
         "e2e": {"value": all_e2e / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": 2 * n * 8,
                 "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches,
         "clocks": cl,
     }
     if not args.no_cpu_baseline:
-        ups, times, cores, _ = oracle_solve_rate(sample_workload(), budget_s=args.cpu_budget)
-        out["cpu_baseline"] = {"value": sum(ups) / sum(times), "unit": UNIT, "cores": cores,
-                               "kind": "oracle",
-                               "sample": f"{len(times)} oracle FGMRES-GMG solves of a 16^3 grid of the "
-                                         f"same 40-sphere geometry (3 levels), setup excluded"}
+        out["cpu_baseline"] = cpu_baseline(args)
     emit(out)
     if dist:
         dist.destroy_process_group()
     s.close()
     return 0
+
+
+def pair_solve_variant(prob, stream, args, s64, b, x64):
+    """The float-pair rows (df64: rows, residual and x as float32 pairs inside
+    the FP64 FGMRES) on the same workload: updates/s of the same timed solves,
+    and how far they land from the FP64 GPU path of this run (solution, and
+    one finest-level sweep).  The oracle parity of both paths is tested."""
+    import torch
+    from paper_2403_11636_gb300 import fc, inputs
+    try:
+        with torch.cuda.stream(stream):
+            t0 = time.perf_counter()
+            sd = fc.Solver(prob, cache="inverse", prec="df64", stream=stream, dedup=args.dedup)
+            torch.cuda.synchronize()
+            setup_ms = 1e3 * (time.perf_counter() - t0)
+            for _ in range(max(1, args.warmup)):
+                sd.solve(b, rtol=prob.rtol)
+            step_ms, total_ms, its_l, rr_l = timed_solves(sd, b, prob, args.steps, stream, torch)
+            x, _, _ = sd.solve(b, rtol=prob.rtol)
+            dx = (x.cpu() - x64).norm().item() / max(x64.norm().item(), 1e-300)
+            x0 = torch.as_tensor(inputs.random_vector(prob, 3)).cuda()
+            bb = torch.as_tensor(inputs.random_vector(prob, 4)).cuda()
+            s_d = sd.smooth(x0, bb) - x0
+            s_f = s64.smooth(x0, bb) - x0
+            dsw = (s_d - s_f).norm().item() / max(s_f.norm().item(), 1e-300)
+            sd.profile(True)
+            timed_solves(sd, b, prob, 1, stream, torch)
+            n_fine, ms_fine, bytes_fine = sd.profile_read(4)
+            sd.profile(False)
+            sd.close()
+        hbm, _ = peaks()
+        gbs = bytes_fine / (ms_fine / max(n_fine, 1) * 1e-3) / 1e9 if ms_fine > 0 else None
+        return {"df64/per-patch": {
+            "dtype": "f32x2", "updates_per_s": sum(updates_per_solve(prob, i) for i in its_l) / (total_ms * 1e-3),
+            "ms_per_solve": total_ms / len(step_ms), "iterations": its_l[0], "relres": max(rr_l),
+            "setup_ms": setup_ms,
+            "solution_rel_diff_vs_fp64_gpu": dx, "sweep_rel_diff_vs_fp64_gpu": dsw,
+            "oracle_parity": "per sweep <= 1e-10 relative (tests: test_gpu_fullsize, test_gpu_midsize, "
+                             "test_gpu_parity)",
+            "finest_apply_ms": ms_fine / max(n_fine, 1),
+            "finest_apply_hbm_frac": gbs / hbm if gbs else None}}
+    except Exception as e:  # reported, not fatal for the headline
+        return {"df64/per-patch": {"error": str(e)[:200]}}
+
+
+def cpu_baseline(args):
+    """The FP64 CPU oracle on the host cores, on a bounded sample of the
+    workload: FGMRES-GMG solves of the same 40-sphere geometry on a 16^3 grid
+    (3 levels; the metric's unit), and per-sweep times of the finest level of
+    that sample with every host thread and with one."""
+    from oracle import oracle as O
+    prob = sample_workload()
+    ups, times, cores, its = oracle_solve_rate(prob, budget_s=args.cpu_budget)
+    out = {"value": sum(ups) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{len(times)} oracle FGMRES-GMG solves of a 16^3 grid of the same 40-sphere geometry "
+                     f"(3 levels, {its[0]} iterations), setup (assembly, patch inverses) excluded"}
+    try:
+        sw = oracle_sweep_rate(args.cpu_sweep_n)
+        out["per_sweep"] = sw
+    except Exception as e:
+        out["per_sweep"] = {"error": str(e)[:200]}
+    return out
+
+
+def oracle_sweep_rate(n):
+    """Per-sweep time of the oracle (residual + cached-row patch apply over
+    every patch) on the finest level of an n^3 grid of the benchmark
+    geometry, with every host thread and with one; setup excluded."""
+    from oracle import oracle as O
+    from paper_2403_11636_gb300 import inputs
+    prob = inputs.porous_3d(0, n=n, nlevels=max(2, int(math.log2(n // 4)) + 1))
+    L = O.Level.from_problem(prob)
+    L.assemble()
+    L.build_inverse()
+    x = inputs.random_vector(prob, 3)
+    b = inputs.random_vector(prob, 4)
+    res = {"grid": f"{n}^3", "free_dofs": free_dofs(prob, prob.nlevels)}
+    nthr = O.num_threads()
+    for label, thr in (("all_threads", nthr), ("one_thread", 1)):
+        O.set_threads(thr)
+        L.sweep(b, x)
+        ts = []
+        t_end = time.perf_counter() + 3.0
+        while time.perf_counter() < t_end or len(ts) < 3:
+            t0 = time.perf_counter()
+            L.sweep(b, x)
+            ts.append(time.perf_counter() - t0)
+        ms = 1e3 * statistics.median(ts)
+        res[label] = {"threads": thr, "sweep_ms": ms, "updates_per_s": res["free_dofs"] / (ms * 1e-3),
+                      "samples": len(ts)}
+    O.set_threads(nthr)
+    return res
 
 
 def run_sweeps(args):
@@ -625,12 +774,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cache", default="inverse", choices=["inverse", "matrix", "none"])
-    ap.add_argument("--prec", default="df64", choices=["fp64", "df64", "fp32", "bf16"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "df64", "fp32", "bf16"])
     ap.add_argument("--policies", type=int, default=1)
     ap.add_argument("--dedup", type=int, default=0,
                     help="1: patches with bit-identical blocks share one stored block (same results)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-sweep-n", type=int, default=16,
+                    help="grid of the oracle per-sweep timing (16: the solve sample's finest level)")
+    ap.add_argument("--profile-steps", type=int, default=3,
+                    help="profiled solves after the timed ones (per-kernel CUDA events)")
     ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep"])
     ap.add_argument("--tile", default="", help="lanes,threads,ctas_per_sm of --mode batch-sweep")
     ap.add_argument("--batch", type=int, default=256, help="problems of --mode batch")

@@ -114,11 +114,26 @@ typedef struct {
   int dedup;           /* 1: patches with bit-identical blocks L_i (uncut, one alpha, away
                           from constraints) share one stored row/factor block; 0: one block
                           per patch (the paper's layout).  Same results either way. */
+  int tc;              /* float32 / bfloat16 rows with dedup 1: how the V-cycle applies the
+                          shared class blocks.  0: CUDA cores (float32 FMA); 1: tensor cores,
+                          rows and residual rounded to TF32; 2: tensor cores, rows and residual
+                          each split into two TF32 terms (three products, float32-class
+                          accuracy); 3: tensor cores, rows and residual in BF16.  FP32
+                          accumulation in every mode; cut patches (own blocks) always take
+                          the CUDA cores.  Ignored for FP64 / float-pair rows. */
+  double badcut_frac;  /* float32 / bfloat16 rows: a patch whose smallest cut-cell fluid
+                          fraction over the 4^d cells its velocity nodes touch is below
+                          badcut_frac gets its rows from the float-pair (FP64-class)
+                          factorisation instead of float32 factors with refinement; 0 off. */
 } fc_options;
 
-/* Fill defaults: eta 1e-3, beta 100, omega 0.8, V(2,2), depth 4 (2D) / 3 (3D)
- * is left to the caller (quad_depth = 4), cache_inverse, FP64, restart 30,
- * channel preset, ubar 0.3, constant zero force, dedup 1. */
+/* Fill the defaults:
+ *   eta 1e-3, nitsche_beta 100, omega 0.8 (Sec. 4), nu_pre = nu_post = 2;
+ *   quad_depth 4 (the 2D configurations; 3D problems use 3, set it);
+ *   cache FC_CACHE_INVERSE, prec FC_PREC_FP64, fgmres_restart 30;
+ *   bc_preset 0 (channel), ubar 0.3, force_kind 0 with force = 0;
+ *   dedup 1 (shared class blocks; the Python binding's default too);
+ *   tc 0 (CUDA cores), badcut_frac 1e-3. */
 fc_status fc_options_default(fc_options* o);
 
 /* Build the hierarchy of `depth` levels (paper Sec. 3, Algorithm 1 on a
@@ -166,7 +181,9 @@ fc_status fc_smooth(fc_handle h, int level, double* x_dev, const double* b_dev, 
  * call's contents: each call clears the part it uses first.  Calls whose
  * work overlaps on the GPU race on the array.  Errors: FC_ERR_INVALID when
  * the level's padded residual exceeds 16 MiB (3D up to 64^3 cells, 2D up to
- * about 700^2 in float64), FC_ERR_CUDA. */
+ * about 700^2 in float64) or when the current device is not the one that
+ * was current at fc_setup (the array is looked up on the current device),
+ * FC_ERR_CUDA. */
 fc_status fc_smooth_noalloc(fc_handle h, int level, double* x_dev, const double* b_dev, int nsweeps);
 
 /* b_coarse <- R r_fine from `level` to `level-1` (eq. restriction_op with the
@@ -212,7 +229,12 @@ fc_status fc_solve_host(fc_handle h, const double* b_host, double* x_host, doubl
  * solve, [4] setup temporaries peak; [5] is a count, not bytes: patches (all
  * levels) whose float32 factorisation with iterative refinement did not
  * converge and that were rebuilt by float-pair elimination (float32 /
- * bfloat16 rows only); [6..7] reserved. Any pointer may be NULL. */
+ * bfloat16 rows only); [6] is a count too: the algorithmic floating-point
+ * operations of one patch apply on `level` with cached rows, 2 x (active
+ * patch DoFs x free owned DoFs) summed over the patches (0 on level 1);
+ * [7] is a count: patches (all levels) whose rows came from the float-pair
+ * factorisation by the bad-cut rule (fc_options.badcut_frac; float32 /
+ * bfloat16 rows only).  Any pointer may be NULL. */
 fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch,
                   size_t* bytes_by_part);
 
@@ -244,6 +266,16 @@ fc_status fc_profile_read(fc_handle h, int kind, long long* launches, double* to
 /* Number of CUDA kernels libfc has launched in this process (all handles),
  * for launch accounting around timed regions. */
 fc_status fc_launch_count(long long* count);
+
+/* Arithmetic throughput of the current GPU, for the roofline of kernels
+ * bound by a pipe rather than by memory (the paper has no counterpart; its
+ * CPU runs need none).  precision 0: FP64 FMA, 1: FP32 FMA.  Runs
+ * independent FMA chains on every SM for one timed launch (CUDA events,
+ * after a warm-up launch) and stores FLOP/s (2 per FMA) in *flop_per_s and
+ * the launch's duration in *launch_ms (may be NULL).  Allocates a few bytes
+ * and a stream of its own; changes no device setting.  Synchronises.
+ * Errors: FC_ERR_INVALID (NULL output, other precision), FC_ERR_CUDA. */
+fc_status fc_probe_fma_rate(int precision, double* flop_per_s, double* launch_ms);
 
 /* ---- Batches: many independent problems in one set of launches --------
  *

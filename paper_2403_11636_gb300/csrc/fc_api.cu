@@ -6,7 +6,10 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "fc_internal.cuh"
 
@@ -19,6 +22,41 @@ void note_launches(int n) {
   if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }
 void set_capturing(bool on) { g_capturing = on; }
+
+cudaError_t persistent_ctas(const void* kern, int threads, size_t smem, int* per_sm, int* nsm) {
+  struct Key {
+    const void* k;
+    int dev, threads;
+    size_t smem;
+  };
+  struct Val {
+    int per_sm, nsm;
+  };
+  static std::mutex mu;
+  static std::vector<std::pair<Key, Val>> known;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& kv : known)
+    if (kv.first.k == kern && kv.first.dev == dev && kv.first.threads == threads && kv.first.smem == smem) {
+      *per_sm = kv.second.per_sm;
+      *nsm = kv.second.nsm;
+      return cudaSuccess;
+    }
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int ps = 0, ns = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (ps < 1) ps = 1;
+  known.push_back({{kern, dev, threads, smem}, {ps, ns}});
+  *per_sm = ps;
+  *nsm = ns;
+  return cudaSuccess;
+}
 }  // namespace fc
 
 namespace {
@@ -113,7 +151,10 @@ __global__ void count_active_kernel(LevelGeom g, const unsigned char* __restrict
                                     unsigned long long* __restrict__ out, const int* __restrict__ list,
                                     long long nlist) {
   // number of active (in-grid, unconstrained) patch DoFs summed over the
-  // patches of `list` (all patches when list is null)
+  // patches of `list` (all patches when list is null) into out[0], and the
+  // same count times the patch's free owned DoFs (the rows a patch solve
+  // needs: the pressure and the unconstrained velocities of its node) into
+  // out[1]
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (list ? nlist : g.nnodes)) return;
   long long i = list ? list[t] : t;
@@ -139,6 +180,42 @@ __global__ void count_active_kernel(LevelGeom g, const unsigned char* __restrict
         cnt += 1;
       }
   atomicAdd(out, cnt);
+  const unsigned long long owned = (mask[i] & 1) ? 1 : (unsigned long long)(g.dim + 1);
+  atomicAdd(out + 1, cnt * owned);
+}
+
+// Badly cut patches (fc_options.badcut_frac): among the work-list patches,
+// those whose smallest cut-cell fluid fraction over the 4^d cells between
+// their velocity nodes (cells i-2 .. i+1 per direction: the cells whose
+// element matrices enter L_i) lies below `frac`.  A cell is cut when its
+// fluid fraction (fluid volume from the cell quadrature / cell volume) is
+// strictly between 0 and 1.  Appends (patch, row block) to the lists.
+__global__ void badcut_kernel(LevelGeom g, const double* __restrict__ estat, const int* __restrict__ work,
+                              long long nwork, double frac, int* __restrict__ bad_node, int* __restrict__ bad_out,
+                              int* __restrict__ nbad) {
+  const long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= nwork) return;
+  const long long i = work ? work[w] : w;
+  const int ia[3] = {(int)(i % g.nn[0]), (int)((i / g.nn[0]) % g.nn[1]),
+                     g.dim == 3 ? (int)(i / ((long long)g.nn[0] * g.nn[1])) : 0};
+  const double vol = g.h[0] * g.h[1] * (g.dim == 3 ? g.h[2] : 1.0);
+  double fmin = 2.0;
+  const int r = g.dim == 3 ? 4 : 1;
+  for (int dz = 0; dz < r; ++dz)
+    for (int dy = 0; dy < 4; ++dy)
+      for (int dx = 0; dx < 4; ++dx) {
+        const int c0 = ia[0] + dx - 2, c1 = ia[1] + dy - 2, c2 = g.dim == 3 ? ia[2] + dz - 2 : 0;
+        if (c0 < 0 || c0 >= g.n[0] || c1 < 0 || c1 >= g.n[1]) continue;
+        if (g.dim == 3 && (c2 < 0 || c2 >= g.n[2])) continue;
+        const long long cell = c0 + (long long)g.n[0] * (c1 + (long long)g.n[1] * c2);
+        const double f = estat[cell * 4] / vol;
+        if (f > 0.0 && f < 1.0 && f < fmin) fmin = f;
+      }
+  if (fmin < frac) {
+    const int k = atomicAdd(nbad, 1);
+    bad_node[k] = (int)i;
+    bad_out[k] = (int)w;
+  }
 }
 
 }  // namespace
@@ -405,6 +482,8 @@ fc_status fc_options_default(fc_options* o) {
   o->ubar = 0.3;
   o->force_kind = 0;
   o->dedup = 1;
+  o->tc = 0;
+  o->badcut_frac = 1e-3;
   return FC_OK;
 }
 
@@ -486,7 +565,8 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   if (!(alpha > 0.0) || !(o->eta > 0.0) || !(o->omega > 0.0) || o->nu_pre < 0 || o->nu_post < 0 ||
       o->quad_depth < 0 || o->quad_depth > 6 || o->fgmres_restart < 1 || o->fgmres_restart > 256 ||
       o->bc_preset < 0 || o->bc_preset > 2 || o->force_kind < 0 || o->force_kind > 3 ||
-      !(o->nitsche_beta >= 0.0) || o->dedup < 0 || o->dedup > 1)
+      !(o->nitsche_beta >= 0.0) || o->dedup < 0 || o->dedup > 1 || o->tc < 0 || o->tc > 3 ||
+      !(o->badcut_frac >= 0.0 && o->badcut_frac < 1.0))
     return fail(h, FC_ERR_INVALID, "invalid options");
   if (o->cache < FC_CACHE_INVERSE || o->cache > FC_CACHE_NONE || o->prec < FC_PREC_FP64 || o->prec > FC_PREC_DF64)
     return fail(h, FC_ERR_INVALID, "invalid cache policy or precision");
@@ -514,6 +594,7 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   h->dim = g->dim;
   h->nlev = depth;
   h->restart = o->fgmres_restart;
+  CK(cudaGetDevice(&h->device));
   h->nshape = nshape;
 
   CK(dalloc(h, &h->d_err, 1, 2));
@@ -521,7 +602,7 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   CK(dalloc(h, &h->d_shapes, (size_t)std::max(nshape, 1), 0));
   if (nshape) CK(cudaMemcpyAsync(h->d_shapes, hs.data(), sizeof(Shape) * nshape, cudaMemcpyHostToDevice, h->stream));
   unsigned long long* d_count = nullptr;
-  CK(dalloc(h, &d_count, 1, -1));
+  CK(dalloc(h, &d_count, 2, -1));
 
   const int dim = g->dim, nd = dim + 1, nb = dim == 3 ? 27 : 9, nl = 1 << dim;
   for (int li = 0; li < depth; ++li) {
@@ -560,7 +641,12 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
       R.force[0] = R.force[1] = R.force[2] = 0.0;
       CK(launch_cell_elements(R, rA, rB, rF, nullptr, h->d_err, nullptr, nullptr, nullptr, h->stream));
     }
-    CK(launch_cell_elements(G, eA, eB, eF, nullptr, h->d_err, rA, rB, cclass, h->stream));
+    // cell fluid volumes for the bad-cut rule (float32 / bfloat16 rows)
+    const bool badcut = li > 0 && o->cache == FC_CACHE_INVERSE && o->badcut_frac > 0.0 &&
+                        (o->prec == FC_PREC_FP32 || o->prec == FC_PREC_BF16);
+    double* estat = nullptr;
+    if (badcut) CK(dalloc(h, &estat, (size_t)G.ncell * 4, -1));
+    CK(launch_cell_elements(G, eA, eB, eF, estat, h->d_err, rA, rB, cclass, h->stream));
     CK(dalloc(h, &L.st, (size_t)G.nnodes * nb * spn(dim), 0));
     CK(dalloc(h, &L.mask, (size_t)G.nnodes, 0));
     CK(dalloc(h, &L.wfix, (size_t)G.ndof, 0));
@@ -647,17 +733,21 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     if (li > 0) {
       for (int pass = 0; pass < 2; ++pass) {
         if (pass == 1 && !work) break;
-        CK(cudaMemsetAsync(d_count, 0, sizeof(unsigned long long), h->stream));
+        CK(cudaMemsetAsync(d_count, 0, 2 * sizeof(unsigned long long), h->stream));
         const long long cnt_n = pass == 0 ? G.nnodes : L.nwork;
         count_active_kernel<<<(unsigned)((cnt_n + 255) / 256), 256, 0, h->stream>>>(
             G, L.mask, d_count, pass == 0 ? nullptr : work, cnt_n);
         CK(cudaGetLastError());
         note_launches(1);
-        unsigned long long cnt = 0;
-        CK(cudaMemcpyAsync(&cnt, d_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+        unsigned long long cnt[2] = {0, 0};
+        CK(cudaMemcpyAsync(cnt, d_count, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
-        if (pass == 0) L.active_slots = cnt;
-        else L.active_work = cnt;
+        if (pass == 0) {
+          L.active_slots = cnt[0];
+          L.active_rows = cnt[1];
+        } else {
+          L.active_work = cnt[0];
+        }
       }
       if (o->cache == FC_CACHE_INVERSE) {
         size_t n = (size_t)L.nwork * nslot(dim) * nd;
@@ -686,6 +776,20 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
             if (nr > 0)
               CK(launch_patch_rows_pair(G, L.st, L.mask, c64, h->d_err, redo_node, nr, redo_out, h->stream));
             h->pair_fallback += nr;
+            if (estat) {
+              // badly cut patches: float pairs whatever the refinement did
+              CK(cudaMemsetAsync(nredo, 0, sizeof(int), h->stream));
+              badcut_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, h->stream>>>(G, estat, work, nw, o->badcut_frac,
+                                                                               redo_node, redo_out, nredo);
+              CK(cudaGetLastError());
+              note_launches(1);
+              int nb = 0;
+              CK(cudaMemcpyAsync(&nb, nredo, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+              CK(cudaStreamSynchronize(h->stream));
+              if (nb > 0)
+                CK(launch_patch_rows_pair(G, L.st, L.mask, c64, h->d_err, redo_node, nb, redo_out, h->stream));
+              h->badcut += nb;
+            }
             dfree(h, redo_node);
             dfree(h, redo_out);
             dfree(h, nredo);
@@ -719,6 +823,7 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
       st = check_err(h);
       if (st != FC_OK) return st;
     }
+    dfree(h, estat);
   }
   dfree(h, d_count);
   // ---- coarse solve
@@ -970,6 +1075,8 @@ fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch, si
   if (bytes_by_part) {
     for (int k = 0; k < 8; ++k) bytes_by_part[k] = h->bytes[k];
     bytes_by_part[5] = (size_t)h->pair_fallback;
+    bytes_by_part[6] = level >= 2 ? (size_t)(2 * L.active_rows) : 0;
+    bytes_by_part[7] = (size_t)h->badcut;
   }
   return FC_OK;
 }

@@ -72,6 +72,11 @@ struct BSeg {
   float* d32;
   float* b32;
   float omega_f;
+  // tensor-core apply of the shared class blocks: the stored blocks of the
+  // classes 1 and 2 (-1: none) and their rows as the MMA tile (see
+  // f_apply_tc_kernel; null when the batch does not use tensor cores)
+  int cls[2];
+  const void* tcA;
 };
 
 struct Chunk {
@@ -678,6 +683,247 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core apply of the shared class blocks (float32 correction form).
+// Patches of a class (bit-identical L_i: uncut, one alpha, away from
+// constraints) share one row block Inv_k ((d+1) x nslot), so their updates
+// are one dense product (Sec. 3.1.2 cache_inverse, applied to many patches
+// at once): the rows of both class blocks, stacked as rows 4k + c (class k,
+// component c) of the M = 16 side of an m16n8 MMA tile (rows 8-15 zero),
+// times the gathered residuals of 8 patches (N = 8, one column per patch)
+// over K = the patch slots (zero rows past nslot).  A patch keeps the rows of
+// its own class.  Cut patches (blocks of their own) take the CUDA cores with
+// 8 lanes each.  A warp owns 32 consecutive nodes of a 256-node chunk.
+//   MODE 1: rows and residual rounded to TF32, one m16n8k8 product per step;
+//   MODE 2: both split into a TF32 head and a TF32 tail, three products
+//           (head x head, head x tail, tail x head): float32-class accuracy;
+//   MODE 3: rows and residual in BF16, one m16n8k16 product per step.
+// FP32 accumulation in every mode.
+template <int DIM>
+struct TcDims {
+  static constexpr int NSLOT = DIM == 3 ? 402 : 59;
+  static constexpr int KP = DIM == 3 ? 416 : 64;   // slots padded to the MMA K steps
+  // row strides of the staged tile (in elements): 32-bit rows at 4 mod 32
+  // words, bf16 rows at 20 mod 32 words, so the 8 fragment rows fall on
+  // distinct banks
+  static constexpr int KS32 = KP + 4;
+  static constexpr int KS16 = DIM == 3 ? 424 : 104;
+};
+
+template <int DIM, int MODE>
+__host__ __device__ constexpr size_t tc_tile_bytes() {
+  return MODE == 3 ? (size_t)8 * TcDims<DIM>::KS16 * 2 : (size_t)(MODE == 2 ? 2 : 1) * 8 * TcDims<DIM>::KS32 * 4;
+}
+
+__device__ __forceinline__ unsigned to_tf32(float v) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float* d, unsigned a0, unsigned a2, unsigned b0, unsigned b1) {
+  // rows 8-15 of the A tile are zero (a1 = a3 = 0)
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(0u), "r"(a2), "r"(0u), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, unsigned a0, unsigned a2, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(0u), "r"(a2), "r"(0u), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// the staged tile of a segment: rows 4k + c of the class blocks, written
+// once per batch from the stored rows (float32 or bfloat16) of the blocks
+template <int DIM, int MODE, typename T>
+__global__ void tc_prepare_kernel(const T* __restrict__ coef, int cls0, int cls1, void* out) {
+  using D = TcDims<DIM>;
+  constexpr int ND = DIM + 1;
+  for (int t = threadIdx.x + blockIdx.x * blockDim.x; t < 8 * D::KP; t += blockDim.x * gridDim.x) {
+    const int row = t / D::KP, j = t % D::KP, k = row >> 2, c = row & 3;
+    const int blk = k == 0 ? cls0 : cls1;
+    float v = 0.0f;
+    if (blk >= 0 && c < ND && j < D::NSLOT) v = (float)coef[((size_t)blk * D::NSLOT + j) * ND + c];
+    if (MODE == 3) {
+      reinterpret_cast<__nv_bfloat16*>(out)[row * D::KS16 + j] = __float2bfloat16_rn(v);
+    } else {
+      const unsigned head = to_tf32(v);
+      reinterpret_cast<unsigned*>(out)[row * D::KS32 + j] = head;
+      if (MODE == 2) reinterpret_cast<unsigned*>(out)[8 * D::KS32 + row * D::KS32 + j] = to_tf32(v - __uint_as_float(head));
+    }
+  }
+}
+
+template <int DIM, int PT, int MODE>
+__global__ void __launch_bounds__(256)
+    f_apply_tc_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch,
+                      const int* __restrict__ state, int gate) {
+  using D = TcDims<DIM>;
+  constexpr int ND = DIM + 1, NSLOT = D::NSLOT, KP = D::KP;
+  using RL = RowLoad<PT, ND>;
+  using T = typename RL::T;
+  extern __shared__ __align__(16) unsigned char tc_shm[];
+  int* soff = reinterpret_cast<int*>(tc_shm);                 // KP slot offsets (0 past nslot)
+  unsigned* sA = reinterpret_cast<unsigned*>(tc_shm + KP * 4);  // the staged tile
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t4 = lane & 3;
+  const BSeg* cur = nullptr;
+  for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+    const Chunk k = ch[c];
+    const BSeg* S = segs + k.seg;
+    if (state && state[S->prob] != gate) continue;  // uniform over the CTA
+    const BGeom gm = S->g;
+    if (S != cur) {
+      __syncthreads();
+      const int px = gm.nn[0] + 4, py = gm.nn[1] + 4;
+      for (int j = threadIdx.x; j < KP; j += blockDim.x) soff[j] = j < NSLOT ? slot_offset<DIM>(j, px, py) : 0;
+      if (S->tcA) {
+        const uint4* src = reinterpret_cast<const uint4*>(S->tcA);
+        uint4* dst = reinterpret_cast<uint4*>(sA);
+        for (int t = threadIdx.x; t < (int)(tc_tile_bytes<DIM, MODE>() / 16); t += blockDim.x) dst[t] = src[t];
+      }
+      __syncthreads();
+      cur = S;
+    }
+    const T* __restrict__ coef = static_cast<const T*>(S->coef);
+    const int* __restrict__ prow = S->prow;
+    const unsigned char* __restrict__ mask = S->mask;
+    const float* __restrict__ rpad = S->rpadf;
+    float* d = S->d32;
+    const float omega = S->omega_f;
+    const long long node = (long long)k.node0 + warp * 32 + lane;
+    const bool valid = node < gm.nnodes;
+    const unsigned i = (unsigned)(valid ? node : gm.nnodes - 1);
+    int ia[3];
+    decode(gm, DIM, i, ia);
+    const long long pb = padded(gm, DIM, ia) * ND;
+    const int pr = prow ? prow[i] : (int)i;
+    int cls = -1;
+    if (S->tcA && pr < 0) {
+      const int blk = -pr - 1;
+      cls = blk == S->cls[0] ? 0 : (blk == S->cls[1] ? 1 : -1);
+    }
+    const unsigned mc = __ballot_sync(0xffffffffu, valid && cls >= 0);
+    const unsigned mu = __ballot_sync(0xffffffffu, valid && cls < 0);
+    // ---- class patches: up to 4 tiles of 8 patches on the tensor cores
+    const int ncls = __popc(mc);
+    if (ncls) {
+      const int ntile = (ncls + 7) >> 3;
+      long long tb[4];   // padded base of patch g of each tile
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int idx = min(8 * t + g, ncls - 1);
+        const int src = __fns(mc, 0, idx + 1);
+        tb[t] = __shfl_sync(0xffffffffu, pb, src);
+      }
+      float acc[4][4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.0f;
+      if (MODE == 3) {
+        const unsigned* arow = sA + g * (D::KS16 / 2);
+#pragma unroll 2
+        for (int k0 = 0; k0 < KP; k0 += 16) {
+          const unsigned a0 = arow[k0 / 2 + t4], a2 = arow[k0 / 2 + t4 + 4];
+          const int o0 = soff[k0 + 2 * t4], o1 = soff[k0 + 2 * t4 + 1];
+          const int o2 = soff[k0 + 2 * t4 + 8], o3 = soff[k0 + 2 * t4 + 9];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            if (t >= ntile) break;
+            const float* rp = rpad + tb[t];
+            mma_bf16(acc[t], a0, a2, pack_bf16(rp[o0], rp[o1]), pack_bf16(rp[o2], rp[o3]));
+          }
+        }
+      } else {
+        const unsigned* ah = sA + g * D::KS32;
+        const unsigned* al = sA + 8 * D::KS32 + g * D::KS32;
+#pragma unroll 2
+        for (int k0 = 0; k0 < KP; k0 += 8) {
+          const unsigned a0 = ah[k0 + t4], a2 = ah[k0 + t4 + 4];
+          unsigned l0 = 0u, l2 = 0u;
+          if (MODE == 2) {
+            l0 = al[k0 + t4];
+            l2 = al[k0 + t4 + 4];
+          }
+          const int o0 = soff[k0 + t4], o1 = soff[k0 + t4 + 4];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            if (t >= ntile) break;
+            const float* rp = rpad + tb[t];
+            const float r0 = rp[o0], r1 = rp[o1];
+            const unsigned h0 = to_tf32(r0), h1 = to_tf32(r1);
+            if (MODE == 2) {
+              const unsigned e0 = to_tf32(r0 - __uint_as_float(h0)), e1 = to_tf32(r1 - __uint_as_float(h1));
+              mma_tf32(acc[t], a0, a2, e0, e1);
+              mma_tf32(acc[t], l0, l2, h0, h1);
+            }
+            mma_tf32(acc[t], a0, a2, h0, h1);
+          }
+        }
+      }
+      // thread (g, t4) holds row g (class g / 4, component g % 4) of the
+      // patches 2 t4 and 2 t4 + 1 of every tile
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (t >= ntile) break;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int idx = 8 * t + 2 * t4 + e;
+          const int src = __fns(mc, 0, min(idx, ncls - 1) + 1);
+          const int cn = __shfl_sync(0xffffffffu, cls, src);
+          const long long pbn = __shfl_sync(0xffffffffu, pb, src);
+          const int comp = g & 3;
+          if (idx < ncls && cn == (g >> 2) && comp < ND) d[pbn + comp] += omega * acc[t][e];
+        }
+      }
+    }
+    // ---- patches with their own rows: 8 lanes per patch, 4 at a time
+    const int nu = __popc(mu);
+    const int q = lane >> 3, l8 = lane & 7;
+    for (int base = 0; base < nu; base += 4) {
+      const int idx = base + q;
+      const int src = __fns(mu, 0, min(idx, nu - 1) + 1);
+      const long long pbq = __shfl_sync(0xffffffffu, pb, src);
+      const int prq = __shfl_sync(0xffffffffu, pr, src);
+      const unsigned iq = __shfl_sync(0xffffffffu, i, src);
+      const bool shared_rows = prq < 0;
+      const T* cf = coef + (size_t)(shared_rows ? -prq - 1 : prq) * NSLOT * ND;
+      const float* rp = rpad + pbq;
+      float y[ND];
+#pragma unroll
+      for (int u = 0; u < ND; ++u) y[u] = 0.0f;
+#pragma unroll 4
+      for (int j = l8; j < NSLOT; j += 8) {
+        const float rv = rp[soff[j]];
+        float cv[ND];
+        RL::load(cf + (size_t)j * ND, shared_rows, cv);
+#pragma unroll
+        for (int u = 0; u < ND; ++u) y[u] = fmaf(cv[u], rv, y[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < ND; ++u)
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) y[u] += __shfl_xor_sync(0xffffffffu, y[u], o);
+      if (idx < nu && l8 < ND) {
+        float yl = y[0];
+#pragma unroll
+        for (int u = 1; u < ND; ++u)
+          if (l8 == u) yl = y[u];
+        const bool fixed = l8 < DIM && ((mask[iq] >> l8) & 1);
+        d[pbq + l8] += fixed ? rp[l8] : omega * yl;
+      }
+    }
+  }
+}
+
 // coarse b32 = R r (fine padded residual), coarse d = 0
 template <int DIM>
 __global__ void __launch_bounds__(256)
@@ -1063,6 +1309,20 @@ ApplyFn fapply_fn(int tpp) {
   }
 }
 
+template <int DIM, int PT>
+ApplyFn tcapply_fn(int mode) {
+  if (mode == 1) return f_apply_tc_kernel<DIM, PT, 1>;
+  if (mode == 2) return f_apply_tc_kernel<DIM, PT, 2>;
+  return f_apply_tc_kernel<DIM, PT, 3>;
+}
+
+size_t tc_bytes(int dim, int mode) {
+  if (dim == 2) return mode == 1 ? tc_tile_bytes<2, 1>() : mode == 2 ? tc_tile_bytes<2, 2>() : tc_tile_bytes<2, 3>();
+  return mode == 1 ? tc_tile_bytes<3, 1>() : mode == 2 ? tc_tile_bytes<3, 2>() : tc_tile_bytes<3, 3>();
+}
+
+size_t tc_smem(int dim, int mode) { return (size_t)(dim == 3 ? TcDims<3>::KP : TcDims<2>::KP) * 4 + tc_bytes(dim, mode); }
+
 ApplyFn pick_apply(int dim, fc_prec prec, int tpp) {
   if (prec == FC_PREC_FP32) return dim == 2 ? fapply_fn<2, 1>(tpp) : fapply_fn<3, 1>(tpp);
   if (prec == FC_PREC_BF16) return dim == 2 ? fapply_fn<2, 2>(tpp) : fapply_fn<3, 2>(tpp);
@@ -1078,6 +1338,8 @@ struct fc_batch_s {
   int nprob = 0, dim = 0, maxl = 0, m = 30, nu_pre = 0, nu_post = 0;
   fc_prec prec = FC_PREC_FP32;
   bool f32 = false;  // float32 correction form (float32 / bfloat16 rows)
+  int tc = 0;        // tensor-core apply of the class blocks (fc_options.tc), float32 form only
+  std::vector<void*> tcbuf;  // staged MMA tiles of the segments
   cudaStream_t user = nullptr, s = nullptr;
   cudaEvent_t ev = nullptr;
   std::vector<fc_handle> hs;
@@ -1127,6 +1389,24 @@ namespace {
 
 using namespace fc;
 
+cudaError_t prepare_tc_tile(int dim, int mode, fc_prec prec, const void* coef, int c0, int c1, void* out,
+                            cudaStream_t s) {
+  const bool f = prec == FC_PREC_FP32;
+  const float* cf = static_cast<const float*>(coef);
+  const __nv_bfloat16* cb = static_cast<const __nv_bfloat16*>(coef);
+  if (dim == 2) {
+    if (mode == 1) f ? tc_prepare_kernel<2, 1><<<4, 256, 0, s>>>(cf, c0, c1, out) : tc_prepare_kernel<2, 1><<<4, 256, 0, s>>>(cb, c0, c1, out);
+    else if (mode == 2) f ? tc_prepare_kernel<2, 2><<<4, 256, 0, s>>>(cf, c0, c1, out) : tc_prepare_kernel<2, 2><<<4, 256, 0, s>>>(cb, c0, c1, out);
+    else f ? tc_prepare_kernel<2, 3><<<4, 256, 0, s>>>(cf, c0, c1, out) : tc_prepare_kernel<2, 3><<<4, 256, 0, s>>>(cb, c0, c1, out);
+  } else {
+    if (mode == 1) f ? tc_prepare_kernel<3, 1><<<16, 256, 0, s>>>(cf, c0, c1, out) : tc_prepare_kernel<3, 1><<<16, 256, 0, s>>>(cb, c0, c1, out);
+    else if (mode == 2) f ? tc_prepare_kernel<3, 2><<<16, 256, 0, s>>>(cf, c0, c1, out) : tc_prepare_kernel<3, 2><<<16, 256, 0, s>>>(cb, c0, c1, out);
+    else f ? tc_prepare_kernel<3, 3><<<16, 256, 0, s>>>(cf, c0, c1, out) : tc_prepare_kernel<3, 3><<<16, 256, 0, s>>>(cb, c0, c1, out);
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
 fc_status bfail(fc_batch b, fc_status st, const std::string& msg) {
   if (b) b->err = msg;
   return st;
@@ -1163,6 +1443,18 @@ fc_status residual(fc_batch B, const Plan& p, int out, int use_b, const int* sta
 
 fc_status apply(fc_batch B, const Plan& p, const Tile& t, const int* state, int gate) {
   if (p.count == 0) return FC_OK;
+  if (B->f32 && B->tc) {
+    const int pt = B->prec == FC_PREC_FP32 ? 1 : 2;
+    ApplyFn fn = B->dim == 2 ? (pt == 1 ? tcapply_fn<2, 1>(B->tc) : tcapply_fn<2, 2>(B->tc))
+                             : (pt == 1 ? tcapply_fn<3, 1>(B->tc) : tcapply_fn<3, 2>(B->tc));
+    const size_t smem = tc_smem(B->dim, B->tc);
+    int per_sm = 0, nsm = 0;
+    BK(persistent_ctas((const void*)fn, 256, smem, &per_sm, &nsm));
+    fn<<<grid_of(B, p, per_sm), 256, smem, B->s>>>(B->segs, B->chunks + p.first, p.count, state, gate);
+    note_launches(1);
+    BK(cudaGetLastError());
+    return FC_OK;
+  }
   ApplyFn fn = pick_apply(B->dim, B->prec, t.tpp);
   const unsigned grid = grid_of(B, p, t.ctas_per_sm);
   fn<<<grid, t.threads, 0, B->s>>>(B->segs, B->chunks + p.first, p.count, state, gate);
@@ -1351,6 +1643,8 @@ void free_batch(fc_batch B) {
                   B->state, B->its, B->kk, B->dj, B->count, B->bh, B->xh};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (void* p : B->tcbuf)
+    if (p) cudaFree(p);
   if (B->hcount) cudaFreeHost(B->hcount);
   if (B->ev) cudaEventDestroy(B->ev);
   if (B->s) cudaStreamDestroy(B->s);
@@ -1459,7 +1753,7 @@ fc_status handle_vcycle_f32(fc_handle h, double* x, const double* b, bool xzero)
     const long long np = h->lev[h->nlev - 1].g.nnodes;
     int cls = 0;
     while ((1LL << (cls + 1)) <= np) ++cls;
-    const long long key = ((long long)h->dim * 8 + (long long)h->opt.prec) * 64 + cls;
+    const long long key = (((long long)h->dim * 8 + (long long)h->opt.prec) * 4 + h->opt.tc) * 64 + cls;
     std::lock_guard<std::mutex> lk(g_tile_mu);
     auto it = g_tiles.find(key);
     fc_status st = create_batch(&h->self_batch, &one, 1, h->stream, it == g_tiles.end() ? nullptr : &it->second);
@@ -1536,6 +1830,7 @@ fc_status create_batch(fc_batch* out, const fc_handle* handles, int nprob, void*
   B->dim = h0->dim;
   B->prec = h0->opt.prec;
   B->f32 = B->prec == FC_PREC_FP32 || B->prec == FC_PREC_BF16;
+  B->tc = B->f32 ? h0->opt.tc : 0;
   B->m = h0->restart;
   B->nu_pre = h0->opt.nu_pre;
   B->nu_post = h0->opt.nu_post;
@@ -1553,6 +1848,8 @@ fc_status create_batch(fc_batch* out, const fc_handle* handles, int nprob, void*
       return bfail(B, FC_ERR_INVALID, "batches take cache_inverse handles with fp64, fp32 or bf16 rows");
     if (h->opt.prec != B->prec || h->restart != B->m || h->opt.nu_pre != B->nu_pre || h->opt.nu_post != B->nu_post)
       return bfail(B, FC_ERR_INVALID, "row precision, FGMRES restart and sweep counts must agree across the batch");
+    if (B->f32 && h->opt.tc != B->tc)
+      return bfail(B, FC_ERR_INVALID, "the tensor-core mode (fc_options.tc) must agree across the batch");
     B->hs.push_back(h);
     B->maxl = std::max(B->maxl, h->nlev);
   }
@@ -1596,6 +1893,16 @@ fc_status create_batch(fc_batch* out, const fc_handle* handles, int nprob, void*
       S.d32 = L.d32;
       S.b32 = L.b32;
       S.omega_f = (float)h->opt.omega;
+      S.cls[0] = L.cls_blk[0];
+      S.cls[1] = L.cls_blk[1];
+      S.tcA = nullptr;
+      if (B->tc && li > 0 && L.coef && (L.cls_blk[0] >= 0 || L.cls_blk[1] >= 0)) {
+        void* buf = nullptr;
+        BK(cudaMalloc(&buf, tc_bytes(B->dim, B->tc)));
+        B->tcbuf.push_back(buf);
+        BK(prepare_tc_tile(B->dim, B->tc, B->prec, L.coef, L.cls_blk[0], L.cls_blk[1], buf, B->s));
+        S.tcA = buf;
+      }
       if (B->f32 && (!L.d32 || !L.b32 || (li > 0 && !L.st32)))
         return bfail(B, FC_ERR_INVALID, "handle without float32 level vectors");
       if (li > 0 && !L.coef) return bfail(B, FC_ERR_INVALID, "handle without a patch cache");
@@ -1662,6 +1969,8 @@ fc_status create_batch(fc_batch* out, const fc_handle* handles, int nprob, void*
   BK(cudaMalloc(&B->R, sizeof(double) * (size_t)B->ntot));
   if (fixed) {
     B->tile = *fixed;
+  } else if (B->tc) {
+    // the tensor-core apply has a fixed tile (a warp per 32 nodes of a chunk)
   } else {
     fc_status st = autotune(B);
     if (st != FC_OK) return st;

@@ -100,6 +100,7 @@ struct Level {
   float* b32 = nullptr;
   size_t vec_bytes = 0;
   unsigned long long active_slots = 0;  // sum over patches of active patch DoFs
+  unsigned long long active_rows = 0;   // sum over patches of active DoFs x free owned DoFs
   // patch classes (bit-identical L_i): prow[i] = row block of patch i;
   // nwork row blocks are factored and stored
   int* prow = nullptr;
@@ -126,6 +127,7 @@ struct fc_handle_s {
   fc_options opt;
   double alpha = 0;
   cudaStream_t stream = nullptr;
+  int device = -1;  // CUDA device current at fc_setup (holds every buffer of the handle)
   fc::Shape* d_shapes = nullptr;
   int nshape = 0;
   unsigned* d_err = nullptr;
@@ -153,6 +155,9 @@ struct fc_handle_s {
   // float32 / bfloat16 rows: patches rebuilt by the float-pair elimination
   // because float32 refinement did not converge (all levels)
   long long pair_fallback = 0;
+  // float32 / bfloat16 rows: patches given float-pair rows by the bad-cut
+  // rule (fc_options.badcut_frac), all levels
+  long long badcut = 0;
   bool capturing = false;
   fc::Profile prof;
   std::string err;
@@ -162,6 +167,10 @@ namespace fc {
 
 // process-wide count of libfc kernel launches (fc_api.cu)
 void note_launches(int n);
+// resident CTAs per SM of a persistent kernel and the SM count, on the
+// current device: computed once per (kernel, device) under a lock, after
+// raising the kernel's dynamic shared-memory limit on that device (fc_api.cu)
+cudaError_t persistent_ctas(const void* kern, int threads, size_t smem, int* per_sm, int* nsm);
 // launches recorded while a stream capture is open are counted at replay
 void set_capturing(bool on);
 // float32 correction-form V-cycle of a handle (x known zero: xzero)

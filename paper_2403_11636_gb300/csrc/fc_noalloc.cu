@@ -17,6 +17,8 @@
 //    start of the call;
 //  - calls whose work overlaps on the GPU (other streams, other host
 //    threads) race on the array; serialise them.
+//  - the handle's device (current at fc_setup) must be the current device;
+//    other devices are rejected with FC_ERR_INVALID;
 //  - the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (with that device current) and caches it; make that
 //    first call before any stream capture.
@@ -65,6 +67,13 @@ extern "C" fc_status fc_smooth_noalloc(fc_handle h, int level, double* x, const 
   if (!h->ready) return fail(h, FC_ERR_INVALID, "handle not set up (fc_setup failed)");
   if (level < 2 || level > h->nlev) return fail(h, FC_ERR_INVALID, "level out of range");
   if (!x || !b || nsweeps < 0) return fail(h, FC_ERR_INVALID, "bad smoother arguments");
+  {
+    // the scratch array is looked up on the current device: it must be the
+    // device that holds the handle's operator and patch cache
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
+      return fail(h, FC_ERR_INVALID, "fc_smooth_noalloc: the handle's device is not the current device");
+  }
   const Level& L = h->lev[level - 1];
   const fc_prec prec = h->opt.prec;
   const bool inverse = h->opt.cache == FC_CACHE_INVERSE;

@@ -515,6 +515,29 @@ __device__ __forceinline__ T pick(const T* v, int c) {
   return r;
 }
 
+// Sum of four per-lane partial sums over a group of TPP lanes (TPP >= 4, a
+// power of two, groups aligned within the warp) as a reduce-scatter: the
+// first exchange halves the values a lane carries, the second halves them
+// again, the remaining ones add a single value.  A lane ends with the full
+// sum of value *c (c = 2 * bit(TPP/2) + bit(TPP/4) of its group lane); every
+// FP64 add counts on this part (FP64 at 1/64 of the FP32 rate), and this
+// takes 3 + log2(TPP/4) adds per lane instead of 4 log2(TPP).
+template <int TPP>
+__device__ __forceinline__ double reduce_scatter4(const double* y, int lane, int* c) {
+  static_assert(TPP >= 4 && (TPP & (TPP - 1)) == 0, "group of at least 4 lanes");
+  const bool h1 = lane & (TPP / 2), h2 = lane & (TPP / 4);
+  double k0 = h1 ? y[2] : y[0], k1 = h1 ? y[3] : y[1];
+  const double s0 = h1 ? y[0] : y[2], s1 = h1 ? y[1] : y[3];
+  k0 += __shfl_xor_sync(0xffffffffu, s0, TPP / 2);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, TPP / 2);
+  double k = h2 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, h2 ? k0 : k1, TPP / 4);
+#pragma unroll
+  for (int o = TPP / 8; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  *c = (h1 ? 2 : 0) + (h2 ? 1 : 0);
+  return k;
+}
+
 template <int DIM, int TPP>
 __global__ void __launch_bounds__(256)
     apply_fp64_kernel(LevelGeom g, const double* __restrict__ coef, const unsigned char* __restrict__ mask,
@@ -537,26 +560,31 @@ __global__ void __launch_bounds__(256)
   const int pr = prow ? prow[i] : (int)i;
   const bool shared_rows = pr < 0;  // class rows: read through the cache
   const double* cf = coef + (size_t)(shared_rows ? -pr - 1 : pr) * NSLOT * ND;
-  double y[ND];
-#pragma unroll
-  for (int k = 0; k < ND; ++k) y[k] = 0.0;
-#pragma unroll 2
+  double y[4] = {0.0, 0.0, 0.0, 0.0};  // 2D: y[3] stays zero
+#pragma unroll 4
   for (int j = lane; j < NSLOT; j += TPP) {
     double rv = rp[soff[j]];
     if (ND == 4) {
       const double2* c2 = reinterpret_cast<const double2*>(cf + (size_t)j * 4);
       double2 a = ldrow(c2, shared_rows), b = ldrow(c2 + 1, shared_rows);
-      y[0] += a.x * rv; y[1] += a.y * rv; y[2] += b.x * rv; y[ND - 1] += b.y * rv;
+      y[0] += a.x * rv; y[1] += a.y * rv; y[2] += b.x * rv; y[3] += b.y * rv;
     } else {
 #pragma unroll
       for (int k = 0; k < ND; ++k) y[k] += ldrow(cf + (size_t)j * ND + k, shared_rows) * rv;
     }
   }
+  if constexpr (TPP >= 4) {
+    // the lane whose group-lane bits below TPP/4 are zero writes component c
+    int c = 0;
+    const double yc = reduce_scatter4<TPP>(y, lane, &c);
+    if (valid && c < ND && (lane & (TPP / 4 - 1)) == 0) owned_update<ND>(i, c, mask, rp[c], yc, omega, x, nullptr);
+  } else {
 #pragma unroll
-  for (int k = 0; k < ND; ++k)
+    for (int k = 0; k < ND; ++k)
 #pragma unroll
-    for (int o = TPP / 2; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
-  if (valid && lane < ND) owned_update<ND>(i, lane, mask, rp[lane], pick<ND>(y, lane), omega, x, nullptr);
+      for (int o = TPP / 2; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
+    if (valid && lane < ND) owned_update<ND>(i, lane, mask, rp[lane], pick<ND>(y, lane), omega, x, nullptr);
+  }
 }
 
 // float32 / bfloat16 rows with float32 residual and float32 accumulation
@@ -1020,16 +1048,29 @@ __global__ void __launch_bounds__(256)
 // the loads latency-bound).  FC_APPLY_TPP (2, 4, 8, 16, 32) overrides the
 // choice of the float-pair apply for tuning runs.
 int apply_tpp(int dim) {
-  static int env = -1;
-  if (env < 0) {
-    env = 0;
-    if (const char* e = getenv("FC_APPLY_TPP")) {
-      const int t = atoi(e);
-      if (t == 2 || t == 4 || t == 8 || t == 16 || t == 32) env = t;
-    }
-  }
+  static const int env = [] {
+    const char* e = getenv("FC_APPLY_TPP");
+    const int t = e ? atoi(e) : 0;
+    return (t == 2 || t == 4 || t == 8 || t == 16 || t == 32) ? t : 0;
+  }();
   if (env) return env;
   return dim == 3 ? 32 : 4;
+}
+
+// lanes per patch of the FP64-row apply.  The kernel is bound by the FP64
+// pipe (2 FMA per clock per SM on this part), so the group is kept small:
+// each lane then accumulates more slots and the group's reduction adds
+// little (8 lanes: 4 FP64 adds per lane, 2 % of a 3D patch's 1,608 FMA;
+// 32 lanes: 6 per lane, 12 %).  4 lanes in 2D (59 slots).  FC_APPLY64_TPP
+// (4, 8, 16, 32) overrides the choice for tuning runs.
+int apply64_tpp(int dim) {
+  static const int env = [] {
+    const char* e = getenv("FC_APPLY64_TPP");
+    const int t = e ? atoi(e) : 0;
+    return (t == 4 || t == 8 || t == 16 || t == 32) ? t : 0;
+  }();
+  if (env) return dim == 2 ? (env >= 8 ? 8 : 4) : env;
+  return dim == 3 ? 8 : 4;
 }
 
 template <int DIM, int TPP>
@@ -1039,18 +1080,9 @@ cudaError_t run_df_persistent_t(const LevelGeom& g, const float2* coef, const un
   using P = PatchDims<DIM>;
   const size_t smem = (size_t)kMaxClassBlocks * P::NSLOT * P::ND * sizeof(float2);
   auto kern = apply_df_persistent_kernel<DIM, TPP>;
-  static int per_sm = 0;
-  static int nsm = 0;
-  if (!per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (per_sm < 1) per_sm = 1;
-  }
+  int per_sm = 0, nsm = 0;
+  cudaError_t e = persistent_ctas((const void*)kern, 256, smem, &per_sm, &nsm);
+  if (e != cudaSuccess) return e;
   const long long need = (g.nnodes + 256 / TPP - 1) / (256 / TPP);
   const long long blocks = std::min<long long>((long long)per_sm * nsm, need);
   kern<<<(unsigned)std::max<long long>(blocks, 1), 256, smem, s>>>(g, coef, mask, rpad, xp2, om2, prow, cls);
@@ -1941,8 +1973,20 @@ cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coe
   // 2D: 4 lanes per patch (see apply_tpp); 3D: a warp per patch
   const unsigned blocks4 = (unsigned)((g.nnodes * 4 + 255) / 256);
   if (prec == FC_PREC_FP64) {
-    if (g.dim == 2) apply_fp64_kernel<2, 4><<<blocks4, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x, prow);
-    else apply_fp64_kernel<3, 32><<<blocks, 256, 0, s>>>(g, (const double*)coef, mask, rpad, omega, x, prow);
+    const int t = apply64_tpp(g.dim);
+    const unsigned bl = (unsigned)((g.nnodes * t + 255) / 256);
+    const double* c = (const double*)coef;
+    if (g.dim == 2) {
+      if (t == 8) apply_fp64_kernel<2, 8><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow);
+      else apply_fp64_kernel<2, 4><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow);
+    } else {
+      switch (t) {
+        case 4: apply_fp64_kernel<3, 4><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow); break;
+        case 16: apply_fp64_kernel<3, 16><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow); break;
+        case 32: apply_fp64_kernel<3, 32><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow); break;
+        default: apply_fp64_kernel<3, 8><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow); break;
+      }
+    }
   } else if (prec == FC_PREC_FP32) {
     if (g.dim == 2) apply_lowp_kernel<2, float, 4><<<blocks4, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x, prow);
     else apply_lowp_kernel<3, float, 32><<<blocks, 256, 0, s>>>(g, (const float*)coef, mask, rpad32, omega, x, prow);

@@ -21,7 +21,7 @@ PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "df64": 3}
 EXPORTS = ("fc_options_default", "fc_setup", "fc_rhs", "fc_residual", "fc_apply", "fc_smooth",
            "fc_smooth_noalloc", "fc_restrict", "fc_prolong_add", "fc_coarse_solve", "fc_vcycle", "fc_solve",
            "fc_gmg_solve", "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
-           "fc_profile_enable", "fc_profile_read", "fc_launch_count", "fc_sync", "fc_last_error",
+           "fc_profile_enable", "fc_profile_read", "fc_launch_count", "fc_probe_fma_rate", "fc_sync", "fc_last_error",
            "fc_destroy", "fc_batch_create", "fc_batch_offsets", "fc_batch_tile", "fc_batch_set_tile",
            "fc_batch_smooth", "fc_batch_vcycle", "fc_batch_solve", "fc_batch_solve_host", "fc_batch_info", "fc_batch_profile_enable",
            "fc_batch_profile_read", "fc_batch_sync",
@@ -85,7 +85,7 @@ class FcOptions(C.Structure):
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("quad_depth", C.c_int),
                 ("cache", C.c_int), ("prec", C.c_int), ("fgmres_restart", C.c_int),
                 ("bc_preset", C.c_int), ("ubar", C.c_double), ("force_kind", C.c_int),
-                ("force", C.c_double * 3), ("dedup", C.c_int)]
+                ("force", C.c_double * 3), ("dedup", C.c_int), ("tc", C.c_int), ("badcut_frac", C.c_double)]
 
 
 _lib = None
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
     lib.fc_profile_enable.argtypes = [vp, i]
     lib.fc_profile_read.argtypes = [vp, i, P(ll), P(d), P(d)]
     lib.fc_launch_count.argtypes = [P(ll)]
+    lib.fc_probe_fma_rate.argtypes = [i, P(d), P(d)]
     lib.fc_sync.argtypes = [vp]
     lib.fc_last_error.restype = C.c_char_p
     lib.fc_last_error.argtypes = [vp]
@@ -158,7 +159,11 @@ def _grid(prob) -> FcGrid:
     return g
 
 
-def _options(prob, cache: str, prec: str, nu=None, dedup: int = 1) -> FcOptions:
+TC = {"none": 0, "tf32": 1, "tf32x3": 2, "bf16": 3}
+
+
+def _options(prob, cache: str, prec: str, nu=None, dedup: int = 1, tc: str = "none",
+             badcut_frac: float | None = None) -> FcOptions:
     o = FcOptions()
     load().fc_options_default(C.byref(o))
     o.eta, o.nitsche_beta, o.omega = prob.eta, prob.beta, prob.omega
@@ -171,6 +176,9 @@ def _options(prob, cache: str, prec: str, nu=None, dedup: int = 1) -> FcOptions:
     for k in range(3):
         o.force[k] = float(prob.force[k])
     o.dedup = int(dedup)
+    o.tc = TC[tc]
+    if badcut_frac is not None:
+        o.badcut_frac = float(badcut_frac)
     return o
 
 
@@ -178,6 +186,16 @@ def launch_count() -> int:
     n = C.c_longlong()
     load().fc_launch_count(C.byref(n))
     return n.value
+
+
+def probe_fma_rate(precision: str = "fp64"):
+    """(FLOP/s, launch ms) of independent FMA chains on every SM of the
+    current GPU (fc_probe_fma_rate)."""
+    f, ms = C.c_double(), C.c_double()
+    st = load().fc_probe_fma_rate({"fp64": 0, "fp32": 1}[precision], C.byref(f), C.byref(ms))
+    if st != FC_OK:
+        raise FcError(st, "fc_probe_fma_rate failed")
+    return f.value, ms.value
 
 
 def footprint_estimate(prob, cache="inverse", prec="fp64") -> int:
@@ -189,7 +207,7 @@ class Solver:
     """A finite cell Stokes problem set up on the GPU (one fc_handle)."""
 
     def __init__(self, prob, cache: str = "inverse", prec: str = "fp64", stream=None, nu=None,
-                 dedup: int = 1):
+                 dedup: int = 1, tc: str = "none", badcut_frac: float | None = None):
         import torch
         if not torch.cuda.is_available():
             raise FcError(-1, "libfc needs a CUDA GPU")
@@ -215,7 +233,8 @@ class Solver:
         ls = FcLevelset(len(shapes), C.cast(arr, C.POINTER(FcShape)))
         self.h = C.c_void_p()
         st = self.lib.fc_setup(C.byref(self.h), C.byref(_grid(prob)), C.byref(ls), float(prob.alpha),
-                               int(prob.nlevels), C.byref(_options(prob, cache, prec, nu, dedup)),
+                               int(prob.nlevels),
+                               C.byref(_options(prob, cache, prec, nu, dedup, tc, badcut_frac)),
                                C.c_void_p(self.stream.cuda_stream))
         self._check(st)
 

@@ -58,9 +58,11 @@ def oracle_rows_in_slots(level: "O.Level", prob, level_n, node):
     return out
 
 
-def oracle_patch_update(level: "O.Level", prob, node, b, x, omega):
+def oracle_patch_update(level: "O.Level", prob, node, b, x, omega, with_scale=False):
     """omega * (L_i^{-1} R_i r)[owned] for one patch, r = b - L x computed from
-    the oracle's own rows of L at the patch DoFs (no assembled operator)."""
+    the oracle's own rows of L at the patch DoFs (no assembled operator).
+    with_scale: also return, per owned component, omega * sum_j |c_j r_j|
+    (the magnitude that rounding of the dot product scales with)."""
     rows, dofs, own = level.patch_inverse_rows(node)
     R, rhs = level.dof_rows(dofs)
     nd = prob.dim + 1
@@ -80,8 +82,9 @@ def oracle_patch_update(level: "O.Level", prob, node, b, x, omega):
             for cb in range(nd):
                 s += R[q, t, cb] * x[nbn * nd + cb]
         r[q] = b[d] - s
-    upd = {}
+    upd, scale = {}, {}
     for c in range(nd):
         if own[c] >= 0:
             upd[c] = omega * float(rows[c] @ r)
-    return upd
+            scale[c] = omega * float(np.abs(rows[c]) @ np.abs(r))
+    return (upd, scale) if with_scale else upd

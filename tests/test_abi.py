@@ -37,6 +37,10 @@ def test_options_default_without_gpu():
     o = fc.FcOptions()
     assert lib.fc_options_default(ctypes.byref(o)) == 0
     assert o.omega == 0.8 and o.eta == 1e-3 and o.fgmres_restart == 30
+    # every default the header states
+    assert (o.nu_pre, o.nu_post, o.quad_depth, o.cache, o.prec) == (2, 2, 4, 0, 0)
+    assert (o.bc_preset, o.ubar, o.force_kind, tuple(o.force)) == (0, 0.3, 0, (0.0, 0.0, 0.0))
+    assert o.nitsche_beta == 100.0 and o.dedup == 1 and o.tc == 0 and o.badcut_frac == 1e-3
     assert lib.fc_setup(None, None, None, 1.0, 1, None, None) == fc.FC_ERR_INVALID
 
 

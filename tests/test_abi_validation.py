@@ -66,6 +66,10 @@ CASES = [
     ("force kind 4", lambda g, ls, sh, o: setattr(o, "force_kind", 4), {}, "invalid options"),
     ("beta -1", lambda g, ls, sh, o: setattr(o, "nitsche_beta", -1.0), {}, "invalid options"),
     ("dedup 2", lambda g, ls, sh, o: setattr(o, "dedup", 2), {}, "invalid options"),
+    ("tc 4", lambda g, ls, sh, o: setattr(o, "tc", 4), {}, "invalid options"),
+    ("tc -1", lambda g, ls, sh, o: setattr(o, "tc", -1), {}, "invalid options"),
+    ("badcut_frac -1", lambda g, ls, sh, o: setattr(o, "badcut_frac", -1.0), {}, "invalid options"),
+    ("badcut_frac 1", lambda g, ls, sh, o: setattr(o, "badcut_frac", 1.0), {}, "invalid options"),
     ("cache 3", lambda g, ls, sh, o: setattr(o, "cache", 3), {}, "invalid cache policy or precision"),
     ("prec 9", lambda g, ls, sh, o: setattr(o, "prec", 9), {}, "invalid cache policy or precision"),
     ("fp32 rows with cache_matrix",

@@ -114,18 +114,24 @@ def test_sweep_parity(fc, name, cache):
     assert rel(x_gpu3, x_or3) <= SWEEP_TOL
 
 
-@pytest.mark.parametrize("name", ["ch2d", "por3d"])
-def test_sweep_parity_coarser_level(fc, name):
-    p = PROBS[name]
-    s = fc.Solver(p)
+COARSER = {"ch2d": PROBS["ch2d"], "por3d16": inputs.porous_3d(0, n=16, nspheres=8, nlevels=3)}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df64"])
+@pytest.mark.parametrize("name", list(COARSER))
+def test_sweep_parity_coarser_level(fc, name, prec):
+    """A sweep on the level below the finest (a smoothed level that the
+    V-cycle reaches through the restriction)."""
+    p = COARSER[name]
+    s = fc.Solver(p, prec=prec)
     lv = p.nlevels - 1
-    if lv < 2:
-        pytest.skip("no smoothed coarse level")
+    assert lv >= 2
     L = O.Level.from_problem(p, lv)
     L.assemble()
     x0 = inputs.random_vector(p, 41, level=lv)
     b = inputs.random_vector(p, 42, level=lv)
-    assert rel(s.smooth(x0, b, level=lv).cpu().numpy(), L.sweep(b, x0)) <= SWEEP_TOL
+    got = s.smooth(x0, b, level=lv).cpu().numpy()
+    assert rel(got - x0, L.sweep(b, x0) - x0) <= SWEEP_TOL
 
 
 @pytest.mark.parametrize("name", ["ch2d", "por3d"])
@@ -153,24 +159,31 @@ def test_coarse_solve(fc, name):
     assert rel(x_gpu, x_or) <= 1e-11
 
 
-@pytest.mark.parametrize("cache", ["inverse", "matrix", "none"])
+@pytest.mark.parametrize("cache,prec", [("inverse", "fp64"), ("inverse", "df64"), ("matrix", "fp64"),
+                                        ("none", "fp64")])
 @pytest.mark.parametrize("name", ["ch2d", "por3d", "ell2d"])
-def test_vcycle_parity(fc, name, cache):
+def test_vcycle_parity(fc, name, cache, prec):
+    """One V-cycle against the oracle's: FP64 rows with every cache policy,
+    and the float-pair rows the benchmark times (pair smoothing phases,
+    FP64 transfers and coarse solve)."""
     p = PROBS[name]
-    s = fc.Solver(p, cache=cache)
+    s = fc.Solver(p, cache=cache, prec=prec)
     mg = O.MG(p)
     b = inputs.random_vector(p, 71)
     x0 = inputs.random_vector(p, 72)
-    assert rel(s.vcycle(x0, b).cpu().numpy(), mg.vcycle(x0, b)) <= SWEEP_TOL
+    got = s.vcycle(x0, b).cpu().numpy()
+    want = mg.vcycle(x0, b)
+    assert rel(got, want) <= SWEEP_TOL
+    assert rel(got - x0, want - x0) <= SWEEP_TOL
 
 
-@pytest.mark.parametrize("cache", ["inverse", "matrix"])
+@pytest.mark.parametrize("cache,prec", [("inverse", "fp64"), ("inverse", "df64"), ("matrix", "fp64")])
 @pytest.mark.parametrize("name", ["ch2d", "por3d", "ch3d", "ell2d"])
-def test_fgmres_parity(fc, name, cache):
+def test_fgmres_parity(fc, name, cache, prec):
     """Same iteration count as the oracle, true residual <= 1e-8, and the same
     solution to the accuracy the tolerance allows."""
     p = PROBS[name]
-    s = fc.Solver(p, cache=cache)
+    s = fc.Solver(p, cache=cache, prec=prec)
     mg = O.MG(p)
     b = mg.rhs()
     x_or, its_or, rel_or, _ = mg.fgmres(b, rtol=1e-8)

@@ -35,11 +35,15 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("prec", ["fp64", "df64", "fp32"])
-def test_noalloc_matches_fc_smooth_twice(fc, prec):
+@pytest.mark.parametrize("cache,prec", [("inverse", "fp64"), ("inverse", "df64"), ("inverse", "fp32"),
+                                        ("inverse", "bf16"), ("matrix", "fp64"), ("none", "fp64")])
+def test_noalloc_matches_fc_smooth_twice(fc, cache, prec):
+    """Every cache policy and row precision: the cached rows (FP64, float
+    pairs, float32, bfloat16), the cached block factors, and the on-the-fly
+    factorisation, each against fc_smooth on the same handle."""
     import torch
     p = inputs.porous_3d(1, n=16, nspheres=5, nlevels=3)
-    s = fc.Solver(p, prec=prec)
+    s = fc.Solver(p, prec=prec, cache=cache)
     lib = s.lib
     for level, seed in ((3, 11), (2, 12)):
         x0 = torch.as_tensor(inputs.random_vector(p, seed, level=level)).cuda()
