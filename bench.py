@@ -514,27 +514,206 @@ def run_sweeps(args):
 def run_serve(args):
     """Serving stream: Poisson arrivals (mean 50/s) of 3D porous solves on
     grids {16,32,48,64,96}^3 with 5-200 spheres, admitted by HBM footprint
-    into a budget; mixed precision (FP32 rows, shared class blocks, FP64
-    FGMRES to 1e-8) on several slots, against the plain FP64 GPU solver
-    (FP64 rows, one block per patch) serving the same stream on one slot."""
+    into a budget, FGMRES to 1e-8.  Four arms with the same slots, budget
+    and shared class blocks, so that batching and precision separate:
+    batched rounds (BatchServer: the sweeps of the requests in flight share
+    fc_batch launches) and per-slot streams (Server), each with float32
+    rows (the mixed-precision form) and with FP64 rows (the plain method)."""
     from paper_2403_11636_gb300 import build, inputs
-    from paper_2403_11636_gb300.serve import Request, Server, latency_stats
+    from paper_2403_11636_gb300.serve import BatchServer, Request, Server, latency_stats
     build.build()
     stream = inputs.serving_stream(0, count=args.requests, rate=args.rate)
     reqs = [Request(k, p, t) for k, (t, p) in enumerate(stream)]
-    mixed = Server.gpu(budget_bytes=args.budget_gb * 1e9, slots=args.slots, prec="fp32", dedup=1).run(reqs)
-    plain = Server.gpu(budget_bytes=args.budget_gb * 1e9, slots=1, prec="fp64", dedup=0).run(reqs)
-    sm, sp = latency_stats(mixed), latency_stats(plain)
-    emit({"mode": "serve", "metric": "GMG solves/s", "value": sm["solves_per_s"], "unit": "solves/s",
+    budget = args.budget_gb * 1e9
+    arms = {}
+    clocks = Clocks(0)
+    clocks.start()
+    for name, make in (
+            ("batched_fp32", lambda: BatchServer.gpu(budget_bytes=budget, slots=args.slots, prec="fp32", dedup=1,
+                                                     tc=args.tc)),
+            ("batched_fp64", lambda: BatchServer.gpu(budget_bytes=budget, slots=args.slots, prec="fp64", dedup=1)),
+            ("streams_fp32", lambda: Server.gpu(budget_bytes=budget, slots=args.slots, prec="fp32", dedup=1)),
+            ("streams_fp64", lambda: Server.gpu(budget_bytes=budget, slots=args.slots, prec="fp64", dedup=1))):
+        try:
+            out = make().run(reqs)
+            st = latency_stats(out)
+            st["n"] = st.pop("requests")
+            st["iterations_mean"] = statistics.mean(r.iterations for r in out)
+            st["max_relres"] = max(r.relres for r in out)
+            st["setup_s_mean"] = statistics.mean(r.setup_s for r in out)
+            st["solve_s_mean"] = statistics.mean(r.solve_s for r in out)
+            if hasattr(out[0], "round_size"):
+                st["rounds"] = len({r.round_id for r in out})
+                st["round_size_mean"] = statistics.mean(r.round_size for r in out)
+            arms[name] = st
+        except Exception as e:
+            arms[name] = {"error": str(e)[:200]}
+    cl = clocks.stop()
+
+    def ratio(a, b):
+        try:
+            return arms[a]["solves_per_s"] / arms[b]["solves_per_s"]
+        except Exception:
+            return None
+
+    head = arms.get("batched_fp32", {})
+    emit({"mode": "serve", "metric": "GMG solves/s", "value": head.get("solves_per_s"), "unit": "solves/s",
           "higher_is_better": True, "data": "synthetic",
           "config": {"workload": f"{args.requests} requests, Poisson arrivals {args.rate}/s, porous3d "
                                  "n in {16,32,48,64,96}, 5-200 spheres, FGMRES rtol 1e-8",
-                     "budget_gb": args.budget_gb, "slots": args.slots},
-          "mixed": {**sm, "iterations_mean": statistics.mean(r.iterations for r in mixed),
-                    "max_relres": max(r.relres for r in mixed)},
-          "plain_fp64_gpu": {**sp, "iterations_mean": statistics.mean(r.iterations for r in plain),
-                             "max_relres": max(r.relres for r in plain)},
-          "speedup_solves_per_s": sm["solves_per_s"] / sp["solves_per_s"]})
+                     "budget_gb": args.budget_gb, "slots": args.slots, "shared_class_blocks": True,
+                     "tc": args.tc, "latency": "seconds from arrival to result; p99 of fewer than 100 "
+                                               "requests is their maximum"},
+          "arms": arms,
+          "speedup_mixed_vs_plain_fp64_batched": ratio("batched_fp32", "batched_fp64"),
+          "speedup_mixed_vs_plain_fp64_streams": ratio("streams_fp32", "streams_fp64"),
+          "speedup_batched_vs_streams_fp32": ratio("batched_fp32", "streams_fp32"),
+          "speedup_batched_vs_streams_fp64": ratio("batched_fp64", "streams_fp64"),
+          "clocks": cl})
+    return 0
+
+
+def run_mixed(args):
+    """Mixed precision on the 128^3 porous medium with 300 spheres (the
+    radius range scaled to a 30 % solid fraction), 5 levels, V(2,2): cached
+    patch rows in float32 / bfloat16 applied on CUDA cores or, for the
+    shared class blocks, on the tensor cores (TF32, two-term TF32, BF16),
+    inside the FP64 FGMRES to 1e-8; the FP64 rows (the plain method) and the
+    float-pair rows beside them.  Per variant: setup, the timed solves,
+    iterations, the error of velocity and pressure against the FP64 GPU
+    solution (whose oracle parity the tests establish), and the
+    finest-level patch apply timed alone (CUDA events)."""
+    import torch
+    from paper_2403_11636_gb300 import build, fc, inputs
+    build.build()
+    prob = inputs.porous_3d(0, n=args.mixed_n, nspheres=300, nlevels=args.mixed_levels)
+    stream = torch.cuda.Stream()
+    variants = [("fp64", "none", 1), ("df64", "none", 1), ("fp32", "none", 1), ("fp32", "tf32x3", 1),
+                ("fp32", "tf32", 1), ("fp32", "bf16", 1), ("bf16", "none", 1), ("bf16", "bf16", 1)]
+    res, x64 = {}, None
+    nd = prob.dim + 1
+    clocks = Clocks(0)
+    clocks.start()
+    for prec, tc, dd in variants:
+        key = f"{prec}/{tc}"
+        try:
+            with torch.cuda.stream(stream):
+                t0 = time.perf_counter()
+                s = fc.Solver(prob, prec=prec, tc=tc, dedup=dd, stream=stream)
+                torch.cuda.synchronize()
+                setup_ms = 1e3 * (time.perf_counter() - t0)
+                b = s.rhs()
+                for _ in range(args.warmup):
+                    s.solve(b, rtol=prob.rtol, maxit=300)
+                step_ms, total_ms, its_l, rr_l = timed_solves(s, b, prob, args.steps, stream, torch)
+                x, _, _ = s.solve(b, rtol=prob.rtol, maxit=300)
+                xc = x.cpu()
+                entry = {"setup_ms": setup_ms, "ms_per_solve": total_ms / args.steps,
+                         "solves_per_s": args.steps / (total_ms * 1e-3), "iterations": its_l[0],
+                         "relres": max(rr_l),
+                         "updates_per_s": sum(updates_per_solve(prob, i) for i in its_l) / (total_ms * 1e-3),
+                         "cache_bytes": s.info()["bytes"][1], "badcut_patches": s.info()["bytes"][7],
+                         "refinement_fallback_patches": s.info()["bytes"][5]}
+                if x64 is None:
+                    x64 = xc
+                else:
+                    for name, comp in (("u", list(range(prob.dim))), ("p", [prob.dim])):
+                        idx = torch.cat([torch.arange(c, xc.numel(), nd) for c in comp])
+                        entry[f"rel_err_{name}_vs_fp64_gpu"] = ((xc[idx] - x64[idx]).norm() / x64[idx].norm()).item()
+                # the finest-level patch apply alone
+                if prec in ("fp32", "bf16"):
+                    B = fc.Batch([s])
+                    X = torch.zeros_like(b)
+                    B.smooth_(X, b, nsweeps=2)
+                    B.profile(True)
+                    B.smooth_(X, b, nsweeps=10)
+                    na, ma, ba = B.profile_read(0)
+                    B.profile(False)
+                    B.close()
+                else:
+                    X = torch.zeros_like(b)
+                    s.smooth_(X, b, nsweeps=2)
+                    s.profile(True)
+                    s.smooth_(X, b, nsweeps=10)
+                    na, ma, ba = s.profile_read(4)
+                    s.profile(False)
+                entry["finest_apply_ms"] = ma / max(na, 1)
+                entry["finest_apply_gbs"] = ba / (ma / max(na, 1) * 1e-3) / 1e9 if ma > 0 else None
+                s.close()
+                del s
+            torch.cuda.synchronize()
+            res[key] = entry
+        except Exception as e:
+            res[key] = {"error": str(e)[:200]}
+    cl = clocks.stop()
+    hbm, peak_kind = peaks()
+    for e in res.values():
+        if e.get("finest_apply_gbs"):
+            e["finest_apply_hbm_frac"] = e["finest_apply_gbs"] / hbm
+    emit({"mode": "mixed", "metric": "GMG solves/s", "unit": "solves/s", "higher_is_better": True,
+          "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+          "config": {"workload": f"porous3d {args.mixed_n}^3, 300 spheres r~0.720 U[0.04,0.12] (30% solid), "
+                                 f"alpha 1e-8, octree depth 3, {args.mixed_levels} levels, V(2,2), FGMRES(30) "
+                                 "rtol 1e-8 in FP64, shared class blocks (dedup 1)",
+                     "ndof": prob.ndof(), "hbm_peak_gbs": hbm, "hbm_peak_source": peak_kind},
+          "variants": res, "clocks": cl})
+    return 0
+
+
+# Table tab:grid (Sec. 4): DoFs and GMG iteration counts of the paper's
+# adaptive channel grids Omega^1..Omega^7 (no count is printed for Omega^1)
+PAPER_TABLE_GRID = [("Omega^1", 790275, None), ("Omega^2", 1583127, 14), ("Omega^3", 4477533, 14),
+                    ("Omega^4", 15004455, 7), ("Omega^5", 53016765, 5), ("Omega^6", 188665497, 5),
+                    ("Omega^7", 665367261, 5)]
+
+
+def run_replay(args):
+    """The paper's experiment setting (Sec. 4): standalone GMG, V(6,6)
+    cycles with damping 0.8, stop at a 1e9 residual reduction, alpha 1e-10,
+    eta 1e-3, on the channel stand-in (2.2 x 0.41 box, cylinder of diameter
+    0.1 near the inflow) at the size of the paper's coarse grid Omega^1
+    (1024 x 256 cells, 790,275 DoFs) and uniform refinements of it, FP64
+    rows.  Cycle counts are printed beside Table tab:grid's counts of the
+    paper's adaptive grids (context only: uniform grids and a seeded
+    cylinder position, not the benchmark's)."""
+    import torch
+    from paper_2403_11636_gb300 import build, fc, inputs
+    build.build()
+    rows = []
+    for k in range(args.replay_sizes):
+        nx, ny = 1024 << k, 256 << k
+        nlev = 7 + k                     # coarsest grid 16 x 4 cells
+        p = inputs.channel_replay_2d(0, nx=nx, ny=ny, nlevels=nlev)
+        try:
+            t0 = time.perf_counter()
+            s = fc.Solver(p, prec="fp64", dedup=1)
+            torch.cuda.synchronize()
+            setup_ms = 1e3 * (time.perf_counter() - t0)
+            b = s.rhs()
+            s.gmg_solve(b, reduction=1e-9, maxit=200)      # warm-up (graphs, caches)
+            stream = torch.cuda.current_stream()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, its, red = s.gmg_solve(b, reduction=1e-9, maxit=200)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rows.append({"grid": f"{nx}x{ny}", "levels": nlev, "dofs": p.ndof(), "cycles": its, "reduction": red,
+                         "solve_ms": ms, "ms_per_cycle": ms / max(its, 1), "setup_ms": setup_ms,
+                         "sweep_updates_per_s": updates_per_solve(p, its) / (ms * 1e-3)})
+            s.close()
+        except Exception as e:
+            rows.append({"grid": f"{nx}x{ny}", "error": str(e)[:200]})
+        torch.cuda.synchronize()
+    emit({"mode": "replay", "metric": "GMG cycles to a 1e9 reduction", "unit": "cycles", "dtype": "f64",
+          "data": "synthetic",
+          "config": {"workload": "channel stand-in 2.2 x 0.41, cylinder diameter 0.1 at a seeded position near the "
+                                 "inflow, parabolic inflow ubar 0.3, alpha 1e-10, eta 1e-3, quadtree depth 4, "
+                                 "standalone V(6,6), damping 0.8, coarsest grid 16 x 4, FP64 rows",
+                     "paper_table_grid": [{"grid": g, "dofs": d, "gmg_iterations": it} for g, d, it in PAPER_TABLE_GRID],
+                     "note": "the paper's counts are for its adaptive grids and benchmark geometry: context, "
+                             "not a parity target"},
+          "sizes": rows})
     return 0
 
 
@@ -684,8 +863,12 @@ def run_batch_sweeps(args):
     import torch
     from paper_2403_11636_gb300 import build, fc, inputs
     build.build()
-    probs = [inputs.batch_2d(s) for s in range(args.batch)]
-    solvers = [fc.Solver(p, prec=args.batch_prec, dedup=args.dedup) for p in probs]
+    if args.batch_workload == "porous3d":
+        # one 3D porous problem of n^3 cells through the batched kernels
+        probs = [inputs.porous_3d(0, n=args.n, nlevels=max(2, int(math.log2(args.n // 4)) + 1))]
+    else:
+        probs = [inputs.batch_2d(s) for s in range(args.batch)]
+    solvers = [fc.Solver(p, prec=args.batch_prec, dedup=args.dedup, tc=args.tc) for p in probs]
     B = fc.Batch(solvers)
     if args.tile:
         B.set_tile(*[int(v) for v in args.tile.split(",")])
@@ -698,8 +881,9 @@ def run_batch_sweeps(args):
     nr, mr, _ = B.profile_read(1)
     hbm, _ = peaks()
     info = B.info()
-    emit({"mode": "batch-sweep", "problems": len(probs), "patches_finest": info["npatch_finest"],
-          "prec": args.batch_prec, "dedup": args.dedup, "tile": B.tile(),
+    emit({"mode": "batch-sweep", "workload": args.batch_workload,
+          "problems": len(probs), "patches_finest": info["npatch_finest"],
+          "prec": args.batch_prec, "dedup": args.dedup, "tc": args.tc, "tile": B.tile(),
           "apply_ms": ma / max(na, 1), "apply_bytes": ba,
           "apply_gbs": ba / (ma / na * 1e-3) / 1e9 if na else None,
           "residual_ms": mr / max(nr, 1),
@@ -784,7 +968,15 @@ def main():
                     help="grid of the oracle per-sweep timing (16: the solve sample's finest level)")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="profiled solves after the timed ones (per-kernel CUDA events)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep", "mixed", "replay"])
+    ap.add_argument("--mixed-n", type=int, default=128, help="grid of --mode mixed")
+    ap.add_argument("--replay-sizes", type=int, default=4,
+                    help="--mode replay: 1024x256 and this many - 1 uniform refinements")
+    ap.add_argument("--batch-workload", default="batch2d", choices=["batch2d", "porous3d"],
+                    help="problems of --mode batch-sweep: the 2D batch, or one porous3d --n problem")
+    ap.add_argument("--tc", default="none", choices=["none", "tf32", "tf32x3", "bf16"],
+                    help="tensor-core apply of the class blocks (--mode batch-sweep)")
+    ap.add_argument("--mixed-levels", type=int, default=5, help="levels of --mode mixed")
     ap.add_argument("--tile", default="", help="lanes,threads,ctas_per_sm of --mode batch-sweep")
     ap.add_argument("--batch", type=int, default=256, help="problems of --mode batch")
     ap.add_argument("--batch-prec", default="fp32", choices=["fp64", "fp32", "bf16"])
@@ -810,6 +1002,10 @@ def main():
         return run_batch(args)
     if args.mode == "batch-sweep":
         return run_batch_sweeps(args)
+    if args.mode == "mixed":
+        return run_mixed(args)
+    if args.mode == "replay":
+        return run_replay(args)
     return run_ours(args, rank, world, local_rank)
 
 

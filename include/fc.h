@@ -309,6 +309,16 @@ typedef struct fc_batch_s* fc_batch;
  * fc_batch_destroy. */
 fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream);
 
+/* As fc_batch_create, with the patch-apply tile given instead of timed:
+ * lanes per patch tpp in {1,2,4,8,16,32}, threads in {128,256,512} with
+ * threads / tpp <= 256, CTAs per SM in 1..64.  A problem's result is then
+ * bit-identical in every batch built with the same tile, whatever the other
+ * members (serving loops build a batch per round of in-flight requests).
+ * Errors: those of fc_batch_create; FC_ERR_INVALID for a tile outside
+ * these sets (*out is then NULL). */
+fc_status fc_batch_create_tiled(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream, int tpp,
+                                int threads, int ctas_per_sm);
+
 /* offsets[0..nprob] (host) of the packed finest-level vectors. */
 fc_status fc_batch_offsets(fc_batch b, long long* offsets);
 

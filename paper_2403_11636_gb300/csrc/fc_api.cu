@@ -652,6 +652,11 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     CK(dalloc(h, &L.wfix, (size_t)G.ndof, 0));
     CK(launch_assemble(G, eA, eB, L.st, h->stream));
     CK(launch_masks(G, L.mask, L.wfix, h->stream));
+    if (dim == 3 && li > 0) {
+      CK(dalloc(h, &L.dead, (size_t)G.nn[1] + G.nn[2], 0));
+      CK(launch_dead_layers(G, L.mask, L.dead, h->stream));
+      L.g.dead_layer = L.dead;
+    }
     // ---- vectors
     long long padn = pad_nodes(G);
     CK(dalloc(h, &L.x, (size_t)G.ndof, 2));
@@ -1166,7 +1171,7 @@ fc_status fc_destroy(fc_handle h) {
   handle_batch_free(h);
   for (int l = 0; l < kMaxLevels; ++l) {
     Level& L = h->lev[l];
-    dfree(h, L.st); dfree(h, L.mask); dfree(h, L.wfix); dfree(h, L.coef); dfree(h, L.fac); dfree(h, L.fpiv);
+    dfree(h, L.st); dfree(h, L.mask); dfree(h, L.dead); dfree(h, L.wfix); dfree(h, L.coef); dfree(h, L.fac); dfree(h, L.fpiv);
     dfree(h, L.x); dfree(h, L.b); dfree(h, L.r); dfree(h, L.rpad); dfree(h, L.rpad32);
     dfree(h, L.st2); dfree(h, L.xp2); dfree(h, L.bp2); dfree(h, L.prow);
     dfree(h, L.st32); dfree(h, L.d32); dfree(h, L.b32);

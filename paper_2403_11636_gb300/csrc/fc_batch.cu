@@ -41,7 +41,7 @@ namespace cg = cooperative_groups;
 namespace fc {
 namespace {
 
-constexpr int kChunk = 256;   // nodes per chunk
+constexpr int kChunk = kChunkNodes;   // nodes per chunk
 constexpr int kCL = 8;        // CTAs per cluster in the Krylov kernels
 constexpr int kKThreads = 256;
 
@@ -1810,6 +1810,19 @@ extern "C" {
 
 fc_status fc_batch_create(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream) {
   return create_batch(out, handles, nprob, cuda_stream, nullptr);
+}
+
+fc_status fc_batch_create_tiled(fc_batch* out, const fc_handle* handles, int nprob, void* cuda_stream, int tpp,
+                                int threads, int ctas_per_sm) {
+  if (!out) return FC_ERR_INVALID;
+  const bool ok_tpp = tpp == 1 || tpp == 2 || tpp == 4 || tpp == 8 || tpp == 16 || tpp == 32;
+  const bool ok_thr = threads == 128 || threads == 256 || threads == 512;
+  if (!ok_tpp || !ok_thr || threads / tpp > fc::kChunkNodes || ctas_per_sm < 1 || ctas_per_sm > 64) {
+    *out = nullptr;
+    return FC_ERR_INVALID;
+  }
+  const Tile t{tpp, threads, ctas_per_sm};
+  return create_batch(out, handles, nprob, cuda_stream, &t);
 }
 
 }  // extern "C"

@@ -12,6 +12,7 @@
 namespace fc {
 
 constexpr int kMaxLevels = 12;
+constexpr int kChunkNodes = 256;  // nodes per chunk of the batched kernels (fc_batch.cu)
 constexpr int kMaxShapesPerCell = 64;
 
 // Device-side error word bits (set by kernels, read back at sync points).
@@ -39,6 +40,11 @@ struct LevelGeom {
   double alpha, eta, lambda, ubar;
   int qdepth, preset, force_kind;
   double force[3];
+  // 3D levels with a patch cache: one flag per y layer (nn[1] entries) then
+  // per z layer (nn[2]), set when every node of the layer has all its
+  // velocity components constrained (a Dirichlet wall); the patch applies
+  // skip such layers and out-of-grid ones.  Null: no flags.
+  const unsigned char* dead_layer;
 };
 
 // Compressed operator stencil: for node a and neighbour offset nb (3^d,
@@ -70,6 +76,7 @@ struct Level {
   LevelGeom g;
   double* st = nullptr;         // stencil, SPN * 3^d * nnodes
   unsigned char* mask = nullptr;  // per node: bit c = velocity comp c constrained
+  unsigned char* dead = nullptr;  // layer flags (LevelGeom::dead_layer), 3D levels above the coarsest
   double* wfix = nullptr;       // Dirichlet values per DoF (0 where free)
   // patch cache
   void* coef = nullptr;         // cache_inverse rows
@@ -195,6 +202,9 @@ cudaError_t launch_patch_classes(const LevelGeom& g, const unsigned char* cclass
 cudaError_t launch_assemble(const LevelGeom& g, const double* eA, const double* eB, double* st,
                             cudaStream_t s);
 cudaError_t launch_masks(const LevelGeom& g, unsigned char* mask, double* wfix, cudaStream_t s);
+// y / z layer flags of g.dead_layer from the node masks (3D); out holds
+// nn[1] + nn[2] bytes
+cudaError_t launch_dead_layers(const LevelGeom& g, const unsigned char* mask, unsigned char* out, cudaStream_t s);
 cudaError_t launch_rhs(const LevelGeom& g, const double* eF, const double* st,
                        const unsigned char* mask, const double* wfix, double* b, cudaStream_t s);
 // operator application (fc_mg.cu)

@@ -561,8 +561,37 @@ __global__ void __launch_bounds__(256)
   const bool shared_rows = pr < 0;  // class rows: read through the cache
   const double* cf = coef + (size_t)(shared_rows ? -pr - 1 : pr) * NSLOT * ND;
   double y[4] = {0.0, 0.0, 0.0, 0.0};  // 2D: y[3] stays zero
+  // Live velocity slots.  Slots of out-of-grid nodes and of wall layers
+  // (every velocity component constrained) have zero coefficients; in 3D the
+  // 5 x 5 x 5 velocity box is clipped in y and z to its live layers
+  // [y0, y1] x [z0, z1], so a patch walks nv = 15 (y1 - y0 + 1)(z1 - z0 + 1)
+  // velocity slots (z-planes of 75 slots, each holding one contiguous run of
+  // 15 per live y row) and then its 3^d pressure slots.  Patches of a warp
+  // are consecutive nodes of an x row and mostly share the clipping.
+  int nv = P::NU * DIM, seg = 75, vbase = 0;
+  if (DIM == 3 && g.dead_layer) {
+    const unsigned char* dy = g.dead_layer;
+    const unsigned char* dz = g.dead_layer + g.nn[1];
+    int y0 = -2, y1 = 2, z0 = -2, z1 = 2;
+    while (y0 <= 2 && (ia[1] + y0 < 0 || ia[1] + y0 > g.n[1] || dy[ia[1] + y0])) ++y0;
+    while (y1 >= y0 && (ia[1] + y1 < 0 || ia[1] + y1 > g.n[1] || dy[ia[1] + y1])) --y1;
+    while (z0 <= 2 && (ia[2] + z0 < 0 || ia[2] + z0 > g.n[2] || dz[ia[2] + z0])) ++z0;
+    while (z1 >= z0 && (ia[2] + z1 < 0 || ia[2] + z1 > g.n[2] || dz[ia[2] + z1])) --z1;
+    seg = 15 * (y1 - y0 + 1);
+    nv = y1 >= y0 && z1 >= z0 ? seg * (z1 - z0 + 1) : 0;
+    vbase = (z0 + 2) * 75 + (y0 + 2) * 15;
+  }
+  const int tot = nv + P::NP;
+  int zi = 0, off = lane;  // loop index t = zi * seg + off while t < nv
+  if (nv > 0)
+    while (off >= seg) { off -= seg; ++zi; }
 #pragma unroll 4
-  for (int j = lane; j < NSLOT; j += TPP) {
+  for (int t = lane; t < tot; t += TPP) {
+    const int j = t < nv ? vbase + zi * 75 + off : P::NU * DIM + (t - nv);
+    if (nv > 0) {
+      off += TPP;
+      while (off >= seg) { off -= seg; ++zi; }
+    }
     double rv = rp[soff[j]];
     if (ND == 4) {
       const double2* c2 = reinterpret_cast<const double2*>(cf + (size_t)j * 4);
@@ -1062,15 +1091,15 @@ int apply_tpp(int dim) {
 // each lane then accumulates more slots and the group's reduction adds
 // little (8 lanes: 4 FP64 adds per lane, 2 % of a 3D patch's 1,608 FMA;
 // 32 lanes: 6 per lane, 12 %).  4 lanes in 2D (59 slots).  FC_APPLY64_TPP
-// (4, 8, 16, 32) overrides the choice for tuning runs.
+// (4, 8, 16, 32) overrides the 3D choice for tuning runs.
 int apply64_tpp(int dim) {
   static const int env = [] {
     const char* e = getenv("FC_APPLY64_TPP");
     const int t = e ? atoi(e) : 0;
     return (t == 4 || t == 8 || t == 16 || t == 32) ? t : 0;
   }();
-  if (env) return dim == 2 ? (env >= 8 ? 8 : 4) : env;
-  return dim == 3 ? 8 : 4;
+  if (dim == 2) return 4;
+  return env ? env : 8;
 }
 
 template <int DIM, int TPP>
@@ -1977,8 +2006,7 @@ cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coe
     const unsigned bl = (unsigned)((g.nnodes * t + 255) / 256);
     const double* c = (const double*)coef;
     if (g.dim == 2) {
-      if (t == 8) apply_fp64_kernel<2, 8><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow);
-      else apply_fp64_kernel<2, 4><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow);
+      apply_fp64_kernel<2, 4><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow);
     } else {
       switch (t) {
         case 4: apply_fp64_kernel<3, 4><<<bl, 256, 0, s>>>(g, c, mask, rpad, omega, x, prow); break;

@@ -22,7 +22,7 @@ EXPORTS = ("fc_options_default", "fc_setup", "fc_rhs", "fc_residual", "fc_apply"
            "fc_smooth_noalloc", "fc_restrict", "fc_prolong_add", "fc_coarse_solve", "fc_vcycle", "fc_solve",
            "fc_gmg_solve", "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
            "fc_profile_enable", "fc_profile_read", "fc_launch_count", "fc_probe_fma_rate", "fc_sync", "fc_last_error",
-           "fc_destroy", "fc_batch_create", "fc_batch_offsets", "fc_batch_tile", "fc_batch_set_tile",
+           "fc_destroy", "fc_batch_create", "fc_batch_create_tiled", "fc_batch_offsets", "fc_batch_tile", "fc_batch_set_tile",
            "fc_batch_smooth", "fc_batch_vcycle", "fc_batch_solve", "fc_batch_solve_host", "fc_batch_info", "fc_batch_profile_enable",
            "fc_batch_profile_read", "fc_batch_sync",
            "fc_batch_last_error", "fc_batch_destroy")
@@ -131,6 +131,7 @@ def load(path: str = LIB_PATH):
     lib.fc_batch_offsets.argtypes = [vp, P(ll)]
     lib.fc_batch_tile.argtypes = [vp, P(i), P(i), P(i)]
     lib.fc_batch_set_tile.argtypes = [vp, i, i, i]
+    lib.fc_batch_create_tiled.argtypes = [P(vp), P(vp), i, vp, i, i, i]
     lib.fc_batch_smooth.argtypes = [vp, vp, vp, i]
     lib.fc_batch_vcycle.argtypes = [vp, vp, vp]
     lib.fc_batch_solve.argtypes = [vp, vp, vp, d, i, P(i), P(d)]
@@ -421,7 +422,10 @@ class Batch:
     (fc_batch_*).  Vectors are packed: every problem's finest-level vector
     back to back, problem p at ``offsets[p]:offsets[p+1]``."""
 
-    def __init__(self, solvers, stream=None):
+    def __init__(self, solvers, stream=None, tile=None):
+        """tile = (lanes per patch, threads, CTAs per SM) builds the batch with
+        that patch-apply tile (fc_batch_create_tiled) instead of timing the
+        candidates (fc_batch_create)."""
         import torch
         self.torch = torch
         self.lib = load()
@@ -430,7 +434,11 @@ class Batch:
         self.device = torch.cuda.current_device()
         hs = (C.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
         self.b = C.c_void_p()
-        st = self.lib.fc_batch_create(C.byref(self.b), hs, len(self.solvers), C.c_void_p(self.stream.cuda_stream))
+        if tile is None:
+            st = self.lib.fc_batch_create(C.byref(self.b), hs, len(self.solvers), C.c_void_p(self.stream.cuda_stream))
+        else:
+            st = self.lib.fc_batch_create_tiled(C.byref(self.b), hs, len(self.solvers),
+                                                C.c_void_p(self.stream.cuda_stream), *[int(v) for v in tile])
         self._check(st)
         off = (C.c_longlong * (len(self.solvers) + 1))()
         self._check(self.lib.fc_batch_offsets(self.b, off))

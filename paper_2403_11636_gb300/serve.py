@@ -1,16 +1,24 @@
-"""Continuous-batching server for finite cell Stokes solves on one GPU.
+"""Continuous-batching servers for finite cell Stokes solves on one GPU.
 
 Requests (a problem and its arrival time) are admitted first-come first-served
 as soon as a slot is free and the request's device footprint
-(``fc_footprint_estimate``) fits into what is left of the HBM budget.  Each
-slot is a host thread with its own CUDA stream: it sets the problem up
-(``fc_setup``: operator, patch caches, coarse solve stay resident while the
-request is in flight), solves it with FGMRES-GMG and releases its memory.
-Requests that arrive while others run are admitted as slots and memory free
-up, and their kernels overlap on the device (separate streams; the library's
-allocations are stream-ordered, so one request's setup or teardown does not
-stall the others).  Every solve is deterministic and uses only its own
-handle, so a result does not depend on what else is in flight.
+(``fc_footprint_estimate``) fits into what is left of the HBM budget.  An
+admitted request is set up on a host thread with its own CUDA stream
+(``fc_setup``: operator, patch caches and coarse solve stay resident while
+the request is in flight); the library's allocations are stream-ordered, so
+one request's setup or teardown does not stall the others.
+
+``BatchServer`` batches the smoother sweeps of the requests in flight: one
+driver thread takes every request whose setup has finished and solves them
+together as one ``fc_batch`` (each V-cycle phase one persistent launch over
+the patches of all of them, each Arnoldi step one CUDA graph, every problem
+with its own FGMRES and stopping test).  Requests whose setup finishes while
+a round runs join the next round, while setups keep overlapping the round on
+their own streams.  The batch is built with a fixed patch-apply tile, so a
+request's result is bit-identical alone and in any mix.
+
+``Server`` is the unbatched form: each slot sets up and solves its own
+request on its own stream, so requests only overlap as independent streams.
 
 The numerical work is all in libfc; this module only schedules.
 """
@@ -161,3 +169,181 @@ class Server:
         if state["errors"]:
             raise RuntimeError(f"{len(state['errors'])} requests failed: {state['errors'][:3]}")
         return sorted(state["results"], key=lambda r: r.rid)
+
+
+@dataclasses.dataclass
+class BatchResult(Result):
+    round_id: int = -1
+    round_size: int = 0
+
+
+class BatchServer:
+    """FIFO admission by footprint into ``budget_bytes`` with ``slots``
+    requests in flight (setting up, waiting for a round or solving), and one
+    driver that solves the set-up requests in rounds of at most
+    ``max_batch``.
+
+    ``setup_fn(problem, stream) -> handle``, ``round_fn([handles], stream) ->
+    [(iterations, relres, solution or None)]`` (one batched solve of the
+    round), ``release_fn(handle)`` and ``footprint_fn(problem) -> bytes``
+    make the scheduler testable without a GPU; ``BatchServer.gpu(...)`` wires
+    libfc in.  ``gather_s``: once a request is ready, how long the driver
+    may wait for setups still running to join the same round (0: start the
+    round at once)."""
+
+    def __init__(self, setup_fn: Callable, round_fn: Callable, release_fn: Callable, footprint_fn: Callable,
+                 budget_bytes: float, slots: int, max_batch: int = 64, make_stream: Callable = lambda: None,
+                 clock: Callable = time.perf_counter, gather_s: float = 0.0):
+        if slots < 1 or max_batch < 1:
+            raise ValueError("slots and max_batch must be >= 1")
+        self.setup_fn = setup_fn
+        self.round_fn = round_fn
+        self.release_fn = release_fn
+        self.footprint_fn = footprint_fn
+        self.budget = float(budget_bytes)
+        self.slots = slots
+        self.max_batch = max_batch
+        self.make_stream = make_stream
+        self.clock = clock
+        self.gather_s = gather_s
+
+    @classmethod
+    def gpu(cls, budget_bytes: float = 150e9, slots: int = 8, prec: str = "fp32", dedup: int = 1,
+            tc: str = "none", tile=(16, 256, 8), keep_solutions: bool = False, rtol: Optional[float] = None,
+            max_batch: int = 64, gather_s: float = 0.0):
+        import torch
+        from . import fc
+
+        def footprint(p):
+            return fc.footprint_estimate(p, cache="inverse", prec=prec)
+
+        def setup(p, stream):
+            with torch.cuda.stream(stream):
+                s = fc.Solver(p, prec=prec, stream=stream, dedup=dedup, tc=tc)
+                b = s.rhs()
+                stream.synchronize()
+            return (s, b, p)
+
+        def solve_round(items, stream):
+            with torch.cuda.stream(stream):
+                B = fc.Batch([s for s, _, _ in items], stream=stream, tile=tile)
+                try:
+                    bp = B.pack([b for _, b, _ in items])
+                    tol = rtol if rtol is not None else items[0][2].rtol
+                    x, its, rr = B.solve(bp, rtol=tol, maxit=400)
+                    sols = [v.cpu().numpy() for v in B.unpack(x)] if keep_solutions else [None] * len(items)
+                finally:
+                    B.close()
+            return [(int(i), float(r), sol) for i, r, sol in zip(its, rr, sols)]
+
+        def release(item):
+            item[0].close()
+
+        return cls(setup, solve_round, release, footprint, budget_bytes, slots, max_batch,
+                   make_stream=lambda: torch.cuda.Stream(), gather_s=gather_s)
+
+    def run(self, requests: List[Request]) -> List[BatchResult]:
+        """Serve ``requests`` (arrival times relative to the call) to completion."""
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        for r in pending:
+            if self.footprint_fn(r.problem) > self.budget:
+                raise ValueError(f"request {r.rid} needs more than the whole budget")
+        lock = threading.Condition()
+        st = {"used": 0.0, "free_slots": list(range(self.slots)), "ready": [], "results": [], "errors": [],
+              "setting_up": 0, "solving": 0, "done_admitting": False, "rounds": 0}
+        streams = [self.make_stream() for _ in range(self.slots)]
+        driver_stream = self.make_stream()
+        t0 = self.clock()
+        threads = []
+
+        def finish(slot, fp):
+            st["used"] -= fp
+            st["free_slots"].append(slot)
+
+        def setup_worker(slot, req, fp, admitted):
+            try:
+                t1 = self.clock()
+                h = self.setup_fn(req.problem, streams[slot])
+                ts = self.clock() - t1
+                with lock:
+                    st["ready"].append((req, h, slot, fp, admitted, ts))
+                    st["setting_up"] -= 1
+                    lock.notify_all()
+            except Exception as e:  # a failed setup is reported; its slot is freed
+                with lock:
+                    st["errors"].append((req.rid, repr(e)))
+                    st["setting_up"] -= 1
+                    finish(slot, fp)
+                    lock.notify_all()
+
+        def driver():
+            while True:
+                with lock:
+                    while not st["ready"] and not (st["done_admitting"] and st["setting_up"] == 0):
+                        lock.wait(timeout=0.05)
+                    if not st["ready"]:
+                        return
+                    deadline = self.clock() + self.gather_s
+                    while (st["setting_up"] > 0 and len(st["ready"]) < self.max_batch
+                           and self.clock() < deadline):
+                        lock.wait(timeout=min(0.01, max(0.0, deadline - self.clock())))
+                    batch = st["ready"][: self.max_batch]
+                    del st["ready"][: len(batch)]
+                    rid_round = st["rounds"]
+                    st["rounds"] += 1
+                t1 = self.clock()
+                try:
+                    outs = self.round_fn([h for _, h, _, _, _, _ in batch], driver_stream)
+                    err = None
+                except Exception as e:
+                    outs, err = None, repr(e)
+                t_end = self.clock()
+                for k, (req, h, slot, fp, admitted, ts) in enumerate(batch):
+                    try:
+                        self.release_fn(h)
+                    except Exception:
+                        pass
+                    with lock:
+                        if err is None:
+                            its, rr, sol = outs[k]
+                            st["results"].append(BatchResult(req.rid, req.arrival, admitted, t_end - t0, its, rr, ts,
+                                                             t_end - t1, fp, sol, rid_round, len(batch)))
+                        else:
+                            st["errors"].append((req.rid, err))
+                        finish(slot, fp)
+                        lock.notify_all()
+
+        drv = threading.Thread(target=driver, daemon=True)
+        drv.start()
+        queue: List = []
+        i = 0
+        with lock:
+            while True:
+                now = self.clock() - t0
+                while i < len(pending) and pending[i].arrival <= now:
+                    heapq.heappush(queue, (pending[i].arrival, pending[i].rid, pending[i]))
+                    i += 1
+                while queue and st["free_slots"]:
+                    req = queue[0][2]
+                    fp = self.footprint_fn(req.problem)
+                    if st["used"] + fp > self.budget:
+                        break
+                    heapq.heappop(queue)
+                    slot = st["free_slots"].pop()
+                    st["used"] += fp
+                    st["setting_up"] += 1
+                    th = threading.Thread(target=setup_worker, args=(slot, req, fp, now), daemon=True)
+                    threads.append(th)
+                    th.start()
+                if i >= len(pending) and not queue:
+                    break
+                wait = max(0.0, pending[i].arrival - (self.clock() - t0)) if i < len(pending) else None
+                lock.wait(timeout=wait if wait is not None else 0.05)
+            st["done_admitting"] = True
+            lock.notify_all()
+        for th in threads:
+            th.join()
+        drv.join()
+        if st["errors"]:
+            raise RuntimeError(f"{len(st['errors'])} requests failed: {st['errors'][:3]}")
+        return sorted(st["results"], key=lambda r: r.rid)

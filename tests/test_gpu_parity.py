@@ -341,7 +341,7 @@ def test_shared_class_blocks_change_nothing(fc, name, prec):
     assert s1.info()["bytes"][1] <= s0.info()["bytes"][1]
 
 
-@pytest.mark.parametrize("nx,ny,nlev", [(128, 32, 3), (256, 64, 4)])
+@pytest.mark.parametrize("nx,ny,nlev", [(128, 32, 3), (256, 64, 4), (512, 128, 6)])
 def test_standalone_gmg_replay(fc, nx, ny, nlev):
     """Standalone GMG in the paper's setting (Sec. 4: V(6,6), damping 0.8, a
     1e9 residual reduction, alpha = 1e-10) on the channel stand-in: the GPU

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2403_11636_gb300 import inputs
-from paper_2403_11636_gb300.serve import Request, Server, latency_stats
+from paper_2403_11636_gb300.serve import BatchServer, Request, Server, latency_stats
 
 
 class FakeProblem:
@@ -118,3 +118,114 @@ def test_results_same_alone_and_in_the_mix():
     for a, m in zip(alone, mixed):
         assert a.iterations == m.iterations and m.relres <= 1e-8
         np.testing.assert_array_equal(a.solution, m.solution)
+
+
+def make_batch_fakes(setup_dur=0.02, round_dur=0.05):
+    """Fakes of setup / round / release that record memory in flight, the
+    rounds and which requests each round held."""
+    lock = threading.Lock()
+    st = {"mem": 0, "max_mem": 0, "n": 0, "max_n": 0, "rounds": []}
+
+    def setup(p, stream):
+        with lock:
+            st["mem"] += p.fp
+            st["n"] += 1
+            st["max_mem"] = max(st["max_mem"], st["mem"])
+            st["max_n"] = max(st["max_n"], st["n"])
+        if getattr(p, "fail", False):
+            with lock:
+                st["mem"] -= p.fp
+                st["n"] -= 1
+            raise RuntimeError("setup failed")
+        time.sleep(p.dur if p.dur else setup_dur)
+        return p
+
+    def solve_round(handles, stream):
+        with lock:
+            st["rounds"].append([h.rid for h in handles])
+        time.sleep(round_dur)
+        return [(5, 1e-9, None) for _ in handles]
+
+    def release(h):
+        with lock:
+            st["mem"] -= h.fp
+            st["n"] -= 1
+
+    return setup, solve_round, release, st
+
+
+class FP:
+    def __init__(self, rid, fp, dur=0.0, fail=False):
+        self.rid, self.fp, self.dur, self.fail = rid, fp, dur, fail
+
+
+def test_batch_server_rounds_budget_and_slots():
+    setup, solve_round, release, st = make_batch_fakes()
+    reqs = [Request(k, FP(k, 30 + 10 * (k % 3)), arrival=0.003 * k) for k in range(16)]
+    res = BatchServer(setup, solve_round, release, lambda p: p.fp, budget_bytes=150, slots=4).run(reqs)
+    assert [r.rid for r in res] == list(range(16))
+    assert st["max_mem"] <= 150 and st["max_n"] <= 4
+    assert max(len(r) for r in st["rounds"]) >= 2            # sweeps of several requests batched
+    assert sorted(sum(st["rounds"], [])) == list(range(16))  # every request solved in exactly one round
+    assert all(r.round_size == len(st["rounds"][r.round_id]) for r in res)
+    assert all(r.arrival <= r.admitted + 1e-9 <= r.finished + 1e-9 for r in res)
+    assert st["mem"] == 0 and st["n"] == 0
+
+
+def test_batch_server_arrival_during_round_joins_a_later_round():
+    setup, solve_round, release, st = make_batch_fakes(setup_dur=0.01, round_dur=0.2)
+    reqs = [Request(0, FP(0, 10), 0.0), Request(1, FP(1, 10), 0.0), Request(2, FP(2, 10), 0.1)]
+    res = BatchServer(setup, solve_round, release, lambda p: p.fp, budget_bytes=100, slots=8).run(reqs)
+    r0 = {r.rid: r.round_id for r in res}
+    assert r0[2] > r0[0]
+    assert res[2].finished > res[0].finished
+
+
+def test_batch_server_fifo_admission_by_memory():
+    setup, solve_round, release, st = make_batch_fakes(setup_dur=0.01, round_dur=0.05)
+    reqs = [Request(0, FP(0, 90), 0.0), Request(1, FP(1, 90), 0.001), Request(2, FP(2, 5), 0.002)]
+    res = BatchServer(setup, solve_round, release, lambda p: p.fp, budget_bytes=100, slots=4).run(reqs)
+    # request 2 fits beside request 0 but arrives after request 1, which does not
+    assert res[2].admitted >= res[1].admitted
+    assert res[1].admitted >= res[0].finished - 1e-3
+
+
+def test_batch_server_failed_setup_reported_and_rest_served():
+    setup, solve_round, release, st = make_batch_fakes()
+    reqs = [Request(k, FP(k, 20, fail=(k == 3)), arrival=0.002 * k) for k in range(6)]
+    with pytest.raises(RuntimeError) as e:
+        BatchServer(setup, solve_round, release, lambda p: p.fp, budget_bytes=100, slots=2).run(reqs)
+    assert "1 requests failed" in str(e.value)
+    assert sorted(sum(st["rounds"], [])) == [0, 1, 2, 4, 5]
+    assert st["mem"] == 0 and st["n"] == 0
+
+
+@pytest.mark.gpu
+def test_batched_results_same_alone_and_in_the_mix():
+    """Rounds of in-flight requests share one fc_batch; with the fixed tile a
+    request's solution is bit-identical when it is served alone (a round of
+    one) and in the mix, and every request reaches the tolerance."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2403_11636_gb300 import build
+    build.build()
+    probs = [inputs.porous_3d(k, n=16, nspheres=5 + 3 * k, nlevels=3) for k in range(4)]
+    probs.append(inputs.porous_3d(9, n=32, nspheres=20, nlevels=4))
+    for prec in ("fp32", "fp64"):
+        alone = BatchServer.gpu(budget_bytes=150e9, slots=1, prec=prec, keep_solutions=True).run(
+            [Request(k, p, 0.0) for k, p in enumerate(probs)])
+        mixed = BatchServer.gpu(budget_bytes=150e9, slots=5, prec=prec, keep_solutions=True, gather_s=5.0).run(
+            [Request(k, p, 0.0) for k, p in enumerate(probs)])
+        assert all(a.round_size == 1 for a in alone)
+        assert max(m.round_size for m in mixed) >= 2
+        for a, m in zip(alone, mixed):
+            assert a.iterations == m.iterations and m.relres <= 1e-8
+            np.testing.assert_array_equal(a.solution, m.solution)
+
+
+def test_batch_server_gather_window_fills_a_round():
+    setup, solve_round, release, st = make_batch_fakes(setup_dur=0.0, round_dur=0.02)
+    reqs = [Request(k, FP(k, 10, dur=0.01 * (k + 1)), 0.0) for k in range(4)]
+    BatchServer(setup, solve_round, release, lambda p: p.fp, budget_bytes=100, slots=4, gather_s=1.0).run(reqs)
+    assert st["rounds"] == [[0, 1, 2, 3]]
