@@ -841,7 +841,7 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     double* dsc = nullptr;
     int* piv = nullptr;
     CK(dalloc(h, &work, (size_t)n * n, -1));
-    CK(dalloc(h, &dsc, (size_t)n, -1));
+    CK(dalloc(h, &dsc, (size_t)2 * n, -1));  // scaling and the elimination's column factors
     CK(dalloc(h, &piv, (size_t)n, -1));
     CK(dalloc(h, &h->coarse_inv, (size_t)n * n, 3));
     CK(launch_coarse_factor(C.g, C.st, C.mask, work, h->coarse_inv, piv, dsc, h->d_err, h->stream));

@@ -4,6 +4,8 @@
 // iteration (Sec. 4 remark on Krylov methods).
 #include <math.h>
 
+#include <algorithm>
+
 #include "fc_internal.cuh"
 
 namespace fc {
@@ -434,96 +436,116 @@ __global__ void coarse_dense_kernel(LevelGeom g, const double* __restrict__ st,
   }
 }
 
+// Explicit inverse of the equilibrated coarsest operator by Gauss-Jordan
+// elimination with partial pivoting (max |a|, lowest row on ties) on the
+// pair [D A D | I], D = |diag A|^{-1/2}: after the n steps the right half is
+// (D A D)^{-1}, and A^{-1} = D (D A D)^{-1} D.  Each step is one pivot
+// launch (one CTA: pivot search, row swap, pivot row scaled, the column's
+// factors saved) and one elimination launch over the whole GPU, so the
+// O(n^3) work spreads over every SM.
+__global__ void gj_scale_kernel(int n, const double* __restrict__ A, double* __restrict__ dsc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double v = fabs(A[(long long)j * n + j]);
+  dsc[j] = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+}
+
+// A <- D A D, R <- I (a block per row)
+__global__ void gj_init_kernel(int n, double* __restrict__ A, double* __restrict__ R, const double* __restrict__ dsc) {
+  for (int rr = blockIdx.x; rr < n; rr += gridDim.x) {
+    const double dr = dsc[rr];
+    double* ar = A + (long long)rr * n;
+    double* rw = R + (long long)rr * n;
+    for (int cc = threadIdx.x; cc < n; cc += blockDim.x) {
+      ar[cc] = dr * ar[cc] * dsc[cc];
+      rw[cc] = rr == cc ? 1.0 : 0.0;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(1024)
-    dense_inverse_kernel(int n, double* __restrict__ A, double* __restrict__ inv, int* __restrict__ piv,
-                         double* __restrict__ dsc, unsigned* __restrict__ d_err) {
+    gj_pivot_kernel(int n, int k, double* __restrict__ A, double* __restrict__ R, double* __restrict__ col,
+                    int* __restrict__ piv, unsigned* __restrict__ d_err) {
   __shared__ double sval[32];
   __shared__ int sidx[32];
   __shared__ int s_p;
+  __shared__ double s_d;
   const int tid = threadIdx.x, nt = blockDim.x;
-  // equilibration D A D, D = |diag A|^{-1/2}
-  for (int j = tid; j < n; j += nt) {
-    double v = fabs(A[(long long)j * n + j]);
-    dsc[j] = v > 0.0 ? 1.0 / sqrt(v) : 1.0;
+  double best = -1.0;
+  int bi = k;
+  for (int rr = k + tid; rr < n; rr += nt) {
+    const double v = fabs(A[(long long)rr * n + k]);
+    if (v > best) { best = v; bi = rr; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, best, o);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+  if ((tid & 31) == 0) { sval[tid >> 5] = best; sidx[tid >> 5] = bi; }
+  __syncthreads();
+  if (tid == 0) {
+    const int nw = (nt + 31) / 32;
+    double bv = sval[0];
+    int bidx = sidx[0];
+    for (int w = 1; w < nw; ++w)
+      if (sval[w] > bv || (sval[w] == bv && sidx[w] < bidx)) { bv = sval[w]; bidx = sidx[w]; }
+    s_p = bidx;
+    piv[k] = bidx;
+    if (bv == 0.0) atomicOr(d_err, kErrSingularCoarse);
   }
   __syncthreads();
-  for (long long t = tid; t < (long long)n * n; t += nt) {
-    long long rr = t / n, cc = t % n;
-    A[t] = dsc[rr] * A[t] * dsc[cc];
-  }
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    // pivot: max |a_rk|, lowest row on ties
-    double best = -1.0;
-    int bi = k;
-    for (int rr = k + tid; rr < n; rr += nt) {
-      double v = fabs(A[(long long)rr * n + k]);
-      if (v > best) { best = v; bi = rr; }
+  const int p = s_p;
+  if (p != k) {
+    for (int cc = k + tid; cc < n; cc += nt) {
+      const double t0 = A[(long long)k * n + cc];
+      A[(long long)k * n + cc] = A[(long long)p * n + cc];
+      A[(long long)p * n + cc] = t0;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, best, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((tid & 31) == 0) { sval[tid >> 5] = best; sidx[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      int nw = (nt + 31) / 32;
-      double bv = sval[0];
-      int bidx = sidx[0];
-      for (int w = 1; w < nw; ++w)
-        if (sval[w] > bv || (sval[w] == bv && sidx[w] < bidx)) { bv = sval[w]; bidx = sidx[w]; }
-      s_p = bidx;
-      piv[k] = bidx;
-      if (bv == 0.0) atomicOr(d_err, kErrSingularCoarse);
-    }
-    __syncthreads();
-    int p = s_p;
-    if (p != k)
-      for (int cc = tid; cc < n; cc += nt) {
-        double t0 = A[(long long)k * n + cc];
-        A[(long long)k * n + cc] = A[(long long)p * n + cc];
-        A[(long long)p * n + cc] = t0;
-      }
-    __syncthreads();
-    double d = A[(long long)k * n + k];
-    for (int rr = k + 1 + tid; rr < n; rr += nt) A[(long long)rr * n + k] = d != 0.0 ? A[(long long)rr * n + k] / d : 0.0;
-    __syncthreads();
-    long long rem = (long long)(n - k - 1) * (n - k - 1);
-    for (long long t = tid; t < rem; t += nt) {
-      int rr = k + 1 + (int)(t / (n - k - 1)), cc = k + 1 + (int)(t % (n - k - 1));
-      A[(long long)rr * n + cc] = A[(long long)rr * n + cc] - A[(long long)rr * n + k] * A[(long long)k * n + cc];
-    }
-    __syncthreads();
-  }
-  // inverse columns: solve (D A D) z = P e_j, inv = D z D; threads own columns
-  for (int j = tid; j < n; j += nt) {
-    double* z = inv + (long long)j * n;  // column j stored contiguously (transposed below)
-    for (int q = 0; q < n; ++q) z[q] = q == j ? 1.0 : 0.0;
-    for (int k = 0; k < n; ++k) {
-      int p = piv[k];
-      if (p != k) { double t0 = z[k]; z[k] = z[p]; z[p] = t0; }
-    }
-    for (int rr = 0; rr < n; ++rr) {
-      double s = z[rr];
-      for (int cc = 0; cc < rr; ++cc) s = s - A[(long long)rr * n + cc] * z[cc];
-      z[rr] = s;
-    }
-    for (int rr = n - 1; rr >= 0; --rr) {
-      double s = z[rr];
-      for (int cc = rr + 1; cc < n; ++cc) s = s - A[(long long)rr * n + cc] * z[cc];
-      z[rr] = s / A[(long long)rr * n + rr];
+    for (int cc = tid; cc < n; cc += nt) {
+      const double t0 = R[(long long)k * n + cc];
+      R[(long long)k * n + cc] = R[(long long)p * n + cc];
+      R[(long long)p * n + cc] = t0;
     }
   }
   __syncthreads();
-  // z_j holds column j of (DAD)^{-1}; inv[r][j] = d_r z_j[r] d_j.  Transpose
-  // in place through A (no longer needed).
-  for (long long t = tid; t < (long long)n * n; t += nt) {
-    long long rr = t / n, cc = t % n;
-    A[rr * n + cc] = dsc[rr] * inv[cc * n + rr] * dsc[cc];
-  }
+  if (tid == 0) s_d = A[(long long)k * n + k];
   __syncthreads();
-  for (long long t = tid; t < (long long)n * n; t += nt) inv[t] = A[t];
+  const double d = s_d;
+  // the factors of column k (taken before the pivot row is scaled)
+  for (int rr = tid; rr < n; rr += nt) col[rr] = rr == k ? 0.0 : A[(long long)rr * n + k];
+  __syncthreads();
+  if (d != 0.0) {
+    for (int cc = k + 1 + tid; cc < n; cc += nt) A[(long long)k * n + cc] = A[(long long)k * n + cc] / d;
+    for (int cc = tid; cc < n; cc += nt) R[(long long)k * n + cc] = R[(long long)k * n + cc] / d;
+  }
+  if (tid == 0) A[(long long)k * n + k] = 1.0;
+}
+
+// rows r != k: row_r -= col[r] * row_k on the columns still live (left part
+// beyond k, all of the right part); a block per row, rows with a zero factor
+// skip the step
+__global__ void gj_eliminate_kernel(int n, int k, double* __restrict__ A, double* __restrict__ R,
+                                    const double* __restrict__ col) {
+  const double* ak = A + (long long)k * n;
+  const double* rk = R + (long long)k * n;
+  for (int rr = blockIdx.x; rr < n; rr += gridDim.x) {
+    const double f = col[rr];
+    if (rr == k || f == 0.0) continue;
+    double* ar = A + (long long)rr * n;
+    double* rw = R + (long long)rr * n;
+    for (int cc = k + 1 + threadIdx.x; cc < n; cc += blockDim.x) ar[cc] -= f * ak[cc];
+    for (int cc = threadIdx.x; cc < n; cc += blockDim.x) rw[cc] -= f * rk[cc];
+  }
+}
+
+// inv = D R D (in place, a block per row)
+__global__ void gj_finish_kernel(int n, double* __restrict__ R, const double* __restrict__ dsc) {
+  for (int rr = blockIdx.x; rr < n; rr += gridDim.x) {
+    const double dr = dsc[rr];
+    double* rw = R + (long long)rr * n;
+    for (int cc = threadIdx.x; cc < n; cc += blockDim.x) rw[cc] = dr * rw[cc] * dsc[cc];
+  }
 }
 
 // y = A x, one warp per row
@@ -847,8 +869,18 @@ cudaError_t launch_coarse_factor(const LevelGeom& g, const double* st, const uns
   else coarse_dense_kernel<3><<<blocks, 128, 0, s>>>(g, st, mask, work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  dense_inverse_kernel<<<1, 1024, 0, s>>>((int)g.ndof, work, inv, piv, dsc, d_err);
-  note_launches(2);
+  // dsc holds 2 n doubles: the scaling, then the factors of the current column
+  const int n = (int)g.ndof;
+  double* col = dsc + n;
+  const unsigned gb = (unsigned)std::min(n, 152 * 16);
+  gj_scale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, work, dsc);
+  gj_init_kernel<<<gb, 256, 0, s>>>(n, work, inv, dsc);
+  for (int k = 0; k < n; ++k) {
+    gj_pivot_kernel<<<1, 1024, 0, s>>>(n, k, work, inv, col, piv, d_err);
+    gj_eliminate_kernel<<<gb, 256, 0, s>>>(n, k, work, inv, col);
+  }
+  gj_finish_kernel<<<gb, 256, 0, s>>>(n, inv, dsc);
+  note_launches(4 + 2 * n);
   return cudaGetLastError();
 }
 
