@@ -10,9 +10,10 @@ and FGMRES.  Problems are passed in duck-typed (any object with the fields
 dim, n, lo, hi, shapes, alpha, qdepth, nlevels, eta, beta, omega, nu_pre,
 nu_post, preset, force_kind, force, ubar).
 
-The environment variable FC_ORACLE_LIB, when set, names another build of
-fc_oracle.c to load instead of the one built here; the planted-mistake
-tests use it to run the pins against altered copies of the oracle.
+The environment variables FC_ORACLE_LIB and FC_ORACLE_Q2_LIB, when set,
+name other builds of fc_oracle.c / fc_oracle_q2.c to load instead of the ones
+built here; the planted-mistake tests use them to run the pins against
+altered copies of the oracle.
 """
 from __future__ import annotations
 
@@ -356,4 +357,254 @@ class MG:
         b = np.ascontiguousarray(b, dtype=np.float64)
         rel = np.zeros(1)
         its = self.lib.or_gmg_solve(self.h, _p(b), _p(x), float(reduction), int(maxit), _p(rel))
+        return x, its, float(rel[0])
+
+
+# ---------------------------------------------------------------------------
+# Q2-Q1 (Taylor-Hood) variant with the lower-corner ownership rule
+# (fc_oracle_q2.c, which includes fc_oracle.c)
+_SRC_Q2 = os.path.join(_HERE, "fc_oracle_q2.c")
+_LIB_Q2 = os.path.join(_HERE, "libfc_oracle_q2.so")
+_lib_q2 = None
+Q2PMAX = 2214
+Q2OMAX = 25
+
+
+def build_q2(force: bool = False) -> str:
+    """Compile fc_oracle_q2.c next to this file (when it or fc_oracle.c changed)."""
+    with _lock:
+        stale = (not os.path.exists(_LIB_Q2) or os.path.getmtime(_LIB_Q2) < os.path.getmtime(_SRC_Q2)
+                 or os.path.getmtime(_LIB_Q2) < os.path.getmtime(_SRC))
+        if force or stale:
+            tmp = _LIB_Q2 + f".tmp{os.getpid()}"
+            compile_source(_SRC_Q2, tmp)
+            os.replace(tmp, _LIB_Q2)
+    return _LIB_Q2
+
+
+def _load_q2():
+    global _lib_q2
+    if _lib_q2 is not None:
+        return _lib_q2
+    alt = os.environ.get("FC_ORACLE_Q2_LIB")
+    if alt:
+        lib = C.CDLL(alt)
+    else:
+        build_q2()
+        lib = C.CDLL(_LIB_Q2)
+    vp, d, i, l = C.c_void_p, C.c_double, C.c_int, C.c_long
+    P = C.POINTER
+    lib.q2_level_new.restype = vp
+    lib.q2_level_new.argtypes = [i, P(C.c_int), P(d), P(d), i, P(d), d, i, d, d, d, i, i, P(d), d]
+    lib.q2_level_free.argtypes = [vp]
+    for fn in ("q2_ndof", "q2_nv", "q2_np", "q2_nnz"):
+        getattr(lib, fn).restype = l
+        getattr(lib, fn).argtypes = [vp]
+    lib.q2_cell_element.restype = i
+    lib.q2_cell_element.argtypes = [vp, l, P(d), P(d), P(d), P(d)]
+    lib.q2_assemble.argtypes = [vp]
+    lib.q2_csr_copy.argtypes = [vp, P(C.c_long), P(C.c_long), P(d), P(d), P(C.c_ubyte)]
+    lib.q2_apply.argtypes = [vp, P(d), P(d)]
+    lib.q2_residual.argtypes = [vp, P(d), P(d), P(d)]
+    lib.q2_patch_dofs.restype = i
+    lib.q2_patch_dofs.argtypes = [vp, l, P(C.c_long), P(C.c_int)]
+    lib.q2_patch_matrix.restype = i
+    lib.q2_patch_matrix.argtypes = [vp, l, P(d), P(C.c_long), P(C.c_int)]
+    lib.q2_patch_inverse_rows.restype = i
+    lib.q2_patch_inverse_rows.argtypes = [vp, l, P(C.c_long), P(C.c_int), P(d)]
+    lib.q2_build_inverse.restype = i
+    lib.q2_build_inverse.argtypes = [vp]
+    lib.q2_sweep.restype = i
+    lib.q2_sweep.argtypes = [vp, P(d), P(d), P(C.c_long)]
+    lib.q2_owner_count.argtypes = [vp, P(C.c_int)]
+    lib.q2_prolong_add.argtypes = [vp, vp, P(d), P(d)]
+    lib.q2_restrict.argtypes = [vp, vp, P(d), P(d)]
+    lib.q2_mg_new.restype = vp
+    lib.q2_mg_new.argtypes = [i, P(vp), i, i]
+    lib.q2_mg_free.argtypes = [vp]
+    lib.q2_vcycle.argtypes = [vp, P(d), P(d)]
+    lib.q2_fgmres.restype = i
+    lib.q2_fgmres.argtypes = [vp, P(d), P(d), d, i, i, P(d)]
+    lib.q2_gmg_solve.restype = i
+    lib.q2_gmg_solve.argtypes = [vp, P(d), P(d), d, i, P(d)]
+    _lib_q2 = lib
+    return lib
+
+
+class Q2Level:
+    """One grid level with the Q2-Q1 discretisation.  DoFs: velocity at the
+    Q2 nodes ((2 n_k + 1) per direction, x fastest, d components inner), then
+    the pressure at the vertices."""
+
+    def __init__(self, dim, n, lo, hi, shapes, alpha, qdepth, eta=1e-3, beta=100.0, omega=0.8, preset=0,
+                 force_kind=0, force=(0.0, 0.0, 0.0), ubar=0.3):
+        lib = _load_q2()
+        self.lib = lib
+        self.dim = int(dim)
+        self.n = tuple(int(k) for k in n)
+        nn = (C.c_int * 3)(*(list(self.n) + [1] * (3 - self.dim)))
+        lo_ = (C.c_double * 3)(*(list(lo) + [0.0] * (3 - self.dim)))
+        hi_ = (C.c_double * 3)(*(list(hi) + [1.0] * (3 - self.dim)))
+        sh = np.ascontiguousarray(np.asarray(shapes, dtype=np.float64).reshape(-1, 9))
+        self._shapes = sh
+        fo = (C.c_double * 3)(*list(force))
+        self.h = lib.q2_level_new(self.dim, nn, lo_, hi_, sh.shape[0], _p(sh), float(alpha), int(qdepth),
+                                  float(eta), float(beta), float(omega), int(preset), int(force_kind), fo,
+                                  float(ubar))
+        self.ndof = lib.q2_ndof(self.h)
+        self.nv = lib.q2_nv(self.h)
+        self.np = lib.q2_np(self.h)
+        self.ncell = int(np.prod(self.n))
+        self._assembled = False
+
+    @classmethod
+    def from_problem(cls, prob, level=None):
+        lvl = prob.nlevels if level is None else level
+        return cls(prob.dim, prob.level_n(lvl), prob.lo, prob.hi, prob.shapes, prob.alpha, prob.qdepth,
+                   prob.eta, prob.beta, prob.omega, prob.preset, prob.force_kind, prob.force, prob.ubar)
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.lib.q2_level_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def cell_element(self, cell: int):
+        na = 27 if self.dim == 3 else 9
+        nb = 1 << self.dim
+        A = np.zeros((na, na)); B = np.zeros((self.dim, na, nb)); f = np.zeros((self.dim, na)); st = np.zeros(4)
+        if self.lib.q2_cell_element(self.h, int(cell), _p(A), _p(B), _p(f), _p(st)) != 0:
+            raise IndexError(f"cell {cell} out of range")
+        return {"A": A, "B": B, "f": f, "fluid_volume": st[0], "boundary_measure": st[1],
+                "nvol": int(st[2]), "nbnd": int(st[3])}
+
+    def assemble(self):
+        if not self._assembled:
+            self.lib.q2_assemble(self.h)
+            self._assembled = True
+
+    def csr(self):
+        import scipy.sparse as sp
+        self.assemble()
+        nnz = self.lib.q2_nnz(self.h)
+        rp = np.zeros(self.ndof + 1, dtype=np.int64); col = np.zeros(nnz, dtype=np.int64)
+        val = np.zeros(nnz); rhs = np.zeros(self.ndof); fixed = np.zeros(self.ndof, dtype=np.uint8)
+        self.lib.q2_csr_copy(self.h, _p(rp, C.c_long), _p(col, C.c_long), _p(val), _p(rhs), _p(fixed, C.c_ubyte))
+        return sp.csr_matrix((val, col, rp), shape=(self.ndof, self.ndof)), rhs, fixed.astype(bool)
+
+    def residual(self, b, x):
+        self.assemble()
+        r = np.zeros(self.ndof)
+        self.lib.q2_residual(self.h, _p(np.ascontiguousarray(b, dtype=np.float64)),
+                             _p(np.ascontiguousarray(x, dtype=np.float64)), _p(r))
+        return r
+
+    def apply(self, x):
+        self.assemble()
+        y = np.zeros(self.ndof)
+        self.lib.q2_apply(self.h, _p(np.ascontiguousarray(x, dtype=np.float64)), _p(y))
+        return y
+
+    def patch_dofs(self, vert: int):
+        self.assemble()
+        d = np.zeros(Q2PMAX, dtype=np.int64); own = np.zeros(Q2OMAX, dtype=np.int32)
+        n = self.lib.q2_patch_dofs(self.h, int(vert), _p(d, C.c_long), _p(own, C.c_int))
+        return d[:n].copy(), own.copy()
+
+    def patch_matrix(self, vert: int):
+        self.assemble()
+        d = np.zeros(Q2PMAX, dtype=np.int64); own = np.zeros(Q2OMAX, dtype=np.int32)
+        Li = np.zeros(Q2PMAX * Q2PMAX)
+        n = self.lib.q2_patch_matrix(self.h, int(vert), _p(Li), _p(d, C.c_long), _p(own, C.c_int))
+        return Li[: n * n].reshape(n, n).copy(), d[:n].copy(), own.copy()
+
+    def patch_inverse_rows(self, vert: int):
+        self.assemble()
+        d = np.zeros(Q2PMAX, dtype=np.int64); own = np.zeros(Q2OMAX, dtype=np.int32)
+        rows = np.zeros((Q2OMAX, Q2PMAX))
+        n = self.lib.q2_patch_inverse_rows(self.h, int(vert), _p(d, C.c_long), _p(own, C.c_int), _p(rows))
+        if n < 0:
+            raise np.linalg.LinAlgError("singular patch")
+        return rows[:, :n].copy(), d[:n].copy(), own.copy()
+
+    def sweep(self, b, x, order=None):
+        self.assemble()
+        xx = np.ascontiguousarray(x, dtype=np.float64).copy()
+        o = None
+        if order is not None:
+            order = np.ascontiguousarray(order, dtype=np.int64)
+            o = _p(order, C.c_long)
+        self.lib.q2_sweep(self.h, _p(np.ascontiguousarray(b, dtype=np.float64)), _p(xx), o)
+        return xx
+
+    def owner_count(self):
+        self.assemble()
+        cnt = np.zeros(self.ndof, dtype=np.int32)
+        self.lib.q2_owner_count(self.h, _p(cnt, C.c_int))
+        return cnt
+
+
+def q2_prolong_add(fine: Q2Level, coarse: Q2Level, ec, xf):
+    fine.assemble(); coarse.assemble()
+    out = np.ascontiguousarray(xf, dtype=np.float64).copy()
+    fine.lib.q2_prolong_add(fine.h, coarse.h, _p(np.ascontiguousarray(ec, dtype=np.float64)), _p(out))
+    return out
+
+
+def q2_restrict(fine: Q2Level, coarse: Q2Level, rf):
+    fine.assemble(); coarse.assemble()
+    bc = np.zeros(coarse.ndof)
+    fine.lib.q2_restrict(fine.h, coarse.h, _p(np.ascontiguousarray(rf, dtype=np.float64)), _p(bc))
+    return bc
+
+
+class Q2MG:
+    """Q2-Q1 multigrid hierarchy: levels[0] coarsest .. levels[-1] finest."""
+
+    def __init__(self, prob=None, levels=None, nu_pre=None, nu_post=None):
+        if levels is None:
+            levels = [Q2Level.from_problem(prob, l) for l in range(1, prob.nlevels + 1)]
+        self.levels = levels
+        self.nu_pre = prob.nu_pre if nu_pre is None else nu_pre
+        self.nu_post = prob.nu_post if nu_post is None else nu_post
+        for lv in levels:
+            lv._assembled = True
+        self.lib = levels[0].lib
+        arr = (C.c_void_p * len(levels))(*[lv.h for lv in levels])
+        self.h = self.lib.q2_mg_new(len(levels), arr, int(self.nu_pre), int(self.nu_post))
+        self.fine = levels[-1]
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.lib.q2_mg_free(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def rhs(self):
+        _, b, _ = self.fine.csr()
+        return b
+
+    def vcycle(self, x, b):
+        xx = np.ascontiguousarray(x, dtype=np.float64).copy()
+        self.lib.q2_vcycle(self.h, _p(xx), _p(np.ascontiguousarray(b, dtype=np.float64)))
+        return xx
+
+    def fgmres(self, b, x0=None, rtol=1e-8, maxit=200, restart=30):
+        n = self.fine.ndof
+        x = np.zeros(n) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).copy()
+        rel = np.zeros(1)
+        its = self.lib.q2_fgmres(self.h, _p(np.ascontiguousarray(b, dtype=np.float64)), _p(x), float(rtol),
+                                 int(maxit), int(restart), _p(rel))
+        return x, its, float(rel[0])
+
+    def gmg_solve(self, b, x0=None, reduction=1e-9, maxit=100):
+        n = self.fine.ndof
+        x = np.zeros(n) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).copy()
+        rel = np.zeros(1)
+        its = self.lib.q2_gmg_solve(self.h, _p(np.ascontiguousarray(b, dtype=np.float64)), _p(x), float(reduction),
+                                    int(maxit), _p(rel))
         return x, its, float(rel[0])
