@@ -717,6 +717,63 @@ def run_replay(args):
     return 0
 
 
+def run_q2(args):
+    """The Q2-Q1 (Taylor-Hood) variant with the lower-corner ownership rule:
+    the 2D channel (unit square, one circle r = 0.2, parabolic inflow,
+    alpha 1e-8, quadtree depth 4) on an n x n grid, levels down to 16 x 16
+    cells, V(2,2), FP64 rows, FGMRES to 1e-8.  Reports solves/s and owned-
+    DoF updates/s over the timed solves, and the finest-level patch apply
+    timed alone with its algorithmic FLOP (171 slots x 9 owned rows x 2 per
+    patch, upper bound) and bytes."""
+    import torch
+    from paper_2403_11636_gb300 import build, fc, inputs
+    build.build()
+    n = args.q2_n
+    nlev = max(2, int(math.log2(n // 16)) + 1)
+    prob = inputs.channel_2d(0, n=n, nlevels=nlev)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        s = fc.Solver(prob, element="q2", stream=stream)
+        torch.cuda.synchronize()
+        setup_ms = 1e3 * (time.perf_counter() - t0)
+        b = s.rhs()
+        for _ in range(args.warmup):
+            s.solve(b, rtol=1e-8)
+        step_ms, total_ms, its_l, rr_l = timed_solves(s, b, prob, args.steps, stream, torch)
+        X = torch.zeros_like(b)
+        s.smooth_(X, b, nsweeps=2)
+        s.profile(True)
+        s.smooth_(X, b, nsweeps=10)
+        na, ma, ba = s.profile_read(4)
+        nr, mr, _ = s.profile_read(1)
+        s.profile(False)
+        ndof = s.ndof()
+        s.close()
+    nv1 = (n + 1) ** 2
+    nq = (2 * n + 1) ** 2
+    upd = (nq * 2 + nv1)                      # owned DoFs of the finest level (each written once per sweep)
+    per_solve = sum(((2 * (n >> k) + 1) ** 2 * 2 + ((n >> k) + 1) ** 2) for k in range(nlev - 1)) * 4
+    avg = ma / max(na, 1)
+    flop = nv1 * 171 * 9 * 2.0
+    tf, note = fp64_peak(torch)
+    hbm, _ = peaks()
+    emit({"mode": "q2", "metric": "smoother patch-DoF updates/s", "unit": "owned-DoF updates/s", "dtype": "f64",
+          "data": "synthetic",
+          "value": sum(its_l) * per_solve / (total_ms * 1e-3),
+          "config": {"workload": f"Q2-Q1 channel2d {n}^2, one circle r 0.2, alpha 1e-8, quadtree depth 4, "
+                                 f"{nlev} levels, V(2,2), FGMRES(30) rtol 1e-8, FP64 rows", "ndof": ndof,
+                     "iterations": its_l[0], "relres": max(rr_l), "setup_ms": setup_ms,
+                     "solves_per_s": args.steps / (total_ms * 1e-3), "ms_per_solve": total_ms / args.steps,
+                     "finest_owned_dofs": upd},
+          "finest_apply": {"ms": avg, "launches": na, "residual_ms": mr / max(nr, 1),
+                           "flop_per_launch": flop, "tflops": flop / (avg * 1e-3) / 1e12 if avg else None,
+                           "frac_of_fp64_peak": flop / (avg * 1e-3) / 1e12 / tf if avg else None,
+                           "fp64_peak_tflops": tf, "fp64_peak_source": note,
+                           "bytes_per_launch": ba, "hbm_frac": ba / (avg * 1e-3) / 1e9 / hbm if avg else None}})
+    return 0
+
+
 def run_batch(args):
     """Uneven batch: 256 independent 2D channel problems (grids 16..128^2,
     1-8 ellipses, alpha 1e-6..1e-10) solved together by fc_batch_solve
@@ -968,8 +1025,9 @@ def main():
                     help="grid of the oracle per-sweep timing (16: the solve sample's finest level)")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="profiled solves after the timed ones (per-kernel CUDA events)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep", "mixed", "replay"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep", "mixed", "replay", "q2"])
     ap.add_argument("--mixed-n", type=int, default=128, help="grid of --mode mixed")
+    ap.add_argument("--q2-n", type=int, default=512, help="grid of --mode q2")
     ap.add_argument("--replay-sizes", type=int, default=4,
                     help="--mode replay: 1024x256 and this many - 1 uniform refinements")
     ap.add_argument("--batch-workload", default="batch2d", choices=["batch2d", "porous3d"],
@@ -1006,6 +1064,8 @@ def main():
         return run_mixed(args)
     if args.mode == "replay":
         return run_replay(args)
+    if args.mode == "q2":
+        return run_q2(args)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fc_geom.cu", "fc_assemble.cu", "fc_mg.cu", "fc_patch.cu", "fc_api.cu", "fc_noalloc.cu", "fc_batch.cu", "fc_probe.cu"]
+SOURCES = ["fc_geom.cu", "fc_assemble.cu", "fc_mg.cu", "fc_patch.cu", "fc_api.cu", "fc_noalloc.cu", "fc_batch.cu",
+           "fc_probe.cu", "fc_q2.cu"]
 EXTRA = {"fc_geom.cu": ["--fmad=false"]}
 
 

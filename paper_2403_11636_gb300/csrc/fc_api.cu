@@ -329,9 +329,27 @@ fc_status smooth_level_pairs(fc_handle h, int li, double* x, const double* b, in
   return FC_OK;
 }
 
+bool q2_path(fc_handle h);
+cudaError_t level_residual(fc_handle h, int li, const double* x, const double* b, double* r);
+cudaError_t level_restrict(fc_handle h, int li, const double* rf, double* bc);
+cudaError_t level_prolong_add(fc_handle h, int li, const double* ec, double* xf);
+
 fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nsweeps) {
   Level& L = h->lev[li];
   if (pair_path(h)) return smooth_level_pairs(h, li, x, b, nsweeps, false);
+  if (q2_path(h)) {
+    for (int s = 0; s < nsweeps; ++s) {
+      {
+        ProfScope ps(h, 1, 0.0);
+        CK(launch_q2_residual(h->dim, L.q2, L.q2A, L.q2B, L.q2T, L.q2mask, x, b, nullptr, L.q2rpv, L.q2rpp,
+                              h->stream));
+      }
+      ProfScope ps(h, 0, (double)L.coef_bytes);
+      ProfScope pf(h, li == h->nlev - 1 ? 4 : -1, (double)L.coef_bytes);
+      CK(launch_q2_apply(L.q2, (const double*)L.coef, L.q2mask, L.q2rpv, L.q2rpp, h->opt.omega, x, h->stream));
+    }
+    return FC_OK;
+  }
   for (int s = 0; s < nsweeps; ++s) {
     fc_status st = smoother_residual(h, li, x, b);
     if (st != FC_OK) return st;
@@ -368,7 +386,7 @@ fc_status coarse_part(fc_handle h) {
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
     fc_status st = FC_OK;
     if (e == cudaSuccess) {
-      if (launch_restrict(L.g, C.g, C.mask, L.r, C.b, h->stream) != cudaSuccess ||
+      if (level_restrict(h, li, L.r, C.b) != cudaSuccess ||
           cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.ndof, h->stream) != cudaSuccess)
         st = FC_ERR_CUDA;
       if (st == FC_OK) st = vcycle_level(h, li - 1, C.x, C.b);
@@ -424,19 +442,19 @@ fc_status vcycle_level(fc_handle h, int li, double* x, const double* b) {
   } else {
     st = smooth_level(h, li, x, b, h->opt.nu_pre);
     if (st != FC_OK) return st;
-    CK(launch_residual(L.g, L.st, L.mask, x, b, L.r, nullptr, h->stream));
+    CK(level_residual(h, li, x, b, L.r));
   }
   if (li == h->nlev - 1 && h->stream != nullptr && h->stream != cudaStreamLegacy &&
       h->stream != cudaStreamPerThread) {
     // (the legacy default stream cannot be captured; it runs the launches directly)
     st = coarse_part(h);
   } else {
-    CK(launch_restrict(L.g, C.g, C.mask, L.r, C.b, h->stream));
+    CK(level_restrict(h, li, L.r, C.b));
     CK(cudaMemsetAsync(C.x, 0, sizeof(double) * C.g.ndof, h->stream));
     st = vcycle_level(h, li - 1, C.x, C.b);
   }
   if (st != FC_OK) return st;
-  CK(launch_prolong_add(L.g, C.g, L.mask, C.x, x, h->stream));
+  CK(level_prolong_add(h, li, C.x, x));
   if (pair_path(h)) return smooth_level_pairs(h, li, x, b, h->opt.nu_post, true);
   return smooth_level(h, li, x, b, h->opt.nu_post);
 }
@@ -462,6 +480,134 @@ fc_status read_scalar(fc_handle h, const double* dptr, double* out) {
   return FC_OK;
 }
 
+bool q2_path(fc_handle h) { return h->opt.element == 1; }
+
+// ---- operator pieces that depend on the element pair
+// r = b - L x (L x when b is null) on level li, unpadded
+cudaError_t level_residual(fc_handle h, int li, const double* x, const double* b, double* r) {
+  Level& L = h->lev[li];
+  if (q2_path(h))
+    return launch_q2_residual(h->dim, L.q2, L.q2A, L.q2B, L.q2T, L.q2mask, x, b, r, nullptr, nullptr, h->stream);
+  return launch_residual(L.g, L.st, L.mask, x, b, r, nullptr, h->stream);
+}
+
+cudaError_t level_restrict(fc_handle h, int li, const double* rf, double* bc) {
+  Level& L = h->lev[li];
+  Level& C = h->lev[li - 1];
+  if (q2_path(h)) return launch_q2_restrict(h->dim, L.q2, C.q2, C.q2mask, rf, bc, h->stream);
+  return launch_restrict(L.g, C.g, C.mask, rf, bc, h->stream);
+}
+
+cudaError_t level_prolong_add(fc_handle h, int li, const double* ec, double* xf) {
+  Level& L = h->lev[li];
+  Level& C = h->lev[li - 1];
+  if (q2_path(h)) return launch_q2_prolong_add(h->dim, L.q2, C.q2, L.q2mask, ec, xf, h->stream);
+  return launch_prolong_add(L.g, C.g, L.mask, ec, xf, h->stream);
+}
+
+// FGMRES workspace of the finest level
+fc_status alloc_krylov(fc_handle h) {
+  const long long n = h->lev[h->nlev - 1].g.ndof;
+  const int m = h->restart;
+  CK(dalloc(h, &h->V, (size_t)n * (m + 1), 2));
+  CK(dalloc(h, &h->Z, (size_t)n * m, 2));
+  CK(dalloc(h, &h->w, (size_t)n, 2));
+  CK(dalloc(h, &h->red, 2048, 2));
+  CK(dalloc(h, &h->small, (size_t)small_len(m), 2));
+  CK(dalloc(h, &h->bh, (size_t)n, 2));
+  CK(dalloc(h, &h->xh, (size_t)n, 2));
+  CK(cudaMallocHost((void**)&h->host_small, sizeof(double) * (size_t)small_len(m)));
+  return FC_OK;
+}
+
+// Q2-Q1 hierarchy (fc_q2.cu): element data with the Q2 basis, node masks,
+// stencil blocks, right-hand side on the finest level, patch rows on every
+// level above the coarsest, dense inverse of the coarsest operator
+fc_status setup_q2(fc_handle h, const fc_grid* g, const fc_options* o, int nshape, double alpha, int depth) {
+  const int dim = g->dim;
+  const int nv = dim == 3 ? 27 : 9, np = 1 << dim;
+  for (int li = 0; li < depth; ++li) {
+    Level& L = h->lev[li];
+    L.g = make_geom(g, nshape, h->d_shapes, alpha, o, depth - 1 - li);
+    L.q2 = make_q2grid(L.g);
+    const Q2Grid& q = L.q2;
+    L.g.ndof = q.nq * dim + q.np;
+    const LevelGeom& G = L.g;
+    const int w5 = dim == 3 ? 125 : 25, w3 = dim == 3 ? 27 : 9;
+    double *eA = nullptr, *eB = nullptr, *eF = nullptr;
+    CK(dalloc(h, &eA, (size_t)G.ncell * nv * nv, -1));
+    CK(dalloc(h, &eB, (size_t)G.ncell * dim * nv * np, -1));
+    CK(dalloc(h, &eF, (size_t)G.ncell * dim * nv, -1));
+    h->bytes[4] = std::max(h->bytes[4], (size_t)G.ncell * (nv * nv + dim * nv * np + dim * nv) * 8);
+    CK(launch_cell_elements_q2(G, eA, eB, eF, nullptr, h->d_err, h->stream));
+    CK(dalloc(h, &L.q2mask, (size_t)q.nq, 0));
+    CK(dalloc(h, &L.wfix, (size_t)q.nq * dim, 0));
+    CK(launch_q2_masks(G, q, L.q2mask, L.wfix, h->stream));
+    CK(dalloc(h, &L.q2A, (size_t)w5 * q.nq, 0));
+    CK(dalloc(h, &L.q2B, (size_t)w3 * dim * q.nq, 0));
+    CK(dalloc(h, &L.q2T, (size_t)w5 * dim * q.np, 0));
+    CK(dalloc(h, &L.x, (size_t)G.ndof, 2));
+    CK(dalloc(h, &L.b, (size_t)G.ndof, 2));
+    CK(dalloc(h, &L.r, (size_t)G.ndof, 2));
+    CK(launch_q2_assemble(G, q, eA, eB, eF, L.q2mask, L.wfix, L.q2A, L.q2B, L.q2T,
+                          li == depth - 1 ? L.b : nullptr, h->stream));
+    long long pv = dim, pp = 1;
+    for (int k = 0; k < dim; ++k) {
+      pv *= q.nf[k] + 8;
+      pp *= q.nv1[k] + 2;
+    }
+    CK(dalloc(h, &L.q2rpv, (size_t)pv, 2));
+    CK(dalloc(h, &L.q2rpp, (size_t)pp, 2));
+    CK(cudaMemsetAsync(L.q2rpv, 0, sizeof(double) * pv, h->stream));
+    CK(cudaMemsetAsync(L.q2rpp, 0, sizeof(double) * pp, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    dfree(h, eA);
+    dfree(h, eB);
+    dfree(h, eF);
+    fc_status st = check_err(h);
+    if (st != FC_OK) return st;
+    if (li > 0) {
+      const size_t n = (size_t)q.np * q2_patch_rows_doubles(dim);
+      double* c64 = nullptr;
+      CK(dalloc(h, &c64, n, 1));
+      {
+        ProfScope ps(h, 3, 0.0);
+        CK(launch_q2_patch_rows(q, L.q2A, L.q2B, L.q2mask, c64, h->d_err, h->stream));
+      }
+      L.coef = c64;
+      L.coef_bytes = n * 8;
+      CK(cudaStreamSynchronize(h->stream));
+      st = check_err(h);
+      if (st != FC_OK) return st;
+    }
+  }
+  // coarse solve: dense inverse of the coarsest operator
+  {
+    Level& C = h->lev[0];
+    const long long n = C.g.ndof;
+    if (n > 4096) return fail(h, FC_ERR_INVALID, "coarsest level too large for the dense solve; increase depth");
+    h->coarse_n = (int)n;
+    double *work = nullptr, *dsc = nullptr;
+    int* piv = nullptr;
+    CK(dalloc(h, &work, (size_t)n * n, -1));
+    CK(dalloc(h, &dsc, (size_t)2 * n, -1));
+    CK(dalloc(h, &piv, (size_t)n, -1));
+    CK(dalloc(h, &h->coarse_inv, (size_t)n * n, 3));
+    CK(launch_q2_dense(dim, C.q2, C.q2A, C.q2B, C.q2T, C.q2mask, work, h->stream));
+    CK(launch_dense_inverse((int)n, work, h->coarse_inv, piv, dsc, h->d_err, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    dfree(h, work);
+    dfree(h, dsc);
+    dfree(h, piv);
+    fc_status st = check_err(h);
+    if (st != FC_OK) return st;
+  }
+  fc_status st = alloc_krylov(h);
+  if (st != FC_OK) return st;
+  CK(cudaStreamSynchronize(h->stream));
+  return FC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -484,11 +630,44 @@ fc_status fc_options_default(fc_options* o) {
   o->dedup = 1;
   o->tc = 0;
   o->badcut_frac = 1e-3;
+  o->element = 0;
   return FC_OK;
 }
 
 size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o) {
   if (!g || !o || (g->dim != 2 && g->dim != 3) || depth < 1) return 0;
+  if (o->element == 1) {
+    // Q2-Q1: stencil blocks, masks and Dirichlet values, vectors and padded
+    // residuals, patch rows (levels above the coarsest), the element data of
+    // a level during setup, the coarse inverse and its elimination pair
+    const int dim = g->dim, nv = dim == 3 ? 27 : 9, np = 1 << dim, w5 = dim == 3 ? 125 : 25, w3 = dim == 3 ? 27 : 9;
+    size_t held = 0, transient = 0, coarse = 0, fine = 0;
+    for (int l = 0; l < depth; ++l) {
+      const int c = depth - 1 - l;
+      size_t nq = 1, npv = 1, cells = 1, padv = 1, padp = 1;
+      for (int k = 0; k < dim; ++k) {
+        const size_t n = (size_t)(g->n[k] >> c);
+        nq *= 2 * n + 1;
+        npv *= n + 1;
+        cells *= n;
+        padv *= 2 * n + 9;
+        padp *= n + 3;
+      }
+      const size_t ndof = nq * dim + npv;
+      if (l == 0) coarse = ndof;
+      if (l == depth - 1) fine = ndof;
+      held += ((size_t)w5 + (size_t)w3 * dim) * nq * 8 + (size_t)w5 * dim * npv * 8 + nq + nq * dim * 8;
+      held += 3 * ndof * 8 + padv * dim * 8 + padp * 8;
+      if (l > 0) held += npv * q2_patch_rows_doubles(dim) * 8;
+      transient = std::max(transient, cells * ((size_t)nv * nv + (size_t)dim * nv * np + (size_t)dim * nv) * 8);
+    }
+    held += coarse * coarse * 8;
+    transient = std::max(transient, coarse * coarse * 8 + coarse * 24);
+    const int m = o->fgmres_restart > 0 ? o->fgmres_restart : 30;
+    held += fine * 8 * (2 * (size_t)m + 4) + 2048 * 8 + (size_t)small_len(m) * 8;
+    const size_t total = held + transient;
+    return total + total / 50 + (8u << 20);
+  }
   const int dim = g->dim, nd = dim + 1, nb = dim == 3 ? 27 : 9, nl = 1 << dim, sp = spn(dim);
   const bool inverse = o->cache == FC_CACHE_INVERSE;
   const bool pairs = inverse && o->prec == FC_PREC_DF64;
@@ -572,6 +751,9 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     return fail(h, FC_ERR_INVALID, "invalid cache policy or precision");
   if (o->prec != FC_PREC_FP64 && o->cache != FC_CACHE_INVERSE)
     return fail(h, FC_ERR_INVALID, "reduced-precision storage applies to cache_inverse only");
+  if (o->element != 0 && o->element != 1) return fail(h, FC_ERR_INVALID, "invalid element pair");
+  if (o->element == 1 && (g->dim != 2 || o->cache != FC_CACHE_INVERSE || o->prec != FC_PREC_FP64))
+    return fail(h, FC_ERR_INVALID, "the Q2-Q1 pair runs in 2D with cache_inverse and FP64 rows");
   {
     long long nodes = 1;
     for (int k = 0; k < g->dim; ++k) nodes *= (long long)g->n[k] + 1;
@@ -601,6 +783,12 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), h->stream));
   CK(dalloc(h, &h->d_shapes, (size_t)std::max(nshape, 1), 0));
   if (nshape) CK(cudaMemcpyAsync(h->d_shapes, hs.data(), sizeof(Shape) * nshape, cudaMemcpyHostToDevice, h->stream));
+  if (o->element == 1) {
+    fc_status st = setup_q2(h, g, o, nshape, alpha, depth);
+    if (st != FC_OK) return st;
+    h->ready = true;
+    return FC_OK;
+  }
   unsigned long long* d_count = nullptr;
   CK(dalloc(h, &d_count, 2, -1));
 
@@ -854,16 +1042,8 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   }
   // ---- FGMRES workspace
   {
-    long long n = h->lev[depth - 1].g.ndof;
-    int m = h->restart;
-    CK(dalloc(h, &h->V, (size_t)n * (m + 1), 2));
-    CK(dalloc(h, &h->Z, (size_t)n * m, 2));
-    CK(dalloc(h, &h->w, (size_t)n, 2));
-    CK(dalloc(h, &h->red, 2048, 2));
-    CK(dalloc(h, &h->small, (size_t)small_len(m), 2));
-    CK(dalloc(h, &h->bh, (size_t)n, 2));
-    CK(dalloc(h, &h->xh, (size_t)n, 2));
-    CK(cudaMallocHost((void**)&h->host_small, sizeof(double) * (size_t)small_len(m)));
+    fc_status st = alloc_krylov(h);
+    if (st != FC_OK) return st;
   }
   CK(cudaStreamSynchronize(h->stream));
   h->ready = true;
@@ -883,8 +1063,7 @@ fc_status fc_residual(fc_handle h, int level, const double* x, const double* b, 
   fc_status st = level_ok(h, level, 1);
   if (st != FC_OK) return st;
   if (!x || !b || !r) return fail(h, FC_ERR_INVALID, "null vector");
-  Level& L = h->lev[level - 1];
-  CK(launch_residual(L.g, L.st, L.mask, x, b, r, nullptr, h->stream));
+  CK(level_residual(h, level - 1, x, b, r));
   return FC_OK;
 }
 
@@ -892,8 +1071,7 @@ fc_status fc_apply(fc_handle h, int level, const double* x, double* y) {
   fc_status st = level_ok(h, level, 1);
   if (st != FC_OK) return st;
   if (!x || !y) return fail(h, FC_ERR_INVALID, "null vector");
-  Level& L = h->lev[level - 1];
-  CK(launch_residual(L.g, L.st, L.mask, x, nullptr, y, nullptr, h->stream));
+  CK(level_residual(h, level - 1, x, nullptr, y));
   return FC_OK;
 }
 
@@ -908,7 +1086,7 @@ fc_status fc_restrict(fc_handle h, int level, const double* rf, double* bc) {
   fc_status st = level_ok(h, level, 2);
   if (st != FC_OK) return st;
   if (!rf || !bc) return fail(h, FC_ERR_INVALID, "null vector");
-  CK(launch_restrict(h->lev[level - 1].g, h->lev[level - 2].g, h->lev[level - 2].mask, rf, bc, h->stream));
+  CK(level_restrict(h, level - 1, rf, bc));
   return FC_OK;
 }
 
@@ -916,7 +1094,7 @@ fc_status fc_prolong_add(fc_handle h, int level, const double* ec, double* xf) {
   fc_status st = level_ok(h, level, 2);
   if (st != FC_OK) return st;
   if (!ec || !xf) return fail(h, FC_ERR_INVALID, "null vector");
-  CK(launch_prolong_add(h->lev[level - 1].g, h->lev[level - 2].g, h->lev[level - 1].mask, ec, xf, h->stream));
+  CK(level_prolong_add(h, level - 1, ec, xf));
   return FC_OK;
 }
 
@@ -964,7 +1142,7 @@ fc_status fc_solve(fc_handle h, const double* b, double* x, double rtol, int max
     return FC_OK;
   }
   for (;;) {
-    CK(launch_residual(F.g, F.st, F.mask, x, b, h->w, nullptr, s));
+    CK(level_residual(h, h->nlev - 1, x, b, h->w));
     double beta2 = 0.0;
     CK(launch_dot(n, h->w, h->w, h->red, sc + 1, s));
     st = read_scalar(h, sc + 1, &beta2);
@@ -987,7 +1165,7 @@ fc_status fc_solve(fc_handle h, const double* b, double* x, double rtol, int max
         if (st != FC_OK) return st;
       }
       its++;
-      CK(launch_residual(F.g, F.st, F.mask, Zj, nullptr, h->w, nullptr, s));
+      CK(level_residual(h, h->nlev - 1, Zj, nullptr, h->w));
       // modified Gram-Schmidt, one fused kernel per step: step i finishes
       // h_{i-1,j} from the block partials, subtracts it and starts the dot
       // with v_i; the last two steps give the norm and v_{j+1}
@@ -1029,7 +1207,7 @@ fc_status fc_gmg_solve(fc_handle h, const double* b, double* x, double reduction
   cudaStream_t s = h->stream;
   double* sc = h->small + small_sc(h->restart);
   double r0 = 0.0, rn = 0.0;
-  CK(launch_residual(F.g, F.st, F.mask, x, b, h->w, nullptr, s));
+  CK(level_residual(h, h->nlev - 1, x, b, h->w));
   CK(launch_dot(n, h->w, h->w, h->red, sc + 1, s));
   fc_status st = read_scalar(h, sc + 1, &r0);
   if (st != FC_OK) return st;
@@ -1042,7 +1220,7 @@ fc_status fc_gmg_solve(fc_handle h, const double* b, double* x, double reduction
       st = f32_path(h) ? handle_vcycle_f32(h, x, b, false) : vcycle_level(h, h->nlev - 1, x, b);
       if (st != FC_OK) return st;
     }
-    CK(launch_residual(F.g, F.st, F.mask, x, b, h->w, nullptr, s));
+    CK(level_residual(h, h->nlev - 1, x, b, h->w));
     CK(launch_dot(n, h->w, h->w, h->red, sc + 1, s));
     st = read_scalar(h, sc + 1, &rn);
     if (st != FC_OK) return st;
@@ -1092,6 +1270,17 @@ fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_hos
   const Level& L = h->lev[level - 1];
   if (!rows_host || node < 0 || node >= L.g.nnodes) return fail(h, FC_ERR_INVALID, "bad patch");
   if (h->opt.cache != FC_CACHE_INVERSE || !L.coef) return fail(h, FC_ERR_INVALID, "no cached rows");
+  if (q2_path(h)) {
+    // 9 owned rows x 171 slots, stored [slot][10]
+    const int NS = 171, NRP = 10;
+    std::vector<double> raw((size_t)NS * NRP);
+    CK(cudaMemcpyAsync(raw.data(), (const double*)L.coef + (size_t)node * NS * NRP, sizeof(double) * raw.size(),
+                       cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 9; ++k)
+      for (int j = 0; j < NS; ++j) rows_host[(size_t)k * NS + j] = raw[(size_t)j * NRP + k];
+    return FC_OK;
+  }
   const int ns = nslot(h->dim), nd = h->dim + 1;
   const size_t cnt = (size_t)ns * nd;
   const size_t eb = coef_elem_bytes(h->opt.prec);
@@ -1175,6 +1364,7 @@ fc_status fc_destroy(fc_handle h) {
     dfree(h, L.x); dfree(h, L.b); dfree(h, L.r); dfree(h, L.rpad); dfree(h, L.rpad32);
     dfree(h, L.st2); dfree(h, L.xp2); dfree(h, L.bp2); dfree(h, L.prow);
     dfree(h, L.st32); dfree(h, L.d32); dfree(h, L.b32);
+    dfree(h, L.q2mask); dfree(h, L.q2A); dfree(h, L.q2B); dfree(h, L.q2T); dfree(h, L.q2rpv); dfree(h, L.q2rpp);
   }
   if (h->coarse_graph) cudaGraphExecDestroy(h->coarse_graph);
   dfree(h, h->d_shapes); dfree(h, h->d_err); dfree(h, h->coarse_inv);

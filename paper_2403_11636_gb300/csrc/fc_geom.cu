@@ -4,12 +4,14 @@
 //   a(v,u) = (eta grad v, alpha grad u) - (v, n.eta grad u)_G - (n.eta grad v, u)_G + (v, lambda u)_G
 //   b(v,p) = -(div v, alpha p) + (v, n p)_G
 //   f(v)   = (v, alpha f)
-// for the 2^d Q1 nodal functions of the cell (eq. stokes_disc_weak_fcm_2),
+// for the nodal functions of the cell (eq. stokes_disc_weak_fcm_2): the 2^d
+// Q1 functions for velocity and pressure (the paper's pair), or the 3^d Q2
+// velocity functions with the Q1 pressure functions (Taylor-Hood variant),
 // with Gamma_D the obstacle boundary (no-slip, w = 0).  The volume rule is
 // the recursive box split: a box is split into 2^d children when the level
 // set changes sign among its 3^d sample points, down to the quadrature depth;
-// leaves take the tensor 2-point Gauss rule with alpha evaluated at each
-// point.  The boundary rule is composite 2-point Gauss in the curve
+// leaves take the tensor 2-point (Q1) or 3-point (Q2) Gauss rule with alpha
+// evaluated at each point.  The boundary rule is composite 2-point Gauss in the curve
 // parameter (circle / ellipse) or in cos(theta) times a uniform rule in the
 // azimuth (sphere); every rule point is owned by the cell that contains it.
 //
@@ -27,7 +29,6 @@ namespace fc {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kWarpsPerBlock = 4;
 constexpr int kStack = 48;
 
 __device__ __forceinline__ double phi_shape(const Shape& s, int dim, const double* x) {
@@ -108,40 +109,95 @@ __device__ __forceinline__ void force_at(const LevelGeom& g, const double* x, do
 }
 
 // Entries handled by one lane: e = lane + 32 t.  Entry index space:
-// [A upper triangle (a <= b, a-major)] [B (c, a, b)] [F (c, a)].
-template <int DIM>
+// [A upper triangle (a <= b, a-major)] [B (c, a, b)] [F (c, a)], with NV
+// velocity and NP pressure functions per cell (Q1: 2^d and 2^d; Q2: 3^d
+// and 2^d).
+template <int DIM, int Q = 1>
 struct Entries {
-  static constexpr int NL = 1 << DIM;
-  static constexpr int NA = NL * (NL + 1) / 2;
-  static constexpr int NB = DIM * NL * NL;
-  static constexpr int NF = DIM * NL;
+  static constexpr int NV = Q == 2 ? (DIM == 3 ? 27 : 9) : (1 << DIM);
+  static constexpr int NP = 1 << DIM;
+  static constexpr int NA = NV * (NV + 1) / 2;
+  static constexpr int NB = DIM * NV * NP;
+  static constexpr int NF = DIM * NV;
   static constexpr int NE = NA + NB + NF;
   static constexpr int PER = (NE + 31) / 32;
+  static constexpr int NG1 = Q + 1;  // Gauss points per direction on a leaf
+  static constexpr int NG = DIM == 3 ? NG1 * NG1 * NG1 : NG1 * NG1;
+  // warps per CTA: the per-warp point queue grows with the basis and static
+  // shared memory is limited to 48 KB per CTA
+  static constexpr int WARPS = Q == 2 ? (DIM == 3 ? 1 : 3) : 4;
 };
 
 struct EntryId {
   int kind, c, a, b;  // kind 0 A, 1 B, 2 F, -1 none
 };
 
-template <int DIM>
+template <int DIM, int Q = 1>
 __device__ EntryId entry_of(int e) {
-  using E = Entries<DIM>;
+  using E = Entries<DIM, Q>;
   EntryId id{-1, 0, 0, 0};
   if (e < E::NA) {
     int a = 0, rem = e;
-    while (rem >= E::NL - a) { rem -= E::NL - a; ++a; }
+    while (rem >= E::NV - a) { rem -= E::NV - a; ++a; }
     id.kind = 0; id.a = a; id.b = a + rem;
   } else if (e < E::NA + E::NB) {
     int t = e - E::NA;
-    id.kind = 1; id.c = t / (E::NL * E::NL); id.a = (t / E::NL) % E::NL; id.b = t % E::NL;
+    id.kind = 1; id.c = t / (E::NV * E::NP); id.a = (t / E::NP) % E::NV; id.b = t % E::NP;
   } else if (e < E::NE) {
     int t = e - E::NA - E::NB;
-    id.kind = 2; id.c = t / E::NL; id.a = t % E::NL;
+    id.kind = 2; id.c = t / E::NV; id.a = t % E::NV;
   }
   return id;
 }
 
+// Q2 functions on [0, 1]: q0 = (1-t)(1-2t), q1 = 4t(1-t), q2 = t(2t-1)
+__device__ __forceinline__ void q2_1d(double t, double* v, double* d) {
+  v[0] = (1.0 - t) * (1.0 - 2.0 * t);
+  v[1] = 4.0 * t * (1.0 - t);
+  v[2] = t * (2.0 * t - 1.0);
+  d[0] = 4.0 * t - 3.0;
+  d[1] = 4.0 - 8.0 * t;
+  d[2] = 4.0 * t - 1.0;
+}
+
+// velocity values / gradients (NV) and pressure values (NP) at x
+template <int DIM, int Q>
+__device__ __forceinline__ void elem_basis(const double* x0, const double* h, const double* x, double* val,
+                                           double (*grad)[3], double* pval) {
+  if (Q == 1) {
+    q1_basis(DIM, x0, h, x, val, grad);
+    for (int a = 0; a < (1 << DIM); ++a) pval[a] = val[a];
+    return;
+  }
+  double v[3][3], d[3][3], t[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < 3; ++k) {
+    t[k] = k < DIM ? (x[k] - x0[k]) / h[k] : 0.0;
+    q2_1d(t[k], v[k], d[k]);
+  }
+  constexpr int NV = DIM == 3 ? 27 : 9;
+  for (int a = 0; a < NV; ++a) {
+    const int ia[3] = {a % 3, (a / 3) % 3, a / 9};
+    double f = 1.0;
+    for (int k = 0; k < DIM; ++k) f = f * v[k][ia[k]];
+    val[a] = f;
+    grad[a][0] = grad[a][1] = grad[a][2] = 0.0;
+    for (int k = 0; k < DIM; ++k) {
+      double gk = d[k][ia[k]] / h[k];
+      for (int m = 0; m < DIM; ++m)
+        if (m != k) gk = gk * v[m][ia[m]];
+      grad[a][k] = gk;
+    }
+  }
+  for (int b = 0; b < (1 << DIM); ++b) {
+    double f = 1.0;
+    for (int k = 0; k < DIM; ++k) f = f * (((b >> k) & 1) ? t[k] : 1.0 - t[k]);
+    pval[b] = f;
+  }
+}
+
+template <int DIM, int Q>
 struct WarpShared {
+  static constexpr int NV = Entries<DIM, Q>::NV, NP = Entries<DIM, Q>::NP;
   int cand[kMaxShapesPerCell];
   double stk_lo[kStack][3];
   int stk_lev[kStack];
@@ -152,8 +208,9 @@ struct WarpShared {
   double pw[32];
   double pal[32];
   double pf[32][3];
-  double pval[32][8];
-  double pgrad[32][8][3];
+  double pval[32][NV];
+  double pgrad[32][NV][3];
+  double ppv[32][Q == 2 ? NP : 1];  // Q1: the pressure functions are the velocity ones (pval)
 };
 
 // Angular index range [lo, hi] (before wrapping) of rule points t = step *
@@ -184,19 +241,19 @@ __device__ bool angular_range(double bx0, double bx1, double by0, double by1, do
   return true;
 }
 
-template <int DIM>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+template <int DIM, int Q>
+__global__ void __launch_bounds__(Entries<DIM, Q>::WARPS * 32)
     cell_elements_kernel(LevelGeom g, double* __restrict__ eA, double* __restrict__ eB,
                          double* __restrict__ eF, double* __restrict__ estat,
                          unsigned* __restrict__ d_err, const double* __restrict__ refA,
                          const double* __restrict__ refB, unsigned char* __restrict__ cclass) {
-  using E = Entries<DIM>;
-  constexpr int NL = E::NL;
-  __shared__ WarpShared wsh[kWarpsPerBlock];
+  using E = Entries<DIM, Q>;
+  constexpr int NL = E::NV, NP = E::NP, WARPS = E::WARPS;
+  __shared__ WarpShared<DIM, Q> wsh[WARPS];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  WarpShared& S = wsh[wib];
-  const long long cell = (long long)blockIdx.x * kWarpsPerBlock + wib;
+  WarpShared<DIM, Q>& S = wsh[wib];
+  const long long cell = (long long)blockIdx.x * WARPS + wib;
   if (cell >= g.ncell) return;
   const unsigned FULL = 0xffffffffu;
 
@@ -247,18 +304,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   // queued points to their entries in queue order, so every entry is still
   // the sum over the points in rule order.
   const double gq[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
-  constexpr int NG = DIM == 3 ? 8 : 4;
+  // 3-point Gauss (Q2 leaves): nodes 1/2 -+ sqrt(3/5)/2, 1/2, weights 5/18, 8/18, 5/18
+  const double gq3[3] = {0.5 - 0.5 * sqrt(0.6), 0.5, 0.5 + 0.5 * sqrt(0.6)};
+  const double gw3[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  constexpr int NG = E::NG;
   int npt = 0;
   auto flush = [&]() {
     if (lane < npt) {
       const double x[3] = {S.px[lane][0], S.px[lane][1], S.px[lane][2]};
       S.pal[lane] = inside_obstacle(g.shapes, S.cand, nc, DIM, x) ? g.alpha : 1.0;
-      double val[8], grad[8][3];
-      q1_basis(DIM, x0, g.h, x, val, grad);
+      double val[NL], grad[NL][3], pv[NP];
+      elem_basis<DIM, Q>(x0, g.h, x, val, grad, pv);
       for (int a = 0; a < NL; ++a) {
         S.pval[lane][a] = val[a];
         for (int k = 0; k < 3; ++k) S.pgrad[lane][a][k] = grad[a][k];
       }
+      if (Q == 2)
+        for (int b = 0; b < NP; ++b) S.ppv[lane][b] = pv[b];
       double f[3] = {0.0, 0.0, 0.0};
       force_at(g, x, f);
       for (int k = 0; k < 3; ++k) S.pf[lane][k] = f[k];
@@ -268,13 +330,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
       const double w = S.pw[q], al = S.pal[q];
 #pragma unroll
       for (int t = 0; t < E::PER; ++t) {
-        EntryId id = entry_of<DIM>(lane + 32 * t);
+        EntryId id = entry_of<DIM, Q>(lane + 32 * t);
         if (id.kind == 0) {
           double gg = 0.0;
           for (int kk = 0; kk < DIM; ++kk) gg = gg + S.pgrad[q][id.a][kk] * S.pgrad[q][id.b][kk];
           acc[t] = acc[t] + w * al * g.eta * gg;
         } else if (id.kind == 1) {
-          acc[t] = acc[t] - w * al * S.pgrad[q][id.a][id.c] * S.pval[q][id.b];
+          acc[t] = acc[t] - w * al * S.pgrad[q][id.a][id.c] * (Q == 2 ? S.ppv[q][id.b] : S.pval[q][id.b]);
         } else if (id.kind == 2) {
           acc[t] = acc[t] + w * al * S.pf[q][id.c] * S.pval[q][id.a];
         }
@@ -343,13 +405,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
     // a leaf: queue its Gauss points
     if (npt + NG > 32) flush();
-    double w = 1.0;
-    for (int k = 0; k < DIM; ++k) w = w * (hb[k] * 0.5);
-    if (lane < NG) {
-      const int i = lane & 1, j = (lane >> 1) & 1, k = lane >> 2;
-      S.px[npt + lane][0] = lo[0] + hb[0] * gq[i];
-      S.px[npt + lane][1] = lo[1] + hb[1] * gq[j];
-      S.px[npt + lane][2] = DIM == 3 ? lo[2] + hb[2] * gq[k] : 0.0;
+    if (Q == 1) {
+      double w = 1.0;
+      for (int k = 0; k < DIM; ++k) w = w * (hb[k] * 0.5);
+      if (lane < NG) {
+        const int i = lane & 1, j = (lane >> 1) & 1, k = lane >> 2;
+        S.px[npt + lane][0] = lo[0] + hb[0] * gq[i];
+        S.px[npt + lane][1] = lo[1] + hb[1] * gq[j];
+        S.px[npt + lane][2] = DIM == 3 ? lo[2] + hb[2] * gq[k] : 0.0;
+        S.pw[npt + lane] = w;
+      }
+    } else if (lane < NG) {
+      const int i = lane % 3, j = (lane / 3) % 3, k = lane / 9;
+      S.px[npt + lane][0] = lo[0] + hb[0] * gq3[i];
+      S.px[npt + lane][1] = lo[1] + hb[1] * gq3[j];
+      S.px[npt + lane][2] = DIM == 3 ? lo[2] + hb[2] * gq3[k] : 0.0;
+      double w = (hb[0] * gw3[i]) * (hb[1] * gw3[j]);
+      if (DIM == 3) w = w * (hb[2] * gw3[k]);
       S.pw[npt + lane] = w;
     }
     npt += NG;
@@ -428,11 +500,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
           }
           // each lane evaluates the basis at its own point; the points are
           // then added in rule order with their values broadcast by shuffle
-          double lval[NL], ldn[NL];
+          double lval[NL], ldn[NL], lpv[NP];
           {
             double bx[3] = {px, py, 0.0};
-            double val[8], grad[8][3];
-            q1_basis(DIM, x0, g.h, bx, val, grad);
+            double val[NL], grad[NL][3];
+            elem_basis<DIM, Q>(x0, g.h, bx, val, grad, lpv);
             for (int q = 0; q < NL; ++q) {
               double sdn = 0.0;
               const double bnl[3] = {nx, ny, 0.0};
@@ -447,21 +519,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             vb &= vb - 1;
             double bn[3] = {__shfl_sync(FULL, nx, src), __shfl_sync(FULL, ny, src), 0.0};
             double bw = __shfl_sync(FULL, wgt, src);
-            double val[8], dn[8];
+            double val[NL], dn[NL], pv[NP];
 #pragma unroll
             for (int q = 0; q < NL; ++q) {
               val[q] = __shfl_sync(FULL, lval[q], src);
               dn[q] = __shfl_sync(FULL, ldn[q], src);
             }
 #pragma unroll
+            for (int q = 0; q < NP; ++q) pv[q] = __shfl_sync(FULL, lpv[q], src);
+#pragma unroll
             for (int u = 0; u < E::PER; ++u) {
-              EntryId id = entry_of<DIM>(lane + 32 * u);
+              EntryId id = entry_of<DIM, Q>(lane + 32 * u);
               if (id.kind == 0) {
                 double tv = -g.eta * val[id.a] * dn[id.b] - g.eta * dn[id.a] * val[id.b] +
                             g.lambda * val[id.a] * val[id.b];
                 acc[u] = acc[u] + bw * tv;
               } else if (id.kind == 1) {
-                acc[u] = acc[u] + bw * val[id.a] * bn[id.c] * val[id.b];
+                acc[u] = acc[u] + bw * val[id.a] * bn[id.c] * pv[id.b];
               }
             }
             bmeasure = bmeasure + bw;
@@ -535,10 +609,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                     if (S.cand[u] != s && phi_shape(g.shapes[S.cand[u]], 3, xx) > 0.0) { ok = false; break; }
                 }
               }
-              double lval[NL], ldn[NL];
+              double lval[NL], ldn[NL], lpv[NP];
               {
-                double val[8], grad[8][3];
-                q1_basis(DIM, x0, g.h, xx, val, grad);
+                double val[NL], grad[NL][3];
+                elem_basis<DIM, Q>(x0, g.h, xx, val, grad, lpv);
                 const double bnl[3] = {-ex, -ey, -mu};
                 for (int qq = 0; qq < NL; ++qq) {
                   double sdn = 0.0;
@@ -552,21 +626,23 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
                 int src = __ffs(vb) - 1;
                 vb &= vb - 1;
                 double bn[3] = {-__shfl_sync(FULL, ex, src), -__shfl_sync(FULL, ey, src), -mu};
-                double val[8], dn[8];
+                double val[NL], dn[NL], pv[NP];
 #pragma unroll
                 for (int qq = 0; qq < NL; ++qq) {
                   val[qq] = __shfl_sync(FULL, lval[qq], src);
                   dn[qq] = __shfl_sync(FULL, ldn[qq], src);
                 }
 #pragma unroll
+                for (int qq = 0; qq < NP; ++qq) pv[qq] = __shfl_sync(FULL, lpv[qq], src);
+#pragma unroll
                 for (int u = 0; u < E::PER; ++u) {
-                  EntryId id = entry_of<DIM>(lane + 32 * u);
+                  EntryId id = entry_of<DIM, Q>(lane + 32 * u);
                   if (id.kind == 0) {
                     double tv = -g.eta * val[id.a] * dn[id.b] - g.eta * dn[id.a] * val[id.b] +
                                 g.lambda * val[id.a] * val[id.b];
                     acc[u] = acc[u] + wgt * tv;
                   } else if (id.kind == 1) {
-                    acc[u] = acc[u] + wgt * val[id.a] * bn[id.c] * val[id.b];
+                    acc[u] = acc[u] + wgt * val[id.a] * bn[id.c] * pv[id.b];
                   }
                 }
                 bmeasure = bmeasure + wgt;
@@ -586,17 +662,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   // patch blocks of uncut regions bit-identical (patch classes).
   const bool plain = refA != nullptr && !split && nbnd == 0 && !al_mixed && al_first > 0.0;
   double* A = eA + cell * NL * NL;
-  double* B = eB + cell * DIM * NL * NL;
+  double* B = eB + cell * DIM * NL * NP;
   double* F = eF + cell * DIM * NL;
 #pragma unroll
   for (int t = 0; t < E::PER; ++t) {
-    EntryId id = entry_of<DIM>(lane + 32 * t);
+    EntryId id = entry_of<DIM, Q>(lane + 32 * t);
     if (id.kind == 0) {
       double v = plain ? al_first * refA[id.a * NL + id.b] : acc[t];
       A[id.a * NL + id.b] = v;
       A[id.b * NL + id.a] = v;
     } else if (id.kind == 1) {
-      B[(id.c * NL + id.a) * NL + id.b] = plain ? al_first * refB[(id.c * NL + id.a) * NL + id.b] : acc[t];
+      B[(id.c * NL + id.a) * NP + id.b] = plain ? al_first * refB[(id.c * NL + id.a) * NP + id.b] : acc[t];
     } else if (id.kind == 2) {
       F[id.c * NL + id.a] = acc[t];
     }
@@ -610,18 +686,29 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
   }
 }
 
+template <int DIM, int Q>
+void run_elements(const LevelGeom& g, double* eA, double* eB, double* eF, double* estat, unsigned* d_err,
+                  const double* refA, const double* refB, unsigned char* cclass, cudaStream_t s) {
+  constexpr int W = Entries<DIM, Q>::WARPS;
+  const long long blocks = (g.ncell + W - 1) / W;
+  cell_elements_kernel<DIM, Q><<<(unsigned)blocks, W * 32, 0, s>>>(g, eA, eB, eF, estat, d_err, refA, refB, cclass);
+}
+
 }  // namespace
 
 cudaError_t launch_cell_elements(const LevelGeom& g, double* eA, double* eB, double* eF,
                                  double* estat, unsigned* d_err, const double* refA, const double* refB,
                                  unsigned char* cclass, cudaStream_t s) {
-  long long blocks = (g.ncell + kWarpsPerBlock - 1) / kWarpsPerBlock;
-  if (g.dim == 2)
-    cell_elements_kernel<2><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, eA, eB, eF, estat, d_err, refA,
-                                                                             refB, cclass);
-  else
-    cell_elements_kernel<3><<<(unsigned)blocks, kWarpsPerBlock * 32, 0, s>>>(g, eA, eB, eF, estat, d_err, refA,
-                                                                             refB, cclass);
+  if (g.dim == 2) run_elements<2, 1>(g, eA, eB, eF, estat, d_err, refA, refB, cclass, s);
+  else run_elements<3, 1>(g, eA, eB, eF, estat, d_err, refA, refB, cclass, s);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_elements_q2(const LevelGeom& g, double* eA, double* eB, double* eF, double* estat,
+                                    unsigned* d_err, cudaStream_t s) {
+  if (g.dim == 2) run_elements<2, 2>(g, eA, eB, eF, estat, d_err, nullptr, nullptr, nullptr, s);
+  else run_elements<3, 2>(g, eA, eB, eF, estat, d_err, nullptr, nullptr, nullptr, s);
   note_launches(1);
   return cudaGetLastError();
 }

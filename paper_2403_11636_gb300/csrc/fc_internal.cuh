@@ -68,6 +68,12 @@ inline long long pad_nodes(const LevelGeom& g) {
   return px * py * pz;
 }
 
+// Q2-Q1 grid sizes of a level: Q2 nodes nf_k = 2 n_k + 1, vertices n_k + 1
+struct Q2Grid {
+  int nf[3], nv1[3];
+  long long nq, np;
+};
+
 // Slot layout of the cached rows: nslot = 5^d * d + 3^d.
 inline __host__ __device__ int nslot_u(int dim) { return dim == 3 ? 375 : 50; }
 inline __host__ __device__ int nslot(int dim) { return dim == 3 ? 402 : 59; }
@@ -114,6 +120,17 @@ struct Level {
   int nwork = 0;
   int cls_blk[2] = {-1, -1};            // stored blocks of the patch classes 1 and 2
   unsigned long long active_work = 0;   // active DoFs summed over the stored blocks
+  // Q2-Q1 variant (fc_options.element = 1, see fc_q2.cu): grid sizes, node
+  // masks, stencil blocks, padded residual copies (velocity halo 4 nodes,
+  // pressure halo 1 vertex); the patch rows live in coef, Dirichlet values
+  // in wfix, vectors in x, b, r
+  Q2Grid q2{};
+  unsigned char* q2mask = nullptr;
+  double* q2A = nullptr;
+  double* q2B = nullptr;
+  double* q2T = nullptr;
+  double* q2rpv = nullptr;
+  double* q2rpp = nullptr;
 };
 
 struct Profile {
@@ -184,6 +201,36 @@ void set_capturing(bool on);
 fc_status handle_vcycle_f32(fc_handle h, double* x, const double* b, bool xzero);
 void handle_batch_free(fc_handle h);
 
+// ---- Q2-Q1 variant (fc_q2.cu, fc_patch.cu) ----
+Q2Grid make_q2grid(const LevelGeom& g);
+cudaError_t launch_q2_masks(const LevelGeom& g, const Q2Grid& q, unsigned char* mask, double* wfix, cudaStream_t s);
+// stencil blocks A, B, T from the element data; b (nullable) gets the
+// right-hand side (load, lifted Dirichlet values)
+cudaError_t launch_q2_assemble(const LevelGeom& g, const Q2Grid& q, const double* eA, const double* eB,
+                               const double* eF, const unsigned char* mask, const double* wfix, double* A,
+                               double* B, double* T, double* b, cudaStream_t s);
+// r = b - L x (L x without b) into r and / or the padded copies (nullable)
+cudaError_t launch_q2_residual(int dim, const Q2Grid& q, const double* A, const double* B, const double* T,
+                               const unsigned char* mask, const double* x, const double* b, double* r, double* rpv,
+                               double* rpp, cudaStream_t s);
+cudaError_t launch_q2_prolong_add(int dim, const Q2Grid& f, const Q2Grid& c, const unsigned char* fmask,
+                                  const double* ec, double* xf, cudaStream_t s);
+cudaError_t launch_q2_restrict(int dim, const Q2Grid& f, const Q2Grid& c, const unsigned char* cmask,
+                               const double* rf, double* bc, cudaStream_t s);
+cudaError_t launch_q2_dense(int dim, const Q2Grid& q, const double* A, const double* B, const double* T,
+                            const unsigned char* mask, double* M, cudaStream_t s);
+// patch rows (2D): [vertex][171 slots][10] (9 owned rows, padded)
+size_t q2_patch_rows_doubles(int dim);
+cudaError_t launch_q2_patch_rows(const Q2Grid& q, const double* A, const double* B, const unsigned char* mask,
+                                 double* coef, unsigned* d_err, cudaStream_t s);
+cudaError_t launch_q2_apply(const Q2Grid& q, const double* coef, const unsigned char* mask, const double* rpv,
+                            const double* rpp, double omega, double* x, cudaStream_t s);
+// explicit inverse of a dense n x n matrix (rows in `work`, destroyed) by
+// the equilibrated Gauss-Jordan elimination of the coarse solve (fc_mg.cu);
+// dsc holds 2 n doubles
+cudaError_t launch_dense_inverse(int n, double* work, double* inv, int* piv, double* dsc, unsigned* d_err,
+                                 cudaStream_t s);
+
 // ---- launchers (defined in the .cu files) ----
 // geometry + element data (fc_geom.cu)
 // refA/refB (nullable): reference element matrices of an uncut cell for
@@ -192,6 +239,10 @@ void handle_batch_free(fc_handle h);
 cudaError_t launch_cell_elements(const LevelGeom& g, double* eA, double* eB, double* eF,
                                  double* estat, unsigned* d_err, const double* refA, const double* refB,
                                  unsigned char* cclass, cudaStream_t s);
+// Q2-Q1 element data: eA [cell][3^d][3^d], eB [cell][d][3^d][2^d],
+// eF [cell][d][3^d]; estat as above (nullable)
+cudaError_t launch_cell_elements_q2(const LevelGeom& g, double* eA, double* eB, double* eF, double* estat,
+                                    unsigned* d_err, cudaStream_t s);
 // patch classes: node class from its 2^d cells, patch class from its 5^d
 // nodes (in grid, unconstrained, one class); representatives and the work
 // list of patches to factor; prow maps every patch to its row block

@@ -869,8 +869,13 @@ cudaError_t launch_coarse_factor(const LevelGeom& g, const double* st, const uns
   else coarse_dense_kernel<3><<<blocks, 128, 0, s>>>(g, st, mask, work);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  note_launches(1);
+  return launch_dense_inverse((int)g.ndof, work, inv, piv, dsc, d_err, s);
+}
+
+cudaError_t launch_dense_inverse(int n, double* work, double* inv, int* piv, double* dsc, unsigned* d_err,
+                                 cudaStream_t s) {
   // dsc holds 2 n doubles: the scaling, then the factors of the current column
-  const int n = (int)g.ndof;
   double* col = dsc + n;
   const unsigned gb = (unsigned)std::min(n, 152 * 16);
   gj_scale_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, work, dsc);
@@ -880,7 +885,7 @@ cudaError_t launch_coarse_factor(const LevelGeom& g, const double* st, const uns
     gj_eliminate_kernel<<<gb, 256, 0, s>>>(n, k, work, inv, col);
   }
   gj_finish_kernel<<<gb, 256, 0, s>>>(n, inv, dsc);
-  note_launches(4 + 2 * n);
+  note_launches(3 + 2 * n);
   return cudaGetLastError();
 }
 

@@ -1961,6 +1961,252 @@ cudaError_t run_pair_factor(const LevelGeom& g, const double* st, const unsigned
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Q2-Q1 patches (2D).  Patch of vertex a: the Q2 nodes 2a - 4 .. 2a + 4 per
+// direction (81 nodes, 2 components, node-major) and the pressures of the
+// vertices a - 1 .. a + 1 (9): 171 slots; constrained and out-of-grid DoFs
+// are absent (zero coefficients).  The vertex owns the Q2 nodes 2a + s,
+// s in {0,1}^2, with both components (rows 2 (sx + 2 sy) + c) and its
+// pressure (row 8).  The local solve is exact (Sec. 3.1.2) on the
+// symmetrically scaled block D L_i D, D = (largest entry of the row)^{-1/2}
+// taken per velocity node over both components, by block elimination:
+// K~ = LU (partial pivoting), W~_c = K~^{-1} B~_c, S~ = -sum_c B~_c' W~_c
+// (the pressure block of Q2-Q1 is zero), LU of S~.
+struct Q2P {
+  static constexpr int NV = 81, NP = 9, NSV = 162, NS = 171, NROWP = 10;  // 9 owned rows, padded
+};
+
+__device__ __forceinline__ bool q2_in(const Q2Grid& q, int I, int J) { return I >= 0 && I < q.nf[0] && J >= 0 && J < q.nf[1]; }
+
+__global__ void __launch_bounds__(256)
+    q2_patch_rows_kernel(Q2Grid q, const double* __restrict__ A, const double* __restrict__ B,
+                         const unsigned char* __restrict__ mask, double* __restrict__ coef, unsigned* d_err) {
+  constexpr int NV = Q2P::NV, NP = Q2P::NP;
+  extern __shared__ double q2sm[];
+  double* K = q2sm;                      // NV x NV row-major
+  double* Bs = K + NV * NV;              // [c][NV][NP]
+  double* W = Bs + 2 * NV * NP;          // [c*NP + q][NV] column-major
+  double* S = W + 2 * NP * NV;           // NP x NP
+  double* dv = S + NP * NP;              // NV
+  double* dp = dv + NV;                  // NP
+  double* Y = dp + NP;                   // [4][NV] owned velocity columns of K~^{-1}
+  double* pv = Y + 4 * NV;               // [9][NP] pressure parts of the owned rows
+  int* piv = reinterpret_cast<int*>(pv + 9 * NP);  // NV + NP
+  int* act = piv + NV + NP;                        // NV + NP
+  int* flag = act + NV + NP;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long v = blockIdx.x;
+  const int ax = (int)(v % q.nv1[0]), ay = (int)(v / q.nv1[0]);
+  if (tid == 0) *flag = 0;
+  for (int j = tid; j < NV + NP; j += nt) {
+    if (j < NV) {
+      const int I = 2 * ax - 4 + j % 9, J = 2 * ay - 4 + j / 9;
+      act[j] = q2_in(q, I, J) && !mask[I + (long long)q.nf[0] * J];
+    } else {
+      const int t = j - NV, X = ax - 1 + t % 3, Y2 = ay - 1 + t / 3;
+      act[j] = X >= 0 && X < q.nv1[0] && Y2 >= 0 && Y2 < q.nv1[1];
+    }
+  }
+  __syncthreads();
+  // gather K and B_c
+  for (int t = tid; t < NV * NV; t += nt) {
+    const int r = t / NV, c = t % NV;
+    double val = 0.0;
+    if (act[r] && act[c]) {
+      const int ox = c % 9 - r % 9, oy = c / 9 - r / 9;
+      if (ox >= -2 && ox <= 2 && oy >= -2 && oy <= 2) {
+        const int I = 2 * ax - 4 + r % 9, J = 2 * ay - 4 + r / 9;
+        const long long i = I + (long long)q.nf[0] * J;
+        val = A[(long long)((ox + 2) + 5 * (oy + 2)) * q.nq + i];
+      }
+    } else if (r == c) {
+      val = 1.0;
+    }
+    K[t] = val;
+  }
+  for (int t = tid; t < 2 * NV * NP; t += nt) {
+    const int cc = t / (NV * NP), r = (t / NP) % NV, pq = t % NP;
+    double val = 0.0;
+    if (act[r] && act[NV + pq]) {
+      const int I = 2 * ax - 4 + r % 9, J = 2 * ay - 4 + r / 9;
+      const int X = ax - 1 + pq % 3, Y2 = ay - 1 + pq / 3;
+      const int ox = X - (I / 2 - 1), oy = Y2 - (J / 2 - 1);
+      if (ox >= 0 && ox <= 2 && oy >= 0 && oy <= 2) {
+        const long long i = I + (long long)q.nf[0] * J;
+        val = B[((long long)(ox + 3 * oy) * 2 + cc) * q.nq + i];
+      }
+    }
+    Bs[t] = val;
+  }
+  __syncthreads();
+  // scaling
+  for (int j = tid; j < NV + NP; j += nt) {
+    double m = 0.0;
+    if (j < NV) {
+      for (int c = 0; c < NV; ++c) m = fmax(m, fabs(K[j * NV + c]));
+      for (int cc = 0; cc < 2; ++cc)
+        for (int pq = 0; pq < NP; ++pq) m = fmax(m, fabs(Bs[(cc * NV + j) * NP + pq]));
+      dv[j] = act[j] && m > 0.0 ? 1.0 / sqrt(m) : 1.0;
+    } else {
+      const int pq = j - NV;
+      for (int cc = 0; cc < 2; ++cc)
+        for (int r = 0; r < NV; ++r) m = fmax(m, fabs(Bs[(cc * NV + r) * NP + pq]));
+      dp[pq] = act[j] && m > 0.0 ? 1.0 / sqrt(m) : 1.0;
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < NV * NV; t += nt) K[t] = dv[t / NV] * K[t] * dv[t % NV];
+  for (int t = tid; t < 2 * NV * NP; t += nt) {
+    const int r = (t / NP) % NV, pq = t % NP;
+    Bs[t] = dv[r] * Bs[t] * dp[pq];
+  }
+  __syncthreads();
+  cta_lu(K, NV, NV, piv, flag);
+  // W~_c = K~^{-1} B~_c (columns c*NP + q)
+  for (int t = tid; t < 2 * NP * NV; t += nt) {
+    const int col = t / NV, r = t % NV, cc = col / NP, pq = col % NP;
+    W[t] = Bs[(cc * NV + r) * NP + pq];
+  }
+  __syncthreads();
+  cta_lu_solve_multi(K, NV, piv, W, 2 * NP);
+  // S~ = -sum_c B~_c' W~_c (identity rows for absent pressures)
+  for (int t = tid; t < NP * NP; t += nt) {
+    const int r = t / NP, c = t % NP;
+    double sum = 0.0;
+    if (act[NV + r] && act[NV + c]) {
+      for (int cc = 0; cc < 2; ++cc)
+        for (int p = 0; p < NV; ++p) sum = sum - Bs[(cc * NV + p) * NP + r] * W[(cc * NP + c) * NV + p];
+    } else if (r == c) {
+      sum = 1.0;
+    }
+    S[t] = sum;
+  }
+  // the columns of K~^{-1} at the owned velocity nodes
+  for (int t = tid; t < 4 * NV; t += nt) {
+    const int s2 = t / NV, r = t % NV;
+    const int own = (4 + (s2 & 1)) + 9 * (4 + (s2 >> 1));
+    Y[t] = r == own ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  cta_lu(S, NP, NP, piv + NV, flag);
+  cta_lu_solve_multi(K, NV, piv, Y, 4);
+  // pressure parts: row (s2, c): S~^{-1} (-B~_c' y_s2); pressure row: S~^{-1} e_centre
+  if (tid < 9) {
+    double z[NP];
+    const int k = tid;
+    for (int pq = 0; pq < NP; ++pq) {
+      if (k < 8) {
+        const int s2 = k >> 1, cc = k & 1;
+        double sum = 0.0;
+        for (int p = 0; p < NV; ++p) sum = sum - Bs[(cc * NV + p) * NP + pq] * Y[s2 * NV + p];
+        z[pq] = sum;
+      } else {
+        z[pq] = pq == 4 ? 1.0 : 0.0;
+      }
+    }
+    lu_solve_vec(S, NP, NP, piv + NV, z);
+    for (int pq = 0; pq < NP; ++pq) pv[k * NP + pq] = z[pq];
+  }
+  __syncthreads();
+  // rows: velocity u_c' = delta_cc' y - W~_c' p, de-scaled; absent owned DoFs give zero rows
+  double* out = coef + (size_t)v * Q2P::NS * Q2P::NROWP;
+  for (int t = tid; t < Q2P::NS * Q2P::NROWP; t += nt) {
+    const int slot = t / Q2P::NROWP, k = t % Q2P::NROWP;
+    double val = 0.0;
+    if (k < 9) {
+      int orow;  // local index of the owned DoF of row k
+      if (k < 8) {
+        const int s2 = k >> 1;
+        orow = (4 + (s2 & 1)) + 9 * (4 + (s2 >> 1));
+      } else {
+        orow = NV + 4;
+      }
+      if (act[orow]) {
+        const double dk = k < 8 ? dv[orow] : dp[4];
+        if (slot < Q2P::NSV) {
+          const int p = slot / 2, c2 = slot % 2;
+          if (act[p]) {
+            double u = 0.0;
+            if (k < 8 && c2 == (k & 1)) u = Y[(k >> 1) * NV + p];
+            for (int pq = 0; pq < NP; ++pq) u = u - W[(c2 * NP + pq) * NV + p] * pv[k * NP + pq];
+            val = dk * u * dv[p];
+          }
+        } else {
+          const int pq = slot - Q2P::NSV;
+          if (act[NV + pq]) val = dk * pv[k * NP + pq] * dp[pq];
+        }
+      }
+    }
+    out[t] = val;
+  }
+  if (tid == 0 && *flag) atomicOr(d_err, kErrSingularPatch);
+}
+
+// apply: 8 lanes per patch; y_k = sum_slots rows[slot][k] r[slot]; the
+// restricted update writes the owned DoFs only (x += omega y, constrained
+// velocity DoFs x += r)
+__global__ void __launch_bounds__(256)
+    q2_apply_kernel(Q2Grid q, const double* __restrict__ coef, const unsigned char* __restrict__ mask,
+                    const double* __restrict__ rpv, const double* __restrict__ rpp, double omega,
+                    double* __restrict__ x) {
+  constexpr int TPP = 8;
+  __shared__ int soff[Q2P::NS];
+  const int PX = q.nf[0] + 8, PXP = q.nv1[0] + 2;
+  for (int j = threadIdx.x; j < Q2P::NS; j += blockDim.x) {
+    if (j < Q2P::NSV) {
+      const int p = j / 2, c = j % 2;
+      soff[j] = ((p % 9 - 4) + PX * (p / 9 - 4)) * 2 + c;
+    } else {
+      const int pq = j - Q2P::NSV;
+      soff[j] = (pq % 3 - 1) + PXP * (pq / 3 - 1);
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x % TPP;
+  const long long gi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
+  const bool valid = gi < q.np;
+  const long long v = valid ? gi : q.np - 1;
+  const int ax = (int)(v % q.nv1[0]), ay = (int)(v / q.nv1[0]);
+  const double* rv = rpv + ((long long)(2 * ay + 4) * PX + (2 * ax + 4)) * 2;
+  const double* rp = rpp + (long long)(ay + 1) * PXP + (ax + 1);
+  const double* cf = coef + (size_t)v * Q2P::NS * Q2P::NROWP;
+  double y[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) y[k] = 0.0;
+  for (int j = lane; j < Q2P::NS; j += TPP) {
+    const double r = j < Q2P::NSV ? rv[soff[j]] : rp[soff[j]];
+    const double2* c2 = reinterpret_cast<const double2*>(cf + (size_t)j * Q2P::NROWP);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const double2 a = __ldcs(c2 + h);
+      y[2 * h] += a.x * r;
+      y[2 * h + 1] += a.y * r;
+    }
+    y[8] += __ldcs(cf + (size_t)j * Q2P::NROWP + 8) * r;
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+#pragma unroll
+    for (int o = TPP / 2; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
+  if (!valid) return;
+  for (int k = lane; k < 9; k += TPP) {
+    double yk = y[0];
+#pragma unroll
+    for (int u = 1; u < 9; ++u)
+      if (k == u) yk = y[u];
+    if (k < 8) {
+      const int s2 = k >> 1, c = k & 1;
+      const int I = 2 * ax + (s2 & 1), J = 2 * ay + (s2 >> 1);
+      if (I >= q.nf[0] || J >= q.nf[1]) continue;
+      const long long i = I + (long long)q.nf[0] * J;
+      const double add = mask[i] ? rv[(((s2 & 1)) + PX * (s2 >> 1)) * 2 + c] : omega * yk;
+      x[i * 2 + c] += add;
+    } else {
+      x[q.nq * 2 + v] += omega * yk;
+    }
+  }
+}
+
 }  // namespace
 
 size_t factor_doubles(int dim) { return dim == 3 ? PatchDims<3>::REC : PatchDims<2>::REC; }
@@ -2058,6 +2304,32 @@ cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* 
   if (prec == FC_PREC_FP32) convert_kernel<float><<<blocks, 256, 0, s>>>(n, coef64, (float*)out);
   else if (prec == FC_PREC_BF16) convert_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(n, coef64, (__nv_bfloat16*)out);
   else if (prec == FC_PREC_DF64) convert_kernel<float2><<<blocks, 256, 0, s>>>(n, coef64, (float2*)out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fc
+
+namespace fc {
+
+size_t q2_patch_rows_doubles(int dim) { return dim == 2 ? (size_t)Q2P::NS * Q2P::NROWP : 0; }
+
+cudaError_t launch_q2_patch_rows(const Q2Grid& q, const double* A, const double* B, const unsigned char* mask,
+                                 double* coef, unsigned* d_err, cudaStream_t s) {
+  constexpr int NV = Q2P::NV, NP = Q2P::NP;
+  const size_t smem = sizeof(double) * ((size_t)NV * NV + 2 * NV * NP + 2 * NP * NV + NP * NP + NV + NP + 4 * NV + 9 * NP) +
+                      sizeof(int) * (2 * (NV + NP) + 1);
+  cudaError_t e = cudaFuncSetAttribute(q2_patch_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  q2_patch_rows_kernel<<<(unsigned)q.np, 256, smem, s>>>(q, A, B, mask, coef, d_err);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_q2_apply(const Q2Grid& q, const double* coef, const unsigned char* mask, const double* rpv,
+                            const double* rpp, double omega, double* x, cudaStream_t s) {
+  const long long threads = q.np * 8;
+  q2_apply_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(q, coef, mask, rpv, rpp, omega, x);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -85,7 +85,8 @@ class FcOptions(C.Structure):
                 ("nu_pre", C.c_int), ("nu_post", C.c_int), ("quad_depth", C.c_int),
                 ("cache", C.c_int), ("prec", C.c_int), ("fgmres_restart", C.c_int),
                 ("bc_preset", C.c_int), ("ubar", C.c_double), ("force_kind", C.c_int),
-                ("force", C.c_double * 3), ("dedup", C.c_int), ("tc", C.c_int), ("badcut_frac", C.c_double)]
+                ("force", C.c_double * 3), ("dedup", C.c_int), ("tc", C.c_int), ("badcut_frac", C.c_double),
+                ("element", C.c_int)]
 
 
 _lib = None
@@ -163,8 +164,11 @@ def _grid(prob) -> FcGrid:
 TC = {"none": 0, "tf32": 1, "tf32x3": 2, "bf16": 3}
 
 
+ELEMENT = {"q1": 0, "q2": 1}
+
+
 def _options(prob, cache: str, prec: str, nu=None, dedup: int = 1, tc: str = "none",
-             badcut_frac: float | None = None) -> FcOptions:
+             badcut_frac: float | None = None, element: str = "q1") -> FcOptions:
     o = FcOptions()
     load().fc_options_default(C.byref(o))
     o.eta, o.nitsche_beta, o.omega = prob.eta, prob.beta, prob.omega
@@ -178,6 +182,7 @@ def _options(prob, cache: str, prec: str, nu=None, dedup: int = 1, tc: str = "no
         o.force[k] = float(prob.force[k])
     o.dedup = int(dedup)
     o.tc = TC[tc]
+    o.element = ELEMENT[element]
     if badcut_frac is not None:
         o.badcut_frac = float(badcut_frac)
     return o
@@ -208,7 +213,7 @@ class Solver:
     """A finite cell Stokes problem set up on the GPU (one fc_handle)."""
 
     def __init__(self, prob, cache: str = "inverse", prec: str = "fp64", stream=None, nu=None,
-                 dedup: int = 1, tc: str = "none", badcut_frac: float | None = None):
+                 dedup: int = 1, tc: str = "none", badcut_frac: float | None = None, element: str = "q1"):
         import torch
         if not torch.cuda.is_available():
             raise FcError(-1, "libfc needs a CUDA GPU")
@@ -218,7 +223,7 @@ class Solver:
         self.dim = prob.dim
         self.nd = prob.dim + 1
         self.nlevels = prob.nlevels
-        self.cache, self.prec = cache, prec
+        self.cache, self.prec, self.element = cache, prec, element
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.device = torch.cuda.current_device()
         self._sizes = {}
@@ -235,7 +240,7 @@ class Solver:
         self.h = C.c_void_p()
         st = self.lib.fc_setup(C.byref(self.h), C.byref(_grid(prob)), C.byref(ls), float(prob.alpha),
                                int(prob.nlevels),
-                               C.byref(_options(prob, cache, prec, nu, dedup, tc, badcut_frac)),
+                               C.byref(_options(prob, cache, prec, nu, dedup, tc, badcut_frac, element)),
                                C.c_void_p(self.stream.cuda_stream))
         self._check(st)
 
@@ -399,8 +404,11 @@ class Solver:
 
     def patch_rows(self, node: int, level=None):
         lv = self.nlevels if level is None else level
-        ns = 402 if self.dim == 3 else 59
-        out = np.zeros((self.nd, ns))
+        if self.element == "q2":
+            out = np.zeros((9, 171))      # 2D Q2-Q1: owned rows x slots
+        else:
+            ns = 402 if self.dim == 3 else 59
+            out = np.zeros((self.nd, ns))
         self._check(self.lib.fc_patch_rows(self.h, lv, int(node),
                                            out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
