@@ -718,19 +718,30 @@ def run_replay(args):
 
 
 def run_q2(args):
-    """The Q2-Q1 (Taylor-Hood) variant with the lower-corner ownership rule:
-    the 2D channel (unit square, one circle r = 0.2, parabolic inflow,
-    alpha 1e-8, quadtree depth 4) on an n x n grid, levels down to 16 x 16
-    cells, V(2,2), FP64 rows, FGMRES to 1e-8.  Reports solves/s and owned-
-    DoF updates/s over the timed solves, and the finest-level patch apply
-    timed alone with its algorithmic FLOP (171 slots x 9 owned rows x 2 per
+    """The Q2-Q1 (Taylor-Hood) variant with the lower-corner ownership rule.
+    2D (--q2-dim 2): the 2D channel (unit square, one circle r = 0.2,
+    parabolic inflow, alpha 1e-8, quadtree depth 4) on an n x n grid, levels
+    down to 16 x 16 cells.  3D (--q2-dim 3): the porous medium of the default
+    line (40 spheres, alpha 1e-8, octree depth 3) on an n^3 grid, levels down
+    to 4^3 cells.  V(2,2), FP64 rows, FGMRES to 1e-8.  Reports solves/s and
+    owned-DoF updates/s over the timed solves, and the finest-level patch
+    apply timed alone with its algorithmic FLOP (slots x owned rows x 2 per
     patch, upper bound) and bytes."""
     import torch
     from paper_2403_11636_gb300 import build, fc, inputs
     build.build()
-    n = args.q2_n
-    nlev = max(2, int(math.log2(n // 16)) + 1)
-    prob = inputs.channel_2d(0, n=n, nlevels=nlev)
+    dim = args.q2_dim
+    n = args.q2_n if dim == 2 else args.q2_n3
+    if dim == 2:
+        nlev = max(2, int(math.log2(n // 16)) + 1)
+        prob = inputs.channel_2d(0, n=n, nlevels=nlev)
+        workload = f"Q2-Q1 channel2d {n}^2, one circle r 0.2, alpha 1e-8, quadtree depth 4, {nlev} levels"
+        nslot, nrow = 171, 9
+    else:
+        nlev = max(2, int(math.log2(n // 4)) + 1)
+        prob = inputs.porous_3d(0, n=n, nspheres=40, nlevels=nlev)
+        workload = f"Q2-Q1 porous3d {n}^3, 40 spheres, alpha 1e-8, octree depth 3, {nlev} levels"
+        nslot, nrow = 2214, 25
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
@@ -750,19 +761,20 @@ def run_q2(args):
         s.profile(False)
         ndof = s.ndof()
         s.close()
-    nv1 = (n + 1) ** 2
-    nq = (2 * n + 1) ** 2
-    upd = (nq * 2 + nv1)                      # owned DoFs of the finest level (each written once per sweep)
-    per_solve = sum(((2 * (n >> k) + 1) ** 2 * 2 + ((n >> k) + 1) ** 2) for k in range(nlev - 1)) * 4
+
+    def owned(m):                              # DoFs of a level with m cells per direction
+        return (2 * m + 1) ** dim * dim + (m + 1) ** dim
+    nv1 = (n + 1) ** dim
+    upd = owned(n)                             # owned DoFs of the finest level (each written once per sweep)
+    per_solve = sum(owned(n >> k) for k in range(nlev - 1)) * 4
     avg = ma / max(na, 1)
-    flop = nv1 * 171 * 9 * 2.0
+    flop = nv1 * nslot * nrow * 2.0
     tf, note = fp64_peak(torch)
     hbm, _ = peaks()
     emit({"mode": "q2", "metric": "smoother patch-DoF updates/s", "unit": "owned-DoF updates/s", "dtype": "f64",
           "data": "synthetic",
           "value": sum(its_l) * per_solve / (total_ms * 1e-3),
-          "config": {"workload": f"Q2-Q1 channel2d {n}^2, one circle r 0.2, alpha 1e-8, quadtree depth 4, "
-                                 f"{nlev} levels, V(2,2), FGMRES(30) rtol 1e-8, FP64 rows", "ndof": ndof,
+          "config": {"workload": workload + ", V(2,2), FGMRES(30) rtol 1e-8, FP64 rows", "dim": dim, "ndof": ndof,
                      "iterations": its_l[0], "relres": max(rr_l), "setup_ms": setup_ms,
                      "solves_per_s": args.steps / (total_ms * 1e-3), "ms_per_solve": total_ms / args.steps,
                      "finest_owned_dofs": upd},
@@ -1027,7 +1039,9 @@ def main():
                     help="profiled solves after the timed ones (per-kernel CUDA events)")
     ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep", "mixed", "replay", "q2"])
     ap.add_argument("--mixed-n", type=int, default=128, help="grid of --mode mixed")
-    ap.add_argument("--q2-n", type=int, default=512, help="grid of --mode q2")
+    ap.add_argument("--q2-n", type=int, default=512, help="grid of --mode q2 in 2D")
+    ap.add_argument("--q2-n3", type=int, default=16, help="grid of --mode q2 in 3D")
+    ap.add_argument("--q2-dim", type=int, default=2, choices=[2, 3], help="dimension of --mode q2")
     ap.add_argument("--replay-sizes", type=int, default=4,
                     help="--mode replay: 1024x256 and this many - 1 uniform refinements")
     ap.add_argument("--batch-workload", default="batch2d", choices=["batch2d", "porous3d"],

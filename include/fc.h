@@ -126,8 +126,8 @@ typedef struct {
                           badcut_frac gets its rows from the float-pair (FP64-class)
                           factorisation instead of float32 factors with refinement; 0 off. */
   int element;         /* 0: equal-order Q1-Q1 with the local L2 pressure projection (the
-                          paper's pair, Sec. 2); 1: Q2-Q1 Taylor-Hood (2D, cache_inverse, FP64
-                          rows): Q2 velocities on the half-spaced grid of 2 n_k + 1 nodes per
+                          paper's pair, Sec. 2); 1: Q2-Q1 Taylor-Hood (cache_inverse, FP64
+                          rows; 2D and 3D): Q2 velocities on the half-spaced grid of 2 n_k + 1 nodes per
                           direction, no stabilisation; patch of pressure vertex a = the Q2
                           nodes 2a-4 .. 2a+4 and the pressures a-1 .. a+1; each Q2 node is
                           written by the vertex at the lower corner of its cell, edge or face
@@ -251,10 +251,11 @@ fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch,
  * inverse only): rows[(d+1)][nslot] in float64 whatever the storage
  * precision, nslot = 5^d d + 3^d; slot order: velocity nodes of the 5^d box
  * around the node (x fastest) with the component inner, then the pressure
- * nodes of the 3^d box; absent DoFs have zero coefficients.  Q2-Q1 (2D):
- * rows[9][171], rows 2 (sx + 2 sy) + c for the owned Q2 nodes 2a + s and
- * row 8 for the pressure; slots: the Q2 nodes 2a-4 .. 2a+4 (x fastest,
- * component inner), then the vertices a-1 .. a+1.  Synchronises. */
+ * nodes of the 3^d box; absent DoFs have zero coefficients.  Q2-Q1:
+ * rows[9][171] (2D) or rows[25][2214] (3D), row d (sx + 2 sy + 4 sz) + c for
+ * the owned Q2 nodes 2a + s and the last row for the pressure; slots: the
+ * Q2 nodes 2a-4 .. 2a+4 (x fastest, component inner), then the vertices
+ * a-1 .. a+1.  Synchronises. */
 fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_host);
 
 /* Upper bound of the device bytes a handle for this problem holds at the

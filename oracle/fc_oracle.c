@@ -1239,6 +1239,67 @@ void or_restrict(const or_level* F, const or_level* Cc, const double* rf, double
     if (Cc->fixed[k]) bc[k] = 0.0;
 }
 
+/* Galerkin coarse operator, the alternative to rediscretising the coarser
+ * grids of the hierarchy (Sec. 3): L_c = R L_f P with the transfers above.
+ * For free coarse DoFs (I,c) and (J,e):
+ *   L_c[(I,c),(J,e)] = sum over free fine DoFs (i,c), (j,e) of
+ *                      P[(i,c),(I,c)] L_f[(i,c),(j,e)] P[(j,e),(J,e)],
+ * P[(i,c),(I,c)] = prod_k w(i_k - 2 I_k), w(0) = 1, w(+-1) = 1/2, else 0
+ * (the Q1 interpolation of or_prolong_add; constrained fine DoFs have zero
+ * rows of P).  Constrained coarse DoFs keep identity rows and zero columns,
+ * as in the rediscretised operator.  Both levels must be assembled; the
+ * values of C's operator are replaced (same structure), its right-hand side
+ * is left alone (only the finest one is used). */
+static double q1_weight(long d) { return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0); }
+
+void or_galerkin(or_level* Cc, const or_level* F) {
+  int dim = F->dim, nd = F->ndpn;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long row = 0; row < Cc->ndof; ++row) {
+    long I = row / nd;
+    int c = (int)(row % nd);
+    long b = Cc->rowptr[row], e = Cc->rowptr[row + 1];
+    for (long q = b; q < e; ++q) Cc->val[q] = (Cc->fixed[row] && Cc->col[q] == row) ? 1.0 : 0.0;
+    if (Cc->fixed[row]) continue;
+    long ia[3] = {0, 0, 0};
+    node_idx(Cc, I, ia);
+    /* fine nodes 2I + s, s in {-1, 0, 1}^d */
+    for (int t = 0; t < (dim == 3 ? 27 : 9); ++t) {
+      long fi[3] = {0, 0, 0};
+      int tt = t, inside = 1;
+      double wi = 1.0;
+      for (int k = 0; k < dim; ++k) {
+        long s = (tt % 3) - 1;
+        tt /= 3;
+        fi[k] = 2 * ia[k] + s;
+        if (fi[k] < 0 || fi[k] > F->n[k]) inside = 0;
+        wi = wi * q1_weight(s);
+      }
+      if (!inside) continue;
+      long frow = node_of(F, fi[0], fi[1], fi[2]) * nd + c;
+      if (F->fixed[frow]) continue;
+      for (long p = F->rowptr[frow]; p < F->rowptr[frow + 1]; ++p) {
+        long fcol = F->col[p];
+        if (F->fixed[fcol]) continue;
+        long j = fcol / nd;
+        int ec = (int)(fcol % nd);
+        long ja[3] = {0, 0, 0};
+        node_idx(F, j, ja);
+        /* coarse nodes J that fine node j interpolates from */
+        for (long q = b; q < e; ++q) {
+          long ccol = Cc->col[q];
+          if ((int)(ccol % nd) != ec || Cc->fixed[ccol]) continue;
+          long Ja[3] = {0, 0, 0};
+          node_idx(Cc, ccol / nd, Ja);
+          double wj = 1.0;
+          for (int k = 0; k < dim; ++k) wj = wj * q1_weight(ja[k] - 2 * Ja[k]);
+          if (wj != 0.0) Cc->val[q] = Cc->val[q] + wi * F->val[p] * wj;
+        }
+      }
+    }
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Multigrid hierarchy, V-cycle and FGMRES                                   */
 /* ------------------------------------------------------------------------ */

@@ -98,6 +98,7 @@ def _load():
     lib.or_owner_count.argtypes = [vp, P(C.c_int)]
     lib.or_prolong_add.argtypes = [vp, vp, P(d), P(d)]
     lib.or_restrict.argtypes = [vp, vp, P(d), P(d)]
+    lib.or_galerkin.argtypes = [vp, vp]
     lib.or_mg_new.restype = vp
     lib.or_mg_new.argtypes = [i, P(vp), i, i, i]
     lib.or_mg_free.argtypes = [vp]
@@ -311,10 +312,17 @@ def restrict(fine: Level, coarse: Level, rf):
 class MG:
     """Multigrid hierarchy of a problem: levels[0] coarsest .. levels[-1] finest."""
 
-    def __init__(self, prob=None, levels=None, nu_pre=None, nu_post=None, mode: int = 0):
+    def __init__(self, prob=None, levels=None, nu_pre=None, nu_post=None, mode: int = 0,
+                 galerkin: bool = False):
         if levels is None:
             levels = [Level.from_problem(prob, l) for l in range(1, prob.nlevels + 1)]
         self.levels = levels
+        if galerkin:
+            # coarse operators R L_f P from the finest level down (or_galerkin)
+            for lv in levels:
+                lv.assemble()
+            for l in range(len(levels) - 2, -1, -1):
+                levels[l].lib.or_galerkin(levels[l].h, levels[l + 1].h)
         self.nu_pre = prob.nu_pre if nu_pre is None and prob is not None else (nu_pre or 0)
         self.nu_post = prob.nu_post if nu_post is None and prob is not None else (nu_post or 0)
         arr = (C.c_void_p * len(levels))(*[lv.h for lv in levels])

@@ -346,7 +346,8 @@ fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nswe
       }
       ProfScope ps(h, 0, (double)L.coef_bytes);
       ProfScope pf(h, li == h->nlev - 1 ? 4 : -1, (double)L.coef_bytes);
-      CK(launch_q2_apply(L.q2, (const double*)L.coef, L.q2mask, L.q2rpv, L.q2rpp, h->opt.omega, x, h->stream));
+      CK(launch_q2_apply(h->dim, L.q2, (const double*)L.coef, L.q2mask, L.q2rpv, L.q2rpp, h->opt.omega, x,
+                         h->stream));
     }
     return FC_OK;
   }
@@ -570,13 +571,17 @@ fc_status setup_q2(fc_handle h, const fc_grid* g, const fc_options* o, int nshap
       const size_t n = (size_t)q.np * q2_patch_rows_doubles(dim);
       double* c64 = nullptr;
       CK(dalloc(h, &c64, n, 1));
+      const int ctas = q2_patch_rows_ctas(dim, q.np);
+      double* work = nullptr;
+      if (ctas > 0) CK(dalloc(h, &work, q2_patch_rows_work_doubles(dim, ctas), -1));
       {
         ProfScope ps(h, 3, 0.0);
-        CK(launch_q2_patch_rows(q, L.q2A, L.q2B, L.q2mask, c64, h->d_err, h->stream));
+        CK(launch_q2_patch_rows(dim, q, L.q2A, L.q2B, L.q2mask, c64, work, ctas, h->d_err, h->stream));
       }
       L.coef = c64;
       L.coef_bytes = n * 8;
       CK(cudaStreamSynchronize(h->stream));
+      dfree(h, work);
       st = check_err(h);
       if (st != FC_OK) return st;
     }
@@ -663,6 +668,7 @@ size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o) {
     }
     held += coarse * coarse * 8;
     transient = std::max(transient, coarse * coarse * 8 + coarse * 24);
+    transient = std::max(transient, q2_patch_rows_work_doubles(dim, kQ2Rows3MaxCtas) * 8);
     const int m = o->fgmres_restart > 0 ? o->fgmres_restart : 30;
     held += fine * 8 * (2 * (size_t)m + 4) + 2048 * 8 + (size_t)small_len(m) * 8;
     const size_t total = held + transient;
@@ -752,8 +758,8 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   if (o->prec != FC_PREC_FP64 && o->cache != FC_CACHE_INVERSE)
     return fail(h, FC_ERR_INVALID, "reduced-precision storage applies to cache_inverse only");
   if (o->element != 0 && o->element != 1) return fail(h, FC_ERR_INVALID, "invalid element pair");
-  if (o->element == 1 && (g->dim != 2 || o->cache != FC_CACHE_INVERSE || o->prec != FC_PREC_FP64))
-    return fail(h, FC_ERR_INVALID, "the Q2-Q1 pair runs in 2D with cache_inverse and FP64 rows");
+  if (o->element == 1 && (o->cache != FC_CACHE_INVERSE || o->prec != FC_PREC_FP64))
+    return fail(h, FC_ERR_INVALID, "the Q2-Q1 pair runs with cache_inverse and FP64 rows");
   {
     long long nodes = 1;
     for (int k = 0; k < g->dim; ++k) nodes *= (long long)g->n[k] + 1;
@@ -1271,14 +1277,17 @@ fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_hos
   if (!rows_host || node < 0 || node >= L.g.nnodes) return fail(h, FC_ERR_INVALID, "bad patch");
   if (h->opt.cache != FC_CACHE_INVERSE || !L.coef) return fail(h, FC_ERR_INVALID, "no cached rows");
   if (q2_path(h)) {
-    // 9 owned rows x 171 slots, stored [slot][10]
-    const int NS = 171, NRP = 10;
-    std::vector<double> raw((size_t)NS * NRP);
-    CK(cudaMemcpyAsync(raw.data(), (const double*)L.coef + (size_t)node * NS * NRP, sizeof(double) * raw.size(),
+    // 2D: 9 owned rows x 171 slots, stored [slot][10]; 3D: 25 x 2214, stored [row][2240]
+    const bool d3 = h->dim == 3;
+    const int NS = d3 ? 2214 : 171, NR = d3 ? 25 : 9;
+    const size_t per = q2_patch_rows_doubles(h->dim);
+    std::vector<double> raw(per);
+    CK(cudaMemcpyAsync(raw.data(), (const double*)L.coef + (size_t)node * per, sizeof(double) * per,
                        cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    for (int k = 0; k < 9; ++k)
-      for (int j = 0; j < NS; ++j) rows_host[(size_t)k * NS + j] = raw[(size_t)j * NRP + k];
+    for (int k = 0; k < NR; ++k)
+      for (int j = 0; j < NS; ++j)
+        rows_host[(size_t)k * NS + j] = d3 ? raw[(size_t)k * 2240 + j] : raw[(size_t)j * 10 + k];
     return FC_OK;
   }
   const int ns = nslot(h->dim), nd = h->dim + 1;

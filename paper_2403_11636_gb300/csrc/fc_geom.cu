@@ -381,21 +381,22 @@ __global__ void __launch_bounds__(Entries<DIM, Q>::WARPS * 32)
     bool cut = (npos != 0 && npos != NS);
     if (cut && level < g.qdepth) {
       split = true;
-      // push children in reverse so that child 0 is processed first
+      // push the 2^d children in reverse so that child 0 is processed first
+      constexpr int NCH = 1 << DIM;
       if (lane == 0) {
-        for (int ch = NL - 1; ch >= 0; --ch) {
+        for (int ch = NCH - 1; ch >= 0; --ch) {
           double lc[3] = {lo[0], lo[1], lo[2]};
           for (int k = 0; k < DIM; ++k)
             if ((ch >> k) & 1) lc[k] = lo[k] + hb[k] * 0.5;
-          if (sp + (NL - 1 - ch) < kStack) {
-            S.stk_lo[sp + (NL - 1 - ch)][0] = lc[0];
-            S.stk_lo[sp + (NL - 1 - ch)][1] = lc[1];
-            S.stk_lo[sp + (NL - 1 - ch)][2] = lc[2];
-            S.stk_lev[sp + (NL - 1 - ch)] = level + 1;
+          if (sp + (NCH - 1 - ch) < kStack) {
+            S.stk_lo[sp + (NCH - 1 - ch)][0] = lc[0];
+            S.stk_lo[sp + (NCH - 1 - ch)][1] = lc[1];
+            S.stk_lo[sp + (NCH - 1 - ch)][2] = lc[2];
+            S.stk_lev[sp + (NCH - 1 - ch)] = level + 1;
           }
         }
       }
-      sp += NL;
+      sp += NCH;
       if (sp > kStack) {
         if (lane == 0) atomicOr(d_err, kErrBadIndex);
         sp = 0;

@@ -219,11 +219,17 @@ cudaError_t launch_q2_restrict(int dim, const Q2Grid& f, const Q2Grid& c, const 
                                const double* rf, double* bc, cudaStream_t s);
 cudaError_t launch_q2_dense(int dim, const Q2Grid& q, const double* A, const double* B, const double* T,
                             const unsigned char* mask, double* M, cudaStream_t s);
-// patch rows (2D): [vertex][171 slots][10] (9 owned rows, padded)
+// patch rows: 2D [vertex][171 slots][10] (9 owned rows, padded); 3D
+// [vertex][25 rows][2240] (2214 slots, padded).  The 3D factorisation takes
+// a global workspace of q2_patch_rows_work_doubles(3, ctas) for `ctas`
+// persistent CTAs (q2_patch_rows_ctas: one per SM, at most kQ2Rows3MaxCtas).
+constexpr int kQ2Rows3MaxCtas = 256;
 size_t q2_patch_rows_doubles(int dim);
-cudaError_t launch_q2_patch_rows(const Q2Grid& q, const double* A, const double* B, const unsigned char* mask,
-                                 double* coef, unsigned* d_err, cudaStream_t s);
-cudaError_t launch_q2_apply(const Q2Grid& q, const double* coef, const unsigned char* mask, const double* rpv,
+size_t q2_patch_rows_work_doubles(int dim, long long ctas);
+int q2_patch_rows_ctas(int dim, long long np);
+cudaError_t launch_q2_patch_rows(int dim, const Q2Grid& q, const double* A, const double* B, const unsigned char* mask,
+                                 double* coef, double* work, int ctas, unsigned* d_err, cudaStream_t s);
+cudaError_t launch_q2_apply(int dim, const Q2Grid& q, const double* coef, const unsigned char* mask, const double* rpv,
                             const double* rpp, double omega, double* x, cudaStream_t s);
 // explicit inverse of a dense n x n matrix (rows in `work`, destroyed) by
 // the equilibrated Gauss-Jordan elimination of the coarse solve (fc_mg.cu);

@@ -2207,6 +2207,359 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---- Q2-Q1 patches in 3D: the Q2 nodes 2a-4 .. 2a+4 (9^3 = 729) with 3
+// components, then the 27 pressures a-1 .. a+1; 25 owned rows (the 8 Q2
+// nodes 2a + s, s in {0,1}^3 with s_x fastest, component inner; then p_a).
+// Rows are stored [row][slot] with the slots padded to 2240.
+struct Q2P3 {
+  static constexpr int NV = 729, NP = 27, NSV = 2187, NS = 2214, NROW = 25, SP = 2240;
+  // K couples Q2 nodes at most 2 apart per direction: in node-lexicographic
+  // order (x fastest) that is a half bandwidth of 2 + 2*9 + 2*81
+  static constexpr int KL = 182;
+  // band row of the LU with row exchanges: KL below, 2 KL above (the fill a
+  // row exchange can bring), the diagonal
+  static constexpr int BW = 3 * KL + 1;
+  static constexpr int NRHS = 3 * NP + 8;  // W~_c columns, then the 8 owned unit vectors
+  static constexpr size_t WS = ((size_t)NV * BW + (size_t)NV * NRHS + (size_t)3 * NP * NV + 31) / 32 * 32;
+};
+
+__device__ __forceinline__ int q2p3_own(int s) { return (4 + (s & 1)) + 9 * (4 + ((s >> 1) & 1)) + 81 * (4 + (s >> 2)); }
+
+// Owned rows of the equilibrated local inverse by block elimination, as in
+// two dimensions, with K~ (729 x 729) factored by a banded LU with partial
+// pivoting in global memory (one workspace per CTA, L2 resident):
+//   K~ W~ = B~ (81 columns) and K~ Y = e_own (8 columns), solved together;
+//   S~ = -sum_c B~_c' W~_c; pressure parts z = S~^{-1}(-B~_c' y) or
+//   S~^{-1} e_centre; velocity parts delta y - W~ z; de-scaled.
+// The RHS solves give each warp its own columns, so they need no CTA
+// barrier; the LU takes three barriers per pivot step (four with a row
+// exchange).  Persistent: CTA b takes vertices b, b + grid, ...
+__global__ void __launch_bounds__(512)
+    q2_patch_rows3_kernel(Q2Grid q, const double* __restrict__ A, const double* __restrict__ B,
+                          const unsigned char* __restrict__ mask, double* __restrict__ coef,
+                          double* __restrict__ work, unsigned* d_err) {
+  using P = Q2P3;
+  constexpr int NV = P::NV, NP = P::NP, KL = P::KL, BW = P::BW, NR = P::NRHS;
+  __shared__ int act[NV + NP];
+  __shared__ int rend[NV];    // last column of the nonzeros of row r (grows with fill)
+  __shared__ int cstart[NV];  // first row with a nonzero of U in column k
+  __shared__ int piv[NV];
+  __shared__ double dv[NV], dp[NP];
+  __shared__ double S[NP * NP];
+  __shared__ int pivS[NP];
+  __shared__ double pv[P::NROW * NP];
+  __shared__ double lcol[KL];     // multipliers of the current pivot step
+  __shared__ double urow[2 * KL];  // pivot row right of the diagonal
+  __shared__ int s_cmax, flag;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nt >> 5;
+  double* Bd = work + (size_t)blockIdx.x * P::WS;  // [row][BW]: column c of row r at c - r + KL
+  double* X = Bd + (size_t)NV * BW;                 // [rhs][NV]
+  double* Bs = X + (size_t)NR * NV;                 // [c][pq][NV]
+  for (long long v = blockIdx.x; v < q.np; v += gridDim.x) {
+    const int ax = (int)(v % q.nv1[0]), ay = (int)((v / q.nv1[0]) % q.nv1[1]),
+              az = (int)(v / ((long long)q.nv1[0] * q.nv1[1]));
+    if (tid == 0) flag = 0;
+    for (int j = tid; j < NV + NP; j += nt) {
+      if (j < NV) {
+        const int I = 2 * ax - 4 + j % 9, J = 2 * ay - 4 + (j / 9) % 9, K = 2 * az - 4 + j / 81;
+        const bool in = I >= 0 && I < q.nf[0] && J >= 0 && J < q.nf[1] && K >= 0 && K < q.nf[2];
+        act[j] = in && !mask[I + (long long)q.nf[0] * (J + (long long)q.nf[1] * K)];
+        rend[j] = min(j + KL, NV - 1);
+      } else {
+        const int t = j - NV, X0 = ax - 1 + t % 3, Y0 = ay - 1 + (t / 3) % 3, Z0 = az - 1 + t / 9;
+        act[j] = X0 >= 0 && X0 < q.nv1[0] && Y0 >= 0 && Y0 < q.nv1[1] && Z0 >= 0 && Z0 < q.nv1[2];
+      }
+    }
+    __syncthreads();
+    // gather the band of K (identity rows for absent nodes) and B_c
+    for (int t = tid; t < NV * BW; t += nt) {
+      const int r = t / BW, c = r - KL + t % BW;
+      double val = 0.0;
+      if (c >= 0 && c < NV) {
+        if (act[r] && act[c]) {
+          const int ox = c % 9 - r % 9, oy = (c / 9) % 9 - (r / 9) % 9, oz = c / 81 - r / 81;
+          if (ox >= -2 && ox <= 2 && oy >= -2 && oy <= 2 && oz >= -2 && oz <= 2) {
+            const int I = 2 * ax - 4 + r % 9, J = 2 * ay - 4 + (r / 9) % 9, K = 2 * az - 4 + r / 81;
+            const long long i = I + (long long)q.nf[0] * (J + (long long)q.nf[1] * K);
+            val = A[(long long)((ox + 2) + 5 * (oy + 2) + 25 * (oz + 2)) * q.nq + i];
+          }
+        } else if (r == c) {
+          val = 1.0;
+        }
+      }
+      Bd[t] = val;
+    }
+    for (int t = tid; t < 3 * NP * NV; t += nt) {
+      const int cc = t / (NP * NV), pq = (t / NV) % NP, r = t % NV;
+      double val = 0.0;
+      if (act[r] && act[NV + pq]) {
+        const int I = 2 * ax - 4 + r % 9, J = 2 * ay - 4 + (r / 9) % 9, K = 2 * az - 4 + r / 81;
+        const int ox = ax - 1 + pq % 3 - (I / 2 - 1), oy = ay - 1 + (pq / 3) % 3 - (J / 2 - 1),
+                  oz = az - 1 + pq / 9 - (K / 2 - 1);
+        if (ox >= 0 && ox <= 2 && oy >= 0 && oy <= 2 && oz >= 0 && oz <= 2) {
+          const long long i = I + (long long)q.nf[0] * (J + (long long)q.nf[1] * K);
+          val = B[((long long)(ox + 3 * oy + 9 * oz) * 3 + cc) * q.nq + i];
+        }
+      }
+      Bs[t] = val;
+    }
+    __syncthreads();
+    // row-max equilibration: one scale per velocity node (K is shared by the
+    // components), one per pressure
+    for (int j = tid; j < NV + NP; j += nt) {
+      double m = 0.0;
+      if (j < NV) {
+        for (int o = 0; o < BW; ++o) m = fmax(m, fabs(Bd[(size_t)j * BW + o]));
+        for (int t = 0; t < 3 * NP; ++t) m = fmax(m, fabs(Bs[(size_t)t * NV + j]));
+        dv[j] = act[j] && m > 0.0 ? 1.0 / sqrt(m) : 1.0;
+      } else {
+        const int pq = j - NV;
+        for (int cc = 0; cc < 3; ++cc)
+          for (int r = 0; r < NV; ++r) m = fmax(m, fabs(Bs[((size_t)cc * NP + pq) * NV + r]));
+        dp[pq] = act[j] && m > 0.0 ? 1.0 / sqrt(m) : 1.0;
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < NV * BW; t += nt) {
+      const int r = t / BW, c = r - KL + t % BW;
+      if (c >= 0 && c < NV) Bd[t] = dv[r] * Bd[t] * dv[c];
+    }
+    for (int t = tid; t < NR * NV; t += nt) {
+      const int m = t / NV, r = t % NV;
+      if (m < 3 * NP) {
+        const double s = dv[r] * Bs[t] * dp[m % NP];
+        Bs[t] = s;
+        X[t] = s;
+      } else {
+        X[t] = r == q2p3_own(m - 3 * NP) ? 1.0 : 0.0;
+      }
+    }
+    __syncthreads();
+    // banded LU with partial pivoting (max |a|, lowest row on ties)
+    for (int k = 0; k < NV; ++k) {
+      const int rlast = min(k + KL, NV - 1);
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = k;
+        for (int r = k + lane; r <= rlast; r += 32) {
+          const double a = fabs(Bd[(size_t)r * BW + (k - r + KL)]);
+          if (a > best) { best = a; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) {
+          piv[k] = bi;
+          if (!(best > 0.0)) flag = 1;
+          s_cmax = max(rend[k], rend[bi]);
+          const int t = rend[k];
+          rend[k] = rend[bi];
+          rend[bi] = t;
+        }
+      }
+      __syncthreads();
+      const int p = piv[k];
+      if (p != k) {
+        const int cmax = s_cmax;
+        for (int c = k + tid; c <= cmax; c += nt) {
+          double* a = Bd + (size_t)k * BW + (c - k + KL);
+          double* b = Bd + (size_t)p * BW + (c - p + KL);
+          const double t = *a;
+          *a = *b;
+          *b = t;
+        }
+        __syncthreads();
+      }
+      const double d = Bd[(size_t)k * BW + KL];
+      const int nr = rlast - k, ncol = rend[k] - k;
+      for (int t = tid; t < nr + ncol; t += nt) {
+        if (t < nr) {
+          const int i = k + 1 + t;
+          double* a = Bd + (size_t)i * BW + (k - i + KL);
+          const double l = d != 0.0 ? *a / d : 0.0;
+          *a = l;
+          lcol[t] = l;
+          if (l != 0.0) rend[i] = max(rend[i], rend[k]);
+        } else {
+          const int c = k + 1 + (t - nr);
+          urow[t - nr] = Bd[(size_t)k * BW + (c - k + KL)];
+        }
+      }
+      __syncthreads();
+      for (int t = tid; t < nr * ncol; t += nt) {
+        const int ii = t / ncol, cc = t % ncol;
+        const double l = lcol[ii];
+        if (l != 0.0) {
+          const int i = k + 1 + ii, c = k + 1 + cc;
+          double* a = Bd + (size_t)i * BW + (c - i + KL);
+          *a = *a - l * urow[cc];
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      // first row with a nonzero of U in column k (non-decreasing in k)
+      int i = 0;
+      for (int k = 0; k < NV; ++k) {
+        while (rend[i] < k) ++i;
+        cstart[k] = i;
+      }
+    }
+    __syncthreads();
+    // solves: warp w takes the columns w, w + nwarp, ...; forward with the
+    // row exchanges in pivot order, then backward with U
+    for (int m = warp; m < NR; m += nwarp) {
+      double* xm = X + (size_t)m * NV;
+      for (int k = 0; k < NV; ++k) {
+        const int p = piv[k];
+        if (p != k && lane == 0) {
+          const double t = xm[k];
+          xm[k] = xm[p];
+          xm[p] = t;
+        }
+        __syncwarp();
+        const double xk = xm[k];
+        const int rlast = min(k + KL, NV - 1);
+        for (int i = k + 1 + lane; i <= rlast; i += 32) xm[i] = xm[i] - Bd[(size_t)i * BW + (k - i + KL)] * xk;
+        __syncwarp();
+      }
+      for (int k = NV - 1; k >= 0; --k) {
+        const double xk = xm[k] / Bd[(size_t)k * BW + KL];
+        __syncwarp();
+        if (lane == 0) xm[k] = xk;
+        for (int i = cstart[k] + lane; i < k; i += 32) xm[i] = xm[i] - Bd[(size_t)i * BW + (k - i + KL)] * xk;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // S~ = -sum_c B~_c' W~_c (identity rows and columns for absent pressures)
+    for (int t = tid; t < NP * NP; t += nt) {
+      const int r = t / NP, c = t % NP;
+      double sum = 0.0;
+      if (act[NV + r] && act[NV + c]) {
+        for (int cc = 0; cc < 3; ++cc) {
+          const double* bp = Bs + ((size_t)cc * NP + r) * NV;
+          const double* wp = X + ((size_t)cc * NP + c) * NV;
+          for (int j = 0; j < NV; ++j) sum = sum - bp[j] * wp[j];
+        }
+      } else if (r == c) {
+        sum = 1.0;
+      }
+      S[t] = sum;
+    }
+    // right-hand sides of the pressure parts: -B~_c' y_s (row 3 s + c), e_centre
+    for (int t = tid; t < P::NROW * NP; t += nt) {
+      const int k = t / NP, pq = t % NP;
+      double sum = 0.0;
+      if (k < 24) {
+        const double* bp = Bs + ((size_t)(k % 3) * NP + pq) * NV;
+        const double* yp = X + ((size_t)3 * NP + k / 3) * NV;
+        for (int j = 0; j < NV; ++j) sum = sum - bp[j] * yp[j];
+      } else {
+        sum = pq == 13 ? 1.0 : 0.0;
+      }
+      pv[t] = sum;
+    }
+    __syncthreads();
+    cta_lu(S, NP, NP, pivS, &flag);
+    if (tid < P::NROW) lu_solve_vec(S, NP, NP, pivS, pv + tid * NP);
+    __syncthreads();
+    // rows: velocity u_c' = delta_cc' y - W~_c' z, pressure z; de-scaled;
+    // absent owned DoFs give zero rows
+    double* out = coef + (size_t)v * P::NROW * P::SP;
+    for (int t = tid; t < P::NROW * P::SP; t += nt) {
+      const int k = t / P::SP, slot = t % P::SP;
+      double val = 0.0;
+      const int orow = k < 24 ? q2p3_own(k / 3) : NV + 13;
+      if (slot < P::NS && act[orow]) {
+        const double dk = k < 24 ? dv[orow] : dp[13];
+        if (slot < P::NSV) {
+          const int pn = slot / 3, c2 = slot % 3;
+          if (act[pn]) {
+            double u = (k < 24 && c2 == k % 3) ? X[((size_t)3 * NP + k / 3) * NV + pn] : 0.0;
+            for (int pq = 0; pq < NP; ++pq) u = u - X[((size_t)c2 * NP + pq) * NV + pn] * pv[k * NP + pq];
+            val = dk * u * dv[pn];
+          }
+        } else {
+          const int pq = slot - P::NSV;
+          if (act[NV + pq]) val = dk * pv[k * NP + pq] * dp[pq];
+        }
+      }
+      out[t] = val;
+    }
+    if (tid == 0 && flag) atomicOr(d_err, kErrSingularPatch);
+    __syncthreads();
+  }
+}
+
+// 3D apply: a warp per vertex; lane l sums the 25 rows over the slots
+// l, l + 32, ... (coalesced row loads, residual gathers from the padded
+// copies), a reduce-scatter leaves row l's sum in lane l, and lanes 0..24
+// write the restricted update of the owned DoFs.
+__global__ void __launch_bounds__(256)
+    q2_apply3_kernel(Q2Grid q, const double* __restrict__ coef, const unsigned char* __restrict__ mask,
+                     const double* __restrict__ rpv, const double* __restrict__ rpp, double omega,
+                     double* __restrict__ x) {
+  using P = Q2P3;
+  __shared__ int soff[P::SP];
+  const int PX = q.nf[0] + 8, PY = q.nf[1] + 8, PXP = q.nv1[0] + 2, PYP = q.nv1[1] + 2;
+  for (int j = threadIdx.x; j < P::SP; j += blockDim.x) {
+    if (j < P::NSV) {
+      const int pn = j / 3, c = j % 3;
+      soff[j] = ((pn % 9 - 4) + PX * ((pn / 9) % 9 - 4 + PY * (pn / 81 - 4))) * 3 + c;
+    } else if (j < P::NS) {
+      const int pq = j - P::NSV;
+      soff[j] = (pq % 3 - 1) + PXP * ((pq / 3) % 3 - 1 + PYP * (pq / 9 - 1));
+    } else {
+      soff[j] = 0;  // padding slots: zero coefficients
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long gv = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const bool valid = gv < q.np;
+  const long long v = valid ? gv : q.np - 1;
+  const int ax = (int)(v % q.nv1[0]), ay = (int)((v / q.nv1[0]) % q.nv1[1]),
+            az = (int)(v / ((long long)q.nv1[0] * q.nv1[1]));
+  const double* rv = rpv + (((long long)(2 * az + 4) * PY + (2 * ay + 4)) * PX + (2 * ax + 4)) * 3;
+  const double* rp = rpp + ((long long)(az + 1) * PYP + (ay + 1)) * PXP + (ax + 1);
+  const double* cf = coef + (size_t)v * P::NROW * P::SP;
+  double y[32];
+#pragma unroll
+  for (int k = 0; k < 32; ++k) y[k] = 0.0;
+  for (int j = lane; j < P::SP; j += 32) {
+    const double r = j < P::NSV ? rv[soff[j]] : rp[soff[j]];
+#pragma unroll
+    for (int k = 0; k < P::NROW; ++k) y[k] += __ldcs(cf + (size_t)k * P::SP + j) * r;
+  }
+  // reduce-scatter over the 32 lanes: after the step of width w each lane
+  // keeps the half of its partial sums selected by bit w of its lane index
+#pragma unroll
+  for (int w = 16; w > 0; w >>= 1) {
+    const bool hi = lane & w;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const double send = hi ? y[i] : y[i + w];
+      const double keep = hi ? y[i + w] : y[i];
+      y[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  if (!valid || lane >= P::NROW) return;
+  const double yk = y[0];
+  if (lane < 24) {
+    const int s = lane / 3, c = lane % 3;
+    const int I = 2 * ax + (s & 1), J = 2 * ay + ((s >> 1) & 1), K = 2 * az + (s >> 2);
+    if (I >= q.nf[0] || J >= q.nf[1] || K >= q.nf[2]) return;
+    const long long i = I + (long long)q.nf[0] * (J + (long long)q.nf[1] * K);
+    const double add = mask[i] ? rv[((s & 1) + PX * (((s >> 1) & 1) + PY * (s >> 2))) * 3 + c] : omega * yk;
+    x[i * 3 + c] += add;
+  } else {
+    x[q.nq * 3 + v] += omega * yk;
+  }
+}
+
 }  // namespace
 
 size_t factor_doubles(int dim) { return dim == 3 ? PatchDims<3>::REC : PatchDims<2>::REC; }
@@ -2312,10 +2665,27 @@ cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* 
 
 namespace fc {
 
-size_t q2_patch_rows_doubles(int dim) { return dim == 2 ? (size_t)Q2P::NS * Q2P::NROWP : 0; }
+size_t q2_patch_rows_doubles(int dim) {
+  return dim == 2 ? (size_t)Q2P::NS * Q2P::NROWP : (size_t)Q2P3::NROW * Q2P3::SP;
+}
 
-cudaError_t launch_q2_patch_rows(const Q2Grid& q, const double* A, const double* B, const unsigned char* mask,
-                                 double* coef, unsigned* d_err, cudaStream_t s) {
+size_t q2_patch_rows_work_doubles(int dim, long long ctas) { return dim == 3 ? (size_t)ctas * Q2P3::WS : 0; }
+
+int q2_patch_rows_ctas(int dim, long long np) {
+  if (dim != 3) return 0;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    nsm = 1;
+  return (int)std::min<long long>(np, std::min(nsm, kQ2Rows3MaxCtas));
+}
+
+cudaError_t launch_q2_patch_rows(int dim, const Q2Grid& q, const double* A, const double* B, const unsigned char* mask,
+                                 double* coef, double* work, int ctas, unsigned* d_err, cudaStream_t s) {
+  if (dim == 3) {
+    q2_patch_rows3_kernel<<<(unsigned)ctas, 512, 0, s>>>(q, A, B, mask, coef, work, d_err);
+    note_launches(1);
+    return cudaGetLastError();
+  }
   constexpr int NV = Q2P::NV, NP = Q2P::NP;
   const size_t smem = sizeof(double) * ((size_t)NV * NV + 2 * NV * NP + 2 * NP * NV + NP * NP + NV + NP + 4 * NV + 9 * NP) +
                       sizeof(int) * (2 * (NV + NP) + 1);
@@ -2326,10 +2696,15 @@ cudaError_t launch_q2_patch_rows(const Q2Grid& q, const double* A, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_q2_apply(const Q2Grid& q, const double* coef, const unsigned char* mask, const double* rpv,
+cudaError_t launch_q2_apply(int dim, const Q2Grid& q, const double* coef, const unsigned char* mask, const double* rpv,
                             const double* rpp, double omega, double* x, cudaStream_t s) {
-  const long long threads = q.np * 8;
-  q2_apply_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(q, coef, mask, rpv, rpp, omega, x);
+  if (dim == 3) {
+    const long long threads = q.np * 32;
+    q2_apply3_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(q, coef, mask, rpv, rpp, omega, x);
+  } else {
+    const long long threads = q.np * 8;
+    q2_apply_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(q, coef, mask, rpv, rpp, omega, x);
+  }
   note_launches(1);
   return cudaGetLastError();
 }

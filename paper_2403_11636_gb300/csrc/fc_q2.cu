@@ -514,11 +514,11 @@ cudaError_t launch_q2_assemble(const LevelGeom& g, const Q2Grid& q, const double
                                const double* eF, const unsigned char* mask, const double* wfix, double* A,
                                double* B, double* T, double* b, cudaStream_t s) {
   if (g.dim == 2) {
-    q2_assemble_vel_kernel<2><<<blocks_for(q.nq), 128, 0, s>>>(g, q, eA, eB, A, B);
+    q2_assemble_vel_kernel<2><<<blocks_for(q.nq), 256, 0, s>>>(g, q, eA, eB, A, B);
     q2_assemble_pres_kernel<2><<<blocks_for(q.np), 256, 0, s>>>(q, B, T);
     if (b) q2_rhs_kernel<2><<<blocks_for(q.nq + q.np), 256, 0, s>>>(g, q, eF, A, T, mask, wfix, b);
   } else {
-    q2_assemble_vel_kernel<3><<<blocks_for(q.nq), 128, 0, s>>>(g, q, eA, eB, A, B);
+    q2_assemble_vel_kernel<3><<<blocks_for(q.nq), 256, 0, s>>>(g, q, eA, eB, A, B);
     q2_assemble_pres_kernel<3><<<blocks_for(q.np), 256, 0, s>>>(q, B, T);
     if (b) q2_rhs_kernel<3><<<blocks_for(q.nq + q.np), 256, 0, s>>>(g, q, eF, A, T, mask, wfix, b);
   }

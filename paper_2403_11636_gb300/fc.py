@@ -404,8 +404,8 @@ class Solver:
 
     def patch_rows(self, node: int, level=None):
         lv = self.nlevels if level is None else level
-        if self.element == "q2":
-            out = np.zeros((9, 171))      # 2D Q2-Q1: owned rows x slots
+        if self.element == "q2":          # Q2-Q1: owned rows x slots
+            out = np.zeros((25, 2214)) if self.dim == 3 else np.zeros((9, 171))
         else:
             ns = 402 if self.dim == 3 else 59
             out = np.zeros((self.nd, ns))

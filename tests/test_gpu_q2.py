@@ -3,9 +3,11 @@
 The element pair with Q2 velocities and Q1 pressures, patches of the Q2
 nodes 2a-4 .. 2a+4 and the pressures a-1 .. a+1 around each vertex a, each
 Q2 node written by the vertex at the lower corner of its cell, edge or face
-(fc_options.element = 1, 2D).  Same bounds as the Q1-Q1 parity tests:
-operator, transfers 1e-12; patch rows 1e-11; sweeps and V-cycles 1e-10
-relative; FGMRES and standalone GMG with the oracle's iteration counts."""
+(fc_options.element = 1), in 2D (9 owned rows over 171 slots) and 3D (25
+owned rows over 2214 slots, the velocity block factored by a banded LU).
+Same bounds as the Q1-Q1 parity tests: operator, transfers 1e-12; patch
+rows 1e-11; sweeps and V-cycles 1e-10 relative; FGMRES and standalone GMG
+with the oracle's iteration counts."""
 import dataclasses
 
 import numpy as np
@@ -36,7 +38,12 @@ PROBS = {
     "ell2d": dataclasses.replace(inputs.batch_2d(7), n=(32, 32), nlevels=3),
     "ragged": dataclasses.replace(inputs.batch_2d(3), n=(48, 16), hi=(2.2, 0.41), nlevels=2,
                                   shapes=np.array([[1.0, 0.5, 0.2, 0.0, 0.08, 0.05, 0.0, 0.8, 0.6]])),
+    "por3d4": inputs.porous_3d(0, n=4, nspheres=2, nlevels=2),
+    "por3d8": inputs.porous_3d(0, n=8, nspheres=4, nlevels=3),
+    "duct3d": dataclasses.replace(inputs.porous_3d(2, n=8, nspheres=3, nlevels=2), n=(8, 4, 4),
+                                  hi=(2.0, 1.0, 1.0), preset=0),
 }
+ROWS_CASES = ["ch2d", "ell2d", "por3d4", "por3d8", "duct3d"]
 
 
 @pytest.fixture(scope="module")
@@ -63,41 +70,55 @@ def test_q2_rhs_and_operator(fc, oracles, name):
     assert rel(s.rhs().cpu().numpy(), b) <= 10 * OPER_TOL
 
 
-@pytest.mark.parametrize("name", ["ch2d", "ell2d"])
+def expected_rows(L, vert):
+    """The oracle's owned rows of the patch of vertex `vert` in the library's
+    slot order: velocity (Q2 node of the 9^d box, x fastest, component inner),
+    then the 3^d pressures; rows of constrained owned DoFs are zero."""
+    dim = L.dim
+    nf = [2 * k + 1 for k in L.n]
+    nv1 = [k + 1 for k in L.n]
+    a = [vert % nv1[0], (vert // nv1[0]) % nv1[1], vert // (nv1[0] * nv1[1]) if dim == 3 else 0]
+    nsv = 9 ** dim * dim
+    ns, nr = nsv + 3 ** dim, (1 << dim) * dim + 1
+    rows, dofs, own = L.patch_inverse_rows(int(vert))
+    pos = {int(d): q for q, d in enumerate(dofs)}
+    want = np.zeros((nr, ns))
+    for slot in range(ns):
+        if slot < nsv:
+            pn, c = divmod(slot, dim)
+            off = (pn % 9, (pn // 9) % 9, pn // 81)
+            idx = [2 * a[k] - 4 + off[k] for k in range(dim)]
+            if any(not 0 <= idx[k] < nf[k] for k in range(dim)):
+                continue
+            node = idx[0] + nf[0] * (idx[1] + (nf[1] * idx[2] if dim == 3 else 0))
+            d = node * dim + c
+        else:
+            t = slot - nsv
+            off = (t % 3, (t // 3) % 3, t // 9)
+            idx = [a[k] - 1 + off[k] for k in range(dim)]
+            if any(not 0 <= idx[k] < nv1[k] for k in range(dim)):
+                continue
+            d = L.nv + idx[0] + nv1[0] * (idx[1] + (nv1[1] * idx[2] if dim == 3 else 0))
+        q = pos.get(d)
+        if q is None:
+            continue
+        for k in range(nr):
+            if own[k] >= 0:
+                want[k, slot] = rows[k, q]
+    return want
+
+
+@pytest.mark.parametrize("name", ROWS_CASES)
 def test_q2_patch_rows(fc, oracles, name):
     p = PROBS[name]
     s = solver(fc, p)
     L = oracles[name].fine
-    n = p.n
-    nf0 = 2 * n[0] + 1
-    nv1 = n[0] + 1
     rng = np.random.default_rng(0)
-    for vert in rng.choice(L.np, 20, replace=False):
+    for vert in rng.choice(L.np, min(20, L.np), replace=False):
         g = s.patch_rows(int(vert))
-        rows, dofs, own = L.patch_inverse_rows(int(vert))
-        pos = {int(d): q for q, d in enumerate(dofs)}
-        ax, ay = int(vert) % nv1, int(vert) // nv1
-        want = np.zeros((9, 171))
-        for slot in range(171):
-            if slot < 162:
-                pnode, c = slot // 2, slot % 2
-                I, J = 2 * ax - 4 + pnode % 9, 2 * ay - 4 + pnode // 9
-                if not (0 <= I < nf0 and 0 <= J < 2 * n[1] + 1):
-                    continue
-                d = (I + nf0 * J) * 2 + c
-            else:
-                t = slot - 162
-                X, Y = ax - 1 + t % 3, ay - 1 + t // 3
-                if not (0 <= X < nv1 and 0 <= Y < n[1] + 1):
-                    continue
-                d = L.nv + X + nv1 * Y
-            q = pos.get(d)
-            if q is None:
-                continue
-            for k in range(9):
-                if own[k] >= 0:
-                    want[k, slot] = rows[k, q]
-        for k in range(9):
+        want = expected_rows(L, int(vert))
+        assert g.shape == want.shape
+        for k in range(want.shape[0]):
             if np.abs(want[k]).max() == 0:
                 assert np.abs(g[k]).max() == 0, (vert, k)
             else:
@@ -119,8 +140,9 @@ def test_q2_sweep_parity(fc, oracles, name):
     assert rel(got3, want3) <= SWEEP_TOL
 
 
-def test_q2_sweep_order_independent_bitwise(fc):
-    p = PROBS["ch2d"]
+@pytest.mark.parametrize("name", ["ch2d", "por3d4"])
+def test_q2_sweep_order_independent_bitwise(fc, name):
+    p = PROBS[name]
     s = solver(fc, p)
     n = s.ndof()
     x0 = inputs.uniform_array(n, 91)
@@ -130,7 +152,7 @@ def test_q2_sweep_order_independent_bitwise(fc):
     np.testing.assert_array_equal(a1, a2)
 
 
-@pytest.mark.parametrize("name", ["ch2d", "ell2d"])
+@pytest.mark.parametrize("name", ["ch2d", "ell2d", "por3d8", "duct3d"])
 def test_q2_transfers_and_coarse_solve(fc, oracles, name):
     p = PROBS[name]
     s = solver(fc, p)
@@ -148,7 +170,7 @@ def test_q2_transfers_and_coarse_solve(fc, oracles, name):
     assert rel(s.coarse_solve(b1).cpu().numpy(), spl.spsolve(A.tocsc(), b1)) <= 1e-11
 
 
-@pytest.mark.parametrize("name", ["ch2d", "ell2d"])
+@pytest.mark.parametrize("name", ["ch2d", "ell2d", "por3d8", "duct3d"])
 def test_q2_vcycle_parity(fc, oracles, name):
     p = PROBS[name]
     s = solver(fc, p)
@@ -185,11 +207,10 @@ def test_q2_standalone_gmg(fc):
 
 
 def test_q2_rejects_unsupported(fc):
-    p3 = inputs.porous_3d(0, n=8, nspheres=2, nlevels=2)
-    with pytest.raises(fc.FcError):
-        fc.Solver(p3, element="q2")
     with pytest.raises(fc.FcError):
         fc.Solver(PROBS["ch2d"], element="q2", prec="df64")
+    with pytest.raises(fc.FcError):
+        fc.Solver(PROBS["por3d4"], element="q2", cache="matrix")
     s = solver(fc, PROBS["ch2d"])
     x = s.zeros()
     assert s.smooth_noalloc_(x, s.rhs()) == fc.FC_ERR_INVALID

@@ -571,3 +571,71 @@ def test_standalone_gmg_reduces_residual():
     _, its, red = mg.gmg_solve(mg.rhs(), reduction=1e-9, maxit=60)
     assert red <= 1e-9
     assert its <= 40
+
+
+def _blocks(A, dim):
+    nd = dim + 1
+    v = np.array([k % nd < dim for k in range(A.shape[0])])
+    A = A.toarray()
+    return A[np.ix_(v, v)], A[np.ix_(v, ~v)], A[np.ix_(~v, v)], A[np.ix_(~v, ~v)]
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_galerkin_equals_rediscretisation_without_obstacles(dim):
+    """Galerkin coarse operator R L_f P (the alternative to rediscretising the
+    coarser grids, Sec. 3) on a grid without obstacles: the Q1 spaces are
+    nested and the Gauss rule integrates the velocity and divergence forms
+    exactly, so those blocks equal the rediscretised coarse operator,
+    constrained wall and inflow rows included; the pressure block (a
+    projection on each cell, which does not nest) does not."""
+    if dim == 2:
+        p = inputs.channel_2d(0, n=8, nlevels=2)
+    else:
+        p = inputs.porous_3d(0, n=4, nspheres=1, nlevels=2)
+        p.preset = 0
+    p.shapes = np.zeros((0, 9))
+    gal = O.MG(p, galerkin=True).levels[0].csr()[0]
+    red = O.Level.from_problem(p, 1).csr()[0]
+    g, r = _blocks(gal, dim), _blocks(red, dim)
+    for k in range(3):
+        assert np.abs(g[k] - r[k]).max() <= 1e-12 * np.abs(r[k]).max(), k
+    assert np.abs(g[3] - r[3]).max() >= 0.1 * np.abs(r[3]).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_galerkin_pressure_block_closed_form(dim):
+    """The Galerkin pressure block applies the fine-grid stabilisation
+    c(q,p) = -(1/eta) sum over fine cells K of |K| var_K(p) (eq.
+    stabilization_l2) to coarse Q1 functions: it vanishes on constants, and
+    for p = x it equals -(1/eta) |Omega| h_f^2 / 12 (the variance of a
+    linear function over a cell of width h_f), a quarter of the rediscretised
+    coarse value."""
+    n = 8 if dim == 2 else 4
+    if dim == 2:
+        p = inputs.channel_2d(0, n=n, nlevels=2)
+    else:
+        p = inputs.porous_3d(0, n=n, nspheres=1, nlevels=2)
+    p.shapes = np.zeros((0, 9))
+    Cg = _blocks(O.MG(p, galerkin=True).levels[0].csr()[0], dim)[3]
+    Cr = _blocks(O.Level.from_problem(p, 1).csr()[0], dim)[3]
+    nc = n // 2
+    xs = np.array([(k % (nc + 1)) / nc for k in range((nc + 1) ** dim)])
+    assert np.abs(Cg @ np.ones(len(xs))).max() <= 1e-12 * np.abs(Cg).max()
+    hf = 1.0 / n
+    want = -(1.0 / p.eta) * hf * hf / 12.0
+    assert xs @ Cg @ xs == pytest.approx(want, rel=1e-12)
+    assert xs @ Cr @ xs == pytest.approx(4.0 * want, rel=1e-12)
+
+
+def test_galerkin_hierarchy_converges():
+    """FGMRES with Galerkin coarse operators on the channel with a cut
+    circle reaches the direct solution within the rediscretised hierarchy's
+    iteration bound (Sec. 4 solver setting)."""
+    p = inputs.channel_2d(0, n=32, nlevels=3)
+    mg = O.MG(p, galerkin=True)
+    A, b, _ = mg.fine.csr()
+    x, its, rel, _ = mg.fgmres(b, rtol=1e-10)
+    assert rel <= 1e-10
+    xd = spl.spsolve(A.tocsc(), b)
+    assert np.linalg.norm(x - xd) <= 1e-7 * np.linalg.norm(xd)
+    assert its <= 16
