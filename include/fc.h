@@ -134,6 +134,11 @@ typedef struct {
                           (the paper's restricted write R~_i, Sec. 3.1, with an explicit owner
                           for the nodes away from the vertices).  Vectors: the velocity block
                           (Q2 node, x fastest, d components inner), then the vertex pressures. */
+  int galerkin;        /* coarser-grid operators (Q1-Q1): 0 rediscretised on each grid of the
+                          hierarchy with the same geometry and data (the paper's hierarchy of
+                          coarser discretisations, Sec. 3); 1 Galerkin products R L P of the
+                          next finer operator with the V-cycle's transfers (no quadrature on
+                          the coarser grids; constrained coarse DoFs keep identity rows). */
 } fc_options;
 
 /* Fill the defaults:
@@ -142,7 +147,8 @@ typedef struct {
  *   cache FC_CACHE_INVERSE, prec FC_PREC_FP64, fgmres_restart 30;
  *   bc_preset 0 (channel), ubar 0.3, force_kind 0 with force = 0;
  *   dedup 1 (shared class blocks; the Python binding's default too);
- *   tc 0 (CUDA cores), badcut_frac 1e-3, element 0 (Q1-Q1). */
+ *   tc 0 (CUDA cores), badcut_frac 1e-3, element 0 (Q1-Q1), galerkin 0
+ *   (rediscretised coarser grids). */
 fc_status fc_options_default(fc_options* o);
 
 /* Build the hierarchy of `depth` levels (paper Sec. 3, Algorithm 1 on a

@@ -636,6 +636,7 @@ fc_status fc_options_default(fc_options* o) {
   o->tc = 0;
   o->badcut_frac = 1e-3;
   o->element = 0;
+  o->galerkin = 0;
   return FC_OK;
 }
 
@@ -758,6 +759,8 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   if (o->prec != FC_PREC_FP64 && o->cache != FC_CACHE_INVERSE)
     return fail(h, FC_ERR_INVALID, "reduced-precision storage applies to cache_inverse only");
   if (o->element != 0 && o->element != 1) return fail(h, FC_ERR_INVALID, "invalid element pair");
+  if (o->galerkin != 0 && o->galerkin != 1) return fail(h, FC_ERR_INVALID, "invalid coarse-operator choice");
+  if (o->galerkin && o->element != 0) return fail(h, FC_ERR_INVALID, "Galerkin coarse operators need the Q1-Q1 pair");
   if (o->element == 1 && (o->cache != FC_CACHE_INVERSE || o->prec != FC_PREC_FP64))
     return fail(h, FC_ERR_INVALID, "the Q2-Q1 pair runs with cache_inverse and FP64 rows");
   {
@@ -799,26 +802,39 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   CK(dalloc(h, &d_count, 2, -1));
 
   const int dim = g->dim, nd = dim + 1, nb = dim == 3 ? 27 : 9, nl = 1 << dim;
-  for (int li = 0; li < depth; ++li) {
+  // Galerkin coarse operators: the levels are built from the finest down,
+  // each coarser operator as R L P of the one above it (no quadrature on
+  // the coarser grids); the finer level's cell classes and statistics are
+  // kept for the next level's
+  const bool galerkin = o->galerkin != 0;
+  unsigned char* fine_cclass = nullptr;
+  double* fine_estat = nullptr;
+  for (int step = 0; step < depth; ++step) {
+    const int li = galerkin ? depth - 1 - step : step;
+    const bool gal = galerkin && li < depth - 1;
     Level& L = h->lev[li];
     L.g = make_geom(g, nshape, h->d_shapes, alpha, o, depth - 1 - li);
     const LevelGeom& G = L.g;
     // ---- element data and operator
     double *eA = nullptr, *eB = nullptr, *eF = nullptr;
-    CK(dalloc(h, &eA, (size_t)G.ncell * nl * nl, -1));
-    CK(dalloc(h, &eB, (size_t)G.ncell * dim * nl * nl, -1));
-    CK(dalloc(h, &eF, (size_t)G.ncell * dim * nl, -1));
-    size_t tmp_bytes = (size_t)G.ncell * (nl * nl * (1 + dim) + dim * nl) * 8;
-    h->bytes[4] = std::max(h->bytes[4], tmp_bytes);
+    if (!gal) {
+      CK(dalloc(h, &eA, (size_t)G.ncell * nl * nl, -1));
+      CK(dalloc(h, &eB, (size_t)G.ncell * dim * nl * nl, -1));
+      CK(dalloc(h, &eF, (size_t)G.ncell * dim * nl, -1));
+      size_t tmp_bytes = (size_t)G.ncell * (nl * nl * (1 + dim) + dim * nl) * 8;
+      h->bytes[4] = std::max(h->bytes[4], tmp_bytes);
+    }
     // reference element matrices of an uncut cell of this level (alpha = 1,
     // same rule), then all cells; plain cells take alpha * reference
     double *rA = nullptr, *rB = nullptr, *rF = nullptr;
     unsigned char* cclass = nullptr;
-    CK(dalloc(h, &rA, (size_t)nl * nl, -1));
-    CK(dalloc(h, &rB, (size_t)dim * nl * nl, -1));
-    CK(dalloc(h, &rF, (size_t)dim * nl, -1));
     CK(dalloc(h, &cclass, (size_t)G.ncell, -1));
-    {
+    if (!gal) {
+      CK(dalloc(h, &rA, (size_t)nl * nl, -1));
+      CK(dalloc(h, &rB, (size_t)dim * nl * nl, -1));
+      CK(dalloc(h, &rF, (size_t)dim * nl, -1));
+    }
+    if (!gal) {
       LevelGeom R = G;
       R.ncell = 1;
       R.nnodes = 1;
@@ -840,11 +856,16 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
                         (o->prec == FC_PREC_FP32 || o->prec == FC_PREC_BF16);
     double* estat = nullptr;
     if (badcut) CK(dalloc(h, &estat, (size_t)G.ncell * 4, -1));
-    CK(launch_cell_elements(G, eA, eB, eF, estat, h->d_err, rA, rB, cclass, h->stream));
+    if (!gal)
+      CK(launch_cell_elements(G, eA, eB, eF, estat, h->d_err, rA, rB, cclass, h->stream));
+    else
+      CK(launch_coarsen_cells(G, h->lev[li + 1].g, fine_cclass, cclass, estat ? fine_estat : nullptr, estat,
+                              h->stream));
     CK(dalloc(h, &L.st, (size_t)G.nnodes * nb * spn(dim), 0));
     CK(dalloc(h, &L.mask, (size_t)G.nnodes, 0));
     CK(dalloc(h, &L.wfix, (size_t)G.ndof, 0));
-    CK(launch_assemble(G, eA, eB, L.st, h->stream));
+    if (!gal) CK(launch_assemble(G, eA, eB, L.st, h->stream));
+    else CK(launch_galerkin(G, h->lev[li + 1].g, h->lev[li + 1].st, h->lev[li + 1].mask, L.st, h->stream));
     CK(launch_masks(G, L.mask, L.wfix, h->stream));
     if (dim == 3 && li > 0) {
       CK(dalloc(h, &L.dead, (size_t)G.nn[1] + G.nn[2], 0));
@@ -925,7 +946,12 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     dfree(h, rA);
     dfree(h, rB);
     dfree(h, rF);
-    dfree(h, cclass);
+    if (galerkin) {
+      dfree(h, fine_cclass);
+      fine_cclass = cclass;
+    } else {
+      dfree(h, cclass);
+    }
     fc_status st = check_err(h);
     if (st != FC_OK) return st;
     // ---- patch cache (every level above the coarsest)
@@ -1022,8 +1048,15 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
       st = check_err(h);
       if (st != FC_OK) return st;
     }
-    dfree(h, estat);
+    if (galerkin) {
+      dfree(h, fine_estat);
+      fine_estat = estat;
+    } else {
+      dfree(h, estat);
+    }
   }
+  dfree(h, fine_cclass);
+  dfree(h, fine_estat);
   dfree(h, d_count);
   // ---- coarse solve
   {

@@ -162,6 +162,104 @@ __global__ void rhs_kernel(LevelGeom g, const double* __restrict__ eF, const dou
   }
 }
 
+// Galerkin coarse operator L_c = R L_f P (the alternative to rediscretising
+// the coarser grids of the hierarchy, Sec. 3), with the transfers of the
+// V-cycle: P = Q1 interpolation per component, weight prod_k w(i_k - 2 I_k),
+// w(0) = 1, w(+-1) = 1/2; constrained fine velocity DoFs have zero rows of P
+// (the prolongation leaves them alone), so the product runs over free fine
+// velocity DoFs only.  One thread per (coarse node I, neighbour offset):
+// the fine nodes i = 2 I + e and j = 2 J + e' (e, e' in {-1, 0, 1}^d) with
+// j - i within the fine 3^d stencil, summed in a fixed order, so equal fine
+// neighbourhoods give bit-equal coarse entries.  The result is a raw coarse
+// stencil like the rediscretised one: the coarse masks act where it is used.
+template <int DIM>
+__global__ void galerkin_kernel(LevelGeom gc, LevelGeom gf, const double* __restrict__ stf,
+                                const unsigned char* __restrict__ maskf, double* __restrict__ stc) {
+  constexpr int NB = DIM == 3 ? 27 : 9, SP = 2 * DIM + 2;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= gc.nnodes * NB) return;
+  const long long node = tid % gc.nnodes;
+  const int nb = (int)(tid / gc.nnodes);
+  const int ia[3] = {(int)(node % gc.nn[0]), (int)((node / gc.nn[0]) % gc.nn[1]),
+                     DIM == 3 ? (int)(node / ((long long)gc.nn[0] * gc.nn[1])) : 0};
+  const int off[3] = {nb % 3 - 1, (nb / 3) % 3 - 1, DIM == 3 ? nb / 9 - 1 : 0};
+  double vA = 0.0, vB[3] = {0, 0, 0}, vT[3] = {0, 0, 0}, vC = 0.0;
+  for (int ti = 0; ti < NB; ++ti) {
+    int fi[3] = {0, 0, 0};
+    double wi = 1.0;
+    bool in = true;
+    for (int k = 0; k < DIM; ++k) {
+      const int e = (k == 0 ? ti % 3 : (k == 1 ? (ti / 3) % 3 : ti / 9)) - 1;
+      fi[k] = 2 * ia[k] + e;
+      if (fi[k] < 0 || fi[k] > gf.n[k]) in = false;
+      wi = wi * (e == 0 ? 1.0 : 0.5);
+    }
+    if (!in) continue;
+    const long long i = fi[0] + (long long)gf.nn[0] * (fi[1] + (long long)gf.nn[1] * fi[2]);
+    const bool fixi = maskf[i] != 0;
+    for (int tj = 0; tj < NB; ++tj) {
+      int fj[3] = {0, 0, 0}, d[3] = {0, 0, 0};
+      double wj = 1.0;
+      bool ok = true;
+      for (int k = 0; k < DIM; ++k) {
+        const int e = (k == 0 ? tj % 3 : (k == 1 ? (tj / 3) % 3 : tj / 9)) - 1;
+        fj[k] = 2 * (ia[k] + off[k]) + e;
+        d[k] = fj[k] - fi[k];
+        if (fj[k] < 0 || fj[k] > gf.n[k] || d[k] < -1 || d[k] > 1) ok = false;
+        wj = wj * (e == 0 ? 1.0 : 0.5);
+      }
+      if (!ok) continue;
+      const long long j = fj[0] + (long long)gf.nn[0] * (fj[1] + (long long)gf.nn[1] * fj[2]);
+      const bool fixj = maskf[j] != 0;
+      const int fnb = (d[0] + 1) + 3 * (d[1] + 1) + (DIM == 3 ? 9 * (d[2] + 1) : 0);
+      const double* sv = stf + (long long)fnb * SP * gf.nnodes + i;
+      const double w = wi * wj;
+      if (!fixi && !fixj) vA = vA + w * sv[0];
+      for (int c = 0; c < DIM; ++c) {
+        if (!fixi) vB[c] = vB[c] + w * sv[(1 + c) * gf.nnodes];
+        if (!fixj) vT[c] = vT[c] + w * sv[(1 + DIM + c) * gf.nnodes];
+      }
+      vC = vC + w * sv[(1 + 2 * DIM) * gf.nnodes];
+    }
+  }
+  const long long base = (long long)nb * SP;
+  stc[(base + 0) * gc.nnodes + node] = vA;
+  for (int c = 0; c < DIM; ++c) {
+    stc[(base + 1 + c) * gc.nnodes + node] = vB[c];
+    stc[(base + 1 + DIM + c) * gc.nnodes + node] = vT[c];
+  }
+  stc[(base + 1 + 2 * DIM) * gc.nnodes + node] = vC;
+}
+
+// cell data of a coarse level from its 2^d children on the finer level:
+// the class is the children's common class (0 when they differ or any is
+// cut), the cell statistics are the children's sums (fluid volume first)
+template <int DIM>
+__global__ void coarsen_cells_kernel(LevelGeom gc, LevelGeom gf, const unsigned char* __restrict__ cf,
+                                     unsigned char* __restrict__ cc, const double* __restrict__ ef,
+                                     double* __restrict__ ec) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= gc.ncell) return;
+  const int ic[3] = {(int)(cell % gc.n[0]), (int)((cell / gc.n[0]) % gc.n[1]),
+                     DIM == 3 ? (int)(cell / ((long long)gc.n[0] * gc.n[1])) : 0};
+  int cls = -1;
+  double st[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int ch = 0; ch < (1 << DIM); ++ch) {
+    int f[3] = {0, 0, 0};
+    for (int k = 0; k < DIM; ++k) f[k] = 2 * ic[k] + ((ch >> k) & 1);
+    const long long fc = f[0] + (long long)gf.n[0] * (f[1] + (long long)gf.n[1] * f[2]);
+    if (cf) {
+      const int c = cf[fc];
+      cls = cls < 0 ? c : (cls == c ? cls : 0);
+    }
+    if (ef)
+      for (int t = 0; t < 4; ++t) st[t] = st[t] + ef[fc * 4 + t];
+  }
+  if (cc) cc[cell] = (unsigned char)(cls < 0 ? 0 : cls);
+  if (ec)
+    for (int t = 0; t < 4; ++t) ec[cell * 4 + t] = st[t];
+}
+
 }  // namespace
 
 cudaError_t launch_assemble(const LevelGeom& g, const double* eA, const double* eB, double* st,
@@ -360,6 +458,26 @@ cudaError_t launch_patch_classes(const LevelGeom& g, const unsigned char* cclass
   place_stored_kernel<<<nb, kScanBlock, 0, s>>>(n, pclass, rep, counts, work, prow);
   class_rows_kernel<<<b256, 256, 0, s>>>(n, pclass, rep, prow);
   note_launches(6);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_galerkin(const LevelGeom& gc, const LevelGeom& gf, const double* stf, const unsigned char* maskf,
+                            double* stc, cudaStream_t s) {
+  const long long n = gc.nnodes * (gc.dim == 3 ? 27 : 9);
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (gc.dim == 2) galerkin_kernel<2><<<blocks, 256, 0, s>>>(gc, gf, stf, maskf, stc);
+  else galerkin_kernel<3><<<blocks, 256, 0, s>>>(gc, gf, stf, maskf, stc);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarsen_cells(const LevelGeom& gc, const LevelGeom& gf, const unsigned char* cclass_f,
+                                 unsigned char* cclass_c, const double* estat_f, double* estat_c, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((gc.ncell + 255) / 256);
+  if (gc.dim == 2) coarsen_cells_kernel<2><<<blocks, 256, 0, s>>>(gc, gf, cclass_f, cclass_c, estat_f, estat_c);
+  else coarsen_cells_kernel<3><<<blocks, 256, 0, s>>>(gc, gf, cclass_f, cclass_c, estat_f, estat_c);
+  note_launches(1);
   return cudaGetLastError();
 }
 

@@ -259,6 +259,12 @@ cudaError_t launch_patch_classes(const LevelGeom& g, const unsigned char* cclass
 cudaError_t launch_assemble(const LevelGeom& g, const double* eA, const double* eB, double* st,
                             cudaStream_t s);
 cudaError_t launch_masks(const LevelGeom& g, unsigned char* mask, double* wfix, cudaStream_t s);
+// Galerkin coarse stencil R L_f P from the finer level's stencil and masks,
+// and the coarse cell classes / statistics from the children's
+cudaError_t launch_galerkin(const LevelGeom& gc, const LevelGeom& gf, const double* stf, const unsigned char* maskf,
+                            double* stc, cudaStream_t s);
+cudaError_t launch_coarsen_cells(const LevelGeom& gc, const LevelGeom& gf, const unsigned char* cclass_f,
+                                 unsigned char* cclass_c, const double* estat_f, double* estat_c, cudaStream_t s);
 // y / z layer flags of g.dead_layer from the node masks (3D); out holds
 // nn[1] + nn[2] bytes
 cudaError_t launch_dead_layers(const LevelGeom& g, const unsigned char* mask, unsigned char* out, cudaStream_t s);

@@ -86,7 +86,7 @@ class FcOptions(C.Structure):
                 ("cache", C.c_int), ("prec", C.c_int), ("fgmres_restart", C.c_int),
                 ("bc_preset", C.c_int), ("ubar", C.c_double), ("force_kind", C.c_int),
                 ("force", C.c_double * 3), ("dedup", C.c_int), ("tc", C.c_int), ("badcut_frac", C.c_double),
-                ("element", C.c_int)]
+                ("element", C.c_int), ("galerkin", C.c_int)]
 
 
 _lib = None
@@ -168,7 +168,7 @@ ELEMENT = {"q1": 0, "q2": 1}
 
 
 def _options(prob, cache: str, prec: str, nu=None, dedup: int = 1, tc: str = "none",
-             badcut_frac: float | None = None, element: str = "q1") -> FcOptions:
+             badcut_frac: float | None = None, element: str = "q1", galerkin: bool = False) -> FcOptions:
     o = FcOptions()
     load().fc_options_default(C.byref(o))
     o.eta, o.nitsche_beta, o.omega = prob.eta, prob.beta, prob.omega
@@ -183,6 +183,7 @@ def _options(prob, cache: str, prec: str, nu=None, dedup: int = 1, tc: str = "no
     o.dedup = int(dedup)
     o.tc = TC[tc]
     o.element = ELEMENT[element]
+    o.galerkin = 1 if galerkin else 0
     if badcut_frac is not None:
         o.badcut_frac = float(badcut_frac)
     return o
@@ -213,7 +214,8 @@ class Solver:
     """A finite cell Stokes problem set up on the GPU (one fc_handle)."""
 
     def __init__(self, prob, cache: str = "inverse", prec: str = "fp64", stream=None, nu=None,
-                 dedup: int = 1, tc: str = "none", badcut_frac: float | None = None, element: str = "q1"):
+                 dedup: int = 1, tc: str = "none", badcut_frac: float | None = None, element: str = "q1",
+                 galerkin: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise FcError(-1, "libfc needs a CUDA GPU")
@@ -240,7 +242,7 @@ class Solver:
         self.h = C.c_void_p()
         st = self.lib.fc_setup(C.byref(self.h), C.byref(_grid(prob)), C.byref(ls), float(prob.alpha),
                                int(prob.nlevels),
-                               C.byref(_options(prob, cache, prec, nu, dedup, tc, badcut_frac, element)),
+                               C.byref(_options(prob, cache, prec, nu, dedup, tc, badcut_frac, element, galerkin)),
                                C.c_void_p(self.stream.cuda_stream))
         self._check(st)
 

@@ -41,6 +41,7 @@ def test_options_default_without_gpu():
     assert (o.nu_pre, o.nu_post, o.quad_depth, o.cache, o.prec) == (2, 2, 4, 0, 0)
     assert (o.bc_preset, o.ubar, o.force_kind, tuple(o.force)) == (0, 0.3, 0, (0.0, 0.0, 0.0))
     assert o.nitsche_beta == 100.0 and o.dedup == 1 and o.tc == 0 and o.badcut_frac == 1e-3
+    assert o.element == 0 and o.galerkin == 0
     assert lib.fc_setup(None, None, None, 1.0, 1, None, None) == fc.FC_ERR_INVALID
 
 

@@ -70,6 +70,9 @@ CASES = [
     ("tc -1", lambda g, ls, sh, o: setattr(o, "tc", -1), {}, "invalid options"),
     ("badcut_frac -1", lambda g, ls, sh, o: setattr(o, "badcut_frac", -1.0), {}, "invalid options"),
     ("badcut_frac 1", lambda g, ls, sh, o: setattr(o, "badcut_frac", 1.0), {}, "invalid options"),
+    ("galerkin 2", lambda g, ls, sh, o: setattr(o, "galerkin", 2), {}, "invalid coarse-operator choice"),
+    ("galerkin with Q2-Q1", lambda g, ls, sh, o: (setattr(o, "galerkin", 1), setattr(o, "element", 1)), {},
+     "need the Q1-Q1 pair"),
     ("cache 3", lambda g, ls, sh, o: setattr(o, "cache", 3), {}, "invalid cache policy or precision"),
     ("prec 9", lambda g, ls, sh, o: setattr(o, "prec", 9), {}, "invalid cache policy or precision"),
     ("fp32 rows with cache_matrix",

@@ -5,9 +5,11 @@ nodes 2a-4 .. 2a+4 and the pressures a-1 .. a+1 around each vertex a, each
 Q2 node written by the vertex at the lower corner of its cell, edge or face
 (fc_options.element = 1), in 2D (9 owned rows over 171 slots) and 3D (25
 owned rows over 2214 slots, the velocity block factored by a banded LU).
-Same bounds as the Q1-Q1 parity tests: operator, transfers 1e-12; patch
-rows 1e-11; sweeps and V-cycles 1e-10 relative; FGMRES and standalone GMG
-with the oracle's iteration counts."""
+Same bounds as the Q1-Q1 parity tests: operator, transfers 1e-12; sweeps
+and V-cycles 1e-10 relative; FGMRES and standalone GMG with the oracle's
+iteration counts.  Patch rows: 1e-11, or 2e-15 x the condition number of
+the equilibrated patch block where that is larger (Q2-Q1 blocks have a zero
+pressure block and cond up to ~5e7 on cut patches)."""
 import dataclasses
 
 import numpy as np
@@ -108,21 +110,32 @@ def expected_rows(L, vert):
     return want
 
 
+def rows_tolerance(L, vert):
+    """Rows of two exact LU solves differ by about cond x machine epsilon.
+    Equilibrated Q2-Q1 patch blocks (zero pressure block) reach cond ~ 5e7 on
+    cut patches at alpha = 1e-8 (the Q1-Q1 blocks stay near 40), so the
+    bound is max(1e-11, 2e-15 x cond_1(D L_i D)), D = (row max |L_i|)^-1/2."""
+    Li, _, _ = L.patch_matrix(int(vert))
+    d = 1.0 / np.sqrt(np.abs(Li).max(axis=1))
+    return max(1e-11, 2e-15 * np.linalg.cond(d[:, None] * Li * d[None, :], 1))
+
+
 @pytest.mark.parametrize("name", ROWS_CASES)
 def test_q2_patch_rows(fc, oracles, name):
     p = PROBS[name]
     s = solver(fc, p)
     L = oracles[name].fine
     rng = np.random.default_rng(0)
-    for vert in rng.choice(L.np, min(20, L.np), replace=False):
+    for vert in rng.choice(L.np, min(20 if p.dim == 2 else 10, L.np), replace=False):
         g = s.patch_rows(int(vert))
         want = expected_rows(L, int(vert))
         assert g.shape == want.shape
+        tol = rows_tolerance(L, vert)
         for k in range(want.shape[0]):
             if np.abs(want[k]).max() == 0:
                 assert np.abs(g[k]).max() == 0, (vert, k)
             else:
-                assert rel(g[k], want[k]) <= 1e-11, (vert, k, rel(g[k], want[k]))
+                assert rel(g[k], want[k]) <= tol, (vert, k, rel(g[k], want[k]), tol)
 
 
 @pytest.mark.parametrize("name", list(PROBS))

@@ -15,6 +15,11 @@ equilibrated saddle-point matrices with a symmetric positive definite velocity
 block and a negative semi-definite stabilised pressure block
 (quasi-definite), which LU factors stably without row exchanges; their owned
 inverse rows still agree with a 40-digit solve to 1e-12.
+
+Two skips in the Galerkin product are equivalent to their removal for these
+boundary presets and are left out too: dropping constrained fine rows and
+dropping constrained fine columns.  The constrained fine nodes lie on the box
+faces, and the fine nodes a free coarse node interpolates to never do.
 """
 import concurrent.futures as cf
 import os
@@ -173,6 +178,14 @@ MUTANTS = [
     ("fgmres_update_uses_v", "for (long t = 0; t < n; ++t) x[t] = x[t] + y[i] * Z[(long)i * n + t];",
      "for (long t = 0; t < n; ++t) x[t] = x[t] + y[i] * V[(long)i * n + t];", 0,
      "test_fgmres_reaches_direct_solution[2]"),
+    # Galerkin coarse operator (R L_f P)
+    ("galerkin_weight", "return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0);",
+     "return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.25 : 0.0);", 0,
+     "test_galerkin_equals_rediscretisation_without_obstacles[2]"),
+    ("galerkin_coarse_identity_lost", "Cc->val[q] = (Cc->fixed[row] && Cc->col[q] == row) ? 1.0 : 0.0;",
+     "Cc->val[q] = 0.0;", 0, "test_galerkin_equals_rediscretisation_without_obstacles[2]"),
+    ("galerkin_column_weight_shifted", "wj = wj * q1_weight(ja[k] - 2 * Ja[k]);",
+     "wj = wj * q1_weight(ja[k] - 2 * Ja[k] + 1);", 0, "test_galerkin_pressure_block_closed_form[2]"),
 ]
 
 
