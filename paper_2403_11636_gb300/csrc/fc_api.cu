@@ -868,7 +868,7 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     else CK(launch_galerkin(G, h->lev[li + 1].g, h->lev[li + 1].st, h->lev[li + 1].mask, L.st, h->stream));
     CK(launch_masks(G, L.mask, L.wfix, h->stream));
     if (dim == 3 && li > 0) {
-      CK(dalloc(h, &L.dead, (size_t)G.nn[1] + G.nn[2], 0));
+      CK(dalloc(h, &L.dead, (size_t)G.nn[0] + G.nn[1] + G.nn[2], 0));
       CK(launch_dead_layers(G, L.mask, L.dead, h->stream));
       L.g.dead_layer = L.dead;
     }

@@ -279,7 +279,7 @@ cudaError_t launch_masks(const LevelGeom& g, unsigned char* mask, double* wfix, 
 }
 
 // a layer stays flagged only if every node in it has all velocity
-// components constrained; any other node clears the flags of its y and z
+// components constrained; any other node clears the flags of its x, y and z
 // layers (every writer stores 0, so the races are benign)
 __global__ void dead_layer_kernel(LevelGeom g, const unsigned char* __restrict__ mask, unsigned char* out) {
   const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -287,12 +287,13 @@ __global__ void dead_layer_kernel(LevelGeom g, const unsigned char* __restrict__
   if ((mask[node] & 7) == 7) return;
   const unsigned u = (unsigned)node, nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
   const unsigned t = u / nx;
-  out[t % ny] = 0;
-  out[g.nn[1] + t / ny] = 0;
+  out[u - t * nx] = 0;
+  out[g.nn[0] + t % ny] = 0;
+  out[g.nn[0] + g.nn[1] + t / ny] = 0;
 }
 
 cudaError_t launch_dead_layers(const LevelGeom& g, const unsigned char* mask, unsigned char* out, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(out, 1, (size_t)g.nn[1] + g.nn[2], s);
+  cudaError_t e = cudaMemsetAsync(out, 1, (size_t)g.nn[0] + g.nn[1] + g.nn[2], s);
   if (e != cudaSuccess) return e;
   dead_layer_kernel<<<(unsigned)((g.nnodes + 255) / 256), 256, 0, s>>>(g, mask, out);
   note_launches(1);

@@ -40,10 +40,11 @@ struct LevelGeom {
   double alpha, eta, lambda, ubar;
   int qdepth, preset, force_kind;
   double force[3];
-  // 3D levels with a patch cache: one flag per y layer (nn[1] entries) then
-  // per z layer (nn[2]), set when every node of the layer has all its
-  // velocity components constrained (a Dirichlet wall); the patch applies
-  // skip such layers and out-of-grid ones.  Null: no flags.
+  // 3D levels with a patch cache: one flag per x layer (nn[0] entries), then
+  // per y layer (nn[1]) and per z layer (nn[2]), set when every node of the
+  // layer has all its velocity components constrained (a Dirichlet wall);
+  // the FP64 patch apply skips such layers and out-of-grid ones.  Null: no
+  // flags.
   const unsigned char* dead_layer;
 };
 
@@ -265,8 +266,8 @@ cudaError_t launch_galerkin(const LevelGeom& gc, const LevelGeom& gf, const doub
                             double* stc, cudaStream_t s);
 cudaError_t launch_coarsen_cells(const LevelGeom& gc, const LevelGeom& gf, const unsigned char* cclass_f,
                                  unsigned char* cclass_c, const double* estat_f, double* estat_c, cudaStream_t s);
-// y / z layer flags of g.dead_layer from the node masks (3D); out holds
-// nn[1] + nn[2] bytes
+// x / y / z layer flags of g.dead_layer from the node masks (3D); out holds
+// nn[0] + nn[1] + nn[2] bytes
 cudaError_t launch_dead_layers(const LevelGeom& g, const unsigned char* mask, unsigned char* out, cudaStream_t s);
 cudaError_t launch_rhs(const LevelGeom& g, const double* eF, const double* st,
                        const unsigned char* mask, const double* wfix, double* b, cudaStream_t s);

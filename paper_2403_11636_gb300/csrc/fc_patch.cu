@@ -563,43 +563,70 @@ __global__ void __launch_bounds__(256)
   double y[4] = {0.0, 0.0, 0.0, 0.0};  // 2D: y[3] stays zero
   // Live velocity slots.  Slots of out-of-grid nodes and of wall layers
   // (every velocity component constrained) have zero coefficients; in 3D the
-  // 5 x 5 x 5 velocity box is clipped in y and z to its live layers
-  // [y0, y1] x [z0, z1], so a patch walks nv = 15 (y1 - y0 + 1)(z1 - z0 + 1)
-  // velocity slots (z-planes of 75 slots, each holding one contiguous run of
-  // 15 per live y row) and then its 3^d pressure slots.  Patches of a warp
-  // are consecutive nodes of an x row and mostly share the clipping.
-  int nv = P::NU * DIM, seg = 75, vbase = 0;
+  // 5 x 5 x 5 velocity box is clipped per direction to its live layers
+  // [x0, x1] x [y0, y1] x [z0, z1]: a patch walks rows of rx = 3 (x1 - x0 + 1)
+  // contiguous slots (a y row of a z-plane holds 15), ny rows per z-plane,
+  // nz planes, then its 3^d pressure slots.  Patches of a warp are
+  // consecutive nodes of an x row and mostly share the clipping.
+  int nv = P::NU * DIM, rx = 15 * (DIM == 3 ? 5 : 1), ny = 1, vbase = 0;
   if (DIM == 3 && g.dead_layer) {
-    const unsigned char* dy = g.dead_layer;
-    const unsigned char* dz = g.dead_layer + g.nn[1];
-    int y0 = -2, y1 = 2, z0 = -2, z1 = 2;
+    const unsigned char* dx = g.dead_layer;
+    const unsigned char* dy = dx + g.nn[0];
+    const unsigned char* dz = dy + g.nn[1];
+    int x0 = -2, x1 = 2, y0 = -2, y1 = 2, z0 = -2, z1 = 2;
+    while (x0 <= 2 && (ia[0] + x0 < 0 || ia[0] + x0 > g.n[0] || dx[ia[0] + x0])) ++x0;
+    while (x1 >= x0 && (ia[0] + x1 < 0 || ia[0] + x1 > g.n[0] || dx[ia[0] + x1])) --x1;
     while (y0 <= 2 && (ia[1] + y0 < 0 || ia[1] + y0 > g.n[1] || dy[ia[1] + y0])) ++y0;
     while (y1 >= y0 && (ia[1] + y1 < 0 || ia[1] + y1 > g.n[1] || dy[ia[1] + y1])) --y1;
     while (z0 <= 2 && (ia[2] + z0 < 0 || ia[2] + z0 > g.n[2] || dz[ia[2] + z0])) ++z0;
     while (z1 >= z0 && (ia[2] + z1 < 0 || ia[2] + z1 > g.n[2] || dz[ia[2] + z1])) --z1;
-    seg = 15 * (y1 - y0 + 1);
-    nv = y1 >= y0 && z1 >= z0 ? seg * (z1 - z0 + 1) : 0;
-    vbase = (z0 + 2) * 75 + (y0 + 2) * 15;
+    rx = 3 * (x1 - x0 + 1);
+    ny = y1 - y0 + 1;
+    nv = x1 >= x0 && y1 >= y0 && z1 >= z0 ? rx * ny * (z1 - z0 + 1) : 0;
+    vbase = (z0 + 2) * 75 + (y0 + 2) * 15 + (x0 + 2) * 3;
   }
+  // a patch whose node has every velocity component constrained owns only
+  // its pressure: its velocity rows are zero and only row d is summed
+  const bool wall = DIM == 3 && (mask[i] & 7) == 7;
   const int tot = nv + P::NP;
-  int zi = 0, off = lane;  // loop index t = zi * seg + off while t < nv
+  int zi = 0, yi = 0, o = lane;  // loop index t = (zi ny + yi) rx + o while t < nv
   if (nv > 0)
-    while (off >= seg) { off -= seg; ++zi; }
-#pragma unroll 4
-  for (int t = lane; t < tot; t += TPP) {
-    const int j = t < nv ? vbase + zi * 75 + off : P::NU * DIM + (t - nv);
-    if (nv > 0) {
-      off += TPP;
-      while (off >= seg) { off -= seg; ++zi; }
+    while (o >= rx) {
+      o -= rx;
+      if (++yi == ny) { yi = 0; ++zi; }
     }
-    double rv = rp[soff[j]];
-    if (ND == 4) {
-      const double2* c2 = reinterpret_cast<const double2*>(cf + (size_t)j * 4);
-      double2 a = ldrow(c2, shared_rows), b = ldrow(c2 + 1, shared_rows);
-      y[0] += a.x * rv; y[1] += a.y * rv; y[2] += b.x * rv; y[3] += b.y * rv;
-    } else {
+  if (DIM == 3 && wall) {
+    for (int t = lane; t < tot; t += TPP) {
+      const int j = t < nv ? vbase + zi * 75 + yi * 15 + o : P::NU * DIM + (t - nv);
+      if (nv > 0) {
+        o += TPP;
+        while (o >= rx) {
+          o -= rx;
+          if (++yi == ny) { yi = 0; ++zi; }
+        }
+      }
+      y[ND - 1] += ldrow(cf + (size_t)j * ND + (ND - 1), shared_rows) * rp[soff[j]];
+    }
+  } else {
+#pragma unroll 4
+    for (int t = lane; t < tot; t += TPP) {
+      const int j = t < nv ? vbase + zi * 75 + yi * 15 + o : P::NU * DIM + (t - nv);
+      if (nv > 0) {
+        o += TPP;
+        while (o >= rx) {
+          o -= rx;
+          if (++yi == ny) { yi = 0; ++zi; }
+        }
+      }
+      double rv = rp[soff[j]];
+      if (ND == 4) {
+        const double2* c2 = reinterpret_cast<const double2*>(cf + (size_t)j * 4);
+        double2 a = ldrow(c2, shared_rows), b = ldrow(c2 + 1, shared_rows);
+        y[0] += a.x * rv; y[1] += a.y * rv; y[2] += b.x * rv; y[3] += b.y * rv;
+      } else {
 #pragma unroll
-      for (int k = 0; k < ND; ++k) y[k] += ldrow(cf + (size_t)j * ND + k, shared_rows) * rv;
+        for (int k = 0; k < ND; ++k) y[k] += ldrow(cf + (size_t)j * ND + k, shared_rows) * rv;
+      }
     }
   }
   if constexpr (TPP >= 4) {
