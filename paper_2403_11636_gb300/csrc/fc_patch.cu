@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(256)
   // contiguous slots (a y row of a z-plane holds 15), ny rows per z-plane,
   // nz planes, then its 3^d pressure slots.  Patches of a warp are
   // consecutive nodes of an x row and mostly share the clipping.
-  int nv = P::NU * DIM, rx = 15 * (DIM == 3 ? 5 : 1), ny = 1, vbase = 0;
+  int nv = P::NU * DIM, rx = nv, ny = 1, vbase = 0;  // unclipped: one run of all velocity slots
   if (DIM == 3 && g.dead_layer) {
     const unsigned char* dx = g.dead_layer;
     const unsigned char* dy = dx + g.nn[0];
