@@ -107,6 +107,12 @@ typedef struct or_level {
   long* pdof;    /* [nnodes][402] */
   int* pown;     /* [nnodes][4] local index of owned dof or -1 */
   double* pinv;  /* [nnodes][4][402] owned rows of L_i^{-1} */
+  /* adaptive grids (fc_oracle_amr.c): the prolongation from the next coarser
+   * level as a node-to-node sparse matrix (rows: nodes of this level), used
+   * by or_prolong_add / or_restrict in place of the uniform Q1 weights */
+  long* tp_rowptr;
+  long* tp_col;
+  double* tp_val;
 } or_level;
 
 #define PMAX 402
@@ -597,6 +603,7 @@ void or_level_free(or_level* L) {
   free(L->shape); free(L->bp); free(L->cell_bstart); free(L->elem);
   free(L->rowptr); free(L->col); free(L->val); free(L->rhs); free(L->fixed); free(L->wfix);
   free(L->pn); free(L->pdof); free(L->pown); free(L->pinv);
+  free(L->tp_rowptr); free(L->tp_col); free(L->tp_val);
   free(L);
 }
 
@@ -1177,6 +1184,17 @@ void or_owner_count(const or_level* L, int* count) {
 /* x_f += P e_c on every component; constrained fine DoFs are left alone. */
 void or_prolong_add(const or_level* F, const or_level* Cc, const double* ec, double* xf) {
   int dim = F->dim, nd = F->ndpn;
+  if (F->tp_rowptr) { /* adaptive grids: the stored node-to-node weights */
+    for (long node = 0; node < F->nnodes; ++node)
+      for (int c = 0; c < nd; ++c) {
+        long dof = node * nd + c;
+        if (F->fixed[dof]) continue;
+        double s = 0.0;
+        for (long q = F->tp_rowptr[node]; q < F->tp_rowptr[node + 1]; ++q) s = s + F->tp_val[q] * ec[F->tp_col[q] * nd + c];
+        xf[dof] = xf[dof] + s;
+      }
+    return;
+  }
   for (long node = 0; node < F->nnodes; ++node) {
     long ia[3];
     node_idx(F, node, ia);
@@ -1212,6 +1230,14 @@ void or_prolong_add(const or_level* F, const or_level* Cc, const double* ec, dou
 void or_restrict(const or_level* F, const or_level* Cc, const double* rf, double* bc) {
   int dim = F->dim, nd = F->ndpn;
   memset(bc, 0, sizeof(double) * (size_t)Cc->ndof);
+  if (F->tp_rowptr) { /* adaptive grids: the transpose of the stored weights */
+    for (long node = 0; node < F->nnodes; ++node)
+      for (long q = F->tp_rowptr[node]; q < F->tp_rowptr[node + 1]; ++q)
+        for (int c = 0; c < nd; ++c) bc[F->tp_col[q] * nd + c] = bc[F->tp_col[q] * nd + c] + F->tp_val[q] * rf[node * nd + c];
+    for (long k = 0; k < Cc->ndof; ++k)
+      if (Cc->fixed[k]) bc[k] = 0.0;
+    return;
+  }
   for (long node = 0; node < F->nnodes; ++node) {
     long ia[3];
     node_idx(F, node, ia);

@@ -62,6 +62,13 @@ def _load():
     else:
         build()
         lib = C.CDLL(_LIB)
+    _lib = _declare(lib)
+    return _lib
+
+
+def _declare(lib):
+    """ctypes signatures of the fc_oracle.c entry points (also in the
+    libraries of the variants that include it)."""
     vp, d, i, l = C.c_void_p, C.c_double, C.c_int, C.c_long
     P = C.POINTER
     lib.or_level_new.restype = vp
@@ -110,7 +117,6 @@ def _load():
     lib.or_num_threads.restype = i
     lib.or_set_threads.argtypes = [i]
     lib.or_bpoints_copy.argtypes = [vp, P(d), P(d), P(d), P(C.c_long)]
-    _lib = lib
     return lib
 
 
@@ -142,8 +148,8 @@ class Level:
     """One grid level with its finite cell discretisation."""
 
     def __init__(self, dim, n, lo, hi, shapes, alpha, qdepth, eta=1e-3, beta=100.0,
-                 omega=0.8, preset=0, force_kind=0, force=(0.0, 0.0, 0.0), ubar=0.3):
-        lib = _load()
+                 omega=0.8, preset=0, force_kind=0, force=(0.0, 0.0, 0.0), ubar=0.3, lib=None):
+        lib = _load() if lib is None else lib
         self.dim = int(dim)
         self.n = tuple(int(k) for k in n)
         nn = (C.c_int * 3)(*(list(self.n) + [1] * (3 - self.dim)))
@@ -616,3 +622,159 @@ class Q2MG:
         its = self.lib.q2_gmg_solve(self.h, _p(np.ascontiguousarray(b, dtype=np.float64)), _p(x), float(reduction),
                                     int(maxit), _p(rel))
         return x, its, float(rel[0])
+
+
+# ---------------------------------------------------------------------------
+# Adaptive quadtree grids (fc_oracle_amr.c, which includes fc_oracle.c)
+_SRC_AMR = os.path.join(_HERE, "fc_oracle_amr.c")
+_LIB_AMR = os.path.join(_HERE, "libfc_oracle_amr.so")
+_lib_amr = None
+
+
+def build_amr(force: bool = False) -> str:
+    """Compile fc_oracle_amr.c next to this file (when it or fc_oracle.c changed)."""
+    with _lock:
+        stale = (not os.path.exists(_LIB_AMR) or os.path.getmtime(_LIB_AMR) < os.path.getmtime(_SRC_AMR)
+                 or os.path.getmtime(_LIB_AMR) < os.path.getmtime(_SRC))
+        if force or stale:
+            tmp = _LIB_AMR + f".tmp{os.getpid()}"
+            compile_source(_SRC_AMR, tmp)
+            os.replace(tmp, _LIB_AMR)
+    return _LIB_AMR
+
+
+def _load_amr():
+    global _lib_amr
+    if _lib_amr is not None:
+        return _lib_amr
+    alt = os.environ.get("FC_ORACLE_AMR_LIB")
+    if alt:
+        lib = C.CDLL(alt)
+    else:
+        build_amr()
+        lib = C.CDLL(_LIB_AMR)
+    _declare(lib)
+    vp, i, l = C.c_void_p, C.c_int, C.c_long
+    P = C.POINTER
+    lib.amr_tree_fine.restype = vp
+    lib.amr_tree_fine.argtypes = [vp, P(C.c_int), i, i]
+    lib.amr_tree_coarsen.restype = vp
+    lib.amr_tree_coarsen.argtypes = [vp]
+    lib.amr_tree_free.argtypes = [vp]
+    lib.amr_tree_level.restype = i
+    lib.amr_tree_level.argtypes = [vp, i, i]
+    lib.amr_level_new.restype = vp
+    lib.amr_level_new.argtypes = [vp, P(vp), vp]
+    lib.amr_free_nodes.restype = l
+    lib.amr_free_nodes.argtypes = [vp, P(l)]
+    lib.amr_hanging.restype = l
+    lib.amr_hanging.argtypes = [vp, P(l), P(l)]
+    lib.amr_patch_rows.restype = i
+    lib.amr_patch_rows.argtypes = [vp, l, P(l), P(i), P(C.c_double)]
+    lib.amr_prolongation.restype = l
+    lib.amr_prolongation.argtypes = [vp, P(l), P(l), P(C.c_double)]
+    _lib_amr = lib
+    return lib
+
+
+class AMRLevel(Level):
+    """One level of an adaptive quadtree hierarchy (2D): an or_level whose
+    operator, patches and prolongation fc_oracle_amr.c built.  DoFs: the free
+    nodes in lattice order (y-major, x fastest), (u, v, p) per node."""
+
+    def __init__(self, handle, tree, lib, lattice_n, dim=2):
+        self.lib = lib
+        self.h = handle
+        self.tree = tree
+        self.dim = dim
+        self.n = tuple(lattice_n)
+        self.ndof = lib.or_ndof(handle)
+        self.nnodes = lib.or_nnodes(handle)
+        self.ndpn = dim + 1
+        self._assembled = True
+
+    def patch_inverse_rows(self, vert: int):
+        d = np.zeros(PMAX, dtype=np.int64); own = np.zeros(OMAX, dtype=np.int32)
+        rows = np.zeros((OMAX, PMAX))
+        n = self.lib.amr_patch_rows(self.h, int(vert), _p(d, C.c_long), _p(own, C.c_int), _p(rows))
+        return rows[:, :n].copy(), d[:n].copy(), own.copy()
+
+    def patch_dofs(self, vert: int):
+        _, d, own = self.patch_inverse_rows(vert)
+        return d, own
+
+    def free_vertices(self):
+        n = self.lib.amr_free_nodes(self.tree, None)
+        v = np.zeros(n, dtype=np.int64)
+        self.lib.amr_free_nodes(self.tree, _p(v, C.c_long))
+        return v
+
+    def hanging(self):
+        n = self.lib.amr_hanging(self.tree, None, None)
+        v = np.zeros(n, dtype=np.int64); par = np.zeros((n, 2), dtype=np.int64)
+        self.lib.amr_hanging(self.tree, _p(v, C.c_long), _p(par, C.c_long))
+        return v, par
+
+    def leaf_levels(self):
+        nx, ny = self.n
+        return np.array([[self.lib.amr_tree_level(self.tree, x, y) for x in range(nx)] for y in range(ny)])
+
+    def prolongation(self):
+        import scipy.sparse as sp
+        nnz = self.lib.amr_prolongation(self.h, None, None, None)
+        if nnz < 0:
+            return None
+        rp = np.zeros(self.nnodes + 1, dtype=np.int64); col = np.zeros(nnz, dtype=np.int64)
+        val = np.zeros(nnz)
+        self.lib.amr_prolongation(self.h, _p(rp, C.c_long), _p(col, C.c_long), _p(val))
+        return sp.csr_matrix((val, col, rp), shape=(self.nnodes, int(col.max()) + 1 if nnz else 0))
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                self.lib.or_level_free(self.h)
+                self.h = None
+            if getattr(self, "tree", None):
+                self.lib.amr_tree_free(self.tree)
+                self.tree = None
+        except Exception:
+            pass
+
+
+def amr_levels(prob):
+    """The adaptive hierarchy of a 2D problem with prob.amr_uniform = U >= 0:
+    lattice prob.n (the cells of the finest level), root grid
+    prob.n / 2^(L-1), every cell refined uniformly to level U, cut cells to
+    level L-1, 2:1 balanced; coarser levels by Algorithm 1.  Returns the
+    AMRLevel objects, coarsest first."""
+    assert prob.dim == 2 and prob.amr_uniform >= 0
+    lib = _load_amr()
+    L = prob.nlevels
+    R = L - 1
+    root = [k >> R for k in prob.n]
+    uni = [Level(2, (root[0] << r, root[1] << r), prob.lo, prob.hi, prob.shapes, prob.alpha, prob.qdepth,
+                 prob.eta, prob.beta, prob.omega, prob.preset, prob.force_kind, prob.force, prob.ubar, lib=lib)
+           for r in range(R + 1)]
+    uarr = (C.c_void_p * len(uni))(*[u.h for u in uni])
+    nr = (C.c_int * 2)(*root)
+    trees = [lib.amr_tree_fine(uni[R].h, nr, int(prob.amr_uniform), R)]
+    for _ in range(R):
+        trees.append(lib.amr_tree_coarsen(trees[-1]))
+    trees = trees[::-1]  # coarsest first
+    levels = []
+    for l in range(L):
+        h = lib.amr_level_new(trees[l], uarr, trees[l - 1] if l > 0 else None)
+        if not h:
+            raise RuntimeError("adaptive level construction failed (patch or adjacency overflow)")
+        levels.append(AMRLevel(h, trees[l], lib, prob.n))
+    for lv in levels:
+        lv._uniform = uni  # keep the element data alive
+    return levels
+
+
+class AMRMG(MG):
+    """Multigrid on the adaptive hierarchy: fc_oracle.c's V-cycle, FGMRES and
+    standalone GMG with the adaptive levels."""
+
+    def __init__(self, prob):
+        super().__init__(prob, levels=amr_levels(prob))

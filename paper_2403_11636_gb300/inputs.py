@@ -97,6 +97,8 @@ class Problem:
     ubar: float = 0.3                # inflow mean (channel preset)
     rtol: float = 1e-8
     restart: int = 30
+    amr_uniform: int = -1            # >= 0: adaptive 2D quadtree, cells refined uniformly to this
+                                     # level and cut cells to the finest (n = lattice of the finest level)
 
     def level_n(self, level: int) -> Tuple[int, ...]:
         """Cells per direction on level ``level`` (1 = coarsest, L = finest)."""
