@@ -139,6 +139,16 @@ typedef struct {
                           coarser discretisations, Sec. 3); 1 Galerkin products R L P of the
                           next finer operator with the V-cycle's transfers (no quadrature on
                           the coarser grids; constrained coarse DoFs keep identity rows). */
+  int amr_uniform;     /* -1: uniform grids (fc_grid.n cells on the finest level).  >= 0: adaptive
+                          2D quadtree grids (Sec. 3; Q1-Q1, cache_inverse, FP64 rows, 2D):
+                          fc_grid.n is the lattice of the finest level's cells, the root grid
+                          is fc_grid.n / 2^(depth-1); every cell is refined uniformly to level
+                          amr_uniform, a cell whose level set changes sign among its 3 x 3
+                          sample points to level depth-1, and the tree is 2:1 balanced across
+                          faces and corners; hanging nodes are constrained to the mean of
+                          their edge's end points; the coarser grids follow Algorithm 1.
+                          Vectors: the free nodes in lattice order (y-major, x fastest),
+                          (u, v, p) per node. */
 } fc_options;
 
 /* Fill the defaults:
@@ -148,7 +158,7 @@ typedef struct {
  *   bc_preset 0 (channel), ubar 0.3, force_kind 0 with force = 0;
  *   dedup 1 (shared class blocks; the Python binding's default too);
  *   tc 0 (CUDA cores), badcut_frac 1e-3, element 0 (Q1-Q1), galerkin 0
- *   (rediscretised coarser grids). */
+ *   (rediscretised coarser grids), amr_uniform -1 (uniform grids). */
 fc_status fc_options_default(fc_options* o);
 
 /* Build the hierarchy of `depth` levels (paper Sec. 3, Algorithm 1 on a
@@ -263,6 +273,14 @@ fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch,
  * Q2 nodes 2a-4 .. 2a+4 (x fastest, component inner), then the vertices
  * a-1 .. a+1.  Synchronises. */
 fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_host);
+
+/* Adaptive grids (fc_options.amr_uniform >= 0): the DoFs of the patch of
+ * free node `node` on `level` (velocity DoFs of the connected nodes in
+ * ascending order, then the pressures), at most `capacity` of them, into
+ * dofs_host, and their count into *n; fc_patch_rows then gives rows[3][n]
+ * (u, v, p of the node; zero rows for constrained velocity DoFs) in the same
+ * order.  FC_ERR_INVALID on uniform grids or a short buffer.  Synchronises. */
+fc_status fc_patch_dofs(fc_handle h, int level, long long node, long long* dofs_host, int capacity, int* n);
 
 /* Upper bound of the device bytes a handle for this problem holds at the
  * peak of fc_setup: everything it keeps, plus the largest setup temporary

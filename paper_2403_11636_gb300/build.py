@@ -19,8 +19,8 @@ LIB = os.path.join(HERE, "libfc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fc_geom.cu", "fc_assemble.cu", "fc_mg.cu", "fc_patch.cu", "fc_api.cu", "fc_noalloc.cu", "fc_batch.cu",
-           "fc_probe.cu", "fc_q2.cu"]
-EXTRA = {"fc_geom.cu": ["--fmad=false"]}
+           "fc_probe.cu", "fc_q2.cu", "fc_amr.cu"]
+EXTRA = {"fc_geom.cu": ["--fmad=false"], "fc_amr.cu": ["--fmad=false", "-Xcompiler", "-ffp-contract=off"]}
 
 
 def _nvcc() -> str:

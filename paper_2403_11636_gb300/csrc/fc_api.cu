@@ -330,6 +330,7 @@ fc_status smooth_level_pairs(fc_handle h, int li, double* x, const double* b, in
 }
 
 bool q2_path(fc_handle h);
+bool amr_path(fc_handle h);
 cudaError_t level_residual(fc_handle h, int li, const double* x, const double* b, double* r);
 cudaError_t level_restrict(fc_handle h, int li, const double* rf, double* bc);
 cudaError_t level_prolong_add(fc_handle h, int li, const double* ec, double* xf);
@@ -337,6 +338,18 @@ cudaError_t level_prolong_add(fc_handle h, int li, const double* ec, double* xf)
 fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nsweeps) {
   Level& L = h->lev[li];
   if (pair_path(h)) return smooth_level_pairs(h, li, x, b, nsweeps, false);
+  if (amr_path(h)) {
+    for (int s = 0; s < nsweeps; ++s) {
+      {
+        ProfScope ps(h, 1, 0.0);
+        CK(launch_amr_residual(L.amr, x, b, L.r, h->stream));
+      }
+      ProfScope ps(h, 0, (double)L.coef_bytes);
+      ProfScope pf(h, li == h->nlev - 1 ? 4 : -1, (double)L.coef_bytes);
+      CK(launch_amr_apply(L.amr, L.r, h->opt.omega, x, h->stream));
+    }
+    return FC_OK;
+  }
   if (q2_path(h)) {
     for (int s = 0; s < nsweeps; ++s) {
       {
@@ -482,11 +495,13 @@ fc_status read_scalar(fc_handle h, const double* dptr, double* out) {
 }
 
 bool q2_path(fc_handle h) { return h->opt.element == 1; }
+bool amr_path(fc_handle h) { return h->opt.amr_uniform >= 0; }
 
 // ---- operator pieces that depend on the element pair
 // r = b - L x (L x when b is null) on level li, unpadded
 cudaError_t level_residual(fc_handle h, int li, const double* x, const double* b, double* r) {
   Level& L = h->lev[li];
+  if (amr_path(h)) return launch_amr_residual(L.amr, x, b, r, h->stream);
   if (q2_path(h))
     return launch_q2_residual(h->dim, L.q2, L.q2A, L.q2B, L.q2T, L.q2mask, x, b, r, nullptr, nullptr, h->stream);
   return launch_residual(L.g, L.st, L.mask, x, b, r, nullptr, h->stream);
@@ -495,6 +510,7 @@ cudaError_t level_residual(fc_handle h, int li, const double* x, const double* b
 cudaError_t level_restrict(fc_handle h, int li, const double* rf, double* bc) {
   Level& L = h->lev[li];
   Level& C = h->lev[li - 1];
+  if (amr_path(h)) return launch_amr_restrict(L.amr, C.amr, rf, bc, h->stream);
   if (q2_path(h)) return launch_q2_restrict(h->dim, L.q2, C.q2, C.q2mask, rf, bc, h->stream);
   return launch_restrict(L.g, C.g, C.mask, rf, bc, h->stream);
 }
@@ -502,6 +518,7 @@ cudaError_t level_restrict(fc_handle h, int li, const double* rf, double* bc) {
 cudaError_t level_prolong_add(fc_handle h, int li, const double* ec, double* xf) {
   Level& L = h->lev[li];
   Level& C = h->lev[li - 1];
+  if (amr_path(h)) return launch_amr_prolong_add(L.amr, ec, xf, h->stream);
   if (q2_path(h)) return launch_q2_prolong_add(h->dim, L.q2, C.q2, L.q2mask, ec, xf, h->stream);
   return launch_prolong_add(L.g, C.g, L.mask, ec, xf, h->stream);
 }
@@ -613,6 +630,142 @@ fc_status setup_q2(fc_handle h, const fc_grid* g, const fc_options* o, int nshap
   return FC_OK;
 }
 
+// Adaptive 2D quadtree hierarchy (fc_amr.cu): trees from the finest down
+// (Algorithm 1), per level the nodes and leaves on the host, the element
+// data of the leaves on the GPU (the element kernel on the uniform grid of
+// each leaf level), the constrained assembly, patches and transfers on the
+// host, then the device arrays, the patch rows (levels above the coarsest)
+// and the dense inverse of the coarsest operator.
+fc_status setup_amr(fc_handle h, const fc_grid* g, const fc_options* o, const std::vector<Shape>& hs, int nshape,
+                    double alpha, int depth) {
+  const int R = depth - 1;
+  const int nroot[2] = {g->n[0] >> R, g->n[1] >> R};
+  std::vector<AmrTree> trees(depth);
+  trees[depth - 1] = amr_tree_fine(hs, g->lo, g->hi, nroot, o->amr_uniform, R);
+  for (int li = depth - 2; li >= 0; --li) trees[li] = amr_tree_coarsen(trees[li + 1]);
+  std::vector<AmrHost> H(depth);
+  std::vector<std::vector<std::vector<long long>>> adj(depth);
+  for (int li = 0; li < depth; ++li) amr_structure(trees[li], H[li], adj[li]);
+  std::vector<int> maxn(depth, 0);
+  for (int li = 0; li < depth; ++li) {
+    Level& L = h->lev[li];
+    L.g = make_geom(g, nshape, h->d_shapes, alpha, o, 0);
+    AmrHost& Hl = H[li];
+    const size_t nleaf = Hl.leaf.size() / 3;
+    std::vector<double> eA(nleaf * 16), eB(nleaf * 32), eF(nleaf * 8);
+    for (int r = 0; r <= R; ++r) {
+      std::vector<long long> slots;
+      std::vector<long long> cells = amr_leaf_cells(trees[li], Hl, r, &slots);
+      if (cells.empty()) continue;
+      const long long n = (long long)cells.size();
+      const LevelGeom Gr = make_geom(g, nshape, h->d_shapes, alpha, o, R - r);
+      long long* dcells = nullptr;
+      double *dA = nullptr, *dB = nullptr, *dF = nullptr;
+      CK(dalloc(h, &dcells, (size_t)n, -1));
+      CK(dalloc(h, &dA, (size_t)n * 16, -1));
+      CK(dalloc(h, &dB, (size_t)n * 32, -1));
+      CK(dalloc(h, &dF, (size_t)n * 8, -1));
+      CK(cudaMemcpyAsync(dcells, cells.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, h->stream));
+      CK(launch_cell_elements_list(Gr, dcells, n, dA, dB, dF, h->d_err, h->stream));
+      std::vector<double> tA((size_t)n * 16), tB((size_t)n * 32), tF((size_t)n * 8);
+      CK(cudaMemcpyAsync(tA.data(), dA, sizeof(double) * tA.size(), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(tB.data(), dB, sizeof(double) * tB.size(), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(tF.data(), dF, sizeof(double) * tF.size(), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      for (long long q = 0; q < n; ++q) {
+        std::copy(&tA[q * 16], &tA[q * 16] + 16, &eA[slots[q] * 16]);
+        std::copy(&tB[q * 32], &tB[q * 32] + 32, &eB[slots[q] * 32]);
+        std::copy(&tF[q * 8], &tF[q * 8] + 8, &eF[slots[q] * 8]);
+      }
+      dfree(h, dcells); dfree(h, dA); dfree(h, dB); dfree(h, dF);
+    }
+    fc_status st = check_err(h);
+    if (st != FC_OK) return st;
+    maxn[li] = amr_assemble(trees[li], L.g, eA, eB, eF, adj[li], Hl);
+    if (li > 0) amr_transfers(trees[li], Hl, trees[li - 1], H[li - 1]);
+    if (maxn[li] > 160) return fail(h, FC_ERR_INVALID, "adaptive patch larger than 160 DoFs");
+  }
+  for (int li = 0; li < depth; ++li) {
+    Level& L = h->lev[li];
+    AmrHost& Hl = H[li];
+    AmrLevel& A = L.amr;
+    A.nfree = Hl.nfree;
+    A.maxn = maxn[li];
+    const long long ndof = Hl.nfree * 3;
+    L.g.ndof = ndof;
+    L.g.nnodes = Hl.nfree;
+    auto up = [&](auto** dst, const auto& v, int part) -> cudaError_t {
+      cudaError_t e = dalloc(h, dst, std::max<size_t>(v.size(), 1), part);
+      if (e != cudaSuccess || v.empty()) return e;
+      return cudaMemcpyAsync(*dst, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice, h->stream);
+    };
+    CK(up(&A.rowptr, Hl.rowptr, 0));
+    CK(up(&A.col, Hl.col, 0));
+    CK(up(&A.val, Hl.val, 0));
+    CK(up(&A.fixed, Hl.fixed, 0));
+    CK(up(&A.pstart, Hl.pstart, 1));
+    CK(up(&A.pdof, Hl.pdof, 1));
+    CK(up(&A.pown, Hl.pown, 1));
+    if (li > 0) {
+      CK(up(&A.prp, Hl.prp, 0));
+      CK(up(&A.pcl, Hl.pcl, 0));
+      CK(up(&A.pvl, Hl.pvl, 0));
+      CK(up(&A.rrp, Hl.rrp, 0));
+      CK(up(&A.rcl, Hl.rcl, 0));
+      CK(up(&A.rvl, Hl.rvl, 0));
+    }
+    CK(dalloc(h, &L.x, (size_t)ndof, 2));
+    CK(dalloc(h, &L.b, (size_t)ndof, 2));
+    CK(dalloc(h, &L.r, (size_t)ndof, 2));
+    if (li == depth - 1)
+      CK(cudaMemcpyAsync(L.b, Hl.rhs.data(), sizeof(double) * ndof, cudaMemcpyHostToDevice, h->stream));
+    if (li > 0) {
+      const size_t nrows = (size_t)3 * Hl.pstart[Hl.nfree];
+      CK(dalloc(h, &A.rows, nrows, 1));
+      {
+        ProfScope ps(h, 3, 0.0);
+        CK(launch_amr_patch_rows(A, h->d_err, h->stream));
+      }
+      L.coef = A.rows;
+      L.coef_bytes = nrows * 8;
+      unsigned long long act = 0;
+      for (long long i = 0; i < Hl.nfree; ++i) {
+        int nown = 0;
+        for (int c = 0; c < 3; ++c) nown += Hl.pown[i * 3 + c] >= 0;
+        act += (unsigned long long)(Hl.pstart[i + 1] - Hl.pstart[i]) * nown;
+      }
+      L.active_rows = act;
+      CK(cudaStreamSynchronize(h->stream));
+      fc_status st = check_err(h);
+      if (st != FC_OK) return st;
+    }
+  }
+  {
+    Level& C = h->lev[0];
+    const long long n = C.g.ndof;
+    if (n > 4096) return fail(h, FC_ERR_INVALID, "coarsest level too large for the dense solve; increase depth");
+    h->coarse_n = (int)n;
+    double *work = nullptr, *dsc = nullptr;
+    int* piv = nullptr;
+    CK(dalloc(h, &work, (size_t)n * n, -1));
+    CK(dalloc(h, &dsc, (size_t)2 * n, -1));
+    CK(dalloc(h, &piv, (size_t)n, -1));
+    CK(dalloc(h, &h->coarse_inv, (size_t)n * n, 3));
+    CK(launch_amr_dense(C.amr, work, h->stream));
+    CK(launch_dense_inverse((int)n, work, h->coarse_inv, piv, dsc, h->d_err, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    dfree(h, work);
+    dfree(h, dsc);
+    dfree(h, piv);
+    fc_status st = check_err(h);
+    if (st != FC_OK) return st;
+  }
+  fc_status st = alloc_krylov(h);
+  if (st != FC_OK) return st;
+  CK(cudaStreamSynchronize(h->stream));
+  return FC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -637,6 +790,7 @@ fc_status fc_options_default(fc_options* o) {
   o->badcut_frac = 1e-3;
   o->element = 0;
   o->galerkin = 0;
+  o->amr_uniform = -1;
   return FC_OK;
 }
 
@@ -760,6 +914,11 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
     return fail(h, FC_ERR_INVALID, "reduced-precision storage applies to cache_inverse only");
   if (o->element != 0 && o->element != 1) return fail(h, FC_ERR_INVALID, "invalid element pair");
   if (o->galerkin != 0 && o->galerkin != 1) return fail(h, FC_ERR_INVALID, "invalid coarse-operator choice");
+  if (o->amr_uniform < -1 || o->amr_uniform > depth - 1)
+    return fail(h, FC_ERR_INVALID, "amr_uniform must be -1 or a level of the hierarchy");
+  if (o->amr_uniform >= 0 && (g->dim != 2 || o->element != 0 || o->galerkin || o->cache != FC_CACHE_INVERSE ||
+                              o->prec != FC_PREC_FP64))
+    return fail(h, FC_ERR_INVALID, "adaptive grids run in 2D with the Q1-Q1 pair, cache_inverse and FP64 rows");
   if (o->galerkin && o->element != 0) return fail(h, FC_ERR_INVALID, "Galerkin coarse operators need the Q1-Q1 pair");
   if (o->element == 1 && (o->cache != FC_CACHE_INVERSE || o->prec != FC_PREC_FP64))
     return fail(h, FC_ERR_INVALID, "the Q2-Q1 pair runs with cache_inverse and FP64 rows");
@@ -794,6 +953,12 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   if (nshape) CK(cudaMemcpyAsync(h->d_shapes, hs.data(), sizeof(Shape) * nshape, cudaMemcpyHostToDevice, h->stream));
   if (o->element == 1) {
     fc_status st = setup_q2(h, g, o, nshape, alpha, depth);
+    if (st != FC_OK) return st;
+    h->ready = true;
+    return FC_OK;
+  }
+  if (o->amr_uniform >= 0) {
+    fc_status st = setup_amr(h, g, o, hs, nshape, alpha, depth);
     if (st != FC_OK) return st;
     h->ready = true;
     return FC_OK;
@@ -1303,12 +1468,41 @@ fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch, si
   return FC_OK;
 }
 
+fc_status fc_patch_dofs(fc_handle h, int level, long long node, long long* dofs_host, int capacity, int* n) {
+  fc_status st = level_ok(h, level, 2);
+  if (st != FC_OK) return st;
+  const Level& L = h->lev[level - 1];
+  if (!amr_path(h)) return fail(h, FC_ERR_INVALID, "patch DoF lists are given for adaptive grids");
+  if (!dofs_host || !n || node < 0 || node >= L.amr.nfree) return fail(h, FC_ERR_INVALID, "bad patch");
+  long long se[2] = {0, 0};
+  CK(cudaMemcpyAsync(se, L.amr.pstart + node, sizeof(se), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int cnt = (int)(se[1] - se[0]);
+  if (cnt > capacity) return fail(h, FC_ERR_INVALID, "patch DoF buffer too short");
+  std::vector<int> d((size_t)std::max(cnt, 1));
+  CK(cudaMemcpyAsync(d.data(), L.amr.pdof + se[0], sizeof(int) * cnt, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int t = 0; t < cnt; ++t) dofs_host[t] = d[t];
+  *n = cnt;
+  return FC_OK;
+}
+
 fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_host) {
   fc_status st = level_ok(h, level, 2);
   if (st != FC_OK) return st;
   const Level& L = h->lev[level - 1];
   if (!rows_host || node < 0 || node >= L.g.nnodes) return fail(h, FC_ERR_INVALID, "bad patch");
   if (h->opt.cache != FC_CACHE_INVERSE || !L.coef) return fail(h, FC_ERR_INVALID, "no cached rows");
+  if (amr_path(h)) {
+    long long se[2] = {0, 0};
+    CK(cudaMemcpyAsync(se, L.amr.pstart + node, sizeof(se), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const size_t n = (size_t)(se[1] - se[0]);
+    CK(cudaMemcpyAsync(rows_host, L.amr.rows + 3 * se[0], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FC_OK;
+  }
   if (q2_path(h)) {
     // 2D: 9 owned rows x 171 slots, stored [slot][10]; 3D: 25 x 2214, stored [row][2240]
     const bool d3 = h->dim == 3;
@@ -1407,6 +1601,10 @@ fc_status fc_destroy(fc_handle h) {
     dfree(h, L.st2); dfree(h, L.xp2); dfree(h, L.bp2); dfree(h, L.prow);
     dfree(h, L.st32); dfree(h, L.d32); dfree(h, L.b32);
     dfree(h, L.q2mask); dfree(h, L.q2A); dfree(h, L.q2B); dfree(h, L.q2T); dfree(h, L.q2rpv); dfree(h, L.q2rpp);
+    dfree(h, L.amr.rowptr); dfree(h, L.amr.col); dfree(h, L.amr.val); dfree(h, L.amr.fixed);
+    dfree(h, L.amr.pstart); dfree(h, L.amr.pdof); dfree(h, L.amr.pown);
+    dfree(h, L.amr.prp); dfree(h, L.amr.pcl); dfree(h, L.amr.pvl);
+    dfree(h, L.amr.rrp); dfree(h, L.amr.rcl); dfree(h, L.amr.rvl);
   }
   if (h->coarse_graph) cudaGraphExecDestroy(h->coarse_graph);
   dfree(h, h->d_shapes); dfree(h, h->d_err); dfree(h, h->coarse_inv);

@@ -1859,7 +1859,8 @@ fc_status create_batch(fc_batch* out, const fc_handle* handles, int nprob, void*
     if (h->dim != B->dim) return bfail(B, FC_ERR_INVALID, "all problems of a batch must have the same dimension");
     if (h->opt.cache != FC_CACHE_INVERSE || h->opt.prec == FC_PREC_DF64)
       return bfail(B, FC_ERR_INVALID, "batches take cache_inverse handles with fp64, fp32 or bf16 rows");
-    if (h->opt.element != 0) return bfail(B, FC_ERR_INVALID, "batches take Q1-Q1 handles");
+    if (h->opt.element != 0 || h->opt.amr_uniform >= 0)
+      return bfail(B, FC_ERR_INVALID, "batches take Q1-Q1 handles on uniform grids");
     if (h->opt.prec != B->prec || h->restart != B->m || h->opt.nu_pre != B->nu_pre || h->opt.nu_post != B->nu_post)
       return bfail(B, FC_ERR_INVALID, "row precision, FGMRES restart and sweep counts must agree across the batch");
     if (B->f32 && h->opt.tc != B->tc)

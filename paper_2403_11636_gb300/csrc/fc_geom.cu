@@ -246,15 +246,19 @@ __global__ void __launch_bounds__(Entries<DIM, Q>::WARPS * 32)
     cell_elements_kernel(LevelGeom g, double* __restrict__ eA, double* __restrict__ eB,
                          double* __restrict__ eF, double* __restrict__ estat,
                          unsigned* __restrict__ d_err, const double* __restrict__ refA,
-                         const double* __restrict__ refB, unsigned char* __restrict__ cclass) {
+                         const double* __restrict__ refB, unsigned char* __restrict__ cclass,
+                         const long long* __restrict__ cell_list, long long nlist) {
   using E = Entries<DIM, Q>;
   constexpr int NL = E::NV, NP = E::NP, WARPS = E::WARPS;
   __shared__ WarpShared<DIM, Q> wsh[WARPS];
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   WarpShared<DIM, Q>& S = wsh[wib];
-  const long long cell = (long long)blockIdx.x * WARPS + wib;
-  if (cell >= g.ncell) return;
+  // with a cell list (the leaves of one level of an adaptive grid), slot q
+  // integrates cell cell_list[q] of g and writes its outputs at position q
+  const long long slot = (long long)blockIdx.x * WARPS + wib;
+  if (slot >= (cell_list ? nlist : g.ncell)) return;
+  const long long cell = cell_list ? cell_list[slot] : slot;
   const unsigned FULL = 0xffffffffu;
 
   long long ci = cell % g.n[0];
@@ -662,9 +666,9 @@ __global__ void __launch_bounds__(Entries<DIM, Q>::WARPS * 32)
   // to rounding, but bit-identical across plain cells, which makes the
   // patch blocks of uncut regions bit-identical (patch classes).
   const bool plain = refA != nullptr && !split && nbnd == 0 && !al_mixed && al_first > 0.0;
-  double* A = eA + cell * NL * NL;
-  double* B = eB + cell * DIM * NL * NP;
-  double* F = eF + cell * DIM * NL;
+  double* A = eA + slot * NL * NL;
+  double* B = eB + slot * DIM * NL * NP;
+  double* F = eF + slot * DIM * NL;
 #pragma unroll
   for (int t = 0; t < E::PER; ++t) {
     EntryId id = entry_of<DIM, Q>(lane + 32 * t);
@@ -678,21 +682,24 @@ __global__ void __launch_bounds__(Entries<DIM, Q>::WARPS * 32)
       F[id.c * NL + id.a] = acc[t];
     }
   }
-  if (lane == 0 && cclass) cclass[cell] = plain ? (al_first == 1.0 ? 1 : 2) : 0;
+  if (lane == 0 && cclass) cclass[slot] = plain ? (al_first == 1.0 ? 1 : 2) : 0;
   if (lane == 0 && estat) {
-    estat[cell * 4 + 0] = fluid_volume;
-    estat[cell * 4 + 1] = bmeasure;
-    estat[cell * 4 + 2] = (double)nvol;
-    estat[cell * 4 + 3] = (double)nbnd;
+    estat[slot * 4 + 0] = fluid_volume;
+    estat[slot * 4 + 1] = bmeasure;
+    estat[slot * 4 + 2] = (double)nvol;
+    estat[slot * 4 + 3] = (double)nbnd;
   }
 }
 
 template <int DIM, int Q>
 void run_elements(const LevelGeom& g, double* eA, double* eB, double* eF, double* estat, unsigned* d_err,
-                  const double* refA, const double* refB, unsigned char* cclass, cudaStream_t s) {
+                  const double* refA, const double* refB, unsigned char* cclass, cudaStream_t s,
+                  const long long* cell_list = nullptr, long long nlist = 0) {
   constexpr int W = Entries<DIM, Q>::WARPS;
-  const long long blocks = (g.ncell + W - 1) / W;
-  cell_elements_kernel<DIM, Q><<<(unsigned)blocks, W * 32, 0, s>>>(g, eA, eB, eF, estat, d_err, refA, refB, cclass);
+  const long long blocks = ((cell_list ? nlist : g.ncell) + W - 1) / W;
+  if (blocks == 0) return;
+  cell_elements_kernel<DIM, Q><<<(unsigned)blocks, W * 32, 0, s>>>(g, eA, eB, eF, estat, d_err, refA, refB, cclass,
+                                                                   cell_list, nlist);
 }
 
 }  // namespace
@@ -702,6 +709,14 @@ cudaError_t launch_cell_elements(const LevelGeom& g, double* eA, double* eB, dou
                                  unsigned char* cclass, cudaStream_t s) {
   if (g.dim == 2) run_elements<2, 1>(g, eA, eB, eF, estat, d_err, refA, refB, cclass, s);
   else run_elements<3, 1>(g, eA, eB, eF, estat, d_err, refA, refB, cclass, s);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cell_elements_list(const LevelGeom& g, const long long* cells, long long ncells, double* eA,
+                                      double* eB, double* eF, unsigned* d_err, cudaStream_t s) {
+  if (g.dim == 2) run_elements<2, 1>(g, eA, eB, eF, nullptr, d_err, nullptr, nullptr, nullptr, s, cells, ncells);
+  else run_elements<3, 1>(g, eA, eB, eF, nullptr, d_err, nullptr, nullptr, nullptr, s, cells, ncells);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -79,6 +79,43 @@ struct Q2Grid {
 inline __host__ __device__ int nslot_u(int dim) { return dim == 3 ? 375 : 50; }
 inline __host__ __device__ int nslot(int dim) { return dim == 3 ? 402 : 59; }
 
+// Adaptive 2D quadtree grids (fc_amr.cu): the tree as the leaf level of
+// every lattice cell (the cells of the finest level R), the host half of a
+// level, and its device arrays.
+struct AmrTree {
+  int R = 0, nroot[2] = {0, 0}, NX = 0, NY = 0;
+  std::vector<unsigned char> lev;  // [NY][NX]
+};
+
+struct AmrHost {
+  long long nfree = 0;
+  std::vector<long long> fid, hp, fvert;  // vertex -> free node, hanging parents, free node -> vertex
+  std::vector<int> leaf;                  // (X, Y, level) per leaf, lattice order
+  std::vector<int> rowptr, col;           // operator, node-interleaved (u, v, p)
+  std::vector<double> val, rhs, wfix;
+  std::vector<unsigned char> fixed;
+  std::vector<long long> pstart;          // patch DoF offsets
+  std::vector<int> pdof, pown;            // patch DoFs; owned local index (3 per patch) or -1
+  std::vector<int> prp, pcl, rrp, rcl;    // prolongation from the coarser level and its transpose
+  std::vector<double> pvl, rvl;
+};
+
+struct AmrLevel {
+  long long nfree = 0;
+  int maxn = 0;                  // largest patch
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* val = nullptr;
+  unsigned char* fixed = nullptr;
+  long long* pstart = nullptr;
+  int* pdof = nullptr;
+  int* pown = nullptr;
+  double* rows = nullptr;        // 3 owned rows per patch, at 3 * pstart[p], row-major over the patch
+  int *prp = nullptr, *pcl = nullptr, *rrp = nullptr, *rcl = nullptr;
+  double *pvl = nullptr, *rvl = nullptr;
+  unsigned long long rows_flop = 0;  // 2 x (patch DoFs x free owned DoFs) summed over the patches
+};
+
 struct Level {
   LevelGeom g;
   double* st = nullptr;         // stencil, SPN * 3^d * nnodes
@@ -132,7 +169,26 @@ struct Level {
   double* q2T = nullptr;
   double* q2rpv = nullptr;
   double* q2rpp = nullptr;
+  // adaptive 2D grids (fc_options.amr_uniform >= 0, see fc_amr.cu)
+  AmrLevel amr{};
 };
+
+AmrTree amr_tree_fine(const std::vector<Shape>& sh, const double* lo, const double* hi, const int* nroot, int U,
+                      int R);
+AmrTree amr_tree_coarsen(const AmrTree& F);
+bool amr_structure(const AmrTree& T, AmrHost& H, std::vector<std::vector<long long>>& adj);
+int amr_assemble(const AmrTree& T, const LevelGeom& g, const std::vector<double>& eA, const std::vector<double>& eB,
+                 const std::vector<double>& eF, const std::vector<std::vector<long long>>& adj, AmrHost& H);
+void amr_transfers(const AmrTree& T, AmrHost& H, const AmrTree& Tc, const AmrHost& Hc);
+std::vector<long long> amr_leaf_cells(const AmrTree& T, const AmrHost& H, int level, std::vector<long long>* slots);
+cudaError_t launch_amr_residual(const AmrLevel& A, const double* x, const double* b, double* r, cudaStream_t s);
+cudaError_t launch_amr_apply(const AmrLevel& A, const double* r, double omega, double* x, cudaStream_t s);
+cudaError_t launch_amr_prolong_add(const AmrLevel& F, const double* ec, double* xf, cudaStream_t s);
+cudaError_t launch_amr_restrict(const AmrLevel& F, const AmrLevel& C, const double* rf, double* bc, cudaStream_t s);
+cudaError_t launch_amr_dense(const AmrLevel& A, double* M, cudaStream_t s);
+// owned rows of every patch (fc_patch.cu): one CTA per patch, L_i gathered
+// from the CSR, equilibrated LU with partial pivoting, rows of the owned DoFs
+cudaError_t launch_amr_patch_rows(const AmrLevel& A, unsigned* d_err, cudaStream_t s);
 
 struct Profile {
   bool on = false;
@@ -248,6 +304,10 @@ cudaError_t launch_cell_elements(const LevelGeom& g, double* eA, double* eB, dou
                                  unsigned char* cclass, cudaStream_t s);
 // Q2-Q1 element data: eA [cell][3^d][3^d], eB [cell][d][3^d][2^d],
 // eF [cell][d][3^d]; estat as above (nullable)
+// element data of the listed cells of g (adaptive grids: the leaves of one
+// level), outputs in list order
+cudaError_t launch_cell_elements_list(const LevelGeom& g, const long long* cells, long long ncells, double* eA,
+                                      double* eB, double* eF, unsigned* d_err, cudaStream_t s);
 cudaError_t launch_cell_elements_q2(const LevelGeom& g, double* eA, double* eB, double* eF, double* estat,
                                     unsigned* d_err, cudaStream_t s);
 // patch classes: node class from its 2^d cells, patch class from its 5^d

@@ -67,7 +67,8 @@ extern "C" fc_status fc_smooth_noalloc(fc_handle h, int level, double* x, const 
   if (!h->ready) return fail(h, FC_ERR_INVALID, "handle not set up (fc_setup failed)");
   if (level < 2 || level > h->nlev) return fail(h, FC_ERR_INVALID, "level out of range");
   if (!x || !b || nsweeps < 0) return fail(h, FC_ERR_INVALID, "bad smoother arguments");
-  if (h->opt.element != 0) return fail(h, FC_ERR_INVALID, "fc_smooth_noalloc runs the Q1-Q1 pair only");
+  if (h->opt.element != 0 || h->opt.amr_uniform >= 0)
+    return fail(h, FC_ERR_INVALID, "fc_smooth_noalloc runs the Q1-Q1 pair on uniform grids only");
   {
     // the scratch array is looked up on the current device: it must be the
     // device that holds the handle's operator and patch cache

@@ -2521,6 +2521,65 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+// ---- adaptive 2D grids: owned rows of the patches (variable size).  One
+// CTA per patch: L_i gathered from the CSR rows of the patch DoFs (binary
+// search in each sorted row), symmetrically equilibrated D L_i D with
+// D = |diag L_i|^-1/2, LU with partial pivoting, and the owned columns of
+// (D L_i D)^-1 (= its owned rows, L_i symmetric), de-scaled; rows of absent
+// owned DoFs are zero.
+__global__ void __launch_bounds__(256)
+    amr_patch_rows_kernel(long long np, const long long* __restrict__ pstart, const int* __restrict__ pdof,
+                          const int* __restrict__ pown, const int* __restrict__ rp, const int* __restrict__ col,
+                          const double* __restrict__ val, double* __restrict__ rows, unsigned* d_err) {
+  extern __shared__ double am[];
+  const long long p = blockIdx.x;
+  const long long s0 = pstart[p];
+  const int n = (int)(pstart[p + 1] - s0);
+  double* K = am;                 // n x n row-major
+  double* dsc = K + (size_t)n * n;
+  double* z = dsc + n;            // 3 x n
+  int* piv = reinterpret_cast<int*>(z + 3 * n);
+  int* flag = piv + n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) *flag = 0;
+  for (int t = tid; t < n * n; t += nt) {
+    const int a = t / n, b = t % n;
+    const int ra = pdof[s0 + a], cb = pdof[s0 + b];
+    double v = 0.0;
+    int lo = rp[ra], hi = rp[ra + 1] - 1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int c = col[mid];
+      if (c == cb) { v = val[mid]; break; }
+      if (c < cb) lo = mid + 1; else hi = mid - 1;
+    }
+    K[t] = v;
+  }
+  __syncthreads();
+  for (int a = tid; a < n; a += nt) {
+    const double d = fabs(K[(size_t)a * n + a]);
+    dsc[a] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
+  }
+  __syncthreads();
+  for (int t = tid; t < n * n; t += nt) K[t] = dsc[t / n] * K[t] * dsc[t % n];
+  __syncthreads();
+  cta_lu(K, n, n, piv, flag);
+  if (tid < 3) {
+    double* zz = z + tid * n;
+    const int o = pown[p * 3 + tid];
+    for (int j = 0; j < n; ++j) zz[j] = (o >= 0 && j == o) ? 1.0 : 0.0;
+    if (o >= 0) lu_solve_vec(K, n, n, piv, zz);
+  }
+  __syncthreads();
+  double* out = rows + 3 * s0;
+  for (int t = tid; t < 3 * n; t += nt) {
+    const int k = t / n, j = t % n;
+    const int o = pown[p * 3 + k];
+    out[t] = o >= 0 ? dsc[o] * z[t] * dsc[j] : 0.0;
+  }
+  if (tid == 0 && *flag) atomicOr(d_err, kErrSingularPatch);
+}
+
 // 3D apply: a warp per vertex; lane l sums the 25 rows over the slots
 // l, l + 32, ... (coalesced row loads, residual gathers from the padded
 // copies), a reduce-scatter leaves row l's sum in lane l, and lanes 0..24
@@ -2732,6 +2791,18 @@ cudaError_t launch_q2_apply(int dim, const Q2Grid& q, const double* coef, const 
     const long long threads = q.np * 8;
     q2_apply_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(q, coef, mask, rpv, rpp, omega, x);
   }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_amr_patch_rows(const AmrLevel& A, unsigned* d_err, cudaStream_t s) {
+  if (A.nfree == 0) return cudaSuccess;
+  const int n = A.maxn;
+  const size_t smem = sizeof(double) * ((size_t)n * n + 4 * (size_t)n) + sizeof(int) * ((size_t)n + 1);
+  cudaError_t e = cudaFuncSetAttribute(amr_patch_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  amr_patch_rows_kernel<<<(unsigned)A.nfree, 256, smem, s>>>(A.nfree, A.pstart, A.pdof, A.pown, A.rowptr, A.col,
+                                                             A.val, A.rows, d_err);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -20,7 +20,7 @@ CACHE = {"inverse": 0, "matrix": 1, "none": 2}
 PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "df64": 3}
 EXPORTS = ("fc_options_default", "fc_setup", "fc_rhs", "fc_residual", "fc_apply", "fc_smooth",
            "fc_smooth_noalloc", "fc_restrict", "fc_prolong_add", "fc_coarse_solve", "fc_vcycle", "fc_solve",
-           "fc_gmg_solve", "fc_solve_host", "fc_info", "fc_patch_rows", "fc_footprint_estimate",
+           "fc_gmg_solve", "fc_solve_host", "fc_info", "fc_patch_rows", "fc_patch_dofs", "fc_footprint_estimate",
            "fc_profile_enable", "fc_profile_read", "fc_launch_count", "fc_probe_fma_rate", "fc_sync", "fc_last_error",
            "fc_destroy", "fc_batch_create", "fc_batch_create_tiled", "fc_batch_offsets", "fc_batch_tile", "fc_batch_set_tile",
            "fc_batch_smooth", "fc_batch_vcycle", "fc_batch_solve", "fc_batch_solve_host", "fc_batch_info", "fc_batch_profile_enable",
@@ -86,7 +86,7 @@ class FcOptions(C.Structure):
                 ("cache", C.c_int), ("prec", C.c_int), ("fgmres_restart", C.c_int),
                 ("bc_preset", C.c_int), ("ubar", C.c_double), ("force_kind", C.c_int),
                 ("force", C.c_double * 3), ("dedup", C.c_int), ("tc", C.c_int), ("badcut_frac", C.c_double),
-                ("element", C.c_int), ("galerkin", C.c_int)]
+                ("element", C.c_int), ("galerkin", C.c_int), ("amr_uniform", C.c_int)]
 
 
 _lib = None
@@ -184,6 +184,7 @@ def _options(prob, cache: str, prec: str, nu=None, dedup: int = 1, tc: str = "no
     o.tc = TC[tc]
     o.element = ELEMENT[element]
     o.galerkin = 1 if galerkin else 0
+    o.amr_uniform = int(getattr(prob, "amr_uniform", -1))
     if badcut_frac is not None:
         o.badcut_frac = float(badcut_frac)
     return o
@@ -406,7 +407,9 @@ class Solver:
 
     def patch_rows(self, node: int, level=None):
         lv = self.nlevels if level is None else level
-        if self.element == "q2":          # Q2-Q1: owned rows x slots
+        if getattr(self.prob, "amr_uniform", -1) >= 0:   # adaptive: 3 owned rows x patch DoFs
+            out = np.zeros((3, len(self.patch_dofs(node, level))))
+        elif self.element == "q2":          # Q2-Q1: owned rows x slots
             out = np.zeros((25, 2214)) if self.dim == 3 else np.zeros((9, 171))
         else:
             ns = 402 if self.dim == 3 else 59
@@ -414,6 +417,15 @@ class Solver:
         self._check(self.lib.fc_patch_rows(self.h, lv, int(node),
                                            out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
+
+    def patch_dofs(self, node: int, level=None):
+        """Adaptive grids: the DoFs of the patch of free node `node`."""
+        lv = self.nlevels if level is None else level
+        buf = np.zeros(512, dtype=np.int64)
+        n = C.c_int()
+        self._check(self.lib.fc_patch_dofs(self.h, lv, int(node), buf.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                           len(buf), C.byref(n)))
+        return buf[:n.value].copy()
 
     def profile(self, on: bool = True):
         self._check(self.lib.fc_profile_enable(self.h, 1 if on else 0))

@@ -1,0 +1,156 @@
+"""Parity of the adaptive-grid GPU path with the adaptive-grid oracle
+(oracle/fc_oracle_amr.c): 2D quadtree grids refined towards the obstacle
+boundaries with 2:1 balance, hanging nodes as constraints, Algorithm 1's
+hierarchy (Sec. 3), fc_options.amr_uniform >= 0.
+
+Bounds as for the uniform grids: operator, load and transfers 1e-12; patch
+DoF lists identical and owned rows 1e-11; one sweep and a V-cycle 1e-10
+relative; coarse solve 1e-11; FGMRES and standalone GMG with the oracle's
+iteration counts and the solution within 1e-6."""
+import dataclasses
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spl
+
+from oracle import oracle as O
+from paper_2403_11636_gb300 import inputs
+from tests.gpu_util import rel
+
+pytestmark = pytest.mark.gpu
+
+OPER_TOL = 1e-12
+SWEEP_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def fc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2403_11636_gb300 import build, fc as fcmod
+    build.build()
+    return fcmod
+
+
+PROBS = {
+    "ch64": dataclasses.replace(inputs.channel_2d(0, n=64, nlevels=4), amr_uniform=1),
+    "ch128": dataclasses.replace(inputs.channel_2d(3, n=128, nlevels=5), amr_uniform=2),
+    "ell64": dataclasses.replace(inputs.batch_2d(7), n=(64, 64), nlevels=4, amr_uniform=1),
+    "replay": dataclasses.replace(inputs.channel_replay_2d(0, nx=256, ny=64, nlevels=5), amr_uniform=1),
+}
+
+
+@pytest.fixture(scope="module")
+def oracles():
+    return {name: O.AMRMG(p) for name, p in PROBS.items()}
+
+
+def solver(fc, p):
+    return fc.Solver(p)
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_amr_operator_and_load(fc, oracles, name):
+    p = PROBS[name]
+    s = solver(fc, p)
+    mg = oracles[name]
+    for lv in range(1, p.nlevels + 1):
+        L = mg.levels[lv - 1]
+        A, b, _ = L.csr()
+        assert s.ndof(lv) == L.ndof
+        x = inputs.uniform_array(L.ndof, 17 + lv)
+        assert rel(s.apply(x, level=lv).cpu().numpy(), A @ x) <= OPER_TOL, lv
+    _, b, _ = mg.fine.csr()
+    assert rel(s.rhs().cpu().numpy(), b) <= OPER_TOL
+
+
+@pytest.mark.parametrize("name", ["ch64", "ell64", "replay"])
+def test_amr_patch_rows(fc, oracles, name):
+    p = PROBS[name]
+    s = solver(fc, p)
+    for lv in (p.nlevels, p.nlevels - 1):
+        L = oracles[name].levels[lv - 1]
+        rng = np.random.default_rng(lv)
+        for node in rng.choice(L.nnodes, min(25, L.nnodes), replace=False):
+            rows, dofs, own = L.patch_inverse_rows(int(node))
+            d = s.patch_dofs(int(node), level=lv)
+            assert np.array_equal(d, dofs), (lv, node)
+            g = s.patch_rows(int(node), level=lv)
+            for k in range(3):
+                if own[k] < 0:
+                    assert np.abs(g[k]).max() == 0
+                else:
+                    assert rel(g[k], rows[k]) <= 1e-11, (lv, node, k, rel(g[k], rows[k]))
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_amr_sweep(fc, oracles, name):
+    p = PROBS[name]
+    s = solver(fc, p)
+    mg = oracles[name]
+    for lv in (p.nlevels, 2):
+        L = mg.levels[lv - 1]
+        x0 = inputs.uniform_array(L.ndof, 31 + lv)
+        b = inputs.uniform_array(L.ndof, 41 + lv)
+        want = L.sweep(b, x0)
+        got = s.smooth(x0, b, level=lv).cpu().numpy()
+        assert rel(got - x0, want - x0) <= SWEEP_TOL, lv
+
+
+@pytest.mark.parametrize("name", ["ch64", "replay"])
+def test_amr_transfers_and_coarse_solve(fc, oracles, name):
+    p = PROBS[name]
+    s = solver(fc, p)
+    mg = oracles[name]
+    F, Cc = mg.levels[-1], mg.levels[-2]
+    r = inputs.uniform_array(F.ndof, 51)
+    assert rel(s.restrict(r).cpu().numpy(), O.restrict(F, Cc, r)) <= OPER_TOL
+    e = inputs.uniform_array(Cc.ndof, 52)
+    x = inputs.uniform_array(F.ndof, 53)
+    assert rel(s.prolong_add(e, x).cpu().numpy(), O.prolong_add(F, Cc, e, x)) <= OPER_TOL
+    C1 = mg.levels[0]
+    A, _, _ = C1.csr()
+    b1 = inputs.uniform_array(C1.ndof, 61)
+    assert rel(s.coarse_solve(b1).cpu().numpy(), spl.spsolve(A.tocsc(), b1)) <= 1e-11
+
+
+@pytest.mark.parametrize("name", list(PROBS))
+def test_amr_vcycle_and_fgmres(fc, oracles, name):
+    p = PROBS[name]
+    s = solver(fc, p)
+    mg = oracles[name]
+    n = mg.fine.ndof
+    b = inputs.uniform_array(n, 71)
+    x0 = inputs.uniform_array(n, 72)
+    want = mg.vcycle(x0, b)
+    assert rel(s.vcycle(x0, b).cpu().numpy() - x0, want - x0) <= SWEEP_TOL
+    x_or, its_or, _, _ = mg.fgmres(mg.rhs(), rtol=1e-8)
+    x, its, rr = s.solve(s.rhs(), rtol=1e-8)
+    assert its == its_or and rr <= 1e-8
+    assert rel(x.cpu().numpy(), x_or) <= 1e-6
+
+
+def test_amr_standalone_gmg(fc):
+    """The paper's standalone setting (Sec. 4: V(6,6), damping 0.8, a 1e9
+    residual reduction, alpha = 1e-10) on an adaptive channel stand-in: the
+    GPU needs the oracle's cycle count."""
+    p = dataclasses.replace(inputs.channel_replay_2d(0, nx=256, ny=64, nlevels=5), amr_uniform=1)
+    mg = O.AMRMG(p)
+    b = mg.rhs()
+    x_or, its_or, _ = mg.gmg_solve(b, reduction=1e-9, maxit=80)
+    s = solver(fc, p)
+    x, its, red = s.gmg_solve(s.rhs(), reduction=1e-9, maxit=80)
+    assert its == its_or and red <= 1e-9
+    assert rel(x.cpu().numpy(), x_or) <= 1e-6
+
+
+def test_amr_rejects_unsupported(fc):
+    p = PROBS["ch64"]
+    for kw in ({"prec": "df64"}, {"cache": "matrix"}, {"element": "q2"}, {"galerkin": True}):
+        with pytest.raises(fc.FcError):
+            fc.Solver(p, **kw)
+    with pytest.raises(fc.FcError):
+        fc.Solver(dataclasses.replace(inputs.porous_3d(0, n=8, nspheres=2, nlevels=2), amr_uniform=0))
+    s = solver(fc, p)
+    assert s.smooth_noalloc_(s.zeros(), s.rhs()) == fc.FC_ERR_INVALID

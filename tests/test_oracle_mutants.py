@@ -109,7 +109,7 @@ MUTANTS = [
      0, "test_prolongation_exact_on_linear_fields[2]"),
     ("restriction_weight", "wgt = wgt * (lo[k] == hi[k] ? 1.0 : 0.5);", "wgt = wgt * (lo[k] == hi[k] ? 1.0 : 0.25);",
      1, "test_restriction_is_transpose_of_prolongation[2]"),
-    ("restriction_keeps_constrained", "if (Cc->fixed[k]) bc[k] = 0.0;", "if (0) bc[k] = 0.0;", 0,
+    ("restriction_keeps_constrained", "if (Cc->fixed[k]) bc[k] = 0.0;", "if (0) bc[k] = 0.0;", 1,
      "test_restriction_with_strong_dirichlet_rows[2-1]"),
     # V-cycle
     ("coarse_correction_dropped", "  or_prolong_add(L, C, xc, x);\n", "\n", 0,
