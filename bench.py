@@ -25,6 +25,7 @@ workload (a 16^3 grid of the same sphere geometry, 3 levels).
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -709,13 +710,21 @@ def run_replay(args):
     from paper_2403_11636_gb300 import build, fc, inputs
     build.build()
     rows = []
+    amr = args.replay_amr
     for k in range(args.replay_sizes):
-        nx, ny = 1024 << k, 256 << k
-        nlev = 7 + k                     # coarsest grid 16 x 4 cells
-        p = inputs.channel_replay_2d(0, nx=nx, ny=ny, nlevels=nlev)
+        if amr:
+            # adaptive: the 1024 x 256 grid everywhere (uniform level 6 over the
+            # 16 x 4 root) and k + 1 further levels at the cylinder
+            nx, ny = 1024 << (k + 1), 256 << (k + 1)
+            nlev = 8 + k
+            p = dataclasses.replace(inputs.channel_replay_2d(0, nx=nx, ny=ny, nlevels=nlev), amr_uniform=6)
+        else:
+            nx, ny = 1024 << k, 256 << k
+            nlev = 7 + k                     # coarsest grid 16 x 4 cells
+            p = inputs.channel_replay_2d(0, nx=nx, ny=ny, nlevels=nlev)
         try:
             t0 = time.perf_counter()
-            s = fc.Solver(p, prec="fp64", dedup=1)
+            s = fc.Solver(p, prec="fp64", dedup=0 if amr else 1)
             torch.cuda.synchronize()
             setup_ms = 1e3 * (time.perf_counter() - t0)
             b = s.rhs()
@@ -727,9 +736,15 @@ def run_replay(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
-            rows.append({"grid": f"{nx}x{ny}", "levels": nlev, "dofs": p.ndof(), "cycles": its, "reduction": red,
+            if amr:
+                ups = its * sum(s.ndof(lv) for lv in range(2, nlev + 1)) * (p.nu_pre + p.nu_post)
+                dofs = s.ndof()
+            else:
+                ups, dofs = updates_per_solve(p, its), p.ndof()
+            rows.append({"grid": f"{nx}x{ny}" + (" lattice, adaptive" if amr else ""), "levels": nlev,
+                         "dofs": dofs, "cycles": its, "reduction": red,
                          "solve_ms": ms, "ms_per_cycle": ms / max(its, 1), "setup_ms": setup_ms,
-                         "sweep_updates_per_s": updates_per_solve(p, its) / (ms * 1e-3)})
+                         "sweep_updates_per_s": ups / (ms * 1e-3)})
             s.close()
         except Exception as e:
             rows.append({"grid": f"{nx}x{ny}", "error": str(e)[:200]})
@@ -738,7 +753,9 @@ def run_replay(args):
           "data": "synthetic",
           "config": {"workload": "channel stand-in 2.2 x 0.41, cylinder diameter 0.1 at a seeded position near the "
                                  "inflow, parabolic inflow ubar 0.3, alpha 1e-10, eta 1e-3, quadtree depth 4, "
-                                 "standalone V(6,6), damping 0.8, coarsest grid 16 x 4, FP64 rows",
+                                 "standalone V(6,6), damping 0.8, coarsest grid 16 x 4, FP64 rows" +
+                                 ("; adaptive quadtree: 1024 x 256 everywhere, cut cells refined k + 1 further "
+                                  "levels, 2:1 balanced, Algorithm 1 hierarchy" if amr else "; uniform grids"),
                      "paper_table_grid": [{"grid": g, "dofs": d, "gmg_iterations": it} for g, d, it in PAPER_TABLE_GRID],
                      "note": "the paper's counts are for its adaptive grids and benchmark geometry: context, "
                              "not a parity target"},
@@ -1069,6 +1086,7 @@ def main():
     ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep", "mixed", "replay", "q2"])
     ap.add_argument("--mixed-n", type=int, default=128, help="grid of --mode mixed")
     ap.add_argument("--q2-n", type=int, default=256, help="grid of --mode q2 in 2D")
+    ap.add_argument("--replay-amr", action="store_true", help="--mode replay on adaptive quadtree grids")
     ap.add_argument("--q2-n3", type=int, default=16, help="grid of --mode q2 in 3D")
     ap.add_argument("--q2-dim", type=int, default=2, choices=[2, 3], help="dimension of --mode q2")
     ap.add_argument("--replay-sizes", type=int, default=4,
