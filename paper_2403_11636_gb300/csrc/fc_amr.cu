@@ -372,6 +372,32 @@ int amr_assemble(const AmrTree& T, const LevelGeom& g, const std::vector<double>
     H.pstart[i + 1] = H.pstart[i] + n;
     maxn = std::max(maxn, n);
   }
+  // node blocks of the operator: the velocity rows couple the same component
+  // only, with one scalar A for both (identity rows on constrained nodes)
+  H.nbp.assign((size_t)nf + 1, 0);
+  H.nbc.clear();
+  H.nbv.clear();
+  auto at = [&](long long row, long long colj) {
+    int lo = H.rowptr[row], hi = H.rowptr[row + 1] - 1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) / 2;
+      if (H.col[mid] == colj) return H.val[mid];
+      if (H.col[mid] < colj) lo = mid + 1; else hi = mid - 1;
+    }
+    return 0.0;
+  };
+  for (long long f = 0; f < nf; ++f) {
+    for (long long g2 : adj[f]) {
+      H.nbc.push_back((int)g2);
+      H.nbv.push_back(at(f * nd + 0, g2 * nd + 0));
+      H.nbv.push_back(at(f * nd + 0, g2 * nd + 2));
+      H.nbv.push_back(at(f * nd + 1, g2 * nd + 2));
+      H.nbv.push_back(at(f * nd + 2, g2 * nd + 0));
+      H.nbv.push_back(at(f * nd + 2, g2 * nd + 1));
+      H.nbv.push_back(at(f * nd + 2, g2 * nd + 2));
+    }
+    H.nbp[f + 1] = (int)H.nbc.size();
+  }
   return maxn;
 }
 
@@ -452,25 +478,48 @@ std::vector<long long> amr_leaf_cells(const AmrTree& T, const AmrHost& H, int le
 // ------------------------------------------------------------- kernels
 namespace {
 
-// r = b - A x (A x when b is null), a thread per row
-__global__ void amr_residual_kernel(long long n, const int* __restrict__ rp, const int* __restrict__ col,
-                                    const double* __restrict__ val, const double* __restrict__ x,
-                                    const double* __restrict__ b, double* __restrict__ r) {
-  const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n) return;
-  double s = 0.0;
-  for (int p = rp[row]; p < rp[row + 1]; ++p) s = s + val[p] * x[col[p]];
+// r = b - L x (L x when b is null) on node blocks: 4 lanes per free node,
+// each over every 4th neighbour (index, then the record A, B_0, B_1, T_0,
+// T_1, C as three 16-byte loads, then the neighbour's u, v, p), a shuffle
+// sum of the three row sums
+__global__ void __launch_bounds__(256)
+    amr_residual_kernel(long long nf, const int* __restrict__ nbp, const int* __restrict__ nbc,
+                        const double* __restrict__ nbv, const double* __restrict__ x,
+                        const double* __restrict__ b, double* __restrict__ r) {
+  constexpr int LPN = 4;
+  const int lane = threadIdx.x % LPN;
+  const long long gf = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / LPN;
+  const long long f = gf < nf ? gf : nf - 1;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  for (int p = nbp[f] + lane; p < nbp[f + 1]; p += LPN) {
+    const long long g = nbc[p];
+    const double2* v = reinterpret_cast<const double2*>(nbv + 6 * (long long)p);
+    const double2 m0 = v[0], m1 = v[1], m2 = v[2];  // (A, B0), (B1, T0), (T1, C)
+    const double xu = x[3 * g], xv = x[3 * g + 1], xp = x[3 * g + 2];
+    a0 += m0.x * xu + m0.y * xp;
+    a1 += m0.x * xv + m1.x * xp;
+    a2 += m1.y * xu + m2.x * xv + m2.y * xp;
+  }
+#pragma unroll
+  for (int o = LPN / 2; o > 0; o >>= 1) {
+    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+  }
+  if (gf >= nf || lane >= 3) return;
+  const double s = lane == 0 ? a0 : (lane == 1 ? a1 : a2);
+  const long long row = f * 3 + lane;
   r[row] = b ? b[row] - s : s;
 }
 
-// patch apply: 4 lanes per patch; y_k = sum_j rows[k][j] r[dof_j] for the
-// 3 owned rows; restricted write x[owned] += omega y (constrained velocity
-// DoFs: identity rows, x += r)
+// patch apply: 4 lanes per patch over the patch's slot records (dof index
+// in the bits of a double, then the 3 owned-row coefficients: two 16-byte
+// loads per slot); y_k = sum_j rows[k][j] r[dof_j]; restricted write
+// x[owned] += omega y (constrained velocity DoFs: identity rows, x += r)
 __global__ void __launch_bounds__(256)
-    amr_apply_kernel(long long np, const long long* __restrict__ pstart, const int* __restrict__ pdof,
-                     const int* __restrict__ pown, const double* __restrict__ rows,
-                     const unsigned char* __restrict__ fixed, const double* __restrict__ r, double omega,
-                     double* __restrict__ x) {
+    amr_apply_kernel(long long np, const long long* __restrict__ pstart, const int* __restrict__ pown,
+                     const double* __restrict__ rows, const unsigned char* __restrict__ fixed,
+                     const double* __restrict__ r, double omega, double* __restrict__ x) {
   constexpr int TPP = 4;
   const int lane = threadIdx.x % TPP;
   const long long gi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
@@ -478,13 +527,15 @@ __global__ void __launch_bounds__(256)
   const long long i = valid ? gi : np - 1;
   const long long s0 = pstart[i];
   const int n = (int)(pstart[i + 1] - s0);
-  const double* R = rows + 3 * s0;
+  const double2* rec = reinterpret_cast<const double2*>(rows + 4 * s0);
   double y[3] = {0.0, 0.0, 0.0};
+#pragma unroll 4
   for (int j = lane; j < n; j += TPP) {
-    const double rv = r[pdof[s0 + j]];
-    y[0] += R[j] * rv;
-    y[1] += R[n + j] * rv;
-    y[2] += R[2 * n + j] * rv;
+    const double2 a = __ldcs(rec + 2 * j), c = __ldcs(rec + 2 * j + 1);
+    const double rv = r[__double_as_longlong(a.x)];
+    y[0] += a.y * rv;
+    y[1] += c.x * rv;
+    y[2] += c.y * rv;
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -537,15 +588,13 @@ unsigned nblocks(long long n) { return (unsigned)((n + 255) / 256); }
 }  // namespace
 
 cudaError_t launch_amr_residual(const AmrLevel& A, const double* x, const double* b, double* r, cudaStream_t s) {
-  const long long n = A.nfree * 3;
-  amr_residual_kernel<<<nblocks(n), 256, 0, s>>>(n, A.rowptr, A.col, A.val, x, b, r);
+  amr_residual_kernel<<<nblocks(A.nfree * 4), 256, 0, s>>>(A.nfree, A.nbp, A.nbc, A.nbv, x, b, r);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_amr_apply(const AmrLevel& A, const double* r, double omega, double* x, cudaStream_t s) {
-  amr_apply_kernel<<<nblocks(A.nfree * 4), 256, 0, s>>>(A.nfree, A.pstart, A.pdof, A.pown, A.rows, A.fixed, r,
-                                                        omega, x);
+  amr_apply_kernel<<<nblocks(A.nfree * 4), 256, 0, s>>>(A.nfree, A.pstart, A.pown, A.rows, A.fixed, r, omega, x);
   note_launches(1);
   return cudaGetLastError();
 }

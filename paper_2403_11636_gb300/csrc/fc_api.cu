@@ -706,6 +706,9 @@ fc_status setup_amr(fc_handle h, const fc_grid* g, const fc_options* o, const st
     CK(up(&A.pstart, Hl.pstart, 1));
     CK(up(&A.pdof, Hl.pdof, 1));
     CK(up(&A.pown, Hl.pown, 1));
+    CK(up(&A.nbp, Hl.nbp, 0));
+    CK(up(&A.nbc, Hl.nbc, 0));
+    CK(up(&A.nbv, Hl.nbv, 0));
     if (li > 0) {
       CK(up(&A.prp, Hl.prp, 0));
       CK(up(&A.pcl, Hl.pcl, 0));
@@ -720,7 +723,7 @@ fc_status setup_amr(fc_handle h, const fc_grid* g, const fc_options* o, const st
     if (li == depth - 1)
       CK(cudaMemcpyAsync(L.b, Hl.rhs.data(), sizeof(double) * ndof, cudaMemcpyHostToDevice, h->stream));
     if (li > 0) {
-      const size_t nrows = (size_t)3 * Hl.pstart[Hl.nfree];
+      const size_t nrows = (size_t)4 * Hl.pstart[Hl.nfree];  // 32-byte slot records
       CK(dalloc(h, &A.rows, nrows, 1));
       {
         ProfScope ps(h, 3, 0.0);
@@ -1498,9 +1501,12 @@ fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_hos
     CK(cudaMemcpyAsync(se, L.amr.pstart + node, sizeof(se), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     const size_t n = (size_t)(se[1] - se[0]);
-    CK(cudaMemcpyAsync(rows_host, L.amr.rows + 3 * se[0], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost,
+    std::vector<double> raw(4 * n);
+    CK(cudaMemcpyAsync(raw.data(), L.amr.rows + 4 * se[0], sizeof(double) * 4 * n, cudaMemcpyDeviceToHost,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 3; ++k)
+      for (size_t j = 0; j < n; ++j) rows_host[k * n + j] = raw[4 * j + 1 + k];
     return FC_OK;
   }
   if (q2_path(h)) {
@@ -1603,6 +1609,7 @@ fc_status fc_destroy(fc_handle h) {
     dfree(h, L.q2mask); dfree(h, L.q2A); dfree(h, L.q2B); dfree(h, L.q2T); dfree(h, L.q2rpv); dfree(h, L.q2rpp);
     dfree(h, L.amr.rowptr); dfree(h, L.amr.col); dfree(h, L.amr.val); dfree(h, L.amr.fixed);
     dfree(h, L.amr.pstart); dfree(h, L.amr.pdof); dfree(h, L.amr.pown);
+    dfree(h, L.amr.nbp); dfree(h, L.amr.nbc); dfree(h, L.amr.nbv);
     dfree(h, L.amr.prp); dfree(h, L.amr.pcl); dfree(h, L.amr.pvl);
     dfree(h, L.amr.rrp); dfree(h, L.amr.rcl); dfree(h, L.amr.rvl);
   }

@@ -98,6 +98,8 @@ struct AmrHost {
   std::vector<int> pdof, pown;            // patch DoFs; owned local index (3 per patch) or -1
   std::vector<int> prp, pcl, rrp, rcl;    // prolongation from the coarser level and its transpose
   std::vector<double> pvl, rvl;
+  std::vector<int> nbp, nbc;              // node blocks: neighbours of each free node (CSR over nodes)
+  std::vector<double> nbv;                // per neighbour pair: A, B_0, B_1, T_0, T_1, C
 };
 
 struct AmrLevel {
@@ -110,7 +112,10 @@ struct AmrLevel {
   long long* pstart = nullptr;
   int* pdof = nullptr;
   int* pown = nullptr;
-  double* rows = nullptr;        // 3 owned rows per patch, at 3 * pstart[p], row-major over the patch
+  double* rows = nullptr;        // per patch slot (from 4 * pstart[p]): DoF index bits, 3 owned-row coefficients
+  int* nbp = nullptr;            // node-block operator for the residual (the velocity block is the same
+  int* nbc = nullptr;            // scalar A for both components, as in the uniform stencil)
+  double* nbv = nullptr;
   int *prp = nullptr, *pcl = nullptr, *rrp = nullptr, *rcl = nullptr;
   double *pvl = nullptr, *rvl = nullptr;
   unsigned long long rows_flop = 0;  // 2 x (patch DoFs x free owned DoFs) summed over the patches

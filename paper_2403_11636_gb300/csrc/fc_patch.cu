@@ -2526,7 +2526,8 @@ __global__ void __launch_bounds__(512)
 // search in each sorted row), symmetrically equilibrated D L_i D with
 // D = |diag L_i|^-1/2, LU with partial pivoting, and the owned columns of
 // (D L_i D)^-1 (= its owned rows, L_i symmetric), de-scaled; rows of absent
-// owned DoFs are zero.
+// owned DoFs are zero.  Stored per slot as a 32-byte record: the DoF index
+// in the bits of a double, then the three owned-row coefficients.
 __global__ void __launch_bounds__(256)
     amr_patch_rows_kernel(long long np, const long long* __restrict__ pstart, const int* __restrict__ pdof,
                           const int* __restrict__ pown, const int* __restrict__ rp, const int* __restrict__ col,
@@ -2571,11 +2572,16 @@ __global__ void __launch_bounds__(256)
     if (o >= 0) lu_solve_vec(K, n, n, piv, zz);
   }
   __syncthreads();
-  double* out = rows + 3 * s0;
-  for (int t = tid; t < 3 * n; t += nt) {
-    const int k = t / n, j = t % n;
-    const int o = pown[p * 3 + k];
-    out[t] = o >= 0 ? dsc[o] * z[t] * dsc[j] : 0.0;
+  // slot records: the DoF index (bits of a double), then the 3 owned rows
+  double* out = rows + 4 * s0;
+  for (int t = tid; t < 4 * n; t += nt) {
+    const int j = t >> 2, f = t & 3;
+    if (f == 0) {
+      out[t] = __longlong_as_double((long long)pdof[s0 + j]);
+    } else {
+      const int k = f - 1, o = pown[p * 3 + k];
+      out[t] = o >= 0 ? dsc[o] * z[k * n + j] * dsc[j] : 0.0;
+    }
   }
   if (tid == 0 && *flag) atomicOr(d_err, kErrSingularPatch);
 }
