@@ -113,6 +113,9 @@ typedef struct or_level {
   long* tp_rowptr;
   long* tp_col;
   double* tp_val;
+  /* adaptive grids: the stride of the cached patch arrays (pdof, pinv)
+   * when their patches exceed PMAX DoFs; 0 means PMAX */
+  int pstride;
 } or_level;
 
 #define PMAX 402
@@ -1103,12 +1106,13 @@ int or_sweep(or_level* L, const double* b, double* x, int mode, const long* orde
     double y[OMAX] = {0, 0, 0, 0};
     if (mode == 0) {
       int n = L->pn[i];
-      const long* pd = L->pdof + i * PMAX;
-      const double* rows = L->pinv + i * OMAX * PMAX;
+      const long PS = L->pstride ? L->pstride : PMAX;
+      const long* pd = L->pdof + i * PS;
+      const double* rows = L->pinv + i * OMAX * PS;
       for (int c = 0; c < OMAX; ++c) {
         if (L->pown[i * OMAX + c] < 0) continue;
         double s = 0.0;
-        for (int q = 0; q < n; ++q) s = s + rows[c * PMAX + q] * r[pd[q]];
+        for (int q = 0; q < n; ++q) s = s + rows[c * PS + q] * r[pd[q]];
         y[c] = s;
       }
       for (int c = 0; c < OMAX; ++c) own[c] = L->pown[i * OMAX + c];
@@ -1152,13 +1156,14 @@ void or_apply_patches(or_level* L, const double* r, double* x, long np, const lo
   for (long t = 0; t < np; ++t) {
     long i = list[t];
     int n = L->pn[i];
-    const long* pd = L->pdof + i * PMAX;
-    const double* rows = L->pinv + i * OMAX * PMAX;
+    const long PS = L->pstride ? L->pstride : PMAX;
+    const long* pd = L->pdof + i * PS;
+    const double* rows = L->pinv + i * OMAX * PS;
     for (int c = 0; c < OMAX; ++c) {
       int o = L->pown[i * OMAX + c];
       if (o < 0) continue;
       double s = 0.0;
-      for (int q = 0; q < n; ++q) s = s + rows[c * PMAX + q] * r[pd[q]];
+      for (int q = 0; q < n; ++q) s = s + rows[c * PS + q] * r[pd[q]];
       x[i * nd + c] = x[i * nd + c] + L->omega * s;
     }
   }

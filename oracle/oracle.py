@@ -662,15 +662,17 @@ def _load_amr():
     lib.amr_tree_coarsen.argtypes = [vp]
     lib.amr_tree_free.argtypes = [vp]
     lib.amr_tree_level.restype = i
-    lib.amr_tree_level.argtypes = [vp, i, i]
+    lib.amr_tree_level.argtypes = [vp, i, i, i]
     lib.amr_level_new.restype = vp
     lib.amr_level_new.argtypes = [vp, P(vp), vp]
     lib.amr_free_nodes.restype = l
     lib.amr_free_nodes.argtypes = [vp, P(l)]
     lib.amr_hanging.restype = l
-    lib.amr_hanging.argtypes = [vp, P(l), P(l)]
+    lib.amr_hanging.argtypes = [vp, P(l), P(i), P(l)]
     lib.amr_patch_rows.restype = i
-    lib.amr_patch_rows.argtypes = [vp, l, P(l), P(i), P(C.c_double)]
+    lib.amr_patch_rows.argtypes = [vp, l, P(l), P(i), P(C.c_double), i]
+    lib.amr_patch_stride.restype = i
+    lib.amr_patch_stride.argtypes = [vp]
     lib.amr_prolongation.restype = l
     lib.amr_prolongation.argtypes = [vp, P(l), P(l), P(C.c_double)]
     _lib_amr = lib
@@ -678,9 +680,10 @@ def _load_amr():
 
 
 class AMRLevel(Level):
-    """One level of an adaptive quadtree hierarchy (2D): an or_level whose
-    operator, patches and prolongation fc_oracle_amr.c built.  DoFs: the free
-    nodes in lattice order (y-major, x fastest), (u, v, p) per node."""
+    """One level of an adaptive space-tree hierarchy (quadtree in 2D, octree
+    in 3D): an or_level whose operator, patches and prolongation
+    fc_oracle_amr.c built.  DoFs: the free nodes in lattice order (x fastest,
+    then y, then z), the velocity components and then p per node."""
 
     def __init__(self, handle, tree, lib, lattice_n, dim=2):
         self.lib = lib
@@ -694,9 +697,10 @@ class AMRLevel(Level):
         self._assembled = True
 
     def patch_inverse_rows(self, vert: int):
-        d = np.zeros(PMAX, dtype=np.int64); own = np.zeros(OMAX, dtype=np.int32)
-        rows = np.zeros((OMAX, PMAX))
-        n = self.lib.amr_patch_rows(self.h, int(vert), _p(d, C.c_long), _p(own, C.c_int), _p(rows))
+        cap = self.lib.amr_patch_stride(self.h)
+        d = np.zeros(cap, dtype=np.int64); own = np.zeros(OMAX, dtype=np.int32)
+        rows = np.zeros((OMAX, cap))
+        n = self.lib.amr_patch_rows(self.h, int(vert), _p(d, C.c_long), _p(own, C.c_int), _p(rows), cap)
         return rows[:, :n].copy(), d[:n].copy(), own.copy()
 
     def patch_dofs(self, vert: int):
@@ -710,14 +714,23 @@ class AMRLevel(Level):
         return v
 
     def hanging(self):
-        n = self.lib.amr_hanging(self.tree, None, None)
-        v = np.zeros(n, dtype=np.int64); par = np.zeros((n, 2), dtype=np.int64)
-        self.lib.amr_hanging(self.tree, _p(v, C.c_long), _p(par, C.c_long))
-        return v, par
+        """Hanging lattice vertices and their parents: (n, 2) in 2D (edge
+        midpoints); in 3D (n, 4) with -1 after the two parents of an edge
+        midpoint (face centres have four)."""
+        n = self.lib.amr_hanging(self.tree, None, None, None)
+        v = np.zeros(n, dtype=np.int64); npar = np.zeros(n, dtype=np.int32)
+        par = np.zeros((n, 4), dtype=np.int64)
+        self.lib.amr_hanging(self.tree, _p(v, C.c_long), _p(npar, C.c_int), _p(par, C.c_long))
+        return v, (par[:, :2].copy() if self.dim == 2 else par)
 
     def leaf_levels(self):
-        nx, ny = self.n
-        return np.array([[self.lib.amr_tree_level(self.tree, x, y) for x in range(nx)] for y in range(ny)])
+        """Leaf level of every lattice cell: [y][x] in 2D, [z][y][x] in 3D."""
+        if self.dim == 2:
+            nx, ny = self.n
+            return np.array([[self.lib.amr_tree_level(self.tree, x, y, 0) for x in range(nx)] for y in range(ny)])
+        nx, ny, nz = self.n
+        return np.array([[[self.lib.amr_tree_level(self.tree, x, y, z) for x in range(nx)] for y in range(ny)]
+                         for z in range(nz)])
 
     def prolongation(self):
         import scipy.sparse as sp
@@ -742,21 +755,21 @@ class AMRLevel(Level):
 
 
 def amr_levels(prob):
-    """The adaptive hierarchy of a 2D problem with prob.amr_uniform = U >= 0:
+    """The adaptive hierarchy of a problem with prob.amr_uniform = U >= 0:
     lattice prob.n (the cells of the finest level), root grid
     prob.n / 2^(L-1), every cell refined uniformly to level U, cut cells to
     level L-1, 2:1 balanced; coarser levels by Algorithm 1.  Returns the
     AMRLevel objects, coarsest first."""
-    assert prob.dim == 2 and prob.amr_uniform >= 0
+    assert prob.dim in (2, 3) and prob.amr_uniform >= 0
     lib = _load_amr()
     L = prob.nlevels
     R = L - 1
     root = [k >> R for k in prob.n]
-    uni = [Level(2, (root[0] << r, root[1] << r), prob.lo, prob.hi, prob.shapes, prob.alpha, prob.qdepth,
+    uni = [Level(prob.dim, tuple(k << r for k in root), prob.lo, prob.hi, prob.shapes, prob.alpha, prob.qdepth,
                  prob.eta, prob.beta, prob.omega, prob.preset, prob.force_kind, prob.force, prob.ubar, lib=lib)
            for r in range(R + 1)]
     uarr = (C.c_void_p * len(uni))(*[u.h for u in uni])
-    nr = (C.c_int * 2)(*root)
+    nr = (C.c_int * 3)(*(list(root) + [1] * (3 - len(root))))
     trees = [lib.amr_tree_fine(uni[R].h, nr, int(prob.amr_uniform), R)]
     for _ in range(R):
         trees.append(lib.amr_tree_coarsen(trees[-1]))
@@ -766,7 +779,7 @@ def amr_levels(prob):
         h = lib.amr_level_new(trees[l], uarr, trees[l - 1] if l > 0 else None)
         if not h:
             raise RuntimeError("adaptive level construction failed (patch or adjacency overflow)")
-        levels.append(AMRLevel(h, trees[l], lib, prob.n))
+        levels.append(AMRLevel(h, trees[l], lib, prob.n, dim=prob.dim))
     for lv in levels:
         lv._uniform = uni  # keep the element data alive
     return levels

@@ -3,7 +3,9 @@
 Each translation unit is compiled in parallel to an object file under
 ``_build/`` and linked into ``libfc.so`` next to this file.  The geometry
 unit is compiled with ``--fmad=false`` so that its sums follow the operation
-order of the quadrature definition.
+order of the quadrature definition; the host code of the adaptive-grid unit
+(its constrained assembly) with ``-ffp-contract=off`` for the same reason,
+while its device kernels keep fused multiply-adds.
 """
 from __future__ import annotations
 
@@ -20,7 +22,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["fc_geom.cu", "fc_assemble.cu", "fc_mg.cu", "fc_patch.cu", "fc_api.cu", "fc_noalloc.cu", "fc_batch.cu",
            "fc_probe.cu", "fc_q2.cu", "fc_amr.cu"]
-EXTRA = {"fc_geom.cu": ["--fmad=false"], "fc_amr.cu": ["--fmad=false", "-Xcompiler", "-ffp-contract=off"]}
+EXTRA = {"fc_geom.cu": ["--fmad=false"], "fc_amr.cu": ["-Xcompiler", "-ffp-contract=off"]}
 
 
 def _nvcc() -> str:
