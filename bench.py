@@ -832,6 +832,71 @@ def run_q2(args):
     return 0
 
 
+def run_amr(args):
+    """Adaptive space-tree grids, FGMRES with the V(2,2) RA smoother on every
+    level.  3D (--amr-dim 3): the duct on the unit cube with one sphere
+    (r = 0.2, seeded centre, product-parabola inflow, alpha 1e-8, octree
+    depth 3) on an --amr-n^3 lattice, root grid 8^3, every cell refined to
+    the quarter lattice and the cut cells to the lattice; 2D (--amr-dim 2):
+    the 2D channel with one circle on an --amr-n^2 lattice, root 16^2, every
+    cell refined to the quarter lattice.  FP64 rows.  Reports solves/s, the
+    finest-level patch apply timed alone (algorithmic FLOP: owned rows x
+    patch DoFs x 2 summed over the patches) against the FP64 peak, and the
+    residual time."""
+    import torch
+    from paper_2403_11636_gb300 import build, fc, inputs
+    build.build()
+    dim, n = args.amr_dim, args.amr_n
+    root = 8 if dim == 3 else 16
+    nlev = int(round(math.log2(n // root))) + 1
+    if dim == 3:
+        prob = dataclasses.replace(inputs.channel_3d(0, n=n, nlevels=nlev), amr_uniform=nlev - 3)
+        workload = (f"adaptive octree, duct on the unit cube with one sphere r 0.2, lattice {n}^3, root 8^3, "
+                    f"uniform to {n // 4}^3, cut cells to {n}^3, 2:1 balanced, {nlev} levels (Algorithm 1), "
+                    f"alpha 1e-8, octree depth 3")
+    else:
+        prob = dataclasses.replace(inputs.channel_2d(0, n=n, nlevels=nlev), amr_uniform=nlev - 3)
+        workload = (f"adaptive quadtree, channel on the unit square with one circle r 0.2, lattice {n}^2, root "
+                    f"16^2, uniform to {n // 4}^2, cut cells to {n}^2, 2:1 balanced, {nlev} levels (Algorithm 1), "
+                    f"alpha 1e-8, quadtree depth 4")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        s = fc.Solver(prob, stream=stream, dedup=0)
+        torch.cuda.synchronize()
+        setup_ms = 1e3 * (time.perf_counter() - t0)
+        b = s.rhs()
+        for _ in range(args.warmup):
+            s.solve(b, rtol=1e-8)
+        step_ms, total_ms, its_l, rr_l = timed_solves(s, b, prob, args.steps, stream, torch)
+        X = torch.zeros_like(b)
+        s.smooth_(X, b, nsweeps=2)
+        s.profile(True)
+        s.smooth_(X, b, nsweeps=10)
+        na, ma, ba = s.profile_read(4)
+        nr, mr, _ = s.profile_read(1)
+        s.profile(False)
+        ndof = [s.ndof(lv) for lv in range(1, nlev + 1)]
+        flop = float(s.info()["bytes"][6])
+        s.close()
+    avg = ma / max(na, 1)
+    per_solve = sum(ndof[1:]) * (prob.nu_pre + prob.nu_post)
+    tf, note = fp64_peak(torch)
+    hbm, _ = peaks()
+    emit({"mode": "amr", "metric": "smoother patch-DoF updates/s", "unit": "owned-DoF updates/s", "dtype": "f64",
+          "data": "synthetic",
+          "value": sum(its_l) * per_solve / (total_ms * 1e-3),
+          "config": {"workload": workload + ", V(2,2), FGMRES(30) rtol 1e-8, FP64 rows", "dim": dim,
+                     "ndof_per_level": ndof, "iterations": its_l[0], "relres": max(rr_l), "setup_ms": setup_ms,
+                     "solves_per_s": args.steps / (total_ms * 1e-3), "ms_per_solve": total_ms / args.steps},
+          "finest_apply": {"ms": avg, "launches": na, "residual_ms": mr / max(nr, 1),
+                           "flop_per_launch": flop, "tflops": flop / (avg * 1e-3) / 1e12 if avg else None,
+                           "frac_of_fp64_peak": flop / (avg * 1e-3) / 1e12 / tf if avg else None,
+                           "fp64_peak_tflops": tf, "fp64_peak_source": note,
+                           "bytes_per_launch": ba, "hbm_frac": ba / (avg * 1e-3) / 1e9 / hbm if avg else None}})
+    return 0
+
+
 def run_batch(args):
     """Uneven batch: 256 independent 2D channel problems (grids 16..128^2,
     1-8 ellipses, alpha 1e-6..1e-10) solved together by fc_batch_solve
@@ -1083,12 +1148,14 @@ def main():
                     help="grid of the oracle per-sweep timing (16: the solve sample's finest level)")
     ap.add_argument("--profile-steps", type=int, default=3,
                     help="profiled solves after the timed ones (per-kernel CUDA events)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep", "mixed", "replay", "q2"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "serve", "batch", "batch-sweep", "mixed", "replay", "q2", "amr"])
     ap.add_argument("--mixed-n", type=int, default=128, help="grid of --mode mixed")
     ap.add_argument("--q2-n", type=int, default=256, help="grid of --mode q2 in 2D")
     ap.add_argument("--replay-amr", action="store_true", help="--mode replay on adaptive quadtree grids")
     ap.add_argument("--q2-n3", type=int, default=16, help="grid of --mode q2 in 3D")
     ap.add_argument("--q2-dim", type=int, default=2, choices=[2, 3], help="dimension of --mode q2")
+    ap.add_argument("--amr-dim", type=int, default=3, choices=[2, 3], help="dimension of --mode amr")
+    ap.add_argument("--amr-n", type=int, default=64, help="lattice of --mode amr (cells per direction)")
     ap.add_argument("--replay-sizes", type=int, default=4,
                     help="--mode replay: 1024x256 and this many - 1 uniform refinements")
     ap.add_argument("--batch-workload", default="batch2d", choices=["batch2d", "porous3d"],
@@ -1127,6 +1194,8 @@ def main():
         return run_replay(args)
     if args.mode == "q2":
         return run_q2(args)
+    if args.mode == "amr":
+        return run_amr(args)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -140,15 +140,16 @@ typedef struct {
                           next finer operator with the V-cycle's transfers (no quadrature on
                           the coarser grids; constrained coarse DoFs keep identity rows). */
   int amr_uniform;     /* -1: uniform grids (fc_grid.n cells on the finest level).  >= 0: adaptive
-                          2D quadtree grids (Sec. 3; Q1-Q1, cache_inverse, FP64 rows, 2D):
-                          fc_grid.n is the lattice of the finest level's cells, the root grid
-                          is fc_grid.n / 2^(depth-1); every cell is refined uniformly to level
-                          amr_uniform, a cell whose level set changes sign among its 3 x 3
-                          sample points to level depth-1, and the tree is 2:1 balanced across
-                          faces and corners; hanging nodes are constrained to the mean of
-                          their edge's end points; the coarser grids follow Algorithm 1.
-                          Vectors: the free nodes in lattice order (y-major, x fastest),
-                          (u, v, p) per node. */
+                          space-tree grids, quadtrees in 2D and octrees in 3D (Sec. 3; Q1-Q1,
+                          cache_inverse, FP64 rows): fc_grid.n is the lattice of the finest
+                          level's cells, the root grid is fc_grid.n / 2^(depth-1); every cell
+                          is refined uniformly to level amr_uniform, a cell whose level set
+                          changes sign among its 3^d sample points to level depth-1, and the
+                          tree is 2:1 balanced across faces, edges and corners; a hanging
+                          node is constrained to the mean of the end points of its edge or,
+                          in 3D, of the four corners of its face; the coarser grids follow
+                          Algorithm 1.  Vectors: the free nodes in lattice order (x fastest,
+                          then y, then z), the velocity components and then p per node. */
 } fc_options;
 
 /* Fill the defaults:
@@ -276,10 +277,11 @@ fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_hos
 
 /* Adaptive grids (fc_options.amr_uniform >= 0): the DoFs of the patch of
  * free node `node` on `level` (velocity DoFs of the connected nodes in
- * ascending order, then the pressures), at most `capacity` of them, into
- * dofs_host, and their count into *n; fc_patch_rows then gives rows[3][n]
- * (u, v, p of the node; zero rows for constrained velocity DoFs) in the same
- * order.  FC_ERR_INVALID on uniform grids or a short buffer.  Synchronises. */
+ * ascending order, then the pressures; at most 2048), at most `capacity` of
+ * them, into dofs_host, and their count into *n; fc_patch_rows then gives
+ * rows[d+1][n] (the velocity components and p of the node; zero rows for
+ * constrained velocity DoFs) in the same order.  FC_ERR_INVALID on uniform
+ * grids or a short buffer.  Synchronises. */
 fc_status fc_patch_dofs(fc_handle h, int level, long long node, long long* dofs_host, int capacity, int* n);
 
 /* Upper bound of the device bytes a handle for this problem holds at the

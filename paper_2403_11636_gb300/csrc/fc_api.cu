@@ -630,29 +630,32 @@ fc_status setup_q2(fc_handle h, const fc_grid* g, const fc_options* o, int nshap
   return FC_OK;
 }
 
-// Adaptive 2D quadtree hierarchy (fc_amr.cu): trees from the finest down
-// (Algorithm 1), per level the nodes and leaves on the host, the element
-// data of the leaves on the GPU (the element kernel on the uniform grid of
-// each leaf level), the constrained assembly, patches and transfers on the
-// host, then the device arrays, the patch rows (levels above the coarsest)
-// and the dense inverse of the coarsest operator.
+// Adaptive hierarchy, quadtrees in 2D and octrees in 3D (fc_amr.cu): trees
+// from the finest down (Algorithm 1), per level the nodes and leaves on the
+// host, the element data of the leaves on the GPU (the element kernel on the
+// uniform grid of each leaf level), the constrained assembly, patches and
+// transfers on the host, then the device arrays, the patch rows (levels
+// above the coarsest) and the dense inverse of the coarsest operator.
 fc_status setup_amr(fc_handle h, const fc_grid* g, const fc_options* o, const std::vector<Shape>& hs, int nshape,
                     double alpha, int depth) {
-  const int R = depth - 1;
-  const int nroot[2] = {g->n[0] >> R, g->n[1] >> R};
+  const int R = depth - 1, dim = g->dim, NC = 1 << dim;
+  const int nroot[3] = {g->n[0] >> R, g->n[1] >> R, dim == 3 ? g->n[2] >> R : 1};
   std::vector<AmrTree> trees(depth);
-  trees[depth - 1] = amr_tree_fine(hs, g->lo, g->hi, nroot, o->amr_uniform, R);
+  trees[depth - 1] = amr_tree_fine(hs, dim, g->lo, g->hi, nroot, o->amr_uniform, R);
   for (int li = depth - 2; li >= 0; --li) trees[li] = amr_tree_coarsen(trees[li + 1]);
   std::vector<AmrHost> H(depth);
   std::vector<std::vector<std::vector<long long>>> adj(depth);
-  for (int li = 0; li < depth; ++li) amr_structure(trees[li], H[li], adj[li]);
+  for (int li = 0; li < depth; ++li)
+    if (!amr_structure(trees[li], H[li], adj[li]))
+      return fail(h, FC_ERR_INVALID, "adaptive tree with a hanging parent of a hanging node");
   std::vector<int> maxn(depth, 0);
+  const size_t wa = (size_t)NC * NC, wb = (size_t)dim * NC * NC, wf = (size_t)dim * NC;
   for (int li = 0; li < depth; ++li) {
     Level& L = h->lev[li];
     L.g = make_geom(g, nshape, h->d_shapes, alpha, o, 0);
     AmrHost& Hl = H[li];
-    const size_t nleaf = Hl.leaf.size() / 3;
-    std::vector<double> eA(nleaf * 16), eB(nleaf * 32), eF(nleaf * 8);
+    const size_t nleaf = Hl.leaf.size() / 4;
+    std::vector<double> eA(nleaf * wa), eB(nleaf * wb), eF(nleaf * wf);
     for (int r = 0; r <= R; ++r) {
       std::vector<long long> slots;
       std::vector<long long> cells = amr_leaf_cells(trees[li], Hl, r, &slots);
@@ -662,20 +665,20 @@ fc_status setup_amr(fc_handle h, const fc_grid* g, const fc_options* o, const st
       long long* dcells = nullptr;
       double *dA = nullptr, *dB = nullptr, *dF = nullptr;
       CK(dalloc(h, &dcells, (size_t)n, -1));
-      CK(dalloc(h, &dA, (size_t)n * 16, -1));
-      CK(dalloc(h, &dB, (size_t)n * 32, -1));
-      CK(dalloc(h, &dF, (size_t)n * 8, -1));
+      CK(dalloc(h, &dA, (size_t)n * wa, -1));
+      CK(dalloc(h, &dB, (size_t)n * wb, -1));
+      CK(dalloc(h, &dF, (size_t)n * wf, -1));
       CK(cudaMemcpyAsync(dcells, cells.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, h->stream));
       CK(launch_cell_elements_list(Gr, dcells, n, dA, dB, dF, h->d_err, h->stream));
-      std::vector<double> tA((size_t)n * 16), tB((size_t)n * 32), tF((size_t)n * 8);
+      std::vector<double> tA((size_t)n * wa), tB((size_t)n * wb), tF((size_t)n * wf);
       CK(cudaMemcpyAsync(tA.data(), dA, sizeof(double) * tA.size(), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaMemcpyAsync(tB.data(), dB, sizeof(double) * tB.size(), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaMemcpyAsync(tF.data(), dF, sizeof(double) * tF.size(), cudaMemcpyDeviceToHost, h->stream));
       CK(cudaStreamSynchronize(h->stream));
       for (long long q = 0; q < n; ++q) {
-        std::copy(&tA[q * 16], &tA[q * 16] + 16, &eA[slots[q] * 16]);
-        std::copy(&tB[q * 32], &tB[q * 32] + 32, &eB[slots[q] * 32]);
-        std::copy(&tF[q * 8], &tF[q * 8] + 8, &eF[slots[q] * 8]);
+        std::copy(&tA[q * wa], &tA[q * wa] + wa, &eA[slots[q] * wa]);
+        std::copy(&tB[q * wb], &tB[q * wb] + wb, &eB[slots[q] * wb]);
+        std::copy(&tF[q * wf], &tF[q * wf] + wf, &eF[slots[q] * wf]);
       }
       dfree(h, dcells); dfree(h, dA); dfree(h, dB); dfree(h, dF);
     }
@@ -683,15 +686,17 @@ fc_status setup_amr(fc_handle h, const fc_grid* g, const fc_options* o, const st
     if (st != FC_OK) return st;
     maxn[li] = amr_assemble(trees[li], L.g, eA, eB, eF, adj[li], Hl);
     if (li > 0) amr_transfers(trees[li], Hl, trees[li - 1], H[li - 1]);
-    if (maxn[li] > 160) return fail(h, FC_ERR_INVALID, "adaptive patch larger than 160 DoFs");
+    if (maxn[li] > kAmrMaxPatch) return fail(h, FC_ERR_INVALID, "adaptive patch larger than 2048 DoFs");
   }
   for (int li = 0; li < depth; ++li) {
     Level& L = h->lev[li];
     AmrHost& Hl = H[li];
     AmrLevel& A = L.amr;
+    A.dim = dim;
     A.nfree = Hl.nfree;
     A.maxn = maxn[li];
-    const long long ndof = Hl.nfree * 3;
+    const int nd = dim + 1;
+    const long long ndof = Hl.nfree * nd;
     L.g.ndof = ndof;
     L.g.nnodes = Hl.nfree;
     auto up = [&](auto** dst, const auto& v, int part) -> cudaError_t {
@@ -723,22 +728,26 @@ fc_status setup_amr(fc_handle h, const fc_grid* g, const fc_options* o, const st
     if (li == depth - 1)
       CK(cudaMemcpyAsync(L.b, Hl.rhs.data(), sizeof(double) * ndof, cudaMemcpyHostToDevice, h->stream));
     if (li > 0) {
-      const size_t nrows = (size_t)4 * Hl.pstart[Hl.nfree];  // 32-byte slot records
+      const size_t nrows = (size_t)(nd + 1) * Hl.pstart[Hl.nfree];  // slot records of d + 2 doubles
       CK(dalloc(h, &A.rows, nrows, 1));
+      const int ctas = amr_patch_rows_ctas(A);
+      double* work = nullptr;
+      if (ctas > 0) CK(dalloc(h, &work, amr_patch_rows_work_doubles(A, ctas), -1));
       {
         ProfScope ps(h, 3, 0.0);
-        CK(launch_amr_patch_rows(A, h->d_err, h->stream));
+        CK(launch_amr_patch_rows(A, work, ctas, h->d_err, h->stream));
       }
       L.coef = A.rows;
       L.coef_bytes = nrows * 8;
       unsigned long long act = 0;
       for (long long i = 0; i < Hl.nfree; ++i) {
         int nown = 0;
-        for (int c = 0; c < 3; ++c) nown += Hl.pown[i * 3 + c] >= 0;
+        for (int c = 0; c < nd; ++c) nown += Hl.pown[i * nd + c] >= 0;
         act += (unsigned long long)(Hl.pstart[i + 1] - Hl.pstart[i]) * nown;
       }
       L.active_rows = act;
       CK(cudaStreamSynchronize(h->stream));
+      dfree(h, work);
       fc_status st = check_err(h);
       if (st != FC_OK) return st;
     }
@@ -919,9 +928,9 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
   if (o->galerkin != 0 && o->galerkin != 1) return fail(h, FC_ERR_INVALID, "invalid coarse-operator choice");
   if (o->amr_uniform < -1 || o->amr_uniform > depth - 1)
     return fail(h, FC_ERR_INVALID, "amr_uniform must be -1 or a level of the hierarchy");
-  if (o->amr_uniform >= 0 && (g->dim != 2 || o->element != 0 || o->galerkin || o->cache != FC_CACHE_INVERSE ||
+  if (o->amr_uniform >= 0 && (o->element != 0 || o->galerkin || o->cache != FC_CACHE_INVERSE ||
                               o->prec != FC_PREC_FP64))
-    return fail(h, FC_ERR_INVALID, "adaptive grids run in 2D with the Q1-Q1 pair, cache_inverse and FP64 rows");
+    return fail(h, FC_ERR_INVALID, "adaptive grids run with the Q1-Q1 pair, cache_inverse and FP64 rows");
   if (o->galerkin && o->element != 0) return fail(h, FC_ERR_INVALID, "Galerkin coarse operators need the Q1-Q1 pair");
   if (o->element == 1 && (o->cache != FC_CACHE_INVERSE || o->prec != FC_PREC_FP64))
     return fail(h, FC_ERR_INVALID, "the Q2-Q1 pair runs with cache_inverse and FP64 rows");
@@ -1500,13 +1509,13 @@ fc_status fc_patch_rows(fc_handle h, int level, long long node, double* rows_hos
     long long se[2] = {0, 0};
     CK(cudaMemcpyAsync(se, L.amr.pstart + node, sizeof(se), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    const size_t n = (size_t)(se[1] - se[0]);
-    std::vector<double> raw(4 * n);
-    CK(cudaMemcpyAsync(raw.data(), L.amr.rows + 4 * se[0], sizeof(double) * 4 * n, cudaMemcpyDeviceToHost,
+    const size_t n = (size_t)(se[1] - se[0]), nd = (size_t)h->dim + 1, rec = nd + 1;
+    std::vector<double> raw(rec * n);
+    CK(cudaMemcpyAsync(raw.data(), L.amr.rows + rec * se[0], sizeof(double) * rec * n, cudaMemcpyDeviceToHost,
                        h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    for (int k = 0; k < 3; ++k)
-      for (size_t j = 0; j < n; ++j) rows_host[k * n + j] = raw[4 * j + 1 + k];
+    for (size_t k = 0; k < nd; ++k)
+      for (size_t j = 0; j < n; ++j) rows_host[k * n + j] = raw[rec * j + 1 + k];
     return FC_OK;
   }
   if (q2_path(h)) {

@@ -79,30 +79,34 @@ struct Q2Grid {
 inline __host__ __device__ int nslot_u(int dim) { return dim == 3 ? 375 : 50; }
 inline __host__ __device__ int nslot(int dim) { return dim == 3 ? 402 : 59; }
 
-// Adaptive 2D quadtree grids (fc_amr.cu): the tree as the leaf level of
-// every lattice cell (the cells of the finest level R), the host half of a
-// level, and its device arrays.
+// Adaptive space-tree grids, quadtrees in 2D and octrees in 3D (fc_amr.cu):
+// the tree as the leaf level of every lattice cell (the cells of the finest
+// level R), the host half of a level, and its device arrays.
 struct AmrTree {
-  int R = 0, nroot[2] = {0, 0}, NX = 0, NY = 0;
-  std::vector<unsigned char> lev;  // [NY][NX]
+  int dim = 2, R = 0, nroot[3] = {0, 0, 1}, NX = 0, NY = 0, NZ = 1;
+  std::vector<unsigned char> lev;  // [NZ][NY][NX]
 };
 
 struct AmrHost {
+  int dim = 2;
   long long nfree = 0;
-  std::vector<long long> fid, hp, fvert;  // vertex -> free node, hanging parents, free node -> vertex
-  std::vector<int> leaf;                  // (X, Y, level) per leaf, lattice order
-  std::vector<int> rowptr, col;           // operator, node-interleaved (u, v, p)
+  std::vector<long long> fid, fvert;      // vertex -> free node or -1; free node -> vertex
+  std::vector<long long> hp;              // 4 per vertex: parents of a hanging vertex
+  std::vector<unsigned char> hn;          // per vertex: parents of a hanging vertex (2 or 4), 0 otherwise
+  std::vector<int> leaf;                  // (X, Y, Z, level) per leaf, lattice order
+  std::vector<int> rowptr, col;           // operator, node-interleaved (velocity components, p)
   std::vector<double> val, rhs, wfix;
   std::vector<unsigned char> fixed;
   std::vector<long long> pstart;          // patch DoF offsets
-  std::vector<int> pdof, pown;            // patch DoFs; owned local index (3 per patch) or -1
+  std::vector<int> pdof, pown;            // patch DoFs; owned local index (dim + 1 per patch) or -1
   std::vector<int> prp, pcl, rrp, rcl;    // prolongation from the coarser level and its transpose
   std::vector<double> pvl, rvl;
   std::vector<int> nbp, nbc;              // node blocks: neighbours of each free node (CSR over nodes)
-  std::vector<double> nbv;                // per neighbour pair: A, B_0, B_1, T_0, T_1, C
+  std::vector<double> nbv;                // per neighbour pair: A, B_0 .. B_{d-1}, T_0 .. T_{d-1}, C
 };
 
 struct AmrLevel {
+  int dim = 2;
   long long nfree = 0;
   int maxn = 0;                  // largest patch
   int* rowptr = nullptr;
@@ -112,9 +116,10 @@ struct AmrLevel {
   long long* pstart = nullptr;
   int* pdof = nullptr;
   int* pown = nullptr;
-  double* rows = nullptr;        // per patch slot (from 4 * pstart[p]): DoF index bits, 3 owned-row coefficients
+  double* rows = nullptr;        // per patch slot (from (dim + 2) * pstart[p]): DoF index bits, dim + 1
+                                 // owned-row coefficients
   int* nbp = nullptr;            // node-block operator for the residual (the velocity block is the same
-  int* nbc = nullptr;            // scalar A for both components, as in the uniform stencil)
+  int* nbc = nullptr;            // scalar A for every component, as in the uniform stencil)
   double* nbv = nullptr;
   int *prp = nullptr, *pcl = nullptr, *rrp = nullptr, *rcl = nullptr;
   double *pvl = nullptr, *rvl = nullptr;
@@ -174,11 +179,11 @@ struct Level {
   double* q2T = nullptr;
   double* q2rpv = nullptr;
   double* q2rpp = nullptr;
-  // adaptive 2D grids (fc_options.amr_uniform >= 0, see fc_amr.cu)
+  // adaptive grids (fc_options.amr_uniform >= 0, see fc_amr.cu)
   AmrLevel amr{};
 };
 
-AmrTree amr_tree_fine(const std::vector<Shape>& sh, const double* lo, const double* hi, const int* nroot, int U,
+AmrTree amr_tree_fine(const std::vector<Shape>& sh, int dim, const double* lo, const double* hi, const int* nroot, int U,
                       int R);
 AmrTree amr_tree_coarsen(const AmrTree& F);
 bool amr_structure(const AmrTree& T, AmrHost& H, std::vector<std::vector<long long>>& adj);
@@ -191,9 +196,16 @@ cudaError_t launch_amr_apply(const AmrLevel& A, const double* r, double omega, d
 cudaError_t launch_amr_prolong_add(const AmrLevel& F, const double* ec, double* xf, cudaStream_t s);
 cudaError_t launch_amr_restrict(const AmrLevel& F, const AmrLevel& C, const double* rf, double* bc, cudaStream_t s);
 cudaError_t launch_amr_dense(const AmrLevel& A, double* M, cudaStream_t s);
-// owned rows of every patch (fc_patch.cu): one CTA per patch, L_i gathered
-// from the CSR, equilibrated LU with partial pivoting, rows of the owned DoFs
-cudaError_t launch_amr_patch_rows(const AmrLevel& A, unsigned* d_err, cudaStream_t s);
+// owned rows of every patch of an adaptive level (fc_patch.cu): L_i gathered
+// from the CSR, equilibrated LU with partial pivoting, rows of the owned
+// DoFs; the dense block in shared memory (a CTA per patch) when it fits,
+// else in a global workspace of amr_patch_rows_work_doubles() (ctas
+// persistent CTAs over the patches)
+constexpr int kAmrMaxPatch = 2048;  // largest adaptive patch (DoFs)
+bool amr_patch_rows_in_smem(int dim, int maxn);
+int amr_patch_rows_ctas(const AmrLevel& A);
+size_t amr_patch_rows_work_doubles(const AmrLevel& A, int ctas);
+cudaError_t launch_amr_patch_rows(const AmrLevel& A, double* work, int ctas, unsigned* d_err, cudaStream_t s);
 
 struct Profile {
   bool on = false;

@@ -2521,69 +2521,76 @@ __global__ void __launch_bounds__(512)
   }
 }
 
-// ---- adaptive 2D grids: owned rows of the patches (variable size).  One
-// CTA per patch: L_i gathered from the CSR rows of the patch DoFs (binary
-// search in each sorted row), symmetrically equilibrated D L_i D with
-// D = |diag L_i|^-1/2, LU with partial pivoting, and the owned columns of
-// (D L_i D)^-1 (= its owned rows, L_i symmetric), de-scaled; rows of absent
-// owned DoFs are zero.  Stored per slot as a 32-byte record: the DoF index
-// in the bits of a double, then the three owned-row coefficients.
-__global__ void __launch_bounds__(256)
+// ---- adaptive grids: owned rows of the patches (variable size).  L_i
+// gathered from the CSR rows of the patch DoFs (binary search in each
+// sorted row), symmetrically equilibrated D L_i D with D = |diag L_i|^-1/2,
+// LU with partial pivoting, and the owned columns of (D L_i D)^-1 (= its
+// owned rows, L_i symmetric) by a CTA-cooperative solve with the d + 1 unit
+// vectors, de-scaled; rows of absent owned DoFs are zero.  The dense block
+// lives in dynamic shared memory (one CTA per patch) or, for the larger 3D
+// patches, in a per-CTA slice of a global workspace (persistent CTAs).
+// Stored per slot as a record of d + 2 doubles: the DoF index in the bits
+// of a double, then the d + 1 owned-row coefficients.
+template <int DIM>
+__global__ void __launch_bounds__(512)
     amr_patch_rows_kernel(long long np, const long long* __restrict__ pstart, const int* __restrict__ pdof,
                           const int* __restrict__ pown, const int* __restrict__ rp, const int* __restrict__ col,
-                          const double* __restrict__ val, double* __restrict__ rows, unsigned* d_err) {
+                          const double* __restrict__ val, double* __restrict__ rows, double* work,
+                          long long wstride, unsigned* d_err) {
+  constexpr int ND = DIM + 1, REC = ND + 1;
   extern __shared__ double am[];
-  const long long p = blockIdx.x;
-  const long long s0 = pstart[p];
-  const int n = (int)(pstart[p + 1] - s0);
-  double* K = am;                 // n x n row-major
-  double* dsc = K + (size_t)n * n;
-  double* z = dsc + n;            // 3 x n
-  int* piv = reinterpret_cast<int*>(z + 3 * n);
-  int* flag = piv + n;
+  __shared__ int s_piv[kAmrMaxPatch];
+  __shared__ int s_flag;
+  double* base = work ? work + (long long)blockIdx.x * wstride : am;
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) *flag = 0;
-  for (int t = tid; t < n * n; t += nt) {
-    const int a = t / n, b = t % n;
-    const int ra = pdof[s0 + a], cb = pdof[s0 + b];
-    double v = 0.0;
-    int lo = rp[ra], hi = rp[ra + 1] - 1;
-    while (lo <= hi) {
-      const int mid = (lo + hi) >> 1;
-      const int c = col[mid];
-      if (c == cb) { v = val[mid]; break; }
-      if (c < cb) lo = mid + 1; else hi = mid - 1;
+  for (long long p = blockIdx.x; p < np; p += gridDim.x) {
+    const long long s0 = pstart[p];
+    const int n = (int)(pstart[p + 1] - s0);
+    double* K = base;               // n x n row-major
+    double* dsc = K + (size_t)n * n;
+    double* W = dsc + n;            // n x (d + 1), column-major
+    if (tid == 0) s_flag = 0;
+    for (int t = tid; t < n * n; t += nt) {
+      const int a = t / n, b = t % n;
+      const int ra = pdof[s0 + a], cb = pdof[s0 + b];
+      double v = 0.0;
+      int lo = rp[ra], hi = rp[ra + 1] - 1;
+      while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int c = col[mid];
+        if (c == cb) { v = val[mid]; break; }
+        if (c < cb) lo = mid + 1; else hi = mid - 1;
+      }
+      K[t] = v;
     }
-    K[t] = v;
-  }
-  __syncthreads();
-  for (int a = tid; a < n; a += nt) {
-    const double d = fabs(K[(size_t)a * n + a]);
-    dsc[a] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
-  }
-  __syncthreads();
-  for (int t = tid; t < n * n; t += nt) K[t] = dsc[t / n] * K[t] * dsc[t % n];
-  __syncthreads();
-  cta_lu(K, n, n, piv, flag);
-  if (tid < 3) {
-    double* zz = z + tid * n;
-    const int o = pown[p * 3 + tid];
-    for (int j = 0; j < n; ++j) zz[j] = (o >= 0 && j == o) ? 1.0 : 0.0;
-    if (o >= 0) lu_solve_vec(K, n, n, piv, zz);
-  }
-  __syncthreads();
-  // slot records: the DoF index (bits of a double), then the 3 owned rows
-  double* out = rows + 4 * s0;
-  for (int t = tid; t < 4 * n; t += nt) {
-    const int j = t >> 2, f = t & 3;
-    if (f == 0) {
-      out[t] = __longlong_as_double((long long)pdof[s0 + j]);
-    } else {
-      const int k = f - 1, o = pown[p * 3 + k];
-      out[t] = o >= 0 ? dsc[o] * z[k * n + j] * dsc[j] : 0.0;
+    __syncthreads();
+    for (int a = tid; a < n; a += nt) {
+      const double d = fabs(K[(size_t)a * n + a]);
+      dsc[a] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
     }
+    __syncthreads();
+    for (int t = tid; t < n * n; t += nt) K[t] = dsc[t / n] * K[t] * dsc[t % n];
+    __syncthreads();
+    cta_lu(K, n, n, s_piv, &s_flag);
+    for (int t = tid; t < ND * n; t += nt) {
+      const int k = t / n, j = t % n, o = pown[p * ND + k];
+      W[t] = (o >= 0 && j == o) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    cta_lu_solve_multi(K, n, s_piv, W, ND);
+    double* out = rows + REC * s0;
+    for (int t = tid; t < REC * n; t += nt) {
+      const int j = t / REC, f = t % REC;
+      if (f == 0) {
+        out[t] = __longlong_as_double((long long)pdof[s0 + j]);
+      } else {
+        const int k = f - 1, o = pown[p * ND + k];
+        out[t] = o >= 0 ? dsc[o] * W[(size_t)k * n + j] * dsc[j] : 0.0;
+      }
+    }
+    if (tid == 0 && s_flag) atomicOr(d_err, kErrSingularPatch);
+    __syncthreads();  // the next patch reuses the block
   }
-  if (tid == 0 && *flag) atomicOr(d_err, kErrSingularPatch);
 }
 
 // 3D apply: a warp per vertex; lane l sums the 25 rows over the slots
@@ -2801,14 +2808,42 @@ cudaError_t launch_q2_apply(int dim, const Q2Grid& q, const double* coef, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_amr_patch_rows(const AmrLevel& A, unsigned* d_err, cudaStream_t s) {
+namespace {
+size_t amr_block_doubles(int dim, int n) { return (size_t)n * n + (size_t)(dim + 2) * n; }
+constexpr size_t kAmrSmemBytes = 216 * 1024;  // + 8 KB of pivots within the 227 KB per CTA
+}  // namespace
+
+bool amr_patch_rows_in_smem(int dim, int maxn) { return amr_block_doubles(dim, maxn) * 8 <= kAmrSmemBytes; }
+
+int amr_patch_rows_ctas(const AmrLevel& A) {
+  if (A.nfree == 0 || amr_patch_rows_in_smem(A.dim, A.maxn)) return 0;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return (int)std::min<long long>(A.nfree, std::max(nsm, 1));
+}
+
+size_t amr_patch_rows_work_doubles(const AmrLevel& A, int ctas) {
+  return (size_t)ctas * amr_block_doubles(A.dim, A.maxn);
+}
+
+cudaError_t launch_amr_patch_rows(const AmrLevel& A, double* work, int ctas, unsigned* d_err, cudaStream_t s) {
   if (A.nfree == 0) return cudaSuccess;
-  const int n = A.maxn;
-  const size_t smem = sizeof(double) * ((size_t)n * n + 4 * (size_t)n) + sizeof(int) * ((size_t)n + 1);
-  cudaError_t e = cudaFuncSetAttribute(amr_patch_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  amr_patch_rows_kernel<<<(unsigned)A.nfree, 256, smem, s>>>(A.nfree, A.pstart, A.pdof, A.pown, A.rowptr, A.col,
-                                                             A.val, A.rows, d_err);
+  if (A.maxn > kAmrMaxPatch) return cudaErrorInvalidValue;
+  const long long wstride = (long long)amr_block_doubles(A.dim, A.maxn);
+  auto kern = A.dim == 2 ? amr_patch_rows_kernel<2> : amr_patch_rows_kernel<3>;
+  if (work == nullptr) {
+    if (!amr_patch_rows_in_smem(A.dim, A.maxn)) return cudaErrorInvalidValue;
+    const size_t smem = sizeof(double) * (size_t)wstride;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)A.nfree, 256, smem, s>>>(A.nfree, A.pstart, A.pdof, A.pown, A.rowptr, A.col, A.val, A.rows,
+                                               nullptr, 0, d_err);
+  } else {
+    if (ctas <= 0) return cudaErrorInvalidValue;
+    kern<<<(unsigned)ctas, 512, 0, s>>>(A.nfree, A.pstart, A.pdof, A.pown, A.rowptr, A.col, A.val, A.rows, work,
+                                        wstride, d_err);
+  }
   note_launches(1);
   return cudaGetLastError();
 }

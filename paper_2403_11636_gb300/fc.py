@@ -407,8 +407,8 @@ class Solver:
 
     def patch_rows(self, node: int, level=None):
         lv = self.nlevels if level is None else level
-        if getattr(self.prob, "amr_uniform", -1) >= 0:   # adaptive: 3 owned rows x patch DoFs
-            out = np.zeros((3, len(self.patch_dofs(node, level))))
+        if getattr(self.prob, "amr_uniform", -1) >= 0:   # adaptive: d + 1 owned rows x patch DoFs
+            out = np.zeros((self.nd, len(self.patch_dofs(node, level))))
         elif self.element == "q2":          # Q2-Q1: owned rows x slots
             out = np.zeros((25, 2214)) if self.dim == 3 else np.zeros((9, 171))
         else:
@@ -421,7 +421,7 @@ class Solver:
     def patch_dofs(self, node: int, level=None):
         """Adaptive grids: the DoFs of the patch of free node `node`."""
         lv = self.nlevels if level is None else level
-        buf = np.zeros(512, dtype=np.int64)
+        buf = np.zeros(2048, dtype=np.int64)
         n = C.c_int()
         self._check(self.lib.fc_patch_dofs(self.h, lv, int(node), buf.ctypes.data_as(C.POINTER(C.c_longlong)),
                                            len(buf), C.byref(n)))

@@ -97,8 +97,8 @@ class Problem:
     ubar: float = 0.3                # inflow mean (channel preset)
     rtol: float = 1e-8
     restart: int = 30
-    amr_uniform: int = -1            # >= 0: adaptive 2D quadtree, cells refined uniformly to this
-                                     # level and cut cells to the finest (n = lattice of the finest level)
+    amr_uniform: int = -1            # >= 0: adaptive quadtree (2D) or octree (3D), cells refined uniformly
+                                     # to this level and cut cells to the finest (n = lattice of the finest level)
 
     def level_n(self, level: int) -> Tuple[int, ...]:
         """Cells per direction on level ``level`` (1 = coarsest, L = finest)."""
@@ -158,6 +158,19 @@ def channel_2d(seed: int = 0, n: int = 32, nlevels: int = 3, alpha: float = 1e-8
     return Problem(name=f"channel2d_n{n}_s{seed}", dim=2, n=(n, n), lo=(0.0, 0.0), hi=(1.0, 1.0),
                    shapes=shapes, alpha=alpha, qdepth=qdepth, nlevels=nlevels, preset=0,
                    force_kind=1, force=(1.0, 1.0, 0.0))
+
+
+def channel_3d(seed: int = 0, n: int = 16, nlevels: int = 3, alpha: float = 1e-8,
+               qdepth: int = 3, radius: float = 0.2) -> Problem:
+    """3D duct on the unit cube with one spherical obstacle (centre drawn in
+    [0.35, 0.65]^3), inflow at x = 0 with the product of the parabolas in y
+    and z, no-slip on the y and z faces, a unit body force in x."""
+    rng = SplitMix64(seed)
+    c = [rng.uniform(0.35, 0.65) for _ in range(3)]
+    shapes = np.array([[0.0, c[0], c[1], c[2], radius, radius, radius, 1.0, 0.0]])
+    return Problem(name=f"channel3d_n{n}_s{seed}", dim=3, n=(n, n, n), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
+                   shapes=shapes, alpha=alpha, qdepth=qdepth, nlevels=nlevels, preset=0, force_kind=0,
+                   force=(1.0, 0.0, 0.0))
 
 
 def porous_3d(seed: int = 0, n: int = 64, nspheres: int = 40, nlevels: int = 5,

@@ -1,7 +1,9 @@
 """Parity of the adaptive-grid GPU path with the adaptive-grid oracle
-(oracle/fc_oracle_amr.c): 2D quadtree grids refined towards the obstacle
-boundaries with 2:1 balance, hanging nodes as constraints, Algorithm 1's
-hierarchy (Sec. 3), fc_options.amr_uniform >= 0.
+(oracle/fc_oracle_amr.c): quadtree (2D) and octree (3D) grids refined
+towards the obstacle boundaries with 2:1 balance, hanging nodes as
+constraints, Algorithm 1's hierarchy (Sec. 3), fc_options.amr_uniform >= 0.
+The octree cases have patches of up to 841 DoFs, factorised in the global
+workspace of the patch-rows kernel.
 
 Bounds as for the uniform grids: operator, load and transfers 1e-12; patch
 DoF lists identical and owned rows 1e-11; one sweep and a V-cycle 1e-10
@@ -38,6 +40,9 @@ PROBS = {
     "ch128": dataclasses.replace(inputs.channel_2d(3, n=128, nlevels=5), amr_uniform=2),
     "ell64": dataclasses.replace(inputs.batch_2d(7), n=(64, 64), nlevels=4, amr_uniform=1),
     "replay": dataclasses.replace(inputs.channel_replay_2d(0, nx=256, ny=64, nlevels=5), amr_uniform=1),
+    "oct16": dataclasses.replace(inputs.channel_3d(0, n=16, nlevels=3), amr_uniform=0),
+    "oct16p": dataclasses.replace(inputs.porous_3d(1, n=16, nspheres=3, nlevels=3), amr_uniform=1),
+    "oct32": dataclasses.replace(inputs.channel_3d(2, n=32, nlevels=4), amr_uniform=1),
 }
 
 
@@ -65,7 +70,7 @@ def test_amr_operator_and_load(fc, oracles, name):
     assert rel(s.rhs().cpu().numpy(), b) <= OPER_TOL
 
 
-@pytest.mark.parametrize("name", ["ch64", "ell64", "replay"])
+@pytest.mark.parametrize("name", ["ch64", "ell64", "replay", "oct16", "oct16p", "oct32"])
 def test_amr_patch_rows(fc, oracles, name):
     p = PROBS[name]
     s = solver(fc, p)
@@ -77,7 +82,8 @@ def test_amr_patch_rows(fc, oracles, name):
             d = s.patch_dofs(int(node), level=lv)
             assert np.array_equal(d, dofs), (lv, node)
             g = s.patch_rows(int(node), level=lv)
-            for k in range(3):
+            assert g.shape == (p.dim + 1, len(dofs))
+            for k in range(p.dim + 1):
                 if own[k] < 0:
                     assert np.abs(g[k]).max() == 0
                 else:
@@ -98,7 +104,7 @@ def test_amr_sweep(fc, oracles, name):
         assert rel(got - x0, want - x0) <= SWEEP_TOL, lv
 
 
-@pytest.mark.parametrize("name", ["ch64", "replay"])
+@pytest.mark.parametrize("name", ["ch64", "replay", "oct16", "oct32"])
 def test_amr_transfers_and_coarse_solve(fc, oracles, name):
     p = PROBS[name]
     s = solver(fc, p)
@@ -151,6 +157,6 @@ def test_amr_rejects_unsupported(fc):
         with pytest.raises(fc.FcError):
             fc.Solver(p, **kw)
     with pytest.raises(fc.FcError):
-        fc.Solver(dataclasses.replace(inputs.porous_3d(0, n=8, nspheres=2, nlevels=2), amr_uniform=0))
+        fc.Solver(dataclasses.replace(inputs.porous_3d(0, n=8, nspheres=2, nlevels=2), amr_uniform=0), prec="fp32")
     s = solver(fc, p)
     assert s.smooth_noalloc_(s.zeros(), s.rhs()) == fc.FC_ERR_INVALID
