@@ -36,6 +36,7 @@
 // finite element function at its position; restriction its transpose,
 // constrained coarse DoFs zeroed.
 #include <math.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <vector>
@@ -412,12 +413,16 @@ int amr_assemble(const AmrTree& T, const LevelGeom& g, const std::vector<double>
   H.pown.assign((size_t)nf * nd, -1);
   int maxn = 0;
   std::vector<long long> vel;
+  std::vector<long long> seen((size_t)nf, -1);  // last patch that listed the node
   for (long long i = 0; i < nf; ++i) {
     vel.clear();
     for (long long j : adj[i])
-      for (long long k : adj[j]) vel.push_back(k);
+      for (long long k : adj[j])
+        if (seen[k] != i) {
+          seen[k] = i;
+          vel.push_back(k);
+        }
     std::sort(vel.begin(), vel.end());
-    vel.erase(std::unique(vel.begin(), vel.end()), vel.end());
     int n = 0;
     for (long long k : vel)
       for (int c = 0; c < dim; ++c) {
@@ -587,17 +592,17 @@ __global__ void __launch_bounds__(256)
   r[row] = b ? b[row] - s : s;
 }
 
-// patch apply: 4 lanes per patch over the patch's slot records (the DoF
+// patch apply: TPP lanes per patch over the patch's slot records (the DoF
 // index in the bits of a double, then the d + 1 owned-row coefficients;
 // 2D: two 16-byte loads per 32-byte record; 3D: five 8-byte loads per
 // 40-byte record); y_k = sum_j rows[k][j] r[dof_j]; restricted write
 // x[owned] += omega y (constrained velocity DoFs: identity rows, x += r)
-template <int DIM>
+template <int DIM, int TPP>
 __global__ void __launch_bounds__(256)
     amr_apply_kernel(long long np, const long long* __restrict__ pstart, const int* __restrict__ pown,
                      const double* __restrict__ rows, const unsigned char* __restrict__ fixed,
                      const double* __restrict__ r, double omega, double* __restrict__ x) {
-  constexpr int TPP = 4, ND = DIM + 1, REC = ND + 1;
+  constexpr int ND = DIM + 1, REC = ND + 1;
   const int lane = threadIdx.x % TPP;
   const long long gi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / TPP;
   const bool valid = gi < np;
@@ -694,12 +699,45 @@ cudaError_t launch_amr_residual(const AmrLevel& A, const double* x, const double
   return cudaGetLastError();
 }
 
+// lanes per patch: the fewest of 4, 8, 16 that give the launch two waves of
+// resident threads (2048 per SM), so that small levels still fill the GPU;
+// FC_AMR_LANES = 4, 8 or 16 in the environment fixes it (tests, tuning)
+static int amr_apply_lanes(long long npatch) {
+  if (const char* e = getenv("FC_AMR_LANES")) {
+    const int t = atoi(e);
+    if (t == 4 || t == 8 || t == 16) return t;
+  }
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  const long long want = 2LL * nsm * 2048;
+  for (int t = 4; t < 16; t *= 2)
+    if (npatch * t >= want) return t;
+  return 16;
+}
+
+template <int DIM, int TPP>
+static void apply_as(const AmrLevel& A, const double* r, double omega, double* x, cudaStream_t s) {
+  amr_apply_kernel<DIM, TPP><<<nblocks(A.nfree * TPP), 256, 0, s>>>(A.nfree, A.pstart, A.pown, A.rows, A.fixed, r,
+                                                                     omega, x);
+}
+
 cudaError_t launch_amr_apply(const AmrLevel& A, const double* r, double omega, double* x, cudaStream_t s) {
   if (A.nfree == 0) return cudaSuccess;
-  if (A.dim == 2)
-    amr_apply_kernel<2><<<nblocks(A.nfree * 4), 256, 0, s>>>(A.nfree, A.pstart, A.pown, A.rows, A.fixed, r, omega, x);
-  else
-    amr_apply_kernel<3><<<nblocks(A.nfree * 4), 256, 0, s>>>(A.nfree, A.pstart, A.pown, A.rows, A.fixed, r, omega, x);
+  const int t = amr_apply_lanes(A.nfree);
+  if (A.dim == 2) {
+    if (t == 4) apply_as<2, 4>(A, r, omega, x, s);
+    else if (t == 8) apply_as<2, 8>(A, r, omega, x, s);
+    else apply_as<2, 16>(A, r, omega, x, s);
+  } else {
+    if (t == 4) apply_as<3, 4>(A, r, omega, x, s);
+    else if (t == 8) apply_as<3, 8>(A, r, omega, x, s);
+    else apply_as<3, 16>(A, r, omega, x, s);
+  }
   note_launches(1);
   return cudaGetLastError();
 }

@@ -696,6 +696,12 @@ fc_status setup_amr(fc_handle h, const fc_grid* g, const fc_options* o, const st
     A.nfree = Hl.nfree;
     A.maxn = maxn[li];
     const int nd = dim + 1;
+    for (long long i = 0; i < Hl.nfree; ++i) {
+      int nvd = 0;
+      for (long long t = Hl.pstart[i]; t < Hl.pstart[i + 1]; ++t) nvd += Hl.pdof[t] % nd != dim;
+      A.maxnv = std::max(A.maxnv, nvd / dim);
+      A.maxnp = std::max(A.maxnp, (int)(Hl.pstart[i + 1] - Hl.pstart[i]) - nvd);
+    }
     const long long ndof = Hl.nfree * nd;
     L.g.ndof = ndof;
     L.g.nnodes = Hl.nfree;

@@ -109,6 +109,7 @@ struct AmrLevel {
   int dim = 2;
   long long nfree = 0;
   int maxn = 0;                  // largest patch
+  int maxnv = 0, maxnp = 0;      // most velocity nodes / pressures in a patch
   int* rowptr = nullptr;
   int* col = nullptr;
   double* val = nullptr;
@@ -197,10 +198,10 @@ cudaError_t launch_amr_prolong_add(const AmrLevel& F, const double* ec, double* 
 cudaError_t launch_amr_restrict(const AmrLevel& F, const AmrLevel& C, const double* rf, double* bc, cudaStream_t s);
 cudaError_t launch_amr_dense(const AmrLevel& A, double* M, cudaStream_t s);
 // owned rows of every patch of an adaptive level (fc_patch.cu): L_i gathered
-// from the CSR, equilibrated LU with partial pivoting, rows of the owned
-// DoFs; the dense block in shared memory (a CTA per patch) when it fits,
-// else in a global workspace of amr_patch_rows_work_doubles() (ctas
-// persistent CTAs over the patches)
+// from the CSR, equilibrated, rows of the owned DoFs; a dense LU with
+// partial pivoting in shared memory (a CTA per patch, work null) when the
+// block fits, else block elimination of the velocity block in a global
+// workspace of amr_patch_rows_work_doubles() (ctas persistent CTAs)
 constexpr int kAmrMaxPatch = 2048;  // largest adaptive patch (DoFs)
 bool amr_patch_rows_in_smem(int dim, int maxn);
 int amr_patch_rows_ctas(const AmrLevel& A);

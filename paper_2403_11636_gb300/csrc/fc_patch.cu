@@ -2527,21 +2527,20 @@ __global__ void __launch_bounds__(512)
 // LU with partial pivoting, and the owned columns of (D L_i D)^-1 (= its
 // owned rows, L_i symmetric) by a CTA-cooperative solve with the d + 1 unit
 // vectors, de-scaled; rows of absent owned DoFs are zero.  The dense block
-// lives in dynamic shared memory (one CTA per patch) or, for the larger 3D
-// patches, in a per-CTA slice of a global workspace (persistent CTAs).
-// Stored per slot as a record of d + 2 doubles: the DoF index in the bits
-// of a double, then the d + 1 owned-row coefficients.
+// lives in dynamic shared memory, one CTA per patch (the patches whose
+// block fits; larger ones take the block elimination below).  Stored per
+// slot as a record of d + 2 doubles: the DoF index in the bits of a double,
+// then the d + 1 owned-row coefficients.
 template <int DIM>
 __global__ void __launch_bounds__(512)
     amr_patch_rows_kernel(long long np, const long long* __restrict__ pstart, const int* __restrict__ pdof,
                           const int* __restrict__ pown, const int* __restrict__ rp, const int* __restrict__ col,
-                          const double* __restrict__ val, double* __restrict__ rows, double* work,
-                          long long wstride, unsigned* d_err) {
+                          const double* __restrict__ val, double* __restrict__ rows, unsigned* d_err) {
   constexpr int ND = DIM + 1, REC = ND + 1;
   extern __shared__ double am[];
   __shared__ int s_piv[kAmrMaxPatch];
   __shared__ int s_flag;
-  double* base = work ? work + (long long)blockIdx.x * wstride : am;
+  double* base = am;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (long long p = blockIdx.x; p < np; p += gridDim.x) {
     const long long s0 = pstart[p];
@@ -2590,6 +2589,148 @@ __global__ void __launch_bounds__(512)
     }
     if (tid == 0 && s_flag) atomicOr(d_err, kErrSingularPatch);
     __syncthreads();  // the next patch reuses the block
+  }
+}
+
+// ---- adaptive grids, larger patches: the owned rows by block elimination.
+// The patch's velocity DoFs come node by node with all d components (the
+// constrained ones leave with their node), and the velocity block is
+// I_d (x) A_s with one scalar block A_s over the patch's velocity nodes, so
+// with B_c the pressure-velocity block of component c and C the pressure
+// block (all equilibrated as in the dense kernel, D = |diag L_i|^-1/2):
+//   W_c = A_s^-1 B_c^T,   S = C - sum_c B_c W_c,
+// and the rows of L_i^-1 (L_i symmetric) of the owned DoFs are
+//   pressure q0:         p part z,       velocity part (a, c) -(W_c z)_a,
+//                        z = S^-1 e_q0;
+//   velocity (j0, c0):   p part -y,      velocity part d_{c c0} (A_s^-1 e_j0)_a
+//                        + (W_c y)_a,    y = S^-1 (row j0 of W_c0).
+// LU with partial pivoting of A_s (n_v^3 / 3 FMA against (d n_v + n_p)^3 / 3
+// for the whole block), d n_p right-hand sides for W, LU of S.  Each CTA
+// works on its own slice of a global workspace (persistent CTAs).
+template <int DIM>
+__global__ void __launch_bounds__(512)
+    amr_patch_rows_schur_kernel(long long npatch, const long long* __restrict__ pstart, const int* __restrict__ pdof,
+                                const int* __restrict__ pown, const int* __restrict__ rp,
+                                const int* __restrict__ col, const double* __restrict__ val,
+                                double* __restrict__ rows, double* work, long long wstride, int maxnv, int maxnp,
+                                unsigned* d_err) {
+  constexpr int ND = DIM + 1, REC = ND + 1;
+  __shared__ int s_piv[kAmrMaxPatch];
+  __shared__ int s_flag, s_bad, s_nvd;
+  double* Ah = work + (long long)blockIdx.x * wstride;  // n_v x n_v row-major
+  double* Bt = Ah + (size_t)maxnv * maxnv;              // B_c^T: column c n_p + q of length n_v
+  double* W = Bt + (size_t)DIM * maxnp * maxnv;         // A_s^-1 B_c^T, same layout
+  double* S = W + (size_t)DIM * maxnp * maxnv;          // n_p x n_p row-major
+  double* Dg = S + (size_t)maxnp * maxnp;               // scaling per patch DoF
+  double* Z = Dg + (size_t)DIM * maxnv + maxnp;         // d + 1 solves with S, column-major
+  double* U0 = Z + (size_t)ND * maxnp;                  // A_s^-1 e_j0
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto entry = [&](int row, int cj) {
+    int lo = rp[row], hi = rp[row + 1] - 1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) >> 1;
+      const int c = col[mid];
+      if (c == cj) return val[mid];
+      if (c < cj) lo = mid + 1; else hi = mid - 1;
+    }
+    return 0.0;
+  };
+  for (long long p = blockIdx.x; p < npatch; p += gridDim.x) {
+    const long long s0 = pstart[p];
+    const int n = (int)(pstart[p + 1] - s0);
+    const int* dof = pdof + s0;
+    if (tid == 0) { s_flag = 0; s_bad = 0; s_nvd = n; }
+    __syncthreads();
+    for (int j = tid; j < n; j += nt)
+      if (dof[j] % ND == DIM) atomicMin(&s_nvd, j);
+    __syncthreads();
+    const int nvd = s_nvd, npp = n - nvd, nv = nvd / DIM;
+    for (int j = tid; j < n; j += nt) {
+      const int c = j % DIM;
+      const bool ok = j >= nvd ? dof[j] % ND == DIM : (dof[j] % ND == c && dof[j] - c == dof[j - c]);
+      if (!ok) s_bad = 1;
+    }
+    if (tid == 0 && (nvd % DIM != 0 || nv > maxnv || npp > maxnp)) s_bad = 1;
+    __syncthreads();
+    if (s_bad) {
+      if (tid == 0) atomicOr(d_err, kErrBadIndex);
+      continue;  // uniform: every thread read s_bad after the barrier
+    }
+    for (int t = tid; t < nv * nv; t += nt) Ah[t] = entry(dof[(t / nv) * DIM], dof[(t % nv) * DIM]);
+    for (int t = tid; t < DIM * npp * nv; t += nt) {
+      const int a = t % nv, cq = t / nv, c = cq / npp, q = cq % npp;
+      Bt[t] = entry(dof[a * DIM + c], dof[nvd + q]);
+    }
+    for (int t = tid; t < npp * npp; t += nt) S[t] = entry(dof[nvd + t / npp], dof[nvd + t % npp]);
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+      const double d = j < nvd ? fabs(Ah[(size_t)(j / DIM) * nv + j / DIM]) : fabs(S[(size_t)(j - nvd) * npp + j - nvd]);
+      Dg[j] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    for (int t = tid; t < nv * nv; t += nt) Ah[t] = Dg[(t / nv) * DIM] * Ah[t] * Dg[(t % nv) * DIM];
+    for (int t = tid; t < DIM * npp * nv; t += nt) {
+      const int a = t % nv, cq = t / nv, c = cq / npp, q = cq % npp;
+      const double v = Dg[a * DIM + c] * Bt[t] * Dg[nvd + q];
+      Bt[t] = v;
+      W[t] = v;
+    }
+    for (int t = tid; t < npp * npp; t += nt) S[t] = Dg[nvd + t / npp] * S[t] * Dg[nvd + t % npp];
+    __syncthreads();
+    cta_lu(Ah, nv, nv, s_piv, &s_flag);
+    cta_lu_solve_multi(Ah, nv, s_piv, W, DIM * npp);
+    for (int t = tid; t < npp * npp; t += nt) {
+      const int q = t / npp, r = t % npp;
+      double acc = S[t];
+      for (int c = 0; c < DIM; ++c) {
+        const double* bq = Bt + (size_t)(c * npp + q) * nv;
+        const double* wr = W + (size_t)(c * npp + r) * nv;
+        for (int a = 0; a < nv; ++a) acc = fma(-bq[a], wr[a], acc);
+      }
+      S[t] = acc;
+    }
+    __syncthreads();
+    cta_lu(S, npp, npp, s_piv + nv, &s_flag);
+    // right-hand sides with S: row j0 of W_k for an owned velocity
+    // component k, e_q0 for the owned pressure; A_s^-1 e_j0 for the owned node
+    int jn = -1;
+    for (int k = 0; k < DIM; ++k)
+      if (pown[p * ND + k] >= 0) jn = pown[p * ND + k] / DIM;
+    for (int t = tid; t < ND * npp; t += nt) {
+      const int k = t / npp, q = t % npp, o = pown[p * ND + k];
+      Z[t] = o < 0 ? 0.0 : (k < DIM ? W[(size_t)(k * npp + q) * nv + o / DIM] : (q == o - nvd ? 1.0 : 0.0));
+    }
+    for (int a = tid; a < nv; a += nt) U0[a] = a == jn ? 1.0 : 0.0;
+    __syncthreads();
+    cta_lu_solve_multi(S, npp, s_piv + nv, Z, ND);
+    if (jn >= 0) cta_lu_solve_multi(Ah, nv, s_piv, U0, 1);
+    double* out = rows + REC * s0;
+    for (int t = tid; t < REC * n; t += nt) {
+      const int j = t / REC, f = t % REC;
+      if (f == 0) {
+        out[t] = __longlong_as_double((long long)dof[j]);
+        continue;
+      }
+      const int k = f - 1, o = pown[p * ND + k];
+      if (o < 0) {
+        out[t] = 0.0;
+        continue;
+      }
+      const double* z = Z + (size_t)k * npp;
+      const double sg = k < DIM ? 1.0 : -1.0;
+      double v;
+      if (j < nvd) {
+        const int a = j / DIM, c = j % DIM;
+        double acc = 0.0;
+        for (int q = 0; q < npp; ++q) acc = fma(W[(size_t)(c * npp + q) * nv + a], z[q], acc);
+        v = sg * acc + (k < DIM && c == k ? U0[a] : 0.0);
+      } else {
+        v = -sg * z[j - nvd];
+      }
+      out[t] = Dg[o] * v * Dg[j];
+    }
+    if (tid == 0 && s_flag) atomicOr(d_err, kErrSingularPatch);
+    __syncthreads();  // the next patch reuses the workspace
   }
 }
 
@@ -2810,6 +2951,10 @@ cudaError_t launch_q2_apply(int dim, const Q2Grid& q, const double* coef, const 
 
 namespace {
 size_t amr_block_doubles(int dim, int n) { return (size_t)n * n + (size_t)(dim + 2) * n; }
+size_t amr_schur_doubles(int dim, int nv, int np) {
+  return (size_t)nv * nv + 2 * (size_t)dim * np * nv + (size_t)np * np + (size_t)dim * nv + np +
+         (size_t)(dim + 1) * np + nv;
+}
 constexpr size_t kAmrSmemBytes = 216 * 1024;  // + 8 KB of pivots within the 227 KB per CTA
 }  // namespace
 
@@ -2824,25 +2969,28 @@ int amr_patch_rows_ctas(const AmrLevel& A) {
 }
 
 size_t amr_patch_rows_work_doubles(const AmrLevel& A, int ctas) {
-  return (size_t)ctas * amr_block_doubles(A.dim, A.maxn);
+  return (size_t)ctas * amr_schur_doubles(A.dim, A.maxnv, A.maxnp);
 }
 
 cudaError_t launch_amr_patch_rows(const AmrLevel& A, double* work, int ctas, unsigned* d_err, cudaStream_t s) {
   if (A.nfree == 0) return cudaSuccess;
   if (A.maxn > kAmrMaxPatch) return cudaErrorInvalidValue;
-  const long long wstride = (long long)amr_block_doubles(A.dim, A.maxn);
-  auto kern = A.dim == 2 ? amr_patch_rows_kernel<2> : amr_patch_rows_kernel<3>;
   if (work == nullptr) {
+    // dense block in shared memory, one CTA per patch
     if (!amr_patch_rows_in_smem(A.dim, A.maxn)) return cudaErrorInvalidValue;
-    const size_t smem = sizeof(double) * (size_t)wstride;
+    auto kern = A.dim == 2 ? amr_patch_rows_kernel<2> : amr_patch_rows_kernel<3>;
+    const size_t smem = sizeof(double) * amr_block_doubles(A.dim, A.maxn);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)A.nfree, 256, smem, s>>>(A.nfree, A.pstart, A.pdof, A.pown, A.rowptr, A.col, A.val, A.rows,
-                                               nullptr, 0, d_err);
+                                               d_err);
   } else {
+    // block elimination in the global workspace, persistent CTAs
     if (ctas <= 0) return cudaErrorInvalidValue;
+    auto kern = A.dim == 2 ? amr_patch_rows_schur_kernel<2> : amr_patch_rows_schur_kernel<3>;
     kern<<<(unsigned)ctas, 512, 0, s>>>(A.nfree, A.pstart, A.pdof, A.pown, A.rowptr, A.col, A.val, A.rows, work,
-                                        wstride, d_err);
+                                        (long long)amr_schur_doubles(A.dim, A.maxnv, A.maxnp), A.maxnv, A.maxnp,
+                                        d_err);
   }
   note_launches(1);
   return cudaGetLastError();

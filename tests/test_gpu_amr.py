@@ -104,6 +104,22 @@ def test_amr_sweep(fc, oracles, name):
         assert rel(got - x0, want - x0) <= SWEEP_TOL, lv
 
 
+@pytest.mark.parametrize("lanes", ["4", "8", "16"])
+@pytest.mark.parametrize("name", ["ch128", "oct32"])
+def test_amr_sweep_every_lane_count(fc, oracles, name, lanes, monkeypatch):
+    """The apply's lanes per patch (chosen by level size) forced to each
+    value: the same sweep as the oracle's."""
+    monkeypatch.setenv("FC_AMR_LANES", lanes)
+    p = PROBS[name]
+    s = solver(fc, p)
+    L = oracles[name].levels[-1]
+    x0 = inputs.uniform_array(L.ndof, 81)
+    b = inputs.uniform_array(L.ndof, 82)
+    want = L.sweep(b, x0)
+    got = s.smooth(x0, b).cpu().numpy()
+    assert rel(got - x0, want - x0) <= SWEEP_TOL
+
+
 @pytest.mark.parametrize("name", ["ch64", "replay", "oct16", "oct32"])
 def test_amr_transfers_and_coarse_solve(fc, oracles, name):
     p = PROBS[name]
