@@ -736,15 +736,33 @@ def run_replay(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
+            apply = None
             if amr:
                 ups = its * sum(s.ndof(lv) for lv in range(2, nlev + 1)) * (p.nu_pre + p.nu_post)
                 dofs = s.ndof()
+                # the finest-level apply alone: 10 sweeps under the per-launch profiler
+                X = torch.zeros_like(b)
+                s.smooth_(X, b, nsweeps=2)
+                s.profile(True)
+                s.smooth_(X, b, nsweeps=10)
+                na, ma, ba = s.profile_read(4)
+                s.profile(False)
+                torch.cuda.synchronize()
+                avg = ma / max(na, 1)
+                flop = float(s.info()["bytes"][6])
+                tf, _ = fp64_peak(torch)
+                hbm, _ = peaks()
+                apply = {"ms": avg, "flop_per_launch": flop, "bytes_per_launch": ba,
+                         "frac_of_fp64_peak": flop / (avg * 1e-3) / 1e12 / tf if avg else None,
+                         "hbm_frac": ba / (avg * 1e-3) / 1e9 / hbm if avg else None}
             else:
                 ups, dofs = updates_per_solve(p, its), p.ndof()
             rows.append({"grid": f"{nx}x{ny}" + (" lattice, adaptive" if amr else ""), "levels": nlev,
                          "dofs": dofs, "cycles": its, "reduction": red,
                          "solve_ms": ms, "ms_per_cycle": ms / max(its, 1), "setup_ms": setup_ms,
                          "sweep_updates_per_s": ups / (ms * 1e-3)})
+            if apply:
+                rows[-1]["finest_apply"] = apply
             s.close()
         except Exception as e:
             rows.append({"grid": f"{nx}x{ny}", "error": str(e)[:200]})
