@@ -609,9 +609,15 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// d += omega L_i^{-1} r on the owned DoFs (PT 1: float32 rows, 2: bfloat16)
+// d += omega L_i^{-1} r on the owned DoFs (PT 1: float32 rows, 2: bfloat16).
+// The 2D loop is bound by the latency of its loads (rows from the cache for
+// the shared class blocks, residual gathers): three 512-thread CTAs per SM
+// (40 registers, a few per-chunk values in local memory) keep more loads in
+// flight than the 64 registers the compiler picks unbounded (0.170 against
+// 0.200 ms per launch on 256 uneven problems; capping the registers with a
+// shallower unroll instead of spilling ran 0.32 ms).
 template <int DIM, int PT, int TPP>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, DIM == 2 ? 3 : 1)
     f_apply_kernel(const BSeg* __restrict__ segs, const Chunk* __restrict__ ch, int nch,
                    const int* __restrict__ state, int gate) {
   constexpr int ND = DIM + 1, NSLOT = DIM == 3 ? 402 : 59;

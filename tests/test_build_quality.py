@@ -4,6 +4,13 @@ A spill in the smoother's apply or residual kernels turns into local-memory
 traffic on every patch or node, so each of them is compiled for sm_103a
 with the library's own flags plus ptxas's resource report, and the report
 must show no spill stores.  Needs only nvcc (no GPU).
+
+One measured exception: the 2D batched float apply (`f_apply_kernel<2, ...>`)
+is compiled for three 512-thread CTAs per SM, which leaves at most 64 bytes
+of per-chunk values in local memory (L1-resident).  It runs 0.170 ms per
+launch on the 256-problem batch against 0.200 ms without the bound; the
+spill-free ways to the same occupancy (40 registers with the slot loop
+unrolled once or twice) ran 0.32 ms.
 """
 import concurrent.futures as cf
 import os
@@ -24,6 +31,10 @@ HOT = {
     "fc_batch.cu": ("f_apply_kernel", "f_residual_kernel", "b_apply_kernel", "f_restrict_kernel",
                     "f_prolong_kernel"),
 }
+
+
+# the measured exception above: 2D instances of the batched float apply
+ALLOW = re.compile(r"f_apply_kernelILi2E")
 
 
 def resources(src, tmp):
@@ -61,5 +72,5 @@ def test_hot_kernels_do_not_spill(reports, src):
     # every listed kernel family is present (the pattern still matches the names)
     for p in HOT[src]:
         assert any(re.search(r"\d" + p + r"I", k) for k in hot), (src, p)
-    spilling = {k: v for k, v in hot.items() if v > 0}
+    spilling = {k: v for k, v in hot.items() if v > 0 and not (ALLOW.search(k) and v <= 64)}
     assert not spilling, spilling
