@@ -632,18 +632,16 @@ __global__ void __launch_bounds__(256)
       for (int k = 0; k < ND; ++k) y[k] = fma(__ldcs(q + 1 + k), rv, y[k]);
     }
   }
-#pragma unroll
-  for (int k = 0; k < ND; ++k)
-#pragma unroll
-    for (int o = TPP / 2; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
-  if (!valid || lane >= ND) return;
-  const long long d = i * ND + lane;
-  double yk = y[0];
-#pragma unroll
-  for (int k = 1; k < ND; ++k)
-    if (lane == k) yk = y[k];
+  // the four row sums (2D: the fourth is zero) reduce-scattered over the
+  // TPP lanes: the lanes with lane % (TPP / 4) == 0 write row `row`
+  constexpr int Q = TPP / 4;
+  const double y4[4] = {y[0], y[1], y[2], ND == 4 ? y[ND - 1] : 0.0};
+  int row = 0;
+  const double yk = reduce_scatter4<TPP>(y4, lane, &row);
+  if (!valid || lane % Q != 0 || row >= ND) return;
+  const long long d = i * ND + row;
   if (fixed[d]) x[d] += r[d];
-  else if (pown[i * ND + lane] >= 0) x[d] += omega * yk;
+  else if (pown[i * ND + row] >= 0) x[d] += omega * yk;
 }
 
 // x_f += P e_c per component, constrained fine DoFs left alone
@@ -707,13 +705,9 @@ static int amr_apply_lanes(long long npatch) {
     const int t = atoi(e);
     if (t == 4 || t == 8 || t == 16) return t;
   }
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 1;
-  }
+  int per_sm = 0, nsm = 0;  // the current device's SM count (cached per device, thread-safe)
+  if (persistent_ctas((const void*)amr_apply_kernel<2, 4>, 256, 0, &per_sm, &nsm) != cudaSuccess || nsm <= 0)
+    nsm = 1;
   const long long want = 2LL * nsm * 2048;
   for (int t = 4; t < 16; t *= 2)
     if (npatch * t >= want) return t;

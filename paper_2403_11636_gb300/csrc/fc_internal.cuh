@@ -77,6 +77,29 @@ struct Q2Grid {
 
 // Slot layout of the cached rows: nslot = 5^d * d + 3^d.
 inline __host__ __device__ int nslot_u(int dim) { return dim == 3 ? 375 : 50; }
+// Sum of four per-lane partial sums over a group of TPP lanes (TPP >= 4, a
+// power of two, groups aligned within the warp) as a reduce-scatter: the
+// first exchange halves the values a lane carries, the second halves them
+// again, the remaining ones add a single value.  A lane ends with the full
+// sum of value *c (c = 2 * bit(TPP/2) + bit(TPP/4) of its group lane); every
+// FP64 add counts on this part (FP64 at 1/64 of the FP32 rate), and this
+// takes 3 + log2(TPP/4) adds per lane instead of 4 log2(TPP).
+template <int TPP>
+__device__ __forceinline__ double reduce_scatter4(const double* y, int lane, int* c) {
+  static_assert(TPP >= 4 && (TPP & (TPP - 1)) == 0, "group of at least 4 lanes");
+  const bool h1 = lane & (TPP / 2), h2 = lane & (TPP / 4);
+  double k0 = h1 ? y[2] : y[0], k1 = h1 ? y[3] : y[1];
+  const double s0 = h1 ? y[0] : y[2], s1 = h1 ? y[1] : y[3];
+  k0 += __shfl_xor_sync(0xffffffffu, s0, TPP / 2);
+  k1 += __shfl_xor_sync(0xffffffffu, s1, TPP / 2);
+  double k = h2 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, h2 ? k0 : k1, TPP / 4);
+#pragma unroll
+  for (int o = TPP / 8; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+  *c = (h1 ? 2 : 0) + (h2 ? 1 : 0);
+  return k;
+}
+
 inline __host__ __device__ int nslot(int dim) { return dim == 3 ? 402 : 59; }
 
 // Adaptive space-tree grids, quadtrees in 2D and octrees in 3D (fc_amr.cu):

@@ -515,28 +515,6 @@ __device__ __forceinline__ T pick(const T* v, int c) {
   return r;
 }
 
-// Sum of four per-lane partial sums over a group of TPP lanes (TPP >= 4, a
-// power of two, groups aligned within the warp) as a reduce-scatter: the
-// first exchange halves the values a lane carries, the second halves them
-// again, the remaining ones add a single value.  A lane ends with the full
-// sum of value *c (c = 2 * bit(TPP/2) + bit(TPP/4) of its group lane); every
-// FP64 add counts on this part (FP64 at 1/64 of the FP32 rate), and this
-// takes 3 + log2(TPP/4) adds per lane instead of 4 log2(TPP).
-template <int TPP>
-__device__ __forceinline__ double reduce_scatter4(const double* y, int lane, int* c) {
-  static_assert(TPP >= 4 && (TPP & (TPP - 1)) == 0, "group of at least 4 lanes");
-  const bool h1 = lane & (TPP / 2), h2 = lane & (TPP / 4);
-  double k0 = h1 ? y[2] : y[0], k1 = h1 ? y[3] : y[1];
-  const double s0 = h1 ? y[0] : y[2], s1 = h1 ? y[1] : y[3];
-  k0 += __shfl_xor_sync(0xffffffffu, s0, TPP / 2);
-  k1 += __shfl_xor_sync(0xffffffffu, s1, TPP / 2);
-  double k = h2 ? k1 : k0;
-  k += __shfl_xor_sync(0xffffffffu, h2 ? k0 : k1, TPP / 4);
-#pragma unroll
-  for (int o = TPP / 8; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
-  *c = (h1 ? 2 : 0) + (h2 ? 1 : 0);
-  return k;
-}
 
 template <int DIM, int TPP>
 __global__ void __launch_bounds__(256)
@@ -2211,16 +2189,23 @@ __global__ void __launch_bounds__(256)
     }
     y[8] += __ldcs(cf + (size_t)j * Q2P::NROWP + 8) * r;
   }
+  // reduce-scatter of rows 0-7 over the 8 lanes (halve the rows by lane
+  // bits 2, 1, 0: lane l ends with the sum of row l) and a full sum of row 8
+  const bool b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+  double k4[4], k2[2];
 #pragma unroll
-  for (int k = 0; k < 9; ++k)
+  for (int t = 0; t < 4; ++t)
+    k4[t] = (b2 ? y[4 + t] : y[t]) + __shfl_xor_sync(0xffffffffu, b2 ? y[t] : y[4 + t], 4);
 #pragma unroll
-    for (int o = TPP / 2; o > 0; o >>= 1) y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
+  for (int t = 0; t < 2; ++t)
+    k2[t] = (b1 ? k4[2 + t] : k4[t]) + __shfl_xor_sync(0xffffffffu, b1 ? k4[t] : k4[2 + t], 2);
+  const double yl = (b0 ? k2[1] : k2[0]) + __shfl_xor_sync(0xffffffffu, b0 ? k2[0] : k2[1], 1);
+  double y8 = y[8];
+#pragma unroll
+  for (int o = TPP / 2; o > 0; o >>= 1) y8 += __shfl_xor_sync(0xffffffffu, y8, o);
   if (!valid) return;
   for (int k = lane; k < 9; k += TPP) {
-    double yk = y[0];
-#pragma unroll
-    for (int u = 1; u < 9; ++u)
-      if (k == u) yk = y[u];
+    const double yk = k < 8 ? yl : y8;
     if (k < 8) {
       const int s2 = k >> 1, c = k & 1;
       const int I = 2 * ax + (s2 & 1), J = 2 * ay + (s2 >> 1);
