@@ -544,11 +544,13 @@ def run_sweeps(args):
 def run_serve(args):
     """Serving stream: Poisson arrivals (mean 50/s) of 3D porous solves on
     grids {16,32,48,64,96}^3 with 5-200 spheres, admitted by HBM footprint
-    into a budget, FGMRES to 1e-8.  Four arms with the same slots, budget
+    into a budget, FGMRES to 1e-8.  Five arms with the same slots, budget
     and shared class blocks, so that batching and precision separate:
     batched rounds (BatchServer: the sweeps of the requests in flight share
     fc_batch launches) and per-slot streams (Server), each with float32
-    rows (the mixed-precision form) and with FP64 rows (the plain method)."""
+    rows (the mixed-precision form) and with FP64 rows (the plain method);
+    and live batching with float32 rows (requests join and leave the batch
+    between FGMRES restart cycles)."""
     from paper_2403_11636_gb300 import build, inputs
     from paper_2403_11636_gb300.serve import BatchServer, Request, Server, latency_stats
     build.build()
@@ -562,6 +564,8 @@ def run_serve(args):
             ("batched_fp32", lambda: BatchServer.gpu(budget_bytes=budget, slots=args.slots, prec="fp32", dedup=1,
                                                      tc=args.tc)),
             ("batched_fp64", lambda: BatchServer.gpu(budget_bytes=budget, slots=args.slots, prec="fp64", dedup=1)),
+            ("live_fp32", lambda: BatchServer.gpu(budget_bytes=budget, slots=args.slots, prec="fp32", dedup=1,
+                                                  tc=args.tc, live=True)),
             ("streams_fp32", lambda: Server.gpu(budget_bytes=budget, slots=args.slots, prec="fp32", dedup=1)),
             ("streams_fp64", lambda: Server.gpu(budget_bytes=budget, slots=args.slots, prec="fp64", dedup=1))):
         try:
@@ -599,6 +603,7 @@ def run_serve(args):
           "speedup_mixed_vs_plain_fp64_streams": ratio("streams_fp32", "streams_fp64"),
           "speedup_batched_vs_streams_fp32": ratio("batched_fp32", "streams_fp32"),
           "speedup_batched_vs_streams_fp64": ratio("batched_fp64", "streams_fp64"),
+          "speedup_live_vs_rounds_fp32": ratio("live_fp32", "batched_fp32"),
           "clocks": cl})
     return 0
 

@@ -12,9 +12,14 @@ one request's setup or teardown does not stall the others.
 driver thread takes every request whose setup has finished and solves them
 together as one ``fc_batch`` (each V-cycle phase one persistent launch over
 the patches of all of them, each Arnoldi step one CUDA graph, every problem
-with its own FGMRES and stopping test).  Requests whose setup finishes while
-a round runs join the next round, while setups keep overlapping the round on
-their own streams.  The batch is built with a fixed patch-apply tile, so a
+with its own FGMRES and stopping test).  In rounds (the default), requests
+whose setup finishes while a round runs join the next round, while setups
+keep overlapping the round on their own streams.  Live (``live=True``), the
+driver runs one FGMRES restart cycle at a time over the requests in flight:
+requests whose setup finished join at the next cycle boundary (starting from
+x = 0), converged ones leave after the cycle that converged them, and the
+others continue from their current iterate, which is exactly the restart of
+FGMRES(restart).  The batch is built with a fixed patch-apply tile, so a
 request's result is bit-identical alone and in any mix.
 
 ``Server`` is the unbatched form: each slot sets up and solves its own
@@ -189,15 +194,26 @@ class BatchServer:
     make the scheduler testable without a GPU; ``BatchServer.gpu(...)`` wires
     libfc in.  ``gather_s``: once a request is ready, how long the driver
     may wait for setups still running to join the same round (0: start the
-    round at once)."""
+    round at once).
+
+    With ``cycle_fn([(handle, state)], stream) -> [(iterations, relres,
+    state, converged)]`` the driver runs live: one restart cycle per call
+    over the requests in flight (state None for a request that has just
+    joined), new requests joining and converged ones (or ones past
+    ``max_iters`` iterations) leaving between cycles; a request's result
+    holds ``final_fn(state)`` of its last cycle as its solution."""
 
     def __init__(self, setup_fn: Callable, round_fn: Callable, release_fn: Callable, footprint_fn: Callable,
                  budget_bytes: float, slots: int, max_batch: int = 64, make_stream: Callable = lambda: None,
-                 clock: Callable = time.perf_counter, gather_s: float = 0.0):
+                 clock: Callable = time.perf_counter, gather_s: float = 0.0, cycle_fn: Optional[Callable] = None,
+                 max_iters: int = 400, final_fn: Callable = lambda state: state):
         if slots < 1 or max_batch < 1:
             raise ValueError("slots and max_batch must be >= 1")
         self.setup_fn = setup_fn
         self.round_fn = round_fn
+        self.cycle_fn = cycle_fn
+        self.max_iters = max_iters
+        self.final_fn = final_fn
         self.release_fn = release_fn
         self.footprint_fn = footprint_fn
         self.budget = float(budget_bytes)
@@ -210,7 +226,11 @@ class BatchServer:
     @classmethod
     def gpu(cls, budget_bytes: float = 150e9, slots: int = 8, prec: str = "fp32", dedup: int = 1,
             tc: str = "none", tile=(16, 256, 8), keep_solutions: bool = False, rtol: Optional[float] = None,
-            max_batch: int = 64, gather_s: float = 0.0):
+            max_batch: int = 64, gather_s: float = 0.0, live: bool = False, cycle_iters: int = 30):
+        """libfc form.  ``live``: one FGMRES restart cycle of ``cycle_iters``
+        iterations (the solvers' restart length) per batched call, requests
+        joining and leaving between cycles; the batch is rebuilt only when
+        its membership changes."""
         import torch
         from . import fc
 
@@ -236,11 +256,37 @@ class BatchServer:
                     B.close()
             return [(int(i), float(r), sol) for i, r, sol in zip(its, rr, sols)]
 
+        cache = {"key": None, "batch": None}
+
+        def solve_cycle(items, stream):
+            # items: [((solver, b, problem), x or None)]
+            with torch.cuda.stream(stream):
+                key = tuple(id(h[0]) for h, _ in items)
+                if cache["key"] != key:
+                    if cache["batch"] is not None:
+                        cache["batch"].close()
+                    cache["batch"] = fc.Batch([h[0] for h, _ in items], stream=stream, tile=tile)
+                    cache["key"] = key
+                B = cache["batch"]
+                bp = B.pack([h[1] for h, _ in items])
+                xp = B.pack([x if x is not None else torch.zeros_like(h[1]) for h, x in items])
+                tol = rtol if rtol is not None else items[0][0][2].rtol
+                x, its, rr = B.solve(bp, x0=xp, rtol=tol, maxit=cycle_iters)
+                xs = [v.clone() for v in B.unpack(x)]
+            return [(int(i), float(r), xv, float(r) <= tol) for i, r, xv in zip(its, rr, xs)]
+
         def release(item):
+            if cache["key"] is not None and id(item[0]) in cache["key"]:
+                cache["batch"].close()  # the batch refers to the handle being released
+                cache["key"], cache["batch"] = None, None
             item[0].close()
 
+        def final(x):
+            return x.cpu().numpy() if (keep_solutions and x is not None) else None
+
         return cls(setup, solve_round, release, footprint, budget_bytes, slots, max_batch,
-                   make_stream=lambda: torch.cuda.Stream(), gather_s=gather_s)
+                   make_stream=lambda: torch.cuda.Stream(), gather_s=gather_s,
+                   cycle_fn=solve_cycle if live else None, final_fn=final)
 
     def run(self, requests: List[Request]) -> List[BatchResult]:
         """Serve ``requests`` (arrival times relative to the call) to completion."""
@@ -313,7 +359,53 @@ class BatchServer:
                         finish(slot, fp)
                         lock.notify_all()
 
-        drv = threading.Thread(target=driver, daemon=True)
+        def live_driver():
+            active = []  # requests in flight: [req, h, slot, fp, admitted, ts, state, iterations, joined, first]
+            while True:
+                with lock:
+                    while not st["ready"] and not active and not (st["done_admitting"] and st["setting_up"] == 0):
+                        lock.wait(timeout=0.05)
+                    room = self.max_batch - len(active)
+                    joining = st["ready"][:room]
+                    del st["ready"][: len(joining)]
+                    if not active and not joining:
+                        return
+                    cyc = st["rounds"]
+                    st["rounds"] += 1
+                for (req, h, slot, fp, admitted, ts) in joining:
+                    active.append([req, h, slot, fp, admitted, ts, None, 0, self.clock(), cyc])
+                try:
+                    outs = self.cycle_fn([(a[1], a[6]) for a in active], driver_stream)
+                    err = None
+                except Exception as e:
+                    outs, err = None, repr(e)
+                t_end = self.clock()
+                keep = []
+                for k, a in enumerate(active):
+                    req, h, slot, fp, admitted, ts = a[:6]
+                    if err is None:
+                        its, rr, state, conv = outs[k]
+                        a[6] = state
+                        a[7] += int(its)
+                        if not conv and a[7] < self.max_iters:
+                            keep.append(a)
+                            continue
+                    try:
+                        self.release_fn(h)
+                    except Exception:
+                        pass
+                    with lock:
+                        if err is None:
+                            st["results"].append(BatchResult(req.rid, req.arrival, admitted, t_end - t0, a[7],
+                                                             float(rr), ts, t_end - a[8], fp,
+                                                             self.final_fn(a[6]), a[9], len(active)))
+                        else:
+                            st["errors"].append((req.rid, err))
+                        finish(slot, fp)
+                        lock.notify_all()
+                active = keep
+
+        drv = threading.Thread(target=live_driver if self.cycle_fn is not None else driver, daemon=True)
         drv.start()
         queue: List = []
         i = 0

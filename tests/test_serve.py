@@ -229,3 +229,100 @@ def test_batch_server_gather_window_fills_a_round():
     reqs = [Request(k, FP(k, 10, dur=0.01 * (k + 1)), 0.0) for k in range(4)]
     BatchServer(setup, solve_round, release, lambda p: p.fp, budget_bytes=100, slots=4, gather_s=1.0).run(reqs)
     assert st["rounds"] == [[0, 1, 2, 3]]
+
+
+class LiveFP(FP):
+    """A request of the live fakes that converges in its `cycles`-th restart
+    cycle."""
+
+    def __init__(self, rid, fp, cycles):
+        super().__init__(rid, fp)
+        self.cycles = cycles
+
+
+def make_live_fakes(setup_dur=0.01, cycle_dur=0.03):
+    """Fakes for the live driver: the state of a request counts the restart
+    cycles it has run; a cycle reports 30 iterations, or 7 and convergence
+    in the request's last cycle.  Records the members of every cycle."""
+    setup, _, release, st = make_batch_fakes(setup_dur=setup_dur)
+    st["cycles"] = []
+
+    def cycle(items, stream):
+        st["cycles"].append([h.rid for h, _ in items])
+        time.sleep(cycle_dur)
+        out = []
+        for h, state in items:
+            done = (state or 0) + 1
+            conv = done >= h.cycles
+            out.append((7 if conv else 30, 1e-9 if conv else 1e-3, done, conv))
+        return out
+
+    return setup, cycle, release, st
+
+
+def test_live_batch_server_joins_and_leaves_between_cycles():
+    setup, cycle, release, st = make_live_fakes(cycle_dur=0.05)
+    reqs = [Request(0, LiveFP(0, 10, 6), 0.0), Request(1, LiveFP(1, 10, 2), 0.0), Request(2, LiveFP(2, 10, 2), 0.12)]
+    res = BatchServer(setup, None, release, lambda p: p.fp, budget_bytes=100, slots=8, cycle_fn=cycle).run(reqs)
+    assert [r.rid for r in res] == [0, 1, 2]
+    cyc = st["cycles"]
+    # request 2 arrives while request 0 is still cycling and joins a live batch with it
+    assert any(0 in c and 2 in c for c in cyc)
+    # each request runs exactly its cycles and leaves after the last one
+    assert sum(0 in c for c in cyc) == 6 and sum(1 in c for c in cyc) == 2 and sum(2 in c for c in cyc) == 2
+    # iterations add up over the cycles: 30 per unconverged cycle, 7 in the last
+    assert res[0].iterations == 5 * 30 + 7 and res[1].iterations == 30 + 7
+    assert res[2].finished < res[0].finished
+    assert all(r.relres <= 1e-9 for r in res) and st["mem"] == 0 and st["n"] == 0
+
+
+def test_live_batch_server_budget_slots_and_cap():
+    setup, cycle, release, st = make_live_fakes(cycle_dur=0.01)
+    reqs = [Request(k, LiveFP(k, 30 + 10 * (k % 3), 1 + k % 4), arrival=0.004 * k) for k in range(12)]
+    res = BatchServer(setup, None, release, lambda p: p.fp, budget_bytes=150, slots=4, cycle_fn=cycle,
+                      max_iters=60).run(reqs)
+    assert [r.rid for r in res] == list(range(12))
+    assert st["max_mem"] <= 150 and st["max_n"] <= 4
+    assert max(len(c) for c in st["cycles"]) >= 2
+    # the iteration cap ends a request after the cycle that reaches it
+    for r in res:
+        need = 1 + r.rid % 4
+        assert r.iterations == (30 * (need - 1) + 7 if need <= 2 else 60)
+    assert st["mem"] == 0 and st["n"] == 0
+
+
+def test_live_batch_server_failed_cycle_reports_members():
+    setup, _, release, st = make_live_fakes()
+
+    def cycle(items, stream):
+        raise RuntimeError("cycle failed")
+
+    reqs = [Request(k, LiveFP(k, 10, 1), 0.0) for k in range(3)]
+    with pytest.raises(RuntimeError) as e:
+        BatchServer(setup, None, release, lambda p: p.fp, budget_bytes=100, slots=4, cycle_fn=cycle).run(reqs)
+    assert "requests failed" in str(e.value)
+    assert st["mem"] == 0 and st["n"] == 0
+
+
+@pytest.mark.gpu
+def test_live_batched_results_same_alone_and_in_the_mix():
+    """Live batching: requests join and leave between FGMRES restart cycles;
+    a request's solution is bit-identical served alone and in the mix, and
+    every request reaches the tolerance."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2403_11636_gb300 import build
+    build.build()
+    probs = [inputs.porous_3d(k, n=16, nspheres=5 + 3 * k, nlevels=3) for k in range(4)]
+    probs.append(inputs.porous_3d(9, n=32, nspheres=20, nlevels=4))
+    for prec in ("fp32", "fp64"):
+        alone = BatchServer.gpu(budget_bytes=150e9, slots=1, prec=prec, keep_solutions=True, live=True).run(
+            [Request(k, p, 0.0) for k, p in enumerate(probs)])
+        mixed = BatchServer.gpu(budget_bytes=150e9, slots=5, prec=prec, keep_solutions=True, live=True).run(
+            [Request(k, p, 0.02 * k) for k, p in enumerate(probs)])
+        assert all(a.round_size == 1 for a in alone)
+        assert max(m.round_size for m in mixed) >= 2
+        for a, m in zip(alone, mixed):
+            assert a.iterations == m.iterations and m.relres <= 1e-8
+            np.testing.assert_array_equal(a.solution, m.solution)
