@@ -319,13 +319,11 @@ int amr_assemble(const AmrTree& T, const LevelGeom& g, const std::vector<double>
       for (long long j : adj[f])
         for (int e = 0; e < nd; ++e) H.col[p++] = (int)(j * nd + e);
     }
-  auto add = [&](long long row, long long colj, double v) {
-    int lo = H.rowptr[row], hi = H.rowptr[row + 1] - 1;
-    while (lo <= hi) {
-      const int mid = (lo + hi) / 2;
-      if (H.col[mid] == colj) { H.val[mid] = H.val[mid] + v; return; }
-      if (H.col[mid] < colj) lo = mid + 1; else hi = mid - 1;
-    }
+  // every row of node f has the columns of adj[f] x (the d + 1 components),
+  // so entry (f, c; g, e) sits at rowptr[f nd + c] + nd pos(g in adj[f]) + e
+  auto slot_of = [&](long long f, long long g) {
+    const auto& v = adj[f];
+    return (int)(std::lower_bound(v.begin(), v.end(), g) - v.begin()) * nd;
   };
   const size_t nl = H.leaf.size() / 4;
   for (size_t q = 0; q < nl; ++q) {
@@ -353,16 +351,19 @@ int amr_assemble(const AmrTree& T, const LevelGeom& g, const std::vector<double>
         const long long fa = en[a][ta];
         const double wa = ew[a][ta];
         for (int c = 0; c < dim; ++c) H.rhs[fa * nd + c] = H.rhs[fa * nd + c] + wa * F[c * NC + a];
+        double* rows[4];
+        for (int c = 0; c < nd; ++c) rows[c] = &H.val[H.rowptr[fa * nd + c]];
         for (int b = 0; b < NC; ++b)
           for (int tb = 0; tb < ek[b]; ++tb) {
             const long long fb = en[b][tb];
             const double w = wa * ew[b][tb];
+            const int sb = slot_of(fa, fb);
             for (int c = 0; c < dim; ++c) {
-              add(fa * nd + c, fb * nd + c, w * A[a * NC + b]);
-              add(fa * nd + c, fb * nd + dim, w * B[(c * NC + a) * NC + b]);
-              add(fa * nd + dim, fb * nd + c, w * B[(c * NC + b) * NC + a]);
+              rows[c][sb + c] = rows[c][sb + c] + w * A[a * NC + b];
+              rows[c][sb + dim] = rows[c][sb + dim] + w * B[(c * NC + a) * NC + b];
+              rows[dim][sb + c] = rows[dim][sb + c] + w * B[(c * NC + b) * NC + a];
             }
-            add(fa * nd + dim, fb * nd + dim, w * C[a][b]);
+            rows[dim][sb + dim] = rows[dim][sb + dim] + w * C[a][b];
           }
       }
   }
@@ -446,22 +447,15 @@ int amr_assemble(const AmrTree& T, const LevelGeom& g, const std::vector<double>
   H.nbp.assign((size_t)nf + 1, 0);
   H.nbc.clear();
   H.nbv.clear();
-  auto at = [&](long long row, long long colj) {
-    int lo = H.rowptr[row], hi = H.rowptr[row + 1] - 1;
-    while (lo <= hi) {
-      const int mid = (lo + hi) / 2;
-      if (H.col[mid] == colj) return H.val[mid];
-      if (H.col[mid] < colj) lo = mid + 1; else hi = mid - 1;
-    }
-    return 0.0;
-  };
   for (long long f = 0; f < nf; ++f) {
-    for (long long g2 : adj[f]) {
-      H.nbc.push_back((int)g2);
-      H.nbv.push_back(at(f * nd + 0, g2 * nd + 0));
-      for (int c = 0; c < dim; ++c) H.nbv.push_back(at(f * nd + c, g2 * nd + dim));
-      for (int c = 0; c < dim; ++c) H.nbv.push_back(at(f * nd + dim, g2 * nd + c));
-      H.nbv.push_back(at(f * nd + dim, g2 * nd + dim));
+    for (size_t t = 0; t < adj[f].size(); ++t) {
+      const int sb = (int)t * nd;
+      auto at = [&](int c, int e) { return H.val[H.rowptr[f * nd + c] + sb + e]; };
+      H.nbc.push_back((int)adj[f][t]);
+      H.nbv.push_back(at(0, 0));
+      for (int c = 0; c < dim; ++c) H.nbv.push_back(at(c, dim));
+      for (int c = 0; c < dim; ++c) H.nbv.push_back(at(dim, c));
+      H.nbv.push_back(at(dim, dim));
     }
     H.nbp[f + 1] = (int)H.nbc.size();
   }
