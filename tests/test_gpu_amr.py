@@ -167,6 +167,21 @@ def test_amr_standalone_gmg(fc):
     assert rel(x.cpu().numpy(), x_or) <= 1e-6
 
 
+def test_amr_standalone_gmg_octree(fc):
+    """Standalone V(6,6) GMG (damping 0.8, a 1e9 residual reduction) on an
+    octree: the 3D duct with one sphere on a 32^3 lattice; the GPU needs the
+    oracle's cycle count."""
+    p = dataclasses.replace(inputs.channel_3d(2, n=32, nlevels=4, alpha=1e-10), amr_uniform=1,
+                            nu_pre=6, nu_post=6)
+    mg = O.AMRMG(p)
+    b = mg.rhs()
+    x_or, its_or, _ = mg.gmg_solve(b, reduction=1e-9, maxit=80)
+    s = solver(fc, p)
+    x, its, red = s.gmg_solve(s.rhs(), reduction=1e-9, maxit=80)
+    assert its == its_or and red <= 1e-9
+    assert rel(x.cpu().numpy(), x_or) <= 1e-6
+
+
 def test_amr_rejects_unsupported(fc):
     p = PROBS["ch64"]
     for kw in ({"prec": "df64"}, {"cache": "matrix"}, {"element": "q2"}, {"galerkin": True}):
