@@ -625,7 +625,7 @@ class Q2MG:
 
 
 # ---------------------------------------------------------------------------
-# Adaptive quadtree grids (fc_oracle_amr.c, which includes fc_oracle.c)
+# Adaptive space-tree grids, quadtrees and octrees (fc_oracle_amr.c, which includes fc_oracle.c)
 _SRC_AMR = os.path.join(_HERE, "fc_oracle_amr.c")
 _LIB_AMR = os.path.join(_HERE, "libfc_oracle_amr.so")
 _lib_amr = None
