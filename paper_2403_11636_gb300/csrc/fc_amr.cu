@@ -536,16 +536,16 @@ std::vector<long long> amr_leaf_cells(const AmrTree& T, const AmrHost& H, int le
 // ------------------------------------------------------------- kernels
 namespace {
 
-// r = b - L x (L x when b is null) on node blocks: 4 lanes per free node,
-// each over every 4th neighbour (index, then the record A, B_0 .. B_{d-1},
+// r = b - L x (L x when b is null) on node blocks: LPN lanes per free node,
+// each over every LPN-th neighbour (index, then the record A, B_0 .. B_{d-1},
 // T_0 .. T_{d-1}, C as 16-byte loads, then the neighbour's DoFs), a shuffle
 // sum of the d + 1 row sums
-template <int DIM>
+template <int DIM, int LPN>
 __global__ void __launch_bounds__(256)
     amr_residual_kernel(long long nf, const int* __restrict__ nbp, const int* __restrict__ nbc,
                         const double* __restrict__ nbv, const double* __restrict__ x,
                         const double* __restrict__ b, double* __restrict__ r) {
-  constexpr int LPN = 4, ND = DIM + 1, NBV = 2 * DIM + 2;
+  constexpr int ND = DIM + 1, NBV = 2 * DIM + 2;
   const int lane = threadIdx.x % LPN;
   const long long gf = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / LPN;
   const long long f = gf < nf ? gf : nf - 1;
@@ -573,16 +573,12 @@ __global__ void __launch_bounds__(256)
     }
     acc[DIM] = fma(m[NBV - 1], xs[DIM], acc[DIM]);
   }
-#pragma unroll
-  for (int o = LPN / 2; o > 0; o >>= 1)
-#pragma unroll
-    for (int c = 0; c < ND; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-  if (gf >= nf || lane >= ND) return;
-  double s = acc[0];
-#pragma unroll
-  for (int c = 1; c < ND; ++c)
-    if (lane == c) s = acc[c];
-  const long long row = f * ND + lane;
+  // the row sums (2D: a zero fourth) reduce-scattered over the LPN lanes
+  const double a4[4] = {acc[0], acc[1], acc[2], ND == 4 ? acc[ND - 1] : 0.0};
+  int c = 0;
+  const double s = reduce_scatter4<LPN>(a4, lane, &c);
+  if (gf >= nf || lane % (LPN / 4) != 0 || c >= ND) return;
+  const long long row = f * ND + c;
   r[row] = b ? b[row] - s : s;
 }
 
@@ -681,18 +677,32 @@ unsigned nblocks(long long threads) { return (unsigned)((threads + 255) / 256); 
 
 }  // namespace
 
+static int amr_apply_lanes(long long npatch);
+
+template <int DIM, int LPN>
+static void residual_as(const AmrLevel& A, const double* x, const double* b, double* r, cudaStream_t s) {
+  amr_residual_kernel<DIM, LPN><<<nblocks(A.nfree * LPN), 256, 0, s>>>(A.nfree, A.nbp, A.nbc, A.nbv, x, b, r);
+}
+
 cudaError_t launch_amr_residual(const AmrLevel& A, const double* x, const double* b, double* r, cudaStream_t s) {
   if (A.nfree == 0) return cudaSuccess;
-  if (A.dim == 2)
-    amr_residual_kernel<2><<<nblocks(A.nfree * 4), 256, 0, s>>>(A.nfree, A.nbp, A.nbc, A.nbv, x, b, r);
-  else
-    amr_residual_kernel<3><<<nblocks(A.nfree * 4), 256, 0, s>>>(A.nfree, A.nbp, A.nbc, A.nbv, x, b, r);
+  const int t = amr_apply_lanes(A.nfree);  // the apply's rule: two waves of resident threads
+  if (A.dim == 2) {
+    if (t == 4) residual_as<2, 4>(A, x, b, r, s);
+    else if (t == 8) residual_as<2, 8>(A, x, b, r, s);
+    else residual_as<2, 16>(A, x, b, r, s);
+  } else {
+    if (t == 4) residual_as<3, 4>(A, x, b, r, s);
+    else if (t == 8) residual_as<3, 8>(A, x, b, r, s);
+    else residual_as<3, 16>(A, x, b, r, s);
+  }
   note_launches(1);
   return cudaGetLastError();
 }
 
-// lanes per patch: the fewest of 4, 8, 16 that give the launch two waves of
-// resident threads (2048 per SM), so that small levels still fill the GPU;
+// lanes per patch (and per node in the residual): the fewest of 4, 8, 16
+// that give the launch two waves of resident threads (2048 per SM), so that
+// small levels still fill the GPU;
 // FC_AMR_LANES = 4, 8 or 16 in the environment fixes it (tests, tuning)
 static int amr_apply_lanes(long long npatch) {
   if (const char* e = getenv("FC_AMR_LANES")) {
