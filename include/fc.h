@@ -255,7 +255,9 @@ fc_status fc_solve_host(fc_handle h, const double* b_host, double* x_host, doubl
  * solve, [4] setup temporaries peak; [5] is a count, not bytes: patches (all
  * levels) whose float32 factorisation with iterative refinement did not
  * converge and that were rebuilt by float-pair elimination (float32 /
- * bfloat16 rows only); [6] is a count too: the algorithmic floating-point
+ * bfloat16 rows), or, for FP64 rows of 3D Q1-Q1 patches, whose equilibrated
+ * velocity block was not positive definite for the banded LDL^T
+ * factorisation and that were built by the pivoted dense LU; [6] is a count too: the algorithmic floating-point
  * operations of one patch apply on `level` with cached rows, 2 x (active
  * patch DoFs x free owned DoFs) summed over the patches (0 on level 1);
  * [7] is a count: patches (all levels) whose rows came from the float-pair

@@ -1163,7 +1163,27 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
         CK(dalloc(h, &c64, n, o->prec == FC_PREC_FP64 ? 1 : -1));
         {
           ProfScope ps(h, 3, 0.0);
-          if (o->prec == FC_PREC_FP64)
+          if (o->prec == FC_PREC_FP64 && dim == 3) {
+            // banded LDL^T of the velocity block; patches whose block is not
+            // positive definite are redone by the pivoted dense LU
+            const long long nw = work ? L.nwork : G.nnodes;
+            int *redo_node = nullptr, *redo_out = nullptr, *nredo = nullptr;
+            CK(dalloc(h, &redo_node, (size_t)std::max(nw, 1LL), -1));
+            CK(dalloc(h, &redo_out, (size_t)std::max(nw, 1LL), -1));
+            CK(dalloc(h, &nredo, 1, -1));
+            CK(cudaMemsetAsync(nredo, 0, sizeof(int), h->stream));
+            CK(launch_patch_rows_ldl(G, L.st, L.mask, c64, h->d_err, work, L.nwork, redo_node, redo_out, nredo,
+                                     h->stream));
+            int nr = 0;
+            CK(cudaMemcpyAsync(&nr, nredo, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            if (nr > 0)
+              CK(launch_patch_rows_dense_redo(G, L.st, L.mask, c64, h->d_err, redo_node, nr, redo_out, h->stream));
+            h->ldl_fallback += nr;
+            dfree(h, redo_node);
+            dfree(h, redo_out);
+            dfree(h, nredo);
+          } else if (o->prec == FC_PREC_FP64)
             CK(launch_patch_build(G, L.st, L.mask, 0, o->omega, c64, nullptr, nullptr, nullptr, nullptr,
                                   h->d_err, work, L.nwork, h->stream));
           else if (o->prec == FC_PREC_DF64)  // rows kept as float pairs: float-pair factorisation
@@ -1479,7 +1499,7 @@ fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch, si
   if (npatch) *npatch = level >= 2 ? L.g.nnodes : 0;
   if (bytes_by_part) {
     for (int k = 0; k < 8; ++k) bytes_by_part[k] = h->bytes[k];
-    bytes_by_part[5] = (size_t)h->pair_fallback;
+    bytes_by_part[5] = (size_t)(h->pair_fallback + h->ldl_fallback);
     bytes_by_part[6] = level >= 2 ? (size_t)(2 * L.active_rows) : 0;
     bytes_by_part[7] = (size_t)h->badcut;
   }

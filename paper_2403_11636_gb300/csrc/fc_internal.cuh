@@ -277,6 +277,9 @@ struct fc_handle_s {
   // float32 / bfloat16 rows: patches rebuilt by the float-pair elimination
   // because float32 refinement did not converge (all levels)
   long long pair_fallback = 0;
+  // FP64 rows (3D): patches whose velocity block was not positive definite
+  // for the banded LDL^T and took the pivoted dense LU, all levels
+  long long ldl_fallback = 0;
   // float32 / bfloat16 rows: patches given float-pair rows by the bad-cut
   // rule (fc_options.badcut_frac), all levels
   long long badcut = 0;
@@ -401,6 +404,15 @@ cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsig
 cudaError_t launch_patch_rows_ir(const LevelGeom& g, const double* st, const unsigned char* mask,
                                  double* coef64, unsigned* d_err, const int* work, long long nwork,
                                  int* redo_node, int* redo_out, int* nredo, cudaStream_t s);
+// 3D FP64 owned rows by a banded LDL^T of the velocity block; patches whose
+// block is not positive definite go to redo_node / redo_out (count nredo)
+cudaError_t launch_patch_rows_ldl(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                  double* coef64, unsigned* d_err, const int* work, long long nwork,
+                                  int* redo_node, int* redo_out, int* nredo, cudaStream_t s);
+// 3D FP64 owned rows of the redo-list patches by the pivoted dense LU
+cudaError_t launch_patch_rows_dense_redo(const LevelGeom& g, const double* st, const unsigned char* mask,
+                                         double* coef64, unsigned* d_err, const int* redo_node,
+                                         long long nredo, const int* redo_out, cudaStream_t s);
 // float-pair elimination; outidx (nullable) maps a work entry to its row block
 cudaError_t launch_patch_rows_pair(const LevelGeom& g, const double* st, const unsigned char* mask,
                                    double* coef64, unsigned* d_err, const int* work, long long nwork,
