@@ -648,7 +648,7 @@ def run_mixed(args):
                          "relres": max(rr_l),
                          "updates_per_s": sum(updates_per_solve(prob, i) for i in its_l) / (total_ms * 1e-3),
                          "cache_bytes": s.info()["bytes"][1], "badcut_patches": s.info()["bytes"][7],
-                         "refinement_fallback_patches": s.info()["bytes"][5]}
+                         "dense_lu_patches": s.info()["bytes"][5]}
                 if x64 is None:
                     x64 = xc
                 else:

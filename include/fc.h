@@ -124,7 +124,10 @@ typedef struct {
   double badcut_frac;  /* float32 / bfloat16 rows: a patch whose smallest cut-cell fluid
                           fraction over the 4^d cells its velocity nodes touch is below
                           badcut_frac gets its rows from the float-pair (FP64-class)
-                          factorisation instead of float32 factors with refinement; 0 off. */
+                          factorisation instead of float32 factors with refinement; 0 off.
+                          In 3D (Q1-Q1) every patch's rows are factored in FP64 (banded
+                          LDL^T, rounded for storage), so the rule only counts its patches
+                          (fc_info). */
   int element;         /* 0: equal-order Q1-Q1 with the local L2 pressure projection (the
                           paper's pair, Sec. 2); 1: Q2-Q1 Taylor-Hood (cache_inverse, FP64
                           rows; 2D and 3D): Q2 velocities on the half-spaced grid of 2 n_k + 1 nodes per
@@ -254,15 +257,17 @@ fc_status fc_solve_host(fc_handle h, const double* b_host, double* x_host, doubl
  * part: [0] operator, [1] patch cache, [2] vectors/workspace, [3] coarse
  * solve, [4] setup temporaries peak; [5] is a count, not bytes: patches (all
  * levels) whose float32 factorisation with iterative refinement did not
- * converge and that were rebuilt by float-pair elimination (float32 /
- * bfloat16 rows), or, for FP64 rows of 3D Q1-Q1 patches, whose equilibrated
- * velocity block was not positive definite for the banded LDL^T
- * factorisation and that were built by the pivoted dense LU; [6] is a count too: the algorithmic floating-point
+ * converge and that were rebuilt by float-pair elimination (2D float32 /
+ * bfloat16 rows), or, in 3D (FP64, float32 and bfloat16 rows, all factored
+ * in FP64), whose equilibrated velocity block was not positive definite for
+ * the banded LDL^T factorisation and that were built by the pivoted dense
+ * LU; [6] is a count too: the algorithmic floating-point
  * operations of one patch apply on `level` with cached rows, 2 x (active
  * patch DoFs x free owned DoFs) summed over the patches (0 on level 1);
- * [7] is a count: patches (all levels) whose rows came from the float-pair
- * factorisation by the bad-cut rule (fc_options.badcut_frac; float32 /
- * bfloat16 rows only).  Any pointer may be NULL. */
+ * [7] is a count: patches (all levels) that the bad-cut rule selects
+ * (fc_options.badcut_frac; float32 / bfloat16 rows only); in 2D their rows
+ * came from the float-pair factorisation, in 3D from the FP64 one that
+ * every patch takes.  Any pointer may be NULL. */
 fc_status fc_info(fc_handle h, int level, long long* ndof, long long* npatch,
                   size_t* bytes_by_part);
 

@@ -1163,9 +1163,13 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
         CK(dalloc(h, &c64, n, o->prec == FC_PREC_FP64 ? 1 : -1));
         {
           ProfScope ps(h, 3, 0.0);
-          if (o->prec == FC_PREC_FP64 && dim == 3) {
-            // banded LDL^T of the velocity block; patches whose block is not
-            // positive definite are redone by the pivoted dense LU
+          if (dim == 3 && o->prec != FC_PREC_DF64) {
+            // banded LDL^T of the velocity block in FP64; patches whose block
+            // is not positive definite are redone by the pivoted dense LU.
+            // Float32 / bfloat16 rows are these FP64 rows rounded: in 3D the
+            // FP64 band factorisation is cheaper per patch than the float32
+            // dense LU with refinement, so every patch, the badly cut ones
+            // included, is factored in FP64.
             const long long nw = work ? L.nwork : G.nnodes;
             int *redo_node = nullptr, *redo_out = nullptr, *nredo = nullptr;
             CK(dalloc(h, &redo_node, (size_t)std::max(nw, 1LL), -1));
@@ -1180,6 +1184,18 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
             if (nr > 0)
               CK(launch_patch_rows_dense_redo(G, L.st, L.mask, c64, h->d_err, redo_node, nr, redo_out, h->stream));
             h->ldl_fallback += nr;
+            if (estat) {
+              // the bad-cut rule's patches, counted (their rows are FP64 already)
+              CK(cudaMemsetAsync(nredo, 0, sizeof(int), h->stream));
+              badcut_kernel<<<(unsigned)((nw + 255) / 256), 256, 0, h->stream>>>(G, estat, work, nw, o->badcut_frac,
+                                                                               redo_node, redo_out, nredo);
+              CK(cudaGetLastError());
+              note_launches(1);
+              int nb = 0;
+              CK(cudaMemcpyAsync(&nb, nredo, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+              CK(cudaStreamSynchronize(h->stream));
+              h->badcut += nb;
+            }
             dfree(h, redo_node);
             dfree(h, redo_out);
             dfree(h, nredo);
