@@ -65,7 +65,12 @@ typedef enum {
   FC_CACHE_NONE = 2     /* gather L_i from the operator, factor and solve per apply */
 } fc_cache;
 
-/* Storage/arithmetic of the cached patch rows (cache_inverse only). */
+/* Storage/arithmetic of the cached patch rows (cache_inverse only).  The rows
+ * are computed in float64 (3D Q1-Q1: banded LDL^T of the velocity block, or
+ * the pivoted dense LU where that block is not positive definite) and then
+ * stored in the chosen precision; in 2D, float-pair rows come from a
+ * float-pair elimination and float32 / bfloat16 rows from float32 factors
+ * with two refinement steps. */
 typedef enum {
   FC_PREC_FP64 = 0, /* float64 rows, float64 arithmetic */
   FC_PREC_FP32 = 1, /* float32 rows, float32 accumulation */

@@ -1163,11 +1163,12 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
         CK(dalloc(h, &c64, n, o->prec == FC_PREC_FP64 ? 1 : -1));
         {
           ProfScope ps(h, 3, 0.0);
-          if (dim == 3 && o->prec != FC_PREC_DF64) {
+          if (dim == 3) {
             // banded LDL^T of the velocity block in FP64; patches whose block
             // is not positive definite are redone by the pivoted dense LU.
-            // Float32 / bfloat16 rows are these FP64 rows rounded: in 3D the
-            // FP64 band factorisation is cheaper per patch than the float32
+            // Float-pair, float32 and bfloat16 rows are these FP64 rows split
+            // or rounded: in 3D the FP64 band factorisation is cheaper per
+            // patch than the float-pair elimination and than the float32
             // dense LU with refinement, so every patch, the badly cut ones
             // included, is factored in FP64.
             const long long nw = work ? L.nwork : G.nnodes;
