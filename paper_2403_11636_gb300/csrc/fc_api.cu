@@ -374,7 +374,7 @@ fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nswe
                             h->stream));
     } else if (h->opt.cache == FC_CACHE_MATRIX) {
       ProfScope ps(h, 0, (double)L.fac_bytes);
-      CK(launch_factor_apply(L.g, L.fac, L.fpiv, L.mask, L.rpad, h->opt.omega, x, L.prow, h->stream));
+      CK(launch_factor_apply(L.g, L.st, factor_store(L), L.mask, L.rpad, h->opt.omega, x, L.prow, h->stream));
     } else {
       ProfScope ps(h, 0, 0.0);
       CK(launch_patch_build(L.g, L.st, L.mask, 2, h->opt.omega, nullptr, nullptr, nullptr, L.rpad, x,
@@ -1259,8 +1259,41 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
         CK(dalloc(h, &L.fpiv, (size_t)L.nwork * factor_ints(dim), 1));
         L.fac_bytes = (size_t)L.nwork * (factor_doubles(dim) * 8 + factor_ints(dim) * 4);
         ProfScope ps(h, 3, 0.0);
-        CK(launch_patch_build(G, L.st, L.mask, 1, o->omega, nullptr, L.fac, L.fpiv, nullptr, nullptr,
-                              h->d_err, work, L.nwork, h->stream));
+        if (dim == 3) {
+          // band factor records by the banded LDL^T; the patches whose
+          // velocity block is not positive definite get dense records
+          const long long nw = work ? L.nwork : G.nnodes;
+          int *rn = nullptr, *ro = nullptr, *nr_d = nullptr;
+          CK(dalloc(h, &rn, (size_t)std::max(nw, 1LL), -1));
+          CK(dalloc(h, &ro, (size_t)std::max(nw, 1LL), -1));
+          CK(dalloc(h, &nr_d, 1, -1));
+          CK(cudaMemsetAsync(nr_d, 0, sizeof(int), h->stream));
+          CK(launch_band_factors(G, L.st, L.mask, L.fac, L.fpiv, h->d_err, work, L.nwork, rn, ro, nr_d, h->stream));
+          int nr = 0;
+          CK(cudaMemcpyAsync(&nr, nr_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+          CK(cudaStreamSynchronize(h->stream));
+          if (nr > 0) {
+            CK(dalloc(h, &L.facd, (size_t)nr * dense_factor_doubles(dim), 1));
+            CK(dalloc(h, &L.fpivd, (size_t)nr * dense_factor_ints(dim), 1));
+            L.fac_bytes += (size_t)nr * (dense_factor_doubles(dim) * 8 + dense_factor_ints(dim) * 4);
+            CK(launch_dense_factor_redo(G, L.st, L.mask, L.facd, L.fpivd, h->d_err, rn, ro, nr, L.fpiv, h->stream));
+            CK(dalloc(h, &L.lnode, (size_t)G.nnodes, 1));
+            CK(dalloc(h, &L.lrec, (size_t)G.nnodes, 1));
+            CK(cudaMemsetAsync(nr_d, 0, sizeof(int), h->stream));
+            CK(launch_dense_list(G, L.prow, L.fpiv, L.lnode, L.lrec, nr_d, h->stream));
+            int nl = 0;
+            CK(cudaMemcpyAsync(&nl, nr_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+            L.nlist = nl;
+          }
+          h->ldl_fallback += nr;
+          dfree(h, rn);
+          dfree(h, ro);
+          dfree(h, nr_d);
+        } else {
+          CK(launch_patch_build(G, L.st, L.mask, 1, o->omega, nullptr, L.fac, L.fpiv, nullptr, nullptr,
+                                h->d_err, work, L.nwork, h->stream));
+        }
       }
       CK(cudaStreamSynchronize(h->stream));
       dfree(h, work);
@@ -1655,6 +1688,7 @@ fc_status fc_destroy(fc_handle h) {
   for (int l = 0; l < kMaxLevels; ++l) {
     Level& L = h->lev[l];
     dfree(h, L.st); dfree(h, L.mask); dfree(h, L.dead); dfree(h, L.wfix); dfree(h, L.coef); dfree(h, L.fac); dfree(h, L.fpiv);
+    dfree(h, L.facd); dfree(h, L.fpivd); dfree(h, L.lnode); dfree(h, L.lrec);
     dfree(h, L.x); dfree(h, L.b); dfree(h, L.r); dfree(h, L.rpad); dfree(h, L.rpad32);
     dfree(h, L.st2); dfree(h, L.xp2); dfree(h, L.bp2); dfree(h, L.prow);
     dfree(h, L.st32); dfree(h, L.d32); dfree(h, L.b32);

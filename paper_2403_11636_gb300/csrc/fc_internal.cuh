@@ -159,9 +159,16 @@ struct Level {
   // patch cache
   void* coef = nullptr;         // cache_inverse rows
   size_t coef_bytes = 0;
-  double* fac = nullptr;        // cache_matrix factors
+  double* fac = nullptr;        // cache_matrix factors (3D: band records)
   int* fpiv = nullptr;
   size_t fac_bytes = 0;
+  // 3D cache_matrix: dense records of the patches whose velocity block was
+  // not positive definite, and the nodes (with record index) that use them
+  double* facd = nullptr;
+  int* fpivd = nullptr;
+  int* lnode = nullptr;
+  int* lrec = nullptr;
+  long long nlist = 0;
   // level vectors (device)
   double* x = nullptr;          // V-cycle correction on this level
   double* b = nullptr;          // right-hand side on this level
@@ -421,9 +428,44 @@ cudaError_t launch_patch_rows_pair(const LevelGeom& g, const double* st, const u
 cudaError_t launch_patch_apply(const LevelGeom& g, fc_prec prec, const void* coef,
                                const unsigned char* mask, const double* rpad, const float* rpad32,
                                double omega, double* x, const int* prow, cudaStream_t s);
-cudaError_t launch_factor_apply(const LevelGeom& g, const double* fac, const int* fpiv,
-                                const unsigned char* mask, const double* rpad, double omega,
-                                double* x, const int* prow, cudaStream_t s);
+// cache_matrix factors of a level: band records (3D) or dense records (2D),
+// plus the dense records and node list of the 3D patches that need them
+struct FactorStore {
+  const double* fac = nullptr;
+  const int* fpiv = nullptr;
+  const double* facd = nullptr;
+  const int* fpivd = nullptr;
+  const int* lnode = nullptr;
+  const int* lrec = nullptr;
+  long long nlist = 0;
+};
+cudaError_t launch_factor_apply(const LevelGeom& g, const double* st, const FactorStore& f,
+                                const unsigned char* mask, const double* rpad, double omega, double* x,
+                                const int* prow, cudaStream_t s);
+inline FactorStore factor_store(const Level& L) {
+  FactorStore f;
+  f.fac = L.fac;
+  f.fpiv = L.fpiv;
+  f.facd = L.facd;
+  f.fpivd = L.fpivd;
+  f.lnode = L.lnode;
+  f.lrec = L.lrec;
+  f.nlist = L.nlist;
+  return f;
+}
+// 3D band factor records (cache_matrix) by the banded LDL^T; non-positive-
+// definite patches go to redo_node / redo_out and are marked pending
+cudaError_t launch_band_factors(const LevelGeom& g, const double* st, const unsigned char* mask, double* fac,
+                                int* fpiv, unsigned* d_err, const int* work, long long nwork, int* redo_node,
+                                int* redo_out, int* nredo, cudaStream_t s);
+// dense factor records (records 0 .. nredo-1 of facd / fpivd) of the redo
+// patches, and their index in the band records' int field
+cudaError_t launch_dense_factor_redo(const LevelGeom& g, const double* st, const unsigned char* mask, double* facd,
+                                     int* fpivd, unsigned* d_err, const int* redo_node, const int* redo_out, int nredo,
+                                     int* fpiv, cudaStream_t s);
+// nodes whose record (through prow) is dense
+cudaError_t launch_dense_list(const LevelGeom& g, const int* prow, const int* fpiv, int* lnode, int* lrec,
+                              int* nlist, cudaStream_t s);
 cudaError_t launch_convert_rows(const LevelGeom& g, fc_prec prec, const double* coef64, void* out,
                                 long long nblocks, cudaStream_t s);
 // float-pair smoother pieces: split float64 into (hi, lo) pairs; pair
@@ -447,6 +489,8 @@ cudaError_t launch_patch_apply_df2(const LevelGeom& g, const void* coef, const u
                                    const int* cls_blk, cudaStream_t s);
 size_t factor_doubles(int dim);
 size_t factor_ints(int dim);
+size_t dense_factor_doubles(int dim);
+size_t dense_factor_ints(int dim);
 // coarse solve (fc_mg.cu)
 cudaError_t launch_coarse_factor(const LevelGeom& g, const double* st, const unsigned char* mask,
                                  double* work, double* inv, int* piv, double* dsc, unsigned* d_err,

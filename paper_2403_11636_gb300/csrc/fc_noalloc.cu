@@ -103,7 +103,7 @@ extern "C" fc_status fc_smooth_noalloc(fc_handle h, int level, double* x, const 
     if (inverse)
       e = launch_patch_apply(L.g, prec, L.coef, L.mask, rpad, rpadf, h->opt.omega, x, L.prow, h->stream);
     else if (h->opt.cache == FC_CACHE_MATRIX)
-      e = launch_factor_apply(L.g, L.fac, L.fpiv, L.mask, rpad, h->opt.omega, x, L.prow, h->stream);
+      e = launch_factor_apply(L.g, L.st, factor_store(L), L.mask, rpad, h->opt.omega, x, L.prow, h->stream);
     else
       e = launch_patch_build(L.g, L.st, L.mask, 2, h->opt.omega, nullptr, nullptr, nullptr, rpad, x, h->d_err,
                              nullptr, 0, h->stream);

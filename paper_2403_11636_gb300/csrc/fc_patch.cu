@@ -491,10 +491,21 @@ size_t ldl_rows_smem() {
   return (b + 15) & ~(size_t)15;
 }
 
+// Record of the banded block factors of a 3D patch (cache_matrix), doubles:
+// the band of L with 1/d_k on the diagonal (NU x kBand, column-major), the
+// LU of S~ (row-major), the centre rows w_c of W~_c = K~^{-1} B~_c, du, dp;
+// ints: the pivots of S~ and a dense-record index (-1: banded record).
+constexpr int kBandRec = 125 * kBand + 27 * 27 + 3 * 27 + 125 + 27;
+constexpr int kBandRecI = 27 + 1;
+
+// MODE 0: owned rows (cache_inverse) into coef; MODE 1: the band factor
+// record (cache_matrix) into coef / fpiv.
+template <int MODE>
 __global__ void __launch_bounds__(256, 3)
     patch_rows_ldl_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
-                          double* __restrict__ coef, unsigned* __restrict__ d_err, const int* __restrict__ work,
-                          int* __restrict__ redo_node, int* __restrict__ redo_out, int* __restrict__ nredo) {
+                          double* __restrict__ coef, int* __restrict__ fpiv, unsigned* __restrict__ d_err,
+                          const int* __restrict__ work, int* __restrict__ redo_node, int* __restrict__ redo_out,
+                          int* __restrict__ nredo) {
   constexpr int DIM = 3;
   using P = PatchDims<DIM>;
   constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP, NSLOT = P::NSLOT;
@@ -629,6 +640,7 @@ __global__ void __launch_bounds__(256, 3)
       const int slot = atomicAdd(nredo, 1);
       redo_node[slot] = (int)i;
       redo_out[slot] = (int)widx;
+      if (MODE == 1) fpiv[widx * kBandRecI + NP] = -2;  // dense record pending
     }
     return;
   }
@@ -706,6 +718,18 @@ __global__ void __launch_bounds__(256, 3)
   if (s_flag) {
     if (tid == 0) atomicOr(d_err, kErrSingularPatch);
   }
+  if (MODE == 1) {  // cache_matrix: store the band factors, S~ LU, w_c, du, dp
+    double* rec = coef + widx * kBandRec;
+    for (int e = tid; e < NU * kBand; e += nt) rec[e] = (e & (kBand - 1)) == 0 ? rd[e >> 5] : Lb[e];
+    for (int e = tid; e < NP * NP; e += nt) rec[NU * kBand + e] = S[e];
+    for (int e = tid; e < DIM * NP; e += nt) rec[NU * kBand + NP * NP + e] = w[e];
+    for (int v = tid; v < NU; v += nt) rec[NU * kBand + NP * NP + DIM * NP + v] = du[v];
+    for (int p = tid; p < NP; p += nt) rec[NU * kBand + NP * NP + DIM * NP + NU + p] = dp[p];
+    int* ip = fpiv + widx * kBandRecI;
+    for (int p = tid; p < NP; p += nt) ip[p] = pivS[p];
+    if (tid == 0) ip[NP] = -1;
+    return;
+  }
   if (tid < ND) {
     double* z = zp + tid * NP;
     for (int q = 0; q < NP; ++q) z[q] = tid < DIM ? -w[tid * NP + q] : (q == p0 ? 1.0 : 0.0);
@@ -766,6 +790,135 @@ __global__ void __launch_bounds__(256, 3)
       }
     }
     for (int k = 0; k < ND; ++k) out[(long long)j * ND + k] = vals[k];
+  }
+}
+
+// cache_matrix apply with the banded factor records (3D): one 96-thread CTA
+// per patch.  The record's band and S~ LU are staged in shared memory; warp
+// c solves K~ z_c = (D r)_c (forward, 1/d, backward), then
+//   h = D r_p - sum_c B~_c' z_c       (B~ re-read from the operator),
+//   z_p = S~^{-1} h,   u_c(centre) = z_c(centre) - w_c . z_p,
+// and the owned DoFs take omega D (u, p) (the restricted update).  Patches
+// whose record is dense (index >= 0) are left to the dense apply over its
+// node list.
+__global__ void __launch_bounds__(96)
+    band_factor_apply_kernel(LevelGeom g, const double* __restrict__ st, const double* __restrict__ fac,
+                             const int* __restrict__ fpiv, const unsigned char* __restrict__ mask,
+                             const double* __restrict__ rpad, double omega, double* __restrict__ x,
+                             const int* __restrict__ prow) {
+  constexpr int DIM = 3;
+  using P = PatchDims<DIM>;
+  constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP;
+  constexpr int v0 = 62, p0 = 13;
+  __shared__ __align__(16) double sL[NU * kBand];
+  __shared__ double sS[NP * NP];
+  __shared__ double sz[DIM * NU];
+  __shared__ double sh[NP], szp[NP];
+  __shared__ int spiv[NP];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long i = blockIdx.x;
+  const int pr = prow ? prow[i] : (int)i;
+  const long long blk = pr < 0 ? -(long long)pr - 1 : pr;
+  const int* ip = fpiv + blk * kBandRecI;
+  if (ip[NP] >= 0) return;  // dense record: the dense apply takes this patch
+  const double* rec = fac + blk * kBandRec;
+  const double* wv = rec + NU * kBand + NP * NP;
+  const double* du = wv + DIM * NP;
+  const double* dp = du + NU;
+  {
+    const double2* src = reinterpret_cast<const double2*>(rec);
+    double2* dst = reinterpret_cast<double2*>(sL);
+    for (int e = tid; e < NU * kBand / 2; e += 96) dst[e] = __ldcs(src + e);
+    for (int e = tid; e < NP * NP; e += 96) sS[e] = rec[NU * kBand + e];
+    if (tid < NP) spiv[tid] = ip[tid];
+  }
+  const unsigned nx = (unsigned)g.nn[0], ny = (unsigned)g.nn[1];
+  const int ia[3] = {(int)((unsigned)i % nx), (int)(((unsigned)i / nx) % ny), (int)((unsigned)i / (nx * ny))};
+  const long long pbase = pad_node(g, ia[0], ia[1], ia[2]);
+  const long long px = g.nn[0] + 4, py = g.nn[1] + 4;
+  for (int e = tid; e < DIM * NU; e += 96) {
+    const int c = e / NU, v = e - c * NU;
+    int o[3];
+    vel_off<DIM>(v, o);
+    const int b0 = ia[0] + o[0], b1 = ia[1] + o[1], b2 = ia[2] + o[2];
+    const bool in = b0 >= 0 && b0 <= g.n[0] && b1 >= 0 && b1 <= g.n[1] && b2 >= 0 && b2 <= g.n[2];
+    const bool act = in && !(mask[b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2)] & 1);
+    const long long pn = pbase + o[0] + px * (o[1] + py * o[2]);
+    sz[e] = act ? du[v] * rpad[pn * ND + c] : 0.0;
+  }
+  __syncthreads();
+  {  // z_c = K~^{-1} (D r)_c, one warp per component
+    double* y = sz + warp * NU;
+    band_forward(sL, y, NU, 0, lane);
+    __syncwarp();
+    for (int t = lane; t < NU; t += 32) y[t] *= sL[t * kBand];
+    __syncwarp();
+    band_backward(sL, y, NU, lane);
+  }
+  __syncthreads();
+  if (tid < NP) {  // h = D r_p - sum_c B~_c' z_c
+    const int q = tid;
+    int oq[3];
+    prs_off<DIM>(q, oq);
+    const int c0 = ia[0] + oq[0], c1 = ia[1] + oq[1], c2 = ia[2] + oq[2];
+    const bool qin = c0 >= 0 && c0 <= g.n[0] && c1 >= 0 && c1 <= g.n[1] && c2 >= 0 && c2 <= g.n[2];
+    double hv = 0.0;
+    if (qin) {
+      const long long pq = pbase + oq[0] + px * (oq[1] + py * oq[2]);
+      hv = dp[q] * rpad[pq * ND + DIM];
+      for (int t = 0; t < 27; ++t) {
+        const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1};
+        const int ov[3] = {oq[0] + d[0], oq[1] + d[1], oq[2] + d[2]};
+        const int v = (ov[0] + 2) + 5 * (ov[1] + 2) + 25 * (ov[2] + 2);
+        const int b0 = ia[0] + ov[0], b1 = ia[1] + ov[1], b2 = ia[2] + ov[2];
+        if (b0 < 0 || b0 > g.n[0] || b1 < 0 || b1 > g.n[1] || b2 < 0 || b2 > g.n[2]) continue;
+        const long long bn = b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2);
+        if (mask[bn] & 1) continue;
+        const int dvp[3] = {-d[0], -d[1], -d[2]};  // q relative to v
+        const long long base = (long long)nb_index<DIM>(dvp) * SP;
+        for (int c = 0; c < DIM; ++c)
+          hv = fma(-(du[v] * st[(base + 1 + c) * g.nnodes + bn] * dp[q]), sz[c * NU + v], hv);
+      }
+    }
+    sh[q] = hv;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int q = 0; q < NP; ++q) szp[q] = sh[q];
+    lu_solve_vec(sS, NP, NP, spiv, szp);
+    double y[ND];
+    for (int c = 0; c < DIM; ++c) {
+      double sv = sz[c * NU + v0];
+      for (int q = 0; q < NP; ++q) sv = fma(-wv[c * NP + q], szp[q], sv);
+      y[c] = du[v0] * sv;
+    }
+    y[DIM] = dp[p0] * szp[p0];
+    // restricted update of the node's own DoFs; a constrained velocity
+    // component takes its residual (identity row)
+    const unsigned char m = mask[i];
+    for (int c = 0; c < DIM; ++c)
+      x[i * ND + c] = x[i * ND + c] + (((m >> c) & 1) ? rpad[pbase * ND + c] : omega * y[c]);
+    x[i * ND + DIM] = x[i * ND + DIM] + omega * y[DIM];
+  }
+}
+
+__global__ void mark_dense_records_kernel(const int* __restrict__ redo_out, int n, int* __restrict__ fpiv) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) fpiv[(long long)redo_out[j] * kBandRecI + 27] = j;
+}
+
+// nodes whose record (through prow) is dense, with that dense record's index
+__global__ void dense_list_kernel(long long nnodes, const int* __restrict__ prow, const int* __restrict__ fpiv,
+                                  int* __restrict__ lnode, int* __restrict__ lrec, int* __restrict__ nlist) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nnodes) return;
+  const int pr = prow ? prow[i] : (int)i;
+  const long long blk = pr < 0 ? -(long long)pr - 1 : pr;
+  const int d = fpiv[blk * kBandRecI + 27];
+  if (d >= 0) {
+    const int k = atomicAdd(nlist, 1);
+    lnode[k] = (int)i;
+    lrec[k] = d;
   }
 }
 
@@ -1141,17 +1294,20 @@ template <int DIM>
 __global__ void __launch_bounds__(128)
     factor_apply_kernel(LevelGeom g, const double* __restrict__ fac, const int* __restrict__ fpiv,
                         const unsigned char* __restrict__ mask, const double* __restrict__ rpad,
-                        double omega, double* __restrict__ x, const int* __restrict__ prow) {
+                        double omega, double* __restrict__ x, const int* __restrict__ prow,
+                        const int* __restrict__ lnode, const int* __restrict__ lrec, long long nlist) {
   using P = PatchDims<DIM>;
   constexpr int NU = P::NU, NP = P::NP, ND = P::ND;
   __shared__ double sz[4][DIM * NU + 2 * NP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (i >= g.nnodes) return;
+  // every node through prow, or (lnode) the listed nodes with their records
+  const long long wi = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wi >= (lnode ? nlist : g.nnodes)) return;
+  const long long i = lnode ? (long long)lnode[wi] : wi;
   double* z = sz[wib];             // DIM vectors of NU (component-major)
   double* t = z + DIM * NU;        // NP
   double* zpv = t + NP;            // NP
-  const int pr = prow ? prow[i] : (int)i;
+  const int pr = lnode ? lrec[wi] : (prow ? prow[i] : (int)i);
   const long long blk = pr < 0 ? -(long long)pr - 1 : pr;
   const double* rec = fac + blk * (long long)P::REC;
   const double* LUc = rec;                        // column-major
@@ -3132,8 +3288,10 @@ __global__ void __launch_bounds__(256)
 
 }  // namespace
 
-size_t factor_doubles(int dim) { return dim == 3 ? PatchDims<3>::REC : PatchDims<2>::REC; }
-size_t factor_ints(int dim) { return dim == 3 ? PatchDims<3>::RECI : PatchDims<2>::RECI; }
+size_t factor_doubles(int dim) { return dim == 3 ? (size_t)kBandRec : PatchDims<2>::REC; }
+size_t factor_ints(int dim) { return dim == 3 ? (size_t)kBandRecI : PatchDims<2>::RECI; }
+size_t dense_factor_doubles(int dim) { return dim == 3 ? PatchDims<3>::REC : PatchDims<2>::REC; }
+size_t dense_factor_ints(int dim) { return dim == 3 ? PatchDims<3>::RECI : PatchDims<2>::RECI; }
 
 cudaError_t launch_patch_build(const LevelGeom& g, const double* st, const unsigned char* mask, int mode,
                                double omega, double* coef64, double* fac, int* fpiv,
@@ -3154,11 +3312,12 @@ cudaError_t launch_patch_rows_ldl(const LevelGeom& g, const double* st, const un
                                   int* redo_node, int* redo_out, int* nredo, cudaStream_t s) {
   if (g.dim != 3) return cudaErrorInvalidValue;
   const size_t sm = ldl_rows_smem<3>();
-  cudaError_t e = cudaFuncSetAttribute(patch_rows_ldl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(patch_rows_ldl_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const long long nb = work ? nwork : g.nnodes;
   if (nb <= 0) return cudaSuccess;
-  patch_rows_ldl_kernel<<<(unsigned)nb, 256, sm, s>>>(g, st, mask, coef64, d_err, work, redo_node, redo_out, nredo);
+  patch_rows_ldl_kernel<0><<<(unsigned)nb, 256, sm, s>>>(g, st, mask, coef64, nullptr, d_err, work, redo_node, redo_out,
+                                                         nredo);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -3231,13 +3390,57 @@ cudaError_t launch_patch_apply_df2(const LevelGeom& g, const void* coef, const u
   return run_df_persistent<3>(g, (const float2*)coef, mask, (const float2*)rpad2, xp2, om2, prow, cls, s);
 }
 
-cudaError_t launch_factor_apply(const LevelGeom& g, const double* fac, const int* fpiv,
+cudaError_t launch_factor_apply(const LevelGeom& g, const double* st, const FactorStore& f,
                                 const unsigned char* mask, const double* rpad, double omega, double* x,
                                 const int* prow, cudaStream_t s) {
-  long long threads = g.nnodes * 32;
-  unsigned blocks = (unsigned)((threads + 127) / 128);
-  if (g.dim == 2) factor_apply_kernel<2><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x, prow);
-  else factor_apply_kernel<3><<<blocks, 128, 0, s>>>(g, fac, fpiv, mask, rpad, omega, x, prow);
+  if (g.dim == 2) {
+    long long threads = g.nnodes * 32;
+    unsigned blocks = (unsigned)((threads + 127) / 128);
+    factor_apply_kernel<2><<<blocks, 128, 0, s>>>(g, f.fac, f.fpiv, mask, rpad, omega, x, prow, nullptr, nullptr, 0);
+    note_launches(1);
+    return cudaGetLastError();
+  }
+  band_factor_apply_kernel<<<(unsigned)g.nnodes, 96, 0, s>>>(g, st, f.fac, f.fpiv, mask, rpad, omega, x, prow);
+  note_launches(1);
+  if (f.nlist > 0) {
+    const long long threads = f.nlist * 32;
+    const unsigned blocks = (unsigned)((threads + 127) / 128);
+    factor_apply_kernel<3><<<blocks, 128, 0, s>>>(g, f.facd, f.fpivd, mask, rpad, omega, x, nullptr, f.lnode, f.lrec,
+                                                  f.nlist);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_factors(const LevelGeom& g, const double* st, const unsigned char* mask, double* fac,
+                                int* fpiv, unsigned* d_err, const int* work, long long nwork, int* redo_node,
+                                int* redo_out, int* nredo, cudaStream_t s) {
+  if (g.dim != 3) return cudaErrorInvalidValue;
+  const size_t sm = ldl_rows_smem<3>();
+  cudaError_t e = cudaFuncSetAttribute(patch_rows_ldl_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long long nb = work ? nwork : g.nnodes;
+  if (nb <= 0) return cudaSuccess;
+  patch_rows_ldl_kernel<1><<<(unsigned)nb, 256, sm, s>>>(g, st, mask, fac, fpiv, d_err, work, redo_node, redo_out,
+                                                         nredo);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_factor_redo(const LevelGeom& g, const double* st, const unsigned char* mask, double* facd,
+                                     int* fpivd, unsigned* d_err, const int* redo_node, const int* redo_out, int nredo,
+                                     int* fpiv, cudaStream_t s) {
+  if (g.dim != 3 || nredo <= 0) return cudaSuccess;
+  cudaError_t e = run_factor<3, 1>(g, st, mask, 0.0, nullptr, facd, fpivd, nullptr, nullptr, d_err, redo_node, nredo, s);
+  if (e != cudaSuccess) return e;
+  mark_dense_records_kernel<<<(unsigned)((nredo + 255) / 256), 256, 0, s>>>(redo_out, nredo, fpiv);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_list(const LevelGeom& g, const int* prow, const int* fpiv, int* lnode, int* lrec,
+                              int* nlist, cudaStream_t s) {
+  dense_list_kernel<<<(unsigned)((g.nnodes + 255) / 256), 256, 0, s>>>(g.nnodes, prow, fpiv, lnode, lrec, nlist);
   note_launches(1);
   return cudaGetLastError();
 }
