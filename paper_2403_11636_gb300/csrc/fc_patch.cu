@@ -721,7 +721,8 @@ __global__ void __launch_bounds__(256, 3)
   if (MODE == 1) {  // cache_matrix: store the band factors, S~ LU, w_c, du, dp
     double* rec = coef + widx * kBandRec;
     for (int e = tid; e < NU * kBand; e += nt) rec[e] = (e & (kBand - 1)) == 0 ? rd[e >> 5] : Lb[e];
-    for (int e = tid; e < NP * NP; e += nt) rec[NU * kBand + e] = S[e];
+    // S~ LU with the reciprocals of U's diagonal (the apply divides by none)
+    for (int e = tid; e < NP * NP; e += nt) rec[NU * kBand + e] = e / NP == e % NP ? 1.0 / S[e] : S[e];
     for (int e = tid; e < DIM * NP; e += nt) rec[NU * kBand + NP * NP + e] = w[e];
     for (int v = tid; v < NU; v += nt) rec[NU * kBand + NP * NP + DIM * NP + v] = du[v];
     for (int p = tid; p < NP; p += nt) rec[NU * kBand + NP * NP + DIM * NP + NU + p] = dp[p];
@@ -812,8 +813,8 @@ __global__ void __launch_bounds__(96)
   constexpr int v0 = 62, p0 = 13;
   __shared__ __align__(16) double sL[NU * kBand];
   __shared__ double sS[NP * NP];
-  __shared__ double sz[DIM * NU];
-  __shared__ double sh[NP], szp[NP];
+  __shared__ double sz[DIM * NU], szd[DIM * NU];
+  __shared__ double sh[NP];
   __shared__ int spiv[NP];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long i = blockIdx.x;
@@ -847,58 +848,80 @@ __global__ void __launch_bounds__(96)
     sz[e] = act ? du[v] * rpad[pn * ND + c] : 0.0;
   }
   __syncthreads();
-  {  // z_c = K~^{-1} (D r)_c, one warp per component
+  {  // z_c = K~^{-1} (D r)_c, one warp per component; szd = D z_c
     double* y = sz + warp * NU;
     band_forward(sL, y, NU, 0, lane);
     __syncwarp();
     for (int t = lane; t < NU; t += 32) y[t] *= sL[t * kBand];
     __syncwarp();
     band_backward(sL, y, NU, lane);
+    __syncwarp();
+    for (int t = lane; t < NU; t += 32) szd[warp * NU + t] = du[t] * y[t];
   }
   __syncthreads();
-  if (tid < NP) {  // h = D r_p - sum_c B~_c' z_c
-    const int q = tid;
-    int oq[3];
-    prs_off<DIM>(q, oq);
-    const int c0 = ia[0] + oq[0], c1 = ia[1] + oq[1], c2 = ia[2] + oq[2];
-    const bool qin = c0 >= 0 && c0 <= g.n[0] && c1 >= 0 && c1 <= g.n[1] && c2 >= 0 && c2 <= g.n[2];
+  if (warp == 0) {
+    // h = D r_p - sum_c B~_c' z_c = dp (r_p - sum_c B_c' D z_c), lane q
     double hv = 0.0;
-    if (qin) {
-      const long long pq = pbase + oq[0] + px * (oq[1] + py * oq[2]);
-      hv = dp[q] * rpad[pq * ND + DIM];
-      for (int t = 0; t < 27; ++t) {
-        const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1};
-        const int ov[3] = {oq[0] + d[0], oq[1] + d[1], oq[2] + d[2]};
-        const int v = (ov[0] + 2) + 5 * (ov[1] + 2) + 25 * (ov[2] + 2);
-        const int b0 = ia[0] + ov[0], b1 = ia[1] + ov[1], b2 = ia[2] + ov[2];
-        if (b0 < 0 || b0 > g.n[0] || b1 < 0 || b1 > g.n[1] || b2 < 0 || b2 > g.n[2]) continue;
-        const long long bn = b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2);
-        if (mask[bn] & 1) continue;
-        const int dvp[3] = {-d[0], -d[1], -d[2]};  // q relative to v
-        const long long base = (long long)nb_index<DIM>(dvp) * SP;
-        for (int c = 0; c < DIM; ++c)
-          hv = fma(-(du[v] * st[(base + 1 + c) * g.nnodes + bn] * dp[q]), sz[c * NU + v], hv);
+    if (lane < NP) {
+      const int q = lane;
+      int oq[3];
+      prs_off<DIM>(q, oq);
+      const int c0 = ia[0] + oq[0], c1 = ia[1] + oq[1], c2 = ia[2] + oq[2];
+      const bool qin = c0 >= 0 && c0 <= g.n[0] && c1 >= 0 && c1 <= g.n[1] && c2 >= 0 && c2 <= g.n[2];
+      if (qin) {
+        const long long pq = pbase + oq[0] + px * (oq[1] + py * oq[2]);
+        double acc = rpad[pq * ND + DIM];
+        for (int t = 0; t < 27; ++t) {
+          const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1};
+          const int ov[3] = {oq[0] + d[0], oq[1] + d[1], oq[2] + d[2]};
+          const int v = (ov[0] + 2) + 5 * (ov[1] + 2) + 25 * (ov[2] + 2);
+          const int b0 = ia[0] + ov[0], b1 = ia[1] + ov[1], b2 = ia[2] + ov[2];
+          if (b0 < 0 || b0 > g.n[0] || b1 < 0 || b1 > g.n[1] || b2 < 0 || b2 > g.n[2]) continue;
+          const long long bn = b0 + (long long)g.nn[0] * (b1 + (long long)g.nn[1] * b2);
+          if (mask[bn] & 1) continue;
+          const int dvp[3] = {-d[0], -d[1], -d[2]};  // q relative to v
+          const long long base = (long long)nb_index<DIM>(dvp) * SP;
+          for (int c = 0; c < DIM; ++c) acc = fma(-st[(base + 1 + c) * g.nnodes + bn], szd[c * NU + v], acc);
+        }
+        hv = dp[q] * acc;
       }
+      sh[q] = hv;
     }
-    sh[q] = hv;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int q = 0; q < NP; ++q) szp[q] = sh[q];
-    lu_solve_vec(sS, NP, NP, spiv, szp);
+    __syncwarp();
+    // z_p = S~^{-1} h: row interchanges, then lane r carries z_p(r) through
+    // the column steps of L (unit) and U (reciprocal diagonal stored)
+    if (lane == 0)
+      for (int k = 0; k < NP; ++k) {
+        const int pk = spiv[k];
+        if (pk != k) { const double t0 = sh[k]; sh[k] = sh[pk]; sh[pk] = t0; }
+      }
+    __syncwarp();
+    double z = lane < NP ? sh[lane] : 0.0;
+    for (int k = 0; k < NP - 1; ++k) {
+      const double zk = __shfl_sync(0xffffffffu, z, k);
+      if (lane > k && lane < NP) z = fma(-sS[lane * NP + k], zk, z);
+    }
+    for (int k = NP - 1; k >= 0; --k) {
+      const double zk = __shfl_sync(0xffffffffu, z, k) * sS[k * NP + k];
+      if (lane == k) z = zk;
+      if (lane < k) z = fma(-sS[lane * NP + k], zk, z);
+    }
+    // owned update: u_c(centre) = z_c(centre) - w_c . z_p
     double y[ND];
     for (int c = 0; c < DIM; ++c) {
-      double sv = sz[c * NU + v0];
-      for (int q = 0; q < NP; ++q) sv = fma(-wv[c * NP + q], szp[q], sv);
-      y[c] = du[v0] * sv;
+      double pc = lane < NP ? wv[c * NP + lane] * z : 0.0;
+      for (int o = 16; o > 0; o >>= 1) pc += __shfl_xor_sync(0xffffffffu, pc, o);
+      y[c] = du[v0] * (sz[c * NU + v0] - pc);
     }
-    y[DIM] = dp[p0] * szp[p0];
-    // restricted update of the node's own DoFs; a constrained velocity
-    // component takes its residual (identity row)
-    const unsigned char m = mask[i];
-    for (int c = 0; c < DIM; ++c)
-      x[i * ND + c] = x[i * ND + c] + (((m >> c) & 1) ? rpad[pbase * ND + c] : omega * y[c]);
-    x[i * ND + DIM] = x[i * ND + DIM] + omega * y[DIM];
+    y[DIM] = dp[p0] * __shfl_sync(0xffffffffu, z, p0);
+    if (lane == 0) {
+      // restricted update of the node's own DoFs; a constrained velocity
+      // component takes its residual (identity row)
+      const unsigned char m = mask[i];
+      for (int c = 0; c < DIM; ++c)
+        x[i * ND + c] = x[i * ND + c] + (((m >> c) & 1) ? rpad[pbase * ND + c] : omega * y[c]);
+      x[i * ND + DIM] = x[i * ND + DIM] + omega * y[DIM];
+    }
   }
 }
 
