@@ -482,6 +482,31 @@ __device__ __forceinline__ void band_backward(const double* Lb, double* y, int n
   }
 }
 
+// Work items of the Schur products of the 3D band kernel: the 378 pairs
+// p <= q of S~ (item e, row-major over the upper triangle) and the 27
+// centre-row products (items 378 + q), ordered by the first row their dot
+// product reads (max of the two columns' first structural nonzeros), so the
+// lanes of a warp run loops of similar length.
+struct SchurOrder {
+  unsigned short e[27 * 28 / 2 + 27];
+};
+__host__ __device__ constexpr int first_row_of(int q) { return (q % 3) + 5 * ((q / 3) % 3) + 25 * (q / 9); }
+constexpr SchurOrder make_schur_order() {
+  SchurOrder o{};
+  constexpr int NP = 27, NPAIR = NP * (NP + 1) / 2;
+  int key[NPAIR + NP] = {};
+  int e = 0;
+  for (int p = 0; p < NP; ++p)
+    for (int q = p; q < NP; ++q, ++e) key[e] = first_row_of(p) > first_row_of(q) ? first_row_of(p) : first_row_of(q);
+  for (int q = 0; q < NP; ++q, ++e) key[e] = first_row_of(q) > 62 ? first_row_of(q) : 62;
+  int n = 0;
+  for (int k = 0; k < 125; ++k)
+    for (int j = 0; j < NPAIR + NP; ++j)
+      if (key[j] == k) o.e[n++] = (unsigned short)j;
+  return o;
+}
+__constant__ SchurOrder kSchurOrder = make_schur_order();
+
 template <int DIM>
 size_t ldl_rows_smem() {
   using P = PatchDims<DIM>;
@@ -620,7 +645,7 @@ __global__ void __launch_bounds__(256, 3)
     if (warp == 0) {
       const double dk = Lb[k * kBand];
       const double u = Lb[k * kBand + lane];
-      const double r = 1.0 / dk;
+      const double r = __drcp_rn(dk);  // 1 / d_k, correctly rounded
       if (lane == 0) {
         rd[k] = r;
         if (!(dk > 1e-14)) s_fail = 1;
@@ -683,30 +708,23 @@ __global__ void __launch_bounds__(256, 3)
     }
     __syncthreads();
     constexpr int NPAIR = NP * (NP + 1) / 2;
-    for (int e = tid; e < NPAIR + NP; e += nt) {
+    for (int it = tid; it < NPAIR + NP; it += nt) {
+      const int e = kSchurOrder.e[it];
       if (e < NPAIR) {
         int p = 0, r = e;
         while (r >= NP - p) { r -= NP - p; ++p; }
         const int q = p + r;
-        int op[3], oq[3];
-        prs_off<DIM>(p, op);
-        prs_off<DIM>(q, oq);
-        const int fp = (op[0] + 1) + 5 * (op[1] + 1) + 25 * (op[2] + 1);
-        const int fq = (oq[0] + 1) + 5 * (oq[1] + 1) + 25 * (oq[2] + 1);
         const double* yp = Y + p * NU;
         const double* yq = Y + q * NU;
         double acc = 0.0;
-        for (int t = max(fp, fq); t < NU; ++t) acc = fma(yp[t], yq[t], acc);
+        for (int t = max(first_row_of(p), first_row_of(q)); t < NU; ++t) acc = fma(yp[t], yq[t], acc);
         S[p * NP + q] -= acc;
         if (p != q) S[q * NP + p] -= acc;
       } else {
         const int q = e - NPAIR;
-        int oq[3];
-        prs_off<DIM>(q, oq);
-        const int fq = (oq[0] + 1) + 5 * (oq[1] + 1) + 25 * (oq[2] + 1);
         const double* yq = Y + q * NU;
         double acc = 0.0;
-        for (int t = max(fq, v0); t < NU; ++t) acc = fma(sh[t], yq[t], acc);
+        for (int t = max(first_row_of(q), v0); t < NU; ++t) acc = fma(sh[t], yq[t], acc);
         w[c * NP + q] = acc;
       }
     }
