@@ -447,9 +447,11 @@ __global__ void __launch_bounds__(1024)
 // patch_factor_kernel, with the same result up to rounding.  The band solves
 // run one column per warp: lane l carries entry k + l of the column through
 // step k, so a step is one FMA per lane and two shuffles, no block barrier.
-// A pivot d_k <= 1e-14 (K~ not positive definite to working accuracy) puts
-// the patch on a redo list for the pivoted dense LU (patch_factor_kernel
-// mode 0 with an output index).
+// A pivot d_k <= dmin (1e-14: K~ not positive definite to working accuracy)
+// puts the patch on a redo list for the pivoted dense LU (patch_factor_kernel
+// mode 0 with an output index).  FC_LDL_MIN_PIVOT overrides dmin (a value
+// above 1 sends every patch to the dense LU, which validation runs use to
+// compare the two paths).
 constexpr int kBand = 32;       // stored band per column: diagonal + 31 below
 constexpr int kTri = 31 * 32 / 2;  // trailing-update pairs (l, m), 1 <= m <= l <= 31
 
@@ -507,6 +509,15 @@ constexpr SchurOrder make_schur_order() {
 }
 __constant__ SchurOrder kSchurOrder = make_schur_order();
 
+double ldl_min_pivot() {
+  if (const char* env = getenv("FC_LDL_MIN_PIVOT")) {
+    char* end = nullptr;
+    const double v = strtod(env, &end);
+    if (end != env && v >= 0.0) return v;
+  }
+  return 1e-14;
+}
+
 template <int DIM>
 size_t ldl_rows_smem() {
   using P = PatchDims<DIM>;
@@ -530,7 +541,7 @@ __global__ void __launch_bounds__(256, 3)
     patch_rows_ldl_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
                           double* __restrict__ coef, int* __restrict__ fpiv, unsigned* __restrict__ d_err,
                           const int* __restrict__ work, int* __restrict__ redo_node, int* __restrict__ redo_out,
-                          int* __restrict__ nredo) {
+                          int* __restrict__ nredo, double dmin) {
   constexpr int DIM = 3;
   using P = PatchDims<DIM>;
   constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP, NSLOT = P::NSLOT;
@@ -648,7 +659,7 @@ __global__ void __launch_bounds__(256, 3)
       const double r = __drcp_rn(dk);  // 1 / d_k, correctly rounded
       if (lane == 0) {
         rd[k] = r;
-        if (!(dk > 1e-14)) s_fail = 1;
+        if (!(dk > dmin)) s_fail = 1;
       }
       colU[lane] = u;
       if (lane > 0) Lb[k * kBand + lane] = u * r;
@@ -3358,7 +3369,7 @@ cudaError_t launch_patch_rows_ldl(const LevelGeom& g, const double* st, const un
   const long long nb = work ? nwork : g.nnodes;
   if (nb <= 0) return cudaSuccess;
   patch_rows_ldl_kernel<0><<<(unsigned)nb, 256, sm, s>>>(g, st, mask, coef64, nullptr, d_err, work, redo_node, redo_out,
-                                                         nredo);
+                                                         nredo, ldl_min_pivot());
   note_launches(1);
   return cudaGetLastError();
 }
@@ -3463,7 +3474,7 @@ cudaError_t launch_band_factors(const LevelGeom& g, const double* st, const unsi
   const long long nb = work ? nwork : g.nnodes;
   if (nb <= 0) return cudaSuccess;
   patch_rows_ldl_kernel<1><<<(unsigned)nb, 256, sm, s>>>(g, st, mask, fac, fpiv, d_err, work, redo_node, redo_out,
-                                                         nredo);
+                                                         nredo, ldl_min_pivot());
   note_launches(1);
   return cudaGetLastError();
 }
