@@ -35,6 +35,17 @@
  *    after FC_ERR_NOT_CONVERGED and after argument errors.  A handle whose
  *    fc_setup failed answers only fc_last_error, fc_sync and fc_destroy;
  *    every other call returns FC_ERR_INVALID without touching the device.
+ *  - Environment variables (read at setup or first use; unset = the
+ *    defaults, which the results above are measured with).  Tuning: each
+ *    changes a launch shape and so the rounding order only.
+ *      FC_APPLY_TPP       lanes per patch of the float-pair apply (2..32)
+ *      FC_APPLY64_TPP     lanes per 3D patch of the FP64-row apply (4..32)
+ *      FC_AMR_LANES       lanes per patch / node on adaptive levels (4, 8, 16)
+ *      FC_FACTOR_THREADS  threads per CTA of the dense patch factorisations
+ *    Validation: FC_LDL_MIN_PIVOT (default 1e-14) is the smallest pivot the
+ *    banded LDL^T of a 3D patch's velocity block accepts before the patch
+ *    goes to the pivoted dense LU; a value above 1 sends every patch there
+ *    (the two paths give the same rows up to rounding, which tests use).
  */
 #ifndef FC_H
 #define FC_H
