@@ -377,8 +377,8 @@ fc_status smooth_level(fc_handle h, int li, double* x, const double* b, int nswe
       CK(launch_factor_apply(L.g, L.st, factor_store(L), L.mask, L.rpad, h->opt.omega, x, L.prow, h->stream));
     } else {
       ProfScope ps(h, 0, 0.0);
-      CK(launch_patch_build(L.g, L.st, L.mask, 2, h->opt.omega, nullptr, nullptr, nullptr, L.rpad, x,
-                            h->d_err, nullptr, 0, h->stream));
+      CK(launch_none_sweep(L.g, L.st, L.mask, h->opt.omega, L.rpad, x, h->d_err, L.lnode, L.nlist, L.ldl_dmin,
+                           h->stream));
     }
   }
   return FC_OK;
@@ -1294,6 +1294,29 @@ fc_status fc_setup(fc_handle* out, const fc_grid* g, const fc_levelset* ls, doub
           CK(launch_patch_build(G, L.st, L.mask, 1, o->omega, nullptr, L.fac, L.fpiv, nullptr, nullptr,
                                 h->d_err, work, L.nwork, h->stream));
         }
+      } else if (dim == 3) {
+        // cache_none: list once the patches whose velocity block is not
+        // positive definite; every sweep solves them by the dense LU
+        int *rn = nullptr, *ro = nullptr, *nr_d = nullptr;
+        CK(dalloc(h, &rn, (size_t)G.nnodes, -1));
+        CK(dalloc(h, &ro, (size_t)G.nnodes, -1));
+        CK(dalloc(h, &nr_d, 1, -1));
+        CK(cudaMemsetAsync(nr_d, 0, sizeof(int), h->stream));
+        L.ldl_dmin = ldl_min_pivot();
+        CK(launch_none_check(G, L.st, L.mask, h->d_err, rn, ro, nr_d, L.ldl_dmin, h->stream));
+        int nr = 0;
+        CK(cudaMemcpyAsync(&nr, nr_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (nr > 0) {
+          CK(dalloc(h, &L.lnode, (size_t)nr, 1));
+          CK(cudaMemcpyAsync(L.lnode, rn, sizeof(int) * nr, cudaMemcpyDeviceToDevice, h->stream));
+          L.nlist = nr;
+        }
+        h->ldl_fallback += nr;
+        CK(cudaStreamSynchronize(h->stream));
+        dfree(h, rn);
+        dfree(h, ro);
+        dfree(h, nr_d);
       }
       CK(cudaStreamSynchronize(h->stream));
       dfree(h, work);

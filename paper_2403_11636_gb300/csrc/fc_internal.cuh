@@ -169,6 +169,7 @@ struct Level {
   int* lnode = nullptr;
   int* lrec = nullptr;
   long long nlist = 0;
+  double ldl_dmin = 1e-14;  // 3D cache_none: the pivot bound the list was made with
   // level vectors (device)
   double* x = nullptr;          // V-cycle correction on this level
   double* b = nullptr;          // right-hand side on this level
@@ -463,6 +464,17 @@ cudaError_t launch_band_factors(const LevelGeom& g, const double* st, const unsi
 cudaError_t launch_dense_factor_redo(const LevelGeom& g, const double* st, const unsigned char* mask, double* facd,
                                      int* fpivd, unsigned* d_err, const int* redo_node, const int* redo_out, int nredo,
                                      int* fpiv, cudaStream_t s);
+// cache_none in 3D: at setup, list the patches whose velocity block is not
+// positive definite (redo_node, count nredo); per sweep, the banded
+// on-the-fly solve of every patch and the dense one of the listed patches
+// (dmin: the smallest accepted pivot, the same at setup and in every sweep,
+// so that a patch is solved by exactly one of the two kernels)
+double ldl_min_pivot();
+cudaError_t launch_none_check(const LevelGeom& g, const double* st, const unsigned char* mask, unsigned* d_err,
+                              int* redo_node, int* redo_out, int* nredo, double dmin, cudaStream_t s);
+cudaError_t launch_none_sweep(const LevelGeom& g, const double* st, const unsigned char* mask, double omega,
+                              const double* rpad, double* x, unsigned* d_err, const int* dense_nodes,
+                              long long ndense, double dmin, cudaStream_t s);
 // nodes whose record (through prow) is dense
 cudaError_t launch_dense_list(const LevelGeom& g, const int* prow, const int* fpiv, int* lnode, int* lrec,
                               int* nlist, cudaStream_t s);

@@ -105,8 +105,8 @@ extern "C" fc_status fc_smooth_noalloc(fc_handle h, int level, double* x, const 
     else if (h->opt.cache == FC_CACHE_MATRIX)
       e = launch_factor_apply(L.g, L.st, factor_store(L), L.mask, rpad, h->opt.omega, x, L.prow, h->stream);
     else
-      e = launch_patch_build(L.g, L.st, L.mask, 2, h->opt.omega, nullptr, nullptr, nullptr, rpad, x, h->d_err,
-                             nullptr, 0, h->stream);
+      e = launch_none_sweep(L.g, L.st, L.mask, h->opt.omega, rpad, x, h->d_err, L.lnode, L.nlist, L.ldl_dmin,
+                            h->stream);
     if (e != cudaSuccess) return fail(h, FC_ERR_CUDA, cudaGetErrorString(e));
   }
   return FC_OK;

@@ -509,7 +509,7 @@ constexpr SchurOrder make_schur_order() {
 }
 __constant__ SchurOrder kSchurOrder = make_schur_order();
 
-double ldl_min_pivot() {
+double ldl_min_pivot_env() {
   if (const char* env = getenv("FC_LDL_MIN_PIVOT")) {
     char* end = nullptr;
     const double v = strtod(env, &end);
@@ -535,13 +535,17 @@ constexpr int kBandRec = 125 * kBand + 27 * 27 + 3 * 27 + 125 + 27;
 constexpr int kBandRecI = 27 + 1;
 
 // MODE 0: owned rows (cache_inverse) into coef; MODE 1: the band factor
-// record (cache_matrix) into coef / fpiv.
+// record (cache_matrix) into coef / fpiv; MODE 2 (cache_none): solve with
+// the gathered residual rpad and update the owned DoFs of x at once (x null:
+// only factor K~ and list the patches whose block is not positive definite,
+// which a sweep then leaves to the dense on-the-fly kernel).
 template <int MODE>
 __global__ void __launch_bounds__(256, 3)
     patch_rows_ldl_kernel(LevelGeom g, const double* __restrict__ st, const unsigned char* __restrict__ mask,
                           double* __restrict__ coef, int* __restrict__ fpiv, unsigned* __restrict__ d_err,
                           const int* __restrict__ work, int* __restrict__ redo_node, int* __restrict__ redo_out,
-                          int* __restrict__ nredo, double dmin) {
+                          int* __restrict__ nredo, double dmin, const double* __restrict__ rpad,
+                          double* __restrict__ x, double omega) {
   constexpr int DIM = 3;
   using P = PatchDims<DIM>;
   constexpr int NU = P::NU, NP = P::NP, ND = P::ND, SP = P::SP, NSLOT = P::NSLOT;
@@ -672,7 +676,7 @@ __global__ void __launch_bounds__(256, 3)
     __syncthreads();
   }
   if (s_fail) {  // not positive definite: the pivoted dense LU takes the patch
-    if (tid == 0) {
+    if (tid == 0 && nredo) {
       const int slot = atomicAdd(nredo, 1);
       redo_node[slot] = (int)i;
       redo_out[slot] = (int)widx;
@@ -680,6 +684,7 @@ __global__ void __launch_bounds__(256, 3)
     }
     return;
   }
+  if (MODE == 2 && !x) return;  // setup check only
   for (int k = tid; k < NU; k += nt) rsd[k] = sqrt(rd[k]);
   __syncthreads();
 
@@ -746,6 +751,65 @@ __global__ void __launch_bounds__(256, 3)
   cta_lu(S, NP, NP, pivS, &s_flag);
   if (s_flag) {
     if (tid == 0) atomicOr(d_err, kErrSingularPatch);
+  }
+  if (MODE == 2) {
+    // z_c = K~^{-1} (D r)_c, h = D r_p - sum_c B~_c' z_c, z_p = S~^{-1} h,
+    // u_c(centre) = z_c(centre) - w_c . z_p; x[owned] += omega D (u, p)
+    double* zc = Y;   // 3 columns of NU (Y is free after the Schur products)
+    double* hq = zp;  // NP
+    const long long pc = pad_node(g, ia[0], ia[1], ia[2]);
+    const long long px = g.nn[0] + 4, py = g.nn[1] + 4;
+    for (int e = tid; e < DIM * NU; e += nt) {
+      const int c = e / NU, v = e - c * NU;
+      int o[3];
+      vel_off<DIM>(v, o);
+      zc[e] = au[v] ? du[v] * rpad[(pc + o[0] + px * (o[1] + py * o[2])) * ND + c] : 0.0;
+    }
+    __syncthreads();
+    if (warp < DIM) {
+      double* y = zc + warp * NU;
+      band_forward(Lb, y, NU, 0, lane);
+      __syncwarp();
+      for (int t = lane; t < NU; t += 32) y[t] *= rd[t];
+      __syncwarp();
+      band_backward(Lb, y, NU, lane);
+    }
+    __syncthreads();
+    if (tid < NP) {
+      const int q = tid;
+      double hv = 0.0;
+      if (ap[q]) {
+        int oq[3];
+        prs_off<DIM>(q, oq);
+        double acc = rpad[(pc + oq[0] + px * (oq[1] + py * oq[2])) * ND + DIM];
+        for (int t = 0; t < 27; ++t) {
+          const int d[3] = {t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1};
+          const int v = (oq[0] + d[0] + 2) + 5 * (oq[1] + d[1] + 2) + 25 * (oq[2] + d[2] + 2);
+          if (!au[v]) continue;
+          const int dvp[3] = {-d[0], -d[1], -d[2]};  // q relative to v
+          const long long base = (long long)nb_index<DIM>(dvp) * SP;
+          for (int c = 0; c < DIM; ++c) acc = fma(-st[(base + 1 + c) * nn + nodeU[v]] * du[v], zc[c * NU + v], acc);
+        }
+        hv = dp[q] * acc;
+      }
+      hq[q] = hv;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      lu_solve_vec(S, NP, NP, pivS, hq);
+      double y[ND];
+      for (int c = 0; c < DIM; ++c) {
+        double sv = zc[c * NU + v0];
+        for (int q = 0; q < NP; ++q) sv = fma(-w[c * NP + q], hq[q], sv);
+        y[c] = du[v0] * sv;
+      }
+      y[DIM] = dp[p0] * hq[p0];
+      const unsigned char m = mask[i];
+      for (int c = 0; c < DIM; ++c)
+        x[i * ND + c] = x[i * ND + c] + (((m >> c) & 1) ? rpad[pc * ND + c] : omega * y[c]);
+      x[i * ND + DIM] = x[i * ND + DIM] + omega * y[DIM];
+    }
+    return;
   }
   if (MODE == 1) {  // cache_matrix: store the band factors, S~ LU, w_c, du, dp
     double* rec = coef + widx * kBandRec;
@@ -3369,7 +3433,7 @@ cudaError_t launch_patch_rows_ldl(const LevelGeom& g, const double* st, const un
   const long long nb = work ? nwork : g.nnodes;
   if (nb <= 0) return cudaSuccess;
   patch_rows_ldl_kernel<0><<<(unsigned)nb, 256, sm, s>>>(g, st, mask, coef64, nullptr, d_err, work, redo_node, redo_out,
-                                                         nredo, ldl_min_pivot());
+                                                         nredo, ldl_min_pivot_env(), nullptr, nullptr, 0.0);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -3474,9 +3538,36 @@ cudaError_t launch_band_factors(const LevelGeom& g, const double* st, const unsi
   const long long nb = work ? nwork : g.nnodes;
   if (nb <= 0) return cudaSuccess;
   patch_rows_ldl_kernel<1><<<(unsigned)nb, 256, sm, s>>>(g, st, mask, fac, fpiv, d_err, work, redo_node, redo_out,
-                                                         nredo, ldl_min_pivot());
+                                                         nredo, ldl_min_pivot_env(), nullptr, nullptr, 0.0);
   note_launches(1);
   return cudaGetLastError();
+}
+
+cudaError_t launch_none_check(const LevelGeom& g, const double* st, const unsigned char* mask, unsigned* d_err,
+                              int* redo_node, int* redo_out, int* nredo, double dmin, cudaStream_t s) {
+  if (g.dim != 3) return cudaErrorInvalidValue;
+  const size_t sm = ldl_rows_smem<3>();
+  cudaError_t e = cudaFuncSetAttribute(patch_rows_ldl_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  patch_rows_ldl_kernel<2><<<(unsigned)g.nnodes, 256, sm, s>>>(g, st, mask, nullptr, nullptr, d_err, nullptr, redo_node,
+                                                               redo_out, nredo, dmin, nullptr, nullptr, 0.0);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_none_sweep(const LevelGeom& g, const double* st, const unsigned char* mask, double omega,
+                              const double* rpad, double* x, unsigned* d_err, const int* dense_nodes,
+                              long long ndense, double dmin, cudaStream_t s) {
+  if (g.dim != 3) return launch_patch_build(g, st, mask, 2, omega, nullptr, nullptr, nullptr, rpad, x, d_err, nullptr, 0, s);
+  const size_t sm = ldl_rows_smem<3>();
+  cudaError_t e = cudaFuncSetAttribute(patch_rows_ldl_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  patch_rows_ldl_kernel<2><<<(unsigned)g.nnodes, 256, sm, s>>>(g, st, mask, nullptr, nullptr, d_err, nullptr, nullptr,
+                                                               nullptr, nullptr, dmin, rpad, x, omega);
+  note_launches(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || ndense <= 0) return e;
+  return run_factor<3, 2>(g, st, mask, omega, nullptr, nullptr, nullptr, rpad, x, d_err, dense_nodes, ndense, s);
 }
 
 cudaError_t launch_dense_factor_redo(const LevelGeom& g, const double* st, const unsigned char* mask, double* facd,
@@ -3564,6 +3655,8 @@ size_t amr_schur_doubles(int dim, int nv, int np) {
 }
 constexpr size_t kAmrSmemBytes = 216 * 1024;  // + 8 KB of pivots within the 227 KB per CTA
 }  // namespace
+
+double ldl_min_pivot() { return ldl_min_pivot_env(); }
 
 bool amr_patch_rows_in_smem(int dim, int maxn) { return amr_block_doubles(dim, maxn) * 8 <= kAmrSmemBytes; }
 

@@ -128,3 +128,24 @@ def test_shared_class_records_with_dense_fallback(fc):
     assert rel(xb - x0, xd - x0) <= SWEEP_TOL
     band.close()
     dense.close()
+
+
+def test_cache_none_band_and_dense_agree(fc):
+    """cache_none: the banded on-the-fly solve, and the dense one for every
+    patch (all listed at setup), give the oracle's sweep."""
+    p = problem()
+    band = fc.Solver(p, cache="none")
+    dense = solver_all_dense(fc, p, cache="none")
+    assert band.info()["bytes"][5] == 0
+    assert dense.info()["bytes"][5] >= nn_of(p)
+    L = O.Level.from_problem(p)
+    L.assemble()
+    x0 = inputs.random_vector(p, 45)
+    b = inputs.random_vector(p, 46)
+    x_or = L.sweep(b, x0, mode=0)
+    xb = band.smooth(x0, b, nsweeps=1).cpu().numpy()
+    xd = dense.smooth(x0, b, nsweeps=1).cpu().numpy()
+    assert rel(xb - x0, x_or - x0) <= SWEEP_TOL
+    assert rel(xd - x0, x_or - x0) <= SWEEP_TOL
+    band.close()
+    dense.close()
