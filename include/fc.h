@@ -311,9 +311,11 @@ fc_status fc_patch_dofs(fc_handle h, int level, long long node, long long* dofs_
  * peak of fc_setup: everything it keeps, plus the largest setup temporary
  * (element matrices of a level, or the float64 build of reduced-precision
  * rows, which coexists with the converted rows), assuming that no two patches
- * share a stored block (dedup = 1 can only lower the real use), plus 2 % and
- * 8 MiB for small buffers and allocator rounding.  Pure host arithmetic; 0
- * for invalid arguments. */
+ * share a stored block (dedup = 1 can only lower the real use) and, for the
+ * 3D cache_matrix policy, that at most 1 % of the patches need dense factor
+ * records (their velocity block not positive definite; 0.19 % of the 64^3
+ * porous hierarchy), plus 2 % and 8 MiB for small buffers and allocator
+ * rounding.  Pure host arithmetic; 0 for invalid arguments. */
 size_t fc_footprint_estimate(const fc_grid* g, int depth, const fc_options* o);
 
 /* Per-kernel device time of the patch apply, the residual and the whole
