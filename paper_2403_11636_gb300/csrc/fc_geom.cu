@@ -126,6 +126,9 @@ struct Entries {
   // warps per CTA: the per-warp point queue grows with the basis and static
   // shared memory is limited to 48 KB per CTA
   static constexpr int WARPS = Q == 2 ? (DIM == 3 ? 1 : 3) : 4;
+  // CTAs per SM the 3D Q1 kernel is compiled for (at most 128 registers:
+  // the FP64 quadrature is latency-bound, more resident warps hide it)
+  static constexpr int MINB = DIM == 3 && Q == 1 ? 4 : 1;
 };
 
 struct EntryId {
@@ -242,7 +245,7 @@ __device__ bool angular_range(double bx0, double bx1, double by0, double by1, do
 }
 
 template <int DIM, int Q>
-__global__ void __launch_bounds__(Entries<DIM, Q>::WARPS * 32)
+__global__ void __launch_bounds__(Entries<DIM, Q>::WARPS * 32, Entries<DIM, Q>::MINB)
     cell_elements_kernel(LevelGeom g, double* __restrict__ eA, double* __restrict__ eB,
                          double* __restrict__ eF, double* __restrict__ estat,
                          unsigned* __restrict__ d_err, const double* __restrict__ refA,
